@@ -1,0 +1,300 @@
+"""FP64 CPU oracle of the StereoVAE hot path (arXiv 2305.11566).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``; never by the product package.
+
+This module is argument marshalling around ``sv_oracle.c`` (plain C, FP64,
+direct loops; see the header of that file for the passage each function
+follows).  It shares no code with the CUDA library.
+
+Parity status per function (what pins each one, in tests/test_oracle_*.py):
+  downsample4      brute force on tiny images, exact integers
+  zncc_volume      brute-force numpy restatement of Eq. 1-3 on tiny pairs; rho in
+                   [-1, 1]; gain/offset invariance; rho(I, I) = 1; shift recovery
+  zncc_wta         exact integer argmax agrees with FP64 argmax where it is
+                   unambiguous; exact recovery of a constant integer shift
+  upsample4        affine ramps reproduced exactly; torch interpolate at W = 4w
+  conv2d           torch.nn.functional.conv2d in FP64 (library routine),
+                   nearest-x2 via torch interpolate
+  refine_forward   composed of the pinned pieces; layer-by-layer against torch FP64
+  refine_backward  central finite differences in FP64 and torch FP64 autograd
+  end-to-end disparity error vs synthetic ground truth: parity unpinned
+  (random weights; the paper's trained weights and KITTI are absent).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from ctypes import POINTER, c_double, c_float, c_int, c_int32, c_size_t, c_uint8, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sv_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile sv_oracle.c into liboracle.so with gcc (-O2, OpenMP, IEEE math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-fno-fast-math",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = c_void_p
+        L.orc_downsample4.argtypes = [P, c_int, c_int, c_int, P]
+        L.orc_zncc_at.argtypes = [P, P, c_int, c_int, c_int, c_int, c_int, c_int]
+        L.orc_zncc_at.restype = c_double
+        L.orc_zncc_volume.argtypes = [P, P, c_int, c_int, c_int, c_int, P]
+        L.orc_zncc_wta.argtypes = [P, P, c_int, c_int, c_int, c_int, P, P, P]
+        L.orc_upsample4.argtypes = [P, c_int, c_int, c_int, c_int, P]
+        L.orc_upsample4_backward.argtypes = [P, c_int, c_int, c_int, c_int, P]
+        L.orc_conv2d.argtypes = [P, c_int, c_int, c_int, P, P, c_int, c_int, c_int, c_int, c_int, c_int, c_int,
+                                 c_int, P]
+        L.orc_conv2d_backward.argtypes = [P, c_int, c_int, c_int, P, c_int, c_int, c_int, c_int, c_int, c_int,
+                                          c_int, P, P, P, P]
+        L.orc_param_offset.argtypes = [P, c_int, c_int]
+        L.orc_param_offset.restype = c_size_t
+        L.orc_refine_forward.argtypes = [P, P, P, c_int, c_int, c_int, P, c_int, c_int, P, P, P, P, P]
+        L.orc_refine_activation.argtypes = [P, P, P, c_int, c_int, c_int, P, c_int, c_int, P, c_int, P]
+        L.orc_refine_loss.argtypes = [P, P, P, c_int, c_int, c_int, P, c_int, c_int, P, P, c_double, c_double,
+                                      c_double]
+        L.orc_refine_loss.restype = c_double
+        L.orc_refine_backward.argtypes = [P, P, P, c_int, c_int, c_int, P, c_int, c_int, P, P, c_double,
+                                          c_double, c_double, P, P]
+        L.orc_refine_backward.restype = c_double
+        L.orc_adam.argtypes = [P, P, P, P, c_size_t, c_int, c_double, c_double, c_double, c_double]
+        L.orc_num_threads.restype = c_int
+        L.orc_set_threads.argtypes = [c_int]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(c_void_p)
+
+
+def _opt(a):
+    return None if a is None else _p(a)
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(n)
+
+
+# ---------------------------------------------------------------- coarse stage
+def downsample4(img: np.ndarray) -> np.ndarray:
+    """4x4 box sums (int32 [H//4, W//4]) of a uint8 [H, W] image."""
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = img.shape
+    S = np.zeros((H // 4, W // 4), dtype=np.int32)
+    lib().orc_downsample4(_p(img), W, H, W, _p(S))
+    return S
+
+
+def zncc_at(SL, SR, k, x, y, d) -> float:
+    SL = np.ascontiguousarray(SL, dtype=np.int32)
+    SR = np.ascontiguousarray(SR, dtype=np.int32)
+    h, w = SL.shape
+    return lib().orc_zncc_at(_p(SL), _p(SR), w, h, k, x, y, d)
+
+
+def zncc_volume(SL, SR, k: int, D: int) -> np.ndarray:
+    """rho [h, w, D] by Eq. 1-3 in FP64; NaN where x - d < 0."""
+    SL = np.ascontiguousarray(SL, dtype=np.int32)
+    SR = np.ascontiguousarray(SR, dtype=np.int32)
+    h, w = SL.shape
+    rho = np.zeros((h, w, D))
+    lib().orc_zncc_volume(_p(SL), _p(SR), w, h, k, D, _p(rho))
+    return rho
+
+
+def zncc_wta(SL, SR, k: int, D: int):
+    """(disp int32 [h, w], best rho, second-best rho) by Eq. 6, exact integer decisions."""
+    SL = np.ascontiguousarray(SL, dtype=np.int32)
+    SR = np.ascontiguousarray(SR, dtype=np.int32)
+    h, w = SL.shape
+    disp = np.zeros((h, w), dtype=np.int32)
+    best = np.zeros((h, w))
+    second = np.zeros((h, w))
+    lib().orc_zncc_wta(_p(SL), _p(SR), w, h, k, D, _p(disp), _p(best), _p(second))
+    return disp, best, second
+
+
+def coarse_match(left: np.ndarray, right: np.ndarray, k: int, D: int):
+    """Downsample both images and run ZNCC + WTA: (disp, best, second)."""
+    return zncc_wta(downsample4(left), downsample4(right), k, D)
+
+
+def upsample4(disp: np.ndarray, W: int, H: int) -> np.ndarray:
+    d = np.ascontiguousarray(disp, dtype=np.float64)
+    h, w = d.shape
+    U = np.zeros((H, W))
+    lib().orc_upsample4(_p(d), w, h, W, H, _p(U))
+    return U
+
+
+def upsample4_backward(gU: np.ndarray, w: int, h: int) -> np.ndarray:
+    gU = np.ascontiguousarray(gU, dtype=np.float64)
+    H, W = gU.shape
+    g = np.zeros((h, w))
+    lib().orc_upsample4_backward(_p(gU), w, h, W, H, _p(g))
+    return g
+
+
+# ---------------------------------------------------------------- convolution
+def conv2d(x: np.ndarray, wt: np.ndarray, b, stride: int, pad: int, relu: bool = False,
+           up2: bool = False, out_hw=None) -> np.ndarray:
+    """x: [Hi, Wi, Ci] float64; wt: [Co, k, k, Ci] float32; b: [Co] float32 or None."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    wt = np.ascontiguousarray(wt, dtype=np.float32)
+    Hi, Wi, Ci = x.shape
+    Co, ks = wt.shape[0], wt.shape[1]
+    if up2:
+        Ho, Wo = out_hw
+    else:
+        Ho = (Hi + 2 * pad - ks) // stride + 1
+        Wo = (Wi + 2 * pad - ks) // stride + 1
+    out = np.zeros((Ho, Wo, Co))
+    bb = None if b is None else np.ascontiguousarray(b, dtype=np.float32)
+    lib().orc_conv2d(_p(x), Hi, Wi, Ci, _p(wt), _opt(bb), Co, ks, stride, pad, int(up2), Ho, Wo, int(relu), _p(out))
+    return out
+
+
+def conv2d_backward(x, wt, stride, pad, gout, up2=False):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    wt = np.ascontiguousarray(wt, dtype=np.float32)
+    gout = np.ascontiguousarray(gout, dtype=np.float64)
+    Hi, Wi, Ci = x.shape
+    Co, ks = wt.shape[0], wt.shape[1]
+    Ho, Wo = gout.shape[:2]
+    gin = np.zeros_like(x)
+    gw = np.zeros(wt.shape)
+    gb = np.zeros(Co)
+    lib().orc_conv2d_backward(_p(x), Hi, Wi, Ci, _p(wt), Co, ks, stride, pad, int(up2), Ho, Wo, _p(gout), _p(gin),
+                              _p(gw), _p(gb))
+    return gin, gw, gb
+
+
+# ---------------------------------------------------------------- the net
+def widths7(shape) -> np.ndarray:
+    return np.array([*shape.enc, shape.latent, *shape.dec], dtype=np.int32)
+
+
+def level_sizes(H: int, W: int):
+    H1, W1 = (H + 1) // 2, (W + 1) // 2
+    H2, W2 = (H1 + 1) // 2, (W1 + 1) // 2
+    H3, W3 = (H2 + 1) // 2, (W2 + 1) // 2
+    return (H, W), (H1, W1), (H2, W2), (H3, W3)
+
+
+def param_slices(shape):
+    """{layer: (w_offset, w_shape, b_offset, cout)} of the flat parameter vector."""
+    w7 = widths7(shape)
+    out = {}
+    for i, (name, co, ci, k) in enumerate(shape.layers()):
+        ow = lib().orc_param_offset(_p(w7), i, 0)
+        ob = lib().orc_param_offset(_p(w7), i, 1)
+        out[name] = (ow, (co, k, k, ci), ob, co)
+    return out
+
+
+def refine_forward(shape, params: np.ndarray, left: np.ndarray, coarse: np.ndarray, eps=None):
+    """Returns dict with Y, U (float64 [H, W]) and mu, logvar ([H3, W3, lat])."""
+    w7 = widths7(shape)
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    left = np.ascontiguousarray(left, dtype=np.uint8)
+    coarse = np.ascontiguousarray(coarse, dtype=np.float64)
+    H, W = left.shape
+    h, w = coarse.shape
+    _, _, _, (H3, W3) = level_sizes(H, W)
+    Y = np.zeros((H, W))
+    U = np.zeros((H, W))
+    mu = np.zeros((H3, W3, shape.latent))
+    lv = np.zeros((H3, W3, shape.latent))
+    e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float32)
+    lib().orc_refine_forward(_p(w7), _p(params), _p(left), W, H, W, _p(coarse), w, h, _opt(e), _p(Y), _p(U), _p(mu),
+                             _p(lv))
+    return {"Y": Y, "U": U, "mu": mu, "logvar": lv}
+
+
+ACTIVATIONS = ["U", "e1", "e2", "e3", "mu", "logvar", "z", "d1", "d2", "d3", "Y"]
+
+
+def refine_activation(shape, params, left, coarse, which: str, eps=None) -> np.ndarray:
+    w7 = widths7(shape)
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    left = np.ascontiguousarray(left, dtype=np.uint8)
+    coarse = np.ascontiguousarray(coarse, dtype=np.float64)
+    H, W = left.shape
+    h, w = coarse.shape
+    L0, L1, L2, L3 = level_sizes(H, W)
+    c1, c2, c3 = shape.enc
+    d1, d2, d3 = shape.dec
+    dims = {"U": (*L0, 1), "e1": (*L1, c1), "e2": (*L2, c2), "e3": (*L3, c3), "mu": (*L3, shape.latent),
+            "logvar": (*L3, shape.latent), "z": (*L3, shape.latent), "d1": (*L2, d1), "d2": (*L1, d2),
+            "d3": (*L0, d3), "Y": (*L0, 1)}[which]
+    out = np.zeros(dims)
+    e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float32)
+    lib().orc_refine_activation(_p(w7), _p(params), _p(left), W, H, W, _p(coarse), w, h, _opt(e),
+                                ACTIVATIONS.index(which), _p(out))
+    return out
+
+
+def refine_loss(shape, params, left, coarse, eps, gt, n_pix, n_lat, kl_w=1e-3) -> float:
+    w7 = widths7(shape)
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    left = np.ascontiguousarray(left, dtype=np.uint8)
+    coarse = np.ascontiguousarray(coarse, dtype=np.float64)
+    gt = np.ascontiguousarray(gt, dtype=np.float32)
+    H, W = left.shape
+    h, w = coarse.shape
+    e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float32)
+    return lib().orc_refine_loss(_p(w7), _p(params), _p(left), W, H, W, _p(coarse), w, h, _opt(e), _p(gt),
+                                 float(n_pix), float(n_lat), float(kl_w))
+
+
+def refine_backward(shape, params, left, coarse, eps, gt, n_pix, n_lat, kl_w=1e-3, want_coarse=False):
+    """(loss, grad params float64 flat, grad coarse [h, w] or None)."""
+    w7 = widths7(shape)
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    left = np.ascontiguousarray(left, dtype=np.uint8)
+    coarse = np.ascontiguousarray(coarse, dtype=np.float64)
+    gt = np.ascontiguousarray(gt, dtype=np.float32)
+    H, W = left.shape
+    h, w = coarse.shape
+    g = np.zeros(params.size)
+    gc = np.zeros((h, w)) if want_coarse else None
+    e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float32)
+    L = lib().orc_refine_backward(_p(w7), _p(params), _p(left), W, H, W, _p(coarse), w, h, _opt(e), _p(gt),
+                                  float(n_pix), float(n_lat), float(kl_w), _p(g), _opt(gc))
+    return L, g, gc
+
+
+def adam(p, m, v, g, t, lr=5e-4, b1=0.99, b2=0.999, eps=1e-8):
+    """In-place Adam step on float64 arrays."""
+    for a in (p, m, v, g):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    lib().orc_adam(_p(p), _p(m), _p(v), _p(g), p.size, int(t), lr, b1, b2, eps)
+
+
+def pipeline(shape, params, left, right, k, D):
+    """Coarse match + refinement of one pair (inference): returns (Y, disp, best, second)."""
+    disp, best, second = coarse_match(left, right, k, D)
+    out = refine_forward(shape, params, left, disp.astype(np.float64))
+    return out["Y"], disp, best, second

@@ -1,0 +1,609 @@
+/*
+ * sv_oracle.c -- plain FP64 CPU oracle of the StereoVAE hot path
+ * (Chang et al., "StereoVAE: A lightweight stereo-matching system using
+ * embedded GPUs", arXiv 2305.11566).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call this code:
+ * only the tests, the smoke check and the benchmark's CPU-baseline leg load it.
+ * It shares no code, header, table or helper with the CUDA library.
+ *
+ * Every function is the plain definition of one step, written as direct loops
+ * in double precision (integers where the step is integer).  OpenMP only
+ * distributes independent output rows over threads; it never changes the
+ * arithmetic of an output element.
+ *
+ * Steps and the passages they follow:
+ *   orc_downsample4      quarter-size input of the coarse matcher (Sec. I, III-B1, IV-A):
+ *                        4x4 box sums S (integer, no division: ZNCC is gain invariant)
+ *   orc_zncc_at          ZNCC score of one (x, y, d) by Eq. 1-3 with window means
+ *   orc_zncc_wta         winner-take-all of Eq. 6 (argmax of rho = argmin of 1 - rho),
+ *                        decided by exact integer comparison
+ *   orc_upsample4        "linear scaling" of the small map (Sec. IV-C), bilinear x4, values x4
+ *   orc_conv2d           direct convolution (encoder, latent heads, decoder, final layer;
+ *                        Sec. III-B, Table I), optional nearest x2 upsample + crop of its input
+ *   orc_refine_forward   the refinement net and the residual onto the upsampled map
+ *   orc_loss             smooth-L1 reconstruction + KL of the latent (Sec. III-B2, Eq. 9-11)
+ *   orc_refine_backward  hand-derived gradient of orc_loss through the net (FP64)
+ *
+ * Readings of the paper (where it is silent, garbled or inconsistent):
+ *   - cost range: Eq. 1 gives 1 - rho, which lies in [0, 2], not [0, 1]; the
+ *     oracle returns rho in [-1, 1] and WTA takes argmax rho (== argmin 1 - rho).
+ *   - Eq. 1-3 reuse (x, y) as window index; the window is the k x k square of
+ *     offsets (i, j) in [-r, r]^2 around each centre; each window has its own mean.
+ *   - window pixels outside the image take the nearest edge pixel (clamp).
+ *   - a candidate d is valid iff x - d >= 0; d = 0 is always valid.
+ *   - a window with zero variance gives rho = 0 (exact integer test).
+ *   - ties go to the lowest d.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static inline int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+/* ------------------------------------------------------------------ a1
+ * Quarter-size input (Sec. I; Sec. IV-A "initial quarter size"): S(x, y) is the
+ * sum of the 4x4 block of full-resolution pixels (4x+i, 4y+j), i, j < 4.
+ * w = W / 4, h = H / 4 (floor); trailing columns/rows are dropped. */
+void orc_downsample4(const uint8_t* img, int W, int H, int pitch, int32_t* S) {
+  int w = W / 4, h = H / 4;
+  for (int y = 0; y < h; ++y)
+    for (int x = 0; x < w; ++x) {
+      int32_t s = 0;
+      for (int j = 0; j < 4; ++j)
+        for (int i = 0; i < 4; ++i) s += img[(size_t)(4 * y + j) * pitch + 4 * x + i];
+      S[(size_t)y * w + x] = s;
+    }
+}
+
+/* ------------------------------------------------------------------ a2-a3
+ * Eq. 1-3: rho = sum dL * dR / (sigma_L * sigma_R), dI = I - mean over the
+ * window, sigma = sqrt(sum dI^2).  Left window centred at (x, y), right window
+ * centred at (x - d, y).  Returns NAN when x - d < 0 (no candidate). */
+double orc_zncc_at(const int32_t* SL, const int32_t* SR, int w, int h, int k, int x, int y, int d) {
+  if (x - d < 0) return NAN;
+  const int r = k / 2;
+  const int N = k * k;
+  double mL = 0.0, mR = 0.0;
+  for (int j = -r; j <= r; ++j)
+    for (int i = -r; i <= r; ++i) {
+      int yy = clampi(y + j, 0, h - 1);
+      mL += SL[(size_t)yy * w + clampi(x + i, 0, w - 1)];
+      mR += SR[(size_t)yy * w + clampi(x - d + i, 0, w - 1)];
+    }
+  mL /= N;
+  mR /= N;
+  double num = 0.0, sLL = 0.0, sRR = 0.0;
+  for (int j = -r; j <= r; ++j)
+    for (int i = -r; i <= r; ++i) {
+      int yy = clampi(y + j, 0, h - 1);
+      double dl = SL[(size_t)yy * w + clampi(x + i, 0, w - 1)] - mL;
+      double dr = SR[(size_t)yy * w + clampi(x - d + i, 0, w - 1)] - mR;
+      num += dl * dr;
+      sLL += dl * dl;
+      sRR += dr * dr;
+    }
+  /* zero variance is decided exactly on the integer sums below */
+  int64_t s1 = 0, s2 = 0, t1 = 0, t2 = 0;
+  for (int j = -r; j <= r; ++j)
+    for (int i = -r; i <= r; ++i) {
+      int yy = clampi(y + j, 0, h - 1);
+      int64_t a = SL[(size_t)yy * w + clampi(x + i, 0, w - 1)];
+      int64_t b = SR[(size_t)yy * w + clampi(x - d + i, 0, w - 1)];
+      s1 += a; s2 += a * a; t1 += b; t2 += b * b;
+    }
+  if ((int64_t)N * s2 - s1 * s1 == 0 || (int64_t)N * t2 - t1 * t1 == 0) return 0.0;
+  return num / (sqrt(sLL) * sqrt(sRR));
+}
+
+/* Full cost volume rho[(y * w + x) * D + d] (NAN where x - d < 0). */
+void orc_zncc_volume(const int32_t* SL, const int32_t* SR, int w, int h, int k, int D, double* rho) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int y = 0; y < h; ++y)
+    for (int x = 0; x < w; ++x)
+      for (int d = 0; d < D; ++d) rho[((size_t)y * w + x) * D + d] = orc_zncc_at(SL, SR, w, h, k, x, y, d);
+}
+
+/* Exact window sums for one candidate: n = N*sum(LR) - sum(L)*sum(R),
+ * vL = N*sum(L^2) - sum(L)^2, vR = N*sum(R^2) - sum(R)^2 (all exact integers).
+ * rho = n / sqrt(vL * vR) by Eq. 1-3 after multiplying through by N. */
+static void exact_terms(const int32_t* SL, const int32_t* SR, int w, int h, int k, int x, int y, int d,
+                        int64_t* n, int64_t* vL, int64_t* vR) {
+  const int r = k / 2;
+  const int64_t N = (int64_t)k * k;
+  int64_t sl = 0, sr = 0, sll = 0, srr = 0, slr = 0;
+  for (int j = -r; j <= r; ++j)
+    for (int i = -r; i <= r; ++i) {
+      int yy = clampi(y + j, 0, h - 1);
+      int64_t a = SL[(size_t)yy * w + clampi(x + i, 0, w - 1)];
+      int64_t b = SR[(size_t)yy * w + clampi(x - d + i, 0, w - 1)];
+      sl += a; sr += b; sll += a * a; srr += b * b; slr += a * b;
+    }
+  *n = N * slr - sl * sr;
+  *vL = N * sll - sl * sl;
+  *vR = N * srr - sr * sr;
+}
+
+/* Exact comparison of two candidates at the same pixel (common vL > 0):
+ * rho_1 > rho_2  <=>  n1 / sqrt(vR1) > n2 / sqrt(vR2).  A zero-variance right
+ * window counts as n = 0.  Returns +1, 0, -1. */
+static int cmp_exact(int64_t n1, int64_t v1, int64_t n2, int64_t v2) {
+  if (v1 == 0) n1 = 0, v1 = 1;
+  if (v2 == 0) n2 = 0, v2 = 1;
+  int s1 = (n1 > 0) - (n1 < 0), s2 = (n2 > 0) - (n2 < 0);
+  if (s1 != s2) return s1 > s2 ? 1 : -1;
+  if (s1 == 0) return 0;
+  __int128 a = (__int128)n1 * n1 * v2; /* |n| <= v_max ~ 2.7e10, so n^2 v < 2^127 */
+  __int128 b = (__int128)n2 * n2 * v1;
+  int c = (a > b) - (a < b);
+  return s1 > 0 ? c : -c;
+}
+
+/* Eq. 6 winner-take-all over d in [0, D) restricted to x - d >= 0: disp = argmax rho
+ * (lowest d on exact ties), decided exactly; best = rho(disp), second = largest rho over
+ * the other valid candidates (-2 when there is none), both in FP64 from orc_zncc_at. */
+void orc_zncc_wta(const int32_t* SL, const int32_t* SR, int w, int h, int k, int D,
+                  int32_t* disp, double* best, double* second) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int y = 0; y < h; ++y)
+    for (int x = 0; x < w; ++x) {
+      int64_t bn = 0, bvL = 0, bvR = 0;
+      int bd = 0;
+      exact_terms(SL, SR, w, h, k, x, y, 0, &bn, &bvL, &bvR);
+      int dmax = D - 1 < x ? D - 1 : x;
+      for (int d = 1; d <= dmax; ++d) {
+        int64_t n, vL, vR;
+        exact_terms(SL, SR, w, h, k, x, y, d, &n, &vL, &vR);
+        if (vL == 0) continue; /* every rho is 0: keep d = 0 */
+        if (cmp_exact(n, vR, bn, bvR) > 0) { bn = n; bvR = vR; bd = d; }
+      }
+      disp[(size_t)y * w + x] = bd;
+      double b = orc_zncc_at(SL, SR, w, h, k, x, y, bd);
+      double s = -2.0;
+      for (int d = 0; d <= dmax; ++d) {
+        if (d == bd) continue;
+        double v = orc_zncc_at(SL, SR, w, h, k, x, y, d);
+        if (v > s) s = v;
+      }
+      if (best) best[(size_t)y * w + x] = b;
+      if (second) second[(size_t)y * w + x] = s;
+    }
+}
+
+/* ------------------------------------------------------------------ a5
+ * Linear scaling of the small map to full resolution (Sec. IV-C, "Mini+Linear";
+ * Sec. III-B1: the net refines an upscaled coarse map).  Half-pixel centres:
+ * source coordinate s = (X + 1/2) / 4 - 1/2, clamped to [0, w-1]; bilinear
+ * weights; values multiplied by 4 (disparity in full-resolution pixels). */
+void orc_upsample4(const double* disp, int w, int h, int W, int H, double* U) {
+  for (int Y = 0; Y < H; ++Y) {
+    double sy = (Y + 0.5) / 4.0 - 0.5;
+    if (sy < 0) sy = 0;
+    if (sy > h - 1) sy = h - 1;
+    int y0 = (int)floor(sy);
+    int y1 = y0 + 1 < h ? y0 + 1 : h - 1;
+    double fy = sy - y0;
+    for (int X = 0; X < W; ++X) {
+      double sx = (X + 0.5) / 4.0 - 0.5;
+      if (sx < 0) sx = 0;
+      if (sx > w - 1) sx = w - 1;
+      int x0 = (int)floor(sx);
+      int x1 = x0 + 1 < w ? x0 + 1 : w - 1;
+      double fx = sx - x0;
+      double top = (1 - fx) * disp[(size_t)y0 * w + x0] + fx * disp[(size_t)y0 * w + x1];
+      double bot = (1 - fx) * disp[(size_t)y1 * w + x0] + fx * disp[(size_t)y1 * w + x1];
+      U[(size_t)Y * W + X] = 4.0 * ((1 - fy) * top + fy * bot);
+    }
+  }
+}
+
+/* Transpose of orc_upsample4 (gradient of sum(gU * U) w.r.t. disp). */
+void orc_upsample4_backward(const double* gU, int w, int h, int W, int H, double* gdisp) {
+  memset(gdisp, 0, sizeof(double) * (size_t)w * h);
+  for (int Y = 0; Y < H; ++Y) {
+    double sy = (Y + 0.5) / 4.0 - 0.5;
+    if (sy < 0) sy = 0;
+    if (sy > h - 1) sy = h - 1;
+    int y0 = (int)floor(sy);
+    int y1 = y0 + 1 < h ? y0 + 1 : h - 1;
+    double fy = sy - y0;
+    for (int X = 0; X < W; ++X) {
+      double sx = (X + 0.5) / 4.0 - 0.5;
+      if (sx < 0) sx = 0;
+      if (sx > w - 1) sx = w - 1;
+      int x0 = (int)floor(sx);
+      int x1 = x0 + 1 < w ? x0 + 1 : w - 1;
+      double fx = sx - x0;
+      double g = 4.0 * gU[(size_t)Y * W + X];
+      gdisp[(size_t)y0 * w + x0] += g * (1 - fy) * (1 - fx);
+      gdisp[(size_t)y0 * w + x1] += g * (1 - fy) * fx;
+      gdisp[(size_t)y1 * w + x0] += g * fy * (1 - fx);
+      gdisp[(size_t)y1 * w + x1] += g * fy * fx;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ a7-a11
+ * Direct 2-D convolution, NHWC activations, weights wt[co][ky][kx][ci], bias b[co].
+ * out(y, x, co) = b[co] + sum_{ky, kx, ci} wt * V(y*stride + ky - pad, x*stride + kx - pad, ci)
+ * where V is the input, zero outside [0, Hv) x [0, Wv).  With up2 = 1 the input is
+ * first upsampled by nearest x2 and cropped to (Hv, Wv) = (Ho, Wo):
+ * V(Y, X) = in(Y / 2, X / 2).  relu = 1 applies max(0, .) to the output. */
+void orc_conv2d(const double* in, int Hi, int Wi, int Ci, const float* wt, const float* b, int Co, int ks,
+                int stride, int pad, int up2, int Ho, int Wo, int relu, double* out) {
+  const int Hv = up2 ? Ho : Hi, Wv = up2 ? Wo : Wi;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int y = 0; y < Ho; ++y)
+    for (int x = 0; x < Wo; ++x)
+      for (int co = 0; co < Co; ++co) {
+        double acc = b ? (double)b[co] : 0.0;
+        for (int ky = 0; ky < ks; ++ky) {
+          int vy = y * stride + ky - pad;
+          if (vy < 0 || vy >= Hv) continue;
+          int iy = up2 ? vy / 2 : vy;
+          for (int kx = 0; kx < ks; ++kx) {
+            int vx = x * stride + kx - pad;
+            if (vx < 0 || vx >= Wv) continue;
+            int ix = up2 ? vx / 2 : vx;
+            const double* ip = in + ((size_t)iy * Wi + ix) * Ci;
+            const float* wp = wt + (((size_t)co * ks + ky) * ks + kx) * Ci;
+            for (int ci = 0; ci < Ci; ++ci) acc += (double)wp[ci] * ip[ci];
+          }
+        }
+        if (relu && acc < 0) acc = 0;
+        out[((size_t)y * Wo + x) * Co + co] = acc;
+      }
+}
+
+/* Gradient of orc_conv2d (without the ReLU, which the caller applies to gout):
+ * gin += d/d in, gw += d/d wt, gb += d/d b.  Any of gin/gw/gb may be NULL. */
+void orc_conv2d_backward(const double* in, int Hi, int Wi, int Ci, const float* wt, int Co, int ks, int stride,
+                         int pad, int up2, int Ho, int Wo, const double* gout, double* gin, double* gw, double* gb) {
+  const int Hv = up2 ? Ho : Hi, Wv = up2 ? Wo : Wi;
+  if (gb)
+    for (int co = 0; co < Co; ++co) {
+      double s = 0;
+      for (size_t p = 0; p < (size_t)Ho * Wo; ++p) s += gout[p * Co + co];
+      gb[co] += s;
+    }
+  if (gw) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int co = 0; co < Co; ++co)
+      for (int ky = 0; ky < ks; ++ky)
+        for (int kx = 0; kx < ks; ++kx)
+          for (int ci = 0; ci < Ci; ++ci) {
+            double s = 0;
+            for (int y = 0; y < Ho; ++y) {
+              int vy = y * stride + ky - pad;
+              if (vy < 0 || vy >= Hv) continue;
+              int iy = up2 ? vy / 2 : vy;
+              for (int x = 0; x < Wo; ++x) {
+                int vx = x * stride + kx - pad;
+                if (vx < 0 || vx >= Wv) continue;
+                int ix = up2 ? vx / 2 : vx;
+                s += gout[((size_t)y * Wo + x) * Co + co] * in[((size_t)iy * Wi + ix) * Ci + ci];
+              }
+            }
+            gw[(((size_t)co * ks + ky) * ks + kx) * Ci + ci] += s;
+          }
+  }
+  if (gin) {
+    /* scatter form, serial: every (output, tap) adds wt * gout to the input it read */
+    for (int y = 0; y < Ho; ++y)
+      for (int x = 0; x < Wo; ++x)
+        for (int ky = 0; ky < ks; ++ky) {
+          int vy = y * stride + ky - pad;
+          if (vy < 0 || vy >= Hv) continue;
+          int iy = up2 ? vy / 2 : vy;
+          for (int kx = 0; kx < ks; ++kx) {
+            int vx = x * stride + kx - pad;
+            if (vx < 0 || vx >= Wv) continue;
+            int ix = up2 ? vx / 2 : vx;
+            double* gp = gin + ((size_t)iy * Wi + ix) * Ci;
+            for (int co = 0; co < Co; ++co) {
+              double g = gout[((size_t)y * Wo + x) * Co + co];
+              const float* wp = wt + (((size_t)co * ks + ky) * ks + kx) * Ci;
+              for (int ci = 0; ci < Ci; ++ci) gp[ci] += g * wp[ci];
+            }
+          }
+        }
+  }
+}
+
+/* ------------------------------------------------------------------ the net
+ * Refinement network of the build contract: input x0 = concat(L / 256, U / 256)
+ * at full resolution (Sec. III-B2: inputs normalised, factor 256); encoder
+ * 3 x [3x3 conv stride 2 pad 1, ReLU] with widths enc[0..2]; latent heads
+ * mu, logvar = two 1x1 convs (Table I "mu & sigma", 1x1 kernels); z = mu at
+ * inference, z = mu + eps * exp(logvar / 2) in training (reparameterisation, Eq. 8,
+ * in its standard form); decoder 3 x [nearest x2 upsample cropped to the matching
+ * encoder level, 3x3 conv pad 1, ReLU] with widths dec[0..2]; final 3x3 conv to
+ * 1 channel, no activation, added to U (the residual onto the upsampled map).
+ *
+ * Weight vector: per layer in the order enc1, enc2, enc3, mu, logvar, dec1, dec2,
+ * dec3, final: W[cout][kh][kw][cin] followed by b[cout], FP32. */
+typedef struct {
+  int enc[3];
+  int lat;
+  int dec[3];
+} orc_net;
+
+enum { L_ENC1, L_ENC2, L_ENC3, L_MU, L_LV, L_DEC1, L_DEC2, L_DEC3, L_FINAL, L_COUNT };
+
+static void layer_dims(const orc_net* n, int l, int* co, int* ci, int* ks) {
+  switch (l) {
+    case L_ENC1: *co = n->enc[0]; *ci = 2; *ks = 3; break;
+    case L_ENC2: *co = n->enc[1]; *ci = n->enc[0]; *ks = 3; break;
+    case L_ENC3: *co = n->enc[2]; *ci = n->enc[1]; *ks = 3; break;
+    case L_MU: *co = n->lat; *ci = n->enc[2]; *ks = 1; break;
+    case L_LV: *co = n->lat; *ci = n->enc[2]; *ks = 1; break;
+    case L_DEC1: *co = n->dec[0]; *ci = n->lat; *ks = 3; break;
+    case L_DEC2: *co = n->dec[1]; *ci = n->dec[0]; *ks = 3; break;
+    case L_DEC3: *co = n->dec[2]; *ci = n->dec[1]; *ks = 3; break;
+    default: *co = 1; *ci = n->dec[2]; *ks = 3; break;
+  }
+}
+
+/* offsets of W and b of layer l in the flat vector; returns total count when l == L_COUNT */
+size_t orc_param_offset(const int* widths7, int l, int want_bias) {
+  orc_net n = {{widths7[0], widths7[1], widths7[2]}, widths7[3], {widths7[4], widths7[5], widths7[6]}};
+  size_t off = 0;
+  for (int i = 0; i < L_COUNT; ++i) {
+    int co, ci, ks;
+    layer_dims(&n, i, &co, &ci, &ks);
+    size_t nw = (size_t)co * ks * ks * ci;
+    if (i == l) return want_bias ? off + nw : off;
+    off += nw + co;
+  }
+  return off;
+}
+
+/* Activations of one forward pass (all FP64, NHWC). */
+typedef struct {
+  int H, W, H1, W1, H2, W2, H3, W3;
+  double *U, *x0, *e1, *e2, *e3, *mu, *lv, *z, *d1, *d2, *d3, *Y;
+} orc_acts;
+
+static void level_sizes(int H, int W, orc_acts* a) {
+  a->H = H; a->W = W;
+  a->H1 = (H + 1) / 2; a->W1 = (W + 1) / 2;
+  a->H2 = (a->H1 + 1) / 2; a->W2 = (a->W1 + 1) / 2;
+  a->H3 = (a->H2 + 1) / 2; a->W3 = (a->W2 + 1) / 2;
+}
+
+static void acts_alloc(const orc_net* n, int H, int W, orc_acts* a) {
+  level_sizes(H, W, a);
+  size_t P0 = (size_t)H * W, P1 = (size_t)a->H1 * a->W1, P2 = (size_t)a->H2 * a->W2, P3 = (size_t)a->H3 * a->W3;
+  a->U = calloc(P0, sizeof(double));
+  a->x0 = calloc(P0 * 2, sizeof(double));
+  a->e1 = calloc(P1 * n->enc[0], sizeof(double));
+  a->e2 = calloc(P2 * n->enc[1], sizeof(double));
+  a->e3 = calloc(P3 * n->enc[2], sizeof(double));
+  a->mu = calloc(P3 * n->lat, sizeof(double));
+  a->lv = calloc(P3 * n->lat, sizeof(double));
+  a->z = calloc(P3 * n->lat, sizeof(double));
+  a->d1 = calloc(P2 * n->dec[0], sizeof(double));
+  a->d2 = calloc(P1 * n->dec[1], sizeof(double));
+  a->d3 = calloc(P0 * n->dec[2], sizeof(double));
+  a->Y = calloc(P0, sizeof(double));
+}
+
+static void acts_free(orc_acts* a) {
+  free(a->U); free(a->x0); free(a->e1); free(a->e2); free(a->e3); free(a->mu); free(a->lv);
+  free(a->z); free(a->d1); free(a->d2); free(a->d3); free(a->Y);
+}
+
+static const float* Wl(const float* p, const int* w7, int l) { return p + orc_param_offset(w7, l, 0); }
+static const float* Bl(const float* p, const int* w7, int l) { return p + orc_param_offset(w7, l, 1); }
+
+static void net_forward(const orc_net* n, const int* w7, const float* params, const uint8_t* left, int pitch,
+                        const double* coarse, int w, int h, const float* eps, orc_acts* a) {
+  const int H = a->H, W = a->W;
+  int co, ci, ks;
+  orc_upsample4(coarse, w, h, W, H, a->U);
+  for (int Y = 0; Y < H; ++Y)
+    for (int X = 0; X < W; ++X) {
+      a->x0[((size_t)Y * W + X) * 2 + 0] = left[(size_t)Y * pitch + X] / 256.0;
+      a->x0[((size_t)Y * W + X) * 2 + 1] = a->U[(size_t)Y * W + X] / 256.0;
+    }
+  layer_dims(n, L_ENC1, &co, &ci, &ks);
+  orc_conv2d(a->x0, H, W, 2, Wl(params, w7, L_ENC1), Bl(params, w7, L_ENC1), co, 3, 2, 1, 0, a->H1, a->W1, 1, a->e1);
+  layer_dims(n, L_ENC2, &co, &ci, &ks);
+  orc_conv2d(a->e1, a->H1, a->W1, ci, Wl(params, w7, L_ENC2), Bl(params, w7, L_ENC2), co, 3, 2, 1, 0, a->H2, a->W2, 1, a->e2);
+  layer_dims(n, L_ENC3, &co, &ci, &ks);
+  orc_conv2d(a->e2, a->H2, a->W2, ci, Wl(params, w7, L_ENC3), Bl(params, w7, L_ENC3), co, 3, 2, 1, 0, a->H3, a->W3, 1, a->e3);
+  orc_conv2d(a->e3, a->H3, a->W3, n->enc[2], Wl(params, w7, L_MU), Bl(params, w7, L_MU), n->lat, 1, 1, 0, 0, a->H3, a->W3, 0, a->mu);
+  orc_conv2d(a->e3, a->H3, a->W3, n->enc[2], Wl(params, w7, L_LV), Bl(params, w7, L_LV), n->lat, 1, 1, 0, 0, a->H3, a->W3, 0, a->lv);
+  size_t nl = (size_t)a->H3 * a->W3 * n->lat;
+  for (size_t i = 0; i < nl; ++i) a->z[i] = eps ? a->mu[i] + (double)eps[i] * exp(0.5 * a->lv[i]) : a->mu[i];
+  orc_conv2d(a->z, a->H3, a->W3, n->lat, Wl(params, w7, L_DEC1), Bl(params, w7, L_DEC1), n->dec[0], 3, 1, 1, 1, a->H2, a->W2, 1, a->d1);
+  orc_conv2d(a->d1, a->H2, a->W2, n->dec[0], Wl(params, w7, L_DEC2), Bl(params, w7, L_DEC2), n->dec[1], 3, 1, 1, 1, a->H1, a->W1, 1, a->d2);
+  orc_conv2d(a->d2, a->H1, a->W1, n->dec[1], Wl(params, w7, L_DEC3), Bl(params, w7, L_DEC3), n->dec[2], 3, 1, 1, 1, H, W, 1, a->d3);
+  orc_conv2d(a->d3, H, W, n->dec[2], Wl(params, w7, L_FINAL), Bl(params, w7, L_FINAL), 1, 3, 1, 1, 0, H, W, 0, a->Y);
+  for (size_t p = 0; p < (size_t)H * W; ++p) a->Y[p] += a->U[p];
+}
+
+/* Forward of one pair.  widths7 = {enc0, enc1, enc2, lat, dec0, dec1, dec2}.
+ * coarse: h x w coarse disparities (coarse px, as doubles); eps: latent noise
+ * (H3 * W3 * lat, NULL at inference).  Outputs (each nullable): Y [H*W] refined
+ * disparity, U [H*W], mu and logvar [H3*W3*lat]. */
+void orc_refine_forward(const int* widths7, const float* params, const uint8_t* left, int W, int H, int pitch,
+                        const double* coarse, int w, int h, const float* eps, double* Y, double* U, double* mu,
+                        double* logvar) {
+  orc_net n = {{widths7[0], widths7[1], widths7[2]}, widths7[3], {widths7[4], widths7[5], widths7[6]}};
+  orc_acts a;
+  acts_alloc(&n, H, W, &a);
+  net_forward(&n, widths7, params, left, pitch, coarse, w, h, eps, &a);
+  size_t P0 = (size_t)H * W, nl = (size_t)a.H3 * a.W3 * n.lat;
+  if (Y) memcpy(Y, a.Y, P0 * sizeof(double));
+  if (U) memcpy(U, a.U, P0 * sizeof(double));
+  if (mu) memcpy(mu, a.mu, nl * sizeof(double));
+  if (logvar) memcpy(logvar, a.lv, nl * sizeof(double));
+  acts_free(&a);
+}
+
+/* Intermediate activation of a forward pass, for layer-by-layer checks.
+ * which: 0 U, 1 e1, 2 e2, 3 e3, 4 mu, 5 logvar, 6 z, 7 d1, 8 d2, 9 d3, 10 Y. */
+void orc_refine_activation(const int* widths7, const float* params, const uint8_t* left, int W, int H, int pitch,
+                           const double* coarse, int w, int h, const float* eps, int which, double* out) {
+  orc_net n = {{widths7[0], widths7[1], widths7[2]}, widths7[3], {widths7[4], widths7[5], widths7[6]}};
+  orc_acts a;
+  acts_alloc(&n, H, W, &a);
+  net_forward(&n, widths7, params, left, pitch, coarse, w, h, eps, &a);
+  size_t P0 = (size_t)H * W, P1 = (size_t)a.H1 * a.W1, P2 = (size_t)a.H2 * a.W2, P3 = (size_t)a.H3 * a.W3;
+  const double* src = a.Y;
+  size_t cnt = P0;
+  switch (which) {
+    case 0: src = a.U; cnt = P0; break;
+    case 1: src = a.e1; cnt = P1 * n.enc[0]; break;
+    case 2: src = a.e2; cnt = P2 * n.enc[1]; break;
+    case 3: src = a.e3; cnt = P3 * n.enc[2]; break;
+    case 4: src = a.mu; cnt = P3 * n.lat; break;
+    case 5: src = a.lv; cnt = P3 * n.lat; break;
+    case 6: src = a.z; cnt = P3 * n.lat; break;
+    case 7: src = a.d1; cnt = P2 * n.dec[0]; break;
+    case 8: src = a.d2; cnt = P1 * n.dec[1]; break;
+    case 9: src = a.d3; cnt = P0 * n.dec[2]; break;
+    default: break;
+  }
+  memcpy(out, src, cnt * sizeof(double));
+  acts_free(&a);
+}
+
+/* ------------------------------------------------------------------ a12 loss
+ * Reconstruction term: smooth-L1 with beta = 1 px, summed over pixels and divided
+ * by n_pix (the batch's pixel count); KL term of the latent against N(0, 1),
+ * 0.5 * (mu^2 + exp(lv) - 1 - lv) summed and divided by n_lat, weighted by kl_w.
+ * (Eq. 11 of the paper is garbled; this is its standard VAE form.)
+ * Returns this pair's contribution: rec_sum / n_pix + kl_w * kl_sum / n_lat. */
+double orc_loss(const double* Y, const float* gt, size_t P, const double* mu, const double* lv, size_t nl, double n_pix,
+                double n_lat, double kl_w, double* rec_out, double* kl_out) {
+  double rec = 0, kl = 0;
+  for (size_t p = 0; p < P; ++p) {
+    double e = Y[p] - (double)gt[p];
+    double a = fabs(e);
+    rec += a < 1.0 ? 0.5 * e * e : a - 0.5;
+  }
+  for (size_t i = 0; i < nl; ++i) kl += 0.5 * (mu[i] * mu[i] + exp(lv[i]) - 1.0 - lv[i]);
+  if (rec_out) *rec_out = rec / n_pix;
+  if (kl_out) *kl_out = kl / n_lat;
+  return rec / n_pix + kl_w * kl / n_lat;
+}
+
+/* Loss of one pair by forward pass (training form: eps given). */
+double orc_refine_loss(const int* widths7, const float* params, const uint8_t* left, int W, int H, int pitch,
+                       const double* coarse, int w, int h, const float* eps, const float* gt, double n_pix,
+                       double n_lat, double kl_w) {
+  orc_net n = {{widths7[0], widths7[1], widths7[2]}, widths7[3], {widths7[4], widths7[5], widths7[6]}};
+  orc_acts a;
+  acts_alloc(&n, H, W, &a);
+  net_forward(&n, widths7, params, left, pitch, coarse, w, h, eps, &a);
+  double L = orc_loss(a.Y, gt, (size_t)H * W, a.mu, a.lv, (size_t)a.H3 * a.W3 * n.lat, n_pix, n_lat, kl_w, 0, 0);
+  acts_free(&a);
+  return L;
+}
+
+static void relu_mask(double* g, const double* act, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!(act[i] > 0)) g[i] = 0;
+}
+
+/* Gradient of orc_refine_loss w.r.t. the parameters (added into gparams, FP64,
+ * same layout as params) and, if gcoarse != NULL, w.r.t. the coarse map (both
+ * through the residual and through the network input channel U / 256).
+ * Returns the loss. */
+double orc_refine_backward(const int* widths7, const float* params, const uint8_t* left, int W, int H, int pitch,
+                           const double* coarse, int w, int h, const float* eps, const float* gt, double n_pix,
+                           double n_lat, double kl_w, double* gparams, double* gcoarse) {
+  orc_net n = {{widths7[0], widths7[1], widths7[2]}, widths7[3], {widths7[4], widths7[5], widths7[6]}};
+  orc_acts a;
+  acts_alloc(&n, H, W, &a);
+  net_forward(&n, widths7, params, left, pitch, coarse, w, h, eps, &a);
+  const size_t P0 = (size_t)H * W, P1 = (size_t)a.H1 * a.W1, P2 = (size_t)a.H2 * a.W2, P3 = (size_t)a.H3 * a.W3;
+  const size_t nl = P3 * n.lat;
+  double L = orc_loss(a.Y, gt, P0, a.mu, a.lv, nl, n_pix, n_lat, kl_w, 0, 0);
+#define GW(l) (gparams + orc_param_offset(widths7, l, 0))
+#define GB(l) (gparams + orc_param_offset(widths7, l, 1))
+  double* gY = calloc(P0, sizeof(double));
+  for (size_t p = 0; p < P0; ++p) {
+    double e = a.Y[p] - (double)gt[p];
+    gY[p] = (fabs(e) < 1.0 ? e : (e > 0 ? 1.0 : -1.0)) / n_pix;
+  }
+  double* gU = calloc(P0, sizeof(double));
+  for (size_t p = 0; p < P0; ++p) gU[p] = gY[p]; /* Y = U + r */
+  double* gd3 = calloc(P0 * n.dec[2], sizeof(double));
+  orc_conv2d_backward(a.d3, H, W, n.dec[2], Wl(params, widths7, L_FINAL), 1, 3, 1, 1, 0, H, W, gY, gd3, GW(L_FINAL), GB(L_FINAL));
+  relu_mask(gd3, a.d3, P0 * n.dec[2]);
+  double* gd2 = calloc(P1 * n.dec[1], sizeof(double));
+  orc_conv2d_backward(a.d2, a.H1, a.W1, n.dec[1], Wl(params, widths7, L_DEC3), n.dec[2], 3, 1, 1, 1, H, W, gd3, gd2, GW(L_DEC3), GB(L_DEC3));
+  relu_mask(gd2, a.d2, P1 * n.dec[1]);
+  double* gd1 = calloc(P2 * n.dec[0], sizeof(double));
+  orc_conv2d_backward(a.d1, a.H2, a.W2, n.dec[0], Wl(params, widths7, L_DEC2), n.dec[1], 3, 1, 1, 1, a.H1, a.W1, gd2, gd1, GW(L_DEC2), GB(L_DEC2));
+  relu_mask(gd1, a.d1, P2 * n.dec[0]);
+  double* gz = calloc(nl, sizeof(double));
+  orc_conv2d_backward(a.z, a.H3, a.W3, n.lat, Wl(params, widths7, L_DEC1), n.dec[0], 3, 1, 1, 1, a.H2, a.W2, gd1, gz, GW(L_DEC1), GB(L_DEC1));
+  double* gmu = calloc(nl, sizeof(double));
+  double* glv = calloc(nl, sizeof(double));
+  for (size_t i = 0; i < nl; ++i) {
+    gmu[i] = gz[i] + kl_w * a.mu[i] / n_lat;
+    glv[i] = kl_w * 0.5 * (exp(a.lv[i]) - 1.0) / n_lat;
+    if (eps) glv[i] += gz[i] * (double)eps[i] * 0.5 * exp(0.5 * a.lv[i]);
+  }
+  double* ge3 = calloc(P3 * n.enc[2], sizeof(double));
+  orc_conv2d_backward(a.e3, a.H3, a.W3, n.enc[2], Wl(params, widths7, L_MU), n.lat, 1, 1, 0, 0, a.H3, a.W3, gmu, ge3, GW(L_MU), GB(L_MU));
+  orc_conv2d_backward(a.e3, a.H3, a.W3, n.enc[2], Wl(params, widths7, L_LV), n.lat, 1, 1, 0, 0, a.H3, a.W3, glv, ge3, GW(L_LV), GB(L_LV));
+  relu_mask(ge3, a.e3, P3 * n.enc[2]);
+  double* ge2 = calloc(P2 * n.enc[1], sizeof(double));
+  orc_conv2d_backward(a.e2, a.H2, a.W2, n.enc[1], Wl(params, widths7, L_ENC3), n.enc[2], 3, 2, 1, 0, a.H3, a.W3, ge3, ge2, GW(L_ENC3), GB(L_ENC3));
+  relu_mask(ge2, a.e2, P2 * n.enc[1]);
+  double* ge1 = calloc(P1 * n.enc[0], sizeof(double));
+  orc_conv2d_backward(a.e1, a.H1, a.W1, n.enc[0], Wl(params, widths7, L_ENC2), n.enc[1], 3, 2, 1, 0, a.H2, a.W2, ge2, ge1, GW(L_ENC2), GB(L_ENC2));
+  relu_mask(ge1, a.e1, P1 * n.enc[0]);
+  double* gx0 = calloc(P0 * 2, sizeof(double));
+  orc_conv2d_backward(a.x0, H, W, 2, Wl(params, widths7, L_ENC1), n.enc[0], 3, 2, 1, 0, a.H1, a.W1, ge1, gx0, GW(L_ENC1), GB(L_ENC1));
+  if (gcoarse) {
+    for (size_t p = 0; p < P0; ++p) gU[p] += gx0[p * 2 + 1] / 256.0;
+    orc_upsample4_backward(gU, w, h, W, H, gcoarse);
+  }
+#undef GW
+#undef GB
+  free(gY); free(gU); free(gd3); free(gd2); free(gd1); free(gz); free(gmu); free(glv);
+  free(ge3); free(ge2); free(ge1); free(gx0);
+  acts_free(&a);
+  return L;
+}
+
+/* ------------------------------------------------------------------ Adam
+ * One Adam step (Sec. IV-A: Adam, beta1 = 0.99, beta2 = 0.999, lr 5e-4) on FP64
+ * state: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr * mhat / (sqrt(vhat) + eps)
+ * with bias corrections mhat = m / (1 - b1^t), vhat = v / (1 - b2^t). */
+void orc_adam(double* p, double* m, double* v, const double* g, size_t n, int t, double lr, double b1, double b2,
+              double eps) {
+  double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+  for (size_t i = 0; i < n; ++i) {
+    m[i] = b1 * m[i] + (1 - b1) * g[i];
+    v[i] = b2 * v[i] + (1 - b2) * g[i] * g[i];
+    p[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+  }
+}
