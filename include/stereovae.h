@@ -1,0 +1,184 @@
+/*
+ * stereovae.h -- C ABI of the GB300 StereoVAE hot path (arXiv 2305.11566).
+ *
+ * The library computes, for rectified grayscale stereo pairs:
+ *   1. a quarter-size coarse disparity map: 4x4 box downsampling (Sec. I, IV-A
+ *      "quarter size"), ZNCC matching scores (Eq. 1-3) over d = 0..D-1 and
+ *      winner-take-all (Eq. 6);
+ *   2. its refinement to full resolution by a small VAE-style network
+ *      (Sec. III-B): bilinear x4 upsampling of the coarse map ("linear scaling",
+ *      Sec. IV-C), a stride-2 conv encoder, latent mean / log-variance heads
+ *      (Table I "mu & sigma"), a nearest-x2 upsampling conv decoder and a final
+ *      conv whose output is added to the upsampled coarse map.
+ *
+ * Conventions for every entry point:
+ *   - All image, map and tensor pointers are DEVICE pointers owned by the caller,
+ *     except where a comment says "host".  The context owns its weights and
+ *     workspaces.
+ *   - Work is enqueued asynchronously on the given stream (0 = legacy default
+ *     stream); the call returns once it is enqueued.  Outputs are valid after the
+ *     stream is synchronised.
+ *   - Arguments are validated on the host before anything is launched; an invalid
+ *     call returns SV_ERR_INVALID_ARG (or SV_ERR_UNSUPPORTED) and launches nothing.
+ *     No call aborts, throws or traps.  A CUDA failure returns SV_ERR_CUDA; a
+ *     device-side bounded wait that ran out returns SV_ERR_TIMEOUT.  The text of the
+ *     last error of a context is available from sv_last_error().
+ *   - A context is not thread safe: one host thread at a time.
+ *   - Images are uint8, row-major with a row pitch in bytes; pitch % 16 == 0 and
+ *     base pointers 16-byte aligned (rows are read with 16-byte vector loads).
+ *   - Coarse maps are (height / 4) x (width / 4) (floor), row-major, dense.
+ *   - Full-resolution outputs are height x width FP32, row-major, dense.
+ */
+#ifndef STEREOVAE_H
+#define STEREOVAE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SV_API __attribute__((visibility("default")))
+#else
+#define SV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* sv_stream; /* == cudaStream_t */
+
+typedef enum {
+  SV_OK = 0,
+  SV_ERR_INVALID_ARG = 1,
+  SV_ERR_CUDA = 2,
+  SV_ERR_OOM = 3,
+  SV_ERR_UNSUPPORTED = 4,
+  SV_ERR_TIMEOUT = 5,
+  SV_ERR_STATE = 6
+} sv_status;
+
+/* Arithmetic of the refinement convolutions.
+ * SV_FP32: FP32 CUDA-core direct convolutions (the plain method).
+ * SV_BF16: implicit-GEMM convolutions on the tcgen05 tensor cores, BF16 operands,
+ *          FP32 accumulation; the last conv and the residual stay FP32.
+ * SV_FP64_CHECK: FP64 CUDA-core convolutions, for gradient checks on small crops. */
+typedef enum { SV_FP32 = 0, SV_BF16 = 1, SV_FP64_CHECK = 2 } sv_precision;
+
+/* Network and matcher configuration (copied by sv_create). */
+typedef struct {
+  int window;     /* ZNCC window side k: odd, 3 <= k <= 15 (Eq. 1-3 window W) */
+  int enc_ch[3];  /* encoder widths, each a multiple of 16, <= 256 */
+  int latent_ch;  /* latent (mean / logvar) width, multiple of 16, <= 256 */
+  int dec_ch[3];  /* decoder widths, each a multiple of 16, <= 256 */
+  int precision;  /* sv_precision */
+  int flags;      /* reserved, must be 0 */
+} sv_config;
+
+/* One stereo pair.  left / right: device, [height][pitch] uint8. */
+typedef struct {
+  const uint8_t* left;
+  const uint8_t* right;
+  int width;    /* W >= 4 * window; W / 4 coarse columns */
+  int height;   /* H >= 4 * window; H / 4 coarse rows */
+  int pitch;    /* bytes per row, >= width, multiple of 16 */
+  int max_disp; /* D: candidates d = 0..D-1 coarse pixels; 1 <= D <= 128 and D <= W / 4 */
+} sv_pair;
+
+typedef struct sv_ctx sv_ctx;
+
+/* Status code name (static string). */
+SV_API const char* sv_status_string(sv_status s);
+
+/* Text of the last error on this context ("" if none); valid until the next call. */
+SV_API const char* sv_last_error(const sv_ctx* ctx);
+
+/* Number of FP32 parameters of a configuration.  Flat layout, per layer in the
+ * order enc1, enc2, enc3, mu, logvar, dec1, dec2, dec3, final: W[cout][kh][kw][cin]
+ * then b[cout].  enc1 has cin = 2 (left / 256, upsampled disparity / 256), the
+ * latent heads are 1x1, final has cout = 1; all other kernels are 3x3.
+ * Returns 0 for an invalid configuration. */
+SV_API size_t sv_param_count(const sv_config* cfg);
+
+/* Create a context on CUDA device `device` (made current for the call).
+ * Weights start at zero; set them with sv_set_weights. */
+SV_API sv_status sv_create(const sv_config* cfg, int device, sv_ctx** out);
+
+/* Release a context and everything it owns (synchronises its device). */
+SV_API sv_status sv_destroy(sv_ctx* ctx);
+
+/* Copy n = sv_param_count() FP32 parameters (host or device pointer) into the
+ * context's FP32 master copy and refresh the BF16 / FP64 copies. Synchronous. */
+SV_API sv_status sv_set_weights(sv_ctx* ctx, const float* params, size_t n);
+
+/* Copy the FP32 master parameters out (host or device pointer). Synchronous. */
+SV_API sv_status sv_get_weights(sv_ctx* ctx, float* params, size_t n);
+
+/* Coarse matching of n_pairs pairs (Eq. 1-3, Eq. 6).
+ * For pair i, disp_out[i] receives the (H/4) x (W/4) int16 WTA disparity
+ * d* = argmax_d rho(x, y, d) over valid candidates (x - d >= 0, d < D), lowest d
+ * on ties; rho is the ZNCC of the k x k windows of 4x4 box sums centred at (x, y)
+ * in the left and (x - d, y) in the right image, window pixels clamped to the
+ * image, rho = 0 for a window of zero variance.  best[i] / second[i] (the arrays,
+ * or any of their entries, may be NULL) receive FP32 rho(d*) and the largest rho of
+ * the other valid candidates (-2 when there is none).
+ * All pairs are processed by one launch. */
+SV_API sv_status sv_coarse_match(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, int16_t* const* disp_out,
+                          float* const* best, float* const* second, sv_stream stream);
+
+/* Inference refinement (z = mu) of n_pairs pairs given their coarse maps
+ * (coarse[i]: (H/4) x (W/4) int16, e.g. from sv_coarse_match; values are used as
+ * disparities in coarse pixels).  disp_out[i]: H x W FP32 refined disparity in
+ * full-resolution pixels: Y = U + net(L / 256, U / 256) where U is the bilinear x4
+ * upsampled coarse map times 4. */
+SV_API sv_status sv_refine(sv_ctx* ctx, const sv_pair* pairs, const int16_t* const* coarse, int n_pairs,
+                    float* const* disp_out, sv_stream stream);
+
+/* Coarse matching followed by refinement (sv_coarse_match + sv_refine) with the
+ * coarse maps kept in the context's workspace. */
+SV_API sv_status sv_pipeline(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, float* const* disp_out, sv_stream stream);
+
+/* Training forward of n_pairs pairs: z = mu + eps * exp(logvar / 2) (the
+ * reparameterisation of Eq. 8 in its standard form).  Saves in the context what
+ * sv_refine_backward needs (decoder activations and the latent; the encoder is
+ * recomputed there).  Element type of coarse, eps, disp_out, mu_out and logvar_out
+ * is float for SV_FP32 / SV_BF16 contexts and double for SV_FP64_CHECK contexts.
+ * coarse[i]: (H/4) x (W/4) real-valued coarse map; eps[i], mu_out[i], logvar_out[i]:
+ * latent tensors [H3][W3][latent_ch] with H3 = ceil(ceil(ceil(H/2)/2)/2) (same for W3);
+ * disp_out[i]: H x W. */
+SV_API sv_status sv_refine_train(sv_ctx* ctx, const sv_pair* pairs, const void* const* coarse, const void* const* eps,
+                          int n_pairs, void* const* disp_out, void* const* mu_out, void* const* logvar_out,
+                          sv_stream stream);
+
+/* Backward of the last sv_refine_train on this context.  grad_disp[i],
+ * grad_mu[i], grad_logvar[i]: gradients of the loss w.r.t. that call's outputs
+ * (grad_mu / grad_logvar arrays or entries may be NULL = zero).  grad_params
+ * (device, sv_param_count elements, same element type rule) is OVERWRITTEN with the
+ * gradient summed over the pairs.  grad_coarse (array or entries may be NULL)
+ * receives d loss / d coarse[i] (through the residual and the network input).
+ * Returns SV_ERR_STATE if no training forward preceded it. */
+SV_API sv_status sv_refine_backward(sv_ctx* ctx, const void* const* grad_disp, const void* const* grad_mu,
+                             const void* const* grad_logvar, void* grad_params, void* const* grad_coarse,
+                             sv_stream stream);
+
+/* Loss of Sec. III-B2 as used here: smooth-L1 (beta = 1 px) of disp - gt summed over
+ * all pixels of all pairs and divided by their number, plus kl_weight times the KL
+ * divergence of N(mu, exp(logvar)) from N(0, 1) summed over all latent elements and
+ * divided by their number.  loss_out (device, 3 values of the context's element
+ * type): total, reconstruction, KL.  grad_* (arrays or entries nullable) receive
+ * the gradients of the total w.r.t. disp, mu and logvar.  Element types as for
+ * sv_refine_train; gt[i] is always float. */
+SV_API sv_status sv_loss(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, const void* const* disp, const float* const* gt,
+                  const void* const* mu, const void* const* logvar, double kl_weight, void* loss_out,
+                  void* const* grad_disp, void* const* grad_mu, void* const* grad_logvar, sv_stream stream);
+
+/* One Adam step (Sec. IV-A) on the context's master weights with gradient grad
+ * (device, sv_param_count elements, context element type): t = step (1-based),
+ * m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2, p -= lr mhat / (sqrt(vhat) + eps).
+ * Refreshes the BF16 copies. */
+SV_API sv_status sv_adam_step(sv_ctx* ctx, const void* grad, int step, double lr, double beta1, double beta2, double eps,
+                       sv_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STEREOVAE_H */

@@ -1,0 +1,277 @@
+"""ctypes binding of libstereovae.so (include/stereovae.h).
+
+Argument marshalling only: every step of the hot path runs in the library's CUDA
+kernels.  torch tensors provide device memory and streams.  If the library is
+missing the binding raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_size_t, c_void_p
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import synth
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libstereovae.so")
+
+SV_OK, SV_ERR_INVALID_ARG, SV_ERR_CUDA, SV_ERR_OOM, SV_ERR_UNSUPPORTED, SV_ERR_TIMEOUT, SV_ERR_STATE = range(7)
+SV_FP32, SV_BF16, SV_FP64_CHECK = 0, 1, 2
+PRECISIONS = {"fp32": SV_FP32, "bf16": SV_BF16, "fp64": SV_FP64_CHECK}
+
+
+class SvConfig(ctypes.Structure):
+    _fields_ = [("window", c_int), ("enc_ch", c_int * 3), ("latent_ch", c_int), ("dec_ch", c_int * 3),
+                ("precision", c_int), ("flags", c_int)]
+
+
+class SvPair(ctypes.Structure):
+    _fields_ = [("left", c_void_p), ("right", c_void_p), ("width", c_int), ("height", c_int), ("pitch", c_int),
+                ("max_disp", c_int)]
+
+
+class SvError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+API = {
+    "sv_status_string": ([c_int], c_char_p),
+    "sv_last_error": ([c_void_p], c_char_p),
+    "sv_param_count": ([POINTER(SvConfig)], c_size_t),
+    "sv_create": ([POINTER(SvConfig), c_int, POINTER(c_void_p)], c_int),
+    "sv_destroy": ([c_void_p], c_int),
+    "sv_set_weights": ([c_void_p, c_void_p, c_size_t], c_int),
+    "sv_get_weights": ([c_void_p, c_void_p, c_size_t], c_int),
+    "sv_coarse_match": ([c_void_p, POINTER(SvPair), c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
+                         c_void_p], c_int),
+    "sv_refine": ([c_void_p, POINTER(SvPair), POINTER(c_void_p), c_int, POINTER(c_void_p), c_void_p], c_int),
+    "sv_pipeline": ([c_void_p, POINTER(SvPair), c_int, POINTER(c_void_p), c_void_p], c_int),
+    "sv_refine_train": ([c_void_p, POINTER(SvPair), POINTER(c_void_p), POINTER(c_void_p), c_int, POINTER(c_void_p),
+                         POINTER(c_void_p), POINTER(c_void_p), c_void_p], c_int),
+    "sv_refine_backward": ([c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p), c_void_p,
+                            POINTER(c_void_p), c_void_p], c_int),
+    "sv_loss": ([c_void_p, POINTER(SvPair), c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
+                 POINTER(c_void_p), c_double, c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
+                 c_void_p], c_int),
+    "sv_adam_step": ([c_void_p, c_void_p, c_int, c_double, c_double, c_double, c_double, c_void_p], c_int),
+}
+
+
+def lib():
+    """Load libstereovae.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2305_11566_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in API.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _status_name(s: int) -> str:
+    try:
+        return lib().sv_status_string(s).decode()
+    except Exception:  # pragma: no cover
+        return str(s)
+
+
+def make_config(shape: synth.NetShape, window: int, precision: str | int = "fp32") -> SvConfig:
+    c = SvConfig()
+    c.window = window
+    c.enc_ch[:] = list(shape.enc)
+    c.latent_ch = shape.latent
+    c.dec_ch[:] = list(shape.dec)
+    c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    c.flags = 0
+    return c
+
+
+def param_count(shape: synth.NetShape, window: int = 9) -> int:
+    c = make_config(shape, window)
+    return int(lib().sv_param_count(ctypes.byref(c)))
+
+
+def _ptrs(items):
+    arr = (c_void_p * max(1, len(items)))()
+    for i, t in enumerate(items):
+        arr[i] = None if t is None else t.data_ptr()
+    return arr
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_void_p(s.cuda_stream)
+
+
+@dataclass
+class DevicePair:
+    """A stereo pair resident on the GPU: pitched uint8 images [H, pitch]."""
+    left: "object"
+    right: "object"
+    width: int
+    height: int
+    max_disp: int
+
+    @property
+    def pitch(self) -> int:
+        return int(self.left.stride(0))
+
+    def sv(self) -> SvPair:
+        return SvPair(self.left.data_ptr(), self.right.data_ptr(), self.width, self.height, self.pitch,
+                      self.max_disp)
+
+    @property
+    def coarse_hw(self):
+        return self.height // 4, self.width // 4
+
+
+def to_device(pair: synth.Pair, max_disp: int, device="cuda") -> DevicePair:
+    import torch
+    L = torch.from_numpy(synth.pitched(pair.left)).to(device)
+    R = torch.from_numpy(synth.pitched(pair.right)).to(device)
+    return DevicePair(L, R, pair.width, pair.height, max_disp)
+
+
+def _pairs_array(pairs):
+    arr = (SvPair * max(1, len(pairs)))()
+    for i, p in enumerate(pairs):
+        arr[i] = p.sv()
+    return arr
+
+
+class Context:
+    """One sv_ctx: configuration, weights and workspaces on one GPU."""
+
+    def __init__(self, shape: synth.NetShape, window: int, precision: str = "fp32", device: int = 0):
+        self.shape = shape
+        self.window = window
+        self.precision = precision
+        self.device = device
+        cfg = make_config(shape, window, precision)
+        h = c_void_p()
+        s = lib().sv_create(ctypes.byref(cfg), device, ctypes.byref(h))
+        if s != SV_OK:
+            raise SvError(s, "sv_create failed")
+        self._h = h
+        self.n_params = int(lib().sv_param_count(ctypes.byref(cfg)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, s: int):
+        if s != SV_OK:
+            raise SvError(s, lib().sv_last_error(self._h).decode())
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_weights(self, params):
+        import torch
+        if isinstance(params, np.ndarray):
+            params = np.ascontiguousarray(params, dtype=np.float32)
+            self._check(lib().sv_set_weights(self._h, params.ctypes.data_as(c_void_p), params.size))
+        else:
+            t = params.detach().to(torch.float32).contiguous()
+            self._check(lib().sv_set_weights(self._h, c_void_p(t.data_ptr()), t.numel()))
+
+    def get_weights(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        self._check(lib().sv_get_weights(self._h, out.ctypes.data_as(c_void_p), out.size))
+        return out
+
+    # ---------------------------------------------------------------- inference
+    def coarse_match(self, pairs, scores: bool = False, stream=None, out=None):
+        import torch
+        dev = pairs[0].left.device if pairs else "cuda"
+        disp = out if out is not None else [torch.empty(p.coarse_hw, dtype=torch.int16, device=dev) for p in pairs]
+        best = [torch.empty(p.coarse_hw, dtype=torch.float32, device=dev) for p in pairs] if scores else None
+        second = [torch.empty(p.coarse_hw, dtype=torch.float32, device=dev) for p in pairs] if scores else None
+        self._check(lib().sv_coarse_match(self._h, _pairs_array(pairs), len(pairs), _ptrs(disp),
+                                          _ptrs(best) if scores else None, _ptrs(second) if scores else None,
+                                          _stream(stream)))
+        return (disp, best, second) if scores else disp
+
+    def refine(self, pairs, coarse, stream=None, out=None):
+        import torch
+        outs = out if out is not None else [
+            torch.empty((p.height, p.width), dtype=torch.float32, device=p.left.device) for p in pairs]
+        self._check(lib().sv_refine(self._h, _pairs_array(pairs), _ptrs(coarse), len(pairs), _ptrs(outs),
+                                    _stream(stream)))
+        return outs
+
+    def pipeline(self, pairs, stream=None, out=None):
+        import torch
+        outs = out if out is not None else [
+            torch.empty((p.height, p.width), dtype=torch.float32, device=p.left.device) for p in pairs]
+        self._check(lib().sv_pipeline(self._h, _pairs_array(pairs), len(pairs), _ptrs(outs), _stream(stream)))
+        return outs
+
+    # ---------------------------------------------------------------- training
+    def refine_train(self, pairs, coarse, eps, stream=None):
+        import torch
+        dt = torch.float64 if self.precision == "fp64" else torch.float32
+        dev = pairs[0].left.device
+        Y = [torch.empty((p.height, p.width), dtype=dt, device=dev) for p in pairs]
+        mu, lv = [], []
+        for p in pairs:
+            H3, W3 = latent_hw(p.height, p.width)
+            mu.append(torch.empty((H3, W3, self.shape.latent), dtype=dt, device=dev))
+            lv.append(torch.empty((H3, W3, self.shape.latent), dtype=dt, device=dev))
+        self._check(lib().sv_refine_train(self._h, _pairs_array(pairs), _ptrs(coarse), _ptrs(eps), len(pairs),
+                                          _ptrs(Y), _ptrs(mu), _ptrs(lv), _stream(stream)))
+        return Y, mu, lv
+
+    def refine_backward(self, grad_Y, grad_mu, grad_lv, want_coarse: bool, coarse_like, stream=None):
+        import torch
+        dt = torch.float64 if self.precision == "fp64" else torch.float32
+        dev = grad_Y[0].device
+        gparams = torch.empty(self.n_params, dtype=dt, device=dev)
+        gc = [torch.empty_like(c, dtype=dt) for c in coarse_like] if want_coarse else None
+        self._check(lib().sv_refine_backward(self._h, _ptrs(grad_Y), _ptrs(grad_mu), _ptrs(grad_lv),
+                                             c_void_p(gparams.data_ptr()), _ptrs(gc) if want_coarse else None,
+                                             _stream(stream)))
+        return gparams, gc
+
+    def loss(self, pairs, Y, gt, mu, lv, kl_weight=1e-3, want_grads=True, stream=None):
+        import torch
+        dt = torch.float64 if self.precision == "fp64" else torch.float32
+        dev = Y[0].device
+        out = torch.empty(3, dtype=dt, device=dev)
+        gY = [torch.empty_like(t) for t in Y] if want_grads else None
+        gmu = [torch.empty_like(t) for t in mu] if want_grads else None
+        glv = [torch.empty_like(t) for t in lv] if want_grads else None
+        self._check(lib().sv_loss(self._h, _pairs_array(pairs), len(pairs), _ptrs(Y), _ptrs(gt), _ptrs(mu), _ptrs(lv),
+                                  float(kl_weight), c_void_p(out.data_ptr()),
+                                  _ptrs(gY) if want_grads else None, _ptrs(gmu) if want_grads else None,
+                                  _ptrs(glv) if want_grads else None, _stream(stream)))
+        return out, gY, gmu, glv
+
+    def adam_step(self, grad, step: int, lr=5e-4, beta1=0.99, beta2=0.999, eps=1e-8, stream=None):
+        self._check(lib().sv_adam_step(self._h, c_void_p(grad.data_ptr()), int(step), lr, beta1, beta2, eps,
+                                       _stream(stream)))
+
+
+def latent_hw(H: int, W: int):
+    for _ in range(3):
+        H, W = (H + 1) // 2, (W + 1) // 2
+    return H, W

@@ -1,0 +1,373 @@
+// sv_api.cu -- the C ABI declared in include/stereovae.h: context, argument
+// validation, workspaces and the order of launches of each entry point.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sv_internal.cuh"
+#include "sv_ctx.cuh"
+
+namespace sv {
+
+int NetDims::cout(int l) const {
+  switch (l) {
+    case L_ENC1: case L_ENC2: case L_ENC3: return enc[l - L_ENC1];
+    case L_MU: case L_LV: return lat;
+    case L_DEC1: case L_DEC2: case L_DEC3: return dec[l - L_DEC1];
+    default: return 1;
+  }
+}
+int NetDims::cin(int l) const {
+  switch (l) {
+    case L_ENC1: return 2;
+    case L_ENC2: return enc[0];
+    case L_ENC3: return enc[1];
+    case L_MU: case L_LV: return enc[2];
+    case L_DEC1: return lat;
+    case L_DEC2: return dec[0];
+    case L_DEC3: return dec[1];
+    default: return dec[2];
+  }
+}
+int NetDims::ks(int l) const { return (l == L_MU || l == L_LV) ? 1 : 3; }
+size_t NetDims::w_off(int l) const {
+  size_t o = 0;
+  for (int i = 0; i < l; ++i) o += (size_t)cout(i) * ks(i) * ks(i) * cin(i) + cout(i);
+  return o;
+}
+size_t NetDims::b_off(int l) const { return w_off(l) + (size_t)cout(l) * ks(l) * ks(l) * cin(l); }
+size_t NetDims::count() const { return w_off(L_COUNT); }
+
+cudaError_t DevBuf::ensure(size_t bytes) {
+  if (n >= bytes) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  n = 0;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e == cudaSuccess) n = bytes;
+  return e;
+}
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  n = 0;
+}
+
+namespace {
+
+__global__ void f32_to_f64(const float* a, double* b, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+
+}  // namespace
+
+sv_status Ctx::fail(sv_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  err = buf;
+  return s;
+}
+
+sv_status Ctx::cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return SV_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(SV_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  }
+  return fail(SV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+sv_status Ctx::check_pairs(const sv_pair* pairs, int n_pairs) {
+  if (n_pairs < 0) return fail(SV_ERR_INVALID_ARG, "n_pairs < 0");
+  if (n_pairs > 0 && !pairs) return fail(SV_ERR_INVALID_ARG, "pairs is NULL");
+  const int k = cfg.window;
+  for (int i = 0; i < n_pairs; ++i) {
+    const sv_pair& p = pairs[i];
+    if (!p.left || !p.right) return fail(SV_ERR_INVALID_ARG, "pair %d: NULL image", i);
+    if (((uintptr_t)p.left & 15) || ((uintptr_t)p.right & 15))
+      return fail(SV_ERR_INVALID_ARG, "pair %d: image not 16-byte aligned", i);
+    if (p.pitch % 16 || p.pitch < p.width) return fail(SV_ERR_INVALID_ARG, "pair %d: pitch %d invalid", i, p.pitch);
+    if (p.width < 4 * k || p.height < 4 * k)
+      return fail(SV_ERR_INVALID_ARG, "pair %d: %dx%d smaller than 4 * window", i, p.width, p.height);
+    if (p.width > kMaxSide || p.height > kMaxSide)
+      return fail(SV_ERR_UNSUPPORTED, "pair %d: side above %d", i, kMaxSide);
+    if (p.max_disp < 1 || p.max_disp > kMaxDisp || p.max_disp > p.width / 4)
+      return fail(SV_ERR_INVALID_ARG, "pair %d: max_disp %d outside [1, min(%d, W/4)]", i, p.max_disp, kMaxDisp);
+  }
+  return SV_OK;
+}
+
+// ---------------------------------------------------------------- coarse matching
+sv_status Ctx::coarse(const sv_pair* pairs, int n, int16_t* const* disp, float* const* best, float* const* second,
+                      cudaStream_t st) {
+  std::vector<ZPair> zp(n);
+  std::vector<ZJob> jobs;
+  int maxD = 1;
+  for (int i = 0; i < n; ++i) maxD = std::max(maxD, pairs[i].max_disp);
+  const int gx = kZnccWarps * zncc_tx(zncc_kd(maxD));
+  for (int i = 0; i < n; ++i) {
+    const sv_pair& p = pairs[i];
+    ZPair& z = zp[i];
+    z.L = p.left; z.R = p.right; z.W = p.width; z.H = p.height; z.pitch = p.pitch; z.D = p.max_disp;
+    z.w = p.width / 4; z.h = p.height / 4;
+    z.disp = disp[i];
+    z.best = best ? best[i] : nullptr;
+    z.second = second ? second[i] : nullptr;
+    for (int y0 = 0; y0 < z.h; y0 += kZnccTY)
+      for (int x0 = 0; x0 < z.w; x0 += gx) jobs.push_back({i, y0, x0, 0});
+  }
+  if (jobs.empty()) return SV_OK;
+  sv_status s;
+  if ((s = cuda(zpairs.ensure(sizeof(ZPair) * n), "alloc pair table"))) return s;
+  if ((s = cuda(zjobs.ensure(sizeof(ZJob) * jobs.size()), "alloc job table"))) return s;
+  if ((s = cuda(cudaMemcpyAsync(zpairs.p, zp.data(), sizeof(ZPair) * n, cudaMemcpyHostToDevice, st), "upload pairs")))
+    return s;
+  if ((s = cuda(cudaMemcpyAsync(zjobs.p, jobs.data(), sizeof(ZJob) * jobs.size(), cudaMemcpyHostToDevice, st),
+                "upload jobs")))
+    return s;
+  return cuda(launch_zncc_wta((const ZPair*)zpairs.p, (const ZJob*)zjobs.p, (int)jobs.size(), cfg.window / 2, maxD, st),
+              "zncc_wta launch");
+}
+
+// ---------------------------------------------------------------- plain refinement
+template <typename T>
+sv_status Ctx::refine_direct(const sv_pair& p, const void* coarse_map, bool coarse_int16, const T* eps, T* Y, T* mu_out,
+                             T* lv_out, T* const* saved, cudaStream_t st) {
+  const Levels lv(p.height, p.width);
+  const int w = p.width / 4, h = p.height / 4;
+  const T* Wt = weights<T>();
+  auto Wl = [&](int l) { return Wt + net.w_off(l); };
+  auto Bl = [&](int l) { return Wt + net.b_off(l); };
+  sv_status s;
+  // workspaces: e1 e2 e3 z d1 d2 d3 (or the caller's saved buffers)
+  const size_t P0 = (size_t)lv.H[0] * lv.W[0], P1 = (size_t)lv.H[1] * lv.W[1], P2 = (size_t)lv.H[2] * lv.W[2],
+               P3 = (size_t)lv.H[3] * lv.W[3];
+  const size_t need[7] = {P1 * net.enc[0], P2 * net.enc[1], P3 * net.enc[2], P3 * net.lat,
+                          P2 * net.dec[0], P1 * net.dec[1], P0 * net.dec[2]};
+  T* buf[7];
+  for (int i = 0; i < 7; ++i) {
+    if (saved && saved[i]) {
+      buf[i] = saved[i];
+      continue;
+    }
+    if ((s = cuda(act[i].ensure(need[i] * sizeof(T)), "alloc activations"))) return s;
+    buf[i] = (T*)act[i].p;
+  }
+  T *e1 = buf[0], *e2 = buf[1], *e3 = buf[2], *z = buf[3], *d1 = buf[4], *d2 = buf[5], *d3 = buf[6];
+  cudaError_t e;
+  if (coarse_int16)
+    e = launch_enc1<T, int16_t>(p.left, p.pitch, p.width, p.height, (const int16_t*)coarse_map, w, h, Wl(L_ENC1),
+                                Bl(L_ENC1), net.enc[0], e1, st);
+  else
+    e = launch_enc1<T, T>(p.left, p.pitch, p.width, p.height, (const T*)coarse_map, w, h, Wl(L_ENC1), Bl(L_ENC1),
+                          net.enc[0], e1, st);
+  if ((s = cuda(e, "enc1"))) return s;
+  DirectConvArgs<T> a{e1, lv.H[1], lv.W[1], net.enc[0], Wl(L_ENC2), Bl(L_ENC2), net.enc[1], lv.H[2], lv.W[2], 1, e2};
+  if ((s = cuda(launch_conv_direct<T>(a, CM_S2, 3, st), "enc2"))) return s;
+  a = {e2, lv.H[2], lv.W[2], net.enc[1], Wl(L_ENC3), Bl(L_ENC3), net.enc[2], lv.H[3], lv.W[3], 1, e3};
+  if ((s = cuda(launch_conv_direct<T>(a, CM_S2, 3, st), "enc3"))) return s;
+  const bool train = eps != nullptr || lv_out != nullptr;
+  if ((s = cuda(launch_latent<T>(e3, (int)P3, net.enc[2], Wl(L_MU), Bl(L_MU), Wl(L_LV), Bl(L_LV), net.lat, eps, mu_out,
+                                 train ? lv_out : nullptr, z, st),
+                "latent")))
+    return s;
+  a = {z, lv.H[3], lv.W[3], net.lat, Wl(L_DEC1), Bl(L_DEC1), net.dec[0], lv.H[2], lv.W[2], 1, d1};
+  if ((s = cuda(launch_conv_direct<T>(a, CM_UP2, 3, st), "dec1"))) return s;
+  a = {d1, lv.H[2], lv.W[2], net.dec[0], Wl(L_DEC2), Bl(L_DEC2), net.dec[1], lv.H[1], lv.W[1], 1, d2};
+  if ((s = cuda(launch_conv_direct<T>(a, CM_UP2, 3, st), "dec2"))) return s;
+  a = {d2, lv.H[1], lv.W[1], net.dec[1], Wl(L_DEC3), Bl(L_DEC3), net.dec[2], lv.H[0], lv.W[0], 1, d3};
+  if ((s = cuda(launch_conv_direct<T>(a, CM_UP2, 3, st), "dec3"))) return s;
+  if (coarse_int16)
+    e = launch_final<T, int16_t, T>(d3, p.width, p.height, net.dec[2], Wl(L_FINAL), Bl(L_FINAL),
+                                    (const int16_t*)coarse_map, w, h, Y, st);
+  else
+    e = launch_final<T, T, T>(d3, p.width, p.height, net.dec[2], Wl(L_FINAL), Bl(L_FINAL), (const T*)coarse_map, w, h,
+                              Y, st);
+  return cuda(e, "final");
+}
+
+template <> const float* Ctx::weights<float>() const { return (const float*)w32.p; }
+template <> const double* Ctx::weights<double>() const { return (const double*)w64.p; }
+
+template sv_status Ctx::refine_direct<float>(const sv_pair&, const void*, bool, const float*, float*, float*, float*,
+                                             float* const*, cudaStream_t);
+template sv_status Ctx::refine_direct<double>(const sv_pair&, const void*, bool, const double*, double*, double*,
+                                              double*, double* const*, cudaStream_t);
+
+sv_status Ctx::refresh_weight_copies() {
+  sv_status s;
+  const size_t n = net.count();
+  if ((s = cuda(w64.ensure(n * sizeof(double)), "alloc fp64 weights"))) return s;
+  f32_to_f64<<<(unsigned)((n + 255) / 256), 256>>>((const float*)w32.p, (double*)w64.p, n);
+  if ((s = cuda(cudaGetLastError(), "weights to fp64"))) return s;
+  if (cfg.precision == SV_BF16)
+    if ((s = pack_bf16_weights())) return s;
+  return cuda(cudaDeviceSynchronize(), "weight refresh");
+}
+
+}  // namespace sv
+
+using sv::Ctx;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+extern "C" {
+
+const char* sv_status_string(sv_status s) {
+  switch (s) {
+    case SV_OK: return "SV_OK";
+    case SV_ERR_INVALID_ARG: return "SV_ERR_INVALID_ARG";
+    case SV_ERR_CUDA: return "SV_ERR_CUDA";
+    case SV_ERR_OOM: return "SV_ERR_OOM";
+    case SV_ERR_UNSUPPORTED: return "SV_ERR_UNSUPPORTED";
+    case SV_ERR_TIMEOUT: return "SV_ERR_TIMEOUT";
+    case SV_ERR_STATE: return "SV_ERR_STATE";
+  }
+  return "SV_ERR_UNKNOWN";
+}
+
+const char* sv_last_error(const sv_ctx* ctx) {
+  if (!ctx) return "NULL context";
+  return reinterpret_cast<const Ctx*>(ctx)->err.c_str();
+}
+
+static bool config_ok(const sv_config* c) {
+  if (!c) return false;
+  if (c->window < 3 || c->window > 15 || c->window % 2 == 0) return false;
+  for (int i = 0; i < 3; ++i)
+    if (!sv::valid_width_pub(c->enc_ch[i]) || !sv::valid_width_pub(c->dec_ch[i])) return false;
+  if (!sv::valid_width_pub(c->latent_ch)) return false;
+  if (c->precision < SV_FP32 || c->precision > SV_FP64_CHECK) return false;
+  if (c->flags != 0) return false;
+  return true;
+}
+
+size_t sv_param_count(const sv_config* c) {
+  if (!config_ok(c)) return 0;
+  sv::NetDims n{{c->enc_ch[0], c->enc_ch[1], c->enc_ch[2]}, c->latent_ch, {c->dec_ch[0], c->dec_ch[1], c->dec_ch[2]}};
+  return n.count();
+}
+
+sv_status sv_create(const sv_config* cfg, int device, sv_ctx** out) {
+  if (!out) return SV_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!config_ok(cfg)) return SV_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return SV_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return SV_ERR_INVALID_ARG;
+  DeviceGuard g(device);
+  Ctx* c = new Ctx();
+  c->cfg = *cfg;
+  c->device = device;
+  c->net = sv::NetDims{{cfg->enc_ch[0], cfg->enc_ch[1], cfg->enc_ch[2]}, cfg->latent_ch,
+                       {cfg->dec_ch[0], cfg->dec_ch[1], cfg->dec_ch[2]}};
+  const size_t n = c->net.count();
+  sv_status s = c->cuda(c->w32.ensure(n * sizeof(float)), "alloc weights");
+  if (!s) s = c->cuda(cudaMemset(c->w32.p, 0, n * sizeof(float)), "zero weights");
+  if (!s) s = c->refresh_weight_copies();
+  if (s) {
+    delete c;
+    return s;
+  }
+  *out = reinterpret_cast<sv_ctx*>(c);
+  return SV_OK;
+}
+
+sv_status sv_destroy(sv_ctx* ctx) {
+  if (!ctx) return SV_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  {
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    c->release_all();
+  }
+  delete c;
+  return SV_OK;
+}
+
+sv_status sv_set_weights(sv_ctx* ctx, const float* params, size_t n) {
+  if (!ctx) return SV_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!params) return c->fail(SV_ERR_INVALID_ARG, "params is NULL");
+  if (n != c->net.count()) return c->fail(SV_ERR_INVALID_ARG, "expected %zu parameters, got %zu", c->net.count(), n);
+  DeviceGuard g(c->device);
+  sv_status s = c->cuda(cudaMemcpy(c->w32.p, params, n * sizeof(float), cudaMemcpyDefault), "copy weights");
+  if (s) return s;
+  c->adam_t = 0;
+  return c->refresh_weight_copies();
+}
+
+sv_status sv_get_weights(sv_ctx* ctx, float* params, size_t n) {
+  if (!ctx) return SV_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!params) return c->fail(SV_ERR_INVALID_ARG, "params is NULL");
+  if (n != c->net.count()) return c->fail(SV_ERR_INVALID_ARG, "expected %zu parameters, got %zu", c->net.count(), n);
+  DeviceGuard g(c->device);
+  return c->cuda(cudaMemcpy(params, c->w32.p, n * sizeof(float), cudaMemcpyDefault), "copy weights out");
+}
+
+sv_status sv_coarse_match(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, int16_t* const* disp_out,
+                          float* const* best, float* const* second, sv_stream stream) {
+  if (!ctx) return SV_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  c->err.clear();
+  sv_status s = c->check_pairs(pairs, n_pairs);
+  if (s) return s;
+  if (n_pairs == 0) return SV_OK;
+  if (!disp_out) return c->fail(SV_ERR_INVALID_ARG, "disp_out is NULL");
+  for (int i = 0; i < n_pairs; ++i)
+    if (!disp_out[i]) return c->fail(SV_ERR_INVALID_ARG, "disp_out[%d] is NULL", i);
+  DeviceGuard g(c->device);
+  return c->coarse(pairs, n_pairs, disp_out, best, second, (cudaStream_t)stream);
+}
+
+sv_status sv_refine(sv_ctx* ctx, const sv_pair* pairs, const int16_t* const* coarse, int n_pairs,
+                    float* const* disp_out, sv_stream stream) {
+  if (!ctx) return SV_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  c->err.clear();
+  sv_status s = c->check_pairs(pairs, n_pairs);
+  if (s) return s;
+  if (n_pairs == 0) return SV_OK;
+  if (!coarse || !disp_out) return c->fail(SV_ERR_INVALID_ARG, "coarse / disp_out is NULL");
+  for (int i = 0; i < n_pairs; ++i)
+    if (!coarse[i] || !disp_out[i]) return c->fail(SV_ERR_INVALID_ARG, "coarse[%d] / disp_out[%d] is NULL", i, i);
+  DeviceGuard g(c->device);
+  return c->refine_infer(pairs, coarse, n_pairs, disp_out, (cudaStream_t)stream);
+}
+
+sv_status sv_pipeline(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, float* const* disp_out, sv_stream stream) {
+  if (!ctx) return SV_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  c->err.clear();
+  sv_status s = c->check_pairs(pairs, n_pairs);
+  if (s) return s;
+  if (n_pairs == 0) return SV_OK;
+  if (!disp_out) return c->fail(SV_ERR_INVALID_ARG, "disp_out is NULL");
+  for (int i = 0; i < n_pairs; ++i)
+    if (!disp_out[i]) return c->fail(SV_ERR_INVALID_ARG, "disp_out[%d] is NULL", i);
+  DeviceGuard g(c->device);
+  return c->pipeline(pairs, n_pairs, disp_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

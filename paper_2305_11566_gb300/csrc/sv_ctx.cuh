@@ -1,0 +1,64 @@
+// sv_ctx.cuh -- the library context behind the opaque sv_ctx handle.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "sv_internal.cuh"
+
+namespace sv {
+
+constexpr int kMaxSide = 16384;  // largest accepted image width / height
+constexpr int kMaxDisp = 128;    // largest accepted D (4 disparities per lane of a warp)
+
+inline bool valid_width_pub(int c) { return c >= 16 && c <= 256 && c % 16 == 0; }
+
+// Device allocation that only grows.
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t bytes);
+  void release();
+};
+
+struct Ctx {
+  sv_config cfg{};
+  NetDims net{};
+  int device = 0;
+  std::string err;
+
+  DevBuf w32, w64, wbf;          // FP32 master, FP64 copy, packed BF16 GEMM operands
+  DevBuf zpairs, zjobs;          // coarse-matcher tables
+  DevBuf coarse_maps;            // int16 coarse maps of sv_pipeline
+  DevBuf act[7];                 // activations e1 e2 e3 z d1 d2 d3 (direct path)
+  DevBuf tc_act[8];              // BF16 activations of the tensor-core path
+  DevBuf tc_tables;              // tensor-core job tables
+  int adam_t = 0;
+  DevBuf adam_m, adam_v;
+
+  sv_status fail(sv_status s, const char* fmt, ...);
+  sv_status cuda(cudaError_t e, const char* what);
+  sv_status check_pairs(const sv_pair* pairs, int n_pairs);
+
+  sv_status coarse(const sv_pair* pairs, int n, int16_t* const* disp, float* const* best, float* const* second,
+                   cudaStream_t st);
+  template <typename T> const T* weights() const;
+  template <typename T>
+  sv_status refine_direct(const sv_pair& p, const void* coarse_map, bool coarse_int16, const T* eps, T* Y, T* mu_out,
+                          T* lv_out, T* const* saved, cudaStream_t st);
+  sv_status refine_infer(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out,
+                         cudaStream_t st);
+  sv_status pipeline(const sv_pair* pairs, int n, float* const* out, cudaStream_t st);
+  sv_status refresh_weight_copies();
+  sv_status pack_bf16_weights();
+  sv_status refine_tc(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out, cudaStream_t st);
+
+  void release_all() {
+    w32.release(); w64.release(); wbf.release(); zpairs.release(); zjobs.release(); coarse_maps.release();
+    for (auto& b : act) b.release();
+    for (auto& b : tc_act) b.release();
+    tc_tables.release(); adam_m.release(); adam_v.release();
+  }
+};
+
+}  // namespace sv

@@ -1,0 +1,138 @@
+// sv_internal.cuh -- internal declarations shared by the CUDA translation units of
+// the StereoVAE library (context, device descriptors, kernel launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "../../include/stereovae.h"
+
+namespace sv {
+
+// ------------------------------------------------------------------ coarse stage
+// Device descriptor of one pair for the coarse matcher.
+struct ZPair {
+  const uint8_t* L;
+  const uint8_t* R;
+  int W, H, pitch, D;
+  int w, h;          // coarse size = (W / 4, H / 4)
+  int16_t* disp;     // [h][w]
+  float* best;       // [h][w] or nullptr
+  float* second;     // [h][w] or nullptr
+};
+
+// One CTA job: rows [y0, y0 + kZnccTY) and columns [x0, x0 + group width) of a pair.
+struct ZJob {
+  int pair, y0, x0, pad;
+};
+
+constexpr int kZnccTY = 8;      // coarse rows per job
+constexpr int kZnccWarps = 8;   // warps per CTA; each owns a column tile of TX(KD) columns
+
+inline int zncc_kd(int D) { return (D + 31) / 32; }
+inline int zncc_tx(int kd) { return kd == 1 ? 32 : kd == 2 ? 24 : kd == 3 ? 16 : 12; }
+
+// Shared-memory layout of one ZNCC job (window radius r, disparity count D, tile TX).
+struct ZLayout {
+  int nlc, nrc, gx, nrs;  // staged left / right columns, job width, right-window columns
+  size_t off_sl, off_sr, off_suml, off_invl, off_sumr, off_invr, off_cs, off_cs2, total;
+};
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+__host__ __device__ inline ZLayout zlayout(int r, int D, int tx) {
+  ZLayout z;
+  const int TY = kZnccTY;
+  z.gx = kZnccWarps * tx;
+  z.nlc = z.gx + 2 * r;
+  z.nrc = z.gx + 2 * r + D - 1;
+  z.nrs = z.gx + D - 1;
+  size_t o = 0;
+  z.off_sl = o; o = align16(o + sizeof(uint16_t) * (TY + 2 * r) * z.nlc);
+  z.off_sr = o; o = align16(o + sizeof(uint16_t) * (TY + 2 * r) * z.nrc);
+  z.off_suml = o; o = align16(o + sizeof(int) * TY * z.gx);
+  z.off_invl = o; o = align16(o + sizeof(float) * TY * z.gx);
+  z.off_sumr = o; o = align16(o + sizeof(int) * TY * z.nrs);
+  z.off_invr = o; o = align16(o + sizeof(float) * TY * z.nrs);
+  z.off_cs = o; o = align16(o + sizeof(int) * TY * z.nrc);
+  z.off_cs2 = o; o = align16(o + sizeof(unsigned) * TY * z.nrc);
+  z.total = o;
+  return z;
+}
+inline size_t zncc_smem_bytes(int r, int D) { return zlayout(r, D, zncc_tx(zncc_kd(D))).total; }
+
+// Fused downsample + ZNCC + WTA over the given jobs, one entry per window radius
+// r = 1..7 (each compiled in its own translation unit).
+#define SV_ZNCC_DECL(r)                                                                              \
+  cudaError_t launch_zncc_wta_r##r(const ZPair* d_pairs, const ZJob* d_jobs, int n_jobs, int maxD, \
+                                   cudaStream_t st);
+SV_ZNCC_DECL(1) SV_ZNCC_DECL(2) SV_ZNCC_DECL(3) SV_ZNCC_DECL(4) SV_ZNCC_DECL(5) SV_ZNCC_DECL(6) SV_ZNCC_DECL(7)
+inline cudaError_t launch_zncc_wta(const ZPair* p, const ZJob* j, int n, int r, int maxD, cudaStream_t st) {
+  switch (r) {
+    case 1: return launch_zncc_wta_r1(p, j, n, maxD, st);
+    case 2: return launch_zncc_wta_r2(p, j, n, maxD, st);
+    case 3: return launch_zncc_wta_r3(p, j, n, maxD, st);
+    case 4: return launch_zncc_wta_r4(p, j, n, maxD, st);
+    case 5: return launch_zncc_wta_r5(p, j, n, maxD, st);
+    case 6: return launch_zncc_wta_r6(p, j, n, maxD, st);
+    case 7: return launch_zncc_wta_r7(p, j, n, maxD, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ refinement
+enum Layer { L_ENC1 = 0, L_ENC2, L_ENC3, L_MU, L_LV, L_DEC1, L_DEC2, L_DEC3, L_FINAL, L_COUNT };
+
+struct NetDims {
+  int enc[3], lat, dec[3];
+  int cout(int l) const;
+  int cin(int l) const;
+  int ks(int l) const;
+  size_t w_off(int l) const;   // offset of W of layer l in the flat vector
+  size_t b_off(int l) const;   // offset of b
+  size_t count() const;
+};
+
+// Spatial sizes of the four levels of a W x H input.
+struct Levels {
+  int H[4], W[4];
+  explicit Levels(int H0 = 0, int W0 = 0) {
+    H[0] = H0; W[0] = W0;
+    for (int i = 1; i < 4; ++i) { H[i] = (H[i - 1] + 1) / 2; W[i] = (W[i - 1] + 1) / 2; }
+  }
+};
+
+// Direct (CUDA-core) convolution arguments, element type T (float or double).
+// Activations NHWC; weights canonical [cout][ks][ks][cin].
+enum ConvMode { CM_S1 = 0, CM_S2 = 1, CM_UP2 = 2 };
+template <typename T>
+struct DirectConvArgs {
+  const T* in; int Hi, Wi, Ci;
+  const T* wt; const T* bias; int Co;
+  int Ho, Wo;
+  int relu;
+  T* out;
+};
+
+template <typename T>
+cudaError_t launch_conv_direct(const DirectConvArgs<T>& a, int mode, int ks, cudaStream_t st);
+
+// enc1 with the network input built on the fly: x0 = (L / 256, U / 256), U = 4 *
+// bilinear(coarse).  CoarseT = int16_t (inference) or T (training).
+template <typename T, typename CoarseT>
+cudaError_t launch_enc1(const uint8_t* L, int pitch, int W, int H, const CoarseT* coarse, int w, int h,
+                        const T* wt, const T* bias, int Co, T* out, cudaStream_t st);
+
+// final 3x3 conv (cin -> 1) + bias + U (recomputed bilinear) -> Y
+template <typename T, typename CoarseT, typename OutT>
+cudaError_t launch_final(const T* in, int W, int H, int Ci, const T* wt, const T* bias, const CoarseT* coarse,
+                         int w, int h, OutT* Y, cudaStream_t st);
+
+// latent heads: mu = 1x1(e3) + b; optionally logvar and z = mu + eps * exp(lv / 2).
+template <typename T>
+cudaError_t launch_latent(const T* e3, int P, int Ci, const T* wmu, const T* bmu, const T* wlv, const T* blv,
+                          int lat, const T* eps, T* mu, T* lv, T* z, cudaStream_t st);
+
+}  // namespace sv

@@ -1,0 +1,237 @@
+// zncc_wta.cu -- K1: fused quarter-size downsample + ZNCC (Eq. 1-3) + winner-take-all
+// (Eq. 6) for many pairs in one launch.
+//
+// One CTA job = one pair, kZnccTY coarse rows, kZnccWarps * TX coarse columns.
+//  stage 1  4x4 box sums S (uint16, exact) of the rows/columns the job touches,
+//           window positions outside the image clamped to the edge;
+//  stage 2  per-window sums sum(S) and exact variance v = N sum(S^2) - sum(S)^2 for every
+//           left window of the job and every right window any candidate can reach
+//           (right windows are shared across disparities); 1/sigma = rsqrt(v), 0 if v == 0;
+//  stage 3  each warp owns TX output columns, lane l the disparities d = l + 32 kd.
+//           Column sums of L(u, .) * R(u - d, .) over the window rows live in registers
+//           and slide down the rows (add the entering row, drop the leaving one); the
+//           window sum slides along x.  All sums are exact integers; the numerator
+//           n = N sum(LR) - sum(L) sum(R) is exact in int64, and
+//           rho = float(n) * (1/sigma_L) * (1/sigma_R).  The argmax over d is two warp
+//           reductions (__reduce_max_sync on an order-preserving integer key, then
+//           __reduce_min_sync on d among the maxima: lowest d wins ties).
+#include "sv_internal.cuh"
+
+namespace sv {
+
+namespace {
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Order-preserving map float -> int (for finite values): larger float, larger int.
+__device__ __forceinline__ int order_key(float f) {
+  int i = __float_as_int(f + 0.0f);  // -0 -> +0
+  return i >= 0 ? i : (i ^ 0x7FFFFFFF);
+}
+__device__ __forceinline__ float key_value(int k) {
+  if (k == INT_MIN) return -2.0f;
+  return __int_as_float(k >= 0 ? k : (k ^ 0x7FFFFFFF));
+}
+
+// 4x4 box sum of coarse pixel (u, y) (already clamped into the image).
+__device__ __forceinline__ uint16_t box4(const uint8_t* img, int pitch, int u, int y) {
+  const uint8_t* p = img + (size_t)(4 * y) * pitch + 4 * u;
+  unsigned s = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    unsigned v = *reinterpret_cast<const unsigned*>(p + (size_t)j * pitch);  // 4-byte aligned: 4u
+    s += (v & 0xFFu) + ((v >> 8) & 0xFFu) + ((v >> 16) & 0xFFu) + (v >> 24);
+  }
+  return (uint16_t)s;
+}
+
+// Vertical then horizontal window sums of S over rows [yi, yi + 2r] for each of the
+// TY output rows; writes sum and 1/sigma for `ncols_out` windows starting at column
+// `c0` of the staged array (staged column c0 + t is the window's left edge).
+template <int R>
+__device__ void window_stats(const uint16_t* s, int ncols, int* cs, unsigned* cs2, int* sum_out, float* inv_out,
+                             int ncols_out) {
+  const int TY = kZnccTY;
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+    int a = 0;
+    unsigned a2 = 0;
+#pragma unroll
+    for (int j = 0; j <= 2 * R; ++j) {
+      unsigned v = s[j * ncols + c];
+      a += (int)v;
+      a2 += v * v;
+    }
+    cs[c] = a;
+    cs2[c] = a2;
+    for (int yi = 1; yi < TY; ++yi) {
+      unsigned vin = s[(yi + 2 * R) * ncols + c], vout = s[(yi - 1) * ncols + c];
+      a += (int)vin - (int)vout;
+      a2 += vin * vin - vout * vout;  // exact modulo 2^32, true value < 2^32
+      cs[yi * ncols + c] = a;
+      cs2[yi * ncols + c] = a2;
+    }
+  }
+  __syncthreads();
+  const long long N = (long long)(2 * R + 1) * (2 * R + 1);
+  for (int e = threadIdx.x; e < TY * ncols_out; e += blockDim.x) {
+    int yi = e / ncols_out, t = e - yi * ncols_out;
+    int a = 0;
+    unsigned a2 = 0;
+#pragma unroll
+    for (int i = 0; i <= 2 * R; ++i) {
+      a += cs[yi * ncols + t + i];
+      a2 += cs2[yi * ncols + t + i];
+    }
+    long long v = N * (long long)a2 - (long long)a * a;
+    sum_out[e] = a;
+    inv_out[e] = v > 0 ? __frsqrt_rn((float)v) : 0.0f;
+  }
+  __syncthreads();
+}
+
+template <int R, int KD, int TX>
+__global__ void __launch_bounds__(kZnccWarps * 32, 1)
+zncc_wta_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ jobs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int TY = kZnccTY;
+  const ZJob job = jobs[blockIdx.x];
+  const ZPair P = pairs[job.pair];
+  const int D = P.D, w = P.w, h = P.h;
+  const ZLayout Z = zlayout(R, D, TX);
+  uint16_t* sL = reinterpret_cast<uint16_t*>(smem + Z.off_sl);
+  uint16_t* sR = reinterpret_cast<uint16_t*>(smem + Z.off_sr);
+  int* sumL = reinterpret_cast<int*>(smem + Z.off_suml);
+  float* invL = reinterpret_cast<float*>(smem + Z.off_invl);
+  int* sumR = reinterpret_cast<int*>(smem + Z.off_sumr);
+  float* invR = reinterpret_cast<float*>(smem + Z.off_invr);
+  int* cs = reinterpret_cast<int*>(smem + Z.off_cs);
+  unsigned* cs2 = reinterpret_cast<unsigned*>(smem + Z.off_cs2);
+  const int y0 = job.y0, x0 = job.x0;
+  const int lbase = x0 - R;               // coarse column of staged left column 0
+  const int rbase = x0 - R - (D - 1);     // coarse column of staged right column 0
+
+  // ---- stage 1: box sums, clamped rows / columns
+  for (int e = threadIdx.x; e < (TY + 2 * R) * Z.nlc; e += blockDim.x) {
+    int ry = e / Z.nlc, c = e - ry * Z.nlc;
+    sL[e] = box4(P.L, P.pitch, clampi(lbase + c, 0, w - 1), clampi(y0 - R + ry, 0, h - 1));
+  }
+  for (int e = threadIdx.x; e < (TY + 2 * R) * Z.nrc; e += blockDim.x) {
+    int ry = e / Z.nrc, c = e - ry * Z.nrc;
+    sR[e] = box4(P.R, P.pitch, clampi(rbase + c, 0, w - 1), clampi(y0 - R + ry, 0, h - 1));
+  }
+  __syncthreads();
+  // ---- stage 2: window statistics (left windows at x0 + t; right windows at rbase + R + t)
+  window_stats<R>(sL, Z.nlc, cs, cs2, sumL, invL, Z.gx);
+  window_stats<R>(sR, Z.nrc, cs, cs2, sumR, invR, Z.nrs);
+
+  // ---- stage 3: sliding ZNCC + WTA
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int xw = x0 + warp * TX;          // first output column of this warp
+  const int lc0 = warp * TX;              // staged left column of u = xw - R
+  const long long N = (long long)(2 * R + 1) * (2 * R + 1);
+  int dd[KD], rc0[KD];
+#pragma unroll
+  for (int k = 0; k < KD; ++k) {
+    int d = lane + 32 * k;
+    dd[k] = d < D ? d : D - 1;            // reads stay in the staged range; masked below
+    rc0[k] = lc0 - dd[k] + (D - 1);       // staged right column of u - d for u = xw - R
+  }
+  unsigned colsum[KD][TX + 2 * R];
+#pragma unroll
+  for (int c = 0; c < TX + 2 * R; ++c) {
+#pragma unroll
+    for (int k = 0; k < KD; ++k) {
+      unsigned a = 0;
+#pragma unroll
+      for (int j = 0; j <= 2 * R; ++j) a += (unsigned)sL[j * Z.nlc + lc0 + c] * (unsigned)sR[j * Z.nrc + rc0[k] + c];
+      colsum[k][c] = a;
+    }
+  }
+  for (int yi = 0; yi < TY; ++yi) {
+    const int y = y0 + yi;
+    if (yi > 0) {
+      const int rin = yi + 2 * R, rout = yi - 1;
+#pragma unroll
+      for (int c = 0; c < TX + 2 * R; ++c) {
+        unsigned lin = sL[rin * Z.nlc + lc0 + c], lout = sL[rout * Z.nlc + lc0 + c];
+#pragma unroll
+        for (int k = 0; k < KD; ++k)
+          colsum[k][c] += lin * (unsigned)sR[rin * Z.nrc + rc0[k] + c] - lout * (unsigned)sR[rout * Z.nrc + rc0[k] + c];
+      }
+    }
+    unsigned run[KD];
+#pragma unroll
+    for (int k = 0; k < KD; ++k) {
+      unsigned a = 0;
+#pragma unroll
+      for (int i = 0; i <= 2 * R; ++i) a += colsum[k][i];
+      run[k] = a;
+    }
+    int my_d = 0, my_b = INT_MIN, my_s = INT_MIN;
+#pragma unroll
+    for (int t = 0; t < TX; ++t) {
+      if (t > 0) {
+#pragma unroll
+        for (int k = 0; k < KD; ++k) run[k] += colsum[k][t + 2 * R] - colsum[k][t - 1];
+      }
+      const int x = xw + t;
+      const int sl = sumL[yi * Z.gx + lc0 + t];
+      const float il = invL[yi * Z.gx + lc0 + t];
+      int bk = INT_MIN, sk = INT_MIN, bd = 0x7FFFFFFF;
+#pragma unroll
+      for (int k = 0; k < KD; ++k) {
+        const int d = lane + 32 * k;
+        const int rs = yi * Z.nrs + lc0 + t - dd[k] + (D - 1);  // right window at x - d
+        const long long n = N * (long long)run[k] - (long long)sl * (long long)sumR[rs];
+        const float rho = (float)n * il * invR[rs];
+        const bool valid = d < D && d <= x && x < w;
+        const int key = valid ? order_key(rho) : INT_MIN;
+        if (key > bk) { sk = bk; bk = key; bd = d; }
+        else if (key > sk) { sk = key; }
+      }
+      const int gbest = __reduce_max_sync(0xFFFFFFFFu, bk);
+      const unsigned dstar = __reduce_min_sync(0xFFFFFFFFu, (bk == gbest) ? (unsigned)bd : 0x7FFFFFFFu);
+      const int gsec = __reduce_max_sync(0xFFFFFFFFu, ((unsigned)bd == dstar) ? sk : bk);
+      if (lane == t) { my_d = (int)dstar; my_b = gbest; my_s = gsec; }
+    }
+    const int x = xw + lane;
+    if (lane < TX && x < w && y < h) {
+      const size_t o = (size_t)y * w + x;
+      P.disp[o] = (int16_t)my_d;
+      if (P.best) P.best[o] = key_value(my_b);
+      if (P.second) P.second[o] = key_value(my_s);
+    }
+  }
+}
+
+template <int R, int KD>
+cudaError_t launch_rk(const ZPair* p, const ZJob* j, int n, int maxD, cudaStream_t st) {
+  constexpr int TX = KD == 1 ? 32 : KD == 2 ? 24 : KD == 3 ? 16 : 12;
+  auto kern = zncc_wta_kernel<R, KD, TX>;
+  const size_t smem = zlayout(R, maxD, TX).total;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<n, kZnccWarps * 32, smem, st>>>(p, j);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#ifndef SV_ZNCC_R
+#error "compile this file once per window radius with -DSV_ZNCC_R=<r>"
+#endif
+
+#define SV_CAT2(a, b) a##b
+#define SV_CAT(a, b) SV_CAT2(a, b)
+cudaError_t SV_CAT(launch_zncc_wta_r, SV_ZNCC_R)(const ZPair* p, const ZJob* j, int n, int maxD, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  switch (zncc_kd(maxD)) {
+    case 1: return launch_rk<SV_ZNCC_R, 1>(p, j, n, maxD, st);
+    case 2: return launch_rk<SV_ZNCC_R, 2>(p, j, n, maxD, st);
+    case 3: return launch_rk<SV_ZNCC_R, 3>(p, j, n, maxD, st);
+    case 4: return launch_rk<SV_ZNCC_R, 4>(p, j, n, maxD, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace sv

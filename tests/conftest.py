@@ -25,3 +25,18 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def svlib():
+    """The built CUDA library (compiled on first use; nvcc cross-compiles without a GPU)."""
+    from paper_2305_11566_gb300 import build, binding
+    build.build()
+    return binding.lib()
+
+
+@pytest.fixture(scope="session")
+def oracle_lib():
+    import oracle
+    oracle.build()
+    return oracle

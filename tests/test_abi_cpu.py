@@ -1,0 +1,82 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports every
+entry point include/stereovae.h declares, and its host-only functions behave."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2305_11566_gb300 import binding, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            src = open(os.path.join(inc, f)).read()
+            names |= set(re.findall(r"SV_API[^;(]*?\b(sv_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ("sv_create", "sv_coarse_match", "sv_refine", "sv_pipeline", "sv_refine_backward"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(svlib):
+    names = declared_symbols()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(svlib, n), n
+        assert n in binding.API, n
+
+
+def test_param_count_matches_layout(svlib):
+    assert binding.param_count(synth.NET_SMALL, 7) == 91921 == synth.NET_SMALL.n_params()
+    assert binding.param_count(synth.NET_WIDE, 9) == 366113 == synth.NET_WIDE.n_params()
+
+
+def test_invalid_configs_rejected(svlib):
+    bad = []
+    c = binding.make_config(synth.NET_SMALL, 8)       # even window
+    bad.append(c)
+    c = binding.make_config(synth.NET_SMALL, 17)      # too large
+    bad.append(c)
+    c = binding.make_config(synth.NetShape((16, 24, 64), 64, (64, 32, 16)), 7)  # width not /16
+    bad.append(c)
+    c = binding.make_config(synth.NET_SMALL, 7, 5)    # precision
+    bad.append(c)
+    for c in bad:
+        assert svlib.sv_param_count(ctypes.byref(c)) == 0
+        h = ctypes.c_void_p()
+        assert svlib.sv_create(ctypes.byref(c), 0, ctypes.byref(h)) == binding.SV_ERR_INVALID_ARG
+        assert not h.value
+
+
+def test_status_strings(svlib):
+    for i, n in enumerate(["SV_OK", "SV_ERR_INVALID_ARG", "SV_ERR_CUDA", "SV_ERR_OOM", "SV_ERR_UNSUPPORTED",
+                           "SV_ERR_TIMEOUT", "SV_ERR_STATE"]):
+        assert svlib.sv_status_string(i).decode() == n
+    assert svlib.sv_last_error(None).decode() == "NULL context"
+
+
+def test_null_context_calls_rejected(svlib):
+    assert svlib.sv_destroy(None) == binding.SV_ERR_INVALID_ARG
+    assert svlib.sv_coarse_match(None, None, 0, None, None, None, None) == binding.SV_ERR_INVALID_ARG
+    assert svlib.sv_refine(None, None, None, 0, None, None) == binding.SV_ERR_INVALID_ARG
+    assert svlib.sv_pipeline(None, None, 0, None, None) == binding.SV_ERR_INVALID_ARG
+    assert svlib.sv_refine_backward(None, None, None, None, None, None, None) == binding.SV_ERR_INVALID_ARG
+
+
+def test_create_without_device_fails_cleanly(svlib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    c = binding.make_config(synth.NET_SMALL, 7)
+    h = ctypes.c_void_p()
+    assert svlib.sv_create(ctypes.byref(c), 0, ctypes.byref(h)) == binding.SV_ERR_CUDA
+    assert not h.value
