@@ -1,0 +1,424 @@
+#!/usr/bin/env python3
+"""Throughput of the StereoVAE hot path on synthetic 1242x375 stereo pairs.
+
+One step = sv_pipeline over a batch of pairs: coarse ZNCC + WTA on the x4 box-
+downsampled pair (D = 48, 9x9 window) and refinement by the 32/64/128 network to a
+full-resolution disparity map.  Two forms:
+  fp32  the plain method: FP32 CUDA-core convolutions, launched pair by pair;
+  bf16  BF16 tcgen05 implicit-GEMM convolutions, all pairs in one persistent launch
+        per layer (when the library has it).
+The JSON line's value is the headline form (bf16 when available, else fp32);
+both forms are listed under "forms".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank processes its own batch (pairs are independent: weak
+scaling, no data-path collective); rank 0 prints the line.  --impl reference times
+the FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pairs/s at 1242×375 D=48 (plain FP32 vs BF16-batched), ΔEPE vs FP64 oracle"
+W, H, D, WIN = 1242, 375, 48, 9
+DMAX = 190.0
+FP32_PEAK_TFLOPS_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="auto", choices=["auto", "fp32", "bf16", "both"])
+    ap.add_argument("--pairs", type=int, default=64, help="pairs per step per GPU")
+    ap.add_argument("--distinct", type=int, default=16, help="distinct synthetic pairs (cycled)")
+    ap.add_argument("--cpu-sample", type=int, default=2, help="pairs timed on the CPU oracle")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return rows
+
+    @staticmethod
+    def summarise(rows):
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def gpu_id_for(dev: int) -> str:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[dev] if vis else str(dev)
+
+
+def levels(h, w):
+    out = [(h, w)]
+    for _ in range(3):
+        h, w = (h + 1) // 2, (w + 1) // 2
+        out.append((h, w))
+    return out
+
+
+def work_per_pair(shape):
+    """{kernel name: (unit count per pair, unit)}: FLOPs for convolutions, bytes for ZNCC."""
+    (H0, W0), (H1, W1), (H2, W2), (H3, W3) = levels(H, W)
+    c1, c2, c3 = shape.enc
+    d1, d2, d3 = shape.dec
+    lat = shape.latent
+    f = {
+        "enc1": 2 * H1 * W1 * c1 * 9 * 2,
+        "enc2": 2 * H2 * W2 * c2 * 9 * c1,
+        "enc3": 2 * H3 * W3 * c3 * 9 * c2,
+        "latent": 2 * H3 * W3 * lat * c3,
+        "dec1": 2 * H2 * W2 * d1 * 9 * lat,
+        "dec2": 2 * H1 * W1 * d2 * 9 * d1,
+        "dec3": 2 * H0 * W0 * d3 * 9 * d2,
+        "final": 2 * H0 * W0 * 9 * d3,
+    }
+    # tensor-core decoder: 4 output phases x 2x2 taps on the low-resolution grid
+    f["tc_dec1"] = 2 * (2 * H3) * (2 * W3) * d1 * 4 * lat
+    f["tc_dec2"] = 2 * (2 * H2) * (2 * W2) * d2 * 4 * d1
+    f["tc_dec3"] = 2 * (2 * H1) * (2 * W1) * d3 * 4 * d2
+    f["tc_enc2"], f["tc_enc3"], f["tc_latent"] = f["enc2"], f["enc3"], f["latent"]
+    zbytes = 2 * W * H + 2 * (W // 4) * (H // 4)
+    return f, zbytes
+
+
+# ------------------------------------------------------------------ our implementation
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2305_11566_gb300 import binding, build, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.cuda.current_device()
+    build.build()
+    shape = synth.NET_WIDE
+    params = synth.he_normal_weights(shape, 7)
+    B = args.pairs
+    distinct = [synth.make_pair(W, H, DMAX, 1000 + rank * B + i) for i in range(min(args.distinct, B))]
+    pairs = [distinct[i % len(distinct)] for i in range(B)]
+    dps_distinct = [binding.to_device(p, D) for p in distinct]
+    dps = [dps_distinct[i % len(distinct)] for i in range(B)]
+    pk, pk_kind = peaks()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    forms = []
+    if args.form in ("auto", "both"):
+        forms = ["fp32"]
+        try:
+            c = binding.Context(shape, WIN, "bf16", dev)
+            c.close()
+            forms = ["fp32", "bf16"]
+        except Exception:
+            pass
+    else:
+        forms = [args.form]
+
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    results = {}
+    for form in forms:
+        ctx = binding.Context(shape, WIN, form, dev)
+        ctx.set_weights(params)
+        outs = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in range(B)]
+        try:
+            ctx.pipeline(dps[:1], out=outs[:1])
+            torch.cuda.synchronize()
+        except binding.SvError as e:
+            if form == "bf16":
+                ctx.close()
+                continue
+            raise
+        for _ in range(args.warmup):
+            ctx.pipeline(dps, out=outs)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.profile_read(reset=True)
+        l0 = ctx.launch_count()
+        st = torch.cuda.current_stream()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        clk = ClockSampler(gpu_id_for(dev))
+        barrier()
+        torch.cuda.synchronize()
+        clk.start()
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)  # L2 flush between steps, outside the events
+            ev[k][0].record(st)
+            ctx.pipeline(dps, out=outs)
+            ev[k][1].record(st)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall0
+        rows = clk.stop()
+        barrier()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        prof = ctx.profile_read(reset=True)
+        ctx.profile(False)
+        launches = ctx.launch_count() - l0
+        clocks = ClockSampler.summarise(rows)
+        if clocks["samples"] < 3:  # short timed region: sample the same step for ~1.5 s
+            clk2 = ClockSampler(gpu_id_for(dev))
+            clk2.start()
+            t = time.perf_counter()
+            while time.perf_counter() - t < 1.5:
+                ctx.pipeline(dps, out=outs)
+                torch.cuda.synchronize()
+            c2 = ClockSampler.summarise(clk2.stop())
+            c2["note"] = "timed region shorter than the sampling period: sampled while repeating the step"
+            clocks = c2
+        total_ms = max_over_ranks(sum(step_ms))
+        ms_per_step = total_ms / args.steps
+        results[form] = dict(ctx=ctx, outs=outs, ms_per_step=ms_per_step, prof=prof, launches=launches,
+                             clocks=clocks, wall_s=wall, step_ms=step_ms)
+
+    # -------------------------------------------------------------- roofline of the dominant kernel
+    head = "bf16" if "bf16" in results else "fp32"
+    R = results[head]
+    flops, zbytes = work_per_pair(shape)
+    prof = R["prof"]
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, tot_ms) = top
+    avg_s = tot_ms / nl / 1e3
+    if name == "zncc_wta":
+        per_launch = zbytes * B
+        achieved = per_launch / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s"}
+    elif name.startswith("tc_"):
+        pairs_per_launch = B
+        per_launch = flops[name] * pairs_per_launch
+        achieved = per_launch / avg_s / 1e12
+        sustained = R["ms_per_step"] * args.steps > 1000
+        roof = {"bound": "tensor", "achieved": achieved,
+                "peak": pk["bf16_tflops_sustained" if sustained else "bf16_tflops"], "unit": "TFLOP/s"}
+    else:
+        per_launch = flops[name]  # the plain form launches one pair at a time
+        achieved = per_launch / avg_s / 1e12
+        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = name
+    roof["per_launch_units"] = per_launch
+    roof["avg_launch_ms"] = avg_s * 1e3
+    roof["peak_source"] = ("derived: " + FP32_PEAK_TFLOPS_NOTE) if roof["bound"] == "alu" else f"{pk_kind} (MEASURED_PEAKS.json)"
+    roof["traffic"] = None
+    shares = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in sorted(prof.items())}
+
+    # -------------------------------------------------------------- e2e through the host-buffer API
+    e2e = None
+    if not args.no_e2e:
+        ctx = R["ctx"]
+        hl = [torch.from_numpy(synth.pitched(p.left)).pin_memory() for p in distinct]
+        hr = [torch.from_numpy(synth.pitched(p.right)).pin_memory() for p in distinct]
+        L = [hl[i % len(distinct)] for i in range(B)]
+        Rr = [hr[i % len(distinct)] for i in range(B)]
+        ho = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(B)]
+        pitch = L[0].shape[1]
+        args_e2e = (L, Rr, [W] * B, [H] * B, [pitch] * B, [D] * B, ho)
+        for _ in range(max(1, args.warmup)):
+            ctx.pipeline_host(*args_e2e)
+        barrier()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.pipeline_host(*args_e2e)
+        el = max_over_ranks(time.perf_counter() - t)
+        e2e = {"value": B * world * args.steps / el, "unit": "pairs/s",
+               "h2d_bytes_per_step": int(sum(x.numel() for x in L) * 2),
+               "d2h_bytes_per_step": int(sum(x.numel() * 4 for x in ho)),
+               "api": "sv_pipeline_host (pinned host images in, host disparity maps out)"}
+
+    # -------------------------------------------------------------- CPU oracle baseline + accuracy
+    cpu = None
+    accuracy = {}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        n = max(1, min(args.cpu_sample, len(distinct)))
+        cores = os.cpu_count() or 1
+        oracle.set_threads(cores)
+        t = time.perf_counter()
+        ref = []
+        for i in range(n):
+            p = distinct[i]
+            Yo, do, bo, so = oracle.pipeline(shape, params, p.left, p.right, WIN, D)
+            ref.append((Yo, do, bo, so))
+        el = time.perf_counter() - t
+        cpu = {"value": n / el, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n} of the {B} pairs (1242x375, D=48): coarse match + refinement, FP64, "
+                         f"{cores} OpenMP threads, {el:.1f} s"}
+        for form, r in results.items():
+            errs, flips, epe_g, epe_o = [], 0, [], []
+            for i in range(n):
+                Yg = r["outs"][i].cpu().numpy().astype(np.float64)
+                Yo, do, bo, so = ref[i]
+                errs.append(np.abs(Yg - Yo))
+                epe_g.append(np.abs(Yg - distinct[i].gt).mean())
+                epe_o.append(np.abs(Yo - distinct[i].gt).mean())
+            e = np.concatenate([x.ravel() for x in errs])
+            accuracy[form] = {"mean_abs_dy_px": float(e.mean()), "max_abs_dy_px": float(e.max()),
+                              "epe_gpu_vs_gt_px": float(np.mean(epe_g)), "epe_oracle_vs_gt_px": float(np.mean(epe_o)),
+                              "delta_epe_px": float(np.mean(epe_g) - np.mean(epe_o)), "pairs": n}
+
+    value = B * world / (R["ms_per_step"] / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
+        "config": {"workload": f"{B} synthetic 1242x375 stereo pairs per GPU, D=48, 9x9 ZNCC window, "
+                               f"32/64/128 encoder, 128 latent, 128/64/32 decoder ({head} form)",
+                   "global_batch": B * world, "pairs_per_gpu": B, "width": W, "height": H, "max_disp": D,
+                   "window": WIN, "l2": "flushed between steps (512 MB write outside the timed events)",
+                   "parallelism": f"replicas x{world} (pairs sharded, no collective)"},
+        "roofline": roof,
+        "kernel_time_share": shares,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(R["launches"]),
+        "clocks": R["clocks"],
+        "forms": {f: {"pairs_per_s": B * world / (r["ms_per_step"] / 1e3), "ms_per_step": r["ms_per_step"],
+                      "launches_per_step": r["launches"] / args.steps, **accuracy.get(f, {})}
+                  for f, r in results.items()},
+        "delta_epe_px": accuracy.get(head, {}).get("delta_epe_px"),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    for r in results.values():
+        r["ctx"].close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm: the CPU oracle
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2305_11566_gb300 import synth
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    shape = synth.NET_WIDE
+    params = synth.he_normal_weights(shape, 7)
+    p = synth.make_pair(W, H, DMAX, 1000)
+    for _ in range(args.warmup):
+        oracle.pipeline(shape, params, p.left, p.right, WIN, D)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.pipeline(shape, params, p.left, p.right, WIN, D)
+    el = time.perf_counter() - t
+    value = args.steps / el
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "1 synthetic 1242x375 stereo pair per step, D=48, 9x9 ZNCC window, "
+                               "32/64/128 encoder, 128 latent, 128/64/32 decoder", "global_batch": 1},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                         "sample": f"one pair per step (of the {args.steps} timed), FP64 oracle, {cores} threads"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -178,6 +178,45 @@ SV_API sv_status sv_loss(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, const v
 SV_API sv_status sv_adam_step(sv_ctx* ctx, const void* grad, int step, double lr, double beta1, double beta2, double eps,
                        sv_stream stream);
 
+/* sv_pipeline with HOST buffers: pairs[i].left / right are host pointers (pinned or
+ * pageable; any pitch >= width, no alignment rule) and disp_out[i] host H x W FP32.
+ * The images are copied into the context's device workspace on `stream`, the
+ * pipeline runs there and the results are copied back; returns after the stream has
+ * been synchronised. */
+SV_API sv_status sv_pipeline_host(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, float* const* disp_out,
+                                  sv_stream stream);
+
+/* Per-kernel timing.  While enabled, every kernel the context launches is bracketed by
+ * two CUDA events recorded on the launching stream. */
+typedef struct {
+  char name[32];   /* kernel / layer name */
+  long long launches;
+  double total_ms;
+} sv_profile_entry;
+
+SV_API sv_status sv_profile_enable(sv_ctx* ctx, int enable);
+
+/* Synchronises the pending events, adds them to the per-name totals, copies up to
+ * max_entries totals into out (sorted by name) and sets *n_out to the number of names.
+ * reset != 0 clears the totals afterwards. */
+SV_API sv_status sv_profile_read(sv_ctx* ctx, sv_profile_entry* out, int max_entries, int* n_out, int reset);
+
+/* Waits for `stream` and reports device-side failures recorded since the previous
+ * call: SV_ERR_TIMEOUT if a kernel's bounded wait ran out (the kernel then returned
+ * early and its outputs are undefined), SV_ERR_CUDA for a CUDA error.  Clears the
+ * recorded state. */
+SV_API sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream);
+
+/* Tuning / test options (0 = default where noted):
+ *   "spin_limit"     clock cycles one device-side wait may spin before it gives up
+ *                    (default 4e9, about 2 s)
+ *   "tc_strip_rows"  rows per work item of the tensor-core convolutions (0 = automatic)
+ * Returns SV_ERR_INVALID_ARG for an unknown key or a value out of range. */
+SV_API sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value);
+
+/* Number of kernels the context has launched since it was created. */
+SV_API long long sv_launch_count(const sv_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

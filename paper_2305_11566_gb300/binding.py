@@ -32,6 +32,10 @@ class SvPair(ctypes.Structure):
                 ("max_disp", c_int)]
 
 
+class SvProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong), ("total_ms", c_double)]
+
+
 class SvError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{_status_name(status)}: {msg}")
@@ -60,6 +64,12 @@ API = {
                  POINTER(c_void_p), c_double, c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
                  c_void_p], c_int),
     "sv_adam_step": ([c_void_p, c_void_p, c_int, c_double, c_double, c_double, c_double, c_void_p], c_int),
+    "sv_pipeline_host": ([c_void_p, POINTER(SvPair), c_int, POINTER(c_void_p), c_void_p], c_int),
+    "sv_profile_enable": ([c_void_p, c_int], c_int),
+    "sv_profile_read": ([c_void_p, POINTER(SvProfileEntry), c_int, POINTER(c_int), c_int], c_int),
+    "sv_launch_count": ([c_void_p], ctypes.c_longlong),
+    "sv_synchronize": ([c_void_p, c_void_p], c_int),
+    "sv_set_option": ([c_void_p, c_char_p, ctypes.c_longlong], c_int),
 }
 
 
@@ -226,6 +236,34 @@ class Context:
         self._check(lib().sv_pipeline(self._h, _pairs_array(pairs), len(pairs), _ptrs(outs), _stream(stream)))
         return outs
 
+    def pipeline_host(self, lefts, rights, widths, heights, pitches, Ds, outs, stream=None):
+        """sv_pipeline_host: host images (numpy / pinned torch tensors) in, host results out."""
+        arr = (SvPair * max(1, len(lefts)))()
+        for i in range(len(lefts)):
+            arr[i] = SvPair(_host_ptr(lefts[i]), _host_ptr(rights[i]), widths[i], heights[i], pitches[i], Ds[i])
+        optr = (c_void_p * max(1, len(outs)))(*[_host_ptr(o) for o in outs])
+        self._check(lib().sv_pipeline_host(self._h, arr, len(lefts), optr, _stream(stream)))
+        return outs
+
+    # ---------------------------------------------------------------- profiling
+    def profile(self, enable: bool):
+        self._check(lib().sv_profile_enable(self._h, int(enable)))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        buf = (SvProfileEntry * 64)()
+        n = c_int()
+        self._check(lib().sv_profile_read(self._h, buf, 64, ctypes.byref(n), int(reset)))
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(n.value, 64))}
+
+    def synchronize(self, stream=None):
+        self._check(lib().sv_synchronize(self._h, _stream(stream)))
+
+    def set_option(self, key: str, value: int):
+        self._check(lib().sv_set_option(self._h, key.encode(), int(value)))
+
+    def launch_count(self) -> int:
+        return int(lib().sv_launch_count(self._h))
+
     # ---------------------------------------------------------------- training
     def refine_train(self, pairs, coarse, eps, stream=None):
         import torch
@@ -269,6 +307,12 @@ class Context:
     def adam_step(self, grad, step: int, lr=5e-4, beta1=0.99, beta2=0.999, eps=1e-8, stream=None):
         self._check(lib().sv_adam_step(self._h, c_void_p(grad.data_ptr()), int(step), lr, beta1, beta2, eps,
                                        _stream(stream)))
+
+
+def _host_ptr(a):
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
 
 
 def latent_hw(H: int, W: int):

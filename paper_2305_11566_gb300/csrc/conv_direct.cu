@@ -61,12 +61,21 @@ struct SrcEnc1 {
   }
 };
 
+template <typename OutT, typename T> __device__ __forceinline__ OutT to_out(T v) { return (OutT)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16, float>(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <typename T, typename InT> __device__ __forceinline__ T from_in(InT v) { return (T)v; }
+template <> __device__ __forceinline__ float from_in<float, __nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+
 // One CTA: TH x TW output pixels x COT output channels; input channels in chunks of CIC
 // staged channel-planar in shared memory ([ci][row][col]) with the weights [tap][ci][co].
-template <typename T, typename Src, int S, int KS, int COT, int CIC>
+template <typename T, typename Src, int S, int KS, int COT, int CIC, typename OutT>
 __global__ void __launch_bounds__(TW * TH)
 conv_direct_kernel(Src src, int Ci, const T* __restrict__ wt, const T* __restrict__ bias, int Co, int Ho, int Wo,
-                   int relu, T* __restrict__ out) {
+                   int relu, OutT* __restrict__ out) {
   constexpr int PAD = KS / 2;
   constexpr int TR = (TH - 1) * S + KS, TC = (TW - 1) * S + KS;
   __shared__ T tile[CIC][TR][TC];
@@ -104,13 +113,13 @@ conv_direct_kernel(Src src, int Ci, const T* __restrict__ wt, const T* __restric
     __syncthreads();
   }
   if (X < Wo && Y < Ho) {
-    T* op = out + ((size_t)Y * Wo + X) * Co + co0;
+    OutT* op = out + ((size_t)Y * Wo + X) * Co + co0;
 #pragma unroll
     for (int c = 0; c < COT; ++c) {
       if (co0 + c < Co) {
         T v = acc[c] + bias[co0 + c];
         if (relu && v < (T)0) v = (T)0;
-        op[c] = v;
+        op[c] = to_out<OutT, T>(v);
       }
     }
   }
@@ -120,19 +129,20 @@ template <typename T> struct Cfg;
 template <> struct Cfg<float> { static constexpr int COT = 32, CIC = 8; };
 template <> struct Cfg<double> { static constexpr int COT = 16, CIC = 8; };
 
-template <typename T, typename Src, int S, int KS, int CIC = Cfg<T>::CIC>
-cudaError_t run_conv(const Src& src, int Ci, const T* wt, const T* bias, int Co, int Ho, int Wo, int relu, T* out,
+template <typename T, typename Src, int S, int KS, int CIC = Cfg<T>::CIC, typename OutT = T>
+cudaError_t run_conv(const Src& src, int Ci, const T* wt, const T* bias, int Co, int Ho, int Wo, int relu, OutT* out,
                      cudaStream_t st) {
   constexpr int COT = Cfg<T>::COT;
   dim3 grid((Wo + TW - 1) / TW, (Ho + TH - 1) / TH, (Co + COT - 1) / COT);
-  conv_direct_kernel<T, Src, S, KS, COT, CIC><<<grid, dim3(TW, TH), 0, st>>>(src, Ci, wt, bias, Co, Ho, Wo, relu, out);
+  conv_direct_kernel<T, Src, S, KS, COT, CIC, OutT>
+      <<<grid, dim3(TW, TH), 0, st>>>(src, Ci, wt, bias, Co, Ho, Wo, relu, out);
   return cudaGetLastError();
 }
 
 // final layer: Y = U + b + sum_{tap, ci} w * d3 (zero padded), one pixel per thread
-template <typename T, typename CoarseT, typename OutT>
+template <typename T, typename CoarseT, typename OutT, typename InT = T>
 __global__ void __launch_bounds__(256)
-final_kernel(const T* __restrict__ in, int W, int H, int Ci, const T* __restrict__ wt, const T* __restrict__ bias,
+final_kernel(const InT* __restrict__ in, int W, int H, int Ci, const T* __restrict__ wt, const T* __restrict__ bias,
              const CoarseT* __restrict__ coarse, int w, int h, OutT* __restrict__ Y) {
   extern __shared__ __align__(16) unsigned char fsm[];
   T* ws = reinterpret_cast<T*>(fsm);
@@ -147,9 +157,9 @@ final_kernel(const T* __restrict__ in, int W, int H, int Ci, const T* __restrict
     for (int kx = 0; kx < 3; ++kx) {
       int vx = X + kx - 1;
       if (vx < 0 || vx >= W) continue;
-      const T* ip = in + ((size_t)vy * W + vx) * Ci;
+      const InT* ip = in + ((size_t)vy * W + vx) * Ci;
       const T* wp = ws + (ky * 3 + kx) * Ci;
-      for (int ci = 0; ci < Ci; ++ci) acc = fma(wp[ci], ip[ci], acc);
+      for (int ci = 0; ci < Ci; ++ci) acc = fma(wp[ci], from_in<T, InT>(ip[ci]), acc);
     }
   }
   Y[(size_t)Yy * W + X] = (OutT)(upsample4_at<T, CoarseT>(coarse, w, h, X, Yy) + acc);
@@ -223,6 +233,22 @@ cudaError_t launch_latent(const T* e3, int P, int Ci, const T* wmu, const T* bmu
                           const T* eps, T* mu, T* lv, T* z, cudaStream_t st) {
   size_t n = (size_t)P * lat;
   latent_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e3, P, Ci, wmu, bmu, wlv, blv, lat, eps, mu, lv, z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_enc1_bf16(const uint8_t* L, int pitch, int W, int H, const int16_t* coarse, int w, int h,
+                             const float* wt, const float* bias, int Co, __nv_bfloat16* out, cudaStream_t st) {
+  SrcEnc1<float, int16_t> s{L, pitch, W, H, coarse, w, h};
+  Levels lv(H, W);
+  return run_conv<float, SrcEnc1<float, int16_t>, 2, 3, 2, __nv_bfloat16>(s, 2, wt, bias, Co, lv.H[1], lv.W[1], 1, out,
+                                                                          st);
+}
+
+cudaError_t launch_final_bf16(const __nv_bfloat16* in, int W, int H, int Ci, const float* wt, const float* bias,
+                              const int16_t* coarse, int w, int h, float* Y, cudaStream_t st) {
+  dim3 grid((W + 127) / 128, H);
+  final_kernel<float, int16_t, float, __nv_bfloat16><<<grid, 128, sizeof(float) * 9 * Ci, st>>>(in, W, H, Ci, wt, bias,
+                                                                                               coarse, w, h, Y);
   return cudaGetLastError();
 }
 

@@ -1,13 +1,716 @@
-// conv_tc.cu -- implicit-GEMM convolutions on the tcgen05 tensor cores (BF16 operands,
-// FP32 accumulation in tensor memory).
+// conv_tc.cu -- refinement convolutions as implicit GEMMs on the tcgen05 tensor cores:
+// BF16 operands in shared memory, FP32 accumulators in tensor memory (TMEM).
+//
+// GEMM view of one tile: M = 128 consecutive output units of one row, N = NT output
+// channels, K = taps x Cin.  Instead of an im2col copy per tap, the input rows a tile
+// needs are staged ONCE in shared memory in a K-major "planes" layout (plane c holds
+// channels 8c..8c+7 of every staged pixel, 16 bytes per pixel, pixels contiguous), so the
+// A operand of every tap is the same staged rows seen from a shifted start address
+// (matrix descriptor: no swizzle, LBO = plane stride, SBO = 128 B).  Consecutive tiles of
+// a CTA walk down the rows of a column strip and reuse staged rows (ring of row slots).
+//
+// Modes:
+//   TM_S2  3x3 stride-2 conv (encoder): staged rows 2i-1, 2i, 2i+1 with odd and even
+//          pixels de-interleaved into two plane sets, so each tap is a unit-stride view.
+//   TM_UP2 nearest-x2 upsample + 3x3 conv (decoder), computed as four output phases
+//          (py, px) of 2x2 convs on the low-resolution input with the 3x3 weights summed
+//          per phase (rows/cols {0} and {1,2} for phase 0, {0,1} and {2} for phase 1):
+//          4 taps per output instead of 9.  The last row / column of an odd-sized
+//          (cropped) output is recomputed exactly by up2_border_fix afterwards.
+//   TM_P1  1x1 conv (latent mean head).
+//
+// Warp roles (256 threads): warps 0-3 epilogue (TMEM lanes 0-127: tcgen05.ld, bias,
+// ReLU, BF16 store), warp 4 TMEM allocation + one thread issuing tcgen05.mma, warps 5-7
+// producers (cp.async with zero fill for the halo).  Every wait is bounded; on timeout
+// the kernel records an error code and returns.
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
 #include "sv_ctx.cuh"
 
 namespace sv {
 
-sv_status Ctx::pack_bf16_weights() { return SV_OK; }
+namespace tc {
 
-sv_status Ctx::refine_tc(const sv_pair*, const int16_t* const*, int, float* const*, cudaStream_t) {
-  return fail(SV_ERR_UNSUPPORTED, "BF16 tensor-core refinement not built yet");
+using bf16 = __nv_bfloat16;
+
+enum Mode { TM_S2 = 0, TM_UP2 = 1, TM_P1 = 2 };
+
+struct LayerPair {
+  const bf16* in;
+  bf16* out;
+  int Hi, Wi;  // input size
+  int Ho, Wo;  // output size
+  int Hu, Wu;  // unit grid covered by tiles (S2 / P1: output; UP2: low-resolution input)
+};
+
+struct Strip {
+  int pair, j0, i0, cnt;
+};
+
+struct Params {
+  const LayerPair* lp;
+  const Strip* strips;
+  int n_strips;
+  const bf16* wpack;  // [G][T][NT * cin] in the core-matrix layout
+  const float* bias;  // [cout]
+  int cin, cout, G, relu, ring;
+  int* err;
+  long long spin;
+};
+
+template <int MODE> struct Geo;
+template <> struct Geo<TM_S2> { static constexpr int RA = 3, STEP = 2, NPX = 258, T = 9; };
+template <> struct Geo<TM_UP2> { static constexpr int RA = 2, STEP = 1, NPX = 129, T = 4; };
+template <> struct Geo<TM_P1> { static constexpr int RA = 1, STEP = 1, NPX = 128, T = 1; };
+
+constexpr int kThreads = 256;
+constexpr int kProducerWarps = 3;
+constexpr int kBarBytes = 8;
+
+__host__ __device__ inline size_t row_bytes(int mode, int cin) {
+  const int npx = mode == TM_S2 ? 258 : mode == TM_UP2 ? 129 : 128;
+  return (size_t)(cin / 8) * npx * 16;
+}
+__host__ __device__ inline int taps(int mode) { return mode == TM_S2 ? 9 : mode == TM_UP2 ? 4 : 1; }
+__host__ __device__ inline size_t b_bytes(int mode, int NT, int cin) { return (size_t)taps(mode) * NT * cin * 2; }
+__host__ __device__ inline size_t smem_bytes(int mode, int NT, int cin, int ring) {
+  return 1024 + b_bytes(mode, NT, cin) + (size_t)ring * row_bytes(mode, cin) + (size_t)(2 * ring + 4) * kBarBytes + 16;
+}
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+// Wait for the phase with the given parity to complete; false after `spin` cycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long spin) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > spin) return false;
+  }
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
+
+// K-major, no-swizzle shared-memory matrix descriptor (tcgen05 format: bits 46-48 = 0b001).
+__device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%"
+      "20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ geometry
+// first input row staged for unit row i (phase row py for UP2)
+template <int MODE>
+__device__ __forceinline__ int first_row(int i, int py) {
+  return MODE == TM_S2 ? 2 * i - 1 : MODE == TM_UP2 ? i + py - 1 : i;
+}
+// input column of staged pixel t for the strip starting at unit column j0
+template <int MODE>
+__device__ __forceinline__ int staged_col(int t, int j0, int px) {
+  if (MODE == TM_S2) return t < 129 ? 2 * (j0 + t) - 1 : 2 * (j0 + t - 129);
+  if (MODE == TM_UP2) return j0 + px - 1 + t;
+  return j0 + t;
+}
+// (staged row offset, staged pixel start) of tap t
+template <int MODE>
+__device__ __forceinline__ void tap_geo(int t, int& row, int& col) {
+  if (MODE == TM_S2) {
+    row = t / 3;
+    const int dx = t % 3;
+    col = dx == 0 ? 0 : dx == 1 ? 129 : 1;
+  } else if (MODE == TM_UP2) {
+    row = t >> 1;
+    col = t & 1;
+  } else {
+    row = 0;
+    col = 0;
+  }
+}
+
+template <int MODE, int NT>
+__global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_constant__ Params p) {
+  using G_ = Geo<MODE>;
+  constexpr int RA = G_::RA, STEP = G_::STEP, NPX = G_::NPX, T = G_::T;
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  const int cin = p.cin, ring = p.ring;
+  const int kplanes = cin / 8;
+  const uint32_t plane = NPX * 16;
+  const uint32_t rowb = kplanes * plane;
+  const uint32_t sB = base;
+  const uint32_t sA = sB + (uint32_t)T * NT * cin * 2;
+  const uint32_t bars = sA + (uint32_t)ring * rowb;
+  const uint32_t full0 = bars, empty0 = bars + ring * 8, accf0 = bars + 2 * ring * 8, acce0 = accf0 + 16;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + (acce0 + 16 - base));
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = blockIdx.x % p.G, crank = blockIdx.x / p.G, cpg = gridDim.x / p.G;
+  const int phase = MODE == TM_UP2 ? (g & 3) : 0;
+  const int nslice = MODE == TM_UP2 ? (g >> 2) : g;
+  const int py = phase >> 1, px = phase & 1;
+  const int n0 = nslice * NT;
+
+  // ---- weights of this CTA's set, resident for the kernel's lifetime
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(p.wpack + (size_t)g * T * NT * cin);
+    uint4* dst = reinterpret_cast<uint4*>(gbase);
+    const int n16 = T * NT * cin / 8;
+    for (int e = tid; e < n16; e += kThreads) dst[e] = src[e];
+  }
+  if (tid == 0) {
+    for (int r = 0; r < ring; ++r) {
+      mbar_init(full0 + 8 * r, 32);
+      mbar_init(empty0 + 8 * r, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_proxy_async();
+  constexpr uint32_t kCols = NT * 2 <= 32 ? 32 : NT * 2 <= 64 ? 64 : NT * 2 <= 128 ? 128 : NT * 2 <= 256 ? 256 : 512;
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  bool ok = true;
+
+  if (warp >= 5) {
+    // ------------------------------------------------------------ producers
+    const int pw = warp - 5;
+    long long q = 0;
+    for (int s = crank; s < p.n_strips && ok; s += cpg) {
+      const Strip st = p.strips[s];
+      const LayerPair L = p.lp[st.pair];
+      const int nrows = STEP * (st.cnt - 1) + RA;
+      const int y0 = first_row<MODE>(st.i0, py);
+      for (int r = 0; r < nrows; ++r, ++q) {
+        if ((int)(q % kProducerWarps) != pw) continue;
+        const int slot = (int)(q % ring);
+        const long long use = q / ring;
+        if (use > 0 && !mbar_wait(empty0 + 8 * slot, (uint32_t)((use - 1) & 1), p.spin)) {
+          atomicCAS(p.err, 0, 1);
+          ok = false;
+          break;
+        }
+        const int y = y0 + r;
+        const bool yok = y >= 0 && y < L.Hi;
+        const uint32_t dst0 = sA + slot * rowb;
+        const bf16* rowp = L.in + (size_t)(yok ? y : 0) * L.Wi * cin;
+        for (int e = lane; e < kplanes * NPX; e += 32) {
+          const int t = e / kplanes, c = e - t * kplanes;
+          const int x = staged_col<MODE>(t, st.j0, px);
+          const bool v = yok && x >= 0 && x < L.Wi;
+          cp_async16(dst0 + c * plane + t * 16, v ? (const void*)(rowp + (size_t)x * cin + c * 8) : (const void*)L.in, v);
+        }
+        cp_async_wait_all();
+        fence_proxy_async();
+        mbar_arrive(full0 + 8 * slot);
+      }
+    }
+  } else if (warp == 4) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((128u >> 4) << 24);
+      long long qbase = 0, tseq = 0;
+      for (int s = crank; s < p.n_strips && ok; s += cpg) {
+        const Strip st = p.strips[s];
+        const int nrows = STEP * (st.cnt - 1) + RA;
+        for (int ii = 0; ii < st.cnt && ok; ++ii) {
+          const int rlo = ii == 0 ? 0 : STEP * (ii - 1) + RA;  // rows not waited for yet
+          for (int r = rlo; r < STEP * ii + RA; ++r) {
+            const long long qa = qbase + r;
+            if (!mbar_wait(full0 + 8 * (int)(qa % ring), (uint32_t)((qa / ring) & 1), p.spin)) {
+              ok = false;
+              break;
+            }
+          }
+          const int buf = (int)(tseq & 1);
+          const long long use = tseq >> 1;
+          if (ok && use > 0 && !mbar_wait(acce0 + 8 * buf, (uint32_t)((use - 1) & 1), p.spin)) ok = false;
+          if (!ok) {
+            atomicCAS(p.err, 0, 2);
+            break;
+          }
+          fence_proxy_async();
+          tc_fence_after();
+          const uint32_t dcol = tmem + (uint32_t)(buf * NT);
+#pragma unroll 1
+          for (int t = 0; t < T; ++t) {
+            int ro, co;
+            tap_geo<MODE>(t, ro, co);
+            const long long qa = qbase + STEP * ii + ro;
+            const uint32_t abase = sA + (uint32_t)(qa % ring) * rowb + co * 16;
+            const uint32_t bbase = sB + (uint32_t)t * NT * cin * 2;
+#pragma unroll 1
+            for (int kk = 0; kk < cin / 16; ++kk) {
+              const uint64_t ad = make_desc(abase + kk * 2 * plane, plane, 128);
+              const uint64_t bd = make_desc(bbase + kk * 256, 128, cin * 16);
+              mma_bf16(dcol, ad, bd, idesc, (t | kk) ? 1u : 0u);
+            }
+          }
+          mma_commit(accf0 + 8 * buf);
+          // release the rows the next tile of this strip no longer reads
+          const int rel_hi = ii + 1 < st.cnt ? STEP * (ii + 1) : nrows;
+          for (int r = STEP * ii; r < rel_hi; ++r) mma_commit(empty0 + 8 * (int)((qbase + r) % ring));
+          ++tseq;
+        }
+        qbase += nrows;
+      }
+      // drain, also after a timeout: the last commit arrives when every MMA issued by this
+      // CTA has completed, so tensor memory is released only once nothing writes to it
+      if (tseq > 0) {
+        const long long last = tseq - 1;
+        if (!mbar_wait(accf0 + 8 * (int)(last & 1), (uint32_t)((last >> 1) & 1), p.spin)) atomicCAS(p.err, 0, 3);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue (warps 0-3)
+    const int m = warp * 32 + lane;
+    long long tseq = 0;
+    for (int s = crank; s < p.n_strips && ok; s += cpg) {
+      const Strip st = p.strips[s];
+      const LayerPair L = p.lp[st.pair];
+      for (int ii = 0; ii < st.cnt; ++ii, ++tseq) {
+        const int buf = (int)(tseq & 1);
+        if (!mbar_wait(accf0 + 8 * buf, (uint32_t)((tseq >> 1) & 1), p.spin)) {
+          atomicCAS(p.err, 0, 4);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int i = st.i0 + ii, j = st.j0 + m;
+        int oy, ox;
+        if (MODE == TM_UP2) {
+          oy = 2 * i + py;
+          ox = 2 * j + px;
+        } else {
+          oy = i;
+          ox = j;
+        }
+        const bool valid = i < L.Hu && j < L.Wu && oy < L.Ho && ox < L.Wo;
+        bf16* op = L.out + ((size_t)oy * L.Wo + ox) * p.cout + n0;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * NT);
+#pragma unroll 1
+        for (int c0 = 0; c0 < NT; c0 += 32) {
+          uint32_t r[32];
+          if (NT >= 32) tmem_ld32(trow + c0, r);
+          else tmem_ld16(trow + c0, r);
+          constexpr int CW = NT >= 32 ? 32 : NT;
+          if (valid) {
+            uint32_t packed[CW / 2];
+#pragma unroll
+            for (int e = 0; e < CW; e += 2) {
+              float a = __uint_as_float(r[e]) + __ldg(p.bias + n0 + c0 + e);
+              float b = __uint_as_float(r[e + 1]) + __ldg(p.bias + n0 + c0 + e + 1);
+              if (p.relu) {
+                a = fmaxf(a, 0.f);
+                b = fmaxf(b, 0.f);
+              }
+              __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+              packed[e / 2] = *reinterpret_cast<uint32_t*>(&h);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(op + c0);
+#pragma unroll
+            for (int v = 0; v < CW / 8; ++v)
+              dst[v] = make_uint4(packed[4 * v], packed[4 * v + 1], packed[4 * v + 2], packed[4 * v + 3]);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(acce0 + 8 * buf);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+}
+
+// ------------------------------------------------------------------ weight packing
+// Packed B of one layer: [G][T][NT rows (output channels) x cin] in the no-swizzle
+// K-major core-matrix layout: element (n, k) at (n%8)*8 + (n/8)*cin*8 + (k%8) + (k/8)*64.
+__global__ void pack_kernel(const float* __restrict__ W, int mode, int NT, int G, int cin, int cout,
+                            bf16* __restrict__ out) {
+  const int T = taps(mode);
+  const size_t total = (size_t)G * T * NT * cin;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int k = (int)(idx % cin);
+  size_t r = idx / cin;
+  const int n = (int)(r % NT);
+  r /= NT;
+  const int t = (int)(r % T);
+  const int g = (int)(r / T);
+  const int nsl = mode == TM_UP2 ? g / 4 : g;
+  const int co = nsl * NT + n;
+  float v = 0.f;
+  if (co < cout) {
+    if (mode == TM_P1) {
+      v = W[(size_t)co * cin + k];
+    } else if (mode == TM_S2) {
+      v = W[((size_t)co * 9 + t) * cin + k];
+    } else {
+      const int ph = g % 4, py = ph >> 1, px = ph & 1, a = t >> 1, b = t & 1;
+      // rows of the 3x3 kernel folded into tap row a of phase py: {0} / {1,2} (py = 0), {0,1} / {2} (py = 1)
+      const int ky0 = py == 0 ? (a == 0 ? 0 : 1) : (a == 0 ? 0 : 2);
+      const int ky1 = py == 0 ? (a == 0 ? 0 : 2) : (a == 0 ? 1 : 2);
+      const int kx0 = px == 0 ? (b == 0 ? 0 : 1) : (b == 0 ? 0 : 2);
+      const int kx1 = px == 0 ? (b == 0 ? 0 : 2) : (b == 0 ? 1 : 2);
+      for (int ky = ky0; ky <= ky1; ++ky)
+        for (int kx = kx0; kx <= kx1; ++kx) v += W[((size_t)co * 9 + ky * 3 + kx) * cin + k];
+    }
+  }
+  const size_t dst = ((size_t)g * T + t) * NT * cin + (size_t)(n % 8) * 8 + (size_t)(n / 8) * cin * 8 + (k % 8) +
+                     (size_t)(k / 8) * 64;
+  out[dst] = __float2bfloat16_rn(v);
+}
+
+// ------------------------------------------------------------------ exact odd borders of UP2
+// Recomputes the last output row (if Ho is odd) and last column (if Wo is odd) of a
+// nearest-x2 + 3x3 conv with the unfolded (BF16-rounded) weights.
+__global__ void up2_border_fix(const LayerPair* __restrict__ lps, const float* __restrict__ W,
+                               const float* __restrict__ bias, int cin, int cout, int relu) {
+  const LayerPair L = lps[blockIdx.y];
+  const int nrow = (L.Ho & 1) ? L.Wo : 0;
+  const int ncol = (L.Wo & 1) ? L.Ho : 0;
+  const int total = (nrow + ncol) * cout;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int co = e % cout, pix = e / cout;
+    int Y, X;
+    if (pix < nrow) {
+      Y = L.Ho - 1;
+      X = pix;
+    } else {
+      Y = pix - nrow;
+      X = L.Wo - 1;
+    }
+    float acc = bias[co];
+    for (int ky = 0; ky < 3; ++ky) {
+      const int vy = Y + ky - 1;
+      if (vy < 0 || vy >= L.Ho) continue;
+      for (int kx = 0; kx < 3; ++kx) {
+        const int vx = X + kx - 1;
+        if (vx < 0 || vx >= L.Wo) continue;
+        const bf16* ip = L.in + ((size_t)(vy >> 1) * L.Wi + (vx >> 1)) * cin;
+        const float* wp = W + ((size_t)co * 9 + ky * 3 + kx) * cin;
+        for (int ci = 0; ci < cin; ++ci)
+          acc = fmaf(__bfloat162float(__float2bfloat16_rn(wp[ci])), __bfloat162float(ip[ci]), acc);
+      }
+    }
+    if (relu) acc = fmaxf(acc, 0.f);
+    L.out[((size_t)Y * L.Wo + X) * cout + co] = __float2bfloat16_rn(acc);
+  }
+}
+
+template <int MODE, int NT>
+cudaError_t launch_mode_nt(const Params& p, int grid, size_t smem, cudaStream_t st) {
+  auto k = conv_tc_kernel<MODE, NT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kThreads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_mode(const Params& p, int NT, int grid, size_t smem, cudaStream_t st) {
+  switch (NT) {
+    case 16: return launch_mode_nt<MODE, 16>(p, grid, smem, st);
+    case 32: return launch_mode_nt<MODE, 32>(p, grid, smem, st);
+    case 64: return launch_mode_nt<MODE, 64>(p, grid, smem, st);
+    case 128: return launch_mode_nt<MODE, 128>(p, grid, smem, st);
+    case 256: return launch_mode_nt<MODE, 256>(p, grid, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_conv(int mode, const Params& p, int NT, int grid, size_t smem, cudaStream_t st) {
+  switch (mode) {
+    case TM_S2: return launch_mode<TM_S2>(p, NT, grid, smem, st);
+    case TM_UP2: return launch_mode<TM_UP2>(p, NT, grid, smem, st);
+    case TM_P1: return launch_mode<TM_P1>(p, NT, grid, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int blocks_per_sm(int mode, int NT, size_t smem) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+#define SV_OCC(M, N)                                                                                   \
+  if (mode == M && NT == N) {                                                                         \
+    cudaFuncSetAttribute(conv_tc_kernel<M, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, conv_tc_kernel<M, N>, kThreads, smem);       \
+  }
+  SV_OCC(TM_S2, 16) SV_OCC(TM_S2, 32) SV_OCC(TM_S2, 64) SV_OCC(TM_S2, 128) SV_OCC(TM_S2, 256)
+  SV_OCC(TM_UP2, 16) SV_OCC(TM_UP2, 32) SV_OCC(TM_UP2, 64) SV_OCC(TM_UP2, 128) SV_OCC(TM_UP2, 256)
+  SV_OCC(TM_P1, 16) SV_OCC(TM_P1, 32) SV_OCC(TM_P1, 64) SV_OCC(TM_P1, 128) SV_OCC(TM_P1, 256)
+#undef SV_OCC
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  // tensor memory: co-resident CTAs must fit 512 columns
+  const int cols = NT * 2 <= 32 ? 32 : NT * 2 <= 64 ? 64 : NT * 2 <= 128 ? 128 : NT * 2 <= 256 ? 256 : 512;
+  return std::max(0, std::min(n, 512 / cols));
+}
+
+}  // namespace tc
+
+// ------------------------------------------------------------------ host side
+namespace {
+
+constexpr size_t kSmemLimit = 232448;  // 227 KB opt-in per block
+
+struct TcLayerPlan {
+  int layer, mode, NT, G, ring, cin, cout, relu;
+  size_t wofs, smem;
+};
+
+}  // namespace
+
+static void plan_layers(const NetDims& net, std::vector<TcLayerPlan>& plans, size_t& total) {
+  plans.clear();
+  total = 0;
+  const int layers[6] = {L_ENC2, L_ENC3, L_MU, L_DEC1, L_DEC2, L_DEC3};
+  for (int l : layers) {
+    TcLayerPlan pl{};
+    pl.layer = l;
+    pl.mode = (l == L_ENC2 || l == L_ENC3) ? tc::TM_S2 : l == L_MU ? tc::TM_P1 : tc::TM_UP2;
+    pl.cin = net.cin(l);
+    pl.cout = net.cout(l);
+    pl.relu = l != L_MU;
+    const int RA = pl.mode == tc::TM_S2 ? 3 : pl.mode == tc::TM_UP2 ? 2 : 1;
+    const int STEP = pl.mode == tc::TM_S2 ? 2 : 1;
+    int NT = pl.cout;
+    int ring = RA + STEP;
+    while (true) {
+      size_t sm = tc::smem_bytes(pl.mode, NT, pl.cin, ring);
+      if (sm <= kSmemLimit) break;
+      if (ring > RA) { --ring; continue; }
+      NT /= 2;
+      ring = RA + STEP;
+    }
+    // spend leftover shared memory on deeper row prefetch
+    while (ring < RA + 3 * STEP && tc::smem_bytes(pl.mode, NT, pl.cin, ring + 1) <= kSmemLimit) ++ring;
+    pl.NT = NT;
+    pl.ring = ring;
+    const int nsl = (pl.cout + NT - 1) / NT;
+    pl.G = pl.mode == tc::TM_UP2 ? 4 * nsl : nsl;
+    pl.smem = tc::smem_bytes(pl.mode, NT, pl.cin, ring);
+    pl.wofs = total;
+    total += (size_t)pl.G * tc::taps(pl.mode) * NT * pl.cin;
+    plans.push_back(pl);
+  }
+}
+
+sv_status Ctx::pack_bf16_weights() {
+  std::vector<TcLayerPlan> plans;
+  size_t total;
+  plan_layers(net, plans, total);
+  sv_status s = cuda(wbf.ensure(total * sizeof(__nv_bfloat16)), "alloc packed weights");
+  if (s) return s;
+  for (auto& pl : plans) {
+    const size_t n = (size_t)pl.G * tc::taps(pl.mode) * pl.NT * pl.cin;
+    tc::pack_kernel<<<(unsigned)((n + 255) / 256), 256>>>((const float*)w32.p + net.w_off(pl.layer), pl.mode, pl.NT,
+                                                           pl.G, pl.cin, pl.cout, (__nv_bfloat16*)wbf.p + pl.wofs);
+    if ((s = cuda(cudaGetLastError(), "pack weights"))) return s;
+  }
+  return SV_OK;
+}
+
+sv_status Ctx::refine_tc(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out,
+                         cudaStream_t st) {
+  using tc::LayerPair;
+  using tc::Strip;
+  std::vector<TcLayerPlan> plans;
+  size_t wtotal;
+  plan_layers(net, plans, wtotal);
+  sv_status s;
+  int dev = device, nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // ---- activations (BF16, NHWC, all pairs back to back): e1 e2 e3 z d1 d2 d3
+  std::vector<Levels> lv(n);
+  size_t cnt[7] = {0};
+  std::vector<std::array<size_t, 7>> off(n);
+  for (int i = 0; i < n; ++i) {
+    lv[i] = Levels(pairs[i].height, pairs[i].width);
+    const size_t P[4] = {(size_t)lv[i].H[0] * lv[i].W[0], (size_t)lv[i].H[1] * lv[i].W[1],
+                         (size_t)lv[i].H[2] * lv[i].W[2], (size_t)lv[i].H[3] * lv[i].W[3]};
+    const size_t need[7] = {P[1] * net.enc[0], P[2] * net.enc[1], P[3] * net.enc[2], P[3] * net.lat,
+                            P[2] * net.dec[0], P[1] * net.dec[1], P[0] * net.dec[2]};
+    for (int k = 0; k < 7; ++k) {
+      off[i][k] = cnt[k];
+      cnt[k] += (need[k] + 7) / 8 * 8;  // 16-byte aligned per pair
+    }
+  }
+  for (int k = 0; k < 7; ++k)
+    if ((s = cuda(tc_act[k].ensure(std::max<size_t>(cnt[k], 8) * sizeof(__nv_bfloat16)), "alloc bf16 activations")))
+      return s;
+  auto act = [&](int k, int i) { return (__nv_bfloat16*)tc_act[k].p + off[i][k]; };
+  int* d_err = (int*)err_flag.p;
+
+  // ---- tables: per layer, LayerPair[n] and its strips
+  struct LayerTab {
+    size_t lp_ofs, strip_ofs;
+    int n_strips, grid;
+  };
+  std::vector<unsigned char> host;
+  auto put = [&](const void* src, size_t bytes) {
+    size_t o = (host.size() + 15) / 16 * 16;
+    host.resize(o + bytes);
+    memcpy(host.data() + o, src, bytes);
+    return o;
+  };
+  std::vector<LayerTab> tabs(plans.size());
+  for (size_t li = 0; li < plans.size(); ++li) {
+    const TcLayerPlan& pl = plans[li];
+    std::vector<LayerPair> lps(n);
+    const int in_act = pl.layer == L_ENC2 ? 0 : pl.layer == L_ENC3 ? 1 : pl.layer == L_MU ? 2 : pl.layer == L_DEC1 ? 3
+                       : pl.layer == L_DEC2 ? 4 : 5;
+    const int out_act = in_act + 1;
+    const int lin = pl.layer == L_ENC2 ? 1 : pl.layer == L_ENC3 ? 2 : pl.layer == L_MU ? 3 : pl.layer == L_DEC1 ? 3
+                    : pl.layer == L_DEC2 ? 2 : 1;
+    const int lout = pl.layer == L_ENC2 ? 2 : pl.layer == L_ENC3 ? 3 : pl.layer == L_MU ? 3 : pl.layer == L_DEC1 ? 2
+                     : pl.layer == L_DEC2 ? 1 : 0;
+    long long units = 0;
+    for (int i = 0; i < n; ++i) {
+      LayerPair& L = lps[i];
+      L.in = act(in_act, i);
+      L.out = act(out_act, i);
+      L.Hi = lv[i].H[lin]; L.Wi = lv[i].W[lin];
+      L.Ho = lv[i].H[lout]; L.Wo = lv[i].W[lout];
+      if (pl.mode == tc::TM_UP2) { L.Hu = L.Hi; L.Wu = L.Wi; }
+      else { L.Hu = L.Ho; L.Wu = L.Wo; }
+      units += (long long)L.Hu * ((L.Wu + 127) / 128);
+    }
+    int bps = tc::blocks_per_sm(pl.mode, pl.NT, pl.smem);
+    if (bps <= 0) return fail(SV_ERR_UNSUPPORTED, "layer %d: tensor-core kernel does not fit an SM", pl.layer);
+    int grid = std::max(pl.G, (nsm * bps) / pl.G * pl.G);
+    const int cpg = grid / pl.G;
+    // strip height: about four strips per CTA of a weight set, at least 2 rows
+    const long long want = std::max<long long>(1, (long long)cpg * 4);
+    const int hs = tc_strip_rows > 0 ? tc_strip_rows : (int)std::max<long long>(2, (units + want - 1) / want);
+    std::vector<Strip> strips;
+    for (int i = 0; i < n; ++i)
+      for (int j0 = 0; j0 < lps[i].Wu; j0 += 128)
+        for (int i0 = 0; i0 < lps[i].Hu; i0 += hs) strips.push_back({i, j0, i0, std::min(hs, lps[i].Hu - i0)});
+    grid = std::min<long long>(grid, (long long)pl.G * (long long)strips.size());
+    tabs[li].lp_ofs = put(lps.data(), sizeof(LayerPair) * n);
+    tabs[li].strip_ofs = put(strips.data(), sizeof(Strip) * strips.size());
+    tabs[li].n_strips = (int)strips.size();
+    tabs[li].grid = grid;
+  }
+  if ((s = cuda(tc_tables.ensure(host.size()), "alloc tables"))) return s;
+  if ((s = cuda(cudaMemcpyAsync(tc_tables.p, host.data(), host.size(), cudaMemcpyHostToDevice, st), "upload tables")))
+    return s;
+  tc_host_tables.swap(host);  // keep the source alive until the copy has executed
+
+  const float* W = (const float*)w32.p;
+  // ---- enc1: bilinear x4 + normalisation fused into the first conv (CUDA cores, BF16 out)
+  for (int i = 0; i < n; ++i) {
+    const sv_pair& p = pairs[i];
+    LaunchScope ls(*this, "enc1_bf16", st);
+    if ((s = cuda(launch_enc1_bf16(p.left, p.pitch, p.width, p.height, coarse[i], p.width / 4, p.height / 4,
+                                   W + net.w_off(L_ENC1), W + net.b_off(L_ENC1), net.enc[0], act(0, i), st),
+                  "enc1")))
+      return s;
+  }
+  static const char* names[6] = {"tc_enc2", "tc_enc3", "tc_latent", "tc_dec1", "tc_dec2", "tc_dec3"};
+  for (size_t li = 0; li < plans.size(); ++li) {
+    const TcLayerPlan& pl = plans[li];
+    tc::Params prm{};
+    prm.lp = (const LayerPair*)((unsigned char*)tc_tables.p + tabs[li].lp_ofs);
+    prm.strips = (const Strip*)((unsigned char*)tc_tables.p + tabs[li].strip_ofs);
+    prm.n_strips = tabs[li].n_strips;
+    prm.wpack = (const __nv_bfloat16*)wbf.p + pl.wofs;
+    prm.bias = W + net.b_off(pl.layer);
+    prm.cin = pl.cin;
+    prm.cout = pl.cout;
+    prm.G = pl.G;
+    prm.relu = pl.relu;
+    prm.ring = pl.ring;
+    prm.err = d_err;
+    prm.spin = spin_limit;
+    {
+      LaunchScope ls(*this, names[li], st);
+      if ((s = cuda(tc::launch_conv(pl.mode, prm, pl.NT, tabs[li].grid, pl.smem, st), names[li]))) return s;
+    }
+    if (pl.mode == tc::TM_UP2) {
+      LaunchScope ls(*this, "up2_border_fix", st);
+      tc::up2_border_fix<<<dim3(8, n), 256, 0, st>>>(prm.lp, W + net.w_off(pl.layer), prm.bias, pl.cin, pl.cout, 1);
+      if ((s = cuda(cudaGetLastError(), "border fix"))) return s;
+    }
+  }
+  // ---- final conv + residual (CUDA cores, FP32)
+  for (int i = 0; i < n; ++i) {
+    const sv_pair& p = pairs[i];
+    LaunchScope ls(*this, "final_bf16", st);
+    if ((s = cuda(launch_final_bf16(act(6, i), p.width, p.height, net.dec[2], W + net.w_off(L_FINAL),
+                                    W + net.b_off(L_FINAL), coarse[i], p.width / 4, p.height / 4, out[i], st),
+                  "final")))
+      return s;
+  }
+  return SV_OK;
 }
 
 }  // namespace sv

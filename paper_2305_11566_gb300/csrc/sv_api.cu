@@ -132,6 +132,7 @@ sv_status Ctx::coarse(const sv_pair* pairs, int n, int16_t* const* disp, float* 
   if ((s = cuda(cudaMemcpyAsync(zjobs.p, jobs.data(), sizeof(ZJob) * jobs.size(), cudaMemcpyHostToDevice, st),
                 "upload jobs")))
     return s;
+  LaunchScope ls(*this, "zncc_wta", st);
   return cuda(launch_zncc_wta((const ZPair*)zpairs.p, (const ZJob*)zjobs.p, (int)jobs.size(), cfg.window / 2, maxD, st),
               "zncc_wta launch");
 }
@@ -162,28 +163,38 @@ sv_status Ctx::refine_direct(const sv_pair& p, const void* coarse_map, bool coar
   }
   T *e1 = buf[0], *e2 = buf[1], *e3 = buf[2], *z = buf[3], *d1 = buf[4], *d2 = buf[5], *d3 = buf[6];
   cudaError_t e;
+#define SV_SCOPE(n) LaunchScope _ls_##n(*this, #n, st)
+  {
+  SV_SCOPE(enc1);
   if (coarse_int16)
     e = launch_enc1<T, int16_t>(p.left, p.pitch, p.width, p.height, (const int16_t*)coarse_map, w, h, Wl(L_ENC1),
                                 Bl(L_ENC1), net.enc[0], e1, st);
   else
     e = launch_enc1<T, T>(p.left, p.pitch, p.width, p.height, (const T*)coarse_map, w, h, Wl(L_ENC1), Bl(L_ENC1),
                           net.enc[0], e1, st);
+  }
   if ((s = cuda(e, "enc1"))) return s;
   DirectConvArgs<T> a{e1, lv.H[1], lv.W[1], net.enc[0], Wl(L_ENC2), Bl(L_ENC2), net.enc[1], lv.H[2], lv.W[2], 1, e2};
-  if ((s = cuda(launch_conv_direct<T>(a, CM_S2, 3, st), "enc2"))) return s;
+  { SV_SCOPE(enc2); s = cuda(launch_conv_direct<T>(a, CM_S2, 3, st), "enc2"); }
+  if (s) return s;
   a = {e2, lv.H[2], lv.W[2], net.enc[1], Wl(L_ENC3), Bl(L_ENC3), net.enc[2], lv.H[3], lv.W[3], 1, e3};
-  if ((s = cuda(launch_conv_direct<T>(a, CM_S2, 3, st), "enc3"))) return s;
+  { SV_SCOPE(enc3); s = cuda(launch_conv_direct<T>(a, CM_S2, 3, st), "enc3"); }
+  if (s) return s;
   const bool train = eps != nullptr || lv_out != nullptr;
-  if ((s = cuda(launch_latent<T>(e3, (int)P3, net.enc[2], Wl(L_MU), Bl(L_MU), Wl(L_LV), Bl(L_LV), net.lat, eps, mu_out,
+  { SV_SCOPE(latent); s = cuda(launch_latent<T>(e3, (int)P3, net.enc[2], Wl(L_MU), Bl(L_MU), Wl(L_LV), Bl(L_LV), net.lat, eps, mu_out,
                                  train ? lv_out : nullptr, z, st),
-                "latent")))
-    return s;
+                "latent"); }
+  if (s) return s;
   a = {z, lv.H[3], lv.W[3], net.lat, Wl(L_DEC1), Bl(L_DEC1), net.dec[0], lv.H[2], lv.W[2], 1, d1};
-  if ((s = cuda(launch_conv_direct<T>(a, CM_UP2, 3, st), "dec1"))) return s;
+  { SV_SCOPE(dec1); s = cuda(launch_conv_direct<T>(a, CM_UP2, 3, st), "dec1"); }
+  if (s) return s;
   a = {d1, lv.H[2], lv.W[2], net.dec[0], Wl(L_DEC2), Bl(L_DEC2), net.dec[1], lv.H[1], lv.W[1], 1, d2};
-  if ((s = cuda(launch_conv_direct<T>(a, CM_UP2, 3, st), "dec2"))) return s;
+  { SV_SCOPE(dec2); s = cuda(launch_conv_direct<T>(a, CM_UP2, 3, st), "dec2"); }
+  if (s) return s;
   a = {d2, lv.H[1], lv.W[1], net.dec[1], Wl(L_DEC3), Bl(L_DEC3), net.dec[2], lv.H[0], lv.W[0], 1, d3};
-  if ((s = cuda(launch_conv_direct<T>(a, CM_UP2, 3, st), "dec3"))) return s;
+  { SV_SCOPE(dec3); s = cuda(launch_conv_direct<T>(a, CM_UP2, 3, st), "dec3"); }
+  if (s) return s;
+  SV_SCOPE(final);
   if (coarse_int16)
     e = launch_final<T, int16_t, T>(d3, p.width, p.height, net.dec[2], Wl(L_FINAL), Bl(L_FINAL),
                                     (const int16_t*)coarse_map, w, h, Y, st);
@@ -191,6 +202,7 @@ sv_status Ctx::refine_direct(const sv_pair& p, const void* coarse_map, bool coar
     e = launch_final<T, T, T>(d3, p.width, p.height, net.dec[2], Wl(L_FINAL), Bl(L_FINAL), (const T*)coarse_map, w, h,
                               Y, st);
   return cuda(e, "final");
+#undef SV_SCOPE
 }
 
 template <> const float* Ctx::weights<float>() const { return (const float*)w32.p; }
@@ -282,7 +294,9 @@ sv_status sv_create(const sv_config* cfg, int device, sv_ctx** out) {
   c->net = sv::NetDims{{cfg->enc_ch[0], cfg->enc_ch[1], cfg->enc_ch[2]}, cfg->latent_ch,
                        {cfg->dec_ch[0], cfg->dec_ch[1], cfg->dec_ch[2]}};
   const size_t n = c->net.count();
-  sv_status s = c->cuda(c->w32.ensure(n * sizeof(float)), "alloc weights");
+  sv_status s = c->cuda(c->err_flag.ensure(sizeof(int)), "alloc error flag");
+  if (!s) s = c->cuda(cudaMemset(c->err_flag.p, 0, sizeof(int)), "zero error flag");
+  if (!s) s = c->cuda(c->w32.ensure(n * sizeof(float)), "alloc weights");
   if (!s) s = c->cuda(cudaMemset(c->w32.p, 0, n * sizeof(float)), "zero weights");
   if (!s) s = c->refresh_weight_copies();
   if (s) {
@@ -368,6 +382,118 @@ sv_status sv_pipeline(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, float* con
     if (!disp_out[i]) return c->fail(SV_ERR_INVALID_ARG, "disp_out[%d] is NULL", i);
   DeviceGuard g(c->device);
   return c->pipeline(pairs, n_pairs, disp_out, (cudaStream_t)stream);
+}
+
+sv_status sv_pipeline_host(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, float* const* disp_out,
+                           sv_stream stream) {
+  if (!ctx) return SV_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  c->err.clear();
+  if (n_pairs < 0 || (n_pairs > 0 && (!pairs || !disp_out))) return c->fail(SV_ERR_INVALID_ARG, "bad arguments");
+  if (n_pairs == 0) return SV_OK;
+  std::vector<sv_pair> dev(n_pairs);
+  std::vector<size_t> img_off(n_pairs + 1, 0), out_off(n_pairs + 1, 0);
+  for (int i = 0; i < n_pairs; ++i) {
+    const sv_pair& p = pairs[i];
+    if (!p.left || !p.right || !disp_out[i] || p.pitch < p.width || p.width <= 0 || p.height <= 0)
+      return c->fail(SV_ERR_INVALID_ARG, "pair %d: bad host buffers", i);
+    const int dpitch = (p.width + 15) / 16 * 16;
+    img_off[i + 1] = img_off[i] + 2 * (size_t)dpitch * p.height;
+    out_off[i + 1] = out_off[i] + (size_t)p.width * p.height;
+  }
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  sv_status s = c->cuda(c->host_img.ensure(img_off[n_pairs]), "alloc image staging");
+  if (!s) s = c->cuda(c->host_out.ensure(out_off[n_pairs] * sizeof(float)), "alloc output staging");
+  if (s) return s;
+  std::vector<float*> dout(n_pairs);
+  for (int i = 0; i < n_pairs; ++i) {
+    const sv_pair& p = pairs[i];
+    const int dpitch = (p.width + 15) / 16 * 16;
+    uint8_t* L = (uint8_t*)c->host_img.p + img_off[i];
+    uint8_t* R = L + (size_t)dpitch * p.height;
+    s = c->cuda(cudaMemcpy2DAsync(L, dpitch, p.left, p.pitch, p.width, p.height, cudaMemcpyHostToDevice, st), "H2D");
+    if (!s) s = c->cuda(cudaMemcpy2DAsync(R, dpitch, p.right, p.pitch, p.width, p.height, cudaMemcpyHostToDevice, st),
+                        "H2D");
+    if (s) return s;
+    dev[i] = p;
+    dev[i].left = L;
+    dev[i].right = R;
+    dev[i].pitch = dpitch;
+    dout[i] = (float*)c->host_out.p + out_off[i];
+  }
+  if ((s = c->check_pairs(dev.data(), n_pairs))) return s;
+  if ((s = c->pipeline(dev.data(), n_pairs, dout.data(), st))) return s;
+  for (int i = 0; i < n_pairs; ++i)
+    if ((s = c->cuda(cudaMemcpyAsync(disp_out[i], dout[i], sizeof(float) * pairs[i].width * pairs[i].height,
+                                     cudaMemcpyDeviceToHost, st), "D2H")))
+      return s;
+  return c->cuda(cudaStreamSynchronize(st), "synchronise");
+}
+
+sv_status sv_profile_enable(sv_ctx* ctx, int enable) {
+  if (!ctx) return SV_ERR_INVALID_ARG;
+  reinterpret_cast<Ctx*>(ctx)->prof_on = enable != 0;
+  return SV_OK;
+}
+
+sv_status sv_profile_read(sv_ctx* ctx, sv_profile_entry* out, int max_entries, int* n_out, int reset) {
+  if (!ctx || max_entries < 0 || (max_entries > 0 && !out)) return SV_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  DeviceGuard g(c->device);
+  c->prof_flush();
+  int i = 0;
+  for (auto& kv : c->prof_tot) {
+    if (i < max_entries) {
+      memset(out[i].name, 0, sizeof(out[i].name));
+      strncpy(out[i].name, kv.first.c_str(), sizeof(out[i].name) - 1);
+      out[i].launches = kv.second.first;
+      out[i].total_ms = kv.second.second;
+    }
+    ++i;
+  }
+  if (n_out) *n_out = (int)c->prof_tot.size();
+  if (reset) c->prof_tot.clear();
+  return SV_OK;
+}
+
+sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream) {
+  if (!ctx) return SV_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  DeviceGuard g(c->device);
+  sv_status s = c->cuda(cudaStreamSynchronize((cudaStream_t)stream), "synchronise");
+  if (s) return s;
+  int code = 0;
+  if ((s = c->cuda(cudaMemcpy(&code, c->err_flag.p, sizeof(int), cudaMemcpyDeviceToHost), "read error flag")))
+    return s;
+  if (code) {
+    cudaMemset(c->err_flag.p, 0, sizeof(int));
+    static const char* where[] = {"", "producer", "MMA issuer", "MMA drain", "epilogue"};
+    return c->fail(SV_ERR_TIMEOUT, "a device-side wait ran out (%s, code %d)", code >= 1 && code <= 4 ? where[code] : "?",
+                   code);
+  }
+  return SV_OK;
+}
+
+sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value) {
+  if (!ctx || !key) return SV_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!strcmp(key, "spin_limit")) {
+    if (value < 1) return c->fail(SV_ERR_INVALID_ARG, "spin_limit must be >= 1");
+    c->spin_limit = value;
+    return SV_OK;
+  }
+  if (!strcmp(key, "tc_strip_rows")) {
+    if (value < 0 || value > 4096) return c->fail(SV_ERR_INVALID_ARG, "tc_strip_rows out of range");
+    c->tc_strip_rows = (int)value;
+    return SV_OK;
+  }
+  return c->fail(SV_ERR_INVALID_ARG, "unknown option '%s'", key);
+}
+
+long long sv_launch_count(const sv_ctx* ctx) {
+  if (!ctx) return -1;
+  return reinterpret_cast<const Ctx*>(ctx)->launches;
 }
 
 }  // extern "C"

@@ -1,6 +1,7 @@
 // sv_ctx.cuh -- the library context behind the opaque sv_ctx handle.
 #pragma once
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -35,6 +36,25 @@ struct Ctx {
   DevBuf tc_tables;              // tensor-core job tables
   int adam_t = 0;
   DevBuf adam_m, adam_v;
+  DevBuf host_img, host_out;     // device staging of sv_pipeline_host
+  std::vector<unsigned char> tc_host_tables;
+  long long spin_limit = 4000000000LL;  // clock64 cycles a device-side wait may spin
+  int tc_strip_rows = 0;                // 0: automatic
+  DevBuf err_flag;                      // device int: first failure code of a kernel
+
+  // launch accounting and optional per-kernel event timing
+  long long launches = 0;
+  bool prof_on = false;
+  struct ProfRec { std::string name; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> ev_free;
+  std::map<std::string, std::pair<long long, double>> prof_tot;
+  cudaEvent_t take_event() {
+    cudaEvent_t e = nullptr;
+    if (!ev_free.empty()) { e = ev_free.back(); ev_free.pop_back(); }
+    else cudaEventCreate(&e);
+    return e;
+  }
 
   sv_status fail(sv_status s, const char* fmt, ...);
   sv_status cuda(cudaError_t e, const char* what);
@@ -53,7 +73,25 @@ struct Ctx {
   sv_status pack_bf16_weights();
   sv_status refine_tc(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out, cudaStream_t st);
 
+  void prof_flush() {
+    for (auto& r : prof_pending) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+        auto& t = prof_tot[r.name];
+        t.first += 1;
+        t.second += ms;
+      }
+      ev_free.push_back(r.a);
+      ev_free.push_back(r.b);
+    }
+    prof_pending.clear();
+  }
+
   void release_all() {
+    prof_flush();
+    for (auto e : ev_free) cudaEventDestroy(e);
+    ev_free.clear();
+    host_img.release(); host_out.release(); err_flag.release();
     w32.release(); w64.release(); wbf.release(); zpairs.release(); zjobs.release(); coarse_maps.release();
     for (auto& b : act) b.release();
     for (auto& b : tc_act) b.release();
@@ -61,4 +99,28 @@ struct Ctx {
   }
 };
 
+}  // namespace sv
+
+namespace sv {
+// Counts one kernel launch and, when profiling is on, brackets it with events.
+struct LaunchScope {
+  Ctx& c;
+  const char* name;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  LaunchScope(Ctx& ctx, const char* n, cudaStream_t s) : c(ctx), name(n), st(s) {
+    ++c.launches;
+    if (c.prof_on) {
+      a = c.take_event();
+      cudaEventRecord(a, st);
+    }
+  }
+  ~LaunchScope() {
+    if (c.prof_on && a) {
+      cudaEvent_t b = c.take_event();
+      cudaEventRecord(b, st);
+      c.prof_pending.push_back({name, a, b});
+    }
+  }
+};
 }  // namespace sv

@@ -4,7 +4,9 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <array>
 #include <cstdint>
+#include <cstring>
 #include <cstddef>
 #include <string>
 #include <vector>
@@ -129,6 +131,12 @@ cudaError_t launch_enc1(const uint8_t* L, int pitch, int W, int H, const CoarseT
 template <typename T, typename CoarseT, typename OutT>
 cudaError_t launch_final(const T* in, int W, int H, int Ci, const T* wt, const T* bias, const CoarseT* coarse,
                          int w, int h, OutT* Y, cudaStream_t st);
+
+// BF16-activation variants used by the tensor-core form (FP32 arithmetic).
+cudaError_t launch_enc1_bf16(const uint8_t* L, int pitch, int W, int H, const int16_t* coarse, int w, int h,
+                             const float* wt, const float* bias, int Co, __nv_bfloat16* out, cudaStream_t st);
+cudaError_t launch_final_bf16(const __nv_bfloat16* in, int W, int H, int Ci, const float* wt, const float* bias,
+                              const int16_t* coarse, int w, int h, float* Y, cudaStream_t st);
 
 // latent heads: mu = 1x1(e3) + b; optionally logvar and z = mu + eps * exp(lv / 2).
 template <typename T>
