@@ -214,6 +214,11 @@ SV_API sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream);
  * Returns SV_ERR_INVALID_ARG for an unknown key or a value out of range. */
 SV_API sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value);
 
+/* Test hook: copies activation `which` (0 e1, 1 e2, 2 e3, 3 z, 4 d1, 5 d2, 6 d3; NHWC
+ * BF16) of pair `pair` of the last SV_BF16 refinement call into host memory `dst`
+ * (`bytes` must equal the activation's size).  Synchronous. */
+SV_API sv_status sv_debug_activation(sv_ctx* ctx, int which, int pair, void* dst, size_t bytes);
+
 /* Number of kernels the context has launched since it was created. */
 SV_API long long sv_launch_count(const sv_ctx* ctx);
 

@@ -70,6 +70,7 @@ API = {
     "sv_launch_count": ([c_void_p], ctypes.c_longlong),
     "sv_synchronize": ([c_void_p, c_void_p], c_int),
     "sv_set_option": ([c_void_p, c_char_p, ctypes.c_longlong], c_int),
+    "sv_debug_activation": ([c_void_p, c_int, c_int, c_void_p, c_size_t], c_int),
 }
 
 
@@ -260,6 +261,14 @@ class Context:
 
     def set_option(self, key: str, value: int):
         self._check(lib().sv_set_option(self._h, key.encode(), int(value)))
+
+    def debug_activation(self, which: int, pair: int, shape) -> np.ndarray:
+        """BF16 activation of the last tensor-core refinement, as float32 [H, W, C]."""
+        import torch
+        n = int(np.prod(shape))
+        buf = torch.empty(n, dtype=torch.bfloat16)
+        self._check(lib().sv_debug_activation(self._h, which, pair, c_void_p(buf.data_ptr()), n * 2))
+        return buf.float().numpy().reshape(shape)
 
     def launch_count(self) -> int:
         return int(lib().sv_launch_count(self._h))

@@ -320,7 +320,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       // CTA has completed, so tensor memory is released only once nothing writes to it
       if (tseq > 0) {
         const long long last = tseq - 1;
-        if (!mbar_wait(accf0 + 8 * (int)(last & 1), (uint32_t)((last >> 1) & 1), p.spin)) atomicCAS(p.err, 0, 3);
+        const long long drain = p.spin > 2000000000LL ? p.spin : 2000000000LL;
+        if (!mbar_wait(accf0 + 8 * (int)(last & 1), (uint32_t)((last >> 1) & 1), drain)) atomicCAS(p.err, 0, 3);
       }
     }
     __syncwarp();
@@ -541,7 +542,7 @@ static void plan_layers(const NetDims& net, std::vector<TcLayerPlan>& plans, siz
     pl.relu = l != L_MU;
     const int RA = pl.mode == tc::TM_S2 ? 3 : pl.mode == tc::TM_UP2 ? 2 : 1;
     const int STEP = pl.mode == tc::TM_S2 ? 2 : 1;
-    int NT = pl.cout;
+    int NT = std::min(256, pl.cout & -pl.cout);  // a power of two dividing cout (widths are multiples of 16)
     int ring = RA + STEP;
     while (true) {
       size_t sm = tc::smem_bytes(pl.mode, NT, pl.cin, ring);
@@ -591,7 +592,7 @@ sv_status Ctx::refine_tc(const sv_pair* pairs, const int16_t* const* coarse, int
   // ---- activations (BF16, NHWC, all pairs back to back): e1 e2 e3 z d1 d2 d3
   std::vector<Levels> lv(n);
   size_t cnt[7] = {0};
-  std::vector<std::array<size_t, 7>> off(n);
+  std::vector<std::array<size_t, 7>> off(n), lens;
   for (int i = 0; i < n; ++i) {
     lv[i] = Levels(pairs[i].height, pairs[i].width);
     const size_t P[4] = {(size_t)lv[i].H[0] * lv[i].W[0], (size_t)lv[i].H[1] * lv[i].W[1],
@@ -602,11 +603,14 @@ sv_status Ctx::refine_tc(const sv_pair* pairs, const int16_t* const* coarse, int
       off[i][k] = cnt[k];
       cnt[k] += (need[k] + 7) / 8 * 8;  // 16-byte aligned per pair
     }
+    lens.push_back({need[0], need[1], need[2], need[3], need[4], need[5], need[6]});
   }
   for (int k = 0; k < 7; ++k)
     if ((s = cuda(tc_act[k].ensure(std::max<size_t>(cnt[k], 8) * sizeof(__nv_bfloat16)), "alloc bf16 activations")))
       return s;
   auto act = [&](int k, int i) { return (__nv_bfloat16*)tc_act[k].p + off[i][k]; };
+  tc_off = off;
+  tc_len = lens;
   int* d_err = (int*)err_flag.p;
 
   // ---- tables: per layer, LayerPair[n] and its strips

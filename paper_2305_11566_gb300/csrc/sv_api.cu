@@ -491,6 +491,18 @@ sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value) {
   return c->fail(SV_ERR_INVALID_ARG, "unknown option '%s'", key);
 }
 
+sv_status sv_debug_activation(sv_ctx* ctx, int which, int pair, void* dst, size_t bytes) {
+  if (!ctx) return SV_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (which < 0 || which > 6 || pair < 0 || pair >= (int)c->tc_off.size() || !dst)
+    return c->fail(SV_ERR_INVALID_ARG, "no such activation");
+  if (bytes != c->tc_len[pair][which] * sizeof(__nv_bfloat16))
+    return c->fail(SV_ERR_INVALID_ARG, "activation has %zu bytes", c->tc_len[pair][which] * sizeof(__nv_bfloat16));
+  DeviceGuard g(c->device);
+  return c->cuda(cudaMemcpy(dst, (__nv_bfloat16*)c->tc_act[which].p + c->tc_off[pair][which], bytes,
+                            cudaMemcpyDeviceToHost), "copy activation");
+}
+
 long long sv_launch_count(const sv_ctx* ctx) {
   if (!ctx) return -1;
   return reinterpret_cast<const Ctx*>(ctx)->launches;

@@ -40,6 +40,8 @@ struct Ctx {
   std::vector<unsigned char> tc_host_tables;
   long long spin_limit = 4000000000LL;  // clock64 cycles a device-side wait may spin
   int tc_strip_rows = 0;                // 0: automatic
+  std::vector<std::array<size_t, 7>> tc_off;   // per pair offsets of the last tensor-core call
+  std::vector<std::array<size_t, 7>> tc_len;
   DevBuf err_flag;                      // device int: first failure code of a kernel
 
   // launch accounting and optional per-kernel event timing
