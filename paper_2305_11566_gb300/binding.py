@@ -71,6 +71,8 @@ API = {
     "sv_synchronize": ([c_void_p, c_void_p], c_int),
     "sv_set_option": ([c_void_p, c_char_p, ctypes.c_longlong], c_int),
     "sv_debug_activation": ([c_void_p, c_int, c_int, c_void_p, c_size_t], c_int),
+    "sv_coarse_match_static": ([POINTER(SvPair), c_int, c_int, POINTER(c_void_p), POINTER(c_void_p),
+                                POINTER(c_void_p), c_void_p], c_int),
 }
 
 
