@@ -155,6 +155,7 @@ def work_per_pair(shape):
     f["tc_dec2"] = 2 * (2 * H2) * (2 * W2) * d2 * 4 * d1
     f["tc_dec3"] = 2 * (2 * H1) * (2 * W1) * d3 * 4 * d2
     f["tc_enc2"], f["tc_enc3"], f["tc_latent"] = f["enc2"], f["enc3"], f["latent"]
+    f["enc1_bf16"], f["final_bf16"] = f["enc1"], f["final"]
     zbytes = 2 * W * H + 2 * (W // 4) * (H // 4)
     return f, zbytes
 
@@ -275,6 +276,12 @@ def run_ours(args):
         per_launch = zbytes * B
         achieved = per_launch / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s"}
+    elif name in ("final_bf16", "enc1_bf16", "up2_border_fix"):
+        # CUDA-core layers of the tensor-core form, one pair per launch (border fix: all pairs)
+        per_launch = flops.get(name, 0)
+        achieved = per_launch / avg_s / 1e12
+        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s"}
     elif name.startswith("tc_"):
         pairs_per_launch = B
         per_launch = flops[name] * pairs_per_launch

@@ -564,7 +564,7 @@ static void plan_layers(const NetDims& net, std::vector<TcLayerPlan>& plans, siz
   }
 }
 
-sv_status Ctx::pack_bf16_weights() {
+sv_status Ctx::pack_bf16_weights(cudaStream_t st) {
   std::vector<TcLayerPlan> plans;
   size_t total;
   plan_layers(net, plans, total);
@@ -572,7 +572,8 @@ sv_status Ctx::pack_bf16_weights() {
   if (s) return s;
   for (auto& pl : plans) {
     const size_t n = (size_t)pl.G * tc::taps(pl.mode) * pl.NT * pl.cin;
-    tc::pack_kernel<<<(unsigned)((n + 255) / 256), 256>>>((const float*)w32.p + net.w_off(pl.layer), pl.mode, pl.NT,
+    LaunchScope ls(*this, "pack_bf16", st);
+    tc::pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const float*)w32.p + net.w_off(pl.layer), pl.mode, pl.NT,
                                                            pl.G, pl.cin, pl.cout, (__nv_bfloat16*)wbf.p + pl.wofs);
     if ((s = cuda(cudaGetLastError(), "pack weights"))) return s;
   }

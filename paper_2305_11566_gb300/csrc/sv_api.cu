@@ -213,14 +213,23 @@ template sv_status Ctx::refine_direct<float>(const sv_pair&, const void*, bool, 
 template sv_status Ctx::refine_direct<double>(const sv_pair&, const void*, bool, const double*, double*, double*,
                                               double*, double* const*, cudaStream_t);
 
-sv_status Ctx::refresh_weight_copies() {
+sv_status Ctx::refresh_weight_copies_async(cudaStream_t st) {
   sv_status s;
   const size_t n = net.count();
   if ((s = cuda(w64.ensure(n * sizeof(double)), "alloc fp64 weights"))) return s;
-  f32_to_f64<<<(unsigned)((n + 255) / 256), 256>>>((const float*)w32.p, (double*)w64.p, n);
-  if ((s = cuda(cudaGetLastError(), "weights to fp64"))) return s;
+  {
+    LaunchScope ls(*this, "weights_f64", st);
+    f32_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const float*)w32.p, (double*)w64.p, n);
+    if ((s = cuda(cudaGetLastError(), "weights to fp64"))) return s;
+  }
   if (cfg.precision == SV_BF16)
-    if ((s = pack_bf16_weights())) return s;
+    if ((s = pack_bf16_weights(st))) return s;
+  return SV_OK;
+}
+
+sv_status Ctx::refresh_weight_copies() {
+  sv_status s = refresh_weight_copies_async(0);
+  if (s) return s;
   return cuda(cudaDeviceSynchronize(), "weight refresh");
 }
 
@@ -228,17 +237,7 @@ sv_status Ctx::refresh_weight_copies() {
 
 using sv::Ctx;
 
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
+using DeviceGuard = sv::DeviceGuardInt;
 
 extern "C" {
 

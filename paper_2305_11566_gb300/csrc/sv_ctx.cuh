@@ -35,7 +35,15 @@ struct Ctx {
   DevBuf tc_act[8];              // BF16 activations of the tensor-core path
   DevBuf tc_tables;              // tensor-core job tables
   int adam_t = 0;
+  int adam_elem = 0;
   DevBuf adam_m, adam_v;
+  // differentiation form: state saved by the last training forward
+  DevBuf train_saved, train_scratch, loss_acc;
+  std::vector<sv_pair> train_pairs;
+  std::vector<const void*> train_coarse;
+  std::vector<size_t> train_off;
+  int train_elem = 0;
+  bool train_ready = false;
   DevBuf host_img, host_out;     // device staging of sv_pipeline_host
   std::vector<unsigned char> tc_host_tables;
   long long spin_limit = 4000000000LL;  // clock64 cycles a device-side wait may spin
@@ -72,7 +80,20 @@ struct Ctx {
                          cudaStream_t st);
   sv_status pipeline(const sv_pair* pairs, int n, float* const* out, cudaStream_t st);
   sv_status refresh_weight_copies();
-  sv_status pack_bf16_weights();
+  sv_status refresh_weight_copies_async(cudaStream_t st);
+  sv_status pack_bf16_weights(cudaStream_t st = 0);
+  template <typename T>
+  sv_status train_forward(const sv_pair* pairs, const void* const* coarse, const void* const* eps, int n,
+                          void* const* Y, void* const* mu, void* const* lv, cudaStream_t st);
+  template <typename T>
+  sv_status train_backward(const void* const* gY, const void* const* gmu_ext, const void* const* glv_ext, T* gparams,
+                           void* const* gcoarse, cudaStream_t st);
+  template <typename T>
+  sv_status loss(const sv_pair* pairs, int n, const void* const* Y, const float* const* gt, const void* const* mu,
+                 const void* const* lv, double kl_w, void* out, void* const* gY, void* const* gmu, void* const* glv,
+                 cudaStream_t st);
+  template <typename T>
+  sv_status adam(const T* g, int step, double lr, double b1, double b2, double eps, cudaStream_t st);
   sv_status refine_tc(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out, cudaStream_t st);
 
   void prof_flush() {
@@ -98,12 +119,26 @@ struct Ctx {
     for (auto& b : act) b.release();
     for (auto& b : tc_act) b.release();
     tc_tables.release(); adam_m.release(); adam_v.release();
+    train_saved.release(); train_scratch.release(); loss_acc.release();
   }
 };
 
 }  // namespace sv
 
 namespace sv {
+// Makes a device current for the scope of an ABI call and restores the caller's.
+struct DeviceGuardInt {
+  int prev = -1;
+  explicit DeviceGuardInt(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuardInt() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
 // Counts one kernel launch and, when profiling is on, brackets it with events.
 struct LaunchScope {
   Ctx& c;

@@ -1,0 +1,200 @@
+"""GPU parity of the differentiation form (sv_refine_train, sv_loss, sv_refine_backward,
+sv_adam_step) against the FP64 oracle and against finite differences.
+
+FP64 (SV_FP64_CHECK) on a 64x32 crop: loss equal to the oracle's to 1e-12, the analytic
+gradient equal to the oracle's hand-derived gradient to 1e-9 (relative to the largest
+entry), and to central finite differences of the GPU's own FP64 loss within 1e-6
+relative (coarse-map entries: the loss is piecewise quadratic in them; parameters:
+two-step extrapolated differences, entries whose two step sizes disagree -- a ReLU
+kink inside the step -- are skipped and counted).  FP32: gradient within 1e-4 of the
+oracle's (relative to each layer's largest entry), one Adam step within 1e-6."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2305_11566_gb300 import autograd, binding, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def case(W=64, H=32, seed=21, shape=synth.NET_SMALL, k=5, D=6):
+    params = synth.he_normal_weights(shape, 7)
+    sl = oracle.param_slices(shape)
+    rng = np.random.default_rng(seed)
+    ob, co = sl["logvar"][2], sl["logvar"][3]
+    params[ob:ob + co] = rng.normal(scale=0.3, size=co).astype(np.float32)
+    p = synth.make_pair(W, H, 30.0, seed)
+    coarse = oracle.coarse_match(p.left, p.right, k, D)[0].astype(np.float64)
+    coarse += rng.uniform(0.1, 0.4, size=coarse.shape)
+    L3 = oracle.level_sizes(H, W)[3]
+    eps = synth.reparam_noise(L3[0] * L3[1] * shape.latent, seed)
+    return shape, params, p, coarse, eps, k, D
+
+
+def gpu_loss_grad(ctx, dp, coarse, eps, gt, dt, want_coarse=True):
+    c = torch.from_numpy(coarse).to("cuda", dt)
+    e = torch.from_numpy(eps.astype(np.float64)).to("cuda", dt)
+    H3, W3 = binding.latent_hw(dp.height, dp.width)
+    e = e.reshape(H3, W3, -1)
+    Y, mu, lv = ctx.refine_train([dp], [c], [e])
+    out, gY, gmu, glv = ctx.loss([dp], Y, [torch.from_numpy(gt).cuda()], mu, lv, 1e-3)
+    gp, gc = ctx.refine_backward(gY, gmu, glv, want_coarse, [c])
+    ctx.synchronize()
+    return out.cpu().numpy(), gp.cpu().numpy(), (gc[0].cpu().numpy() if want_coarse else None)
+
+
+@pytest.fixture(scope="module")
+def fp64(svlib):
+    shape, params, p, coarse, eps, k, D = case()
+    ctx = binding.Context(shape, k, "fp64")
+    ctx.set_weights(params)
+    yield ctx, shape, params, p, coarse, eps, k, D
+    ctx.close()
+
+
+def test_fp64_gradient_equals_oracle(fp64):
+    ctx, shape, params, p, coarse, eps, k, D = fp64
+    H, W = p.left.shape
+    dp = binding.to_device(p, D)
+    out, gp, gc = gpu_loss_grad(ctx, dp, coarse, eps, p.gt, torch.float64)
+    L3 = oracle.level_sizes(H, W)[3]
+    nlat = L3[0] * L3[1] * shape.latent
+    Lo, go, gco = oracle.refine_backward(shape, params, p.left, coarse, eps, p.gt, H * W, nlat, 1e-3, True)
+    assert abs(out[0] - Lo) <= 1e-12 * abs(Lo)
+    assert np.abs(gp - go).max() <= 1e-9 * np.abs(go).max()
+    assert np.abs(gc - gco).max() <= 1e-9 * np.abs(gco).max()
+
+
+def test_fp64_gradient_matches_finite_differences(fp64):
+    ctx, shape, params, p, coarse, eps, k, D = fp64
+    dp = binding.to_device(p, D)
+    _, g, gc = gpu_loss_grad(ctx, dp, coarse, eps, p.gt, torch.float64)
+
+    def L(par=None, c=None):
+        if par is not None:
+            ctx.set_weights(par)
+        out = gpu_loss_grad(ctx, dp, coarse if c is None else c, eps, p.gt, torch.float64, want_coarse=False)[0][0]
+        return out
+
+    # coarse map: piecewise quadratic in each entry, central differences are exact away from kinks
+    rng = np.random.default_rng(1)
+    h = 1e-5
+    for (y, x) in [(1, 1), (3, 7), (7, 15), (0, 15), (4, 0)]:
+        cp = coarse.copy(); cp[y, x] += h
+        cm = coarse.copy(); cm[y, x] -= h
+        fd = (L(c=cp) - L(c=cm)) / (2 * h)
+        assert abs(fd - gc[y, x]) <= 1e-6 * abs(gc[y, x]) + 1e-12, (y, x, fd, gc[y, x])
+    # parameters: FP32 perturbations (the library's master copy is FP32), two step sizes,
+    # second-order error eliminated; a kink inside the step shows as disagreement
+    sl = oracle.param_slices(shape)
+    idx = []
+    for name, (ow, wshape, ob, co) in sl.items():
+        n = int(np.prod(wshape))
+        idx += list(ow + rng.choice(n, size=3, replace=False)) + [ob + int(rng.integers(co))]
+    checked, skipped, worst = 0, 0, 0.0
+    try:
+        for i in idx:
+            if abs(g[i]) < 1e-8:
+                continue
+            ests = []
+            for rel in (2.0 ** -9, 2.0 ** -11):
+                base = params[i]
+                hh = np.float32(max(abs(base), 1e-2) * rel)
+                pp = params.copy(); pp[i] = base + hh
+                pm = params.copy(); pm[i] = base - hh
+                s = float(np.float64(pp[i]) - np.float64(pm[i])) / 2
+                ests.append(((L(par=pp) - L(par=pm)) / (2 * s), s))
+            (d1, s1), (d2, s2) = ests
+            rich = (s1 ** 2 * d2 - s2 ** 2 * d1) / (s1 ** 2 - s2 ** 2)
+            if abs(d1 - d2) > 1e-3 * abs(g[i]):  # a ReLU kink inside the larger step
+                skipped += 1
+                continue
+            checked += 1
+            worst = max(worst, abs(rich - g[i]) / abs(g[i]))
+    finally:
+        ctx.set_weights(params)
+    assert checked >= 0.6 * (checked + skipped)
+    assert worst <= 1e-6, worst
+
+
+def test_fp32_gradient_and_adam_match_oracle(svlib):
+    shape, params, _, _, _, k, D = case()
+    pairs = [synth.make_pair(W, H, 40.0, 900 + W) for W, H in ((256, 128), (130, 67))]
+    ctx = binding.Context(shape, k, "fp32")
+    try:
+        ctx.set_weights(params)
+        dps = [binding.to_device(p, D) for p in pairs]
+        coarse, eps, cs, es = [], [], [], []
+        rng = np.random.default_rng(3)
+        for p, dp in zip(pairs, dps):
+            c = oracle.coarse_match(p.left, p.right, k, D)[0].astype(np.float64) + rng.uniform(0, 0.5, (p.height // 4, p.width // 4))
+            H3, W3 = binding.latent_hw(p.height, p.width)
+            e = synth.reparam_noise(H3 * W3 * shape.latent, p.seed)
+            coarse.append(c); eps.append(e)
+            cs.append(torch.from_numpy(c).float().cuda())
+            es.append(torch.from_numpy(e).cuda().reshape(H3, W3, -1))
+        Y, mu, lv = ctx.refine_train(dps, cs, es)
+        out, gY, gmu, glv = ctx.loss(dps, Y, [torch.from_numpy(p.gt).cuda() for p in pairs], mu, lv, 1e-3)
+        gp, _ = ctx.refine_backward(gY, gmu, glv, False, cs)
+        ctx.synchronize()
+        npix = sum(p.width * p.height for p in pairs)
+        nlat = sum(np.prod(binding.latent_hw(p.height, p.width)) * shape.latent for p in pairs)
+        Lo, go = 0.0, np.zeros(params.size)
+        for p, c, e in zip(pairs, coarse, eps):
+            l, g, _ = oracle.refine_backward(shape, params, p.left, c, e, p.gt, npix, nlat, 1e-3)
+            Lo += l
+            go += g
+        assert abs(out[0].item() - Lo) <= 1e-5 * abs(Lo)
+        gpn = gp.cpu().numpy()
+        for name, (ow, wshape, ob, co) in oracle.param_slices(shape).items():
+            n = int(np.prod(wshape))
+            ref = go[ow:ow + n]
+            assert np.abs(gpn[ow:ow + n] - ref).max() <= 1e-4 * np.abs(ref).max() + 1e-12, name
+        # one Adam step (paper's betas) against the oracle's Adam on the same gradient
+        ctx.adam_step(gp, 1)
+        ctx.synchronize()
+        p64 = params.astype(np.float64)
+        m = np.zeros_like(p64); v = np.zeros_like(p64)
+        oracle.adam(p64, m, v, gpn.astype(np.float64), 1)
+        assert np.abs(ctx.get_weights() - p64).max() <= 1e-6
+    finally:
+        ctx.close()
+
+
+def test_autograd_function_training_steps_reduce_loss(svlib):
+    """torch.autograd route: SVRefineFn + SVLossFn, loss.backward(), sv_adam_step."""
+    shape, params, p, coarse, eps, k, D = case(W=128, H=64, seed=33)
+    ctx = binding.Context(shape, k, "fp32")
+    try:
+        ctx.set_weights(params)
+        dp = binding.to_device(p, D)
+        c = torch.from_numpy(coarse).float().cuda().requires_grad_(True)
+        H3, W3 = binding.latent_hw(p.height, p.width)
+        e = torch.from_numpy(eps).cuda().reshape(H3, W3, -1)
+        gt = torch.from_numpy(p.gt).cuda()
+        w = torch.from_numpy(params).cuda().requires_grad_(True)
+        losses = []
+        for t in range(1, 6):
+            Y, mu, lv = autograd.refine(ctx, [dp], [c], [e], w)
+            L = autograd.loss(ctx, [dp], Y, [gt], mu, lv)
+            w.grad = None
+            c.grad = None
+            L.backward()
+            assert w.grad is not None and c.grad is not None
+            ctx.adam_step(w.grad, t, lr=1e-3)
+            losses.append(L.item())
+        assert losses[-1] < losses[0]
+    finally:
+        ctx.close()
+
+
+def test_backward_without_forward_is_a_state_error(svlib):
+    ctx = binding.Context(synth.NET_SMALL, 5, "fp32")
+    try:
+        g = torch.zeros(10, device="cuda")
+        with pytest.raises(binding.SvError) as ei:
+            ctx.refine_backward([g], [None], [None], False, [g])
+        assert ei.value.status == binding.SV_ERR_STATE
+    finally:
+        ctx.close()
