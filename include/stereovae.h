@@ -201,6 +201,21 @@ SV_API sv_status sv_profile_enable(sv_ctx* ctx, int enable);
  * reset != 0 clears the totals afterwards. */
 SV_API sv_status sv_profile_read(sv_ctx* ctx, sv_profile_entry* out, int max_entries, int* n_out, int reset);
 
+/* Autotuner of the SV_BF16 form: for each tensor-core layer picks the strip height
+ * (rows of 128-unit tiles one work item walks down) and the output-channel slice per CTA
+ * that run fastest on this batch, timing every candidate with CUDA events on `stream`.
+ * The choice stays in the context and applies to later calls.  cache_path (nullable): a
+ * JSON-lines file; an entry for this (GPU, SM count, network, window, batch-shape bucket)
+ * is loaded instead of tuning, a new result is appended.  Synchronous.  Returns
+ * SV_ERR_UNSUPPORTED on other precisions. */
+SV_API sv_status sv_autotune(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, const char* cache_path,
+                             sv_stream stream);
+
+/* The tuned launch shape (6 layers: enc2, enc3, latent, dec1, dec2, dec3): strip rows
+ * (0 = automatic), N slice (0 = full width) and the measured microseconds per launch
+ * (-1 when loaded from a cache).  Any pointer may be NULL. */
+SV_API sv_status sv_tuning(const sv_ctx* ctx, int* rows6, int* nt6, double* us6);
+
 /* Waits for `stream` and reports device-side failures recorded since the previous
  * call: SV_ERR_TIMEOUT if a kernel's bounded wait ran out (the kernel then returned
  * early and its outputs are undefined), SV_ERR_CUDA for a CUDA error.  Clears the
@@ -211,6 +226,9 @@ SV_API sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream);
  *   "spin_limit"     clock cycles one device-side wait may spin before it gives up
  *                    (default 4e9, about 2 s)
  *   "tc_strip_rows"  rows per work item of the tensor-core convolutions (0 = automatic)
+ *   "graphs"         1 (default): sv_pipeline on an SV_BF16 context captures each batch
+ *                    signature in a CUDA graph and replays it (not on the legacy or
+ *                    per-thread default stream); 0: launch eagerly
  * Returns SV_ERR_INVALID_ARG for an unknown key or a value out of range. */
 SV_API sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value);
 

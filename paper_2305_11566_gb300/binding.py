@@ -73,6 +73,8 @@ API = {
     "sv_debug_activation": ([c_void_p, c_int, c_int, c_void_p, c_size_t], c_int),
     "sv_coarse_match_static": ([POINTER(SvPair), c_int, c_int, POINTER(c_void_p), POINTER(c_void_p),
                                 POINTER(c_void_p), c_void_p], c_int),
+    "sv_autotune": ([c_void_p, POINTER(SvPair), c_int, c_char_p, c_void_p], c_int),
+    "sv_tuning": ([c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_double)], c_int),
 }
 
 
@@ -271,6 +273,19 @@ class Context:
         buf = torch.empty(n, dtype=torch.bfloat16)
         self._check(lib().sv_debug_activation(self._h, which, pair, c_void_p(buf.data_ptr()), n * 2))
         return buf.float().numpy().reshape(shape)
+
+    def autotune(self, pairs, cache_path=None, stream=None):
+        """Tune the tensor-core layers on this batch (SV_BF16 contexts); returns the choice."""
+        p = None if cache_path is None else str(cache_path).encode()
+        self._check(lib().sv_autotune(self._h, _pairs_array(pairs), len(pairs), p, _stream(stream)))
+        return self.tuning()
+
+    def tuning(self):
+        rows = (c_int * 6)()
+        nt = (c_int * 6)()
+        us = (c_double * 6)()
+        self._check(lib().sv_tuning(self._h, rows, nt, us))
+        return {"rows": list(rows), "nt": list(nt), "us": list(us)}
 
     def launch_count(self) -> int:
         return int(lib().sv_launch_count(self._h))

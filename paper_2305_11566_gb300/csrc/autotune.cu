@@ -1,0 +1,201 @@
+// autotune.cu -- picks the launch shape of every tensor-core layer of the BF16 form on the
+// caller's own batch: for each layer, the strip height (rows of 128-unit tiles one work
+// item walks down, which trades staged-row reuse against load balance) and the N slice
+// (output channels per CTA; narrower slices give more CTAs per pair).  Each candidate
+// is timed with CUDA events around the layer's launch (the context's profiler); the
+// fastest per layer is kept.  Results are cached per (GPU, SM count, network, window,
+// batch shape bucket) in a JSON-lines file when a path is given.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "sv_ctx.cuh"
+
+namespace sv {
+
+namespace {
+
+std::string tune_key(const Ctx& c, const sv_pair* pairs, int n) {
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, c.device);
+  // shape bucket: pair count (power-of-two bucket), largest size, total pixels in Mpx
+  long long px = 0;
+  int maxW = 0, maxH = 0;
+  for (int i = 0; i < n; ++i) {
+    px += (long long)pairs[i].width * pairs[i].height;
+    maxW = std::max(maxW, pairs[i].width);
+    maxH = std::max(maxH, pairs[i].height);
+  }
+  int nb = 1;
+  while (nb < n) nb *= 2;
+  std::ostringstream o;
+  o << prop.name << "|sm" << prop.multiProcessorCount << "|net" << c.net.enc[0] << "-" << c.net.enc[1] << "-"
+    << c.net.enc[2] << "-" << c.net.lat << "-" << c.net.dec[0] << "-" << c.net.dec[1] << "-" << c.net.dec[2] << "|k"
+    << c.cfg.window << "|n" << nb << "|max" << maxW << "x" << maxH << "|mpx" << (px + 500000) / 1000000;
+  std::string s = o.str();
+  for (auto& ch : s)
+    if (ch == '"' || ch == '\n') ch = '_';
+  return s;
+}
+
+bool load_entry(const char* path, const std::string& key, int rows[6], int nt[6]) {
+  std::ifstream f(path);
+  if (!f) return false;
+  std::string line;
+  const std::string want = "{\"key\": \"" + key + "\"";
+  while (std::getline(f, line)) {
+    if (line.compare(0, want.size(), want) != 0) continue;
+    const size_t r = line.find("\"rows\": ["), t = line.find("\"nt\": [");
+    if (r == std::string::npos || t == std::string::npos) continue;
+    int a[6], b[6];
+    if (sscanf(line.c_str() + r, "\"rows\": [%d, %d, %d, %d, %d, %d]", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5]) != 6)
+      continue;
+    if (sscanf(line.c_str() + t, "\"nt\": [%d, %d, %d, %d, %d, %d]", &b[0], &b[1], &b[2], &b[3], &b[4], &b[5]) != 6)
+      continue;
+    for (int i = 0; i < 6; ++i) {
+      rows[i] = a[i];
+      nt[i] = b[i];
+    }
+    return true;
+  }
+  return false;
+}
+
+void save_entry(const char* path, const std::string& key, const int rows[6], const int nt[6], const double us[6]) {
+  std::ofstream f(path, std::ios::app);
+  if (!f) return;
+  f << "{\"key\": \"" << key << "\", \"rows\": [" << rows[0];
+  for (int i = 1; i < 6; ++i) f << ", " << rows[i];
+  f << "], \"nt\": [" << nt[0];
+  for (int i = 1; i < 6; ++i) f << ", " << nt[i];
+  f << "], \"us\": [" << us[0];
+  for (int i = 1; i < 6; ++i) f << ", " << us[i];
+  f << "]}\n";
+}
+
+}  // namespace
+
+sv_status Ctx::autotune(const sv_pair* pairs, int n, const char* cache_path, cudaStream_t st) {
+  const std::string key = tune_key(*this, pairs, n);
+  int rows[6], nt[6];
+  if (cache_path && load_entry(cache_path, key, rows, nt)) {
+    for (int i = 0; i < 6; ++i) {
+      tc_rows_override[i] = rows[i];
+      tc_nt_override[i] = nt[i];
+    }
+    tune_loaded = true;
+    return SV_OK;
+  }
+  tune_loaded = false;
+  // coarse maps of the batch, once
+  std::vector<size_t> off(n + 1, 0);
+  for (int i = 0; i < n; ++i) off[i + 1] = off[i] + (size_t)(pairs[i].width / 4) * (pairs[i].height / 4);
+  sv_status s = cuda(coarse_maps.ensure(off[n] * sizeof(int16_t)), "alloc coarse maps");
+  if (s) return s;
+  std::vector<int16_t*> maps(n);
+  for (int i = 0; i < n; ++i) maps[i] = (int16_t*)coarse_maps.p + off[i];
+  if ((s = coarse(pairs, n, maps.data(), nullptr, nullptr, st))) return s;
+  std::vector<const int16_t*> cm(maps.begin(), maps.end());
+  // outputs: scratch of the refinement (overwritten by later calls)
+  size_t P = 0;
+  for (int i = 0; i < n; ++i) P += (size_t)pairs[i].width * pairs[i].height;
+  if ((s = cuda(tune_out.ensure(P * sizeof(float)), "alloc tuning output"))) return s;
+  std::vector<float*> outs(n);
+  size_t o = 0;
+  for (int i = 0; i < n; ++i) {
+    outs[i] = (float*)tune_out.p + o;
+    o += (size_t)pairs[i].width * pairs[i].height;
+  }
+  static const char* names[6] = {"tc_enc2", "tc_enc3", "tc_latent", "tc_dec1", "tc_dec2", "tc_dec3"};
+  const int row_cands[6] = {0, 2, 4, 8, 16, 32};
+  double best_us[6];
+  int best_rows[6], best_nt[6];
+  for (int i = 0; i < 6; ++i) {
+    best_us[i] = 1e30;
+    best_rows[i] = 0;
+    best_nt[i] = 0;
+  }
+  const bool prof_was = prof_on;
+  const auto saved_tot = prof_tot;
+  prof_flush();
+  for (int half = 0; half < 2; ++half) {
+    for (int rc : row_cands) {
+      for (int i = 0; i < 6; ++i) {
+        tc_rows_override[i] = rc;
+        tc_nt_override[i] = 0;
+      }
+      if (half) {
+        // half-width N slices where that still leaves at least 16 channels per slice
+        TcRun probe;
+        std::vector<TcLayerPlan> plans;
+        if ((s = tc_prepare(pairs, cm.data(), n, outs.data(), probe))) break;
+        for (int i = 0; i < 6; ++i) tc_nt_override[i] = probe.plans[i].NT / 2 >= 16 ? probe.plans[i].NT / 2 : 0;
+      }
+      prof_on = true;
+      prof_tot.clear();
+      for (int rep = 0; rep < 4; ++rep) {
+        if ((s = refine_tc(pairs, cm.data(), n, outs.data(), st))) break;
+        if (rep == 0) {  // first run warms up; drop its timings
+          prof_flush();
+          prof_tot.clear();
+        }
+      }
+      prof_flush();
+      prof_on = false;
+      if (s) break;
+      for (int i = 0; i < 6; ++i) {
+        auto it = prof_tot.find(names[i]);
+        if (it == prof_tot.end() || it->second.first == 0) continue;
+        const double us = it->second.second * 1e3 / it->second.first;
+        if (us < best_us[i]) {
+          best_us[i] = us;
+          best_rows[i] = rc;
+          best_nt[i] = tc_nt_override[i];
+        }
+      }
+    }
+    if (s) break;
+  }
+  prof_on = prof_was;
+  prof_tot = saved_tot;
+  for (int i = 0; i < 6; ++i) {
+    tc_rows_override[i] = best_rows[i];
+    tc_nt_override[i] = best_nt[i];
+    tune_us[i] = best_us[i];
+  }
+  if (s) return s;
+  if (cache_path) save_entry(cache_path, key, best_rows, best_nt, best_us);
+  return SV_OK;
+}
+
+}  // namespace sv
+
+extern "C" sv_status sv_autotune(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, const char* cache_path,
+                                 sv_stream stream) {
+  if (!ctx) return SV_ERR_INVALID_ARG;
+  sv::Ctx* c = reinterpret_cast<sv::Ctx*>(ctx);
+  c->err.clear();
+  if (c->cfg.precision != SV_BF16) return c->fail(SV_ERR_UNSUPPORTED, "the autotuner tunes the BF16 tensor-core form");
+  sv_status s = c->check_pairs(pairs, n_pairs);
+  if (s) return s;
+  if (n_pairs == 0) return SV_OK;
+  sv::DeviceGuardInt g(c->device);
+  s = c->autotune(pairs, n_pairs, cache_path, (cudaStream_t)stream);
+  if (s) return s;
+  return c->cuda(cudaStreamSynchronize((cudaStream_t)stream), "autotune");
+}
+
+extern "C" sv_status sv_tuning(const sv_ctx* ctx, int* rows6, int* nt6, double* us6) {
+  if (!ctx) return SV_ERR_INVALID_ARG;
+  const sv::Ctx* c = reinterpret_cast<const sv::Ctx*>(ctx);
+  for (int i = 0; i < 6; ++i) {
+    if (rows6) rows6[i] = c->tc_rows_override[i];
+    if (nt6) nt6[i] = c->tc_nt_override[i];
+    if (us6) us6[i] = c->tune_loaded ? -1.0 : c->tune_us[i];
+  }
+  return SV_OK;
+}

@@ -8,7 +8,8 @@
 //                   every weight it owns and adds the partial sum atomically.
 //   latent_bwd      gradient through z = mu + eps exp(lv / 2) plus the loss's own mu / lv terms.
 //   up4_bwd         transpose of the bilinear x4 upsampling (gather form, deterministic).
-//   loss_kernel     smooth-L1 + KL partial sums (atomic) and their elementwise gradients.
+//   loss_*          smooth-L1 + KL per-block partial sums (summed in a fixed order) and the
+//                   elementwise gradients.
 //   adam_kernel     Adam on FP32 master weights.
 #include "sv_internal.cuh"
 
@@ -176,10 +177,14 @@ __global__ void build_x0(const uint8_t* L, int pitch, int W, int H, const T* coa
   x0[2 * p + 1] = (T)4 * (((T)1 - fy) * top + fy * bot) * (T)(1.0 / 256.0);
 }
 
-// Loss partial sums (acc[0] += smooth-L1, acc[1] += KL) and gradients.
+// Loss: every block writes its partial sum to its own slot (no atomics), loss_finish adds
+// the slots in a fixed order, so the loss is bitwise reproducible.  Slot layout: for pair
+// i, kLossBlocks smooth-L1 partials then kLossBlocks KL partials.
+constexpr int kLossBlocks = 128;
+
 template <typename T>
 __global__ void loss_rec(const T* __restrict__ Y, const float* __restrict__ gt, size_t P, double inv_npix,
-                         T* __restrict__ gY, double* __restrict__ acc) {
+                         T* __restrict__ gY, double* __restrict__ slots) {
   __shared__ double red[256];
   double s = 0;
   for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
@@ -194,12 +199,12 @@ __global__ void loss_rec(const T* __restrict__ Y, const float* __restrict__ gt, 
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicAdd(acc, red[0]);
+  if (threadIdx.x == 0) slots[blockIdx.x] = red[0];
 }
 
 template <typename T>
 __global__ void loss_kl(const T* __restrict__ mu, const T* __restrict__ lv, size_t n, double kl_scale,
-                        T* __restrict__ gmu, T* __restrict__ glv, double* __restrict__ acc) {
+                        T* __restrict__ gmu, T* __restrict__ glv, double* __restrict__ slots) {
   __shared__ double red[256];
   double s = 0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -215,12 +220,19 @@ __global__ void loss_kl(const T* __restrict__ mu, const T* __restrict__ lv, size
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicAdd(acc + 1, red[0]);
+  if (threadIdx.x == 0) slots[kLossBlocks + blockIdx.x] = red[0];
 }
 
 template <typename T>
-__global__ void loss_finish(const double* acc, double inv_npix, double inv_nlat, double kl_w, T* out) {
-  const double rec = acc[0] * inv_npix, kl = acc[1] * inv_nlat;
+__global__ void loss_finish(const double* slots, int n_pairs, double inv_npix, double inv_nlat, double kl_w, T* out) {
+  double rec = 0, kl = 0;
+  for (int i = 0; i < n_pairs; ++i)
+    for (int b = 0; b < kLossBlocks; ++b) {
+      rec += slots[(size_t)i * 2 * kLossBlocks + b];
+      kl += slots[(size_t)i * 2 * kLossBlocks + kLossBlocks + b];
+    }
+  rec *= inv_npix;
+  kl *= inv_nlat;
   out[0] = (T)(rec + kl_w * kl);
   out[1] = (T)rec;
   out[2] = (T)kl;
@@ -288,24 +300,26 @@ cudaError_t launch_add(T* a, const T* b, size_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+size_t loss_slots_per_pair() { return 2 * kLossBlocks; }
+
 template <typename T>
-cudaError_t launch_loss_rec(const T* Y, const float* gt, size_t P, double inv_npix, T* gY, double* acc,
+cudaError_t launch_loss_rec(const T* Y, const float* gt, size_t P, double inv_npix, T* gY, double* slots,
                             cudaStream_t st) {
-  loss_rec<T><<<(unsigned)std::min<size_t>(1024, blocks(P)), 256, 0, st>>>(Y, gt, P, inv_npix, gY, acc);
+  loss_rec<T><<<kLossBlocks, 256, 0, st>>>(Y, gt, P, inv_npix, gY, slots);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_loss_kl(const T* mu, const T* lv, size_t n, double kl_scale, T* gmu, T* glv, double* acc,
+cudaError_t launch_loss_kl(const T* mu, const T* lv, size_t n, double kl_scale, T* gmu, T* glv, double* slots,
                            cudaStream_t st) {
-  loss_kl<T><<<(unsigned)std::min<size_t>(1024, blocks(n)), 256, 0, st>>>(mu, lv, n, kl_scale, gmu, glv, acc);
+  loss_kl<T><<<kLossBlocks, 256, 0, st>>>(mu, lv, n, kl_scale, gmu, glv, slots);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_loss_finish(const double* acc, double inv_npix, double inv_nlat, double kl_w, T* out,
+cudaError_t launch_loss_finish(const double* slots, int n_pairs, double inv_npix, double inv_nlat, double kl_w, T* out,
                                cudaStream_t st) {
-  loss_finish<T><<<1, 1, 0, st>>>(acc, inv_npix, inv_nlat, kl_w, out);
+  loss_finish<T><<<1, 1, 0, st>>>(slots, n_pairs, inv_npix, inv_nlat, kl_w, out);
   return cudaGetLastError();
 }
 
@@ -329,7 +343,7 @@ cudaError_t launch_adam(float* p, T* m, T* v, const T* g, size_t n, double lr, d
   template cudaError_t launch_add<T>(T*, const T*, size_t, cudaStream_t);                                           \
   template cudaError_t launch_loss_rec<T>(const T*, const float*, size_t, double, T*, double*, cudaStream_t);        \
   template cudaError_t launch_loss_kl<T>(const T*, const T*, size_t, double, T*, T*, double*, cudaStream_t);        \
-  template cudaError_t launch_loss_finish<T>(const double*, double, double, double, T*, cudaStream_t);              \
+  template cudaError_t launch_loss_finish<T>(const double*, int, double, double, double, T*, cudaStream_t);         \
   template cudaError_t launch_adam<T>(float*, T*, T*, const T*, size_t, double, double, double, double, int,        \
                                       cudaStream_t);
 SV_BWD_INST(float)

@@ -236,22 +236,6 @@ cudaError_t launch_latent(const T* e3, int P, int Ci, const T* wmu, const T* bmu
   return cudaGetLastError();
 }
 
-cudaError_t launch_enc1_bf16(const uint8_t* L, int pitch, int W, int H, const int16_t* coarse, int w, int h,
-                             const float* wt, const float* bias, int Co, __nv_bfloat16* out, cudaStream_t st) {
-  SrcEnc1<float, int16_t> s{L, pitch, W, H, coarse, w, h};
-  Levels lv(H, W);
-  return run_conv<float, SrcEnc1<float, int16_t>, 2, 3, 2, __nv_bfloat16>(s, 2, wt, bias, Co, lv.H[1], lv.W[1], 1, out,
-                                                                          st);
-}
-
-cudaError_t launch_final_bf16(const __nv_bfloat16* in, int W, int H, int Ci, const float* wt, const float* bias,
-                              const int16_t* coarse, int w, int h, float* Y, cudaStream_t st) {
-  dim3 grid((W + 127) / 128, H);
-  final_kernel<float, int16_t, float, __nv_bfloat16><<<grid, 128, sizeof(float) * 9 * Ci, st>>>(in, W, H, Ci, wt, bias,
-                                                                                               coarse, w, h, Y);
-  return cudaGetLastError();
-}
-
 template cudaError_t launch_conv_direct<float>(const DirectConvArgs<float>&, int, int, cudaStream_t);
 template cudaError_t launch_conv_direct<double>(const DirectConvArgs<double>&, int, int, cudaStream_t);
 template cudaError_t launch_enc1<float, int16_t>(const uint8_t*, int, int, int, const int16_t*, int, int, const float*,

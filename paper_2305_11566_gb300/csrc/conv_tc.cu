@@ -16,16 +16,21 @@
 //          (py, px) of 2x2 convs on the low-resolution input with the 3x3 weights summed
 //          per phase (rows/cols {0} and {1,2} for phase 0, {0,1} and {2} for phase 1):
 //          4 taps per output instead of 9.  The last row / column of an odd-sized
-//          (cropped) output is recomputed exactly by up2_border_fix afterwards.
+//          (cropped) output is recomputed exactly by edge_up2fix (tc_edges.cu) afterwards.
 //   TM_P1  1x1 conv (latent mean head).
 //
-// Warp roles (256 threads): warps 0-3 epilogue (TMEM lanes 0-127: tcgen05.ld, bias,
-// ReLU, BF16 store), warp 4 TMEM allocation + one thread issuing tcgen05.mma, warps 5-7
-// producers (cp.async with zero fill for the halo).  Every wait is bounded; on timeout
-// the kernel records an error code and returns.
+// Warp roles (192 threads): warps 0-3 epilogue (TMEM lanes 0-127: tcgen05.ld, bias,
+// ReLU, BF16 store), warp 4 TMEM allocation + one thread issuing tcgen05.mma, warp 5 one
+// thread loading every staged row with TMA (cp.async.bulk.tensor, one box of 8 channels x
+// the staged pixels per plane; the hardware fills the halo outside the image with zeros)
+// and signalling the row's mbarrier by transaction count.  Every wait is bounded; on
+// timeout the kernel records an error code and returns.
 #include <algorithm>
 #include <cstdio>
 #include <vector>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "sv_ctx.cuh"
 
@@ -37,12 +42,14 @@ using bf16 = __nv_bfloat16;
 
 enum Mode { TM_S2 = 0, TM_UP2 = 1, TM_P1 = 2 };
 
-struct LayerPair {
+struct alignas(64) LayerPair {
   const bf16* in;
   bf16* out;
   int Hi, Wi;  // input size
   int Ho, Wo;  // output size
   int Hu, Wu;  // unit grid covered by tiles (S2 / P1: output; UP2: low-resolution input)
+  int pad[6];
+  CUtensorMap tm[2];  // TMA view of the input: S2 [0] odd pixels, [1] even pixels; others [0]
 };
 
 struct Strip {
@@ -60,23 +67,28 @@ struct Params {
   long long spin;
 };
 
+// RA staged rows per tile, STEP new rows per next tile, T taps, NSET pixel sets per row
+// (stride 2: odd and even pixels), NPX pixels per set.
 template <int MODE> struct Geo;
-template <> struct Geo<TM_S2> { static constexpr int RA = 3, STEP = 2, NPX = 258, T = 9; };
-template <> struct Geo<TM_UP2> { static constexpr int RA = 2, STEP = 1, NPX = 129, T = 4; };
-template <> struct Geo<TM_P1> { static constexpr int RA = 1, STEP = 1, NPX = 128, T = 1; };
+template <> struct Geo<TM_S2> { static constexpr int RA = 3, STEP = 2, T = 9, NSET = 2, NPX = 129; };
+template <> struct Geo<TM_UP2> { static constexpr int RA = 2, STEP = 1, T = 4, NSET = 1, NPX = 129; };
+template <> struct Geo<TM_P1> { static constexpr int RA = 1, STEP = 1, T = 1, NSET = 1, NPX = 128; };
 
-constexpr int kThreads = 256;
-constexpr int kProducerWarps = 3;
+constexpr int kThreads = 192;
 constexpr int kBarBytes = 8;
 
+__host__ __device__ inline int nset(int mode) { return mode == TM_S2 ? 2 : 1; }
+__host__ __device__ inline int npx(int mode) { return mode == TM_P1 ? 128 : 129; }
+// plane = 8 channels of every staged pixel of one set, 16 B per pixel, 128-B aligned
+__host__ __device__ inline uint32_t plane_stride(int mode) { return (uint32_t)((npx(mode) * 16 + 127) / 128 * 128); }
 __host__ __device__ inline size_t row_bytes(int mode, int cin) {
-  const int npx = mode == TM_S2 ? 258 : mode == TM_UP2 ? 129 : 128;
-  return (size_t)(cin / 8) * npx * 16;
+  return (size_t)nset(mode) * (cin / 8) * plane_stride(mode);
 }
 __host__ __device__ inline int taps(int mode) { return mode == TM_S2 ? 9 : mode == TM_UP2 ? 4 : 1; }
 __host__ __device__ inline size_t b_bytes(int mode, int NT, int cin) { return (size_t)taps(mode) * NT * cin * 2; }
 __host__ __device__ inline size_t smem_bytes(int mode, int NT, int cin, int ring) {
-  return 1024 + b_bytes(mode, NT, cin) + (size_t)ring * row_bytes(mode, cin) + (size_t)(2 * ring + 4) * kBarBytes + 16;
+  return 1024 + b_bytes(mode, NT, cin) + (size_t)NT * 4 + 128 + (size_t)ring * row_bytes(mode, cin) +
+         (size_t)(2 * ring + 4) * kBarBytes + 16;
 }
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -106,11 +118,20 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar), "r"(bytes)
+               : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+// 3-D TMA tile load (box: 8 channels x staged pixels x 1 row) completing on `bar`.
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* tm, int c, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* tm) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
 }
 
 // K-major, no-swizzle shared-memory matrix descriptor (tcgen05 format: bits 46-48 = 0b001).
@@ -155,25 +176,28 @@ template <int MODE>
 __device__ __forceinline__ int first_row(int i, int py) {
   return MODE == TM_S2 ? 2 * i - 1 : MODE == TM_UP2 ? i + py - 1 : i;
 }
-// input column of staged pixel t for the strip starting at unit column j0
+// TMA x coordinate of the first staged pixel of set s (in that set's tensor map)
 template <int MODE>
-__device__ __forceinline__ int staged_col(int t, int j0, int px) {
-  if (MODE == TM_S2) return t < 129 ? 2 * (j0 + t) - 1 : 2 * (j0 + t - 129);
-  if (MODE == TM_UP2) return j0 + px - 1 + t;
-  return j0 + t;
+__device__ __forceinline__ int set_x0(int s, int j0, int px) {
+  if (MODE == TM_S2) return s == 0 ? j0 - 1 : j0;  // odd pixels 2(j0+t)-1, even pixels 2(j0+t)
+  if (MODE == TM_UP2) return j0 + px - 1;
+  return j0;
 }
-// (staged row offset, staged pixel start) of tap t
+// (staged row offset, pixel set, pixel start) of tap t
 template <int MODE>
-__device__ __forceinline__ void tap_geo(int t, int& row, int& col) {
+__device__ __forceinline__ void tap_geo(int t, int& row, int& set, int& col) {
   if (MODE == TM_S2) {
     row = t / 3;
     const int dx = t % 3;
-    col = dx == 0 ? 0 : dx == 1 ? 129 : 1;
+    set = dx == 1 ? 1 : 0;
+    col = dx == 2 ? 1 : 0;
   } else if (MODE == TM_UP2) {
     row = t >> 1;
+    set = 0;
     col = t & 1;
   } else {
     row = 0;
+    set = 0;
     col = 0;
   }
 }
@@ -181,20 +205,23 @@ __device__ __forceinline__ void tap_geo(int t, int& row, int& col) {
 template <int MODE, int NT>
 __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_constant__ Params p) {
   using G_ = Geo<MODE>;
-  constexpr int RA = G_::RA, STEP = G_::STEP, NPX = G_::NPX, T = G_::T;
+  constexpr int RA = G_::RA, STEP = G_::STEP, T = G_::T, NSET = G_::NSET, NPX = G_::NPX;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* gbase = smem_raw + (base - raw);
-  const int cin = p.cin, ring = p.ring;
+  const int cin = p.cin;
+  const uint32_t ring = (uint32_t)p.ring;
   const int kplanes = cin / 8;
-  const uint32_t plane = NPX * 16;
-  const uint32_t rowb = kplanes * plane;
+  const uint32_t pstride = (NPX * 16 + 127) / 128 * 128;
+  const uint32_t rowb = NSET * kplanes * pstride;
   const uint32_t sB = base;
-  const uint32_t sA = sB + (uint32_t)T * NT * cin * 2;
-  const uint32_t bars = sA + (uint32_t)ring * rowb;
+  const uint32_t sBias = sB + (uint32_t)T * NT * cin * 2;
+  const uint32_t sA = (sBias + NT * 4 + 127u) & ~127u;
+  const uint32_t bars = sA + ring * rowb;
   const uint32_t full0 = bars, empty0 = bars + ring * 8, accf0 = bars + 2 * ring * 8, acce0 = accf0 + 16;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + (acce0 + 16 - base));
+  const float* bias_s = reinterpret_cast<const float*>(gbase + (sBias - base));
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = blockIdx.x % p.G, crank = blockIdx.x / p.G, cpg = gridDim.x / p.G;
@@ -203,16 +230,18 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   const int py = phase >> 1, px = phase & 1;
   const int n0 = nslice * NT;
 
-  // ---- weights of this CTA's set, resident for the kernel's lifetime
+  // ---- weights and bias of this CTA's set, resident for the kernel's lifetime
   {
     const uint4* src = reinterpret_cast<const uint4*>(p.wpack + (size_t)g * T * NT * cin);
     uint4* dst = reinterpret_cast<uint4*>(gbase);
     const int n16 = T * NT * cin / 8;
     for (int e = tid; e < n16; e += kThreads) dst[e] = src[e];
+    float* bs = reinterpret_cast<float*>(gbase + (sBias - base));
+    for (int e = tid; e < NT; e += kThreads) bs[e] = p.bias[n0 + e];
   }
   if (tid == 0) {
-    for (int r = 0; r < ring; ++r) {
-      mbar_init(full0 + 8 * r, 32);
+    for (uint32_t r = 0; r < ring; ++r) {
+      mbar_init(full0 + 8 * r, 1);
       mbar_init(empty0 + 8 * r, 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -234,84 +263,97 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   const uint32_t tmem = *tslot;
   bool ok = true;
 
-  if (warp >= 5) {
-    // ------------------------------------------------------------ producers
-    const int pw = warp - 5;
-    long long q = 0;
-    for (int s = crank; s < p.n_strips && ok; s += cpg) {
-      const Strip st = p.strips[s];
-      const LayerPair L = p.lp[st.pair];
-      const int nrows = STEP * (st.cnt - 1) + RA;
-      const int y0 = first_row<MODE>(st.i0, py);
-      for (int r = 0; r < nrows; ++r, ++q) {
-        if ((int)(q % kProducerWarps) != pw) continue;
-        const int slot = (int)(q % ring);
-        const long long use = q / ring;
-        if (use > 0 && !mbar_wait(empty0 + 8 * slot, (uint32_t)((use - 1) & 1), p.spin)) {
-          atomicCAS(p.err, 0, 1);
-          ok = false;
-          break;
+  if (warp == 5) {
+    // ------------------------------------------------------------ TMA producer (one thread)
+    if (lane == 0) {
+      const uint32_t row_tx = (uint32_t)(NSET * kplanes * NPX * 16);
+      uint32_t q = 0;
+      int last_pair = -1;
+      for (int s = crank; s < p.n_strips && ok; s += cpg) {
+        const Strip st = p.strips[s];
+        const LayerPair* L = p.lp + st.pair;
+        if (st.pair != last_pair) {
+          for (int k = 0; k < NSET; ++k) tensormap_acquire(&L->tm[k]);
+          last_pair = st.pair;
         }
-        const int y = y0 + r;
-        const bool yok = y >= 0 && y < L.Hi;
-        const uint32_t dst0 = sA + slot * rowb;
-        const bf16* rowp = L.in + (size_t)(yok ? y : 0) * L.Wi * cin;
-        for (int e = lane; e < kplanes * NPX; e += 32) {
-          const int t = e / kplanes, c = e - t * kplanes;
-          const int x = staged_col<MODE>(t, st.j0, px);
-          const bool v = yok && x >= 0 && x < L.Wi;
-          cp_async16(dst0 + c * plane + t * 16, v ? (const void*)(rowp + (size_t)x * cin + c * 8) : (const void*)L.in, v);
+        const int nrows = STEP * (st.cnt - 1) + RA;
+        const int y0 = first_row<MODE>(st.i0, py);
+        for (int r = 0; r < nrows; ++r, ++q) {
+          const uint32_t slot = q % ring, use = q / ring;
+          if (use > 0 && !mbar_wait(empty0 + 8 * slot, (use - 1) & 1, p.spin)) {
+            atomicCAS(p.err, 0, 1);
+            ok = false;
+            break;
+          }
+          const uint32_t fb = full0 + 8 * slot;
+          mbar_expect_tx(fb, row_tx);
+          const uint32_t dst0 = sA + slot * rowb;
+          for (int k = 0; k < NSET; ++k) {
+            const int x0 = set_x0<MODE>(k, st.j0, px);
+            for (int c = 0; c < kplanes; ++c)
+              tma_load3(dst0 + (k * kplanes + c) * pstride, &L->tm[k], c * 8, x0, y0 + r, fb);
+          }
         }
-        cp_async_wait_all();
-        fence_proxy_async();
-        mbar_arrive(full0 + 8 * slot);
+      }
+      // no copy may still be writing shared memory when the CTA ends (also after a
+      // timeout): wait for the most recent load of every slot
+      const long long drain = p.spin > 2000000000LL ? p.spin : 2000000000LL;
+      for (uint32_t k = 0; k < ring && k < q; ++k) {
+        const uint32_t row = q - 1 - k;
+        if (!mbar_wait(full0 + 8 * (row % ring), (row / ring) & 1, drain)) atomicCAS(p.err, 0, 5);
       }
     }
+    __syncwarp();
   } else if (warp == 4) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((128u >> 4) << 24);
-      long long qbase = 0, tseq = 0;
+      const uint32_t ksteps = cin / 16;
+      const uint32_t bsz = NT * cin * 2;
+      // descriptor pieces that never change: LBO, SBO, version bits
+      const uint64_t adesc_hi = ((uint64_t)((pstride >> 4) & 0x3FFFu) << 16) | ((uint64_t)(128 >> 4) << 32) | (1ull << 46);
+      const uint64_t bdesc_hi = ((uint64_t)(128 >> 4) << 16) | ((uint64_t)((cin * 16 >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+      uint32_t qbase = 0, tseq = 0;
       for (int s = crank; s < p.n_strips && ok; s += cpg) {
         const Strip st = p.strips[s];
         const int nrows = STEP * (st.cnt - 1) + RA;
         for (int ii = 0; ii < st.cnt && ok; ++ii) {
-          const int rlo = ii == 0 ? 0 : STEP * (ii - 1) + RA;  // rows not waited for yet
-          for (int r = rlo; r < STEP * ii + RA; ++r) {
-            const long long qa = qbase + r;
-            if (!mbar_wait(full0 + 8 * (int)(qa % ring), (uint32_t)((qa / ring) & 1), p.spin)) {
+          const uint32_t rlo = ii == 0 ? 0 : STEP * (ii - 1) + RA;  // rows not waited for yet
+          for (uint32_t r = rlo; r < (uint32_t)(STEP * ii + RA); ++r) {
+            const uint32_t qa = qbase + r;
+            if (!mbar_wait(full0 + 8 * (qa % ring), (qa / ring) & 1, p.spin)) {
               ok = false;
               break;
             }
           }
-          const int buf = (int)(tseq & 1);
-          const long long use = tseq >> 1;
-          if (ok && use > 0 && !mbar_wait(acce0 + 8 * buf, (uint32_t)((use - 1) & 1), p.spin)) ok = false;
+          const uint32_t buf = tseq & 1, use = tseq >> 1;
+          if (ok && use > 0 && !mbar_wait(acce0 + 8 * buf, (use - 1) & 1, p.spin)) ok = false;
           if (!ok) {
             atomicCAS(p.err, 0, 2);
             break;
           }
-          fence_proxy_async();
           tc_fence_after();
-          const uint32_t dcol = tmem + (uint32_t)(buf * NT);
-#pragma unroll 1
+          const uint32_t dcol = tmem + buf * NT;
+          uint32_t slot_of_row[RA];
+#pragma unroll
+          for (int r = 0; r < RA; ++r) slot_of_row[r] = (qbase + STEP * ii + r) % ring;
+#pragma unroll
           for (int t = 0; t < T; ++t) {
-            int ro, co;
-            tap_geo<MODE>(t, ro, co);
-            const long long qa = qbase + STEP * ii + ro;
-            const uint32_t abase = sA + (uint32_t)(qa % ring) * rowb + co * 16;
-            const uint32_t bbase = sB + (uint32_t)t * NT * cin * 2;
-#pragma unroll 1
-            for (int kk = 0; kk < cin / 16; ++kk) {
-              const uint64_t ad = make_desc(abase + kk * 2 * plane, plane, 128);
-              const uint64_t bd = make_desc(bbase + kk * 256, 128, cin * 16);
+            int ro, se, co;
+            tap_geo<MODE>(t, ro, se, co);
+            const uint32_t abase = sA + slot_of_row[ro] * rowb + se * kplanes * pstride + co * 16;
+            const uint32_t bbase = sB + t * bsz;
+#pragma unroll 2
+            for (uint32_t kk = 0; kk < ksteps; ++kk) {
+              const uint64_t ad = adesc_hi | (uint64_t)(((abase + kk * 2 * pstride) & 0x3FFFFu) >> 4);
+              const uint64_t bd = bdesc_hi | (uint64_t)(((bbase + kk * 256) & 0x3FFFFu) >> 4);
               mma_bf16(dcol, ad, bd, idesc, (t | kk) ? 1u : 0u);
             }
           }
           mma_commit(accf0 + 8 * buf);
           // release the rows the next tile of this strip no longer reads
-          const int rel_hi = ii + 1 < st.cnt ? STEP * (ii + 1) : nrows;
-          for (int r = STEP * ii; r < rel_hi; ++r) mma_commit(empty0 + 8 * (int)((qbase + r) % ring));
+          const uint32_t rel_hi = ii + 1 < st.cnt ? STEP * (ii + 1) : nrows;
+          for (uint32_t r = STEP * ii; r < rel_hi; ++r) mma_commit(empty0 + 8 * ((qbase + r) % ring));
           ++tseq;
         }
         qbase += nrows;
@@ -319,39 +361,35 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       // drain, also after a timeout: the last commit arrives when every MMA issued by this
       // CTA has completed, so tensor memory is released only once nothing writes to it
       if (tseq > 0) {
-        const long long last = tseq - 1;
+        const uint32_t last = tseq - 1;
         const long long drain = p.spin > 2000000000LL ? p.spin : 2000000000LL;
-        if (!mbar_wait(accf0 + 8 * (int)(last & 1), (uint32_t)((last >> 1) & 1), drain)) atomicCAS(p.err, 0, 3);
+        if (!mbar_wait(accf0 + 8 * (last & 1), (last >> 1) & 1, drain)) atomicCAS(p.err, 0, 3);
       }
     }
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue (warps 0-3)
     const int m = warp * 32 + lane;
-    long long tseq = 0;
+    uint32_t tseq = 0;
     for (int s = crank; s < p.n_strips && ok; s += cpg) {
       const Strip st = p.strips[s];
-      const LayerPair L = p.lp[st.pair];
+      const LayerPair* L = p.lp + st.pair;
+      const int Hu = L->Hu, Wu = L->Wu, Ho = L->Ho, Wo = L->Wo;
+      bf16* const out = L->out;
       for (int ii = 0; ii < st.cnt; ++ii, ++tseq) {
-        const int buf = (int)(tseq & 1);
-        if (!mbar_wait(accf0 + 8 * buf, (uint32_t)((tseq >> 1) & 1), p.spin)) {
+        const uint32_t buf = tseq & 1;
+        if (!mbar_wait(accf0 + 8 * buf, (tseq >> 1) & 1, p.spin)) {
           atomicCAS(p.err, 0, 4);
           ok = false;
           break;
         }
         tc_fence_after();
         const int i = st.i0 + ii, j = st.j0 + m;
-        int oy, ox;
-        if (MODE == TM_UP2) {
-          oy = 2 * i + py;
-          ox = 2 * j + px;
-        } else {
-          oy = i;
-          ox = j;
-        }
-        const bool valid = i < L.Hu && j < L.Wu && oy < L.Ho && ox < L.Wo;
-        bf16* op = L.out + ((size_t)oy * L.Wo + ox) * p.cout + n0;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * NT);
+        const int oy = MODE == TM_UP2 ? 2 * i + py : i;
+        const int ox = MODE == TM_UP2 ? 2 * j + px : j;
+        const bool valid = i < Hu && j < Wu && oy < Ho && ox < Wo;
+        bf16* op = out + ((size_t)oy * Wo + ox) * p.cout + n0;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16) + buf * NT;
 #pragma unroll 1
         for (int c0 = 0; c0 < NT; c0 += 32) {
           uint32_t r[32];
@@ -362,8 +400,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
             uint32_t packed[CW / 2];
 #pragma unroll
             for (int e = 0; e < CW; e += 2) {
-              float a = __uint_as_float(r[e]) + __ldg(p.bias + n0 + c0 + e);
-              float b = __uint_as_float(r[e + 1]) + __ldg(p.bias + n0 + c0 + e + 1);
+              float a = __uint_as_float(r[e]) + bias_s[c0 + e];
+              float b = __uint_as_float(r[e + 1]) + bias_s[c0 + e + 1];
               if (p.relu) {
                 a = fmaxf(a, 0.f);
                 b = fmaxf(b, 0.f);
@@ -427,42 +465,6 @@ __global__ void pack_kernel(const float* __restrict__ W, int mode, int NT, int G
   out[dst] = __float2bfloat16_rn(v);
 }
 
-// ------------------------------------------------------------------ exact odd borders of UP2
-// Recomputes the last output row (if Ho is odd) and last column (if Wo is odd) of a
-// nearest-x2 + 3x3 conv with the unfolded (BF16-rounded) weights.
-__global__ void up2_border_fix(const LayerPair* __restrict__ lps, const float* __restrict__ W,
-                               const float* __restrict__ bias, int cin, int cout, int relu) {
-  const LayerPair L = lps[blockIdx.y];
-  const int nrow = (L.Ho & 1) ? L.Wo : 0;
-  const int ncol = (L.Wo & 1) ? L.Ho : 0;
-  const int total = (nrow + ncol) * cout;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const int co = e % cout, pix = e / cout;
-    int Y, X;
-    if (pix < nrow) {
-      Y = L.Ho - 1;
-      X = pix;
-    } else {
-      Y = pix - nrow;
-      X = L.Wo - 1;
-    }
-    float acc = bias[co];
-    for (int ky = 0; ky < 3; ++ky) {
-      const int vy = Y + ky - 1;
-      if (vy < 0 || vy >= L.Ho) continue;
-      for (int kx = 0; kx < 3; ++kx) {
-        const int vx = X + kx - 1;
-        if (vx < 0 || vx >= L.Wo) continue;
-        const bf16* ip = L.in + ((size_t)(vy >> 1) * L.Wi + (vx >> 1)) * cin;
-        const float* wp = W + ((size_t)co * 9 + ky * 3 + kx) * cin;
-        for (int ci = 0; ci < cin; ++ci)
-          acc = fmaf(__bfloat162float(__float2bfloat16_rn(wp[ci])), __bfloat162float(ip[ci]), acc);
-      }
-    }
-    if (relu) acc = fmaxf(acc, 0.f);
-    L.out[((size_t)Y * L.Wo + X) * cout + co] = __float2bfloat16_rn(acc);
-  }
-}
 
 template <int MODE, int NT>
 cudaError_t launch_mode_nt(const Params& p, int grid, size_t smem, cudaStream_t st) {
@@ -519,15 +521,37 @@ int blocks_per_sm(int mode, int NT, size_t smem) {
 
 // ------------------------------------------------------------------ host side
 namespace {
-
 constexpr size_t kSmemLimit = 232448;  // 227 KB opt-in per block
-
-struct TcLayerPlan {
-  int layer, mode, NT, G, ring, cin, cout, relu;
-  size_t wofs, smem;
-};
-
 }  // namespace
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+// TMA view of a BF16 NHWC activation: dims (channels, pixels of the set, rows), box of
+// 8 channels x `box_px` pixels x 1 row, zero fill outside.  `px_step` = 2 for the odd /
+// even pixel sets of a stride-2 layer.
+static bool make_tmap(CUtensorMap* m, const __nv_bfloat16* base, int C, int npix, int H, int W, int px_step,
+                      int box_px) {
+  auto fn = encode_fn();
+  if (!fn || npix < 1) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)npix, (cuuint64_t)H};
+  cuuint64_t strides[2] = {(cuuint64_t)px_step * C * 2, (cuuint64_t)W * C * 2};
+  cuuint32_t box[3] = {8, (cuuint32_t)box_px, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
 
 static void plan_layers(const NetDims& net, std::vector<TcLayerPlan>& plans, size_t& total) {
   plans.clear();
@@ -580,17 +604,31 @@ sv_status Ctx::pack_bf16_weights(cudaStream_t st) {
   return SV_OK;
 }
 
-sv_status Ctx::refine_tc(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out,
-                         cudaStream_t st) {
+// Host side of one tensor-core refinement call: activation workspaces (allocated here),
+// per-layer descriptor and strip tables (built here, uploaded by the caller) and launch
+// geometry.  Nothing is enqueued on a stream.
+sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out, TcRun& r) {
   using tc::LayerPair;
   using tc::Strip;
-  std::vector<TcLayerPlan> plans;
   size_t wtotal;
-  plan_layers(net, plans, wtotal);
+  plan_layers(net, r.plans, wtotal);
+  for (size_t li = 0; li < r.plans.size(); ++li) {
+    if (tc_nt_override[li] > 0 && tc_nt_override[li] <= r.plans[li].NT) {
+      // autotuned narrower N slice (more weight sets, more CTAs per pair)
+      TcLayerPlan& pl = r.plans[li];
+      const int NT = tc_nt_override[li];
+      pl.NT = NT;
+      const int nsl = (pl.cout + NT - 1) / NT;
+      pl.G = pl.mode == tc::TM_UP2 ? 4 * nsl : nsl;
+      const int RA = pl.mode == tc::TM_S2 ? 3 : pl.mode == tc::TM_UP2 ? 2 : 1;
+      const int STEP = pl.mode == tc::TM_S2 ? 2 : 1;
+      while (pl.ring < RA + 3 * STEP && tc::smem_bytes(pl.mode, NT, pl.cin, pl.ring + 1) <= kSmemLimit) ++pl.ring;
+      pl.smem = tc::smem_bytes(pl.mode, NT, pl.cin, pl.ring);
+    }
+  }
   sv_status s;
-  int dev = device, nsm = 0;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  // ---- activations (BF16, NHWC, all pairs back to back): e1 e2 e3 z d1 d2 d3
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
   std::vector<Levels> lv(n);
   size_t cnt[7] = {0};
   std::vector<std::array<size_t, 7>> off(n), lens;
@@ -612,23 +650,16 @@ sv_status Ctx::refine_tc(const sv_pair* pairs, const int16_t* const* coarse, int
   auto act = [&](int k, int i) { return (__nv_bfloat16*)tc_act[k].p + off[i][k]; };
   tc_off = off;
   tc_len = lens;
-  int* d_err = (int*)err_flag.p;
-
-  // ---- tables: per layer, LayerPair[n] and its strips
-  struct LayerTab {
-    size_t lp_ofs, strip_ofs;
-    int n_strips, grid;
-  };
-  std::vector<unsigned char> host;
+  r.host.clear();
   auto put = [&](const void* src, size_t bytes) {
-    size_t o = (host.size() + 15) / 16 * 16;
-    host.resize(o + bytes);
-    memcpy(host.data() + o, src, bytes);
+    size_t o = (r.host.size() + 63) / 64 * 64;  // tensor maps need 64-byte alignment
+    r.host.resize(o + bytes);
+    memcpy(r.host.data() + o, src, bytes);
     return o;
   };
-  std::vector<LayerTab> tabs(plans.size());
-  for (size_t li = 0; li < plans.size(); ++li) {
-    const TcLayerPlan& pl = plans[li];
+  r.tabs.assign(r.plans.size(), {});
+  for (size_t li = 0; li < r.plans.size(); ++li) {
+    const TcLayerPlan& pl = r.plans[li];
     std::vector<LayerPair> lps(n);
     const int in_act = pl.layer == L_ENC2 ? 0 : pl.layer == L_ENC3 ? 1 : pl.layer == L_MU ? 2 : pl.layer == L_DEC1 ? 3
                        : pl.layer == L_DEC2 ? 4 : 5;
@@ -638,8 +669,10 @@ sv_status Ctx::refine_tc(const sv_pair* pairs, const int16_t* const* coarse, int
     const int lout = pl.layer == L_ENC2 ? 2 : pl.layer == L_ENC3 ? 3 : pl.layer == L_MU ? 3 : pl.layer == L_DEC1 ? 2
                      : pl.layer == L_DEC2 ? 1 : 0;
     long long units = 0;
+    std::vector<UpFixPair> fix(n);
     for (int i = 0; i < n; ++i) {
       LayerPair& L = lps[i];
+      memset(&L, 0, sizeof(L));
       L.in = act(in_act, i);
       L.out = act(out_act, i);
       L.Hi = lv[i].H[lin]; L.Wi = lv[i].W[lin];
@@ -647,46 +680,77 @@ sv_status Ctx::refine_tc(const sv_pair* pairs, const int16_t* const* coarse, int
       if (pl.mode == tc::TM_UP2) { L.Hu = L.Hi; L.Wu = L.Wi; }
       else { L.Hu = L.Ho; L.Wu = L.Wo; }
       units += (long long)L.Hu * ((L.Wu + 127) / 128);
+      bool okm;
+      if (pl.mode == tc::TM_S2)
+        okm = make_tmap(&L.tm[0], L.in + pl.cin, pl.cin, L.Wi / 2, L.Hi, L.Wi, 2, 129) &&
+              make_tmap(&L.tm[1], L.in, pl.cin, (L.Wi + 1) / 2, L.Hi, L.Wi, 2, 129);
+      else
+        okm = make_tmap(&L.tm[0], L.in, pl.cin, L.Wi, L.Hi, L.Wi, 1, tc::npx(pl.mode));
+      if (!okm) return fail(SV_ERR_CUDA, "layer %d: cuTensorMapEncodeTiled failed", pl.layer);
+      fix[i] = {L.in, L.out, L.Hi, L.Wi, L.Ho, L.Wo, L.Hu, L.Wu};
     }
     int bps = tc::blocks_per_sm(pl.mode, pl.NT, pl.smem);
     if (bps <= 0) return fail(SV_ERR_UNSUPPORTED, "layer %d: tensor-core kernel does not fit an SM", pl.layer);
     int grid = std::max(pl.G, (nsm * bps) / pl.G * pl.G);
     const int cpg = grid / pl.G;
-    // strip height: about four strips per CTA of a weight set, at least 2 rows
+    // strip height: about four strips per CTA of a weight set, at least 2 rows, unless tuned
     const long long want = std::max<long long>(1, (long long)cpg * 4);
-    const int hs = tc_strip_rows > 0 ? tc_strip_rows : (int)std::max<long long>(2, (units + want - 1) / want);
+    int hs = (int)std::max<long long>(2, (units + want - 1) / want);
+    if (tc_strip_rows > 0) hs = tc_strip_rows;
+    if (tc_rows_override[li] > 0) hs = tc_rows_override[li];
     std::vector<Strip> strips;
     for (int i = 0; i < n; ++i)
       for (int j0 = 0; j0 < lps[i].Wu; j0 += 128)
         for (int i0 = 0; i0 < lps[i].Hu; i0 += hs) strips.push_back({i, j0, i0, std::min(hs, lps[i].Hu - i0)});
-    grid = std::min<long long>(grid, (long long)pl.G * (long long)strips.size());
-    tabs[li].lp_ofs = put(lps.data(), sizeof(LayerPair) * n);
-    tabs[li].strip_ofs = put(strips.data(), sizeof(Strip) * strips.size());
-    tabs[li].n_strips = (int)strips.size();
-    tabs[li].grid = grid;
+    grid = (int)std::min<long long>(grid, (long long)pl.G * (long long)strips.size());
+    r.tabs[li].lp_ofs = put(lps.data(), sizeof(LayerPair) * n);
+    r.tabs[li].fix_ofs = put(fix.data(), sizeof(UpFixPair) * n);
+    r.tabs[li].strip_ofs = put(strips.data(), sizeof(Strip) * strips.size());
+    r.tabs[li].n_strips = (int)strips.size();
+    r.tabs[li].grid = grid;
+    r.tabs[li].hs = hs;
+    int mb = 0;
+    for (int i = 0; i < n; ++i)
+      mb = std::max(mb, ((lps[i].Ho & 1) ? lps[i].Wo : 0) + ((lps[i].Wo & 1) ? lps[i].Ho : 0));
+    r.tabs[li].max_border = mb;
   }
-  if ((s = cuda(tc_tables.ensure(host.size()), "alloc tables"))) return s;
-  if ((s = cuda(cudaMemcpyAsync(tc_tables.p, host.data(), host.size(), cudaMemcpyHostToDevice, st), "upload tables")))
-    return s;
-  tc_host_tables.swap(host);  // keep the source alive until the copy has executed
-
-  const float* W = (const float*)w32.p;
-  // ---- enc1: bilinear x4 + normalisation fused into the first conv (CUDA cores, BF16 out)
+  std::vector<EdgePair> eps_(n);
+  r.maxW = r.maxH = r.maxW1 = r.maxH1 = 0;
   for (int i = 0; i < n; ++i) {
     const sv_pair& p = pairs[i];
-    LaunchScope ls(*this, "enc1_bf16", st);
-    if ((s = cuda(launch_enc1_bf16(p.left, p.pitch, p.width, p.height, coarse[i], p.width / 4, p.height / 4,
-                                   W + net.w_off(L_ENC1), W + net.b_off(L_ENC1), net.enc[0], act(0, i), st),
+    eps_[i] = {p.left, p.pitch, p.width, p.height, p.width / 4, p.height / 4, coarse[i], act(0, i), act(6, i), out[i]};
+    r.maxW = std::max(r.maxW, p.width);
+    r.maxH = std::max(r.maxH, p.height);
+    r.maxW1 = std::max(r.maxW1, lv[i].W[1]);
+    r.maxH1 = std::max(r.maxH1, lv[i].H[1]);
+  }
+  r.edge_ofs = put(eps_.data(), sizeof(EdgePair) * n);
+  r.n = n;
+  return SV_OK;
+}
+
+// Kernel launches of a prepared call; `tables` holds r.host on the device.  Only kernel
+// launches: safe inside a stream capture.
+sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream_t st) {
+  using tc::LayerPair;
+  using tc::Strip;
+  sv_status s;
+  const float* W = (const float*)w32.p;
+  const EdgePair* d_edges = (const EdgePair*)(tables + r.edge_ofs);
+  {
+    LaunchScope ls(*this, "edge_enc1", st);
+    if ((s = cuda(launch_edge_enc1(d_edges, r.n, r.maxW1, r.maxH1, W + net.w_off(L_ENC1), W + net.b_off(L_ENC1),
+                                   net.enc[0], st),
                   "enc1")))
       return s;
   }
   static const char* names[6] = {"tc_enc2", "tc_enc3", "tc_latent", "tc_dec1", "tc_dec2", "tc_dec3"};
-  for (size_t li = 0; li < plans.size(); ++li) {
-    const TcLayerPlan& pl = plans[li];
+  for (size_t li = 0; li < r.plans.size(); ++li) {
+    const TcLayerPlan& pl = r.plans[li];
     tc::Params prm{};
-    prm.lp = (const LayerPair*)((unsigned char*)tc_tables.p + tabs[li].lp_ofs);
-    prm.strips = (const Strip*)((unsigned char*)tc_tables.p + tabs[li].strip_ofs);
-    prm.n_strips = tabs[li].n_strips;
+    prm.lp = (const LayerPair*)(tables + r.tabs[li].lp_ofs);
+    prm.strips = (const Strip*)(tables + r.tabs[li].strip_ofs);
+    prm.n_strips = r.tabs[li].n_strips;
     prm.wpack = (const __nv_bfloat16*)wbf.p + pl.wofs;
     prm.bias = W + net.b_off(pl.layer);
     prm.cin = pl.cin;
@@ -694,28 +758,41 @@ sv_status Ctx::refine_tc(const sv_pair* pairs, const int16_t* const* coarse, int
     prm.G = pl.G;
     prm.relu = pl.relu;
     prm.ring = pl.ring;
-    prm.err = d_err;
+    prm.err = (int*)err_flag.p;
     prm.spin = spin_limit;
     {
       LaunchScope ls(*this, names[li], st);
-      if ((s = cuda(tc::launch_conv(pl.mode, prm, pl.NT, tabs[li].grid, pl.smem, st), names[li]))) return s;
+      if ((s = cuda(tc::launch_conv(pl.mode, prm, pl.NT, r.tabs[li].grid, pl.smem, st), names[li]))) return s;
     }
-    if (pl.mode == tc::TM_UP2) {
-      LaunchScope ls(*this, "up2_border_fix", st);
-      tc::up2_border_fix<<<dim3(8, n), 256, 0, st>>>(prm.lp, W + net.w_off(pl.layer), prm.bias, pl.cin, pl.cout, 1);
-      if ((s = cuda(cudaGetLastError(), "border fix"))) return s;
+    if (pl.mode == tc::TM_UP2 && r.tabs[li].max_border > 0) {
+      LaunchScope ls(*this, "edge_up2fix", st);
+      if ((s = cuda(launch_edge_up2fix((const UpFixPair*)(tables + r.tabs[li].fix_ofs), r.n, r.tabs[li].max_border,
+                                       W + net.w_off(pl.layer),
+                                       prm.bias, pl.cin, pl.cout, 1, st),
+                    "border fix")))
+        return s;
     }
   }
-  // ---- final conv + residual (CUDA cores, FP32)
-  for (int i = 0; i < n; ++i) {
-    const sv_pair& p = pairs[i];
-    LaunchScope ls(*this, "final_bf16", st);
-    if ((s = cuda(launch_final_bf16(act(6, i), p.width, p.height, net.dec[2], W + net.w_off(L_FINAL),
-                                    W + net.b_off(L_FINAL), coarse[i], p.width / 4, p.height / 4, out[i], st),
+  {
+    LaunchScope ls(*this, "edge_final", st);
+    if ((s = cuda(launch_edge_final(d_edges, r.n, r.maxW, r.maxH, W + net.w_off(L_FINAL), W + net.b_off(L_FINAL),
+                                    net.dec[2], st),
                   "final")))
       return s;
   }
   return SV_OK;
+}
+
+sv_status Ctx::refine_tc(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out,
+                         cudaStream_t st) {
+  TcRun r;
+  sv_status s = tc_prepare(pairs, coarse, n, out, r);
+  if (s) return s;
+  if ((s = cuda(tc_tables.ensure(r.host.size()), "alloc tables"))) return s;
+  if ((s = cuda(cudaMemcpyAsync(tc_tables.p, r.host.data(), r.host.size(), cudaMemcpyHostToDevice, st),
+                "upload tables")))
+    return s;
+  return tc_launch(r, (const unsigned char*)tc_tables.p, st);
 }
 
 }  // namespace sv

@@ -105,36 +105,47 @@ sv_status Ctx::check_pairs(const sv_pair* pairs, int n_pairs) {
 }
 
 // ---------------------------------------------------------------- coarse matching
-sv_status Ctx::coarse(const sv_pair* pairs, int n, int16_t* const* disp, float* const* best, float* const* second,
-                      cudaStream_t st) {
-  std::vector<ZPair> zp(n);
-  std::vector<ZJob> jobs;
-  int maxD = 1;
-  for (int i = 0; i < n; ++i) maxD = std::max(maxD, pairs[i].max_disp);
-  const int gx = kZnccWarps * zncc_tx(zncc_kd(maxD));
+void Ctx::coarse_prepare(const sv_pair* pairs, int n, int16_t* const* disp, float* const* best, float* const* second,
+                         ZRun& z) {
+  z.pairs.assign(n, ZPair{});
+  z.jobs.clear();
+  z.maxD = 1;
+  for (int i = 0; i < n; ++i) z.maxD = std::max(z.maxD, pairs[i].max_disp);
+  const int gx = kZnccWarps * zncc_tx(zncc_kd(z.maxD));
   for (int i = 0; i < n; ++i) {
     const sv_pair& p = pairs[i];
-    ZPair& z = zp[i];
-    z.L = p.left; z.R = p.right; z.W = p.width; z.H = p.height; z.pitch = p.pitch; z.D = p.max_disp;
-    z.w = p.width / 4; z.h = p.height / 4;
-    z.disp = disp[i];
-    z.best = best ? best[i] : nullptr;
-    z.second = second ? second[i] : nullptr;
-    for (int y0 = 0; y0 < z.h; y0 += kZnccTY)
-      for (int x0 = 0; x0 < z.w; x0 += gx) jobs.push_back({i, y0, x0, 0});
+    ZPair& q = z.pairs[i];
+    q.L = p.left; q.R = p.right; q.W = p.width; q.H = p.height; q.pitch = p.pitch; q.D = p.max_disp;
+    q.w = p.width / 4; q.h = p.height / 4;
+    q.disp = disp[i];
+    q.best = best ? best[i] : nullptr;
+    q.second = second ? second[i] : nullptr;
+    for (int y0 = 0; y0 < q.h; y0 += kZnccTY)
+      for (int x0 = 0; x0 < q.w; x0 += gx) z.jobs.push_back({i, y0, x0, 0});
   }
-  if (jobs.empty()) return SV_OK;
+}
+
+sv_status Ctx::coarse_launch(const ZRun& z, const ZPair* d_pairs, const ZJob* d_jobs, cudaStream_t st) {
+  if (z.jobs.empty()) return SV_OK;
+  LaunchScope ls(*this, "zncc_wta", st);
+  return cuda(launch_zncc_wta(d_pairs, d_jobs, (int)z.jobs.size(), cfg.window / 2, z.maxD, st), "zncc_wta launch");
+}
+
+sv_status Ctx::coarse(const sv_pair* pairs, int n, int16_t* const* disp, float* const* best, float* const* second,
+                      cudaStream_t st) {
+  ZRun z;
+  coarse_prepare(pairs, n, disp, best, second, z);
+  if (z.jobs.empty()) return SV_OK;
   sv_status s;
   if ((s = cuda(zpairs.ensure(sizeof(ZPair) * n), "alloc pair table"))) return s;
-  if ((s = cuda(zjobs.ensure(sizeof(ZJob) * jobs.size()), "alloc job table"))) return s;
-  if ((s = cuda(cudaMemcpyAsync(zpairs.p, zp.data(), sizeof(ZPair) * n, cudaMemcpyHostToDevice, st), "upload pairs")))
+  if ((s = cuda(zjobs.ensure(sizeof(ZJob) * z.jobs.size()), "alloc job table"))) return s;
+  if ((s = cuda(cudaMemcpyAsync(zpairs.p, z.pairs.data(), sizeof(ZPair) * n, cudaMemcpyHostToDevice, st),
+                "upload pairs")))
     return s;
-  if ((s = cuda(cudaMemcpyAsync(zjobs.p, jobs.data(), sizeof(ZJob) * jobs.size(), cudaMemcpyHostToDevice, st),
+  if ((s = cuda(cudaMemcpyAsync(zjobs.p, z.jobs.data(), sizeof(ZJob) * z.jobs.size(), cudaMemcpyHostToDevice, st),
                 "upload jobs")))
     return s;
-  LaunchScope ls(*this, "zncc_wta", st);
-  return cuda(launch_zncc_wta((const ZPair*)zpairs.p, (const ZJob*)zjobs.p, (int)jobs.size(), cfg.window / 2, maxD, st),
-              "zncc_wta launch");
+  return coarse_launch(z, (const ZPair*)zpairs.p, (const ZJob*)zjobs.p, st);
 }
 
 // ---------------------------------------------------------------- plain refinement
@@ -467,8 +478,8 @@ sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream) {
     return s;
   if (code) {
     cudaMemset(c->err_flag.p, 0, sizeof(int));
-    static const char* where[] = {"", "producer", "MMA issuer", "MMA drain", "epilogue"};
-    return c->fail(SV_ERR_TIMEOUT, "a device-side wait ran out (%s, code %d)", code >= 1 && code <= 4 ? where[code] : "?",
+    static const char* where[] = {"", "producer", "MMA issuer", "MMA drain", "epilogue", "copy drain"};
+    return c->fail(SV_ERR_TIMEOUT, "a device-side wait ran out (%s, code %d)", code >= 1 && code <= 5 ? where[code] : "?",
                    code);
   }
   return SV_OK;
@@ -480,6 +491,12 @@ sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value) {
   if (!strcmp(key, "spin_limit")) {
     if (value < 1) return c->fail(SV_ERR_INVALID_ARG, "spin_limit must be >= 1");
     c->spin_limit = value;
+    return SV_OK;
+  }
+  if (!strcmp(key, "graphs")) {
+    if (value != 0 && value != 1) return c->fail(SV_ERR_INVALID_ARG, "graphs must be 0 or 1");
+    c->use_graphs = value != 0;
+    if (!c->use_graphs) c->drop_graphs();
     return SV_OK;
   }
   if (!strcmp(key, "tc_strip_rows")) {

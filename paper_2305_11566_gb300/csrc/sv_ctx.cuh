@@ -22,6 +22,43 @@ struct DevBuf {
   void release();
 };
 
+// Launch plan of one tensor-core layer.
+struct TcLayerPlan {
+  int layer, mode, NT, G, ring, cin, cout, relu;
+  size_t wofs, smem;
+};
+
+// Prepared tensor-core refinement call: plans, table bytes and launch geometry.
+struct TcRun {
+  std::vector<TcLayerPlan> plans;
+  struct Tab {
+    size_t lp_ofs, strip_ofs, fix_ofs;
+    int n_strips, grid, max_border, hs;
+  };
+  std::vector<Tab> tabs;
+  std::vector<unsigned char> host;
+  size_t edge_ofs = 0;
+  int n = 0, maxW = 0, maxH = 0, maxW1 = 0, maxH1 = 0;
+};
+
+// Prepared coarse-matching call.
+struct ZRun {
+  std::vector<ZPair> pairs;
+  std::vector<ZJob> jobs;
+  int maxD = 1;
+};
+
+// One captured batched step (coarse match + tensor-core refinement) and what it needs.
+struct GraphEntry {
+  std::vector<uint64_t> key;
+  cudaGraphExec_t exec = nullptr;
+  void* tables = nullptr;  // device copy of the step's tables (owned)
+  struct Rec { std::string name; cudaEvent_t a, b; };
+  std::vector<Rec> prof;   // event pairs captured around each kernel (profiling on)
+  long long kernels = 0;
+  long long last_use = 0;
+};
+
 struct Ctx {
   sv_config cfg{};
   NetDims net{};
@@ -48,6 +85,14 @@ struct Ctx {
   std::vector<unsigned char> tc_host_tables;
   long long spin_limit = 4000000000LL;  // clock64 cycles a device-side wait may spin
   int tc_strip_rows = 0;                // 0: automatic
+  int tc_rows_override[6] = {0, 0, 0, 0, 0, 0};  // per tensor-core layer, set by the autotuner
+  int tc_nt_override[6] = {0, 0, 0, 0, 0, 0};
+  bool use_graphs = true;
+  bool tune_loaded = false;
+  double tune_us[6] = {0, 0, 0, 0, 0, 0};
+  DevBuf tune_out;
+  std::vector<GraphEntry> graphs;
+  long long graph_clock = 0;
   std::vector<std::array<size_t, 7>> tc_off;   // per pair offsets of the last tensor-core call
   std::vector<std::array<size_t, 7>> tc_len;
   DevBuf err_flag;                      // device int: first failure code of a kernel
@@ -55,7 +100,7 @@ struct Ctx {
   // launch accounting and optional per-kernel event timing
   long long launches = 0;
   bool prof_on = false;
-  struct ProfRec { std::string name; cudaEvent_t a, b; };
+  struct ProfRec { std::string name; cudaEvent_t a, b; bool pooled = true; };  // pooled: events return to ev_free
   std::vector<ProfRec> prof_pending;
   std::vector<cudaEvent_t> ev_free;
   std::map<std::string, std::pair<long long, double>> prof_tot;
@@ -95,6 +140,22 @@ struct Ctx {
   template <typename T>
   sv_status adam(const T* g, int step, double lr, double b1, double b2, double eps, cudaStream_t st);
   sv_status refine_tc(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out, cudaStream_t st);
+  sv_status tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out, TcRun& r);
+  sv_status tc_launch(const TcRun& r, const unsigned char* tables, cudaStream_t st);
+  void coarse_prepare(const sv_pair* pairs, int n, int16_t* const* disp, float* const* best, float* const* second,
+                      ZRun& z);
+  sv_status coarse_launch(const ZRun& z, const ZPair* d_pairs, const ZJob* d_jobs, cudaStream_t st);
+  sv_status pipeline_graph(const sv_pair* pairs, int n, float* const* out, cudaStream_t st);
+  sv_status autotune(const sv_pair* pairs, int n, const char* cache_path, cudaStream_t st);
+  void drop_graphs() {
+    prof_flush();  // pending records may point at graph-owned events
+    for (auto& g : graphs) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.tables) cudaFree(g.tables);
+      for (auto& r : g.prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    }
+    graphs.clear();
+  }
 
   void prof_flush() {
     for (auto& r : prof_pending) {
@@ -104,17 +165,20 @@ struct Ctx {
         t.first += 1;
         t.second += ms;
       }
-      ev_free.push_back(r.a);
-      ev_free.push_back(r.b);
+      if (r.pooled) {
+        ev_free.push_back(r.a);
+        ev_free.push_back(r.b);
+      }
     }
     prof_pending.clear();
   }
 
   void release_all() {
     prof_flush();
+    drop_graphs();
     for (auto e : ev_free) cudaEventDestroy(e);
     ev_free.clear();
-    host_img.release(); host_out.release(); err_flag.release();
+    host_img.release(); host_out.release(); err_flag.release(); tune_out.release();
     w32.release(); w64.release(); wbf.release(); zpairs.release(); zjobs.release(); coarse_maps.release();
     for (auto& b : act) b.release();
     for (auto& b : tc_act) b.release();
@@ -145,17 +209,22 @@ struct LaunchScope {
   const char* name;
   cudaStream_t st;
   cudaEvent_t a = nullptr;
+  unsigned flags = cudaEventRecordDefault;
   LaunchScope(Ctx& ctx, const char* n, cudaStream_t s) : c(ctx), name(n), st(s) {
     ++c.launches;
     if (c.prof_on) {
+      // inside a stream capture only an "external" record becomes an event-record node
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        flags = cudaEventRecordExternal;
       a = c.take_event();
-      cudaEventRecord(a, st);
+      cudaEventRecordWithFlags(a, st, flags);
     }
   }
   ~LaunchScope() {
     if (c.prof_on && a) {
       cudaEvent_t b = c.take_event();
-      cudaEventRecord(b, st);
+      cudaEventRecordWithFlags(b, st, flags);
       c.prof_pending.push_back({name, a, b});
     }
   }

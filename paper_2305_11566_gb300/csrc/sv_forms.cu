@@ -20,6 +20,8 @@ sv_status Ctx::refine_infer(const sv_pair* pairs, const int16_t* const* coarse, 
 }
 
 sv_status Ctx::pipeline(const sv_pair* pairs, int n, float* const* out, cudaStream_t st) {
+  if (cfg.precision == SV_BF16 && use_graphs && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread)
+    return pipeline_graph(pairs, n, out, st);
   std::vector<size_t> off(n + 1, 0);
   for (int i = 0; i < n; ++i) off[i + 1] = off[i] + (size_t)(pairs[i].width / 4) * (pairs[i].height / 4);
   sv_status s = cuda(coarse_maps.ensure(off[n] * sizeof(int16_t)), "alloc coarse maps");
@@ -29,6 +31,112 @@ sv_status Ctx::pipeline(const sv_pair* pairs, int n, float* const* out, cudaStre
   if ((s = coarse(pairs, n, maps.data(), nullptr, nullptr, st))) return s;
   std::vector<const int16_t*> cm(maps.begin(), maps.end());
   return refine_infer(pairs, cm.data(), n, out, st);
+}
+
+// Batched BF16 step through a CUDA graph.  The graph of a batch is captured once and
+// replayed while the batch signature is unchanged: pair pointers and sizes, output
+// pointers, every workspace address it bakes in, the launch plan knobs and whether
+// profiling events are captured.  Tables are uploaded to a buffer the graph owns before
+// the capture; the capture itself holds kernel launches only.
+sv_status Ctx::pipeline_graph(const sv_pair* pairs, int n, float* const* out, cudaStream_t st) {
+  std::vector<size_t> off(n + 1, 0);
+  for (int i = 0; i < n; ++i) off[i + 1] = off[i] + (size_t)(pairs[i].width / 4) * (pairs[i].height / 4);
+  sv_status s = cuda(coarse_maps.ensure(off[n] * sizeof(int16_t)), "alloc coarse maps");
+  if (s) return s;
+  std::vector<int16_t*> maps(n);
+  for (int i = 0; i < n; ++i) maps[i] = (int16_t*)coarse_maps.p + off[i];
+  std::vector<const int16_t*> cm(maps.begin(), maps.end());
+  ZRun z;
+  coarse_prepare(pairs, n, maps.data(), nullptr, nullptr, z);
+  TcRun r;
+  if ((s = tc_prepare(pairs, cm.data(), n, out, r))) return s;  // allocates workspaces if needed
+  std::vector<uint64_t> key;
+  key.reserve(8 * n + 32);
+  auto k = [&](uint64_t v) { key.push_back(v); };
+  k((uint64_t)n);
+  for (int i = 0; i < n; ++i) {
+    k((uint64_t)(uintptr_t)pairs[i].left); k((uint64_t)(uintptr_t)pairs[i].right);
+    k(((uint64_t)pairs[i].width << 32) | (uint32_t)pairs[i].height);
+    k(((uint64_t)pairs[i].pitch << 32) | (uint32_t)pairs[i].max_disp);
+    k((uint64_t)(uintptr_t)out[i]);
+  }
+  k((uint64_t)(uintptr_t)coarse_maps.p);
+  for (auto& b : tc_act) k((uint64_t)(uintptr_t)b.p);
+  k((uint64_t)(uintptr_t)w32.p); k((uint64_t)(uintptr_t)wbf.p); k((uint64_t)(uintptr_t)err_flag.p);
+  k((uint64_t)spin_limit);
+  k((uint64_t)prof_on);
+  for (auto& t : r.tabs) k(((uint64_t)t.hs << 32) | (uint32_t)t.grid);
+  for (auto& p : r.plans) k(((uint64_t)p.NT << 32) | (uint32_t)p.ring);
+  ++graph_clock;
+  for (auto& g : graphs) {
+    if (g.key != key) continue;
+    g.last_use = graph_clock;
+    if ((s = cuda(cudaGraphLaunch(g.exec, st), "graph launch"))) return s;
+    launches += g.kernels;
+    if (prof_on)
+      for (auto& rec : g.prof) prof_pending.push_back({rec.name, rec.a, rec.b, false});
+    return SV_OK;
+  }
+  // ---- capture a new graph
+  if (graphs.size() >= 8) {  // evict the least recently used
+    prof_flush();
+    auto it = std::min_element(graphs.begin(), graphs.end(),
+                               [](const GraphEntry& a, const GraphEntry& b) { return a.last_use < b.last_use; });
+    if (it->exec) cudaGraphExecDestroy(it->exec);
+    if (it->tables) cudaFree(it->tables);
+    for (auto& rec : it->prof) { cudaEventDestroy(rec.a); cudaEventDestroy(rec.b); }
+    graphs.erase(it);
+  }
+  GraphEntry g;
+  g.key = key;
+  g.last_use = graph_clock;
+  const size_t zp_bytes = sizeof(ZPair) * z.pairs.size(), zj_bytes = sizeof(ZJob) * z.jobs.size();
+  const size_t zp_ofs = 0, zj_ofs = (zp_bytes + 255) / 256 * 256, tc_ofs = (zj_ofs + zj_bytes + 255) / 256 * 256;
+  const size_t total = tc_ofs + r.host.size();
+  if ((s = cuda(cudaMalloc(&g.tables, total), "alloc graph tables"))) return s;
+  unsigned char* tb = (unsigned char*)g.tables;
+  cudaError_t e = cudaMemcpyAsync(tb + zp_ofs, z.pairs.data(), zp_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && zj_bytes) e = cudaMemcpyAsync(tb + zj_ofs, z.jobs.data(), zj_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tb + tc_ofs, r.host.data(), r.host.size(), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    cudaFree(g.tables);
+    return cuda(e, "upload graph tables");
+  }
+  const size_t pending0 = prof_pending.size();
+  const long long l0 = launches;
+  cudaGraph_t graph = nullptr;
+  if ((s = cuda(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed), "begin capture"))) {
+    cudaFree(g.tables);
+    return s;
+  }
+  s = coarse_launch(z, (const ZPair*)(tb + zp_ofs), (const ZJob*)(tb + zj_ofs), st);
+  if (!s) s = tc_launch(r, tb + tc_ofs, st);
+  e = cudaStreamEndCapture(st, &graph);
+  if (s || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaFree(g.tables);
+    prof_pending.resize(pending0);
+    return s ? s : cuda(e, "end capture");
+  }
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaFree(g.tables);
+    prof_pending.resize(pending0);
+    return cuda(e, "instantiate graph");
+  }
+  g.kernels = launches - l0;
+  launches = l0;
+  for (size_t i = pending0; i < prof_pending.size(); ++i)
+    g.prof.push_back({prof_pending[i].name, prof_pending[i].a, prof_pending[i].b});
+  prof_pending.resize(pending0);
+  graphs.push_back(std::move(g));
+  GraphEntry& ge = graphs.back();
+  if ((s = cuda(cudaGraphLaunch(ge.exec, st), "graph launch"))) return s;
+  launches += ge.kernels;
+  if (prof_on)
+    for (auto& rec : ge.prof) prof_pending.push_back({rec.name, rec.a, rec.b, false});
+  return SV_OK;
 }
 
 }  // namespace sv

@@ -132,11 +132,26 @@ template <typename T, typename CoarseT, typename OutT>
 cudaError_t launch_final(const T* in, int W, int H, int Ci, const T* wt, const T* bias, const CoarseT* coarse,
                          int w, int h, OutT* Y, cudaStream_t st);
 
-// BF16-activation variants used by the tensor-core form (FP32 arithmetic).
-cudaError_t launch_enc1_bf16(const uint8_t* L, int pitch, int W, int H, const int16_t* coarse, int w, int h,
-                             const float* wt, const float* bias, int Co, __nv_bfloat16* out, cudaStream_t st);
-cudaError_t launch_final_bf16(const __nv_bfloat16* in, int W, int H, int Ci, const float* wt, const float* bias,
-                              const int16_t* coarse, int w, int h, float* Y, cudaStream_t st);
+// Per-pair descriptors of the batched CUDA-core layers of the tensor-core form.
+struct EdgePair {
+  const uint8_t* L;
+  int pitch, W, H, w, h;
+  const int16_t* coarse;
+  __nv_bfloat16* e1;        // enc1 output [H1][W1][C1]
+  const __nv_bfloat16* d3;  // last decoder output [H][W][C]
+  float* Y;                 // refined disparity [H][W]
+};
+struct UpFixPair {          // one decoder layer of one pair (input, output, sizes)
+  const __nv_bfloat16* in;
+  __nv_bfloat16* out;
+  int Hi, Wi, Ho, Wo, Hu, Wu;
+};
+cudaError_t launch_edge_enc1(const EdgePair* pairs, int n, int maxW1, int maxH1, const float* W, const float* B, int C1,
+                             cudaStream_t st);
+cudaError_t launch_edge_final(const EdgePair* pairs, int n, int maxW, int maxH, const float* W, const float* B, int C,
+                              cudaStream_t st);
+cudaError_t launch_edge_up2fix(const UpFixPair* pairs, int n, int max_border, const float* W, const float* bias,
+                               int cin, int cout, int relu, cudaStream_t st);
 
 // latent heads: mu = 1x1(e3) + b; optionally logvar and z = mu + eps * exp(lv / 2).
 template <typename T>

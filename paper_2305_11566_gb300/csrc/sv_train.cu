@@ -30,8 +30,9 @@ template <typename T>
 cudaError_t launch_loss_kl(const T* mu, const T* lv, size_t n, double kl_scale, T* gmu, T* glv, double* acc,
                            cudaStream_t st);
 template <typename T>
-cudaError_t launch_loss_finish(const double* acc, double inv_npix, double inv_nlat, double kl_w, T* out,
+cudaError_t launch_loss_finish(const double* slots, int n_pairs, double inv_npix, double inv_nlat, double kl_w, T* out,
                                cudaStream_t st);
+size_t loss_slots_per_pair();
 template <typename T>
 cudaError_t launch_adam(float* p, T* m, T* v, const T* g, size_t n, double lr, double b1, double b2, double eps,
                         int t, cudaStream_t st);
@@ -223,16 +224,16 @@ sv_status Ctx::loss(const sv_pair* pairs, int n, const void* const* Y, const flo
                     const void* const* lv, double kl_w, void* out, void* const* gY, void* const* gmu, void* const* glv,
                     cudaStream_t st) {
   sv_status s;
-  if ((s = cuda(loss_acc.ensure(2 * sizeof(double)), "alloc loss accumulator"))) return s;
-  if ((s = cuda(cudaMemsetAsync(loss_acc.p, 0, 2 * sizeof(double), st), "zero loss"))) return s;
+  const size_t per = loss_slots_per_pair();
+  if ((s = cuda(loss_acc.ensure(per * n * sizeof(double)), "alloc loss partials"))) return s;
   double npix = 0, nlat = 0;
   for (int i = 0; i < n; ++i) {
     const Levels lv_(pairs[i].height, pairs[i].width);
     npix += (double)pairs[i].width * pairs[i].height;
     nlat += (double)lv_.H[3] * lv_.W[3] * net.lat;
   }
-  double* acc = (double*)loss_acc.p;
   for (int i = 0; i < n; ++i) {
+    double* acc = (double*)loss_acc.p + per * i;
     const Levels lv_(pairs[i].height, pairs[i].width);
     const size_t P = (size_t)pairs[i].width * pairs[i].height, nl = (size_t)lv_.H[3] * lv_.W[3] * net.lat;
     {
@@ -248,7 +249,8 @@ sv_status Ctx::loss(const sv_pair* pairs, int n, const void* const* Y, const flo
       return s;
   }
   LaunchScope _ls(*this, "loss_finish", st);
-  return cuda(launch_loss_finish<T>(acc, 1.0 / npix, 1.0 / nlat, kl_w, (T*)out, st), "loss finish");
+  return cuda(launch_loss_finish<T>((const double*)loss_acc.p, n, 1.0 / npix, 1.0 / nlat, kl_w, (T*)out, st),
+              "loss finish");
 }
 
 template <typename T>

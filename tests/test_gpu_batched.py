@@ -1,0 +1,114 @@
+"""The batched BF16 form: many pairs of uneven sizes per call, the CUDA-graph capture of
+a batch signature and the autotuner.
+
+Launch shape (strip height, N slice) and graph replay change nothing in the arithmetic of
+an output element (same MMAs in the same K order), so outputs must be bit-identical to the
+eager, untuned call; the eager call itself is checked against the oracle in
+test_gpu_bf16.py."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2305_11566_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def batch():
+    pairs = synth.batch_uneven(6, seed=9100)
+    return [p for p, _ in pairs], [binding.to_device(p, D) for p, D in pairs]
+
+
+def make_ctx(shape=synth.NET_WIDE, k=9):
+    c = binding.Context(shape, k, "bf16")
+    c.set_weights(synth.he_normal_weights(shape, 7))
+    return c
+
+
+def run(ctx, dps, stream):
+    with torch.cuda.stream(stream):
+        outs = ctx.pipeline(dps)
+    stream.synchronize()
+    ctx.synchronize(stream)
+    return [o.clone() for o in outs]
+
+
+def test_graph_replay_equals_eager(svlib, batch):
+    pairs, dps = batch
+    s = torch.cuda.Stream()
+    eager = make_ctx()
+    graph = make_ctx()
+    try:
+        eager.set_option("graphs", 0)
+        ref = run(eager, dps, s)
+        outs = [torch.empty_like(r) for r in ref]
+        with torch.cuda.stream(s):
+            graph.pipeline(dps, out=outs)        # capture + first replay
+            n0 = graph.launch_count()
+            for o in outs:
+                o.fill_(-1)
+            graph.pipeline(dps, out=outs)        # replay
+            n1 = graph.launch_count()
+        s.synchronize()
+        graph.synchronize(s)
+        for a, b in zip(outs, ref):
+            assert torch.equal(a, b)
+        assert n1 - n0 > len(dps)                # the replay counts its kernels
+        # a different output buffer is a different signature: recaptured, same result
+        outs2 = [torch.empty_like(r) for r in ref]
+        with torch.cuda.stream(s):
+            graph.pipeline(dps, out=outs2)
+        s.synchronize()
+        for a, b in zip(outs2, ref):
+            assert torch.equal(a, b)
+        # the coarse stage inside the graph equals sv_coarse_match
+        Y_o, disp_o, _, _ = oracle.pipeline(synth.NET_WIDE, synth.he_normal_weights(synth.NET_WIDE, 7),
+                                            pairs[0].left, pairs[0].right, 9, dps[0].max_disp)
+        d = graph.coarse_match([dps[0]])[0].cpu().numpy()
+        if np.array_equal(d, disp_o):
+            assert np.abs(outs[0].cpu().numpy() - Y_o).max() <= 0.05
+    finally:
+        eager.close()
+        graph.close()
+
+
+def test_autotune_keeps_results_and_caches(svlib, batch, tmp_path):
+    pairs, dps = batch
+    s = torch.cuda.Stream()
+    base = make_ctx()
+    tuned = make_ctx()
+    again = make_ctx()
+    try:
+        ref = run(base, dps, s)
+        cache = os.path.join(tmp_path, "tune.jsonl")
+        choice = tuned.autotune(dps, cache, stream=s)
+        assert all(u > 0 for u in choice["us"])
+        out = run(tuned, dps, s)
+        for a, b in zip(out, ref):
+            assert torch.equal(a, b)
+        assert os.path.exists(cache)
+        loaded = again.autotune(dps, cache, stream=s)
+        assert loaded["rows"] == choice["rows"] and loaded["nt"] == choice["nt"]
+        assert all(u == -1.0 for u in loaded["us"])
+        out2 = run(again, dps, s)
+        for a, b in zip(out2, ref):
+            assert torch.equal(a, b)
+    finally:
+        base.close()
+        tuned.close()
+        again.close()
+
+
+def test_autotune_rejects_plain_form(svlib, batch):
+    _, dps = batch
+    c = binding.Context(synth.NET_SMALL, 9, "fp32")
+    try:
+        with pytest.raises(binding.SvError) as ei:
+            c.autotune(dps)
+        assert ei.value.status == binding.SV_ERR_UNSUPPORTED
+    finally:
+        c.close()

@@ -5,8 +5,9 @@ FP64 (SV_FP64_CHECK) on a 64x32 crop: loss equal to the oracle's to 1e-12, the a
 gradient equal to the oracle's hand-derived gradient to 1e-9 (relative to the largest
 entry), and to central finite differences of the GPU's own FP64 loss within 1e-6
 relative (coarse-map entries: the loss is piecewise quadratic in them; parameters:
-two-step extrapolated differences, entries whose two step sizes disagree -- a ReLU
-kink inside the step -- are skipped and counted).  FP32: gradient within 1e-4 of the
+two-step extrapolated differences on entries whose gradient is at least 1e-3 of the
+largest, where FP64 roundoff of the loss cannot reach 1e-6; entries whose two step sizes
+disagree -- a ReLU kink inside the step -- are skipped and counted).  FP32: gradient within 1e-4 of the
 oracle's (relative to each layer's largest entry), one Adam step within 1e-6."""
 import numpy as np
 import pytest
@@ -67,55 +68,75 @@ def test_fp64_gradient_equals_oracle(fp64):
 
 
 def test_fp64_gradient_matches_finite_differences(fp64):
+    """Central differences of the GPU's own FP64 loss.  The ground truth is the oracle's
+    prediction plus 0.05 px noise, so the loss (~1e-3) and its FP64 roundoff are small and
+    tiny steps (~1e-6) resolve the derivative; a ReLU kink inside a step shows as
+    disagreement between steps h and h/2 and the entry is skipped (and counted)."""
     ctx, shape, params, p, coarse, eps, k, D = fp64
     dp = binding.to_device(p, D)
-    _, g, gc = gpu_loss_grad(ctx, dp, coarse, eps, p.gt, torch.float64)
+    H, W = p.left.shape
+    Yo = oracle.refine_forward(shape, params, p.left, coarse, eps)["Y"]
+    noise = np.random.default_rng(5).normal(scale=0.05, size=Yo.shape)
+    gt = (Yo + noise).astype(np.float32)
+    _, g, gc = gpu_loss_grad(ctx, dp, coarse, eps, gt, torch.float64)
 
     def L(par=None, c=None):
         if par is not None:
             ctx.set_weights(par)
-        out = gpu_loss_grad(ctx, dp, coarse if c is None else c, eps, p.gt, torch.float64, want_coarse=False)[0][0]
-        return out
+        return gpu_loss_grad(ctx, dp, coarse if c is None else c, eps, gt, torch.float64, want_coarse=False)[0][0]
 
-    # coarse map: piecewise quadratic in each entry, central differences are exact away from kinks
+    skips = []
+
+    def check(fd_pair, gi):
+        (d1, d2) = fd_pair
+        if abs(d1 - d2) > 3e-7 * abs(gi):
+            skips.append((d1, d2, gi))
+            return None  # kink inside the step
+        return abs(d2 - gi) / abs(gi)
+
     rng = np.random.default_rng(1)
-    h = 1e-5
+    results, skipped = [], 0
+    # coarse map entries (FP64 inputs)
     for (y, x) in [(1, 1), (3, 7), (7, 15), (0, 15), (4, 0)]:
-        cp = coarse.copy(); cp[y, x] += h
-        cm = coarse.copy(); cm[y, x] -= h
-        fd = (L(c=cp) - L(c=cm)) / (2 * h)
-        assert abs(fd - gc[y, x]) <= 1e-6 * abs(gc[y, x]) + 1e-12, (y, x, fd, gc[y, x])
-    # parameters: FP32 perturbations (the library's master copy is FP32), two step sizes,
-    # second-order error eliminated; a kink inside the step shows as disagreement
+        ests = []
+        for h in (2e-6, 1e-6):
+            cp = coarse.copy(); cp[y, x] += h
+            cm = coarse.copy(); cm[y, x] -= h
+            ests.append((L(c=cp) - L(c=cm)) / (2 * h))
+        r = check(ests, gc[y, x])
+        if r is None:
+            skipped += 1
+        else:
+            results.append(r)
+    # parameters (FP32 master copy: the actual step is taken from the FP32 values)
     sl = oracle.param_slices(shape)
+    gmax = np.abs(g).max()
     idx = []
     for name, (ow, wshape, ob, co) in sl.items():
         n = int(np.prod(wshape))
-        idx += list(ow + rng.choice(n, size=3, replace=False)) + [ob + int(rng.integers(co))]
-    checked, skipped, worst = 0, 0, 0.0
+        cand = np.concatenate([np.arange(ow, ow + n), np.arange(ob, ob + co)])
+        cand = cand[np.abs(g[cand]) >= 1e-3 * gmax]
+        if cand.size:
+            idx += list(rng.choice(cand, size=min(4, cand.size), replace=False))
     try:
         for i in idx:
-            if abs(g[i]) < 1e-8:
-                continue
             ests = []
-            for rel in (2.0 ** -9, 2.0 ** -11):
-                base = params[i]
+            base = params[i]
+            for rel in (2.0 ** -16, 2.0 ** -17):
                 hh = np.float32(max(abs(base), 1e-2) * rel)
                 pp = params.copy(); pp[i] = base + hh
                 pm = params.copy(); pm[i] = base - hh
-                s = float(np.float64(pp[i]) - np.float64(pm[i])) / 2
-                ests.append(((L(par=pp) - L(par=pm)) / (2 * s), s))
-            (d1, s1), (d2, s2) = ests
-            rich = (s1 ** 2 * d2 - s2 ** 2 * d1) / (s1 ** 2 - s2 ** 2)
-            if abs(d1 - d2) > 1e-3 * abs(g[i]):  # a ReLU kink inside the larger step
+                step = float(np.float64(pp[i]) - np.float64(pm[i]))
+                ests.append((L(par=pp) - L(par=pm)) / step)
+            r = check(ests, g[i])
+            if r is None:
                 skipped += 1
-                continue
-            checked += 1
-            worst = max(worst, abs(rich - g[i]) / abs(g[i]))
+            else:
+                results.append(r)
     finally:
         ctx.set_weights(params)
-    assert checked >= 0.6 * (checked + skipped)
-    assert worst <= 1e-6, worst
+    assert len(results) >= 0.6 * (len(results) + skipped), (len(results), skips)
+    assert max(results) <= 1e-6, max(results)
 
 
 def test_fp32_gradient_and_adam_match_oracle(svlib):
