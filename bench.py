@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=2, help="pairs timed on the CPU oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
+    ap.add_argument("--train-pairs", type=int, default=16)
     return ap.parse_args()
 
 
@@ -368,6 +370,53 @@ def run_ours(args):
                               "epe_gpu_vs_gt_px": float(np.mean(epe_g)), "epe_oracle_vs_gt_px": float(np.mean(epe_o)),
                               "delta_epe_px": float(np.mean(epe_g) - np.mean(epe_o)), "pairs": n}
 
+    # -------------------------------------------------------------- training step (differentiation form)
+    train = None
+    if not args.no_train and "bf16" in results:
+        from paper_2305_11566_gb300 import autograd as sv_autograd
+        tshape = synth.NET_SMALL
+        tctx = binding.Context(tshape, WIN, "bf16", dev)
+        tctx.set_weights(synth.he_normal_weights(tshape, 7))
+        nt = args.train_pairs
+        tp = [distinct[i % len(distinct)] for i in range(nt)]
+        tdp = [dps_distinct[i % len(distinct)] for i in range(nt)]
+        H3, W3 = binding.latent_hw(H, W)
+        tco = [torch.from_numpy(np.full((H // 4, W // 4), 10.0, np.float32)).cuda() for _ in range(nt)]
+        with torch.cuda.stream(st):
+            coarse_i = tctx.coarse_match(tdp)
+        st.synchronize()
+        tco = [c.float() for c in coarse_i]
+        teps = [torch.from_numpy(synth.reparam_noise(H3 * W3 * tshape.latent, 3000 + i)).cuda().reshape(H3, W3, -1)
+                for i in range(nt)]
+        tgt = [torch.from_numpy(p.gt).cuda() for p in tp]
+        wt = torch.from_numpy(synth.he_normal_weights(tshape, 7)).cuda().requires_grad_(True)
+
+        def train_step(t):
+            Yt, mut, lvt = sv_autograd.refine(tctx, tdp, tco, teps, wt)
+            Lt = sv_autograd.loss(tctx, tdp, Yt, tgt, mut, lvt)
+            wt.grad = None
+            Lt.backward()
+            tctx.adam_step(wt.grad, t)
+            return Lt
+
+        with torch.cuda.stream(st):
+            for t in range(1, 3):
+                train_step(t)
+            st.synchronize()
+            tsteps = 3
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for t in range(3, 3 + tsteps):
+                Lt = train_step(t)
+            e1.record(st)
+            st.synchronize()
+        tms = e0.elapsed_time(e1) / tsteps
+        train = {"workload": f"training step: {nt} synthetic 1242x375 pairs, 16/32/64 net, BF16 tensor-core forward, "
+                             "FP32 master weights and backward (encoder recomputed), smooth-L1 + 1e-3 KL, Adam",
+                 "ms_per_step": tms, "steps_per_s": 1e3 / tms, "pairs_per_s": nt * 1e3 / tms,
+                 "loss_last": float(Lt.item())}
+        tctx.close()
+
     value = B * world / (R["ms_per_step"] / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
@@ -389,6 +438,7 @@ def run_ours(args):
                   for f, r in results.items()},
         "delta_epe_px": accuracy.get(head, {}).get("delta_epe_px"),
         "tuning": tuning,
+        "train_step": train,
     }
     if rank == 0:
         print(json.dumps(line))

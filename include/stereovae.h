@@ -140,7 +140,9 @@ SV_API sv_status sv_pipeline(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, flo
 /* Training forward of n_pairs pairs: z = mu + eps * exp(logvar / 2) (the
  * reparameterisation of Eq. 8 in its standard form).  Saves in the context what
  * sv_refine_backward needs (decoder activations and the latent; the encoder is
- * recomputed there).  Element type of coarse, eps, disp_out, mu_out and logvar_out
+ * recomputed there).  On SV_BF16 contexts the encoder and decoder convolutions run on
+ * the tensor cores (BF16 operands, FP32 accumulation, FP32 master weights) and the
+ * backward runs in FP32; SV_FP32 runs FP32 throughout, SV_FP64_CHECK FP64.  Element type of coarse, eps, disp_out, mu_out and logvar_out
  * is float for SV_FP32 / SV_BF16 contexts and double for SV_FP64_CHECK contexts.
  * coarse[i]: (H/4) x (W/4) real-valued coarse map; eps[i], mu_out[i], logvar_out[i]:
  * latent tensors [H3][W3][latent_ch] with H3 = ceil(ceil(ceil(H/2)/2)/2) (same for W3);

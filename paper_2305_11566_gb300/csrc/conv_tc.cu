@@ -553,6 +553,23 @@ static bool make_tmap(CUtensorMap* m, const __nv_bfloat16* base, int C, int npix
          CUDA_SUCCESS;
 }
 
+// BF16 copies of the decoder weights in their canonical [co][3][3][ci] order (border fix),
+// stored after the packed GEMM operands; returns their offsets.
+static size_t unfolded_offsets(const NetDims& net, size_t packed_total, size_t ofs[3]) {
+  size_t o = (packed_total + 7) / 8 * 8;
+  const int layers[3] = {L_DEC1, L_DEC2, L_DEC3};
+  for (int k = 0; k < 3; ++k) {
+    ofs[k] = o;
+    o += ((size_t)net.cout(layers[k]) * 9 * net.cin(layers[k]) + 7) / 8 * 8;
+  }
+  return o;
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16_rn(a[i]);
+}
+
 static void plan_layers(const NetDims& net, std::vector<TcLayerPlan>& plans, size_t& total) {
   plans.clear();
   total = 0;
@@ -592,8 +609,18 @@ sv_status Ctx::pack_bf16_weights(cudaStream_t st) {
   std::vector<TcLayerPlan> plans;
   size_t total;
   plan_layers(net, plans, total);
-  sv_status s = cuda(wbf.ensure(total * sizeof(__nv_bfloat16)), "alloc packed weights");
+  size_t unf[3];
+  const size_t all = unfolded_offsets(net, total, unf);
+  sv_status s = cuda(wbf.ensure(all * sizeof(__nv_bfloat16)), "alloc packed weights");
   if (s) return s;
+  const int dl[3] = {L_DEC1, L_DEC2, L_DEC3};
+  for (int k = 0; k < 3; ++k) {
+    const size_t n = (size_t)net.cout(dl[k]) * 9 * net.cin(dl[k]);
+    LaunchScope ls(*this, "pack_bf16", st);
+    to_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const float*)w32.p + net.w_off(dl[k]),
+                                                                (__nv_bfloat16*)wbf.p + unf[k], n);
+    if ((s = cuda(cudaGetLastError(), "unfolded weights"))) return s;
+  }
   for (auto& pl : plans) {
     const size_t n = (size_t)pl.G * tc::taps(pl.mode) * pl.NT * pl.cin;
     LaunchScope ls(*this, "pack_bf16", st);
@@ -607,7 +634,8 @@ sv_status Ctx::pack_bf16_weights(cudaStream_t st) {
 // Host side of one tensor-core refinement call: activation workspaces (allocated here),
 // per-layer descriptor and strip tables (built here, uploaded by the caller) and launch
 // geometry.  Nothing is enqueued on a stream.
-sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out, TcRun& r) {
+sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out, TcRun& r,
+                          const float* const* coarse_f) {
   using tc::LayerPair;
   using tc::Strip;
   size_t wtotal;
@@ -718,7 +746,8 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
   r.maxW = r.maxH = r.maxW1 = r.maxH1 = 0;
   for (int i = 0; i < n; ++i) {
     const sv_pair& p = pairs[i];
-    eps_[i] = {p.left, p.pitch, p.width, p.height, p.width / 4, p.height / 4, coarse[i], act(0, i), act(6, i), out[i]};
+    eps_[i] = {p.left, p.pitch, p.width, p.height, p.width / 4, p.height / 4, coarse ? coarse[i] : nullptr,
+               coarse_f ? coarse_f[i] : nullptr, act(0, i), act(6, i), out[i]};
     r.maxW = std::max(r.maxW, p.width);
     r.maxH = std::max(r.maxH, p.height);
     r.maxW1 = std::max(r.maxW1, lv[i].W[1]);
@@ -731,7 +760,7 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
 
 // Kernel launches of a prepared call; `tables` holds r.host on the device.  Only kernel
 // launches: safe inside a stream capture.
-sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream_t st) {
+sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream_t st, const TcTrainLatent* tl) {
   using tc::LayerPair;
   using tc::Strip;
   sv_status s;
@@ -760,14 +789,31 @@ sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream
     prm.ring = pl.ring;
     prm.err = (int*)err_flag.p;
     prm.spin = spin_limit;
+    if (tl && pl.layer == L_MU) {
+      // training: mu, logvar and the reparameterised z instead of z = mu
+      for (int i = 0; i < r.n; ++i) {
+        LaunchScope ls(*this, "train_latent", st);
+        if ((s = cuda(launch_train_latent_bf16(tl->e3[i], tl->P3[i], net.enc[2], W + net.w_off(L_MU), W + net.b_off(L_MU),
+                                               W + net.w_off(L_LV), W + net.b_off(L_LV), net.lat, tl->eps[i], tl->mu[i],
+                                               tl->lv[i], tl->z[i], st),
+                      "train latent")))
+          return s;
+      }
+      continue;
+    }
     {
       LaunchScope ls(*this, names[li], st);
       if ((s = cuda(tc::launch_conv(pl.mode, prm, pl.NT, r.tabs[li].grid, pl.smem, st), names[li]))) return s;
     }
     if (pl.mode == tc::TM_UP2 && r.tabs[li].max_border > 0) {
       LaunchScope ls(*this, "edge_up2fix", st);
+      size_t unf[3], wtot;
+      std::vector<TcLayerPlan> tmp;
+      plan_layers(net, tmp, wtot);
+      unfolded_offsets(net, wtot, unf);
+      const int dk = pl.layer == L_DEC1 ? 0 : pl.layer == L_DEC2 ? 1 : 2;
       if ((s = cuda(launch_edge_up2fix((const UpFixPair*)(tables + r.tabs[li].fix_ofs), r.n, r.tabs[li].max_border,
-                                       W + net.w_off(pl.layer),
+                                       (const __nv_bfloat16*)wbf.p + unf[dk],
                                        prm.bias, pl.cin, pl.cout, 1, st),
                     "border fix")))
         return s;

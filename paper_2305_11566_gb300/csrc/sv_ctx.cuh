@@ -48,6 +48,15 @@ struct ZRun {
   int maxD = 1;
 };
 
+// Per-pair buffers of the training latent of the tensor-core form.
+struct TcTrainLatent {
+  std::vector<const __nv_bfloat16*> e3;
+  std::vector<int> P3;
+  std::vector<const float*> eps;
+  std::vector<float*> mu, lv;
+  std::vector<__nv_bfloat16*> z;
+};
+
 // One captured batched step (coarse match + tensor-core refinement) and what it needs.
 struct GraphEntry {
   std::vector<uint64_t> key;
@@ -75,7 +84,7 @@ struct Ctx {
   int adam_elem = 0;
   DevBuf adam_m, adam_v;
   // differentiation form: state saved by the last training forward
-  DevBuf train_saved, train_scratch, loss_acc;
+  DevBuf train_saved, train_scratch, loss_acc, train_mu;
   std::vector<sv_pair> train_pairs;
   std::vector<const void*> train_coarse;
   std::vector<size_t> train_off;
@@ -140,8 +149,11 @@ struct Ctx {
   template <typename T>
   sv_status adam(const T* g, int step, double lr, double b1, double b2, double eps, cudaStream_t st);
   sv_status refine_tc(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out, cudaStream_t st);
-  sv_status tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out, TcRun& r);
-  sv_status tc_launch(const TcRun& r, const unsigned char* tables, cudaStream_t st);
+  sv_status tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out, TcRun& r,
+                       const float* const* coarse_f = nullptr);
+  sv_status tc_launch(const TcRun& r, const unsigned char* tables, cudaStream_t st, const TcTrainLatent* tl = nullptr);
+  sv_status train_forward_bf16(const sv_pair* pairs, const void* const* coarse, const void* const* eps, int n,
+                               void* const* Y, void* const* mu, void* const* lv, cudaStream_t st);
   void coarse_prepare(const sv_pair* pairs, int n, int16_t* const* disp, float* const* best, float* const* second,
                       ZRun& z);
   sv_status coarse_launch(const ZRun& z, const ZPair* d_pairs, const ZJob* d_jobs, cudaStream_t st);
@@ -183,7 +195,7 @@ struct Ctx {
     for (auto& b : act) b.release();
     for (auto& b : tc_act) b.release();
     tc_tables.release(); adam_m.release(); adam_v.release();
-    train_saved.release(); train_scratch.release(); loss_acc.release();
+    train_saved.release(); train_scratch.release(); loss_acc.release(); train_mu.release();
   }
 };
 

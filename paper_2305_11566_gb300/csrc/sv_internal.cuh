@@ -136,7 +136,8 @@ cudaError_t launch_final(const T* in, int W, int H, int Ci, const T* wt, const T
 struct EdgePair {
   const uint8_t* L;
   int pitch, W, H, w, h;
-  const int16_t* coarse;
+  const int16_t* coarse;    // integer coarse map (inference), or
+  const float* coarse_f;    // real-valued coarse map (training) when non-null
   __nv_bfloat16* e1;        // enc1 output [H1][W1][C1]
   const __nv_bfloat16* d3;  // last decoder output [H][W][C]
   float* Y;                 // refined disparity [H][W]
@@ -150,8 +151,15 @@ cudaError_t launch_edge_enc1(const EdgePair* pairs, int n, int maxW1, int maxH1,
                              cudaStream_t st);
 cudaError_t launch_edge_final(const EdgePair* pairs, int n, int maxW, int maxH, const float* W, const float* B, int C,
                               cudaStream_t st);
-cudaError_t launch_edge_up2fix(const UpFixPair* pairs, int n, int max_border, const float* W, const float* bias,
-                               int cin, int cout, int relu, cudaStream_t st);
+cudaError_t launch_edge_up2fix(const UpFixPair* pairs, int n, int max_border, const __nv_bfloat16* Wb,
+                               const float* bias, int cin, int cout, int relu, cudaStream_t st);
+
+// Training latent of the tensor-core form: mu, logvar (FP32, caller's buffers) from BF16
+// e3 with FP32 weights, z = mu + eps exp(logvar / 2) stored as BF16 for the decoder.
+cudaError_t launch_train_latent_bf16(const __nv_bfloat16* e3, int P, int Ci, const float* wmu, const float* bmu,
+                                     const float* wlv, const float* blv, int lat, const float* eps, float* mu,
+                                     float* lv, __nv_bfloat16* z, cudaStream_t st);
+cudaError_t launch_bf16_to_f32(const __nv_bfloat16* a, float* b, size_t n, cudaStream_t st);
 
 // latent heads: mu = 1x1(e3) + b; optionally logvar and z = mu + eps * exp(lv / 2).
 template <typename T>

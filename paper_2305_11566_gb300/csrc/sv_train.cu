@@ -97,6 +97,80 @@ sv_status Ctx::train_forward(const sv_pair* pairs, const void* const* coarse, co
   return SV_OK;
 }
 
+// Training forward of the BF16 form: the tensor-core encoder and decoder (BF16 operands,
+// FP32 accumulation), the training latent in FP32 on CUDA cores, the final conv in FP32.
+// The decoder activations and the latent are saved as FP32 for the FP32 backward.
+sv_status Ctx::train_forward_bf16(const sv_pair* pairs, const void* const* coarse, const void* const* eps, int n,
+                                  void* const* Y, void* const* mu, void* const* lv, cudaStream_t st) {
+  using T = float;
+  sv_status s;
+  std::vector<size_t> off(n + 1, 0);
+  size_t lat_total = 0;
+  for (int i = 0; i < n; ++i) {
+    size_t sz[S_COUNT];
+    off[i + 1] = off[i] + saved_sizes<T>(net, Levels(pairs[i].height, pairs[i].width), sz);
+    lat_total += (sz[S_LV] + 1) / 2 * 2;
+  }
+  if ((s = cuda(train_saved.ensure(std::max<size_t>(off[n], 2) * sizeof(T)), "alloc saved activations"))) return s;
+  if ((s = cuda(train_mu.ensure(std::max<size_t>(lat_total, 2) * sizeof(T)), "alloc latent scratch"))) return s;
+  train_pairs.assign(pairs, pairs + n);
+  train_coarse.assign(coarse, coarse + n);
+  train_off = off;
+  train_elem = sizeof(T);
+  std::vector<float*> outs(n);
+  for (int i = 0; i < n; ++i) outs[i] = (float*)Y[i];
+  TcRun r;
+  if ((s = tc_prepare(pairs, nullptr, n, outs.data(), r, (const float* const*)coarse))) return s;
+  if ((s = cuda(tc_tables.ensure(r.host.size()), "alloc tables"))) return s;
+  if ((s = cuda(cudaMemcpyAsync(tc_tables.p, r.host.data(), r.host.size(), cudaMemcpyHostToDevice, st),
+                "upload tables")))
+    return s;
+  TcTrainLatent tl;
+  std::vector<T*> svb(n * S_COUNT);
+  size_t mo = 0;
+  for (int i = 0; i < n; ++i) {
+    const Levels lv_(pairs[i].height, pairs[i].width);
+    size_t sz[S_COUNT];
+    saved_sizes<T>(net, lv_, sz);
+    T* base = (T*)train_saved.p + off[i];
+    for (int k = 0; k < S_COUNT; ++k) {
+      svb[i * S_COUNT + k] = base;
+      base += (sz[k] + 1) / 2 * 2;
+    }
+    tl.e3.push_back((const __nv_bfloat16*)tc_act[2].p + tc_off[i][2]);
+    tl.P3.push_back(lv_.H[3] * lv_.W[3]);
+    tl.eps.push_back((const float*)eps[i]);
+    float* m = mu && mu[i] ? (float*)mu[i] : (float*)train_mu.p + mo;
+    mo += (sz[S_LV] + 1) / 2 * 2;
+    tl.mu.push_back(m);
+    tl.lv.push_back(svb[i * S_COUNT + S_LV]);
+    tl.z.push_back((__nv_bfloat16*)tc_act[3].p + tc_off[i][3]);
+  }
+  if ((s = tc_launch(r, (const unsigned char*)tc_tables.p, st, &tl))) return s;
+  for (int i = 0; i < n; ++i) {
+    const int acts[4] = {3, 4, 5, 6};
+    const int slots[4] = {S_Z, S_D1, S_D2, S_D3};
+    for (int k = 0; k < 4; ++k) {
+      LaunchScope _ls(*this, "save_bf16_to_f32", st);
+      if ((s = cuda(launch_bf16_to_f32((const __nv_bfloat16*)tc_act[acts[k]].p + tc_off[i][acts[k]],
+                                       svb[i * S_COUNT + slots[k]], tc_len[i][acts[k]], st),
+                    "save activations")))
+        return s;
+    }
+    size_t sz[S_COUNT];
+    saved_sizes<T>(net, Levels(pairs[i].height, pairs[i].width), sz);
+    if (lv && lv[i] &&
+        (s = cuda(cudaMemcpyAsync(lv[i], svb[i * S_COUNT + S_LV], sz[S_LV] * sizeof(T), cudaMemcpyDeviceToDevice, st),
+                  "copy logvar")))
+      return s;
+    if ((s = cuda(cudaMemcpyAsync(svb[i * S_COUNT + S_EPS], eps[i], sz[S_EPS] * sizeof(T), cudaMemcpyDeviceToDevice, st),
+                  "copy eps")))
+      return s;
+  }
+  train_ready = true;
+  return SV_OK;
+}
+
 template <typename T>
 sv_status Ctx::train_backward(const void* const* gY, const void* const* gmu_ext, const void* const* glv_ext, T* gparams,
                               void* const* gcoarse, cudaStream_t st) {
@@ -303,6 +377,8 @@ sv_status sv_refine_train(sv_ctx* ctx, const sv_pair* pairs, const void* const* 
   c->train_ready = false;
   if (c->cfg.precision == SV_FP64_CHECK)
     return c->train_forward<double>(pairs, coarse, eps, n_pairs, disp_out, mu_out, logvar_out, (cudaStream_t)stream);
+  if (c->cfg.precision == SV_BF16)
+    return c->train_forward_bf16(pairs, coarse, eps, n_pairs, disp_out, mu_out, logvar_out, (cudaStream_t)stream);
   return c->train_forward<float>(pairs, coarse, eps, n_pairs, disp_out, mu_out, logvar_out, (cudaStream_t)stream);
 }
 

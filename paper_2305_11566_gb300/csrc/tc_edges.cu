@@ -15,7 +15,8 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-__device__ __forceinline__ float upsample4_f(const int16_t* __restrict__ c, int w, int h, int X, int Y) {
+template <typename CT>
+__device__ __forceinline__ float upsample4_f(const CT* __restrict__ c, int w, int h, int X, int Y) {
   float sx = (float)X * 0.25f - 0.375f, sy = (float)Y * 0.25f - 0.375f;
   sx = fminf(fmaxf(sx, 0.f), (float)(w - 1));
   sy = fminf(fmaxf(sy, 0.f), (float)(h - 1));
@@ -52,7 +53,8 @@ __global__ void __launch_bounds__(256) edge_enc1(const EdgePair* __restrict__ pa
     float l = 0.f, u = 0.f;
     if (vy >= 0 && vy < P.H && vx >= 0 && vx < P.W) {
       l = (float)P.L[(size_t)vy * P.pitch + vx] * (1.f / 256.f);
-      u = upsample4_f(P.coarse, P.w, P.h, vx, vy) * (1.f / 256.f);
+      u = (P.coarse_f ? upsample4_f(P.coarse_f, P.w, P.h, vx, vy) : upsample4_f(P.coarse, P.w, P.h, vx, vy)) *
+          (1.f / 256.f);
     }
     x0[r][c][0] = l;
     x0[r][c][1] = u;
@@ -94,14 +96,15 @@ __global__ void __launch_bounds__(256) edge_enc1(const EdgePair* __restrict__ pa
 
 // final: (ETH + 2) x (ETW + 2) x C BF16 tile in shared memory with an 80-byte-per-32-channel
 // pixel stride (conflict-free 16-byte reads), weights [9][C] FP32.
+template <int C>
 __global__ void __launch_bounds__(256) edge_final(const EdgePair* __restrict__ pairs, const float* __restrict__ W,
-                                                  const float* __restrict__ B, int C) {
+                                                  const float* __restrict__ B) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const EdgePair P = pairs[blockIdx.z];
   const int X0 = blockIdx.x * ETW, Y0 = blockIdx.y * ETH;
   if (X0 >= P.W || Y0 >= P.H) return;
-  const int cpx = C / 8;                 // 16-byte chunks per pixel
-  const int pstride = cpx + 1;           // padded pixel stride in chunks
+  constexpr int cpx = C / 8;             // 16-byte chunks per pixel
+  constexpr int pstride = cpx + 1;       // padded pixel stride in chunks
   uint4* tile = reinterpret_cast<uint4*>(fsm);
   float* ws = reinterpret_cast<float*>(fsm + sizeof(uint4) * (ETH + 2) * (ETW + 2) * pstride);
   const int tid = threadIdx.y * ETW + threadIdx.x;
@@ -125,6 +128,7 @@ __global__ void __launch_bounds__(256) edge_final(const EdgePair* __restrict__ p
     for (int kx = 0; kx < 3; ++kx) {
       const uint4* src = tile + ((threadIdx.y + ky) * (ETW + 2) + threadIdx.x + kx) * pstride;
       const float* wp = ws + (ky * 3 + kx) * C;
+#pragma unroll
       for (int q = 0; q < cpx; ++q) {
         const uint4 v = src[q];
         const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
@@ -136,56 +140,107 @@ __global__ void __launch_bounds__(256) edge_final(const EdgePair* __restrict__ p
         }
       }
     }
-  P.Y[(size_t)Y * P.W + X] = upsample4_f(P.coarse, P.w, P.h, X, Y) + acc;
+  const float U = P.coarse_f ? upsample4_f(P.coarse_f, P.w, P.h, X, Y) : upsample4_f(P.coarse, P.w, P.h, X, Y);
+  P.Y[(size_t)Y * P.W + X] = U + acc;
 }
 
-// Exact last row / column of a nearest-x2 + 3x3 conv with an odd output size, BF16-rounded
-// weights, FP32 accumulation.  One thread per (border pixel, output channel).
-__global__ void __launch_bounds__(256) edge_up2fix(const UpFixPair* __restrict__ pairs, const float* __restrict__ W,
+// Exact last row / column of a nearest-x2 + 3x3 conv with an odd output size.  One block
+// per border pixel: the block stages the pixel's 3x3 input neighbourhood (BF16) in shared
+// memory, thread t computes output channel t (and t + blockDim, ...) from the BF16-rounded
+// unfolded weights Wb[co][ky][kx][ci], FP32 accumulation, 8 independent 16-byte weight
+// loads in flight per thread.
+__global__ void __launch_bounds__(128) edge_up2fix(const UpFixPair* __restrict__ pairs, const bf16* __restrict__ Wb,
                                                    const float* __restrict__ bias, int cin, int cout, int relu) {
+  extern __shared__ __align__(16) uint4 patch[];  // [9][cin / 8]
   const UpFixPair L = pairs[blockIdx.y];
   const int nrow = (L.Ho & 1) ? L.Wo : 0;
   const int ncol = (L.Wo & 1) ? L.Ho : 0;
-  const int total = (nrow + ncol) * cout;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const int co = e % cout, pix = e / cout;
-    int Y, X;
-    if (pix < nrow) {
-      Y = L.Ho - 1;
-      X = pix;
-    } else {
-      Y = pix - nrow;
-      X = L.Wo - 1;
-    }
-    float acc = bias[co];
-    for (int ky = 0; ky < 3; ++ky) {
-      const int vy = Y + ky - 1;
-      if (vy < 0 || vy >= L.Ho) continue;
-      for (int kx = 0; kx < 3; ++kx) {
-        const int vx = X + kx - 1;
-        if (vx < 0 || vx >= L.Wo) continue;
-        const uint4* ip = reinterpret_cast<const uint4*>(L.in + ((size_t)(vy >> 1) * L.Wi + (vx >> 1)) * cin);
-        const float4* wp = reinterpret_cast<const float4*>(W + ((size_t)co * 9 + ky * 3 + kx) * cin);
-        for (int q = 0; q < cin / 8; ++q) {
-          const uint4 v = ip[q];
-          const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
-          const float4 wa = wp[2 * q], wb = wp[2 * q + 1];
-          const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+  const int pix = blockIdx.x;
+  if (pix >= nrow + ncol) return;
+  int Y, X;
+  if (pix < nrow) {
+    Y = L.Ho - 1;
+    X = pix;
+  } else {
+    Y = pix - nrow;
+    X = L.Wo - 1;
+  }
+  const int q8 = cin / 8, n = 9 * q8;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int t = e / q8, q = e - t * q8;
+    const int vy = Y + t / 3 - 1, vx = X + t % 3 - 1;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (vy >= 0 && vy < L.Ho && vx >= 0 && vx < L.Wo)
+      v = reinterpret_cast<const uint4*>(L.in + ((size_t)(vy >> 1) * L.Wi + (vx >> 1)) * cin)[q];
+    patch[e] = v;
+  }
+  __syncthreads();
+  for (int co = threadIdx.x; co < cout; co += blockDim.x) {
+    const uint4* wp = reinterpret_cast<const uint4*>(Wb + (size_t)co * 9 * cin);
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int e0 = 0; e0 < n; e0 += 8) {  // n = 9 * cin / 8 is a multiple of 8 (cin % 64 == 0) or handled below
+      uint4 w[8];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float2 f = __bfloat1622float2(h[j]);
-            acc = fmaf(__bfloat162float(__float2bfloat16_rn(wv[2 * j])), f.x, acc);
-            acc = fmaf(__bfloat162float(__float2bfloat16_rn(wv[2 * j + 1])), f.y, acc);
-          }
+      for (int u = 0; u < 8; ++u) w[u] = e0 + u < n ? wp[e0 + u] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (e0 + u >= n) break;
+        const uint4 x = patch[e0 + u];
+        const __nv_bfloat162* wh = reinterpret_cast<const __nv_bfloat162*>(&w[u]);
+        const __nv_bfloat162* xh = reinterpret_cast<const __nv_bfloat162*>(&x);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float2 wf = __bfloat1622float2(wh[j]), xf = __bfloat1622float2(xh[j]);
+          acc[u] = fmaf(wf.x, xf.x, acc[u]);
+          acc[u] = fmaf(wf.y, xf.y, acc[u]);
         }
       }
     }
-    if (relu) acc = fmaxf(acc, 0.f);
-    L.out[((size_t)Y * L.Wo + X) * cout + co] = __float2bfloat16_rn(acc);
+    float v = bias[co] + ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    if (relu) v = fmaxf(v, 0.f);
+    L.out[((size_t)Y * L.Wo + X) * cout + co] = __float2bfloat16_rn(v);
   }
 }
 
+// Training latent: one thread per (latent pixel, channel).
+__global__ void train_latent_bf16(const bf16* __restrict__ e3, int P, int Ci, const float* __restrict__ wmu,
+                                  const float* __restrict__ bmu, const float* __restrict__ wlv,
+                                  const float* __restrict__ blv, int lat, const float* __restrict__ eps,
+                                  float* __restrict__ mu, float* __restrict__ lv, bf16* __restrict__ z) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)P * lat) return;
+  const int co = (int)(i % lat);
+  const bf16* x = e3 + (i / lat) * Ci;
+  float m = bmu[co], l = blv[co];
+  for (int ci = 0; ci < Ci; ++ci) {
+    const float xv = __bfloat162float(x[ci]);
+    m = fmaf(wmu[(size_t)co * Ci + ci], xv, m);
+    l = fmaf(wlv[(size_t)co * Ci + ci], xv, l);
+  }
+  mu[i] = m;
+  lv[i] = l;
+  z[i] = __float2bfloat16_rn(m + eps[i] * expf(0.5f * l));
+}
+
+__global__ void bf16_to_f32(const bf16* __restrict__ a, float* __restrict__ b, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __bfloat162float(a[i]);
+}
+
 }  // namespace
+
+cudaError_t launch_train_latent_bf16(const bf16* e3, int P, int Ci, const float* wmu, const float* bmu,
+                                     const float* wlv, const float* blv, int lat, const float* eps, float* mu,
+                                     float* lv, bf16* z, cudaStream_t st) {
+  const size_t n = (size_t)P * lat;
+  train_latent_bf16<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e3, P, Ci, wmu, bmu, wlv, blv, lat, eps, mu, lv, z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bf16_to_f32(const bf16* a, float* b, size_t n, cudaStream_t st) {
+  bf16_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_edge_enc1(const EdgePair* pairs, int n, int maxW1, int maxH1, const float* W, const float* B, int C1,
                              cudaStream_t st) {
@@ -194,23 +249,37 @@ cudaError_t launch_edge_enc1(const EdgePair* pairs, int n, int maxW1, int maxH1,
   return cudaGetLastError();
 }
 
-cudaError_t launch_edge_final(const EdgePair* pairs, int n, int maxW, int maxH, const float* W, const float* B, int C,
-                              cudaStream_t st) {
+template <int C>
+static cudaError_t run_final(const EdgePair* pairs, int n, int maxW, int maxH, const float* W, const float* B,
+                             cudaStream_t st) {
   dim3 grid((maxW + ETW - 1) / ETW, (maxH + ETH - 1) / ETH, n);
   const size_t smem = sizeof(uint4) * (ETH + 2) * (ETW + 2) * (C / 8 + 1) + sizeof(float) * 9 * C;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(edge_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(edge_final<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  edge_final<<<grid, dim3(ETW, ETH), smem, st>>>(pairs, W, B, C);
+  edge_final<C><<<grid, dim3(ETW, ETH), smem, st>>>(pairs, W, B);
   return cudaGetLastError();
 }
 
-cudaError_t launch_edge_up2fix(const UpFixPair* pairs, int n, int max_border, const float* W, const float* bias,
+cudaError_t launch_edge_final(const EdgePair* pairs, int n, int maxW, int maxH, const float* W, const float* B, int C,
+                              cudaStream_t st) {
+  switch (C) {  // decoder widths are multiples of 16 up to 256
+#define SV_FINAL_CASE(c) \
+  case c: return run_final<c>(pairs, n, maxW, maxH, W, B, st);
+    SV_FINAL_CASE(16) SV_FINAL_CASE(32) SV_FINAL_CASE(48) SV_FINAL_CASE(64) SV_FINAL_CASE(80) SV_FINAL_CASE(96)
+    SV_FINAL_CASE(112) SV_FINAL_CASE(128) SV_FINAL_CASE(144) SV_FINAL_CASE(160) SV_FINAL_CASE(176) SV_FINAL_CASE(192)
+    SV_FINAL_CASE(208) SV_FINAL_CASE(224) SV_FINAL_CASE(240) SV_FINAL_CASE(256)
+#undef SV_FINAL_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_edge_up2fix(const UpFixPair* pairs, int n, int max_border, const bf16* Wb, const float* bias,
                                int cin, int cout, int relu, cudaStream_t st) {
-  const int total = max_border * cout;
-  dim3 grid((unsigned)std::max(1, (total + 255) / 256), n);
-  edge_up2fix<<<grid, 256, 0, st>>>(pairs, W, bias, cin, cout, relu);
+  dim3 grid((unsigned)std::max(1, max_border), n);
+  const size_t smem = sizeof(uint4) * 9 * (cin / 8);
+  edge_up2fix<<<grid, std::min(128, std::max(32, cout)), smem, st>>>(pairs, Wb, bias, cin, cout, relu);
   return cudaGetLastError();
 }
 

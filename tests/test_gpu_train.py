@@ -219,3 +219,59 @@ def test_backward_without_forward_is_a_state_error(svlib):
         assert ei.value.status == binding.SV_ERR_STATE
     finally:
         ctx.close()
+
+
+def test_bf16_training_step_matches_oracle(svlib):
+    """BF16 forward on the tensor cores with FP32 master weights (the training form of the
+    batched path): the training forward within the BF16 output bar of the FP64 oracle,
+    the FP32 backward's gradient aligned with the oracle's (cosine >= 0.99 per layer, max
+    deviation <= 15% of the layer's largest entry), and a few Adam steps lower the loss."""
+    shape, params, _, _, _, k, D = case()
+    pairs = [synth.make_pair(W, H, 40.0, 950 + W) for W, H in ((256, 128), (130, 67))]
+    ctx = binding.Context(shape, k, "bf16")
+    try:
+        ctx.set_weights(params)
+        dps = [binding.to_device(p, D) for p in pairs]
+        rng = np.random.default_rng(7)
+        coarse, eps, cs, es = [], [], [], []
+        for p in pairs:
+            c = oracle.coarse_match(p.left, p.right, k, D)[0].astype(np.float64) + rng.uniform(0, 0.5, (p.height // 4, p.width // 4))
+            H3, W3 = binding.latent_hw(p.height, p.width)
+            e = synth.reparam_noise(H3 * W3 * shape.latent, p.seed + 1)
+            coarse.append(c); eps.append(e)
+            cs.append(torch.from_numpy(c).float().cuda())
+            es.append(torch.from_numpy(e).cuda().reshape(H3, W3, -1))
+        Y, mu, lv = ctx.refine_train(dps, cs, es)
+        gts = [torch.from_numpy(p.gt).cuda() for p in pairs]
+        out, gY, gmu, glv = ctx.loss(dps, Y, gts, mu, lv, 1e-3)
+        gp, _ = ctx.refine_backward(gY, gmu, glv, False, cs)
+        ctx.synchronize()
+        npix = sum(p.width * p.height for p in pairs)
+        nlat = sum(np.prod(binding.latent_hw(p.height, p.width)) * shape.latent for p in pairs)
+        go = np.zeros(params.size)
+        for p, c, e, y in zip(pairs, coarse, eps, Y):
+            ref = oracle.refine_forward(shape, params, p.left, c, e)
+            d = np.abs(y.cpu().numpy().astype(np.float64) - ref["Y"])
+            assert d.max() <= 0.05 and d.mean() <= 0.01
+            _, g, _ = oracle.refine_backward(shape, params, p.left, c, e, p.gt, npix, nlat, 1e-3)
+            go += g
+        gpn = gp.cpu().numpy().astype(np.float64)
+        for name, (ow, wshape, ob, co) in oracle.param_slices(shape).items():
+            n = int(np.prod(wshape))
+            a, b = gpn[ow:ow + n], go[ow:ow + n]
+            cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
+            assert cos >= 0.99, (name, cos)
+            assert np.abs(a - b).max() <= 0.15 * np.abs(b).max(), name
+        # a few steps of the autograd route on the BF16 form
+        w = torch.from_numpy(params).cuda().requires_grad_(True)
+        losses = []
+        for t in range(1, 6):
+            Yt, mut, lvt = autograd.refine(ctx, dps, cs, es, w)
+            L = autograd.loss(ctx, dps, Yt, gts, mut, lvt)
+            w.grad = None
+            L.backward()
+            ctx.adam_step(w.grad, t, lr=1e-3)
+            losses.append(L.item())
+        assert losses[-1] < losses[0]
+    finally:
+        ctx.close()
