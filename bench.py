@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--train-pairs", type=int, default=16)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch plans (fixed launch order, e.g. for profiler captures)")
     return ap.parse_args()
 
 
@@ -227,7 +229,7 @@ def run_ours(args):
                 ctx.close()
                 continue
             raise
-        if form == "bf16":
+        if form == "bf16" and not args.no_tune:
             tuning = ctx.autotune(dps, stream=st)
         with torch.cuda.stream(st):
             for _ in range(args.warmup):

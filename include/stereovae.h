@@ -204,8 +204,9 @@ SV_API sv_status sv_profile_enable(sv_ctx* ctx, int enable);
 SV_API sv_status sv_profile_read(sv_ctx* ctx, sv_profile_entry* out, int max_entries, int* n_out, int reset);
 
 /* Autotuner of the SV_BF16 form: for each tensor-core layer picks the strip height
- * (rows of 128-unit tiles one work item walks down) and the output-channel slice per CTA
- * that run fastest on this batch, timing every candidate with CUDA events on `stream`.
+ * (rows of 128-unit tiles one work item walks down), the output-channel slice per CTA and
+ * the number of CTAs sharing an SM (1-3; the row prefetch ring shrinks to fit) that run
+ * fastest on this batch, timing every candidate with CUDA events on `stream`.
  * The choice stays in the context and applies to later calls.  cache_path (nullable): a
  * JSON-lines file; an entry for this (GPU, SM count, network, window, batch-shape bucket)
  * is loaded instead of tuning, a new result is appended.  Synchronous.  Returns
@@ -214,9 +215,10 @@ SV_API sv_status sv_autotune(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, con
                              sv_stream stream);
 
 /* The tuned launch shape (6 layers: enc2, enc3, latent, dec1, dec2, dec3): strip rows
- * (0 = automatic), N slice (0 = full width) and the measured microseconds per launch
- * (-1 when loaded from a cache).  Any pointer may be NULL. */
-SV_API sv_status sv_tuning(const sv_ctx* ctx, int* rows6, int* nt6, double* us6);
+ * (0 = automatic), N slice (0 = full width), CTAs per SM (0 = the "tc_ctas_per_sm"
+ * option) and the measured microseconds per launch (-1 when loaded from a cache).  Any
+ * pointer may be NULL. */
+SV_API sv_status sv_tuning(const sv_ctx* ctx, int* rows6, int* nt6, int* ctas6, double* us6);
 
 /* Waits for `stream` and reports device-side failures recorded since the previous
  * call: SV_ERR_TIMEOUT if a kernel's bounded wait ran out (the kernel then returned
@@ -228,6 +230,11 @@ SV_API sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream);
  *   "spin_limit"     clock cycles one device-side wait may spin before it gives up
  *                    (default 4e9, about 2 s)
  *   "tc_strip_rows"  rows per work item of the tensor-core convolutions (0 = automatic)
+ *   "tc_ctas_per_sm" 0 (default): each tensor-core convolution stages as many input rows
+ *                    ahead as shared memory holds; k = 1..4: fewer, so that k CTAs share
+ *                    an SM
+ *   "debug_plans"    1: print each tensor-core layer's launch plan (ring depth, shared
+ *                    memory, CTAs per SM, grid, strips) to stderr when a call is prepared
  *   "graphs"         1 (default): sv_pipeline on an SV_BF16 context captures each batch
  *                    signature in a CUDA graph and replays it (not on the legacy or
  *                    per-thread default stream); 0: launch eagerly

@@ -74,7 +74,7 @@ API = {
     "sv_coarse_match_static": ([POINTER(SvPair), c_int, c_int, POINTER(c_void_p), POINTER(c_void_p),
                                 POINTER(c_void_p), c_void_p], c_int),
     "sv_autotune": ([c_void_p, POINTER(SvPair), c_int, c_char_p, c_void_p], c_int),
-    "sv_tuning": ([c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_double)], c_int),
+    "sv_tuning": ([c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_double)], c_int),
 }
 
 
@@ -283,9 +283,10 @@ class Context:
     def tuning(self):
         rows = (c_int * 6)()
         nt = (c_int * 6)()
+        ctas = (c_int * 6)()
         us = (c_double * 6)()
-        self._check(lib().sv_tuning(self._h, rows, nt, us))
-        return {"rows": list(rows), "nt": list(nt), "us": list(us)}
+        self._check(lib().sv_tuning(self._h, rows, nt, ctas, us))
+        return {"rows": list(rows), "nt": list(nt), "ctas": list(ctas), "us": list(us)}
 
     def launch_count(self) -> int:
         return int(lib().sv_launch_count(self._h))

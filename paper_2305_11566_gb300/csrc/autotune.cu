@@ -1,7 +1,8 @@
 // autotune.cu -- picks the launch shape of every tensor-core layer of the BF16 form on the
 // caller's own batch: for each layer, the strip height (rows of 128-unit tiles one work
 // item walks down, which trades staged-row reuse against load balance) and the N slice
-// (output channels per CTA; narrower slices give more CTAs per pair).  Each candidate
+// (output channels per CTA; narrower slices give more CTAs per pair) and the number of
+// CTAs sharing an SM (a shallower row ring each; their MMA streams interleave).  Each candidate
 // is timed with CUDA events around the layer's launch (the context's profiler); the
 // fastest per layer is kept.  Results are cached per (GPU, SM count, network, window,
 // batch shape bucket) in a JSON-lines file when a path is given.
@@ -42,7 +43,7 @@ std::string tune_key(const Ctx& c, const sv_pair* pairs, int n) {
   return s;
 }
 
-bool load_entry(const char* path, const std::string& key, int rows[6], int nt[6]) {
+bool load_entry(const char* path, const std::string& key, int rows[6], int nt[6], int ctas[6]) {
   std::ifstream f(path);
   if (!f) return false;
   std::string line;
@@ -56,22 +57,31 @@ bool load_entry(const char* path, const std::string& key, int rows[6], int nt[6]
       continue;
     if (sscanf(line.c_str() + t, "\"nt\": [%d, %d, %d, %d, %d, %d]", &b[0], &b[1], &b[2], &b[3], &b[4], &b[5]) != 6)
       continue;
+    int c[6] = {0, 0, 0, 0, 0, 0};
+    const size_t k = line.find("\"ctas\": [");
+    if (k != std::string::npos &&
+        sscanf(line.c_str() + k, "\"ctas\": [%d, %d, %d, %d, %d, %d]", &c[0], &c[1], &c[2], &c[3], &c[4], &c[5]) != 6)
+      continue;
     for (int i = 0; i < 6; ++i) {
       rows[i] = a[i];
       nt[i] = b[i];
+      ctas[i] = c[i];
     }
     return true;
   }
   return false;
 }
 
-void save_entry(const char* path, const std::string& key, const int rows[6], const int nt[6], const double us[6]) {
+void save_entry(const char* path, const std::string& key, const int rows[6], const int nt[6], const int ctas[6],
+                const double us[6]) {
   std::ofstream f(path, std::ios::app);
   if (!f) return;
   f << "{\"key\": \"" << key << "\", \"rows\": [" << rows[0];
   for (int i = 1; i < 6; ++i) f << ", " << rows[i];
   f << "], \"nt\": [" << nt[0];
   for (int i = 1; i < 6; ++i) f << ", " << nt[i];
+  f << "], \"ctas\": [" << ctas[0];
+  for (int i = 1; i < 6; ++i) f << ", " << ctas[i];
   f << "], \"us\": [" << us[0];
   for (int i = 1; i < 6; ++i) f << ", " << us[i];
   f << "]}\n";
@@ -81,11 +91,12 @@ void save_entry(const char* path, const std::string& key, const int rows[6], con
 
 sv_status Ctx::autotune(const sv_pair* pairs, int n, const char* cache_path, cudaStream_t st) {
   const std::string key = tune_key(*this, pairs, n);
-  int rows[6], nt[6];
-  if (cache_path && load_entry(cache_path, key, rows, nt)) {
+  int rows[6], nt[6], ctas[6];
+  if (cache_path && load_entry(cache_path, key, rows, nt, ctas)) {
     for (int i = 0; i < 6; ++i) {
       tc_rows_override[i] = rows[i];
       tc_nt_override[i] = nt[i];
+      tc_ctas_override[i] = ctas[i];
     }
     tune_loaded = true;
     return SV_OK;
@@ -113,20 +124,24 @@ sv_status Ctx::autotune(const sv_pair* pairs, int n, const char* cache_path, cud
   static const char* names[6] = {"tc_enc2", "tc_enc3", "tc_latent", "tc_dec1", "tc_dec2", "tc_dec3"};
   const int row_cands[6] = {0, 2, 4, 8, 16, 32};
   double best_us[6];
-  int best_rows[6], best_nt[6];
+  int best_rows[6], best_nt[6], best_ctas[6];
   for (int i = 0; i < 6; ++i) {
     best_us[i] = 1e30;
     best_rows[i] = 0;
     best_nt[i] = 0;
+    best_ctas[i] = 0;
   }
+  const int cta_cands[3] = {1, 2, 3};
   const bool prof_was = prof_on;
   const auto saved_tot = prof_tot;
   prof_flush();
+  for (int cc : cta_cands)
   for (int half = 0; half < 2; ++half) {
     for (int rc : row_cands) {
       for (int i = 0; i < 6; ++i) {
         tc_rows_override[i] = rc;
         tc_nt_override[i] = 0;
+        tc_ctas_override[i] = cc;
       }
       if (half) {
         // half-width N slices where that still leaves at least 16 channels per slice
@@ -155,6 +170,7 @@ sv_status Ctx::autotune(const sv_pair* pairs, int n, const char* cache_path, cud
           best_us[i] = us;
           best_rows[i] = rc;
           best_nt[i] = tc_nt_override[i];
+          best_ctas[i] = cc;
         }
       }
     }
@@ -165,10 +181,11 @@ sv_status Ctx::autotune(const sv_pair* pairs, int n, const char* cache_path, cud
   for (int i = 0; i < 6; ++i) {
     tc_rows_override[i] = best_rows[i];
     tc_nt_override[i] = best_nt[i];
+    tc_ctas_override[i] = best_ctas[i];
     tune_us[i] = best_us[i];
   }
   if (s) return s;
-  if (cache_path) save_entry(cache_path, key, best_rows, best_nt, best_us);
+  if (cache_path) save_entry(cache_path, key, best_rows, best_nt, best_ctas, best_us);
   return SV_OK;
 }
 
@@ -189,12 +206,13 @@ extern "C" sv_status sv_autotune(sv_ctx* ctx, const sv_pair* pairs, int n_pairs,
   return c->cuda(cudaStreamSynchronize((cudaStream_t)stream), "autotune");
 }
 
-extern "C" sv_status sv_tuning(const sv_ctx* ctx, int* rows6, int* nt6, double* us6) {
+extern "C" sv_status sv_tuning(const sv_ctx* ctx, int* rows6, int* nt6, int* ctas6, double* us6) {
   if (!ctx) return SV_ERR_INVALID_ARG;
   const sv::Ctx* c = reinterpret_cast<const sv::Ctx*>(ctx);
   for (int i = 0; i < 6; ++i) {
     if (rows6) rows6[i] = c->tc_rows_override[i];
     if (nt6) nt6[i] = c->tc_nt_override[i];
+    if (ctas6) ctas6[i] = c->tc_ctas_override[i];
     if (us6) us6[i] = c->tune_loaded ? -1.0 : c->tune_us[i];
   }
   return SV_OK;

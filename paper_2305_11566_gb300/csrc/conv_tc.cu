@@ -3,15 +3,17 @@
 //
 // GEMM view of one tile: M = 128 consecutive output units of one row, N = NT output
 // channels, K = taps x Cin.  Instead of an im2col copy per tap, the input rows a tile
-// needs are staged ONCE in shared memory in a K-major "planes" layout (plane c holds
-// channels 8c..8c+7 of every staged pixel, 16 bytes per pixel, pixels contiguous), so the
-// A operand of every tap is the same staged rows seen from a shifted start address
-// (matrix descriptor: no swizzle, LBO = plane stride, SBO = 128 B).  Consecutive tiles of
-// a CTA walk down the rows of a column strip and reuse staged rows (ring of row slots).
+// needs are staged ONCE in shared memory as K-major swizzled pixel rows: channel block kb
+// (RB / 2 channels, RB = 128, 64 or 32 bytes per pixel) of every staged pixel, pixel
+// after pixel, in the 128/64/32-byte swizzle that one TMA box per block writes.  The A
+// operand of every tap is the same staged rows seen from a start address shifted by
+// whole pixels (matrix descriptor: swizzled K-major, SBO = 8 pixels); the K steps of 16
+// channels inside a pixel row advance the start by 32 bytes.  Consecutive tiles of a CTA
+// walk down the rows of a column strip and reuse staged rows (ring of row slots).
 //
 // Modes:
 //   TM_S2  3x3 stride-2 conv (encoder): staged rows 2i-1, 2i, 2i+1 with odd and even
-//          pixels de-interleaved into two plane sets, so each tap is a unit-stride view.
+//          pixels de-interleaved into two pixel sets, so each tap is a unit-stride view.
 //   TM_UP2 nearest-x2 upsample + 3x3 conv (decoder), computed as four output phases
 //          (py, px) of 2x2 convs on the low-resolution input with the 3x3 weights summed
 //          per phase (rows/cols {0} and {1,2} for phase 0, {0,1} and {2} for phase 1):
@@ -20,10 +22,11 @@
 //   TM_P1  1x1 conv (latent mean head).
 //
 // Warp roles (192 threads): warps 0-3 epilogue (TMEM lanes 0-127: tcgen05.ld, bias,
-// ReLU, BF16 store), warp 4 TMEM allocation + one thread issuing tcgen05.mma, warp 5 one
-// thread loading every staged row with TMA (cp.async.bulk.tensor, one box of 8 channels x
-// the staged pixels per plane; the hardware fills the halo outside the image with zeros)
-// and signalling the row's mbarrier by transaction count.  Every wait is bounded; on
+// ReLU, BF16 store), warp 4 TMEM allocation + one thread issuing tcgen05.mma (descriptors
+// advanced by constant increments, no per-MMA address arithmetic), warp 5 one thread
+// loading every staged row with TMA (cp.async.bulk.tensor, one box of RB / 2 channels x
+// the staged pixels per channel block and pixel set; the hardware fills the halo outside
+// the image with zeros) and signalling the row's mbarrier by transaction count.  Every wait is bounded; on
 // timeout the kernel records an error code and returns.
 #include <algorithm>
 #include <cstdio>
@@ -79,15 +82,19 @@ constexpr int kBarBytes = 8;
 
 __host__ __device__ inline int nset(int mode) { return mode == TM_S2 ? 2 : 1; }
 __host__ __device__ inline int npx(int mode) { return mode == TM_P1 ? 128 : 129; }
-// plane = 8 channels of every staged pixel of one set, 16 B per pixel, 128-B aligned
-__host__ __device__ inline uint32_t plane_stride(int mode) { return (uint32_t)((npx(mode) * 16 + 127) / 128 * 128); }
+// bytes per staged pixel and channel block: the widest swizzle span whose channel count
+// divides cin (128 B = 64 channels, 64 B = 32, 32 B = 16)
+__host__ __device__ inline int rb_of(int cin) { return cin % 64 == 0 ? 128 : cin % 32 == 0 ? 64 : 32; }
+// one channel block of every staged pixel of one set, 1024-byte aligned (swizzle atom)
+__host__ __device__ inline uint32_t kb_stride(int mode, int rb) { return (uint32_t)((npx(mode) * rb + 1023) / 1024 * 1024); }
 __host__ __device__ inline size_t row_bytes(int mode, int cin) {
-  return (size_t)nset(mode) * (cin / 8) * plane_stride(mode);
+  const int rb = rb_of(cin);
+  return (size_t)nset(mode) * (cin * 2 / rb) * kb_stride(mode, rb);
 }
 __host__ __device__ inline int taps(int mode) { return mode == TM_S2 ? 9 : mode == TM_UP2 ? 4 : 1; }
 __host__ __device__ inline size_t b_bytes(int mode, int NT, int cin) { return (size_t)taps(mode) * NT * cin * 2; }
 __host__ __device__ inline size_t smem_bytes(int mode, int NT, int cin, int ring) {
-  return 1024 + b_bytes(mode, NT, cin) + (size_t)NT * 4 + 128 + (size_t)ring * row_bytes(mode, cin) +
+  return 1024 + (b_bytes(mode, NT, cin) + (size_t)NT * 4 + 1023) / 1024 * 1024 + (size_t)ring * row_bytes(mode, cin) +
          (size_t)(2 * ring + 4) * kBarBytes + 16;
 }
 
@@ -100,20 +107,35 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
 }
-// Wait for the phase with the given parity to complete; false after `spin` cycles.
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Wait for the phase with the given parity to complete; false after `spin` cycles.  The
+// common case (already complete) costs one try_wait.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long spin) {
+  if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
+    if (mbar_try(bar, parity)) return true;
     if (clock64() - t0 > spin) return false;
   }
 }
+// position in the ring of staged rows, advanced without division
+struct RingPos {
+  uint32_t slot = 0, pass = 0;  // pass = number of completed trips round the ring
+  __device__ __forceinline__ void next(uint32_t ring) {
+    if (++slot == ring) {
+      slot = 0;
+      ++pass;
+    }
+  }
+};
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -122,7 +144,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar), "r"(bytes)
                : "memory");
 }
-// 3-D TMA tile load (box: 8 channels x staged pixels x 1 row) completing on `bar`.
+// 3-D TMA tile load (box: RB / 2 channels x staged pixels x 1 row) completing on `bar`.
 __device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* tm, int c, int x, int y, uint32_t bar) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
@@ -134,17 +156,23 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* tm) {
   asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
 }
 
-// K-major, no-swizzle shared-memory matrix descriptor (tcgen05 format: bits 46-48 = 0b001).
-__device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+// tcgen05 shared-memory matrix descriptors as two 32-bit words.  Low word: start address
+// >> 4 (bits 0-13), leading byte offset >> 4 (bits 16-29).  High word: stride byte offset
+// >> 4 (bits 0-13), version 1 (bit 14), base offset 0, layout (bits 29-31: 0 none,
+// 2 128-byte swizzle, 4 64-byte, 6 32-byte).  The start field stays below 2^14 for any
+// shared address (< 256 KB), so adding to the low word never carries into the LBO field.
+__host__ __device__ constexpr uint32_t desc_lo(uint32_t addr, uint32_t lbo) { return (addr >> 4) | ((lbo >> 4) << 16); }
+__host__ __device__ constexpr uint32_t desc_hi(uint32_t sbo, uint32_t layout) {
+  return ((sbo >> 4) & 0x3FFFu) | (1u << 14) | (layout << 29);
 }
+__host__ __device__ constexpr uint32_t swz_layout(int rb) { return rb == 128 ? 2u : rb == 64 ? 4u : 6u; }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
+                                         uint32_t idesc, uint32_t acc) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+      "{\n .reg .b64 da, db;\n .reg .pred p;\n mov.b64 da, {%1, %2};\n mov.b64 db, {%3, %4};\n"
+      " setp.ne.b32 p, %6, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n}\n" ::"r"(tmem_d),
+      "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -202,22 +230,23 @@ __device__ __forceinline__ void tap_geo(int t, int& row, int& set, int& col) {
   }
 }
 
-template <int MODE, int NT>
+template <int MODE, int NT, int RB>
 __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_constant__ Params p) {
   using G_ = Geo<MODE>;
   constexpr int RA = G_::RA, STEP = G_::STEP, T = G_::T, NSET = G_::NSET, NPX = G_::NPX;
+  constexpr int KPR = RB / 32;                                 // 16-channel K steps per pixel row
+  constexpr uint32_t KBS = (NPX * RB + 1023) / 1024 * 1024;    // channel-block stride
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* gbase = smem_raw + (base - raw);
   const int cin = p.cin;
   const uint32_t ring = (uint32_t)p.ring;
-  const int kplanes = cin / 8;
-  const uint32_t pstride = (NPX * 16 + 127) / 128 * 128;
-  const uint32_t rowb = NSET * kplanes * pstride;
+  const int KB = cin * 2 / RB;  // channel blocks
+  const uint32_t rowb = NSET * KB * KBS;
   const uint32_t sB = base;
   const uint32_t sBias = sB + (uint32_t)T * NT * cin * 2;
-  const uint32_t sA = (sBias + NT * 4 + 127u) & ~127u;
+  const uint32_t sA = (sBias + NT * 4 + 1023u) & ~1023u;
   const uint32_t bars = sA + ring * rowb;
   const uint32_t full0 = bars, empty0 = bars + ring * 8, accf0 = bars + 2 * ring * 8, acce0 = accf0 + 16;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + (acce0 + 16 - base));
@@ -266,11 +295,14 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   if (warp == 5) {
     // ------------------------------------------------------------ TMA producer (one thread)
     if (lane == 0) {
-      const uint32_t row_tx = (uint32_t)(NSET * kplanes * NPX * 16);
+      const uint32_t row_tx = (uint32_t)(NSET * KB * NPX * RB);
+      RingPos w;  // slot of the next row to load; row q goes to slot q % ring on pass q / ring
       uint32_t q = 0;
       int last_pair = -1;
+      Strip nxt = crank < p.n_strips ? p.strips[crank] : Strip{};
       for (int s = crank; s < p.n_strips && ok; s += cpg) {
-        const Strip st = p.strips[s];
+        const Strip st = nxt;
+        if (s + cpg < p.n_strips) nxt = p.strips[s + cpg];  // in flight while this strip loads
         const LayerPair* L = p.lp + st.pair;
         if (st.pair != last_pair) {
           for (int k = 0; k < NSET; ++k) tensormap_acquire(&L->tm[k]);
@@ -278,20 +310,20 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
         }
         const int nrows = STEP * (st.cnt - 1) + RA;
         const int y0 = first_row<MODE>(st.i0, py);
-        for (int r = 0; r < nrows; ++r, ++q) {
-          const uint32_t slot = q % ring, use = q / ring;
-          if (use > 0 && !mbar_wait(empty0 + 8 * slot, (use - 1) & 1, p.spin)) {
+        for (int r = 0; r < nrows; ++r, ++q, w.next(ring)) {
+          // the slot's previous row must have been consumed (pass > 0: released once)
+          if (w.pass > 0 && !mbar_wait(empty0 + 8 * w.slot, (w.pass - 1) & 1, p.spin)) {
             atomicCAS(p.err, 0, 1);
             ok = false;
             break;
           }
-          const uint32_t fb = full0 + 8 * slot;
+          const uint32_t fb = full0 + 8 * w.slot;
           mbar_expect_tx(fb, row_tx);
-          const uint32_t dst0 = sA + slot * rowb;
+          const uint32_t dst0 = sA + w.slot * rowb;
           for (int k = 0; k < NSET; ++k) {
             const int x0 = set_x0<MODE>(k, st.j0, px);
-            for (int c = 0; c < kplanes; ++c)
-              tma_load3(dst0 + (k * kplanes + c) * pstride, &L->tm[k], c * 8, x0, y0 + r, fb);
+            for (int kb = 0; kb < KB; ++kb)
+              tma_load3(dst0 + (k * KB + kb) * KBS, &L->tm[k], kb * (RB / 2), x0, y0 + r, fb);
           }
         }
       }
@@ -308,20 +340,24 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((128u >> 4) << 24);
-      const uint32_t ksteps = cin / 16;
       const uint32_t bsz = NT * cin * 2;
-      // descriptor pieces that never change: LBO, SBO, version bits
-      const uint64_t adesc_hi = ((uint64_t)((pstride >> 4) & 0x3FFFu) << 16) | ((uint64_t)(128 >> 4) << 32) | (1ull << 46);
-      const uint64_t bdesc_hi = ((uint64_t)(128 >> 4) << 16) | ((uint64_t)((cin * 16 >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-      uint32_t qbase = 0, tseq = 0;
+      // A: swizzled K-major pixel rows, SBO = 8 pixels (LBO unused: one swizzle span per
+      // row); B: no-swizzle K-major core matrices, LBO = 128 B (next 8 channels), SBO =
+      // 8 output channels x cin
+      constexpr uint32_t a_hi = desc_hi(8 * RB, swz_layout(RB));
+      const uint32_t b_hi = desc_hi((uint32_t)cin * 16, 0);
+      uint32_t tseq = 0;
+      RingPos wt;  // next row to wait for (rows are waited for in load order)
+      RingPos tb;  // slot of the first row of the current tile
+      Strip nxt = crank < p.n_strips ? p.strips[crank] : Strip{};
       for (int s = crank; s < p.n_strips && ok; s += cpg) {
-        const Strip st = p.strips[s];
+        const Strip st = nxt;
+        if (s + cpg < p.n_strips) nxt = p.strips[s + cpg];
         const int nrows = STEP * (st.cnt - 1) + RA;
         for (int ii = 0; ii < st.cnt && ok; ++ii) {
-          const uint32_t rlo = ii == 0 ? 0 : STEP * (ii - 1) + RA;  // rows not waited for yet
-          for (uint32_t r = rlo; r < (uint32_t)(STEP * ii + RA); ++r) {
-            const uint32_t qa = qbase + r;
-            if (!mbar_wait(full0 + 8 * (qa % ring), (qa / ring) & 1, p.spin)) {
+          const int rlo = ii == 0 ? 0 : STEP * (ii - 1) + RA;  // rows not waited for yet
+          for (int r = rlo; r < STEP * ii + RA; ++r, wt.next(ring)) {
+            if (!mbar_wait(full0 + 8 * wt.slot, wt.pass & 1, p.spin)) {
               ok = false;
               break;
             }
@@ -336,27 +372,34 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
           const uint32_t dcol = tmem + buf * NT;
           uint32_t slot_of_row[RA];
 #pragma unroll
-          for (int r = 0; r < RA; ++r) slot_of_row[r] = (qbase + STEP * ii + r) % ring;
+          for (int r = 0; r < RA; ++r) {
+            const uint32_t sl = tb.slot + r;
+            slot_of_row[r] = sA + (sl >= ring ? sl - ring : sl) * rowb;
+          }
+          uint32_t acc = 0;
 #pragma unroll
           for (int t = 0; t < T; ++t) {
             int ro, se, co;
             tap_geo<MODE>(t, ro, se, co);
-            const uint32_t abase = sA + slot_of_row[ro] * rowb + se * kplanes * pstride + co * 16;
-            const uint32_t bbase = sB + t * bsz;
-#pragma unroll 2
-            for (uint32_t kk = 0; kk < ksteps; ++kk) {
-              const uint64_t ad = adesc_hi | (uint64_t)(((abase + kk * 2 * pstride) & 0x3FFFFu) >> 4);
-              const uint64_t bd = bdesc_hi | (uint64_t)(((bbase + kk * 256) & 0x3FFFFu) >> 4);
-              mma_bf16(dcol, ad, bd, idesc, (t | kk) ? 1u : 0u);
+            uint32_t alo = desc_lo(slot_of_row[ro] + (uint32_t)(se * KB) * KBS + (uint32_t)co * RB, 16);
+            uint32_t blo = desc_lo(sB + t * bsz, 128);
+            for (int kb = 0; kb < KB; ++kb) {
+#pragma unroll
+              for (int k4 = 0; k4 < KPR; ++k4) {
+                // next 16 channels: +32 B inside the swizzled pixel row, +256 B in B
+                mma_bf16(dcol, alo + 2 * k4, a_hi, blo + 16 * k4, b_hi, idesc, acc);
+                acc = 1;
+              }
+              alo += KBS >> 4;
+              blo += 16 * KPR;
             }
           }
           mma_commit(accf0 + 8 * buf);
           // release the rows the next tile of this strip no longer reads
-          const uint32_t rel_hi = ii + 1 < st.cnt ? STEP * (ii + 1) : nrows;
-          for (uint32_t r = STEP * ii; r < rel_hi; ++r) mma_commit(empty0 + 8 * ((qbase + r) % ring));
+          const int rel_hi = ii + 1 < st.cnt ? STEP * (ii + 1) : nrows;
+          for (int r = STEP * ii; r < rel_hi; ++r, tb.next(ring)) mma_commit(empty0 + 8 * tb.slot);
           ++tseq;
         }
-        qbase += nrows;
       }
       // drain, also after a timeout: the last commit arrives when every MMA issued by this
       // CTA has completed, so tensor memory is released only once nothing writes to it
@@ -466,23 +509,36 @@ __global__ void pack_kernel(const float* __restrict__ W, int mode, int NT, int G
 }
 
 
-template <int MODE, int NT>
+template <int MODE, int NT, int RB>
 cudaError_t launch_mode_nt(const Params& p, int grid, size_t smem, cudaStream_t st) {
-  auto k = conv_tc_kernel<MODE, NT>;
+  auto k = conv_tc_kernel<MODE, NT, RB>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // all of the SM's unified L1 / shared storage as shared memory: co-resident CTAs
+  e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   k<<<grid, kThreads, smem, st>>>(p);
   return cudaGetLastError();
 }
 
+template <int MODE, int RB>
+cudaError_t launch_mode_rb(const Params& p, int NT, int grid, size_t smem, cudaStream_t st) {
+  switch (NT) {
+    case 16: return launch_mode_nt<MODE, 16, RB>(p, grid, smem, st);
+    case 32: return launch_mode_nt<MODE, 32, RB>(p, grid, smem, st);
+    case 64: return launch_mode_nt<MODE, 64, RB>(p, grid, smem, st);
+    case 128: return launch_mode_nt<MODE, 128, RB>(p, grid, smem, st);
+    case 256: return launch_mode_nt<MODE, 256, RB>(p, grid, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <int MODE>
 cudaError_t launch_mode(const Params& p, int NT, int grid, size_t smem, cudaStream_t st) {
-  switch (NT) {
-    case 16: return launch_mode_nt<MODE, 16>(p, grid, smem, st);
-    case 32: return launch_mode_nt<MODE, 32>(p, grid, smem, st);
-    case 64: return launch_mode_nt<MODE, 64>(p, grid, smem, st);
-    case 128: return launch_mode_nt<MODE, 128>(p, grid, smem, st);
-    case 256: return launch_mode_nt<MODE, 256>(p, grid, smem, st);
+  switch (rb_of(p.cin)) {
+    case 128: return launch_mode_rb<MODE, 128>(p, NT, grid, smem, st);
+    case 64: return launch_mode_rb<MODE, 64>(p, NT, grid, smem, st);
+    case 32: return launch_mode_rb<MODE, 32>(p, NT, grid, smem, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -496,25 +552,57 @@ cudaError_t launch_conv(int mode, const Params& p, int NT, int grid, size_t smem
   return cudaErrorInvalidValue;
 }
 
-int blocks_per_sm(int mode, int NT, size_t smem) {
-  int n = 0;
-  cudaError_t e = cudaErrorInvalidValue;
-#define SV_OCC(M, N)                                                                                   \
-  if (mode == M && NT == N) {                                                                         \
-    cudaFuncSetAttribute(conv_tc_kernel<M, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, conv_tc_kernel<M, N>, kThreads, smem);       \
+// CTAs of one layer that fit an SM.  Computed from the kernel's resources: the occupancy
+// API answers 1 for any kernel that allocates tensor memory, although the hardware runs
+// several such CTAs per SM when their columns fit the SM's 512.
+template <int MODE, int NT, int RB>
+static int regs_of() {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, conv_tc_kernel<MODE, NT, RB>) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
   }
-  SV_OCC(TM_S2, 16) SV_OCC(TM_S2, 32) SV_OCC(TM_S2, 64) SV_OCC(TM_S2, 128) SV_OCC(TM_S2, 256)
-  SV_OCC(TM_UP2, 16) SV_OCC(TM_UP2, 32) SV_OCC(TM_UP2, 64) SV_OCC(TM_UP2, 128) SV_OCC(TM_UP2, 256)
-  SV_OCC(TM_P1, 16) SV_OCC(TM_P1, 32) SV_OCC(TM_P1, 64) SV_OCC(TM_P1, 128) SV_OCC(TM_P1, 256)
-#undef SV_OCC
-  if (e != cudaSuccess) {
+  return fa.numRegs;
+}
+template <int MODE, int RB>
+static int regs_rb(int NT) {
+  switch (NT) {
+    case 16: return regs_of<MODE, 16, RB>();
+    case 32: return regs_of<MODE, 32, RB>();
+    case 64: return regs_of<MODE, 64, RB>();
+    case 128: return regs_of<MODE, 128, RB>();
+    case 256: return regs_of<MODE, 256, RB>();
+  }
+  return -1;
+}
+template <int MODE>
+static int regs_mode(int NT, int cin) {
+  switch (rb_of(cin)) {
+    case 128: return regs_rb<MODE, 128>(NT);
+    case 64: return regs_rb<MODE, 64>(NT);
+    case 32: return regs_rb<MODE, 32>(NT);
+  }
+  return -1;
+}
+
+int blocks_per_sm(int mode, int NT, int cin, size_t smem, int device) {
+  const int regs = mode == TM_S2 ? regs_mode<TM_S2>(NT, cin) : mode == TM_UP2 ? regs_mode<TM_UP2>(NT, cin)
+                                                                               : regs_mode<TM_P1>(NT, cin);
+  int per_sm = 0, reserved = 0, regfile = 0, max_threads = 0;
+  if (regs <= 0 || cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regfile, cudaDevAttrMaxRegistersPerMultiprocessor, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&max_threads, cudaDevAttrMaxThreadsPerMultiProcessor, device) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
+  const int by_smem = (int)((size_t)per_sm / (smem + (size_t)reserved));
+  const int warp_regs = (regs * 32 + 255) / 256 * 256;  // allocated per warp in units of 256
+  const int by_regs = regfile / (warp_regs * (kThreads / 32));
+  const int by_threads = max_threads / kThreads;
   // tensor memory: co-resident CTAs must fit 512 columns
   const int cols = NT * 2 <= 32 ? 32 : NT * 2 <= 64 ? 64 : NT * 2 <= 128 ? 128 : NT * 2 <= 256 ? 256 : 512;
-  return std::max(0, std::min(n, 512 / cols));
+  return std::max(0, std::min(std::min(by_smem, by_regs), std::min(by_threads, 512 / cols)));
 }
 
 }  // namespace tc
@@ -522,6 +610,7 @@ int blocks_per_sm(int mode, int NT, size_t smem) {
 // ------------------------------------------------------------------ host side
 namespace {
 constexpr size_t kSmemLimit = 232448;  // 227 KB opt-in per block
+constexpr int kPrefetchSteps = 8;      // row steps staged ahead of the tile being computed
 }  // namespace
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda).
@@ -538,19 +627,22 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // TMA view of a BF16 NHWC activation: dims (channels, pixels of the set, rows), box of
-// 8 channels x `box_px` pixels x 1 row, zero fill outside.  `px_step` = 2 for the odd /
-// even pixel sets of a stride-2 layer.
+// one channel block (RB / 2 channels) x `box_px` pixels x 1 row in the RB-byte swizzle,
+// zero fill outside.  `px_step` = 2 for the odd / even pixel sets of a stride-2 layer.
 static bool make_tmap(CUtensorMap* m, const __nv_bfloat16* base, int C, int npix, int H, int W, int px_step,
                       int box_px) {
   auto fn = encode_fn();
   if (!fn || npix < 1) return false;
+  const int rb = tc::rb_of(C);
   cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)npix, (cuuint64_t)H};
   cuuint64_t strides[2] = {(cuuint64_t)px_step * C * 2, (cuuint64_t)W * C * 2};
-  cuuint32_t box[3] = {8, (cuuint32_t)box_px, 1};
+  cuuint32_t box[3] = {(cuuint32_t)(rb / 2), (cuuint32_t)box_px, 1};
   cuuint32_t es[3] = {1, 1, 1};
+  const CUtensorMapSwizzle sw = rb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : rb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                           : CU_TENSOR_MAP_SWIZZLE_32B;
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-         CUDA_SUCCESS;
+            sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // BF16 copies of the decoder weights in their canonical [co][3][3][ci] order (border fix),
@@ -592,17 +684,23 @@ static void plan_layers(const NetDims& net, std::vector<TcLayerPlan>& plans, siz
       NT /= 2;
       ring = RA + STEP;
     }
-    // spend leftover shared memory on deeper row prefetch
-    while (ring < RA + 3 * STEP && tc::smem_bytes(pl.mode, NT, pl.cin, ring + 1) <= kSmemLimit) ++ring;
+    // spend leftover shared memory on deeper row prefetch: a staged row is needed by one
+    // tile of MMAs only, so many rows in flight hide the load latency
+    while (ring < RA + kPrefetchSteps * STEP && tc::smem_bytes(pl.mode, NT, pl.cin, ring + 1) <= kSmemLimit) ++ring;
     pl.NT = NT;
     pl.ring = ring;
     const int nsl = (pl.cout + NT - 1) / NT;
     pl.G = pl.mode == tc::TM_UP2 ? 4 * nsl : nsl;
     pl.smem = tc::smem_bytes(pl.mode, NT, pl.cin, ring);
     pl.wofs = total;
+    pl.fix_wofs = 0;
     total += (size_t)pl.G * tc::taps(pl.mode) * NT * pl.cin;
     plans.push_back(pl);
   }
+  size_t unf[3];
+  unfolded_offsets(net, total, unf);
+  for (auto& pl : plans)
+    if (pl.mode == tc::TM_UP2) pl.fix_wofs = unf[pl.layer == L_DEC1 ? 0 : pl.layer == L_DEC2 ? 1 : 2];
 }
 
 sv_status Ctx::pack_bf16_weights(cudaStream_t st) {
@@ -650,8 +748,27 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
       pl.G = pl.mode == tc::TM_UP2 ? 4 * nsl : nsl;
       const int RA = pl.mode == tc::TM_S2 ? 3 : pl.mode == tc::TM_UP2 ? 2 : 1;
       const int STEP = pl.mode == tc::TM_S2 ? 2 : 1;
-      while (pl.ring < RA + 3 * STEP && tc::smem_bytes(pl.mode, NT, pl.cin, pl.ring + 1) <= kSmemLimit) ++pl.ring;
+      while (pl.ring < RA + kPrefetchSteps * STEP && tc::smem_bytes(pl.mode, NT, pl.cin, pl.ring + 1) <= kSmemLimit)
+        ++pl.ring;
       pl.smem = tc::smem_bytes(pl.mode, NT, pl.cin, pl.ring);
+    }
+  }
+  {
+    // shallower rings so that k CTAs share an SM (k per layer from the autotuner, else the
+    // context option); one CTA's control overhead between its MMA batches is then
+    // covered by the other CTAs' MMAs
+    int per_sm = 0, reserved = 0;
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
+    for (size_t li = 0; li < r.plans.size(); ++li) {
+      const int k = tc_ctas_override[li] > 0 ? tc_ctas_override[li] : tc_ctas_per_sm;
+      if (k <= 1) continue;
+      TcLayerPlan& pl = r.plans[li];
+      const size_t budget = (size_t)per_sm / k - (size_t)reserved;
+      const int RA = pl.mode == tc::TM_S2 ? 3 : pl.mode == tc::TM_UP2 ? 2 : 1;
+      const int STEP = pl.mode == tc::TM_S2 ? 2 : 1;
+      while (pl.ring > RA + STEP && tc::smem_bytes(pl.mode, pl.NT, pl.cin, pl.ring) > budget) --pl.ring;
+      pl.smem = tc::smem_bytes(pl.mode, pl.NT, pl.cin, pl.ring);
     }
   }
   sv_status s;
@@ -717,7 +834,7 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
       if (!okm) return fail(SV_ERR_CUDA, "layer %d: cuTensorMapEncodeTiled failed", pl.layer);
       fix[i] = {L.in, L.out, L.Hi, L.Wi, L.Ho, L.Wo, L.Hu, L.Wu};
     }
-    int bps = tc::blocks_per_sm(pl.mode, pl.NT, pl.smem);
+    int bps = tc::blocks_per_sm(pl.mode, pl.NT, pl.cin, pl.smem, device);
     if (bps <= 0) return fail(SV_ERR_UNSUPPORTED, "layer %d: tensor-core kernel does not fit an SM", pl.layer);
     int grid = std::max(pl.G, (nsm * bps) / pl.G * pl.G);
     const int cpg = grid / pl.G;
@@ -737,10 +854,12 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
     r.tabs[li].n_strips = (int)strips.size();
     r.tabs[li].grid = grid;
     r.tabs[li].hs = hs;
+    if (debug_plans)
+      fprintf(stderr, "[sv] tc layer %d: mode %d cin %d cout %d NT %d ring %d smem %zu blocks/SM %d grid %d strips %zu rows %d\n",
+              pl.layer, pl.mode, pl.cin, pl.cout, pl.NT, pl.ring, pl.smem, bps, grid, strips.size(), hs);
     int mb = 0;
-    for (int i = 0; i < n; ++i)
-      mb = std::max(mb, ((lps[i].Ho & 1) ? lps[i].Wo : 0) + ((lps[i].Wo & 1) ? lps[i].Ho : 0));
-    r.tabs[li].max_border = mb;
+    for (int i = 0; i < n; ++i) mb = std::max(mb, upfix_segments(lps[i].Ho, lps[i].Wo));
+    r.tabs[li].fix_segments = mb;
   }
   std::vector<EdgePair> eps_(n);
   r.maxW = r.maxH = r.maxW1 = r.maxH1 = 0;
@@ -805,16 +924,10 @@ sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream
       LaunchScope ls(*this, names[li], st);
       if ((s = cuda(tc::launch_conv(pl.mode, prm, pl.NT, r.tabs[li].grid, pl.smem, st), names[li]))) return s;
     }
-    if (pl.mode == tc::TM_UP2 && r.tabs[li].max_border > 0) {
+    if (pl.mode == tc::TM_UP2 && r.tabs[li].fix_segments > 0) {
       LaunchScope ls(*this, "edge_up2fix", st);
-      size_t unf[3], wtot;
-      std::vector<TcLayerPlan> tmp;
-      plan_layers(net, tmp, wtot);
-      unfolded_offsets(net, wtot, unf);
-      const int dk = pl.layer == L_DEC1 ? 0 : pl.layer == L_DEC2 ? 1 : 2;
-      if ((s = cuda(launch_edge_up2fix((const UpFixPair*)(tables + r.tabs[li].fix_ofs), r.n, r.tabs[li].max_border,
-                                       (const __nv_bfloat16*)wbf.p + unf[dk],
-                                       prm.bias, pl.cin, pl.cout, 1, st),
+      if ((s = cuda(launch_edge_up2fix((const UpFixPair*)(tables + r.tabs[li].fix_ofs), r.n, r.tabs[li].fix_segments,
+                                       (const __nv_bfloat16*)wbf.p + pl.fix_wofs, prm.bias, pl.cin, pl.cout, 1, st),
                     "border fix")))
         return s;
     }

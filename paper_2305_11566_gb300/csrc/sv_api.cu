@@ -499,6 +499,17 @@ sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value) {
     if (!c->use_graphs) c->drop_graphs();
     return SV_OK;
   }
+  if (!strcmp(key, "debug_plans")) {
+    if (value != 0 && value != 1) return c->fail(SV_ERR_INVALID_ARG, "debug_plans must be 0 or 1");
+    c->debug_plans = (int)value;
+    return SV_OK;
+  }
+  if (!strcmp(key, "tc_ctas_per_sm")) {
+    if (value < 0 || value > 4) return c->fail(SV_ERR_INVALID_ARG, "tc_ctas_per_sm must be 0..4");
+    c->tc_ctas_per_sm = (int)value;
+    c->drop_graphs();
+    return SV_OK;
+  }
   if (!strcmp(key, "tc_strip_rows")) {
     if (value < 0 || value > 4096) return c->fail(SV_ERR_INVALID_ARG, "tc_strip_rows out of range");
     c->tc_strip_rows = (int)value;

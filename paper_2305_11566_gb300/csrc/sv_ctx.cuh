@@ -26,6 +26,7 @@ struct DevBuf {
 struct TcLayerPlan {
   int layer, mode, NT, G, ring, cin, cout, relu;
   size_t wofs, smem;
+  size_t fix_wofs;  // decoder layers: BF16 [co][3][3][ci] weights of the border fix
 };
 
 // Prepared tensor-core refinement call: plans, table bytes and launch geometry.
@@ -33,7 +34,7 @@ struct TcRun {
   std::vector<TcLayerPlan> plans;
   struct Tab {
     size_t lp_ofs, strip_ofs, fix_ofs;
-    int n_strips, grid, max_border, hs;
+    int n_strips, grid, fix_segments, hs;  // fix_segments: border-fix blocks per pair (max)
   };
   std::vector<Tab> tabs;
   std::vector<unsigned char> host;
@@ -94,8 +95,11 @@ struct Ctx {
   std::vector<unsigned char> tc_host_tables;
   long long spin_limit = 4000000000LL;  // clock64 cycles a device-side wait may spin
   int tc_strip_rows = 0;                // 0: automatic
+  int debug_plans = 0;                  // 1: print each tensor-core layer's launch plan to stderr
+  int tc_ctas_per_sm = 0;               // 0: deepest row ring (one CTA per SM); k: ring sized for k
   int tc_rows_override[6] = {0, 0, 0, 0, 0, 0};  // per tensor-core layer, set by the autotuner
   int tc_nt_override[6] = {0, 0, 0, 0, 0, 0};
+  int tc_ctas_override[6] = {0, 0, 0, 0, 0, 0};  // CTAs per SM the ring is sized for (0: tc_ctas_per_sm)
   bool use_graphs = true;
   bool tune_loaded = false;
   double tune_us[6] = {0, 0, 0, 0, 0, 0};

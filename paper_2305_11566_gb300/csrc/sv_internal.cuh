@@ -151,7 +151,15 @@ cudaError_t launch_edge_enc1(const EdgePair* pairs, int n, int maxW1, int maxH1,
                              cudaStream_t st);
 cudaError_t launch_edge_final(const EdgePair* pairs, int n, int maxW, int maxH, const float* W, const float* B, int C,
                               cudaStream_t st);
-cudaError_t launch_edge_up2fix(const UpFixPair* pairs, int n, int max_border, const __nv_bfloat16* Wb,
+// Border pixels of a cropped nearest-x2 + 3x3 conv output that the 4-phase form folds
+// wrongly: the last row when Ho is odd, the last column (above that row) when Wo is odd.
+// The fix kernel takes them in segments of kUpFixSeg pixels, one block per segment.
+constexpr int kUpFixSeg = 64;
+inline int upfix_segments(int Ho, int Wo) {
+  const int nrow = (Ho & 1) ? Wo : 0, ncol = (Wo & 1) ? Ho - (Ho & 1) : 0;
+  return (nrow + kUpFixSeg - 1) / kUpFixSeg + (ncol + kUpFixSeg - 1) / kUpFixSeg;
+}
+cudaError_t launch_edge_up2fix(const UpFixPair* pairs, int n, int max_segments, const __nv_bfloat16* Wb,
                                const float* bias, int cin, int cout, int relu, cudaStream_t st);
 
 // Training latent of the tensor-core form: mu, logvar (FP32, caller's buffers) from BF16

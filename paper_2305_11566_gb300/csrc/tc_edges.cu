@@ -4,9 +4,11 @@
 //   edge_enc1    first conv (3x3 stride 2, 2 -> C1, ReLU) with its input built while
 //                staging: x0 = (L / 256, U / 256), U = 4 * bilinear(coarse) (a5, a6, a7).
 //                FP32 arithmetic, BF16 NHWC output.
-//   edge_final   last conv (3x3, C -> 1) + bias + U (residual), BF16 input, FP32 output (a11).
+//   edge_final   last conv (3x3, C -> 1) + bias + U (residual), BF16 input, FP32 output (a11);
+//                register-blocked packed-FP32 form for C = 16, 32, 64, 128.
 //   edge_up2fix  exact recomputation of the last row / column of an odd-sized (cropped)
-//                nearest-x2 + 3x3 conv output, which the 4-phase tensor-core form folds wrongly.
+//                nearest-x2 + 3x3 conv output, which the 4-phase tensor-core form folds
+//                wrongly: segments of 64 border pixels x 32 channels per block.
 #include "sv_ctx.cuh"
 
 namespace sv {
@@ -26,6 +28,17 @@ __device__ __forceinline__ float upsample4_f(const CT* __restrict__ c, int w, in
   const float top = (1.f - fx) * (float)c[(size_t)y0 * w + x0] + fx * (float)c[(size_t)y0 * w + x1];
   const float bot = (1.f - fx) * (float)c[(size_t)y1 * w + x0] + fx * (float)c[(size_t)y1 * w + x1];
   return 4.f * ((1.f - fy) * top + fy * bot);
+}
+
+// 16-byte asynchronous global -> shared copy (zero fill when !valid: no bytes are read,
+// `src` is only a placeholder then); every copy of a staging loop is in flight at once.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
 }
 
 constexpr int ETW = 32, ETH = 8;  // output tile of the edge kernels (256 threads)
@@ -113,11 +126,10 @@ __global__ void __launch_bounds__(256) edge_final(const EdgePair* __restrict__ p
     const int q = e % cpx, pix = e / cpx;
     const int r = pix / (ETW + 2), c = pix - r * (ETW + 2);
     const int vy = Y0 - 1 + r, vx = X0 - 1 + c;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (vy >= 0 && vy < P.H && vx >= 0 && vx < P.W)
-      v = *reinterpret_cast<const uint4*>(P.d3 + ((size_t)vy * P.W + vx) * C + q * 8);
-    tile[pix * pstride + q] = v;
+    const bool in = vy >= 0 && vy < P.H && vx >= 0 && vx < P.W;
+    cp_async16(tile + pix * pstride + q, in ? P.d3 + ((size_t)vy * P.W + vx) * C + q * 8 : P.d3, in);
   }
+  cp_async_wait_all();
   __syncthreads();
   const int X = X0 + threadIdx.x, Y = Y0 + threadIdx.y;
   if (X >= P.W || Y >= P.H) return;
@@ -144,59 +156,184 @@ __global__ void __launch_bounds__(256) edge_final(const EdgePair* __restrict__ p
   P.Y[(size_t)Y * P.W + X] = U + acc;
 }
 
-// Exact last row / column of a nearest-x2 + 3x3 conv with an odd output size.  One block
-// per border pixel: the block stages the pixel's 3x3 input neighbourhood (BF16) in shared
-// memory, thread t computes output channel t (and t + blockDim, ...) from the BF16-rounded
-// unfolded weights Wb[co][ky][kx][ci], FP32 accumulation, 8 independent 16-byte weight
-// loads in flight per thread.
-__global__ void __launch_bounds__(128) edge_up2fix(const UpFixPair* __restrict__ pairs, const bf16* __restrict__ Wb,
-                                                   const float* __restrict__ bias, int cin, int cout, int relu) {
-  extern __shared__ __align__(16) uint4 patch[];  // [9][cin / 8]
-  const UpFixPair L = pairs[blockIdx.y];
-  const int nrow = (L.Ho & 1) ? L.Wo : 0;
-  const int ncol = (L.Wo & 1) ? L.Ho : 0;
-  const int pix = blockIdx.x;
-  if (pix >= nrow + ncol) return;
-  int Y, X;
-  if (pix < nrow) {
-    Y = L.Ho - 1;
-    X = pix;
-  } else {
-    Y = pix - nrow;
-    X = L.Wo - 1;
+// final, register-blocked form for C in {16, 32, 64, 128}: TPP = C / 8 threads per output
+// column, each holding the 9 x 8 weights of its 8 channels in registers and computing RPT
+// consecutive output rows of its column, so each staged 8-channel load serves up to three
+// output rows.  Packed FP32 FMA (two channels per instruction); the TPP partial sums of a
+// pixel are added with xor shuffles.  Tile: 32 columns x TH rows, BF16 staged with
+// pixels contiguous (16-byte reads of 8 consecutive lanes hit 8 distinct bank groups).
+template <int C>
+struct FinalGeo {
+  static constexpr int TPP = C / 8, RPT = 8, RGN = TPP >= 8 ? 1 : 8 / TPP;
+  static constexpr int NTH = 32 * TPP * RGN, TW = 32, TH = RPT * RGN, SR = TH + 2, SC = TW + 2;
+  static constexpr size_t smem = sizeof(uint4) * SR * SC * TPP;
+};
+
+template <int C>
+__global__ void __launch_bounds__(FinalGeo<C>::NTH) edge_final_rb(const EdgePair* __restrict__ pairs,
+                                                                 const float* __restrict__ W,
+                                                                 const float* __restrict__ B) {
+  using G = FinalGeo<C>;
+  constexpr int TPP = G::TPP, RPT = G::RPT, TW = G::TW, TH = G::TH, SR = G::SR, SC = G::SC;
+  extern __shared__ __align__(16) uint4 ftile[];  // [SR][SC][TPP]
+  const EdgePair P = pairs[blockIdx.z];
+  const int X0 = blockIdx.x * TW, Y0 = blockIdx.y * TH;
+  if (X0 >= P.W || Y0 >= P.H) return;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < SR * SC * TPP; e += G::NTH) {
+    const int q = e % TPP, pix = e / TPP;
+    const int r = pix / SC, c = pix - r * SC;
+    const int vy = Y0 - 1 + r, vx = X0 - 1 + c;
+    const bool in = vy >= 0 && vy < P.H && vx >= 0 && vx < P.W;
+    cp_async16(ftile + e, in ? P.d3 + ((size_t)vy * P.W + vx) * C + q * 8 : P.d3, in);
   }
-  const int q8 = cin / 8, n = 9 * q8;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int t = e / q8, q = e - t * q8;
-    const int vy = Y + t / 3 - 1, vx = X + t % 3 - 1;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (vy >= 0 && vy < L.Ho && vx >= 0 && vx < L.Wo)
-      v = reinterpret_cast<const uint4*>(L.in + ((size_t)(vy >> 1) * L.Wi + (vx >> 1)) * cin)[q];
-    patch[e] = v;
-  }
+  const int rg = tid / (32 * TPP), rem = tid - rg * 32 * TPP, cx = rem / TPP, q = rem - cx * TPP;
+  float2 w[9][4];
+#pragma unroll
+  for (int t = 0; t < 9; ++t)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[t][j] = make_float2(W[t * C + q * 8 + 2 * j], W[t * C + q * 8 + 2 * j + 1]);
+  cp_async_wait_all();  // the weight loads above overlap the tile copies
   __syncthreads();
-  for (int co = threadIdx.x; co < cout; co += blockDim.x) {
-    const uint4* wp = reinterpret_cast<const uint4*>(Wb + (size_t)co * 9 * cin);
-    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int e0 = 0; e0 < n; e0 += 8) {  // n = 9 * cin / 8 is a multiple of 8 (cin % 64 == 0) or handled below
-      uint4 w[8];
+  float2 acc[RPT];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) w[u] = e0 + u < n ? wp[e0 + u] : make_uint4(0, 0, 0, 0);
+  for (int k = 0; k < RPT; ++k) acc[k] = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (e0 + u >= n) break;
-        const uint4 x = patch[e0 + u];
-        const __nv_bfloat162* wh = reinterpret_cast<const __nv_bfloat162*>(&w[u]);
-        const __nv_bfloat162* xh = reinterpret_cast<const __nv_bfloat162*>(&x);
+  for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float2 wf = __bfloat1622float2(wh[j]), xf = __bfloat1622float2(xh[j]);
-          acc[u] = fmaf(wf.x, xf.x, acc[u]);
-          acc[u] = fmaf(wf.y, xf.y, acc[u]);
+    for (int r = 0; r < RPT + 2; ++r) {
+      const uint4 v = ftile[((rg * RPT + r) * SC + cx + kx) * TPP + q];
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+      float2 a[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a[j] = __bfloat1622float2(h[j]);
+      // staged row r feeds output row k = r - ky of this thread's column
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky) {
+        const int k = r - ky;
+        if (k >= 0 && k < RPT) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[k] = __ffma2_rn(a[j], w[ky * 3 + kx][j], acc[k]);
         }
       }
     }
-    float v = bias[co] + ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  float sum[RPT];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    sum[k] = acc[k].x + acc[k].y;
+#pragma unroll
+    for (int o = TPP / 2; o > 0; o >>= 1) sum[k] += __shfl_xor_sync(0xffffffffu, sum[k], o);
+  }
+  const int X = X0 + cx;
+  if (X >= P.W) return;
+  const float b = B[0];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    if (k % TPP != q) continue;  // the TPP lanes of a column share the rows' epilogue
+    const int Y = Y0 + rg * RPT + k;
+    if (Y >= P.H) break;
+    const float U = P.coarse_f ? upsample4_f(P.coarse_f, P.w, P.h, X, Y) : upsample4_f(P.coarse, P.w, P.h, X, Y);
+    P.Y[(size_t)Y * P.W + X] = U + (b + sum[k]);
+  }
+}
+
+// Exact last row / column of a nearest-x2 + 3x3 conv with an odd (cropped) output size.
+// At those pixels one tap row (column) of the 3x3 window falls on the cropped-away part of
+// the up-sampled map and must read zero, which the 4-phase form cannot express; only the
+// six other taps contribute.  One block per (segment of kUpFixSeg border pixels, 32 output
+// channels, pair), chunks of kFixCk input channels at a time:
+//   S[a][q][c]   the two up-sampled rows (row fix) or columns (column fix) that can be
+//                non-zero, positions p0 - 1 + q along the border, FP32, zero outside the crop
+//   Wf[t][c][o]  the six live taps t = 3a + b of the BF16-rounded weights, FP32
+// Lane = output channel (conflict-free weight reads), warp = 8 consecutive border pixels
+// (broadcast S reads); FP32 accumulation as in the tensor-core form.
+constexpr int kFixCk = 64;
+constexpr int kFixQ = kUpFixSeg + 2;
+constexpr size_t kFixSmem = sizeof(float) * (2 * kFixQ * kFixCk + 6 * kFixCk * 32);
+
+__device__ __forceinline__ void bf16x8_to_f32(const uint4& v, float* d) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float2 f = __bfloat1622float2(h[j]);
+    d[2 * j] = f.x;
+    d[2 * j + 1] = f.y;
+  }
+}
+
+__global__ void __launch_bounds__(256) edge_up2fix(const UpFixPair* __restrict__ pairs, const bf16* __restrict__ Wb,
+                                                   const float* __restrict__ bias, int cin, int cout, int relu) {
+  extern __shared__ __align__(16) float xsm[];
+  float* S = xsm;                          // [2][kFixQ][kFixCk]
+  float* Wf = xsm + 2 * kFixQ * kFixCk;    // [6][kFixCk][32]
+  const UpFixPair L = pairs[blockIdx.z];
+  const int nrow = (L.Ho & 1) ? L.Wo : 0;               // last row, every column
+  const int ncol = (L.Wo & 1) ? L.Ho - (L.Ho & 1) : 0;  // last column, rows above a fixed last row
+  const int segr = (nrow + kUpFixSeg - 1) / kUpFixSeg, segc = (ncol + kUpFixSeg - 1) / kUpFixSeg;
+  int seg = blockIdx.x;
+  if (seg >= segr + segc) return;
+  const bool rowfix = seg < segr;
+  if (!rowfix) seg -= segr;
+  const int p0 = seg * kUpFixSeg;
+  const int npix = min(kUpFixSeg, (rowfix ? nrow : ncol) - p0);
+  const int cb = blockIdx.y * 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+  for (int c0 = 0; c0 < cin; c0 += kFixCk) {
+    const int ck = min(kFixCk, cin - c0), c8 = ck / 8;
+    __syncthreads();  // the previous chunk has been consumed
+    // row fix: up rows Ho-2, Ho-1 (a = ky) x up columns p0-1+q; column fix: up columns
+    // Wo-2, Wo-1 (a = kx) x up rows p0-1+q
+    for (int e = threadIdx.x; e < 2 * kFixQ * c8; e += blockDim.x) {
+      const int a = e / (kFixQ * c8), r = e - a * kFixQ * c8, q = r / c8, u = r - q * c8;
+      const int uy = rowfix ? L.Ho - 2 + a : p0 - 1 + q;
+      const int ux = rowfix ? p0 - 1 + q : L.Wo - 2 + a;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (uy >= 0 && uy < L.Ho && ux >= 0 && ux < L.Wo)
+        v = *reinterpret_cast<const uint4*>(L.in + ((size_t)(uy >> 1) * L.Wi + (ux >> 1)) * cin + c0 + u * 8);
+      bf16x8_to_f32(v, S + ((size_t)a * kFixQ + q) * kFixCk + u * 8);
+    }
+    // tap t = 3a + b: (ky, kx) = (a, b) for the row fix, (b, a) for the column fix
+    for (int e = threadIdx.x; e < 6 * c8 * 32; e += blockDim.x) {
+      const int o = e & 31, r = e >> 5, t = r / c8, u = r - t * c8;
+      const int a = t / 3, b = t - 3 * a, ky = rowfix ? a : b, kx = rowfix ? b : a;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (cb + o < cout)
+        v = *reinterpret_cast<const uint4*>(Wb + ((size_t)((cb + o) * 3 + ky) * 3 + kx) * cin + c0 + u * 8);
+      float f[8];
+      bf16x8_to_f32(v, f);
+      float* d = Wf + ((size_t)t * kFixCk + u * 8) * 32 + o;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) d[j * 32] = f[j];
+    }
+    __syncthreads();
+    for (int t = 0; t < 6; ++t) {
+      const int a = t / 3, b = t - 3 * a;
+      const float* sp = S + ((size_t)a * kFixQ + warp * 8 + b) * kFixCk;
+      const float* wp = Wf + (size_t)t * kFixCk * 32 + lane;
+      for (int c = 0; c < ck; c += 4) {
+        const float w0 = wp[(c + 0) * 32], w1 = wp[(c + 1) * 32], w2 = wp[(c + 2) * 32], w3 = wp[(c + 3) * 32];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float4 x = *reinterpret_cast<const float4*>(sp + j * kFixCk + c);
+          acc[j] = fmaf(w0, x.x, acc[j]);
+          acc[j] = fmaf(w1, x.y, acc[j]);
+          acc[j] = fmaf(w2, x.z, acc[j]);
+          acc[j] = fmaf(w3, x.w, acc[j]);
+        }
+      }
+    }
+  }
+  const int co = cb + lane;
+  if (co >= cout) return;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int p = warp * 8 + j;
+    if (p >= npix) break;
+    const int Y = rowfix ? L.Ho - 1 : p0 + p, X = rowfix ? p0 + p : L.Wo - 1;
+    float v = bias[co] + acc[j];
     if (relu) v = fmaxf(v, 0.f);
     L.out[((size_t)Y * L.Wo + X) * cout + co] = __float2bfloat16_rn(v);
   }
@@ -250,8 +387,22 @@ cudaError_t launch_edge_enc1(const EdgePair* pairs, int n, int maxW1, int maxH1,
 }
 
 template <int C>
+static cudaError_t run_final_rb(const EdgePair* pairs, int n, int maxW, int maxH, const float* W, const float* B,
+                                cudaStream_t st) {
+  using G = FinalGeo<C>;
+  dim3 grid((maxW + G::TW - 1) / G::TW, (maxH + G::TH - 1) / G::TH, n);
+  if (G::smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(edge_final_rb<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
+    if (e != cudaSuccess) return e;
+  }
+  edge_final_rb<C><<<grid, G::NTH, G::smem, st>>>(pairs, W, B);
+  return cudaGetLastError();
+}
+
+template <int C>
 static cudaError_t run_final(const EdgePair* pairs, int n, int maxW, int maxH, const float* W, const float* B,
                              cudaStream_t st) {
+  if constexpr (C == 16 || C == 32 || C == 64 || C == 128) return run_final_rb<C>(pairs, n, maxW, maxH, W, B, st);
   dim3 grid((maxW + ETW - 1) / ETW, (maxH + ETH - 1) / ETH, n);
   const size_t smem = sizeof(uint4) * (ETH + 2) * (ETW + 2) * (C / 8 + 1) + sizeof(float) * 9 * C;
   if (smem > 48 * 1024) {
@@ -275,11 +426,13 @@ cudaError_t launch_edge_final(const EdgePair* pairs, int n, int maxW, int maxH, 
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_edge_up2fix(const UpFixPair* pairs, int n, int max_border, const bf16* Wb, const float* bias,
+cudaError_t launch_edge_up2fix(const UpFixPair* pairs, int n, int max_segments, const bf16* Wb, const float* bias,
                                int cin, int cout, int relu, cudaStream_t st) {
-  dim3 grid((unsigned)std::max(1, max_border), n);
-  const size_t smem = sizeof(uint4) * 9 * (cin / 8);
-  edge_up2fix<<<grid, std::min(128, std::max(32, cout)), smem, st>>>(pairs, Wb, bias, cin, cout, relu);
+  if (cin % 8 != 0) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(edge_up2fix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixSmem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)std::max(1, max_segments), (unsigned)((cout + 31) / 32), (unsigned)n);
+  edge_up2fix<<<grid, 256, kFixSmem, st>>>(pairs, Wb, bias, cin, cout, relu);
   return cudaGetLastError();
 }
 

@@ -92,7 +92,7 @@ def test_autotune_keeps_results_and_caches(svlib, batch, tmp_path):
             assert torch.equal(a, b)
         assert os.path.exists(cache)
         loaded = again.autotune(dps, cache, stream=s)
-        assert loaded["rows"] == choice["rows"] and loaded["nt"] == choice["nt"]
+        assert loaded["rows"] == choice["rows"] and loaded["nt"] == choice["nt"] and loaded["ctas"] == choice["ctas"]
         assert all(u == -1.0 for u in loaded["us"])
         out2 = run(again, dps, s)
         for a, b in zip(out2, ref):
