@@ -645,6 +645,20 @@ static bool make_tmap(CUtensorMap* m, const __nv_bfloat16* base, int C, int npix
             sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// TMA view of a BF16 NHWC map [H][W][C] for a whole-pixel tile: box C x box_w x box_h, no
+// swizzle (pixels contiguous in shared memory), zero fill outside.
+static bool make_tmap_tile(CUtensorMap* m, const __nv_bfloat16* base, int C, int W, int H, int box_w, int box_h) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H};
+  cuuint64_t strides[2] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2};
+  cuuint32_t box[3] = {(cuuint32_t)C, (cuuint32_t)box_w, (cuuint32_t)box_h};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 // BF16 copies of the decoder weights in their canonical [co][3][3][ci] order (border fix),
 // stored after the packed GEMM operands; returns their offsets.
 static size_t unfolded_offsets(const NetDims& net, size_t packed_total, size_t ofs[3]) {
@@ -866,7 +880,10 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
   for (int i = 0; i < n; ++i) {
     const sv_pair& p = pairs[i];
     eps_[i] = {p.left, p.pitch, p.width, p.height, p.width / 4, p.height / 4, coarse ? coarse[i] : nullptr,
-               coarse_f ? coarse_f[i] : nullptr, act(0, i), act(6, i), out[i]};
+               coarse_f ? coarse_f[i] : nullptr, act(0, i), act(6, i), out[i], CUtensorMap{}};
+    if (final_staged_by_tma(net.dec[2]) &&
+        !make_tmap_tile(&eps_[i].d3_map, act(6, i), net.dec[2], p.width, p.height, 34, final_tile_rows(net.dec[2]) + 2))
+      return fail(SV_ERR_CUDA, "pair %d: cuTensorMapEncodeTiled failed (final conv)", i);
     r.maxW = std::max(r.maxW, p.width);
     r.maxH = std::max(r.maxH, p.height);
     r.maxW1 = std::max(r.maxW1, lv[i].W[1]);
@@ -935,7 +952,7 @@ sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream
   {
     LaunchScope ls(*this, "edge_final", st);
     if ((s = cuda(launch_edge_final(d_edges, r.n, r.maxW, r.maxH, W + net.w_off(L_FINAL), W + net.b_off(L_FINAL),
-                                    net.dec[2], st),
+                                    net.dec[2], (int*)err_flag.p, spin_limit, st),
                   "final")))
       return s;
   }

@@ -478,8 +478,8 @@ sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream) {
     return s;
   if (code) {
     cudaMemset(c->err_flag.p, 0, sizeof(int));
-    static const char* where[] = {"", "producer", "MMA issuer", "MMA drain", "epilogue", "copy drain"};
-    return c->fail(SV_ERR_TIMEOUT, "a device-side wait ran out (%s, code %d)", code >= 1 && code <= 5 ? where[code] : "?",
+    static const char* where[] = {"", "producer", "MMA issuer", "MMA drain", "epilogue", "copy drain", "final-conv staging"};
+    return c->fail(SV_ERR_TIMEOUT, "a device-side wait ran out (%s, code %d)", code >= 1 && code <= 6 ? where[code] : "?",
                    code);
   }
   return SV_OK;

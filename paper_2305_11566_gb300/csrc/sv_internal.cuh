@@ -2,6 +2,7 @@
 // the StereoVAE library (context, device descriptors, kernel launchers).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <array>
@@ -133,7 +134,7 @@ cudaError_t launch_final(const T* in, int W, int H, int Ci, const T* wt, const T
                          int w, int h, OutT* Y, cudaStream_t st);
 
 // Per-pair descriptors of the batched CUDA-core layers of the tensor-core form.
-struct EdgePair {
+struct alignas(64) EdgePair {
   const uint8_t* L;
   int pitch, W, H, w, h;
   const int16_t* coarse;    // integer coarse map (inference), or
@@ -141,7 +142,12 @@ struct EdgePair {
   __nv_bfloat16* e1;        // enc1 output [H1][W1][C1]
   const __nv_bfloat16* d3;  // last decoder output [H][W][C]
   float* Y;                 // refined disparity [H][W]
+  CUtensorMap d3_map;       // TMA view of d3 for the final conv (final_staged_by_tma(C))
 };
+// Final conv of the tensor-core form: widths with the register-blocked kernel stage their
+// (rows + 2) x 34 x C input tile with one TMA box; its height in output rows per block.
+inline bool final_staged_by_tma(int C) { return C == 16 || C == 32 || C == 64 || C == 128; }
+inline int final_tile_rows(int C) { return 16 * (C / 8 >= 8 ? 1 : 8 / (C / 8)); }
 struct UpFixPair {          // one decoder layer of one pair (input, output, sizes)
   const __nv_bfloat16* in;
   __nv_bfloat16* out;
@@ -150,7 +156,7 @@ struct UpFixPair {          // one decoder layer of one pair (input, output, siz
 cudaError_t launch_edge_enc1(const EdgePair* pairs, int n, int maxW1, int maxH1, const float* W, const float* B, int C1,
                              cudaStream_t st);
 cudaError_t launch_edge_final(const EdgePair* pairs, int n, int maxW, int maxH, const float* W, const float* B, int C,
-                              cudaStream_t st);
+                              int* err, long long spin, cudaStream_t st);
 // Border pixels of a cropped nearest-x2 + 3x3 conv output that the 4-phase form folds
 // wrongly: the last row when Ho is odd, the last column (above that row) when Wo is odd.
 // The fix kernel takes them in segments of kUpFixSeg pixels, one block per segment.

@@ -160,46 +160,107 @@ __global__ void __launch_bounds__(256) edge_final(const EdgePair* __restrict__ p
 // column, each holding the 9 x 8 weights of its 8 channels in registers and computing RPT
 // consecutive output rows of its column, so each staged 8-channel load serves up to three
 // output rows.  Packed FP32 FMA (two channels per instruction); the TPP partial sums of a
-// pixel are added with xor shuffles.  Tile: 32 columns x TH rows, BF16 staged with
-// pixels contiguous (16-byte reads of 8 consecutive lanes hit 8 distinct bank groups).
+// pixel are added with xor shuffles.  Tile: 32 columns x TH rows; its (TH + 2) x 34 x C
+// BF16 input (pixels contiguous: the 16-byte reads of 8 consecutive lanes hit 8 distinct
+// bank groups) arrives by one TMA box, zero-filled outside the map.
 template <int C>
 struct FinalGeo {
-  static constexpr int TPP = C / 8, RPT = 8, RGN = TPP >= 8 ? 1 : 8 / TPP;
+  static constexpr int TPP = C / 8, RPT = 16, RGN = TPP >= 8 ? 1 : 8 / TPP;
   static constexpr int NTH = 32 * TPP * RGN, TW = 32, TH = RPT * RGN, SR = TH + 2, SC = TW + 2;
-  static constexpr size_t smem = sizeof(uint4) * SR * SC * TPP;
+  static constexpr uint32_t tile_bytes = (uint32_t)SR * SC * C * 2;
+  static constexpr size_t smem = tile_bytes + 128 + 9 * C * 4;  // tile (+ alignment slack), FP32 weights
 };
+
+__device__ __forceinline__ bool mbar_try_e(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait_e(uint32_t bar, uint32_t parity, long long spin) {
+  if (mbar_try_e(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_e(bar, parity))
+    if (clock64() - t0 > spin) return false;
+  return true;
+}
 
 template <int C>
 __global__ void __launch_bounds__(FinalGeo<C>::NTH) edge_final_rb(const EdgePair* __restrict__ pairs,
                                                                  const float* __restrict__ W,
-                                                                 const float* __restrict__ B) {
+                                                                 const float* __restrict__ B, int* err,
+                                                                 long long spin) {
   using G = FinalGeo<C>;
-  constexpr int TPP = G::TPP, RPT = G::RPT, TW = G::TW, TH = G::TH, SR = G::SR, SC = G::SC;
-  extern __shared__ __align__(16) uint4 ftile[];  // [SR][SC][TPP]
-  const EdgePair P = pairs[blockIdx.z];
+  constexpr int TPP = G::TPP, RPT = G::RPT, TW = G::TW, TH = G::TH, SC = G::SC;
+  extern __shared__ unsigned char fraw[];
+  __shared__ __align__(8) uint64_t fbar;
+  const EdgePair* P = pairs + blockIdx.z;
+  const int Wd = P->W, Hd = P->H;
   const int X0 = blockIdx.x * TW, Y0 = blockIdx.y * TH;
-  if (X0 >= P.W || Y0 >= P.H) return;
+  if (X0 >= Wd || Y0 >= Hd) return;
+  const uint32_t tile_s = ((uint32_t)__cvta_generic_to_shared(fraw) + 127u) & ~127u;
+  const uint4* ftile = reinterpret_cast<const uint4*>(fraw + (tile_s - (uint32_t)__cvta_generic_to_shared(fraw)));
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&fbar);
   const int tid = threadIdx.x;
-  for (int e = tid; e < SR * SC * TPP; e += G::NTH) {
-    const int q = e % TPP, pix = e / TPP;
-    const int r = pix / SC, c = pix - r * SC;
-    const int vy = Y0 - 1 + r, vx = X0 - 1 + c;
-    const bool in = vy >= 0 && vy < P.H && vx >= 0 && vx < P.W;
-    cp_async16(ftile + e, in ? P.d3 + ((size_t)vy * P.W + vx) * C + q * 8 : P.d3, in);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(&P->d3_map))
+                 : "memory");
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+                 "r"(G::tile_bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            tile_s),
+        "l"(reinterpret_cast<uint64_t>(&P->d3_map)), "r"(0), "r"(X0 - 1), "r"(Y0 - 1), "r"(bar)
+        : "memory");
   }
   const int rg = tid / (32 * TPP), rem = tid - rg * 32 * TPP, cx = rem / TPP, q = rem - cx * TPP;
-  float2 w[9][4];
+  float* ws = reinterpret_cast<float*>(fraw + 128 + G::tile_bytes);  // [9][C]
+  for (int e = tid; e < 9 * C; e += G::NTH) ws[e] = W[e];
+  // residual U (bilinear x4 of the coarse map) of the rows this lane writes, k = q + e TPP:
+  // its global loads overlap the tile copy
+  constexpr int NE = (RPT + TPP - 1) / TPP;
+  const int X = X0 + cx;
+  float Ue[NE];
+  {
+    const int16_t* coarse = P->coarse;
+    const float* coarse_f = P->coarse_f;
+    const int w4 = P->w, h4 = P->h;
+    const int Xc = min(X, Wd - 1);
 #pragma unroll
-  for (int t = 0; t < 9; ++t)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) w[t][j] = make_float2(W[t * C + q * 8 + 2 * j], W[t * C + q * 8 + 2 * j + 1]);
-  cp_async_wait_all();  // the weight loads above overlap the tile copies
-  __syncthreads();
+    for (int e = 0; e < NE; ++e) {
+      const int Yr = min(Y0 + rg * RPT + q + e * TPP, Hd - 1);
+      Ue[e] = coarse_f ? upsample4_f(coarse_f, w4, h4, Xc, Yr) : upsample4_f(coarse, w4, h4, Xc, Yr);
+    }
+  }
+  __syncthreads();  // barrier initialised
+  if (!mbar_wait_e(bar, 0, spin)) {
+    atomicCAS(err, 0, 6);
+    // the copy may still land: no thread leaves while it can write this block's memory
+    mbar_wait_e(bar, 0, spin > 2000000000LL ? spin : 2000000000LL);
+    return;
+  }
   float2 acc[RPT];
 #pragma unroll
   for (int k = 0; k < RPT; ++k) acc[k] = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int kx = 0; kx < 3; ++kx)
+  for (int kx = 0; kx < 3; ++kx) {
+    // this lane's 8 channels of the three taps of column kx (broadcast reads)
+    float2 w[3][4];
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) {
+      const float4 lo = *reinterpret_cast<const float4*>(ws + (ky * 3 + kx) * C + q * 8);
+      const float4 hi = *reinterpret_cast<const float4*>(ws + (ky * 3 + kx) * C + q * 8 + 4);
+      w[ky][0] = make_float2(lo.x, lo.y);
+      w[ky][1] = make_float2(lo.z, lo.w);
+      w[ky][2] = make_float2(hi.x, hi.y);
+      w[ky][3] = make_float2(hi.z, hi.w);
+    }
 #pragma unroll
     for (int r = 0; r < RPT + 2; ++r) {
       const uint4 v = ftile[((rg * RPT + r) * SC + cx + kx) * TPP + q];
@@ -213,10 +274,11 @@ __global__ void __launch_bounds__(FinalGeo<C>::NTH) edge_final_rb(const EdgePair
         const int k = r - ky;
         if (k >= 0 && k < RPT) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[k] = __ffma2_rn(a[j], w[ky * 3 + kx][j], acc[k]);
+          for (int j = 0; j < 4; ++j) acc[k] = __ffma2_rn(a[j], w[ky][j], acc[k]);
         }
       }
     }
+  }
   float sum[RPT];
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
@@ -224,16 +286,15 @@ __global__ void __launch_bounds__(FinalGeo<C>::NTH) edge_final_rb(const EdgePair
 #pragma unroll
     for (int o = TPP / 2; o > 0; o >>= 1) sum[k] += __shfl_xor_sync(0xffffffffu, sum[k], o);
   }
-  const int X = X0 + cx;
-  if (X >= P.W) return;
+  if (X >= Wd) return;
   const float b = B[0];
+  float* Y = P->Y;
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
     if (k % TPP != q) continue;  // the TPP lanes of a column share the rows' epilogue
-    const int Y = Y0 + rg * RPT + k;
-    if (Y >= P.H) break;
-    const float U = P.coarse_f ? upsample4_f(P.coarse_f, P.w, P.h, X, Y) : upsample4_f(P.coarse, P.w, P.h, X, Y);
-    P.Y[(size_t)Y * P.W + X] = U + (b + sum[k]);
+    const int Yr = Y0 + rg * RPT + k;
+    if (Yr >= Hd) break;
+    Y[(size_t)Yr * Wd + X] = Ue[k / TPP] + (b + sum[k]);
   }
 }
 
@@ -388,21 +449,23 @@ cudaError_t launch_edge_enc1(const EdgePair* pairs, int n, int maxW1, int maxH1,
 
 template <int C>
 static cudaError_t run_final_rb(const EdgePair* pairs, int n, int maxW, int maxH, const float* W, const float* B,
-                                cudaStream_t st) {
+                                int* err, long long spin, cudaStream_t st) {
   using G = FinalGeo<C>;
+  static_assert(G::TH == 16 * (C / 8 >= 8 ? 1 : 8 / (C / 8)), "tile height must match final_tile_rows()");
   dim3 grid((maxW + G::TW - 1) / G::TW, (maxH + G::TH - 1) / G::TH, n);
   if (G::smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(edge_final_rb<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
     if (e != cudaSuccess) return e;
   }
-  edge_final_rb<C><<<grid, G::NTH, G::smem, st>>>(pairs, W, B);
+  edge_final_rb<C><<<grid, G::NTH, G::smem, st>>>(pairs, W, B, err, spin);
   return cudaGetLastError();
 }
 
 template <int C>
 static cudaError_t run_final(const EdgePair* pairs, int n, int maxW, int maxH, const float* W, const float* B,
-                             cudaStream_t st) {
-  if constexpr (C == 16 || C == 32 || C == 64 || C == 128) return run_final_rb<C>(pairs, n, maxW, maxH, W, B, st);
+                             int* err, long long spin, cudaStream_t st) {
+  if constexpr (C == 16 || C == 32 || C == 64 || C == 128)
+    return run_final_rb<C>(pairs, n, maxW, maxH, W, B, err, spin, st);
   dim3 grid((maxW + ETW - 1) / ETW, (maxH + ETH - 1) / ETH, n);
   const size_t smem = sizeof(uint4) * (ETH + 2) * (ETW + 2) * (C / 8 + 1) + sizeof(float) * 9 * C;
   if (smem > 48 * 1024) {
@@ -414,10 +477,10 @@ static cudaError_t run_final(const EdgePair* pairs, int n, int maxW, int maxH, c
 }
 
 cudaError_t launch_edge_final(const EdgePair* pairs, int n, int maxW, int maxH, const float* W, const float* B, int C,
-                              cudaStream_t st) {
+                              int* err, long long spin, cudaStream_t st) {
   switch (C) {  // decoder widths are multiples of 16 up to 256
 #define SV_FINAL_CASE(c) \
-  case c: return run_final<c>(pairs, n, maxW, maxH, W, B, st);
+  case c: return run_final<c>(pairs, n, maxW, maxH, W, B, err, spin, st);
     SV_FINAL_CASE(16) SV_FINAL_CASE(32) SV_FINAL_CASE(48) SV_FINAL_CASE(64) SV_FINAL_CASE(80) SV_FINAL_CASE(96)
     SV_FINAL_CASE(112) SV_FINAL_CASE(128) SV_FINAL_CASE(144) SV_FINAL_CASE(160) SV_FINAL_CASE(176) SV_FINAL_CASE(192)
     SV_FINAL_CASE(208) SV_FINAL_CASE(224) SV_FINAL_CASE(240) SV_FINAL_CASE(256)
