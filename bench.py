@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--train-pairs", type=int, default=16)
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch plans (fixed launch order, e.g. for profiler captures)")
+    ap.add_argument("--tc-ctas", type=int, default=0,
+                    help="with --no-tune: CTAs per SM every tensor-core layer is planned for (0 = deepest ring)")
     return ap.parse_args()
 
 
@@ -219,6 +221,8 @@ def run_ours(args):
     for form in forms:
         ctx = binding.Context(shape, WIN, form, dev)
         ctx.set_weights(params)
+        if form == "bf16" and args.tc_ctas:
+            ctx.set_option("tc_ctas_per_sm", args.tc_ctas)
         outs = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in range(B)]
         try:
             with torch.cuda.stream(st):

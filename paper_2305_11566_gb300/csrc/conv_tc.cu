@@ -346,6 +346,10 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       // 8 output channels x cin
       constexpr uint32_t a_hi = desc_hi(8 * RB, swz_layout(RB));
       const uint32_t b_hi = desc_hi((uint32_t)cin * 16, 0);
+      // B descriptors (K step 0) of every tap: fixed for the CTA's lifetime
+      uint32_t b0[T];
+#pragma unroll
+      for (int t = 0; t < T; ++t) b0[t] = desc_lo(sB + t * bsz, 128);
       uint32_t tseq = 0;
       RingPos wt;  // next row to wait for (rows are waited for in load order)
       RingPos tb;  // slot of the first row of the current tile
@@ -376,28 +380,29 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
             const uint32_t sl = tb.slot + r;
             slot_of_row[r] = sA + (sl >= ring ? sl - ring : sl) * rowb;
           }
-          uint32_t acc = 0;
+          // A descriptors (K step 0) of every tap for this tile's staged rows; all MMAs
+          // of a channel block then issue back to back from independent additions
+          uint32_t a0[T];
 #pragma unroll
           for (int t = 0; t < T; ++t) {
             int ro, se, co;
             tap_geo<MODE>(t, ro, se, co);
-            uint32_t alo = desc_lo(slot_of_row[ro] + (uint32_t)(se * KB) * KBS + (uint32_t)co * RB, 16);
-            uint32_t blo = desc_lo(sB + t * bsz, 128);
-            for (int kb = 0; kb < KB; ++kb) {
-#pragma unroll
-              for (int k4 = 0; k4 < KPR; ++k4) {
-                // next 16 channels: +32 B inside the swizzled pixel row, +256 B in B
-                mma_bf16(dcol, alo + 2 * k4, a_hi, blo + 16 * k4, b_hi, idesc, acc);
-                acc = 1;
-              }
-              alo += KBS >> 4;
-              blo += 16 * KPR;
-            }
+            a0[t] = desc_lo(slot_of_row[ro] + (uint32_t)(se * KB) * KBS + (uint32_t)co * RB, 16);
           }
-          mma_commit(accf0 + 8 * buf);
-          // release the rows the next tile of this strip no longer reads
-          const int rel_hi = ii + 1 < st.cnt ? STEP * (ii + 1) : nrows;
-          for (int r = STEP * ii; r < rel_hi; ++r, tb.next(ring)) mma_commit(empty0 + 8 * tb.slot);
+          for (int kb = 0; kb < KB; ++kb) {
+            const uint32_t ak = (uint32_t)kb * (KBS >> 4), bk = (uint32_t)kb * (16 * KPR);
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+#pragma unroll
+              for (int k4 = 0; k4 < KPR; ++k4)
+                // next 16 channels: +32 B inside the swizzled pixel row, +256 B in B
+                mma_bf16(dcol, a0[t] + ak + 2 * k4, a_hi, b0[t] + bk + 16 * k4, b_hi, idesc,
+                         (kb | t | k4) != 0 ? 1u : 0u);
+          }
+          mma_commit(accf0 + 8 * buf);  // also releases the tile's rows (the epilogue arrives)
+          tb.slot += STEP;            // first row of the next tile (the strip's last tile: + RA)
+          if (ii + 1 == st.cnt) tb.slot += RA - STEP;
+          while (tb.slot >= ring) tb.slot -= ring;
           ++tseq;
         }
       }
@@ -414,11 +419,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
     // ------------------------------------------------------------ epilogue (warps 0-3)
     const int m = warp * 32 + lane;
     uint32_t tseq = 0;
+    RingPos rel;  // thread 0: slot of the next staged row to hand back to the producer
     for (int s = crank; s < p.n_strips && ok; s += cpg) {
       const Strip st = p.strips[s];
       const LayerPair* L = p.lp + st.pair;
       const int Hu = L->Hu, Wu = L->Wu, Ho = L->Ho, Wo = L->Wo;
       bf16* const out = L->out;
+      const int nrows = STEP * (st.cnt - 1) + RA;
       for (int ii = 0; ii < st.cnt; ++ii, ++tseq) {
         const uint32_t buf = tseq & 1;
         if (!mbar_wait(accf0 + 8 * buf, (tseq >> 1) & 1, p.spin)) {
@@ -427,6 +434,12 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
           break;
         }
         tc_fence_after();
+        if (tid == 0) {
+          // the tile's MMAs have completed: the rows the next tile of the strip no longer
+          // reads can be reloaded
+          const int rel_hi = ii + 1 < st.cnt ? STEP * (ii + 1) : nrows;
+          for (int r = STEP * ii; r < rel_hi; ++r, rel.next(ring)) mbar_arrive(empty0 + 8 * rel.slot);
+        }
         const int i = st.i0 + ii, j = st.j0 + m;
         const int oy = MODE == TM_UP2 ? 2 * i + py : i;
         const int ox = MODE == TM_UP2 ? 2 * j + px : j;

@@ -3,7 +3,7 @@
 //
 //   edge_enc1    first conv (3x3 stride 2, 2 -> C1, ReLU) with its input built while
 //                staging: x0 = (L / 256, U / 256), U = 4 * bilinear(coarse) (a5, a6, a7).
-//                FP32 arithmetic, BF16 NHWC output.
+//                FP32 arithmetic, BF16 NHWC output; 4 output rows per thread.
 //   edge_final   last conv (3x3, C -> 1) + bias + U (residual), BF16 input, FP32 output (a11);
 //                register-blocked packed-FP32 form for C = 16, 32, 64, 128.
 //   edge_up2fix  exact recomputation of the last row / column of an odd-sized (cropped)
@@ -43,67 +43,152 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 constexpr int ETW = 32, ETH = 8;  // output tile of the edge kernels (256 threads)
 
-// enc1: 17 x 65 x 2 input tile in shared memory, weights [18][C1] (broadcast), one output
-// pixel and all C1 channels per thread.
+// enc1, register-blocked: a block computes 32 output columns x 32 output rows; thread
+// (cx, g) computes rows 4g .. 4g + 3 of column cx for 8 channels at a time, so each
+// broadcast weight read feeds four pixels.  Its input, x0 = (L / 256, U / 256) on the
+// 65 x 65 positions the tile reads, is staged in shared memory; U (bilinear x4 of the
+// coarse map) is separable: the coarse rows the tile touches are interpolated along x
+// once (T), then every position interpolates T along y.  The four rows' overlapping
+// 9 x 3 x 2 input window sits in registers.
+constexpr int E1W = 32, E1H = 32, E1R = 2 * E1H + 1, E1C = 2 * E1W + 1, E1CR = 20;
+
+template <typename CT>
+__device__ __forceinline__ void coarse_axis(float v, int n, int& i0, int& i1, float& f) {
+  float s = v * 0.25f - 0.375f;
+  s = fminf(fmaxf(s, 0.f), (float)(n - 1));
+  i0 = (int)s;
+  i1 = min(i0 + 1, n - 1);
+  f = s - (float)i0;
+}
+
+template <typename CT>
+__device__ __forceinline__ void enc1_stage(const EdgePair* P, const CT* __restrict__ cmap, int X0, int Y0,
+                                           float (*xs)[E1C][2], float (*T)[E1C]) {
+  const int Wd = P->W, Hd = P->H, w4 = P->w, h4 = P->h, pitch = P->pitch;
+  const uint8_t* Lp = P->L;
+  int cy_lo, dummy;
+  float fdummy;
+  coarse_axis<CT>((float)max(0, 2 * Y0 - 1), h4, cy_lo, dummy, fdummy);
+  // every load of a pass is issued before any is used (one memory round trip per pass)
+  constexpr int NTT = (E1CR * E1C + 255) / 256, NXS = (E1R * E1C + 255) / 256;
+  {
+    float c0v[NTT], c1v[NTT], fxv[NTT];
+#pragma unroll
+    for (int i = 0; i < NTT; ++i) {
+      const int e = min((int)threadIdx.x + 256 * i, E1CR * E1C - 1);
+      const int ry = e / E1C, c = e - ry * E1C;
+      const int cy = min(cy_lo + ry, h4 - 1);
+      const int vx = min(max(2 * X0 - 1 + c, 0), Wd - 1);
+      int x0, x1;
+      coarse_axis<CT>((float)vx, w4, x0, x1, fxv[i]);
+      c0v[i] = (float)cmap[(size_t)cy * w4 + x0];
+      c1v[i] = (float)cmap[(size_t)cy * w4 + x1];
+    }
+#pragma unroll
+    for (int i = 0; i < NTT; ++i) {
+      const int e = (int)threadIdx.x + 256 * i;
+      if (e < E1CR * E1C) T[e / E1C][e % E1C] = (1.f - fxv[i]) * c0v[i] + fxv[i] * c1v[i];
+    }
+  }
+  uint32_t lv[NXS];
+#pragma unroll
+  for (int i = 0; i < NXS; ++i) {
+    const int e = (int)threadIdx.x + 256 * i;
+    const int r = e / E1C, c = e - r * E1C;
+    const int vy = 2 * Y0 - 1 + r, vx = 2 * X0 - 1 + c;
+    lv[i] = (e < E1R * E1C && vy >= 0 && vy < Hd && vx >= 0 && vx < Wd) ? (uint32_t)Lp[(size_t)vy * pitch + vx] : 256u;
+  }
+  __syncthreads();  // T complete
+#pragma unroll
+  for (int i = 0; i < NXS; ++i) {
+    const int e = (int)threadIdx.x + 256 * i;
+    if (e >= E1R * E1C) break;
+    const int r = e / E1C, c = e - r * E1C;
+    const int vy = 2 * Y0 - 1 + r;
+    float l = 0.f, u = 0.f;
+    if (lv[i] != 256u) {  // inside the image
+      int y0, y1;
+      float fy;
+      coarse_axis<CT>((float)vy, h4, y0, y1, fy);
+      l = (float)lv[i] * (1.f / 256.f);
+      u = 4.f * ((1.f - fy) * T[y0 - cy_lo][c] + fy * T[y1 - cy_lo][c]) * (1.f / 256.f);
+    }
+    xs[r][c][0] = l;
+    xs[r][c][1] = u;
+  }
+}
+
 __global__ void __launch_bounds__(256) edge_enc1(const EdgePair* __restrict__ pairs, const float* __restrict__ W,
                                                  const float* __restrict__ B, int C1) {
-  constexpr int TR = 2 * ETH + 1, TC = 2 * ETW + 1;
-  __shared__ float x0[TR][TC][2];
+  // blockDim.x must be 256 (the staging passes are unrolled for it)
+  __shared__ float xs[E1R][E1C][2];
+  __shared__ float T[E1CR][E1C];
   extern __shared__ __align__(16) float wsm[];  // [18][C1] then bias[C1]
-  const EdgePair P = pairs[blockIdx.z];
-  const int H1 = (P.H + 1) / 2, W1 = (P.W + 1) / 2;
-  const int X0 = blockIdx.x * ETW, Y0 = blockIdx.y * ETH;
+  const EdgePair* P = pairs + blockIdx.z;
+  const int H1 = (P->H + 1) / 2, W1 = (P->W + 1) / 2;
+  const int X0 = blockIdx.x * E1W, Y0 = blockIdx.y * E1H;
   if (X0 >= W1 || Y0 >= H1) return;
-  const int tid = threadIdx.y * ETW + threadIdx.x;
-  for (int e = tid; e < 18 * C1; e += 256) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 18 * C1; e += blockDim.x) {
     const int co = e % C1, k = e / C1;  // k = tap * 2 + channel
     wsm[e] = W[(size_t)co * 18 + k];
   }
-  for (int e = tid; e < C1; e += 256) wsm[18 * C1 + e] = B[e];
-  for (int e = tid; e < TR * TC; e += 256) {
-    const int r = e / TC, c = e - r * TC;
-    const int vy = 2 * Y0 - 1 + r, vx = 2 * X0 - 1 + c;
-    float l = 0.f, u = 0.f;
-    if (vy >= 0 && vy < P.H && vx >= 0 && vx < P.W) {
-      l = (float)P.L[(size_t)vy * P.pitch + vx] * (1.f / 256.f);
-      u = (P.coarse_f ? upsample4_f(P.coarse_f, P.w, P.h, vx, vy) : upsample4_f(P.coarse, P.w, P.h, vx, vy)) *
-          (1.f / 256.f);
-    }
-    x0[r][c][0] = l;
-    x0[r][c][1] = u;
-  }
+  for (int e = tid; e < C1; e += blockDim.x) wsm[18 * C1 + e] = B[e];
+  if (P->coarse_f) enc1_stage(P, P->coarse_f, X0, Y0, xs, T);
+  else enc1_stage(P, P->coarse, X0, Y0, xs, T);
   __syncthreads();
-  const int X = X0 + threadIdx.x, Y = Y0 + threadIdx.y;
-  if (X >= W1 || Y >= H1) return;
-  float xin[18];
+  const int cx = tid & 31, g = tid >> 5;
+  const int X = X0 + cx;
+  // input window of rows 4g .. 4g + 3: staged rows 8g .. 8g + 8, columns 2cx .. 2cx + 2
+  float xv[9][3][2];
 #pragma unroll
-  for (int ky = 0; ky < 3; ++ky)
+  for (int r = 0; r < 9; ++r)
 #pragma unroll
     for (int kx = 0; kx < 3; ++kx) {
-      xin[(ky * 3 + kx) * 2] = x0[2 * threadIdx.y + ky][2 * threadIdx.x + kx][0];
-      xin[(ky * 3 + kx) * 2 + 1] = x0[2 * threadIdx.y + ky][2 * threadIdx.x + kx][1];
+      const float2 v = *reinterpret_cast<const float2*>(&xs[8 * g + r][2 * cx + kx][0]);
+      xv[r][kx][0] = v.x;
+      xv[r][kx][1] = v.y;
     }
-  bf16* out = P.e1 + ((size_t)Y * W1 + X) * C1;
   for (int c0 = 0; c0 < C1; c0 += 8) {
-    float acc[8];
+    float acc[4][8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = wsm[18 * C1 + c0 + j];
+    for (int j = 0; j < 8; ++j) {
+      const float bj = wsm[18 * C1 + c0 + j];
 #pragma unroll
-    for (int k = 0; k < 18; ++k) {
-      const float4 a = *reinterpret_cast<const float4*>(&wsm[k * C1 + c0]);
-      const float4 b = *reinterpret_cast<const float4*>(&wsm[k * C1 + c0 + 4]);
-      acc[0] = fmaf(a.x, xin[k], acc[0]); acc[1] = fmaf(a.y, xin[k], acc[1]);
-      acc[2] = fmaf(a.z, xin[k], acc[2]); acc[3] = fmaf(a.w, xin[k], acc[3]);
-      acc[4] = fmaf(b.x, xin[k], acc[4]); acc[5] = fmaf(b.y, xin[k], acc[5]);
-      acc[6] = fmaf(b.z, xin[k], acc[6]); acc[7] = fmaf(b.w, xin[k], acc[7]);
+      for (int k = 0; k < 4; ++k) acc[k][j] = bj;
     }
-    uint32_t pk[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(acc[2 * j], 0.f), fmaxf(acc[2 * j + 1], 0.f));
-      pk[j] = *reinterpret_cast<uint32_t*>(&h);
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+          const int kk = (ky * 3 + kx) * 2 + ch;
+          const float4 a = *reinterpret_cast<const float4*>(&wsm[kk * C1 + c0]);
+          const float4 b = *reinterpret_cast<const float4*>(&wsm[kk * C1 + c0 + 4]);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float x = xv[2 * k + ky][kx][ch];
+            acc[k][0] = fmaf(a.x, x, acc[k][0]); acc[k][1] = fmaf(a.y, x, acc[k][1]);
+            acc[k][2] = fmaf(a.z, x, acc[k][2]); acc[k][3] = fmaf(a.w, x, acc[k][3]);
+            acc[k][4] = fmaf(b.x, x, acc[k][4]); acc[k][5] = fmaf(b.y, x, acc[k][5]);
+            acc[k][6] = fmaf(b.z, x, acc[k][6]); acc[k][7] = fmaf(b.w, x, acc[k][7]);
+          }
+        }
+    if (X < W1) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int Y = Y0 + 4 * g + k;
+        if (Y >= H1) break;
+        uint32_t pk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(acc[k][2 * j], 0.f), fmaxf(acc[k][2 * j + 1], 0.f));
+          pk[j] = *reinterpret_cast<uint32_t*>(&h);
+        }
+        *reinterpret_cast<uint4*>(P->e1 + ((size_t)Y * W1 + X) * C1 + c0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
     }
-    *reinterpret_cast<uint4*>(out + c0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
 }
 
@@ -347,27 +432,51 @@ __global__ void __launch_bounds__(256) edge_up2fix(const UpFixPair* __restrict__
     __syncthreads();  // the previous chunk has been consumed
     // row fix: up rows Ho-2, Ho-1 (a = ky) x up columns p0-1+q; column fix: up columns
     // Wo-2, Wo-1 (a = kx) x up rows p0-1+q
-    for (int e = threadIdx.x; e < 2 * kFixQ * c8; e += blockDim.x) {
-      const int a = e / (kFixQ * c8), r = e - a * kFixQ * c8, q = r / c8, u = r - q * c8;
-      const int uy = rowfix ? L.Ho - 2 + a : p0 - 1 + q;
-      const int ux = rowfix ? p0 - 1 + q : L.Wo - 2 + a;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (uy >= 0 && uy < L.Ho && ux >= 0 && ux < L.Wo)
-        v = *reinterpret_cast<const uint4*>(L.in + ((size_t)(uy >> 1) * L.Wi + (ux >> 1)) * cin + c0 + u * 8);
-      bf16x8_to_f32(v, S + ((size_t)a * kFixQ + q) * kFixCk + u * 8);
+    // loads of 4 elements per thread are issued before any is converted and stored
+    constexpr int U = 4;
+    for (int e0 = threadIdx.x; e0 < 2 * kFixQ * c8; e0 += U * blockDim.x) {
+      uint4 v[U];
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int e = e0 + i * (int)blockDim.x;
+        const int a = e / (kFixQ * c8), r = e - a * kFixQ * c8, q = r / c8, u = r - q * c8;
+        const int uy = rowfix ? L.Ho - 2 + a : p0 - 1 + q;
+        const int ux = rowfix ? p0 - 1 + q : L.Wo - 2 + a;
+        v[i] = make_uint4(0, 0, 0, 0);
+        if (e < 2 * kFixQ * c8 && uy >= 0 && uy < L.Ho && ux >= 0 && ux < L.Wo)
+          v[i] = *reinterpret_cast<const uint4*>(L.in + ((size_t)(uy >> 1) * L.Wi + (ux >> 1)) * cin + c0 + u * 8);
+      }
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int e = e0 + i * (int)blockDim.x;
+        if (e >= 2 * kFixQ * c8) break;
+        const int a = e / (kFixQ * c8), r = e - a * kFixQ * c8, q = r / c8, u = r - q * c8;
+        bf16x8_to_f32(v[i], S + ((size_t)a * kFixQ + q) * kFixCk + u * 8);
+      }
     }
     // tap t = 3a + b: (ky, kx) = (a, b) for the row fix, (b, a) for the column fix
-    for (int e = threadIdx.x; e < 6 * c8 * 32; e += blockDim.x) {
-      const int o = e & 31, r = e >> 5, t = r / c8, u = r - t * c8;
-      const int a = t / 3, b = t - 3 * a, ky = rowfix ? a : b, kx = rowfix ? b : a;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (cb + o < cout)
-        v = *reinterpret_cast<const uint4*>(Wb + ((size_t)((cb + o) * 3 + ky) * 3 + kx) * cin + c0 + u * 8);
-      float f[8];
-      bf16x8_to_f32(v, f);
-      float* d = Wf + ((size_t)t * kFixCk + u * 8) * 32 + o;
+    for (int e0 = threadIdx.x; e0 < 6 * c8 * 32; e0 += U * blockDim.x) {
+      uint4 v[U];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) d[j * 32] = f[j];
+      for (int i = 0; i < U; ++i) {
+        const int e = e0 + i * (int)blockDim.x;
+        const int o = e & 31, r = e >> 5, t = r / c8, u = r - t * c8;
+        const int a = t / 3, b = t - 3 * a, ky = rowfix ? a : b, kx = rowfix ? b : a;
+        v[i] = make_uint4(0, 0, 0, 0);
+        if (e < 6 * c8 * 32 && cb + o < cout)
+          v[i] = *reinterpret_cast<const uint4*>(Wb + ((size_t)((cb + o) * 3 + ky) * 3 + kx) * cin + c0 + u * 8);
+      }
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int e = e0 + i * (int)blockDim.x;
+        if (e >= 6 * c8 * 32) break;
+        const int o = e & 31, r = e >> 5, t = r / c8, u = r - t * c8;
+        float f[8];
+        bf16x8_to_f32(v[i], f);
+        float* d = Wf + ((size_t)t * kFixCk + u * 8) * 32 + o;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[j * 32] = f[j];
+      }
     }
     __syncthreads();
     for (int t = 0; t < 6; ++t) {
@@ -442,8 +551,8 @@ cudaError_t launch_bf16_to_f32(const bf16* a, float* b, size_t n, cudaStream_t s
 
 cudaError_t launch_edge_enc1(const EdgePair* pairs, int n, int maxW1, int maxH1, const float* W, const float* B, int C1,
                              cudaStream_t st) {
-  dim3 grid((maxW1 + ETW - 1) / ETW, (maxH1 + ETH - 1) / ETH, n);
-  edge_enc1<<<grid, dim3(ETW, ETH), sizeof(float) * 19 * C1, st>>>(pairs, W, B, C1);
+  dim3 grid((maxW1 + E1W - 1) / E1W, (maxH1 + E1H - 1) / E1H, n);
+  edge_enc1<<<grid, 256, sizeof(float) * 19 * C1, st>>>(pairs, W, B, C1);
   return cudaGetLastError();
 }
 

@@ -33,16 +33,36 @@ __device__ __forceinline__ float key_value(int k) {
   return __int_as_float(k >= 0 ? k : (k ^ 0x7FFFFFFF));
 }
 
-// 4x4 box sum of coarse pixel (u, y) (already clamped into the image).
-__device__ __forceinline__ uint16_t box4(const uint8_t* img, int pitch, int u, int y) {
-  const uint8_t* p = img + (size_t)(4 * y) * pitch + 4 * u;
-  unsigned s = 0;
+// Stage 4x4 box sums of rows y0 - R .. y0 + TY + R - 1 (clamped) and columns base_c ..
+// base_c + ncols - 1 (clamped) into dst[row][col]; the loads of 8 elements per thread are
+// all issued before any is summed (one memory round trip per 8 elements, not per element).
+template <int R>
+__device__ __forceinline__ void stage_box(const uint8_t* __restrict__ img, int pitch, int w, int h, int base_c,
+                                          int y0, int ncols, uint16_t* dst) {
+  const int n = (kZnccTY + 2 * R) * ncols;
+  constexpr int U = 8;
+  for (int e0 = threadIdx.x; e0 < n; e0 += U * blockDim.x) {
+    unsigned v[U][4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    unsigned v = *reinterpret_cast<const unsigned*>(p + (size_t)j * pitch);  // 4-byte aligned: 4u
-    s += (v & 0xFFu) + ((v >> 8) & 0xFFu) + ((v >> 16) & 0xFFu) + (v >> 24);
+    for (int u = 0; u < U; ++u) {
+      const int e = min(e0 + u * (int)blockDim.x, n - 1);
+      const int ry = e / ncols, c = e - ry * ncols;
+      const uint8_t* p = img + (size_t)(4 * clampi(y0 - R + ry, 0, h - 1)) * pitch + 4 * clampi(base_c + c, 0, w - 1);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[u][j] = *reinterpret_cast<const unsigned*>(p + (size_t)j * pitch);  // 4u: aligned
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < n) {
+        unsigned t = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          t += (v[u][j] & 0xFFu) + ((v[u][j] >> 8) & 0xFFu) + ((v[u][j] >> 16) & 0xFFu) + (v[u][j] >> 24);
+        dst[e] = (uint16_t)t;
+      }
+    }
   }
-  return (uint16_t)s;
 }
 
 // Vertical then horizontal window sums of S over rows [yi, yi + 2r] for each of the
@@ -111,14 +131,8 @@ zncc_wta_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ jobs) 
   const int rbase = x0 - R - (D - 1);     // coarse column of staged right column 0
 
   // ---- stage 1: box sums, clamped rows / columns
-  for (int e = threadIdx.x; e < (TY + 2 * R) * Z.nlc; e += blockDim.x) {
-    int ry = e / Z.nlc, c = e - ry * Z.nlc;
-    sL[e] = box4(P.L, P.pitch, clampi(lbase + c, 0, w - 1), clampi(y0 - R + ry, 0, h - 1));
-  }
-  for (int e = threadIdx.x; e < (TY + 2 * R) * Z.nrc; e += blockDim.x) {
-    int ry = e / Z.nrc, c = e - ry * Z.nrc;
-    sR[e] = box4(P.R, P.pitch, clampi(rbase + c, 0, w - 1), clampi(y0 - R + ry, 0, h - 1));
-  }
+  stage_box<R>(P.L, P.pitch, w, h, lbase, y0, Z.nlc, sL);
+  stage_box<R>(P.R, P.pitch, w, h, rbase, y0, Z.nrc, sR);
   __syncthreads();
   // ---- stage 2: window statistics (left windows at x0 + t; right windows at rbase + R + t)
   window_stats<R>(sL, Z.nlc, cs, cs2, sumL, invL, Z.gx);
