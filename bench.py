@@ -67,6 +67,30 @@ def peaks():
             "fallback"
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel from one ncu
+# capture, per pair; valid only while the kernel's sources are unchanged since the capture
+# (checked by content hash), else the roofline reports traffic as null.
+MEASURED_TRAFFIC = {
+    "tc_dec3": {"bytes_per_pair": 669.65e6 / 16,
+                "sources": {"paper_2305_11566_gb300/csrc/conv_tc.cu": "71bdb6404d56",
+                            "paper_2305_11566_gb300/csrc/sv_ctx.cuh": "47f4f013d40a",
+                            "paper_2305_11566_gb300/csrc/sv_internal.cuh": "018c7630b6c8"},
+                "capture": "profiles/conv_tc_dec3_16x1242x375.md (16 pairs, scaled by pairs)"},
+}
+
+
+def measured_traffic(kernel, pairs):
+    import hashlib
+    m = MEASURED_TRAFFIC.get(kernel)
+    if m is None:
+        return None
+    for path, h in m["sources"].items():
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest()[:12] != h:
+                return None
+    return m["bytes_per_pair"] * pairs
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -317,7 +341,7 @@ def run_ours(args):
     roof["per_launch_units"] = per_launch
     roof["avg_launch_ms"] = avg_s * 1e3
     roof["peak_source"] = ("derived: " + FP32_PEAK_TFLOPS_NOTE) if roof["bound"] == "alu" else f"{pk_kind} (MEASURED_PEAKS.json)"
-    roof["traffic"] = None
+    roof["traffic"] = measured_traffic(name, B)
     shares = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in sorted(prof.items())}
 
     # -------------------------------------------------------------- e2e through the host-buffer API
