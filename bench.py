@@ -186,6 +186,9 @@ def work_per_pair(shape):
     f["tc_dec3"] = 2 * (2 * H1) * (2 * W1) * d3 * 4 * d2
     f["tc_enc2"], f["tc_enc3"], f["tc_latent"] = f["enc2"], f["enc3"], f["latent"]
     f["edge_enc1"], f["edge_final"] = f["enc1"], f["final"]
+    # fused last decoder layer + final conv: its tensor-core work (the final conv's FP32
+    # FLOPs run on the CUDA cores beside it)
+    f["tc_dec3_final"] = f["tc_dec3"]
     zbytes = 2 * W * H + 2 * (W // 4) * (H // 4)
     return f, zbytes
 

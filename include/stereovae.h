@@ -233,6 +233,10 @@ SV_API sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream);
  *   "tc_ctas_per_sm" 0 (default): each tensor-core convolution stages as many input rows
  *                    ahead as shared memory holds; k = 1..4: fewer, so that k CTAs share
  *                    an SM
+ *   "fused_final"    1 (default): an SV_BF16 inference call computes the last decoder
+ *                    layer, the final conv and the residual in one kernel (d3 stays in
+ *                    shared memory) when the decoder widths allow it and every output
+ *                    width is even; 0: separate kernels (d3 materialised in HBM)
  *   "debug_plans"    1: print each tensor-core layer's launch plan (ring depth, shared
  *                    memory, CTAs per SM, grid, strips) to stderr when a call is prepared
  *   "graphs"         1 (default): sv_pipeline on an SV_BF16 context captures each batch
@@ -243,7 +247,8 @@ SV_API sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value);
 
 /* Test hook: copies activation `which` (0 e1, 1 e2, 2 e3, 3 z, 4 d1, 5 d2, 6 d3; NHWC
  * BF16) of pair `pair` of the last SV_BF16 refinement call into host memory `dst`
- * (`bytes` must equal the activation's size).  Synchronous. */
+ * (`bytes` must equal the activation's size).  Synchronous.  d3 is SV_ERR_STATE after a
+ * call that fused the final conv (option "fused_final"). */
 SV_API sv_status sv_debug_activation(sv_ctx* ctx, int which, int pair, void* dst, size_t bytes);
 
 /* sv_coarse_match without any device allocation, and without a context.

@@ -164,6 +164,7 @@ sv_status Ctx::autotune(const sv_pair* pairs, int n, const char* cache_path, cud
       if (s) break;
       for (int i = 0; i < 6; ++i) {
         auto it = prof_tot.find(names[i]);
+        if (i == 5 && (it == prof_tot.end() || it->second.first == 0)) it = prof_tot.find("tc_dec3_final");  // fused
         if (it == prof_tot.end() || it->second.first == 0) continue;
         const double us = it->second.second * 1e3 / it->second.first;
         if (us < best_us[i]) {

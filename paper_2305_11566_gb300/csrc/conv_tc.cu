@@ -482,6 +482,367 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
 }
 
+// ------------------------------------------------------------------ fused dec3 + final
+// The last decoder layer (nearest x2 + crop + 3x3 conv + ReLU, a10), the final 3x3 conv to
+// one channel and the residual onto U (a11) in one kernel, so that d3 never leaves the SM.
+// A CTA computes all four output phases of 128 input pixels of one row per tile (16 MMAs
+// per phase into four TMEM accumulators), writes the two resulting d3 rows (BF16, 256
+// columns) into a 4-row ring in shared memory, and its epilogue warps run the final conv
+// on the ring: after tile i the final rows 2i - 1 and 2i have their 3x3 neighbourhoods.
+// Column strips step by 127 input pixels (tile = input pixels j0 .. j0 + 127 with
+// j0 = 127 s - 1), so each strip's 254 final columns 2 j0 + 1 .. 2 j0 + 254 have both
+// neighbours in the tile; a strip starts with one halo tile above its first row (none at
+// row 0, where the ring's rows -2, -1 are zero) and, when the output height is even, ends
+// with a zero tile below the last row.  d3 outside the output is stored as zero (the final
+// conv's padding).  An odd output height crops half of the last up-sampled row: the last
+// tile's phase-0 rows then use the unfolded weights of that tap row alone (4 extra B
+// blocks), which gives the cropped conv exactly.  Odd output widths are not handled here.
+struct alignas(64) FusedPair {
+  float* Y;                    // refined disparity [Ho][Wo]
+  const int16_t* coarse;       // coarse map [h4][w4]
+  int Hu, Wu, Ho, Wo, w4, h4;  // input (d2) rows / cols, output size, coarse-map size
+  int pad[4];
+  CUtensorMap tm;              // TMA view of d2 (box: cin channels x 130 pixels x 1 row)
+};
+
+struct FusedParams {
+  const FusedPair* fp;
+  const Strip* strips;
+  int n_strips;
+  const bf16* wpack;  // [20][NT x cin]: 16 (phase, tap) blocks, then 4 last-row blocks (px, co)
+  const float* bias;  // [NT] decoder bias
+  const float* wf;    // [9][NT] final conv weights (tap-major)
+  const float* bf;    // final bias
+  int ring;
+  int* err;
+  long long spin;
+};
+
+constexpr int kFusedNpx = 130;
+__host__ __device__ inline uint32_t fused_kbs(int rb) { return (uint32_t)((kFusedNpx * rb + 1023) / 1024 * 1024); }
+__host__ __device__ inline size_t fused_param_bytes(int NT) { return (size_t)(NT + 9 * NT + 4) * 4; }
+__host__ __device__ inline size_t fused_smem_bytes(int NT, int cin, int ring) {
+  const int rb = cin * 2;
+  const size_t head = ((size_t)20 * NT * cin * 2 + fused_param_bytes(NT) + 1023) / 1024 * 1024;
+  return 1024 + head + (size_t)ring * fused_kbs(rb) + (size_t)4 * 256 * NT * 2 + (size_t)(2 * ring + 4) * 8 + 16;
+}
+
+// 320 threads: warps 0-7 epilogue + final conv, warp 8 TMEM allocation + MMA issue, warp 9 TMA.
+constexpr int kFusedThreads = 320, kFusedEpi = 256;
+// Named barrier 1 over the 256 epilogue threads (warps 0-7) only; the producer and MMA warps
+// never take part.
+__device__ __forceinline__ void named_sync_epi() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// Same barrier with an OR over the 256 threads' predicates.
+__device__ __forceinline__ bool epi_any(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 256, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+template <int NT, int RB>
+__global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_constant__ FusedParams p) {
+  constexpr int RA = 3, KPR = RB / 32, CIN = RB / 2;
+  constexpr uint32_t KBS = (kFusedNpx * RB + 1023) / 1024 * 1024;
+  constexpr int NCH = NT / 8;                                  // 16-byte chunks per d3 pixel
+  constexpr int SWS = NCH == 4 ? 1 : 2;                        // ring chunk swizzle: col >> SWS
+  constexpr uint32_t BBLK = NT * CIN * 2;                      // one (phase, tap) weight block
+  static_assert(NT == 16 || NT == 32, "fused decoder widths");
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  const uint32_t ring = (uint32_t)p.ring;
+  const uint32_t sB = base;
+  const uint32_t sPar = sB + 20 * BBLK;
+  const uint32_t sA = (sPar + (uint32_t)fused_param_bytes(NT) + 1023u) & ~1023u;
+  const uint32_t sD = sA + ring * KBS;                         // d3 ring [4][256][NCH] x 16 B
+  const uint32_t bars = sD + 4 * 256 * NT * 2;
+  const uint32_t full0 = bars, empty0 = bars + ring * 8, accf0 = bars + 2 * ring * 8, acce0 = accf0 + 16;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + (acce0 + 16 - base));
+  float* bias_s = reinterpret_cast<float*>(gbase + (sPar - base));
+  float* wf_s = bias_s + NT;
+  float* bf_s = wf_s + 9 * NT;
+  uint4* d3r = reinterpret_cast<uint4*>(gbase + (sD - base));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int crank = blockIdx.x, cpg = gridDim.x;
+
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(p.wpack);
+    uint4* dst = reinterpret_cast<uint4*>(gbase);
+    for (int e = tid; e < (int)(20 * BBLK / 16); e += kFusedThreads) dst[e] = src[e];
+    for (int e = tid; e < NT; e += kFusedThreads) bias_s[e] = p.bias[e];
+    for (int e = tid; e < 9 * NT; e += kFusedThreads) wf_s[e] = p.wf[e];
+    if (tid == 0) bf_s[0] = p.bf[0];
+  }
+  if (tid == 0) {
+    for (uint32_t r = 0; r < ring; ++r) {
+      mbar_init(full0 + 8 * r, 1);
+      mbar_init(empty0 + 8 * r, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, kFusedEpi);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_proxy_async();
+  constexpr uint32_t kCols = 8 * NT <= 128 ? 128 : 256;  // 2 buffers x 4 phases x NT
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  bool ok = true;
+
+  if (warp == 9) {
+    // ------------------------------------------------------------ TMA producer (one thread)
+    if (lane == 0) {
+      const uint32_t row_tx = (uint32_t)(kFusedNpx * RB);
+      RingPos w;
+      uint32_t q = 0;
+      int last_pair = -1;
+      for (int s = crank; s < p.n_strips && ok; s += cpg) {
+        const Strip st = p.strips[s];
+        const FusedPair* F = p.fp + st.pair;
+        if (st.pair != last_pair) {
+          tensormap_acquire(&F->tm);
+          last_pair = st.pair;
+        }
+        const int first = st.i0 > 0 ? st.i0 - 1 : st.i0;
+        const int nrows = (st.i0 + st.cnt - first) - 1 + RA;
+        for (int r = 0; r < nrows; ++r, ++q, w.next(ring)) {
+          if (w.pass > 0 && !mbar_wait(empty0 + 8 * w.slot, (w.pass - 1) & 1, p.spin)) {
+            atomicCAS(p.err, 0, 1);
+            ok = false;
+            break;
+          }
+          const uint32_t fb = full0 + 8 * w.slot;
+          mbar_expect_tx(fb, row_tx);
+          tma_load3(sA + w.slot * KBS, &F->tm, 0, st.j0 - 1, first - 1 + r, fb);
+        }
+      }
+      const long long drain = p.spin > 2000000000LL ? p.spin : 2000000000LL;
+      for (uint32_t k = 0; k < ring && k < q; ++k) {
+        const uint32_t row = q - 1 - k;
+        if (!mbar_wait(full0 + 8 * (row % ring), (row / ring) & 1, drain)) atomicCAS(p.err, 0, 5);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 8) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((128u >> 4) << 24);
+      constexpr uint32_t a_hi = desc_hi(8 * RB, swz_layout(RB));
+      constexpr uint32_t b_hi = desc_hi((uint32_t)CIN * 16, 0);
+      uint32_t tseq = 0;
+      RingPos wt, tb;
+      for (int s = crank; s < p.n_strips && ok; s += cpg) {
+        const Strip st = p.strips[s];
+        const FusedPair* F = p.fp + st.pair;
+        const int Hu = F->Hu, Ho = F->Ho;
+        const int first = st.i0 > 0 ? st.i0 - 1 : st.i0;
+        const int ntiles = st.i0 + st.cnt - first;
+        for (int k = 0; k < ntiles && ok; ++k) {
+          const int rlo = k == 0 ? 0 : k - 1 + RA;
+          for (int r = rlo; r < k + RA; ++r, wt.next(ring)) {
+            if (!mbar_wait(full0 + 8 * wt.slot, wt.pass & 1, p.spin)) {
+              ok = false;
+              break;
+            }
+          }
+          const uint32_t buf = tseq & 1, use = tseq >> 1;
+          if (ok && use > 0 && !mbar_wait(acce0 + 8 * buf, (use - 1) & 1, p.spin)) ok = false;
+          if (!ok) {
+            atomicCAS(p.err, 0, 2);
+            break;
+          }
+          tc_fence_after();
+          uint32_t slot_of_row[RA];
+#pragma unroll
+          for (int r = 0; r < RA; ++r) {
+            const uint32_t sl = tb.slot + r;
+            slot_of_row[r] = sA + (sl >= ring ? sl - ring : sl) * KBS;
+          }
+          const bool crop_row = (first + k == Hu - 1) && (Ho & 1);  // odd height: last row's py = 0
+#pragma unroll
+          for (int ph = 0; ph < 4; ++ph) {
+            const int py = ph >> 1, px = ph & 1;
+            const uint32_t dcol = tmem + buf * (4 * NT) + ph * NT;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const int ro = t >> 1, co = t & 1;
+              const uint32_t a0 = desc_lo(slot_of_row[py + ro] + (uint32_t)(px + co) * RB, 16);
+              const uint32_t blk = (py == 0 && ro == 1 && crop_row) ? 16u + 2u * px + co : (uint32_t)(ph * 4 + t);
+              const uint32_t b0 = desc_lo(sB + blk * BBLK, 128);
+#pragma unroll
+              for (int k4 = 0; k4 < KPR; ++k4)
+                mma_bf16(dcol, a0 + 2 * k4, a_hi, b0 + 16 * k4, b_hi, idesc, (t | k4) != 0 ? 1u : 0u);
+            }
+          }
+          mma_commit(accf0 + 8 * buf);
+          tb.slot += 1;
+          if (k + 1 == ntiles) tb.slot += RA - 1;
+          while (tb.slot >= ring) tb.slot -= ring;
+          ++tseq;
+        }
+      }
+      if (tseq > 0) {
+        const uint32_t last = tseq - 1;
+        const long long drain = p.spin > 2000000000LL ? p.spin : 2000000000LL;
+        if (!mbar_wait(accf0 + 8 * (last & 1), (last >> 1) & 1, drain)) atomicCAS(p.err, 0, 3);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue + final conv (warps 0-7)
+    // warps 0-3 convert phases (0, 0), (0, 1) (d3 row 2i), warps 4-7 phases (1, 0), (1, 1)
+    // (row 2i + 1); TMEM lane quarter = warp % 4
+    const int m = tid & 127;  // input pixel j0 + m of the tile / TMEM lane
+    const int grp = tid >> 7;
+    // final conv: thread (cl, q) = (tid >> 2, tid & 3) takes channels 8q .. 8q + 7 of the
+    // columns col = 1 + cl + 64 g (g = 0..3); its 9 x 8 weights stay in registers
+    const int fq = tid & 3, fcl = tid >> 2;
+    float2 wr[9][4];
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        wr[t][j] = NCH == 4 || fq < NCH ? make_float2(wf_s[t * NT + fq * 8 + 2 * j], wf_s[t * NT + fq * 8 + 2 * j + 1])
+                                        : make_float2(0.f, 0.f);
+    uint32_t tseq = 0;
+    RingPos rel;
+    auto ring_at = [&](int y, int col, int q) -> uint4* {  // row y (any integer), local column col
+      return d3r + (((uint32_t)y & 3u) * 256u + (uint32_t)col) * NCH + (uint32_t)(q ^ ((col >> SWS) & (NCH - 1)));
+    };
+    for (int s = crank; s < p.n_strips && ok; s += cpg) {
+      const Strip st = p.strips[s];
+      const FusedPair* F = p.fp + st.pair;
+      const int Hu = F->Hu, Wu = F->Wu, Ho = F->Ho, Wo = F->Wo;
+      const int j0 = st.j0;
+      const int first = st.i0 > 0 ? st.i0 - 1 : st.i0;
+      const int ntiles = st.i0 + st.cnt - first;
+      const int nrows = ntiles - 1 + RA;
+      const bool below = st.i0 + st.cnt == Hu && Ho == 2 * Hu;  // zero tile under the last row
+      if (st.i0 == 0) {
+        // rows -2 and -1 of the ring: zero padding above the image
+        for (int e = tid; e < 2 * 256 * NCH; e += kFusedEpi) d3r[(2u * 256u) * NCH + e] = make_uint4(0, 0, 0, 0);
+      }
+      for (int k = 0; k < ntiles + (below ? 1 : 0); ++k) {
+        const int i = first + k;
+        // residual U of the final outputs this lane writes after this tile (column group
+        // g = fq, rows 2i - 1 and 2i; loads in flight while the tile's MMAs run)
+        float Uv[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int X = min(max(2 * j0 + 1 + fcl + 64 * fq, 0), Wo - 1);
+          const int Yr = min(max(2 * i - 1 + r, 0), Ho - 1);
+          Uv[r] = upsample4_f(F->coarse, F->w4, F->h4, X, Yr);
+        }
+        if (k < ntiles) {
+          const uint32_t buf = tseq & 1;
+          const bool got = mbar_wait(accf0 + 8 * buf, (tseq >> 1) & 1, p.spin);
+          // all 128 epilogue threads take the same decision, so none is left waiting at a
+          // named barrier
+          if (epi_any(!got)) {
+            if (tid == 0) atomicCAS(p.err, 0, 4);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          if (tid == 0) {
+            const int rel_hi = k + 1 < ntiles ? k + 1 : nrows;
+            for (int r = k; r < rel_hi; ++r, rel.next(ring)) mbar_arrive(empty0 + 8 * rel.slot);
+          }
+          const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + buf * (4 * NT);
+#pragma unroll 1
+          for (int ph = 2 * grp; ph < 2 * grp + 2; ++ph) {
+            const int py = ph >> 1, px = ph & 1;
+            uint32_t r[32];
+            if (NT == 32) tmem_ld32(trow + ph * NT, r);
+            else tmem_ld16(trow + ph * NT, r);
+            const int oy = 2 * i + py, ox = 2 * (j0 + m) + px;
+            const bool valid = oy < Ho && ox >= 0 && ox < Wo && j0 + m < Wu;
+            const int col = 2 * m + px;
+#pragma unroll
+            for (int q = 0; q < NCH; ++q) {
+              uint32_t pk[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const int c0 = q * 8 + 2 * e;
+                float a = fmaxf(__uint_as_float(r[c0]) + bias_s[c0], 0.f);
+                float b = fmaxf(__uint_as_float(r[c0 + 1]) + bias_s[c0 + 1], 0.f);
+                __nv_bfloat162 h = __floats2bfloat162_rn(valid ? a : 0.f, valid ? b : 0.f);
+                pk[e] = *reinterpret_cast<uint32_t*>(&h);
+              }
+              *ring_at(oy, col, q) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(acce0 + 8 * buf);
+          ++tseq;
+        } else {
+          // zero rows 2 Hu and 2 Hu + 1 below the output
+#pragma unroll
+          for (int px = 0; px < 2; ++px)
+#pragma unroll
+            for (int q = 0; q < NCH; ++q) *ring_at(2 * i + grp, 2 * m + px, q) = make_uint4(0, 0, 0, 0);
+        }
+        named_sync_epi();  // the tile's two d3 rows are in the ring
+        if (i >= st.i0) {
+          // final conv + residual for output rows 2i - 1 and 2i, columns 2 j0 + col with
+          // col in [1, 254]: each d3 row y = 2i - 2 + r feeds row 2i - 1 (ky = r) and row 2i
+          // (ky = r - 1) from one load; the four channel quarters of a pixel are added with
+          // xor shuffles (lanes 4 cl .. 4 cl + 3)
+          const float b = bf_s[0];
+#pragma unroll 1
+          for (int g = 0; g < 4; ++g) {
+            const int col = min(1 + fcl + 64 * g, 254);  // lanes past column 254 compute a duplicate
+            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+            if (fq < NCH) {
+#pragma unroll
+              for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                  const uint4 v = *ring_at(2 * i - 2 + r, col - 1 + kx, fq);
+                  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+                  for (int j = 0; j < 4; ++j) {
+                    const float2 f = __bfloat1622float2(h[j]);
+                    if (r <= 2) a0 = __ffma2_rn(f, wr[r * 3 + kx][j], a0);
+                    if (r >= 1) a1 = __ffma2_rn(f, wr[(r - 1) * 3 + kx][j], a1);
+                  }
+                }
+            }
+            float s0 = a0.x + a0.y, s1 = a1.x + a1.y;
+            s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+            s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+            const int X = 2 * j0 + col;
+            if (g == fq && 1 + fcl + 64 * g <= 254 && X >= 0 && X < Wo) {
+              if (2 * i - 1 >= 0 && 2 * i - 1 < Ho) F->Y[(size_t)(2 * i - 1) * Wo + X] = Uv[0] + (b + s0);
+              if (2 * i < Ho) F->Y[(size_t)(2 * i) * Wo + X] = Uv[1] + (b + s1);
+            }
+          }
+        }
+        named_sync_epi();  // the ring rows read above may now be overwritten
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+}
+
 // ------------------------------------------------------------------ weight packing
 // Packed B of one layer: [G][T][NT rows (output channels) x cin] in the no-swizzle
 // K-major core-matrix layout: element (n, k) at (n%8)*8 + (n/8)*cin*8 + (k%8) + (k/8)*64.
@@ -521,6 +882,66 @@ __global__ void pack_kernel(const float* __restrict__ W, int mode, int NT, int G
   out[dst] = __float2bfloat16_rn(v);
 }
 
+
+// Packed B of the fused dec3 kernel: 20 blocks of [NT output channels x cin] in the same
+// core-matrix layout.  Blocks 4 ph + t: phase ph = (py, px), tap t = (ro, co) of the 4-phase
+// form (3x3 weights summed per phase as in pack_kernel).  Blocks 16 + 2 px + co: phase
+// (0, px), tap row ro = 1 with only the kernel row ky = 1 (the row ky = 2 falls on the
+// cropped-away half of the up-sampled map when the output height is odd).
+__global__ void pack_fused_kernel(const float* __restrict__ W, int NT, int cin, bf16* __restrict__ out) {
+  const size_t total = (size_t)20 * NT * cin;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int k = (int)(idx % cin);
+  const int n = (int)((idx / cin) % NT);
+  const int blk = (int)(idx / ((size_t)cin * NT));
+  int py, px, a, b;
+  bool crop = false;
+  if (blk < 16) {
+    py = (blk / 4) >> 1;
+    px = (blk / 4) & 1;
+    a = (blk % 4) >> 1;
+    b = (blk % 4) & 1;
+  } else {
+    py = 0;
+    px = (blk - 16) >> 1;
+    a = 1;
+    b = (blk - 16) & 1;
+    crop = true;
+  }
+  const int ky0 = py == 0 ? (a == 0 ? 0 : 1) : (a == 0 ? 0 : 2);
+  const int ky1 = crop ? 1 : py == 0 ? (a == 0 ? 0 : 2) : (a == 0 ? 1 : 2);
+  const int kx0 = px == 0 ? (b == 0 ? 0 : 1) : (b == 0 ? 0 : 2);
+  const int kx1 = px == 0 ? (b == 0 ? 0 : 2) : (b == 0 ? 1 : 2);
+  float v = 0.f;
+  for (int ky = ky0; ky <= ky1; ++ky)
+    for (int kx = kx0; kx <= kx1; ++kx) v += W[((size_t)n * 9 + ky * 3 + kx) * cin + k];
+  const size_t dst = (size_t)blk * NT * cin + (size_t)(n % 8) * 8 + (size_t)(n / 8) * cin * 8 + (k % 8) + (size_t)(k / 8) * 64;
+  out[dst] = __float2bfloat16_rn(v);
+}
+
+template <int NT, int RB>
+cudaError_t launch_fused_nt(const FusedParams& p, int grid, size_t smem, cudaStream_t st) {
+  auto k = dec3f_kernel<NT, RB>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kFusedThreads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused(const FusedParams& p, int NT, int cin, int grid, size_t smem, cudaStream_t st) {
+  if (NT == 32 && cin == 64) return launch_fused_nt<32, 128>(p, grid, smem, st);
+  if (NT == 16 && cin == 64) return launch_fused_nt<16, 128>(p, grid, smem, st);
+  if (NT == 32 && cin == 32) return launch_fused_nt<32, 64>(p, grid, smem, st);
+  if (NT == 16 && cin == 32) return launch_fused_nt<16, 64>(p, grid, smem, st);
+  return cudaErrorInvalidValue;
+}
+
+// The fused dec3 + final kernel applies to decoder widths (cout, cin) in {16, 32} x {32, 64}
+// when its shared memory fits.
+bool fused_supported(int cout, int cin) {
+  return (cout == 16 || cout == 32) && (cin == 32 || cin == 64) && fused_smem_bytes(cout, cin, 4) <= 232448;
+}
 
 template <int MODE, int NT, int RB>
 cudaError_t launch_mode_nt(const Params& p, int grid, size_t smem, cudaStream_t st) {
@@ -746,6 +1167,14 @@ sv_status Ctx::pack_bf16_weights(cudaStream_t st) {
                                                                 (__nv_bfloat16*)wbf.p + unf[k], n);
     if ((s = cuda(cudaGetLastError(), "unfolded weights"))) return s;
   }
+  if (tc::fused_supported(net.dec[2], net.dec[1])) {
+    const size_t n = (size_t)20 * net.dec[2] * net.dec[1];
+    if ((s = cuda(wfuse.ensure(n * sizeof(__nv_bfloat16)), "alloc fused weights"))) return s;
+    LaunchScope ls(*this, "pack_bf16", st);
+    tc::pack_fused_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const float*)w32.p + net.w_off(L_DEC3), net.dec[2],
+                                                                  net.dec[1], (__nv_bfloat16*)wfuse.p);
+    if ((s = cuda(cudaGetLastError(), "fused weights"))) return s;
+  }
   for (auto& pl : plans) {
     const size_t n = (size_t)pl.G * tc::taps(pl.mode) * pl.NT * pl.cin;
     LaunchScope ls(*this, "pack_bf16", st);
@@ -904,6 +1333,52 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
   }
   r.edge_ofs = put(eps_.data(), sizeof(EdgePair) * n);
   r.n = n;
+
+  // fused last decoder layer + final conv: inference only (training keeps d3 for backward)
+  r.fused = false;
+  bool even = true;
+  for (int i = 0; i < n; ++i) even = even && (pairs[i].width % 2 == 0);
+  if (!coarse_f && fused_final && even && tc::fused_supported(net.dec[2], net.dec[1]) && wfuse.p) {
+    const int NT = net.dec[2], cin = net.dec[1];
+    int ring = 4;  // 3 rows per tile + 1 ahead; more where shared memory allows
+    while (ring < 3 + kPrefetchSteps && tc::fused_smem_bytes(NT, cin, ring + 1) <= kSmemLimit) ++ring;
+    std::vector<tc::FusedPair> fps(n);
+    long long units = 0;
+    for (int i = 0; i < n; ++i) {
+      tc::FusedPair& F = fps[i];
+      memset(&F, 0, sizeof(F));
+      F.Y = out[i];
+      F.coarse = coarse ? coarse[i] : nullptr;
+      F.Hu = lv[i].H[1];
+      F.Wu = lv[i].W[1];
+      F.Ho = lv[i].H[0];
+      F.Wo = lv[i].W[0];
+      F.w4 = pairs[i].width / 4;
+      F.h4 = pairs[i].height / 4;
+      if (!make_tmap(&F.tm, act(5, i), cin, F.Wu, F.Hu, F.Wu, 1, tc::kFusedNpx))
+        return fail(SV_ERR_CUDA, "pair %d: cuTensorMapEncodeTiled failed (fused decoder)", i);
+      units += (long long)F.Hu * ((F.Wo + 1 + 253) / 254);
+    }
+    const int grid0 = nsm;  // one CTA per SM (about 214 KB of shared memory each)
+    int hs = (int)std::max<long long>(2, (units + grid0 * 4LL - 1) / (grid0 * 4LL));
+    if (tc_strip_rows > 0) hs = tc_strip_rows;
+    if (tc_rows_override[5] > 0) hs = tc_rows_override[5];
+    std::vector<tc::Strip> strips;
+    for (int i = 0; i < n; ++i)
+      for (int sx = 0; 254 * sx - 1 < fps[i].Wo; ++sx)
+        for (int i0 = 0; i0 < fps[i].Hu; i0 += hs) strips.push_back({i, 127 * sx - 1, i0, std::min(hs, fps[i].Hu - i0)});
+    r.fused_fp_ofs = put(fps.data(), sizeof(tc::FusedPair) * n);
+    r.fused_strip_ofs = put(strips.data(), sizeof(tc::Strip) * strips.size());
+    r.fused_n_strips = (int)strips.size();
+    r.fused_grid = (int)std::min<long long>(grid0, (long long)strips.size());
+    r.fused_ring = ring;
+    r.fused_hs = hs;
+    r.fused_smem = tc::fused_smem_bytes(NT, cin, ring);
+    r.fused = true;
+    if (debug_plans)
+      fprintf(stderr, "[sv] fused dec3+final: NT %d cin %d ring %d smem %zu grid %d strips %zu rows %d\n", NT, cin, ring,
+              r.fused_smem, r.fused_grid, strips.size(), hs);
+  }
   return SV_OK;
 }
 
@@ -950,6 +1425,23 @@ sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream
       }
       continue;
     }
+    if (r.fused && pl.layer == L_DEC3) {
+      tc::FusedParams fp{};
+      fp.fp = (const tc::FusedPair*)(tables + r.fused_fp_ofs);
+      fp.strips = (const Strip*)(tables + r.fused_strip_ofs);
+      fp.n_strips = r.fused_n_strips;
+      fp.wpack = (const __nv_bfloat16*)wfuse.p;
+      fp.bias = prm.bias;
+      fp.wf = W + net.w_off(L_FINAL);
+      fp.bf = W + net.b_off(L_FINAL);
+      fp.ring = r.fused_ring;
+      fp.err = (int*)err_flag.p;
+      fp.spin = spin_limit;
+      LaunchScope ls(*this, "tc_dec3_final", st);
+      if ((s = cuda(tc::launch_fused(fp, net.dec[2], net.dec[1], r.fused_grid, r.fused_smem, st), "fused dec3 + final")))
+        return s;
+      continue;  // no border fix: the crop is exact inside the fused kernel
+    }
     {
       LaunchScope ls(*this, names[li], st);
       if ((s = cuda(tc::launch_conv(pl.mode, prm, pl.NT, r.tabs[li].grid, pl.smem, st), names[li]))) return s;
@@ -962,6 +1454,8 @@ sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream
         return s;
     }
   }
+  last_fused = r.fused;
+  if (r.fused) return SV_OK;  // the final conv ran inside the fused decoder kernel
   {
     LaunchScope ls(*this, "edge_final", st);
     if ((s = cuda(launch_edge_final(d_edges, r.n, r.maxW, r.maxH, W + net.w_off(L_FINAL), W + net.b_off(L_FINAL),

@@ -499,6 +499,12 @@ sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value) {
     if (!c->use_graphs) c->drop_graphs();
     return SV_OK;
   }
+  if (!strcmp(key, "fused_final")) {
+    if (value != 0 && value != 1) return c->fail(SV_ERR_INVALID_ARG, "fused_final must be 0 or 1");
+    c->fused_final = (int)value;
+    c->drop_graphs();
+    return SV_OK;
+  }
   if (!strcmp(key, "debug_plans")) {
     if (value != 0 && value != 1) return c->fail(SV_ERR_INVALID_ARG, "debug_plans must be 0 or 1");
     c->debug_plans = (int)value;
@@ -525,6 +531,8 @@ sv_status sv_debug_activation(sv_ctx* ctx, int which, int pair, void* dst, size_
     return c->fail(SV_ERR_INVALID_ARG, "no such activation");
   if (bytes != c->tc_len[pair][which] * sizeof(__nv_bfloat16))
     return c->fail(SV_ERR_INVALID_ARG, "activation has %zu bytes", c->tc_len[pair][which] * sizeof(__nv_bfloat16));
+  if (which == 6 && c->last_fused)
+    return c->fail(SV_ERR_STATE, "d3 stayed on chip (fused final conv); set option fused_final 0 to keep it");
   DeviceGuard g(c->device);
   return c->cuda(cudaMemcpy(dst, (__nv_bfloat16*)c->tc_act[which].p + c->tc_off[pair][which], bytes,
                             cudaMemcpyDeviceToHost), "copy activation");

@@ -40,6 +40,10 @@ struct TcRun {
   std::vector<unsigned char> host;
   size_t edge_ofs = 0;
   int n = 0, maxW = 0, maxH = 0, maxW1 = 0, maxH1 = 0;
+  // fused last decoder layer + final conv (inference, even output widths)
+  bool fused = false;
+  size_t fused_fp_ofs = 0, fused_strip_ofs = 0, fused_smem = 0;
+  int fused_n_strips = 0, fused_grid = 0, fused_ring = 0, fused_hs = 0;
 };
 
 // Prepared coarse-matching call.
@@ -76,6 +80,7 @@ struct Ctx {
   std::string err;
 
   DevBuf w32, w64, wbf;          // FP32 master, FP64 copy, packed BF16 GEMM operands
+  DevBuf wfuse;                  // packed BF16 operands of the fused last decoder layer
   DevBuf zpairs, zjobs;          // coarse-matcher tables
   DevBuf coarse_maps;            // int16 coarse maps of sv_pipeline
   DevBuf act[7];                 // activations e1 e2 e3 z d1 d2 d3 (direct path)
@@ -96,6 +101,8 @@ struct Ctx {
   long long spin_limit = 4000000000LL;  // clock64 cycles a device-side wait may spin
   int tc_strip_rows = 0;                // 0: automatic
   int debug_plans = 0;                  // 1: print each tensor-core layer's launch plan to stderr
+  int fused_final = 1;                  // 1: last decoder layer + final conv in one kernel when possible
+  bool last_fused = false;              // the last tensor-core call did not materialise d3
   int tc_ctas_per_sm = 0;               // 0: deepest row ring (one CTA per SM); k: ring sized for k
   int tc_rows_override[6] = {0, 0, 0, 0, 0, 0};  // per tensor-core layer, set by the autotuner
   int tc_nt_override[6] = {0, 0, 0, 0, 0, 0};
@@ -195,7 +202,8 @@ struct Ctx {
     for (auto e : ev_free) cudaEventDestroy(e);
     ev_free.clear();
     host_img.release(); host_out.release(); err_flag.release(); tune_out.release();
-    w32.release(); w64.release(); wbf.release(); zpairs.release(); zjobs.release(); coarse_maps.release();
+    w32.release(); w64.release(); wbf.release(); wfuse.release(); zpairs.release(); zjobs.release();
+    coarse_maps.release();
     for (auto& b : act) b.release();
     for (auto& b : tc_act) b.release();
     tc_tables.release(); adam_m.release(); adam_v.release();

@@ -144,6 +144,21 @@ struct alignas(64) EdgePair {
   float* Y;                 // refined disparity [H][W]
   CUtensorMap d3_map;       // TMA view of d3 for the final conv (final_staged_by_tma(C))
 };
+// U = 4 x bilinear(coarse) at full-resolution pixel (X, Y), half-pixel centres, source
+// clamped to the coarse map (Sec. IV-C "linear scaling", reading N1), FP32.
+template <typename CT>
+__device__ __forceinline__ float upsample4_f(const CT* __restrict__ c, int w, int h, int X, int Y) {
+  float sx = (float)X * 0.25f - 0.375f, sy = (float)Y * 0.25f - 0.375f;
+  sx = fminf(fmaxf(sx, 0.f), (float)(w - 1));
+  sy = fminf(fmaxf(sy, 0.f), (float)(h - 1));
+  const int x0 = (int)sx, y0 = (int)sy;
+  const int x1 = min(x0 + 1, w - 1), y1 = min(y0 + 1, h - 1);
+  const float fx = sx - (float)x0, fy = sy - (float)y0;
+  const float top = (1.f - fx) * (float)c[(size_t)y0 * w + x0] + fx * (float)c[(size_t)y0 * w + x1];
+  const float bot = (1.f - fx) * (float)c[(size_t)y1 * w + x0] + fx * (float)c[(size_t)y1 * w + x1];
+  return 4.f * ((1.f - fy) * top + fy * bot);
+}
+
 // Final conv of the tensor-core form: widths with the register-blocked kernel stage their
 // (rows + 2) x 34 x C input tile with one TMA box; its height in output rows per block.
 inline bool final_staged_by_tma(int C) { return C == 16 || C == 32 || C == 64 || C == 128; }

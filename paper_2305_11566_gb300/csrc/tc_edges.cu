@@ -17,19 +17,6 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-template <typename CT>
-__device__ __forceinline__ float upsample4_f(const CT* __restrict__ c, int w, int h, int X, int Y) {
-  float sx = (float)X * 0.25f - 0.375f, sy = (float)Y * 0.25f - 0.375f;
-  sx = fminf(fmaxf(sx, 0.f), (float)(w - 1));
-  sy = fminf(fmaxf(sy, 0.f), (float)(h - 1));
-  const int x0 = (int)sx, y0 = (int)sy;
-  const int x1 = min(x0 + 1, w - 1), y1 = min(y0 + 1, h - 1);
-  const float fx = sx - (float)x0, fy = sy - (float)y0;
-  const float top = (1.f - fx) * (float)c[(size_t)y0 * w + x0] + fx * (float)c[(size_t)y0 * w + x1];
-  const float bot = (1.f - fx) * (float)c[(size_t)y1 * w + x0] + fx * (float)c[(size_t)y1 * w + x1];
-  return 4.f * ((1.f - fy) * top + fy * bot);
-}
-
 // 16-byte asynchronous global -> shared copy (zero fill when !valid: no bytes are read,
 // `src` is only a placeholder then); every copy of a staging loop is in flight at once.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {

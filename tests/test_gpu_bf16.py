@@ -63,8 +63,12 @@ def test_bf16_layers_match_oracle(contexts, name, shape, W, H, dmax, k, D):
     params = synth.he_normal_weights(shape, 7)
     ctx = contexts(shape, k)
     dp = binding.to_device(p, D)
-    Y = ctx.refine([dp], [torch.from_numpy(disp_o.astype(np.int16)).cuda()])[0]
-    ctx.synchronize()
+    ctx.set_option("fused_final", 0)  # keep d3 in HBM so that it can be compared
+    try:
+        Y = ctx.refine([dp], [torch.from_numpy(disp_o.astype(np.int16)).cuda()])[0]
+        ctx.synchronize()
+    finally:
+        ctx.set_option("fused_final", 1)
     for wi, a in enumerate(ACTS):
         g = ctx.debug_activation(wi, 0, act_shape(shape, H, W, a))
         ref = oracle.refine_activation(shape, params, p.left, disp_o.astype(np.float64), a)
@@ -144,3 +148,37 @@ def test_device_wait_timeout_is_reported_and_recoverable(contexts):
     ctx.synchronize()
     ref = oracle.refine_forward(shape, synth.he_normal_weights(shape, 7), p.left, disp_o.astype(np.float64))
     check_output(Y.cpu().numpy().astype(np.float64), ref, p.gt, "after timeout")
+
+
+@pytest.mark.parametrize("name,shape,W,H,dmax,k,D,rows", [
+    ("1242x375 wide net, default strips", synth.NET_WIDE, 1242, 375, 190.0, 9, 48, 0),
+    ("1242x375 wide net, 7-row strips", synth.NET_WIDE, 1242, 375, 190.0, 9, 48, 7),
+    ("256x128 small net, 5-row strips", synth.NET_SMALL, 256, 128, 60.0, 7, 16, 5),
+])
+def test_bf16_fused_final(contexts, name, shape, W, H, dmax, k, D, rows):
+    """The fused last-decoder-layer + final-conv kernel (d3 kept in shared memory; odd output
+    height handled by the last-row weights, even height by the zero tile below; column
+    strips overlapping by one input pixel; halo tiles above row strips) against the
+    unfused kernels of the same context and against the FP64 oracle."""
+    p = synth.make_pair(W, H, dmax, 8100 + W + rows)
+    disp_o = oracle.coarse_match(p.left, p.right, k, D)[0]
+    params = synth.he_normal_weights(shape, 7)
+    ctx = contexts(shape, k)
+    dp = binding.to_device(p, D)
+    cm = [torch.from_numpy(disp_o.astype(np.int16)).cuda()]
+    ctx.set_option("tc_strip_rows", rows)
+    try:
+        ctx.set_option("fused_final", 0)
+        Yu = ctx.refine([dp], cm)[0].cpu().numpy().astype(np.float64)
+        ctx.set_option("fused_final", 1)
+        Yf = ctx.refine([dp], cm)[0].cpu().numpy().astype(np.float64)
+        ctx.synchronize()
+        with pytest.raises(binding.SvError):  # d3 was not materialised
+            ctx.debug_activation(6, 0, act_shape(shape, H, W, "d3"))
+    finally:
+        ctx.set_option("tc_strip_rows", 0)
+        ctx.set_option("fused_final", 1)
+    d = np.abs(Yf - Yu)
+    assert d.max() <= 5e-3, f"{name}: fused vs unfused max |dY| = {d.max():.2e}"
+    ref = oracle.refine_forward(shape, params, p.left, disp_o.astype(np.float64))
+    check_output(Yf, ref, p.gt, name)
