@@ -189,6 +189,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// tcgen05.ld of 32 columns without the wait: several loads in flight, then tmem_wait_ld()
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%"
+      "20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -707,16 +727,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
     // (row 2i + 1); TMEM lane quarter = warp % 4
     const int m = tid & 127;  // input pixel j0 + m of the tile / TMEM lane
     const int grp = tid >> 7;
-    // final conv: thread (cl, q) = (tid >> 2, tid & 3) takes channels 8q .. 8q + 7 of the
-    // columns col = 1 + cl + 64 g (g = 0..3); its 9 x 8 weights stay in registers
+    // final conv: thread (cl, q) = (tid >> 2, tid & 3) takes channels 8q .. 8q + 7 of
+    // columns 1 + 4 cl .. 4 + 4 cl
     const int fq = tid & 3, fcl = tid >> 2;
-    float2 wr[9][4];
-#pragma unroll
-    for (int t = 0; t < 9; ++t)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        wr[t][j] = NCH == 4 || fq < NCH ? make_float2(wf_s[t * NT + fq * 8 + 2 * j], wf_s[t * NT + fq * 8 + 2 * j + 1])
-                                        : make_float2(0.f, 0.f);
     uint32_t tseq = 0;
     RingPos rel;
     auto ring_at = [&](int y, int col, int q) -> uint4* {  // row y (any integer), local column col
@@ -737,19 +750,37 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
       }
       for (int k = 0; k < ntiles + (below ? 1 : 0); ++k) {
         const int i = first + k;
-        // residual U of the final outputs this lane writes after this tile (column group
-        // g = fq, rows 2i - 1 and 2i; loads in flight while the tile's MMAs run)
-        float Uv[2];
+        // residual U of the two final outputs this lane writes after this tile (column
+        // col_own, rows 2i - 1 and 2i): the coarse values are loaded now as raw integers (in
+        // flight while the tile's MMAs run) and interpolated at the store
+        const int col_own = 1 + 4 * fcl + fq;
+        int16_t cv[2][4];
+        float fxy[2][2];
+        {
+          const int X = min(max(2 * j0 + col_own, 0), Wo - 1);
+          float sx = (float)X * 0.25f - 0.375f;
+          sx = fminf(fmaxf(sx, 0.f), (float)(F->w4 - 1));
+          const int x0 = (int)sx, x1 = min(x0 + 1, F->w4 - 1);
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const int X = min(max(2 * j0 + 1 + fcl + 64 * fq, 0), Wo - 1);
-          const int Yr = min(max(2 * i - 1 + r, 0), Ho - 1);
-          Uv[r] = upsample4_f(F->coarse, F->w4, F->h4, X, Yr);
+          for (int r = 0; r < 2; ++r) {
+            const int Yr = min(max(2 * i - 1 + r, 0), Ho - 1);
+            float sy = (float)Yr * 0.25f - 0.375f;
+            sy = fminf(fmaxf(sy, 0.f), (float)(F->h4 - 1));
+            const int y0 = (int)sy, y1 = min(y0 + 1, F->h4 - 1);
+            const int16_t* c0p = F->coarse + (size_t)y0 * F->w4;
+            const int16_t* c1p = F->coarse + (size_t)y1 * F->w4;
+            cv[r][0] = c0p[x0];
+            cv[r][1] = c0p[x1];
+            cv[r][2] = c1p[x0];
+            cv[r][3] = c1p[x1];
+            fxy[r][0] = sx - (float)x0;
+            fxy[r][1] = sy - (float)y0;
+          }
         }
         if (k < ntiles) {
           const uint32_t buf = tseq & 1;
           const bool got = mbar_wait(accf0 + 8 * buf, (tseq >> 1) & 1, p.spin);
-          // all 128 epilogue threads take the same decision, so none is left waiting at a
+          // all epilogue threads take the same decision, so none is left waiting at a
           // named barrier
           if (epi_any(!got)) {
             if (tid == 0) atomicCAS(p.err, 0, 4);
@@ -762,27 +793,37 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
             for (int r = k; r < rel_hi; ++r, rel.next(ring)) mbar_arrive(empty0 + 8 * rel.slot);
           }
           const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + buf * (4 * NT);
-#pragma unroll 1
-          for (int ph = 2 * grp; ph < 2 * grp + 2; ++ph) {
-            const int py = ph >> 1, px = ph & 1;
-            uint32_t r[32];
-            if (NT == 32) tmem_ld32(trow + ph * NT, r);
-            else tmem_ld16(trow + ph * NT, r);
-            const int oy = 2 * i + py, ox = 2 * (j0 + m) + px;
+          uint32_t rr[2][32];
+          // both phases of this group in flight, one wait
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (NT == 32) tmem_ld32_nowait(trow + (2 * grp + h) * NT, rr[h]);
+            else tmem_ld16_nowait(trow + (2 * grp + h) * NT, rr[h]);
+          }
+          tmem_wait_ld();
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int px = h;
+            const int oy = 2 * i + grp, ox = 2 * (j0 + m) + px;
             const bool valid = oy < Ho && ox >= 0 && ox < Wo && j0 + m < Wu;
             const int col = 2 * m + px;
+            if (valid) {
 #pragma unroll
-            for (int q = 0; q < NCH; ++q) {
-              uint32_t pk[4];
+              for (int q = 0; q < NCH; ++q) {
+                uint32_t pk[4];
 #pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const int c0 = q * 8 + 2 * e;
-                float a = fmaxf(__uint_as_float(r[c0]) + bias_s[c0], 0.f);
-                float b = fmaxf(__uint_as_float(r[c0 + 1]) + bias_s[c0 + 1], 0.f);
-                __nv_bfloat162 h = __floats2bfloat162_rn(valid ? a : 0.f, valid ? b : 0.f);
-                pk[e] = *reinterpret_cast<uint32_t*>(&h);
+                for (int e = 0; e < 4; ++e) {
+                  const int c0 = q * 8 + 2 * e;
+                  const float a = fmaxf(__uint_as_float(rr[h][c0]) + bias_s[c0], 0.f);
+                  const float b = fmaxf(__uint_as_float(rr[h][c0 + 1]) + bias_s[c0 + 1], 0.f);
+                  __nv_bfloat162 hh = __floats2bfloat162_rn(a, b);
+                  pk[e] = *reinterpret_cast<uint32_t*>(&hh);
+                }
+                *ring_at(oy, col, q) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
               }
-              *ring_at(oy, col, q) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            } else {  // outside the output: the final conv's zero padding
+#pragma unroll
+              for (int q = 0; q < NCH; ++q) *ring_at(oy, col, q) = make_uint4(0, 0, 0, 0);
             }
           }
           tc_fence_before();
@@ -797,39 +838,94 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
         }
         named_sync_epi();  // the tile's two d3 rows are in the ring
         if (i >= st.i0) {
-          // final conv + residual for output rows 2i - 1 and 2i, columns 2 j0 + col with
-          // col in [1, 254]: each d3 row y = 2i - 2 + r feeds row 2i - 1 (ky = r) and row 2i
-          // (ky = r - 1) from one load; the four channel quarters of a pixel are added with
-          // xor shuffles (lanes 4 cl .. 4 cl + 3)
+          // final conv + residual for output rows 2i - 1 and 2i, columns 2 j0 + col with col
+          // in [1, 254]: thread (cl, q) takes the four adjacent columns cA = 1 + 4 cl .. cA + 3
+          // for channels 8q .. 8q + 7.  Each d3 row y = 2i - 2 + r is read at columns
+          // cA - 1 .. cA + 4 once and feeds all four columns and both output rows (row 2i - 1
+          // with ky = r, row 2i with ky = r - 1): eight independent accumulators.  The four
+          // channel quarters of a pixel are added with xor shuffles; lane q stores column
+          // cA + q.
           const float b = bf_s[0];
-#pragma unroll 1
-          for (int g = 0; g < 4; ++g) {
-            const int col = min(1 + fcl + 64 * g, 254);  // lanes past column 254 compute a duplicate
-            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-            if (fq < NCH) {
+          const int cA = 1 + 4 * fcl;  // the last group (253 .. 256) stores 253, 254 only
+          float2 acc[4][2];  // [column e][row]
 #pragma unroll
-              for (int kx = 0; kx < 3; ++kx)
+          for (int e = 0; e < 4; ++e) acc[e][0] = acc[e][1] = make_float2(0.f, 0.f);
+          if (fq < NCH) {
+            // weights of kernel rows ky = r (output row 2i - 1) and ky = r - 1 (row 2i) for this
+            // lane's 8 channels, read from shared memory per d3 row (broadcast)
+            float2 wa[3][4], wb[3][4];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                  const uint4 v = *ring_at(2 * i - 2 + r, col - 1 + kx, fq);
-                  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+            for (int r = 0; r < 4; ++r) {
 #pragma unroll
-                  for (int j = 0; j < 4; ++j) {
-                    const float2 f = __bfloat1622float2(h[j]);
-                    if (r <= 2) a0 = __ffma2_rn(f, wr[r * 3 + kx][j], a0);
-                    if (r >= 1) a1 = __ffma2_rn(f, wr[(r - 1) * 3 + kx][j], a1);
+              for (int kx = 0; kx < 3; ++kx) {
+                if (r >= 1) {
+#pragma unroll
+                  for (int j = 0; j < 4; ++j) wb[kx][j] = wa[kx][j];  // row r - 1 of the previous step
+                }
+                if (r <= 2) {
+                  const float4 lo = *reinterpret_cast<const float4*>(wf_s + (r * 3 + kx) * NT + fq * 8);
+                  const float4 hi = *reinterpret_cast<const float4*>(wf_s + (r * 3 + kx) * NT + fq * 8 + 4);
+                  wa[kx][0] = make_float2(lo.x, lo.y);
+                  wa[kx][1] = make_float2(lo.z, lo.w);
+                  wa[kx][2] = make_float2(hi.x, hi.y);
+                  wa[kx][3] = make_float2(hi.z, hi.w);
+                }
+              }
+              uint4 v[6];
+              // columns past 255 (last group only) feed just the unstored outputs 255, 256.
+              // Odd column groups load in an order rotated by one, so that the 8 lanes of a
+              // quarter warp (two groups x four channel quarters) read pixels of both parities
+              // (8 distinct 16-byte bank groups), then rotate back in registers.
+              const bool rot = fcl & 1;
+#pragma unroll
+              for (int cc = 0; cc < 6; ++cc) {
+                const int c2 = rot ? (cc + 1 < 6 ? cc + 1 : 0) : cc;
+                v[cc] = *ring_at(2 * i - 2 + r, min(cA - 1 + c2, 255), fq);
+              }
+              if (rot) {
+                const uint4 last = v[5];
+#pragma unroll
+                for (int cc = 5; cc > 0; --cc) v[cc] = v[cc - 1];
+                v[0] = last;
+              }
+#pragma unroll
+              for (int cc = 0; cc < 6; ++cc) {
+                const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&v[cc]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  const float2 f = __bfloat1622float2(hv[j]);
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) {
+                    const int kx = cc - e;  // column cA + e reads column cA - 1 + cc at tap kx
+                    if (kx < 0 || kx > 2) continue;
+                    if (r <= 2) acc[e][0] = __ffma2_rn(f, wa[kx][j], acc[e][0]);
+                    if (r >= 1) acc[e][1] = __ffma2_rn(f, wb[kx][j], acc[e][1]);
                   }
                 }
+              }
             }
-            float s0 = a0.x + a0.y, s1 = a1.x + a1.y;
-            s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-            s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-            const int X = 2 * j0 + col;
-            if (g == fq && 1 + fcl + 64 * g <= 254 && X >= 0 && X < Wo) {
-              if (2 * i - 1 >= 0 && 2 * i - 1 < Ho) F->Y[(size_t)(2 * i - 1) * Wo + X] = Uv[0] + (b + s0);
-              if (2 * i < Ho) F->Y[(size_t)(2 * i) * Wo + X] = Uv[1] + (b + s1);
+          }
+          float mine[2] = {0.f, 0.f};
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+#pragma unroll
+            for (int rw = 0; rw < 2; ++rw) {
+              float sm = acc[e][rw].x + acc[e][rw].y;
+              sm += __shfl_xor_sync(0xffffffffu, sm, 1);
+              sm += __shfl_xor_sync(0xffffffffu, sm, 2);
+              if (e == fq) mine[rw] = sm;
+            }
+          const int X = 2 * j0 + col_own;
+          if (col_own <= 254 && X >= 0 && X < Wo) {
+#pragma unroll
+            for (int rw = 0; rw < 2; ++rw) {
+              const int oy = 2 * i - 1 + rw;
+              if (oy < 0 || oy >= Ho) continue;
+              const float fx = fxy[rw][0], fy = fxy[rw][1];
+              const float top = (1.f - fx) * (float)cv[rw][0] + fx * (float)cv[rw][1];
+              const float bot = (1.f - fx) * (float)cv[rw][2] + fx * (float)cv[rw][3];
+              const float U = 4.f * ((1.f - fy) * top + fy * bot);
+              F->Y[(size_t)oy * Wo + X] = U + (b + mine[rw]);
             }
           }
         }
