@@ -110,7 +110,7 @@ __device__ void window_stats(const uint16_t* s, int ncols, int* cs, unsigned* cs
 }
 
 template <int R, int KD, int TX>
-__global__ void __launch_bounds__(kZnccWarps * 32, 1)
+__global__ void __launch_bounds__(kZnccWarps * 32, (KD == 1 || (KD == 2 && R <= 5)) ? 2 : 1)
 zncc_wta_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ jobs) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int TY = kZnccTY;
