@@ -71,11 +71,11 @@ def peaks():
 # capture, per pair; valid only while the kernel's sources are unchanged since the capture
 # (checked by content hash), else the roofline reports traffic as null.
 MEASURED_TRAFFIC = {
-    "tc_dec3": {"bytes_per_pair": 669.65e6 / 16,
-                "sources": {"paper_2305_11566_gb300/csrc/conv_tc.cu": "71bdb6404d56",
-                            "paper_2305_11566_gb300/csrc/sv_ctx.cuh": "47f4f013d40a",
-                            "paper_2305_11566_gb300/csrc/sv_internal.cuh": "018c7630b6c8"},
-                "capture": "profiles/conv_tc_dec3_16x1242x375.md (16 pairs, scaled by pairs)"},
+    "tc_dec3_final": {"bytes_per_pair": 264.467e6 / 16,
+                      "sources": {"paper_2305_11566_gb300/csrc/conv_tc.cu": "4f2ccc5c7541",
+                                  "paper_2305_11566_gb300/csrc/sv_ctx.cuh": "1486f8a59fc9",
+                                  "paper_2305_11566_gb300/csrc/sv_internal.cuh": "f27a474eb515"},
+                      "capture": "profiles/dec3_final_fused_16x1242x375.md (16 pairs, scaled by pairs)"},
 }
 
 

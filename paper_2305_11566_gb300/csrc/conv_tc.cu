@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf0 + 8 * b, 1);
-      mbar_init(acce0 + 8 * b, 128);
+      mbar_init(acce0 + 8 * b, 4);  // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -448,11 +448,16 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       const int nrows = STEP * (st.cnt - 1) + RA;
       for (int ii = 0; ii < st.cnt; ++ii, ++tseq) {
         const uint32_t buf = tseq & 1;
-        if (!mbar_wait(accf0 + 8 * buf, (tseq >> 1) & 1, p.spin)) {
-          atomicCAS(p.err, 0, 4);
+        // lane 0 waits for the accumulator and tells the warp (a warp-uniform decision)
+        bool got = true;
+        if (lane == 0) got = mbar_wait(accf0 + 8 * buf, (tseq >> 1) & 1, p.spin);
+        got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+        if (!got) {
+          if (lane == 0) atomicCAS(p.err, 0, 4);
           ok = false;
           break;
         }
+        __syncwarp();  // orders the other lanes after lane 0's acquire of the barrier
         tc_fence_after();
         if (tid == 0) {
           // the tile's MMAs have completed: the rows the next tile of the strip no longer
@@ -492,7 +497,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
           }
         }
         tc_fence_before();
-        mbar_arrive(acce0 + 8 * buf);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acce0 + 8 * buf);  // the warp's TMEM reads are complete
       }
     }
   }
@@ -605,7 +611,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf0 + 8 * b, 1);
-      mbar_init(acce0 + 8 * b, kFusedEpi);
+      mbar_init(acce0 + 8 * b, kFusedEpi / 32);  // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -779,7 +785,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
         }
         if (k < ntiles) {
           const uint32_t buf = tseq & 1;
-          const bool got = mbar_wait(accf0 + 8 * buf, (tseq >> 1) & 1, p.spin);
+          // lane 0 of each warp waits; the OR below makes the decision uniform
+          const bool got = lane != 0 || mbar_wait(accf0 + 8 * buf, (tseq >> 1) & 1, p.spin);
           // all epilogue threads take the same decision, so none is left waiting at a
           // named barrier
           if (epi_any(!got)) {
@@ -827,7 +834,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
             }
           }
           tc_fence_before();
-          mbar_arrive(acce0 + 8 * buf);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acce0 + 8 * buf);  // the warp's TMEM reads are complete
           ++tseq;
         } else {
           // zero rows 2 Hu and 2 Hu + 1 below the output

@@ -137,10 +137,11 @@ __global__ void __launch_bounds__(256) edge_enc1(const EdgePair* __restrict__ pa
       xv[r][kx][1] = v.y;
     }
   for (int c0 = 0; c0 < C1; c0 += 8) {
-    float acc[4][8];
+    // packed FP32 FMA: channel pairs (c, c + 1) of one pixel share the input value
+    float2 acc[4][4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float bj = wsm[18 * C1 + c0 + j];
+    for (int j = 0; j < 4; ++j) {
+      const float2 bj = make_float2(wsm[18 * C1 + c0 + 2 * j], wsm[18 * C1 + c0 + 2 * j + 1]);
 #pragma unroll
       for (int k = 0; k < 4; ++k) acc[k][j] = bj;
     }
@@ -153,13 +154,14 @@ __global__ void __launch_bounds__(256) edge_enc1(const EdgePair* __restrict__ pa
           const int kk = (ky * 3 + kx) * 2 + ch;
           const float4 a = *reinterpret_cast<const float4*>(&wsm[kk * C1 + c0]);
           const float4 b = *reinterpret_cast<const float4*>(&wsm[kk * C1 + c0 + 4]);
+          const float2 w2[4] = {make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                                make_float2(b.z, b.w)};
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const float x = xv[2 * k + ky][kx][ch];
-            acc[k][0] = fmaf(a.x, x, acc[k][0]); acc[k][1] = fmaf(a.y, x, acc[k][1]);
-            acc[k][2] = fmaf(a.z, x, acc[k][2]); acc[k][3] = fmaf(a.w, x, acc[k][3]);
-            acc[k][4] = fmaf(b.x, x, acc[k][4]); acc[k][5] = fmaf(b.y, x, acc[k][5]);
-            acc[k][6] = fmaf(b.z, x, acc[k][6]); acc[k][7] = fmaf(b.w, x, acc[k][7]);
+            const float2 xx = make_float2(x, x);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[k][j] = __ffma2_rn(w2[j], xx, acc[k][j]);
           }
         }
     if (X < W1) {
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(256) edge_enc1(const EdgePair* __restrict__ pa
         uint32_t pk[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(acc[k][2 * j], 0.f), fmaxf(acc[k][2 * j + 1], 0.f));
+          __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(acc[k][j].x, 0.f), fmaxf(acc[k][j].y, 0.f));
           pk[j] = *reinterpret_cast<uint32_t*>(&h);
         }
         *reinterpret_cast<uint4*>(P->e1 + ((size_t)Y * W1 + X) * C1 + c0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
