@@ -184,7 +184,9 @@ SV_API sv_status sv_adam_step(sv_ctx* ctx, const void* grad, int step, double lr
  * pageable; any pitch >= width, no alignment rule) and disp_out[i] host H x W FP32.
  * The images are copied into the context's device workspace on `stream`, the
  * pipeline runs there and the results are copied back; returns after the stream has
- * been synchronised. */
+ * been synchronised.  With option "host_copy" and device-accessible host memory (pinned /
+ * mapped) one kernel gathers all images (and optionally one writes all results back),
+ * reading and writing host memory directly; otherwise one copy call per buffer. */
 SV_API sv_status sv_pipeline_host(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, float* const* disp_out,
                                   sv_stream stream);
 
@@ -237,6 +239,10 @@ SV_API sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream);
  *                    layer, the final conv and the residual in one kernel (d3 stays in
  *                    shared memory) when the decoder widths allow it and every output
  *                    width is even; 0: separate kernels (d3 materialised in HBM)
+ *   "host_copy"      sv_pipeline_host with device-accessible (pinned) host buffers: 0 one
+ *                    copy call per buffer, 1 (default) one kernel gathers the images and
+ *                    the results go back by copy calls, 2 kernels both ways (GPU writes
+ *                    to host memory were the slowest of the three on GB300)
  *   "debug_plans"    1: print each tensor-core layer's launch plan (ring depth, shared
  *                    memory, CTAs per SM, grid, strips) to stderr when a call is prepared
  *   "graphs"         1 (default): sv_pipeline on an SV_BF16 context captures each batch

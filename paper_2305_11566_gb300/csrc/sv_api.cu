@@ -416,23 +416,75 @@ sv_status sv_pipeline_host(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, float
   sv_status s = c->cuda(c->host_img.ensure(img_off[n_pairs]), "alloc image staging");
   if (!s) s = c->cuda(c->host_out.ensure(out_off[n_pairs] * sizeof(float)), "alloc output staging");
   if (s) return s;
+  // Device-accessible views of the host buffers (pinned or mapped host memory, reached
+  // through the unified address space): with all of them, one kernel gathers every image
+  // and one scatters every result; otherwise (pageable memory) one copy call per buffer.
+  auto dev_view = [](const void* ptr) -> void* {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+  };
+  bool direct = c->host_copy > 0;
+  const bool scatter = c->host_copy > 1;
+  std::vector<sv::HostRowCopy> jobs(3 * (size_t)n_pairs);
   std::vector<float*> dout(n_pairs);
+  int max_rows = 0;
   for (int i = 0; i < n_pairs; ++i) {
     const sv_pair& p = pairs[i];
     const int dpitch = (p.width + 15) / 16 * 16;
     uint8_t* L = (uint8_t*)c->host_img.p + img_off[i];
     uint8_t* R = L + (size_t)dpitch * p.height;
-    s = c->cuda(cudaMemcpy2DAsync(L, dpitch, p.left, p.pitch, p.width, p.height, cudaMemcpyHostToDevice, st), "H2D");
-    if (!s) s = c->cuda(cudaMemcpy2DAsync(R, dpitch, p.right, p.pitch, p.width, p.height, cudaMemcpyHostToDevice, st),
-                        "H2D");
-    if (s) return s;
     dev[i] = p;
     dev[i].left = L;
     dev[i].right = R;
     dev[i].pitch = dpitch;
     dout[i] = (float*)c->host_out.p + out_off[i];
+    max_rows = std::max(max_rows, p.height);
+    if (direct) {
+      void* lv = dev_view(p.left);
+      void* rv = dev_view(p.right);
+      void* ov = scatter ? dev_view(disp_out[i]) : (void*)1;
+      if (!lv || !rv || !ov) {
+        direct = false;
+      } else {
+        jobs[2 * i] = {(const unsigned char*)lv, L, p.pitch, dpitch, p.width, p.height};
+        jobs[2 * i + 1] = {(const unsigned char*)rv, R, p.pitch, dpitch, p.width, p.height};
+        const int ob = (int)sizeof(float) * p.width;
+        jobs[2 * (size_t)n_pairs + i] = {(const unsigned char*)dout[i], (unsigned char*)ov, ob, ob, ob, p.height};
+      }
+    }
   }
   if ((s = c->check_pairs(dev.data(), n_pairs))) return s;
+  if (direct) {
+    const size_t jb = sizeof(sv::HostRowCopy) * jobs.size();
+    if ((s = c->cuda(c->host_jobs.ensure(jb), "alloc copy jobs"))) return s;
+    if ((s = c->cuda(cudaMemcpyAsync(c->host_jobs.p, jobs.data(), jb, cudaMemcpyHostToDevice, st), "copy jobs")))
+      return s;
+    const sv::HostRowCopy* dj = (const sv::HostRowCopy*)c->host_jobs.p;
+    if ((s = c->cuda(sv::launch_copy_rows(dj, 2 * n_pairs, max_rows, 1, st), "gather images"))) return s;
+    if ((s = c->pipeline(dev.data(), n_pairs, dout.data(), st))) return s;
+    if (scatter) {
+      if ((s = c->cuda(sv::launch_copy_rows(dj + 2 * n_pairs, n_pairs, max_rows, 1, st), "scatter results")))
+        return s;
+    } else {
+      for (int i = 0; i < n_pairs; ++i)
+        if ((s = c->cuda(cudaMemcpyAsync(disp_out[i], dout[i], sizeof(float) * pairs[i].width * pairs[i].height,
+                                         cudaMemcpyDeviceToHost, st), "D2H")))
+          return s;
+    }
+    return c->cuda(cudaStreamSynchronize(st), "synchronise");
+  }
+  for (int i = 0; i < n_pairs; ++i) {
+    const sv_pair& p = pairs[i];
+    s = c->cuda(cudaMemcpy2DAsync((void*)dev[i].left, dev[i].pitch, p.left, p.pitch, p.width, p.height,
+                                  cudaMemcpyHostToDevice, st), "H2D");
+    if (!s) s = c->cuda(cudaMemcpy2DAsync((void*)dev[i].right, dev[i].pitch, p.right, p.pitch, p.width, p.height,
+                                          cudaMemcpyHostToDevice, st), "H2D");
+    if (s) return s;
+  }
   if ((s = c->pipeline(dev.data(), n_pairs, dout.data(), st))) return s;
   for (int i = 0; i < n_pairs; ++i)
     if ((s = c->cuda(cudaMemcpyAsync(disp_out[i], dout[i], sizeof(float) * pairs[i].width * pairs[i].height,
@@ -497,6 +549,11 @@ sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value) {
     if (value != 0 && value != 1) return c->fail(SV_ERR_INVALID_ARG, "graphs must be 0 or 1");
     c->use_graphs = value != 0;
     if (!c->use_graphs) c->drop_graphs();
+    return SV_OK;
+  }
+  if (!strcmp(key, "host_copy")) {
+    if (value < 0 || value > 2) return c->fail(SV_ERR_INVALID_ARG, "host_copy must be 0, 1 or 2");
+    c->host_copy = (int)value;
     return SV_OK;
   }
   if (!strcmp(key, "fused_final")) {

@@ -97,11 +97,13 @@ struct Ctx {
   int train_elem = 0;
   bool train_ready = false;
   DevBuf host_img, host_out;     // device staging of sv_pipeline_host
+  DevBuf host_jobs;              // row-copy job tables of sv_pipeline_host (gather + scatter)
   std::vector<unsigned char> tc_host_tables;
   long long spin_limit = 4000000000LL;  // clock64 cycles a device-side wait may spin
   int tc_strip_rows = 0;                // 0: automatic
   int debug_plans = 0;                  // 1: print each tensor-core layer's launch plan to stderr
   int fused_final = 1;                  // 1: last decoder layer + final conv in one kernel when possible
+  int host_copy = 1;                    // sv_pipeline_host: 0 copy calls, 1 gather kernel in, 2 kernels both ways
   bool last_fused = false;              // the last tensor-core call did not materialise d3
   int tc_ctas_per_sm = 0;               // 0: deepest row ring (one CTA per SM); k: ring sized for k
   int tc_rows_override[6] = {0, 0, 0, 0, 0, 0};  // per tensor-core layer, set by the autotuner
@@ -201,7 +203,7 @@ struct Ctx {
     drop_graphs();
     for (auto e : ev_free) cudaEventDestroy(e);
     ev_free.clear();
-    host_img.release(); host_out.release(); err_flag.release(); tune_out.release();
+    host_img.release(); host_out.release(); host_jobs.release(); err_flag.release(); tune_out.release();
     w32.release(); w64.release(); wbf.release(); wfuse.release(); zpairs.release(); zjobs.release();
     coarse_maps.release();
     for (auto& b : act) b.release();

@@ -144,6 +144,15 @@ struct alignas(64) EdgePair {
   float* Y;                 // refined disparity [H][W]
   CUtensorMap d3_map;       // TMA view of d3 for the final conv (final_staged_by_tma(C))
 };
+// Row copy between device-accessible buffers (host_io.cu): `height` rows of `width`
+// elements of elem_bytes bytes.
+struct HostRowCopy {
+  const unsigned char* src;
+  unsigned char* dst;
+  int spitch, dpitch, width, height;  // pitches in bytes
+};
+cudaError_t launch_copy_rows(const HostRowCopy* jobs, int njobs, int max_rows, int elem_bytes, cudaStream_t st);
+
 // U = 4 x bilinear(coarse) at full-resolution pixel (X, Y), half-pixel centres, source
 // clamped to the coarse map (Sec. IV-C "linear scaling", reading N1), FP32.
 template <typename CT>

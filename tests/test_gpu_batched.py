@@ -112,3 +112,44 @@ def test_autotune_rejects_plain_form(svlib, batch):
         assert ei.value.status == binding.SV_ERR_UNSUPPORTED
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("pinned,mode", [(True, 0), (True, 1), (True, 2), (False, 2)])
+def test_pipeline_host_buffers(svlib, batch, pinned, mode):
+    """sv_pipeline_host: host images in, host disparity maps out, through copy calls (mode
+    0), a gather kernel (1) or gather and scatter kernels (2) over the CPU-GPU link for
+    pinned buffers; pageable buffers always take copy calls.  All must give exactly the
+    device-buffer pipeline's result (same kernels).
+    Odd pitches and an unaligned row start exercise the byte-wise copy path."""
+    pairs, dps = batch
+    s = torch.cuda.Stream()
+    ctx = make_ctx()
+    try:
+        ref = run(ctx, dps, s)
+        ctx.set_option("host_copy", mode)
+        Ls, Rs, outs, Ws, Hs, ps, Ds = [], [], [], [], [], [], []
+        for i, (p, dp) in enumerate(zip(pairs, dps)):
+            H, W = p.left.shape
+            extra = 3 if i % 2 else 16                 # odd pitch for every other pair
+            lh = np.zeros((H, W + extra), np.uint8)
+            rh = np.zeros((H, W + extra), np.uint8)
+            lh[:, :W] = p.left
+            rh[:, :W] = p.right
+            o = np.zeros((H, W), np.float32)
+            if pinned:
+                lh = torch.from_numpy(lh).pin_memory()
+                rh = torch.from_numpy(rh).pin_memory()
+                o = torch.from_numpy(o).pin_memory()
+            Ls.append(lh)
+            Rs.append(rh)
+            outs.append(o)
+            Ws.append(W)
+            Hs.append(H)
+            ps.append(W + extra)
+            Ds.append(dp.max_disp)
+        ctx.pipeline_host(Ls, Rs, Ws, Hs, ps, Ds, outs, stream=s)
+        for o, r in zip(outs, ref):
+            got = o.numpy() if pinned else o
+            assert np.array_equal(got, r.cpu().numpy())
+    finally:
+        ctx.close()
