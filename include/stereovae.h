@@ -243,6 +243,9 @@ SV_API sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream);
  *                    copy call per buffer, 1 (default) one kernel gathers the images and
  *                    the results go back by copy calls, 2 kernels both ways (GPU writes
  *                    to host memory were the slowest of the three on GB300)
+ *   "host_chunks"    1..4 (default 3): sv_pipeline_host computes a batch in up to this many
+ *                    parts (at least 8 pairs each) and copies a part's results back while
+ *                    the next part computes
  *   "debug_plans"    1: print each tensor-core layer's launch plan (ring depth, shared
  *                    memory, CTAs per SM, grid, strips) to stderr when a call is prepared
  *   "graphs"         1 (default): sv_pipeline on an SV_BF16 context captures each batch

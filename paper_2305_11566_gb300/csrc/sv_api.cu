@@ -465,17 +465,34 @@ sv_status sv_pipeline_host(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, float
       return s;
     const sv::HostRowCopy* dj = (const sv::HostRowCopy*)c->host_jobs.p;
     if ((s = c->cuda(sv::launch_copy_rows(dj, 2 * n_pairs, max_rows, 1, st), "gather images"))) return s;
-    if ((s = c->pipeline(dev.data(), n_pairs, dout.data(), st))) return s;
     if (scatter) {
+      if ((s = c->pipeline(dev.data(), n_pairs, dout.data(), st))) return s;
       if ((s = c->cuda(sv::launch_copy_rows(dj + 2 * n_pairs, n_pairs, max_rows, 1, st), "scatter results")))
         return s;
-    } else {
-      for (int i = 0; i < n_pairs; ++i)
-        if ((s = c->cuda(cudaMemcpyAsync(disp_out[i], dout[i], sizeof(float) * pairs[i].width * pairs[i].height,
-                                         cudaMemcpyDeviceToHost, st), "D2H")))
-          return s;
+      return c->cuda(cudaStreamSynchronize(st), "synchronise");
     }
-    return c->cuda(cudaStreamSynchronize(st), "synchronise");
+    // the batch in parts of at least 8 pairs: a part's results are copied back on the
+    // context's copy stream while the next part computes
+    const int nch = std::max(1, std::min(c->host_chunks, n_pairs / 8));
+    if (!c->copy_stream && (s = c->cuda(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "stream")))
+      return s;
+    for (auto& e : c->chunk_done)
+      if (!e && (s = c->cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event"))) return s;
+    int start = 0;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int cnt = ch + 1 == nch ? n_pairs - start : n_pairs / nch;
+      if ((s = c->pipeline(dev.data() + start, cnt, dout.data() + start, st))) break;
+      if ((s = c->cuda(cudaEventRecord(c->chunk_done[ch], st), "record"))) break;
+      if ((s = c->cuda(cudaStreamWaitEvent(c->copy_stream, c->chunk_done[ch], 0), "wait"))) break;
+      for (int i = start; i < start + cnt && !s; ++i)
+        s = c->cuda(cudaMemcpyAsync(disp_out[i], dout[i], sizeof(float) * pairs[i].width * pairs[i].height,
+                                    cudaMemcpyDeviceToHost, c->copy_stream), "D2H");
+      if (s) break;
+      start += cnt;
+    }
+    const sv_status s1 = c->cuda(cudaStreamSynchronize(st), "synchronise");
+    const sv_status s2 = c->cuda(cudaStreamSynchronize(c->copy_stream), "synchronise copies");
+    return s ? s : s1 ? s1 : s2;
   }
   for (int i = 0; i < n_pairs; ++i) {
     const sv_pair& p = pairs[i];
@@ -549,6 +566,11 @@ sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value) {
     if (value != 0 && value != 1) return c->fail(SV_ERR_INVALID_ARG, "graphs must be 0 or 1");
     c->use_graphs = value != 0;
     if (!c->use_graphs) c->drop_graphs();
+    return SV_OK;
+  }
+  if (!strcmp(key, "host_chunks")) {
+    if (value < 1 || value > 4) return c->fail(SV_ERR_INVALID_ARG, "host_chunks must be 1..4");
+    c->host_chunks = (int)value;
     return SV_OK;
   }
   if (!strcmp(key, "host_copy")) {

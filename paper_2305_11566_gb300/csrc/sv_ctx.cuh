@@ -98,6 +98,9 @@ struct Ctx {
   bool train_ready = false;
   DevBuf host_img, host_out;     // device staging of sv_pipeline_host
   DevBuf host_jobs;              // row-copy job tables of sv_pipeline_host (gather + scatter)
+  cudaStream_t copy_stream = nullptr;    // sv_pipeline_host: results go back here while the
+  cudaEvent_t chunk_done[4] = {nullptr, nullptr, nullptr, nullptr};  // next part computes
+  int host_chunks = 3;                  // parts of an sv_pipeline_host batch (>= 8 pairs each)
   std::vector<unsigned char> tc_host_tables;
   long long spin_limit = 4000000000LL;  // clock64 cycles a device-side wait may spin
   int tc_strip_rows = 0;                // 0: automatic
@@ -201,6 +204,14 @@ struct Ctx {
   void release_all() {
     prof_flush();
     drop_graphs();
+    if (copy_stream) cudaStreamSynchronize(copy_stream);
+    for (auto& e : chunk_done)
+      if (e) {
+        cudaEventDestroy(e);
+        e = nullptr;
+      }
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    copy_stream = nullptr;
     for (auto e : ev_free) cudaEventDestroy(e);
     ev_free.clear();
     host_img.release(); host_out.release(); host_jobs.release(); err_flag.release(); tune_out.release();

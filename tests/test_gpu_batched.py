@@ -153,3 +153,24 @@ def test_pipeline_host_buffers(svlib, batch, pinned, mode):
             assert np.array_equal(got, r.cpu().numpy())
     finally:
         ctx.close()
+
+
+def test_pipeline_host_two_halves(svlib):
+    """16 or more pairs: sv_pipeline_host computes the batch in two halves and copies the
+    first half's results back while the second half computes; the result must equal the
+    device-buffer pipeline's for every pair."""
+    pairs = synth.batch_uneven(16, seed=9300)
+    dps = [binding.to_device(p, D) for p, D in pairs]
+    s = torch.cuda.Stream()
+    ctx = make_ctx()
+    try:
+        ref = run(ctx, dps, s)
+        Ls = [torch.from_numpy(synth.pitched(p.left)).pin_memory() for p, _ in pairs]
+        Rs = [torch.from_numpy(synth.pitched(p.right)).pin_memory() for p, _ in pairs]
+        outs = [torch.zeros((p.height, p.width), dtype=torch.float32).pin_memory() for p, _ in pairs]
+        ctx.pipeline_host(Ls, Rs, [p.width for p, _ in pairs], [p.height for p, _ in pairs],
+                          [x.shape[1] for x in Ls], [D for _, D in pairs], outs, stream=s)
+        for o, r in zip(outs, ref):
+            assert torch.equal(o, r.cpu())
+    finally:
+        ctx.close()
