@@ -193,6 +193,34 @@ def work_per_pair(shape):
     return f, zbytes
 
 
+# ------------------------------------------------------------------ ranks (host side)
+def rank_pair_seeds(rank: int, pairs_per_rank: int, distinct: int):
+    """Seeds of one rank's distinct synthetic pairs: every rank gets its own pairs (the
+    work is sharded by pairs, no data-path collective), disjoint from every other rank's."""
+    return [1000 + rank * pairs_per_rank + i for i in range(min(distinct, pairs_per_rank))]
+
+
+def rank_reducers(world: int, dist, device: str):
+    """barrier() and max_over_ranks(x): the step time of the job is the slowest rank's."""
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return barrier, max_over_ranks
+
+
+def whole_job_value(pairs_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Pairs per second of the whole job: every rank's pairs over the slowest rank's step."""
+    return pairs_per_rank * world / (ms_per_step / 1e3)
+
+
 # ------------------------------------------------------------------ our implementation
 def run_ours(args):
     import numpy as np
@@ -212,22 +240,13 @@ def run_ours(args):
     shape = synth.NET_WIDE
     params = synth.he_normal_weights(shape, 7)
     B = args.pairs
-    distinct = [synth.make_pair(W, H, DMAX, 1000 + rank * B + i) for i in range(min(args.distinct, B))]
+    distinct = [synth.make_pair(W, H, DMAX, sd) for sd in rank_pair_seeds(rank, B, args.distinct)]
     pairs = [distinct[i % len(distinct)] for i in range(B)]
     dps_distinct = [binding.to_device(p, D) for p in distinct]
     dps = [dps_distinct[i % len(distinct)] for i in range(B)]
     pk, pk_kind = peaks()
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = rank_reducers(world, dist, "cuda")
 
     forms = []
     if args.form in ("auto", "both"):
@@ -450,7 +469,7 @@ def run_ours(args):
                  "loss_last": float(Lt.item())}
         tctx.close()
 
-    value = B * world / (R["ms_per_step"] / 1e3)
+    value = whole_job_value(B, world, R["ms_per_step"])
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True, "scaling": "weak",
