@@ -239,6 +239,10 @@ SV_API sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream);
  *                    layer, the final conv and the residual in one kernel (d3 stays in
  *                    shared memory) when the decoder widths allow it and every output
  *                    width is even; 0: separate kernels (d3 materialised in HBM)
+ *   "fused_ring"     0 (default): the fused kernel stages as many input rows ahead as
+ *                    shared memory holds; 4..16: at most this many rows in its ring
+ *   "fused_prefetch" 0..16 (default 4): the fused kernel's producer prefetches the input row
+ *                    this many rows ahead into L2 (0: no prefetch)
  *   "host_copy"      sv_pipeline_host with device-accessible (pinned) host buffers: 0 one
  *                    copy call per buffer, 1 (default) one kernel gathers the images and
  *                    the results go back by copy calls, 2 kernels both ways (GPU writes

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include <cuda.h>
+#include <type_traits>
 #include <cudaTypedefs.h>
 
 #include "sv_ctx.cuh"
@@ -151,6 +152,14 @@ __device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* tm, i
           dst),
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(c), "r"(x), "r"(y), "r"(bar)
       : "memory");
+}
+// L2 prefetch of a 3-D TMA box (no shared memory, no completion): a later load of the same
+// box then finds it in L2.
+__device__ __forceinline__ void tma_prefetch3(const CUtensorMap* tm, int c, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)),
+               "r"(c), "r"(x), "r"(y)
+               : "memory");
 }
 __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* tm) {
   asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
@@ -419,7 +428,16 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
                 mma_bf16(dcol, a0[t] + ak + 2 * k4, a_hi, b0[t] + bk + 16 * k4, b_hi, idesc,
                          (kb | t | k4) != 0 ? 1u : 0u);
           }
-          mma_commit(accf0 + 8 * buf);  // also releases the tile's rows (the epilogue arrives)
+          mma_commit(accf0 + 8 * buf);
+          // the rows the strip's next tile no longer reads go back to the producer as soon as
+          // these MMAs complete: one commit per row, arriving on that row's empty barrier
+          {
+            const int nrel = ii + 1 < st.cnt ? STEP : RA;
+            for (int r = 0; r < nrel; ++r) {
+              const uint32_t sl = tb.slot + r;
+              mma_commit(empty0 + 8 * (sl >= ring ? sl - ring : sl));
+            }
+          }
           tb.slot += STEP;            // first row of the next tile (the strip's last tile: + RA)
           if (ii + 1 == st.cnt) tb.slot += RA - STEP;
           while (tb.slot >= ring) tb.slot -= ring;
@@ -439,13 +457,11 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
     // ------------------------------------------------------------ epilogue (warps 0-3)
     const int m = warp * 32 + lane;
     uint32_t tseq = 0;
-    RingPos rel;  // thread 0: slot of the next staged row to hand back to the producer
     for (int s = crank; s < p.n_strips && ok; s += cpg) {
       const Strip st = p.strips[s];
       const LayerPair* L = p.lp + st.pair;
       const int Hu = L->Hu, Wu = L->Wu, Ho = L->Ho, Wo = L->Wo;
       bf16* const out = L->out;
-      const int nrows = STEP * (st.cnt - 1) + RA;
       for (int ii = 0; ii < st.cnt; ++ii, ++tseq) {
         const uint32_t buf = tseq & 1;
         // lane 0 waits for the accumulator and tells the warp (a warp-uniform decision)
@@ -459,12 +475,6 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
         }
         __syncwarp();  // orders the other lanes after lane 0's acquire of the barrier
         tc_fence_after();
-        if (tid == 0) {
-          // the tile's MMAs have completed: the rows the next tile of the strip no longer
-          // reads can be reloaded
-          const int rel_hi = ii + 1 < st.cnt ? STEP * (ii + 1) : nrows;
-          for (int r = STEP * ii; r < rel_hi; ++r, rel.next(ring)) mbar_arrive(empty0 + 8 * rel.slot);
-        }
         const int i = st.i0 + ii, j = st.j0 + m;
         const int oy = MODE == TM_UP2 ? 2 * i + py : i;
         const int ox = MODE == TM_UP2 ? 2 * j + px : j;
@@ -509,20 +519,28 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
 }
 
 // ------------------------------------------------------------------ fused dec3 + final
-// The last decoder layer (nearest x2 + crop + 3x3 conv + ReLU, a10), the final 3x3 conv to
-// one channel and the residual onto U (a11) in one kernel, so that d3 never leaves the SM.
-// A CTA computes all four output phases of 128 input pixels of one row per tile (16 MMAs
-// per phase into four TMEM accumulators), writes the two resulting d3 rows (BF16, 256
-// columns) into a 4-row ring in shared memory, and its epilogue warps run the final conv
-// on the ring: after tile i the final rows 2i - 1 and 2i have their 3x3 neighbourhoods.
+// The last decoder layer (nearest x2 + crop + 3x3 conv + ReLU), the final 3x3 conv to one
+// channel and the residual onto U in one kernel, so that d3 never leaves the SM.  A CTA
+// computes all four output phases of 128 input pixels of one row per tile (16 MMAs per
+// phase into four TMEM accumulators) and writes the two resulting d3 rows (BF16, 256
+// columns) into shared memory, in the swizzled K-major layout of an MMA operand.  The
+// final conv runs on the tensor cores as well: with a d3 row as A (M = 128 columns, K = the
+// d3 channels) and one B holding all nine taps' weights (N = 32: each weight split into a
+// BF16 high part and a BF16 low part, hi + lo = w to about 2^-16 relative), one MMA pass
+// per row and column half gives every pixel's nine tap products P_r(x, ky, kx).  The
+// epilogue adds them: out(y, x) = sum over (ky, kx) of P_{y+ky-1}(x+kx-1, ky, kx), the kx
+// shifts by warp shuffles, the ky rows through two partial sums per column carried from
+// tile to tile, so that tile i (d3 rows 2i, 2i + 1) completes output rows 2i - 1 and 2i.
 // Column strips step by 127 input pixels (tile = input pixels j0 .. j0 + 127 with
 // j0 = 127 s - 1), so each strip's 254 final columns 2 j0 + 1 .. 2 j0 + 254 have both
 // neighbours in the tile; a strip starts with one halo tile above its first row (none at
-// row 0, where the ring's rows -2, -1 are zero) and, when the output height is even, ends
-// with a zero tile below the last row.  d3 outside the output is stored as zero (the final
-// conv's padding).  An odd output height crops half of the last up-sampled row: the last
-// tile's phase-0 rows then use the unfolded weights of that tap row alone (4 extra B
-// blocks), which gives the cropped conv exactly.  Odd output widths are not handled here.
+// row 0, where the carried sums start at zero: the padding above).  d3 outside the output
+// is stored as zero (the final conv's padding), and the rows below an even-height output
+// are zero, so the carried sum of the last row is complete after the last tile.  An odd
+// output height crops half of the last up-sampled row: the last tile's phase-0 rows then
+// subtract the kernel row that falls on the cropped half (4 extra MMA groups with B
+// negated, reusing phase-1 blocks), which gives the cropped conv.  Odd output widths are not
+// handled here.
 struct alignas(64) FusedPair {
   float* Y;                    // refined disparity [Ho][Wo]
   const int16_t* coarse;       // coarse map [h4][w4]
@@ -535,25 +553,29 @@ struct FusedParams {
   const FusedPair* fp;
   const Strip* strips;
   int n_strips;
-  const bf16* wpack;  // [20][NT x cin]: 16 (phase, tap) blocks, then 4 last-row blocks (px, co)
+  const bf16* wpack;  // [16][NT x cin] decoder blocks, then the final conv's [32 x NT] block
   const float* bias;  // [NT] decoder bias
-  const float* wf;    // [9][NT] final conv weights (tap-major)
   const float* bf;    // final bias
   int ring;
+  int pf;             // rows the producer prefetches into L2 ahead of the row it loads
   int* err;
   long long spin;
 };
 
 constexpr int kFusedNpx = 130;
+constexpr int kFinalN = 32;  // final conv MMA width: 9 high parts, 9 low parts, 14 zero rows
 __host__ __device__ inline uint32_t fused_kbs(int rb) { return (uint32_t)((kFusedNpx * rb + 1023) / 1024 * 1024); }
-__host__ __device__ inline size_t fused_param_bytes(int NT) { return (size_t)(NT + 9 * NT + 4) * 4; }
+__host__ __device__ inline size_t fused_wpack_elems(int NT, int cin) {
+  return (size_t)16 * NT * cin + (size_t)kFinalN * NT;
+}
+// decoder bias [NT], final bias (+ 3 pad), tap-sum exchange [2 parities][8 warps][2 sides][8]
+__host__ __device__ inline size_t fused_param_bytes(int NT) { return (size_t)(NT + 4 + 256) * 4; }
 __host__ __device__ inline size_t fused_smem_bytes(int NT, int cin, int ring) {
-  const int rb = cin * 2;
-  const size_t head = ((size_t)20 * NT * cin * 2 + fused_param_bytes(NT) + 1023) / 1024 * 1024;
-  return 1024 + head + (size_t)ring * fused_kbs(rb) + (size_t)4 * 256 * NT * 2 + (size_t)(2 * ring + 4) * 8 + 16;
+  const size_t head = (fused_wpack_elems(NT, cin) * 2 + fused_param_bytes(NT) + 1023) / 1024 * 1024;
+  return 1024 + head + (size_t)ring * fused_kbs(cin * 2) + (size_t)4 * 256 * NT * 2 + (size_t)(2 * ring + 8) * 8 + 16;
 }
 
-// 320 threads: warps 0-7 epilogue + final conv, warp 8 TMEM allocation + MMA issue, warp 9 TMA.
+// 320 threads: warps 0-7 epilogue, warp 8 TMEM allocation + MMA issue, warp 9 TMA.
 constexpr int kFusedThreads = 320, kFusedEpi = 256;
 // Named barrier 1 over the 256 epilogue threads (warps 0-7) only; the producer and MMA warps
 // never take part.
@@ -568,14 +590,21 @@ __device__ __forceinline__ bool epi_any(bool v) {
       : "memory");
   return r != 0;
 }
+__device__ __forceinline__ void tmem_ld2_nowait(uint32_t taddr, uint32_t& a, uint32_t& b) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(a), "=r"(b) : "r"(taddr));
+}
 
 template <int NT, int RB>
 __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_constant__ FusedParams p) {
   constexpr int RA = 3, KPR = RB / 32, CIN = RB / 2;
   constexpr uint32_t KBS = (kFusedNpx * RB + 1023) / 1024 * 1024;
   constexpr int NCH = NT / 8;                                  // 16-byte chunks per d3 pixel
-  constexpr int SWS = NCH == 4 ? 1 : 2;                        // ring chunk swizzle: col >> SWS
+  constexpr int SWS = NCH == 4 ? 1 : 2;                        // d3 chunk swizzle: col >> SWS
+  constexpr uint32_t PXB = NT * 2;                             // bytes per d3 pixel
   constexpr uint32_t BBLK = NT * CIN * 2;                      // one (phase, tap) weight block
+  constexpr int FKS = NT / 16;                                 // K steps of the final conv
+  constexpr uint32_t kCols = 512;                              // 2 x 4 x NT accumulators + 2 x 128 partials
+  constexpr uint32_t FCOL = 8 * NT;                            // first TMEM column of the final partials
   static_assert(NT == 16 || NT == 32, "fused decoder widths");
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -583,15 +612,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
   unsigned char* gbase = smem_raw + (base - raw);
   const uint32_t ring = (uint32_t)p.ring;
   const uint32_t sB = base;
-  const uint32_t sPar = sB + 20 * BBLK;
+  const uint32_t sF = sB + 16 * BBLK;                          // final conv B [32 x NT]
+  const uint32_t sPar = sF + kFinalN * NT * 2;
   const uint32_t sA = (sPar + (uint32_t)fused_param_bytes(NT) + 1023u) & ~1023u;
-  const uint32_t sD = sA + ring * KBS;                         // d3 ring [4][256][NCH] x 16 B
-  const uint32_t bars = sD + 4 * 256 * NT * 2;
+  const uint32_t sD = sA + ring * KBS;                         // d3 rows [4][256][NCH] x 16 B
+  const uint32_t bars = sD + 4 * 256 * PXB;
   const uint32_t full0 = bars, empty0 = bars + ring * 8, accf0 = bars + 2 * ring * 8, acce0 = accf0 + 16;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + (acce0 + 16 - base));
+  const uint32_t finf0 = acce0 + 16, fine0 = finf0 + 16;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + (fine0 + 16 - base));
   float* bias_s = reinterpret_cast<float*>(gbase + (sPar - base));
-  float* wf_s = bias_s + NT;
-  float* bf_s = wf_s + 9 * NT;
+  float* bf_s = bias_s + NT;
+  float* edge_s = bias_s + NT + 4;
   uint4* d3r = reinterpret_cast<uint4*>(gbase + (sD - base));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int crank = blockIdx.x, cpg = gridDim.x;
@@ -599,9 +630,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
   {
     const uint4* src = reinterpret_cast<const uint4*>(p.wpack);
     uint4* dst = reinterpret_cast<uint4*>(gbase);
-    for (int e = tid; e < (int)(20 * BBLK / 16); e += kFusedThreads) dst[e] = src[e];
+    for (int e = tid; e < (int)((16 * BBLK + kFinalN * NT * 2) / 16); e += kFusedThreads) dst[e] = src[e];
     for (int e = tid; e < NT; e += kFusedThreads) bias_s[e] = p.bias[e];
-    for (int e = tid; e < 9 * NT; e += kFusedThreads) wf_s[e] = p.wf[e];
     if (tid == 0) bf_s[0] = p.bf[0];
   }
   if (tid == 0) {
@@ -612,11 +642,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf0 + 8 * b, 1);
       mbar_init(acce0 + 8 * b, kFusedEpi / 32);  // one arrival per epilogue warp
+      mbar_init(finf0 + 8 * b, 1);
+      mbar_init(fine0 + 8 * b, kFusedEpi / 32);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_proxy_async();
-  constexpr uint32_t kCols = 8 * NT <= 128 ? 128 : 256;  // 2 buffers x 4 phases x NT
   if (warp == 8) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(kCols));
@@ -644,6 +675,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
         }
         const int first = st.i0 > 0 ? st.i0 - 1 : st.i0;
         const int nrows = (st.i0 + st.cnt - first) - 1 + RA;
+        const int Hu = F->Hu;
         for (int r = 0; r < nrows; ++r, ++q, w.next(ring)) {
           if (w.pass > 0 && !mbar_wait(empty0 + 8 * w.slot, (w.pass - 1) & 1, p.spin)) {
             atomicCAS(p.err, 0, 1);
@@ -653,6 +685,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
           const uint32_t fb = full0 + 8 * w.slot;
           mbar_expect_tx(fb, row_tx);
           tma_load3(sA + w.slot * KBS, &F->tm, 0, st.j0 - 1, first - 1 + r, fb);
+          const int yp = first - 1 + r + p.pf;  // L2 prefetch (inside the image, x clamped at 0)
+          if (p.pf > 0 && r + p.pf < nrows && yp >= 0 && yp < Hu) tma_prefetch3(&F->tm, 0, st.j0 > 1 ? st.j0 - 1 : 0, yp);
         }
       }
       const long long drain = p.spin > 2000000000LL ? p.spin : 2000000000LL;
@@ -666,10 +700,36 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((128u >> 4) << 24);
+      const uint32_t fdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kFinalN >> 3) << 17) | ((128u >> 4) << 24);
       constexpr uint32_t a_hi = desc_hi(8 * RB, swz_layout(RB));
       constexpr uint32_t b_hi = desc_hi((uint32_t)CIN * 16, 0);
-      uint32_t tseq = 0;
+      constexpr uint32_t fa_hi = desc_hi(8 * PXB, swz_layout(PXB));  // d3 rows: swizzled K-major
+      constexpr uint32_t fb_hi = desc_hi((uint32_t)NT * 16, 0);
+      const uint32_t fb0 = desc_lo(sF, 128);
+      uint32_t tseq = 0, fseq = 0;
       RingPos wt, tb;
+      // Final conv MMAs of the tile with sequence number fseq and image row i (d3 rows 2i and
+      // 2i + 1): waits until the epilogue has written those rows (the same arrival that frees
+      // the tile's accumulators) and has read out the partial-sum buffer's previous use.
+      auto issue_final = [&](int i) -> bool {
+        const uint32_t b = fseq & 1, use = fseq >> 1;
+        if (!mbar_wait(acce0 + 8 * b, use & 1, p.spin)) return false;
+        if (use > 0 && !mbar_wait(fine0 + 8 * b, (use - 1) & 1, p.spin)) return false;
+        tc_fence_after();
+#pragma unroll
+        for (int rho = 0; rho < 2; ++rho)
+#pragma unroll
+          for (int mu = 0; mu < 2; ++mu) {
+            const uint32_t a0 = desc_lo(sD + ((uint32_t)((2 * i + rho) & 3) * 256u + 128u * mu) * PXB, 16);
+            const uint32_t d = tmem + FCOL + b * 128 + 32 * (2 * rho + mu);
+#pragma unroll
+            for (int ks = 0; ks < FKS; ++ks)
+              mma_bf16(d, a0 + 2 * ks, fa_hi, fb0 + 16 * ks, fb_hi, fdesc, ks != 0 ? 1u : 0u);
+          }
+        mma_commit(finf0 + 8 * b);
+        ++fseq;
+        return true;
+      };
       for (int s = crank; s < p.n_strips && ok; s += cpg) {
         const Strip st = p.strips[s];
         const FusedPair* F = p.fp + st.pair;
@@ -698,48 +758,106 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
             slot_of_row[r] = sA + (sl >= ring ? sl - ring : sl) * KBS;
           }
           const bool crop_row = (first + k == Hu - 1) && (Ho & 1);  // odd height: last row's py = 0
+          // one straight-line issue sequence per case (the crop case adds 4 MMA groups)
+          auto issue_phases = [&](auto crop_tag) {
+            constexpr bool CROP = decltype(crop_tag)::value;
 #pragma unroll
-          for (int ph = 0; ph < 4; ++ph) {
-            const int py = ph >> 1, px = ph & 1;
-            const uint32_t dcol = tmem + buf * (4 * NT) + ph * NT;
+            for (int ph = 0; ph < 4; ++ph) {
+              const int py = ph >> 1, px = ph & 1;
+              const uint32_t dcol = tmem + buf * (4 * NT) + ph * NT;
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-              const int ro = t >> 1, co = t & 1;
-              const uint32_t a0 = desc_lo(slot_of_row[py + ro] + (uint32_t)(px + co) * RB, 16);
-              const uint32_t blk = (py == 0 && ro == 1 && crop_row) ? 16u + 2u * px + co : (uint32_t)(ph * 4 + t);
-              const uint32_t b0 = desc_lo(sB + blk * BBLK, 128);
+              for (int t = 0; t < 4; ++t) {
+                const int ro = t >> 1, co = t & 1;
+                const uint32_t a0 = desc_lo(slot_of_row[py + ro] + (uint32_t)(px + co) * RB, 16);
+                const uint32_t b0 = desc_lo(sB + (uint32_t)(ph * 4 + t) * BBLK, 128);
 #pragma unroll
-              for (int k4 = 0; k4 < KPR; ++k4)
-                mma_bf16(dcol, a0 + 2 * k4, a_hi, b0 + 16 * k4, b_hi, idesc, (t | k4) != 0 ? 1u : 0u);
+                for (int k4 = 0; k4 < KPR; ++k4)
+                  mma_bf16(dcol, a0 + 2 * k4, a_hi, b0 + 16 * k4, b_hi, idesc, (t | k4) != 0 ? 1u : 0u);
+                if (CROP && py == 0 && ro == 1) {
+                  // the kernel row ky = 2 of this tap reads the cropped-away up-sampled row:
+                  // subtract it again with the block of phase (1, px), tap (1, co), which
+                  // holds exactly that kernel row (B negated through the instruction
+                  // descriptor)
+                  const uint32_t bn = desc_lo(sB + (uint32_t)((2 + px) * 4 + 2 + co) * BBLK, 128);
+#pragma unroll
+                  for (int k4 = 0; k4 < KPR; ++k4)
+                    mma_bf16(dcol, a0 + 2 * k4, a_hi, bn + 16 * k4, b_hi, idesc | (1u << 14), 1u);
+                }
+              }
+            }
+          };
+          if (crop_row) issue_phases(std::true_type{});
+          else issue_phases(std::false_type{});
+          mma_commit(accf0 + 8 * buf);
+          // rows no later tile of the strip reads go back to the producer when these MMAs
+          // complete (one commit per row on its empty barrier)
+          {
+            const int nrel = k + 1 < ntiles ? 1 : RA;
+            for (int r = 0; r < nrel; ++r) {
+              const uint32_t sl = tb.slot + r;
+              mma_commit(empty0 + 8 * (sl >= ring ? sl - ring : sl));
             }
           }
-          mma_commit(accf0 + 8 * buf);
           tb.slot += 1;
           if (k + 1 == ntiles) tb.slot += RA - 1;
           while (tb.slot >= ring) tb.slot -= ring;
           ++tseq;
+          // the previous tile's final conv runs while this tile's decoder MMAs are queued
+          if (k > 0 && !issue_final(first + k - 1)) {
+            atomicCAS(p.err, 0, 2);
+            ok = false;
+          }
+        }
+        if (ok && ntiles > 0 && !issue_final(first + ntiles - 1)) {
+          atomicCAS(p.err, 0, 2);
+          ok = false;
         }
       }
+      const long long drain = p.spin > 2000000000LL ? p.spin : 2000000000LL;
       if (tseq > 0) {
         const uint32_t last = tseq - 1;
-        const long long drain = p.spin > 2000000000LL ? p.spin : 2000000000LL;
         if (!mbar_wait(accf0 + 8 * (last & 1), (last >> 1) & 1, drain)) atomicCAS(p.err, 0, 3);
+      }
+      if (fseq > 0) {
+        const uint32_t last = fseq - 1;
+        if (!mbar_wait(finf0 + 8 * (last & 1), (last >> 1) & 1, drain)) atomicCAS(p.err, 0, 3);
       }
     }
     __syncwarp();
   } else {
-    // ------------------------------------------------------------ epilogue + final conv (warps 0-7)
-    // warps 0-3 convert phases (0, 0), (0, 1) (d3 row 2i), warps 4-7 phases (1, 0), (1, 1)
-    // (row 2i + 1); TMEM lane quarter = warp % 4
+    // ------------------------------------------------------------ epilogue (warps 0-7)
+    // Decoder part: warps 0-3 convert phases (0, 0), (0, 1) (d3 row 2i), warps 4-7 phases
+    // (1, 0), (1, 1) (row 2i + 1); TMEM lane quarter = warp % 4.  Final part: thread tid owns
+    // local d3 column tid (TMEM lane tid % 128 of column half tid / 128), so warp w holds
+    // columns 32 w .. 32 w + 31.
     const int m = tid & 127;  // input pixel j0 + m of the tile / TMEM lane
     const int grp = tid >> 7;
-    // final conv: thread (cl, q) = (tid >> 2, tid & 3) takes channels 8q .. 8q + 7 of
-    // columns 1 + 4 cl .. 4 + 4 cl
-    const int fq = tid & 3, fcl = tid >> 2;
-    uint32_t tseq = 0;
-    RingPos rel;
+    uint32_t tseq = 0, fseq = 0;
     auto ring_at = [&](int y, int col, int q) -> uint4* {  // row y (any integer), local column col
       return d3r + (((uint32_t)y & 3u) * 256u + (uint32_t)col) * NCH + (uint32_t)(q ^ ((col >> SWS) & (NCH - 1)));
+    };
+    // residual U at output row Yr, column X: the four raw coarse values around it and the
+    // bilinear fractions (loads only; interpolated at the store)
+    auto coarse4 = [](const int16_t* cmap, int w4, int h4, int X, int Yr, int16_t (&cv)[4], float& fx, float& fy) {
+      float sx = (float)X * 0.25f - 0.375f;
+      sx = fminf(fmaxf(sx, 0.f), (float)(w4 - 1));
+      const int x0 = (int)sx, x1 = min(x0 + 1, w4 - 1);
+      float sy = (float)Yr * 0.25f - 0.375f;
+      sy = fminf(fmaxf(sy, 0.f), (float)(h4 - 1));
+      const int y0 = (int)sy, y1 = min(y0 + 1, h4 - 1);
+      const int16_t* c0p = cmap + (size_t)y0 * w4;
+      const int16_t* c1p = cmap + (size_t)y1 * w4;
+      cv[0] = __ldg(c0p + x0);
+      cv[1] = __ldg(c0p + x1);
+      cv[2] = __ldg(c1p + x0);
+      cv[3] = __ldg(c1p + x1);
+      fx = sx - (float)x0;
+      fy = sy - (float)y0;
+    };
+    auto residual = [](const int16_t (&cv)[4], float fx, float fy) {
+      const float top = (1.f - fx) * (float)cv[0] + fx * (float)cv[1];
+      const float bot = (1.f - fx) * (float)cv[2] + fx * (float)cv[3];
+      return 4.f * ((1.f - fy) * top + fy * bot);
     };
     for (int s = crank; s < p.n_strips && ok; s += cpg) {
       const Strip st = p.strips[s];
@@ -748,40 +866,24 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
       const int j0 = st.j0;
       const int first = st.i0 > 0 ? st.i0 - 1 : st.i0;
       const int ntiles = st.i0 + st.cnt - first;
-      const int nrows = ntiles - 1 + RA;
-      const bool below = st.i0 + st.cnt == Hu && Ho == 2 * Hu;  // zero tile under the last row
-      if (st.i0 == 0) {
-        // rows -2 and -1 of the ring: zero padding above the image
-        for (int e = tid; e < 2 * 256 * NCH; e += kFusedEpi) d3r[(2u * 256u) * NCH + e] = make_uint4(0, 0, 0, 0);
-      }
-      for (int k = 0; k < ntiles + (below ? 1 : 0); ++k) {
+      const bool below = st.i0 + st.cnt == Hu && Ho == 2 * Hu;  // zero rows under the last row
+      const int16_t* cmap = F->coarse;
+      float* Yout = F->Y;
+      const int w4 = F->w4, h4 = F->h4;
+      const int X = 2 * j0 + tid;                                // this thread's output column
+      const bool col_out = tid >= 1 && tid <= 254 && X >= 0 && X < Wo;
+      float c1 = 0.f, c2 = 0.f;  // carried partial sums of output rows 2i + 1 and 2i + 2
+      // raw coarse values of the residual U for the rows finished in the next iteration,
+      // loaded one iteration ahead so that their latency is hidden
+      int16_t cv[2][4] = {}, cvn[2][4] = {};
+      float fxy[2][2] = {}, fxyn[2][2] = {};
+      for (int k = 0; k <= ntiles; ++k) {
         const int i = first + k;
-        // residual U of the two final outputs this lane writes after this tile (column
-        // col_own, rows 2i - 1 and 2i): the coarse values are loaded now as raw integers (in
-        // flight while the tile's MMAs run) and interpolated at the store
-        const int col_own = 1 + 4 * fcl + fq;
-        int16_t cv[2][4];
-        float fxy[2][2];
-        {
-          const int X = min(max(2 * j0 + col_own, 0), Wo - 1);
-          float sx = (float)X * 0.25f - 0.375f;
-          sx = fminf(fmaxf(sx, 0.f), (float)(F->w4 - 1));
-          const int x0 = (int)sx, x1 = min(x0 + 1, F->w4 - 1);
+        if (k < ntiles && col_out) {
+          // iteration k + 1 finishes rows 2 (i + 1) - 3 and 2 (i + 1) - 2
 #pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            const int Yr = min(max(2 * i - 1 + r, 0), Ho - 1);
-            float sy = (float)Yr * 0.25f - 0.375f;
-            sy = fminf(fmaxf(sy, 0.f), (float)(F->h4 - 1));
-            const int y0 = (int)sy, y1 = min(y0 + 1, F->h4 - 1);
-            const int16_t* c0p = F->coarse + (size_t)y0 * F->w4;
-            const int16_t* c1p = F->coarse + (size_t)y1 * F->w4;
-            cv[r][0] = c0p[x0];
-            cv[r][1] = c0p[x1];
-            cv[r][2] = c1p[x0];
-            cv[r][3] = c1p[x1];
-            fxy[r][0] = sx - (float)x0;
-            fxy[r][1] = sy - (float)y0;
-          }
+          for (int r = 0; r < 2; ++r)
+            coarse4(cmap, w4, h4, X, min(max(2 * i - 1 + r, 0), Ho - 1), cvn[r], fxyn[r][0], fxyn[r][1]);
         }
         if (k < ntiles) {
           const uint32_t buf = tseq & 1;
@@ -795,10 +897,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
             break;
           }
           tc_fence_after();
-          if (tid == 0) {
-            const int rel_hi = k + 1 < ntiles ? k + 1 : nrows;
-            for (int r = k; r < rel_hi; ++r, rel.next(ring)) mbar_arrive(empty0 + 8 * rel.slot);
-          }
           const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + buf * (4 * NT);
           uint32_t rr[2][32];
           // both phases of this group in flight, one wait
@@ -817,12 +915,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
             if (valid) {
 #pragma unroll
               for (int q = 0; q < NCH; ++q) {
+                const float4 bl = *reinterpret_cast<const float4*>(bias_s + q * 8);
+                const float4 bh = *reinterpret_cast<const float4*>(bias_s + q * 8 + 4);
+                const float bv[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
                 uint32_t pk[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                   const int c0 = q * 8 + 2 * e;
-                  const float a = fmaxf(__uint_as_float(rr[h][c0]) + bias_s[c0], 0.f);
-                  const float b = fmaxf(__uint_as_float(rr[h][c0 + 1]) + bias_s[c0 + 1], 0.f);
+                  const float a = fmaxf(__uint_as_float(rr[h][c0]) + bv[2 * e], 0.f);
+                  const float b = fmaxf(__uint_as_float(rr[h][c0 + 1]) + bv[2 * e + 1], 0.f);
                   __nv_bfloat162 hh = __floats2bfloat162_rn(a, b);
                   pk[e] = *reinterpret_cast<uint32_t*>(&hh);
                 }
@@ -833,111 +934,96 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
               for (int q = 0; q < NCH; ++q) *ring_at(oy, col, q) = make_uint4(0, 0, 0, 0);
             }
           }
+          // the d3 rows are read by the tensor cores next: generic-proxy writes made visible
+          // to the async proxy before the warp's arrival
+          fence_proxy_async();
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(acce0 + 8 * buf);  // the warp's TMEM reads are complete
+          if (lane == 0) mbar_arrive(acce0 + 8 * buf);  // TMEM read out, d3 rows written
           ++tseq;
-        } else {
-          // zero rows 2 Hu and 2 Hu + 1 below the output
-#pragma unroll
-          for (int px = 0; px < 2; ++px)
-#pragma unroll
-            for (int q = 0; q < NCH; ++q) *ring_at(2 * i + grp, 2 * m + px, q) = make_uint4(0, 0, 0, 0);
         }
-        named_sync_epi();  // the tile's two d3 rows are in the ring
-        if (i >= st.i0) {
-          // final conv + residual for output rows 2i - 1 and 2i, columns 2 j0 + col with col
-          // in [1, 254]: thread (cl, q) takes the four adjacent columns cA = 1 + 4 cl .. cA + 3
-          // for channels 8q .. 8q + 7.  Each d3 row y = 2i - 2 + r is read at columns
-          // cA - 1 .. cA + 4 once and feeds all four columns and both output rows (row 2i - 1
-          // with ky = r, row 2i with ky = r - 1): eight independent accumulators.  The four
-          // channel quarters of a pixel are added with xor shuffles; lane q stores column
-          // cA + q.
-          const float b = bf_s[0];
-          const int cA = 1 + 4 * fcl;  // the last group (253 .. 256) stores 253, 254 only
-          float2 acc[4][2];  // [column e][row]
-#pragma unroll
-          for (int e = 0; e < 4; ++e) acc[e][0] = acc[e][1] = make_float2(0.f, 0.f);
-          if (fq < NCH) {
-            // weights of kernel rows ky = r (output row 2i - 1) and ky = r - 1 (row 2i) for this
-            // lane's 8 channels, read from shared memory per d3 row (broadcast)
-            float2 wa[3][4], wb[3][4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-#pragma unroll
-              for (int kx = 0; kx < 3; ++kx) {
-                if (r >= 1) {
-#pragma unroll
-                  for (int j = 0; j < 4; ++j) wb[kx][j] = wa[kx][j];  // row r - 1 of the previous step
-                }
-                if (r <= 2) {
-                  const float4 lo = *reinterpret_cast<const float4*>(wf_s + (r * 3 + kx) * NT + fq * 8);
-                  const float4 hi = *reinterpret_cast<const float4*>(wf_s + (r * 3 + kx) * NT + fq * 8 + 4);
-                  wa[kx][0] = make_float2(lo.x, lo.y);
-                  wa[kx][1] = make_float2(lo.z, lo.w);
-                  wa[kx][2] = make_float2(hi.x, hi.y);
-                  wa[kx][3] = make_float2(hi.z, hi.w);
-                }
-              }
-              uint4 v[6];
-              // columns past 255 (last group only) feed just the unstored outputs 255, 256.
-              // Odd column groups load in an order rotated by one, so that the 8 lanes of a
-              // quarter warp (two groups x four channel quarters) read pixels of both parities
-              // (8 distinct 16-byte bank groups), then rotate back in registers.
-              const bool rot = fcl & 1;
-#pragma unroll
-              for (int cc = 0; cc < 6; ++cc) {
-                const int c2 = rot ? (cc + 1 < 6 ? cc + 1 : 0) : cc;
-                v[cc] = *ring_at(2 * i - 2 + r, min(cA - 1 + c2, 255), fq);
-              }
-              if (rot) {
-                const uint4 last = v[5];
-#pragma unroll
-                for (int cc = 5; cc > 0; --cc) v[cc] = v[cc - 1];
-                v[0] = last;
-              }
-#pragma unroll
-              for (int cc = 0; cc < 6; ++cc) {
-                const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&v[cc]);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                  const float2 f = __bfloat1622float2(hv[j]);
-#pragma unroll
-                  for (int e = 0; e < 4; ++e) {
-                    const int kx = cc - e;  // column cA + e reads column cA - 1 + cc at tap kx
-                    if (kx < 0 || kx > 2) continue;
-                    if (r <= 2) acc[e][0] = __ffma2_rn(f, wa[kx][j], acc[e][0]);
-                    if (r >= 1) acc[e][1] = __ffma2_rn(f, wb[kx][j], acc[e][1]);
-                  }
-                }
-              }
-            }
+        if (k > 0) {
+          // final conv of the previous tile (image row ip, d3 rows 2 ip and 2 ip + 1)
+          const int ip = i - 1;
+          const uint32_t fb = fseq & 1;
+          const bool got = lane != 0 || mbar_wait(finf0 + 8 * fb, (fseq >> 1) & 1, p.spin);
+          if (epi_any(!got)) {
+            if (tid == 0) atomicCAS(p.err, 0, 4);
+            ok = false;
+            break;
           }
-          float mine[2] = {0.f, 0.f};
+          tc_fence_after();
+          uint32_t q0[32], q1[32];
+          const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + FCOL + fb * 128 + 32 * grp;
+          tmem_ld16_nowait(taddr, q0);
+          tmem_ld2_nowait(taddr + 16, q0[16], q0[17]);
+          tmem_ld16_nowait(taddr + 64, q1);
+          tmem_ld2_nowait(taddr + 64 + 16, q1[16], q1[17]);
+          tmem_wait_ld();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(fine0 + 8 * fb);  // partial-sum buffer read out
+          float P[2][9];
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
+          for (int t = 0; t < 9; ++t) {
+            P[0][t] = __uint_as_float(q0[t]) + __uint_as_float(q0[t + 9]);
+            P[1][t] = __uint_as_float(q1[t]) + __uint_as_float(q1[t + 9]);
+          }
+          // kx = 0 taps come from column x - 1, kx = 2 taps from x + 1: lanes 0 and 31 take
+          // them from the neighbouring warps through shared memory
+          float* eb = edge_s + (fseq & 1) * 128;
+          if (lane == 31) {
 #pragma unroll
-            for (int rw = 0; rw < 2; ++rw) {
-              float sm = acc[e][rw].x + acc[e][rw].y;
-              sm += __shfl_xor_sync(0xffffffffu, sm, 1);
-              sm += __shfl_xor_sync(0xffffffffu, sm, 2);
-              if (e == fq) mine[rw] = sm;
+            for (int rho = 0; rho < 2; ++rho)
+#pragma unroll
+              for (int ky = 0; ky < 3; ++ky) eb[(warp * 2 + 0) * 8 + 3 * rho + ky] = P[rho][3 * ky];
+          }
+          if (lane == 0) {
+#pragma unroll
+            for (int rho = 0; rho < 2; ++rho)
+#pragma unroll
+              for (int ky = 0; ky < 3; ++ky) eb[(warp * 2 + 1) * 8 + 3 * rho + ky] = P[rho][3 * ky + 2];
+          }
+          named_sync_epi();
+          float S[2][3];
+#pragma unroll
+          for (int rho = 0; rho < 2; ++rho)
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+              float l = __shfl_up_sync(0xffffffffu, P[rho][3 * ky], 1);
+              float r = __shfl_down_sync(0xffffffffu, P[rho][3 * ky + 2], 1);
+              if (lane == 0) l = warp > 0 ? eb[((warp - 1) * 2 + 0) * 8 + 3 * rho + ky] : 0.f;
+              if (lane == 31) r = warp < 7 ? eb[((warp + 1) * 2 + 1) * 8 + 3 * rho + ky] : 0.f;
+              S[rho][ky] = l + P[rho][3 * ky + 1] + r;
             }
-          const int X = 2 * j0 + col_own;
-          if (col_own <= 254 && X >= 0 && X < Wo) {
-#pragma unroll
-            for (int rw = 0; rw < 2; ++rw) {
-              const int oy = 2 * i - 1 + rw;
-              if (oy < 0 || oy >= Ho) continue;
-              const float fx = fxy[rw][0], fy = fxy[rw][1];
-              const float top = (1.f - fx) * (float)cv[rw][0] + fx * (float)cv[rw][1];
-              const float bot = (1.f - fx) * (float)cv[rw][2] + fx * (float)cv[rw][3];
-              const float U = 4.f * ((1.f - fy) * top + fy * bot);
-              F->Y[(size_t)oy * Wo + X] = U + (b + mine[rw]);
-            }
+          // d3 row r adds S_0 to output row r + 1, S_1 to row r, S_2 to row r - 1
+          const float outA = c1 + S[0][2];            // row 2 ip - 1: complete
+          const float outB = c2 + S[0][1] + S[1][2];  // row 2 ip: complete
+          c1 = S[0][0] + S[1][1];                     // row 2 ip + 1
+          c2 = S[1][0];                               // row 2 ip + 2
+          ++fseq;
+          if (ip >= st.i0 && col_out) {
+            const float b = bf_s[0];
+            const int yA = 2 * ip - 1, yB = 2 * ip;
+            if (yA >= 0 && yA < Ho) Yout[(size_t)yA * Wo + X] = residual(cv[0], fxy[0][0], fxy[0][1]) + (b + outA);
+            if (yB < Ho) Yout[(size_t)yB * Wo + X] = residual(cv[1], fxy[1][0], fxy[1][1]) + (b + outB);
           }
         }
-        named_sync_epi();  // the ring rows read above may now be overwritten
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) cv[r][e] = cvn[r][e];
+          fxy[r][0] = fxyn[r][0];
+          fxy[r][1] = fxyn[r][1];
+        }
+      }
+      if (ok && below && col_out) {
+        // last output row 2 Hu - 1: its rows below (2 Hu, 2 Hu + 1) are zero
+        int16_t cc[4];
+        float fx, fy;
+        const int yC = 2 * Hu - 1;
+        coarse4(cmap, w4, h4, X, yC, cc, fx, fy);
+        Yout[(size_t)yC * Wo + X] = residual(cc, fx, fy) + (bf_s[0] + c1);
       }
     }
   }
@@ -987,34 +1073,19 @@ __global__ void pack_kernel(const float* __restrict__ W, int mode, int NT, int G
 }
 
 
-// Packed B of the fused dec3 kernel: 20 blocks of [NT output channels x cin] in the same
-// core-matrix layout.  Blocks 4 ph + t: phase ph = (py, px), tap t = (ro, co) of the 4-phase
-// form (3x3 weights summed per phase as in pack_kernel).  Blocks 16 + 2 px + co: phase
-// (0, px), tap row ro = 1 with only the kernel row ky = 1 (the row ky = 2 falls on the
-// cropped-away half of the up-sampled map when the output height is odd).
+// Packed B of the fused dec3 kernel: 16 blocks of [NT output channels x cin] in the same
+// core-matrix layout.  Block 4 ph + t: phase ph = (py, px), tap t = (ro, co) of the 4-phase
+// form (3x3 weights summed per phase as in pack_kernel).
 __global__ void pack_fused_kernel(const float* __restrict__ W, int NT, int cin, bf16* __restrict__ out) {
-  const size_t total = (size_t)20 * NT * cin;
+  const size_t total = (size_t)16 * NT * cin;
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   const int k = (int)(idx % cin);
   const int n = (int)((idx / cin) % NT);
   const int blk = (int)(idx / ((size_t)cin * NT));
-  int py, px, a, b;
-  bool crop = false;
-  if (blk < 16) {
-    py = (blk / 4) >> 1;
-    px = (blk / 4) & 1;
-    a = (blk % 4) >> 1;
-    b = (blk % 4) & 1;
-  } else {
-    py = 0;
-    px = (blk - 16) >> 1;
-    a = 1;
-    b = (blk - 16) & 1;
-    crop = true;
-  }
+  const int py = (blk / 4) >> 1, px = (blk / 4) & 1, a = (blk % 4) >> 1, b = (blk % 4) & 1;
   const int ky0 = py == 0 ? (a == 0 ? 0 : 1) : (a == 0 ? 0 : 2);
-  const int ky1 = crop ? 1 : py == 0 ? (a == 0 ? 0 : 2) : (a == 0 ? 1 : 2);
+  const int ky1 = py == 0 ? (a == 0 ? 0 : 2) : (a == 0 ? 1 : 2);
   const int kx0 = px == 0 ? (b == 0 ? 0 : 1) : (b == 0 ? 0 : 2);
   const int kx1 = px == 0 ? (b == 0 ? 0 : 2) : (b == 0 ? 1 : 2);
   float v = 0.f;
@@ -1022,6 +1093,23 @@ __global__ void pack_fused_kernel(const float* __restrict__ W, int NT, int cin, 
     for (int kx = kx0; kx <= kx1; ++kx) v += W[((size_t)n * 9 + ky * 3 + kx) * cin + k];
   const size_t dst = (size_t)blk * NT * cin + (size_t)(n % 8) * 8 + (size_t)(n / 8) * cin * 8 + (k % 8) + (size_t)(k / 8) * 64;
   out[dst] = __float2bfloat16_rn(v);
+}
+
+// Packed B of the fused kernel's final conv: [32 rows x NT channels] in the same core-matrix
+// layout.  Rows 0-8: the BF16 high parts hi = bf16(w) of the nine taps (row 3 ky + kx), rows
+// 9-17: the low parts bf16(w - hi), rows 18-31: zero.  hi + lo equals the FP32 weight to
+// about 2^-16 relative, so the tensor-core final conv keeps FP32-weight accuracy.
+__global__ void pack_final_kernel(const float* __restrict__ wf, int NT, bf16* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kFinalN * NT) return;
+  const int k = idx % NT, n = idx / NT;
+  float v = 0.f;
+  if (n < 18) {
+    const float w = wf[(n % 9) * NT + k];
+    const float hi = __bfloat162float(__float2bfloat16_rn(w));
+    v = n < 9 ? hi : w - hi;
+  }
+  out[(size_t)(n % 8) * 8 + (size_t)(n / 8) * NT * 8 + (k % 8) + (size_t)(k / 8) * 64] = __float2bfloat16_rn(v);
 }
 
 template <int NT, int RB>
@@ -1272,12 +1360,18 @@ sv_status Ctx::pack_bf16_weights(cudaStream_t st) {
     if ((s = cuda(cudaGetLastError(), "unfolded weights"))) return s;
   }
   if (tc::fused_supported(net.dec[2], net.dec[1])) {
-    const size_t n = (size_t)20 * net.dec[2] * net.dec[1];
-    if ((s = cuda(wfuse.ensure(n * sizeof(__nv_bfloat16)), "alloc fused weights"))) return s;
+    const size_t n = (size_t)16 * net.dec[2] * net.dec[1];
+    if ((s = cuda(wfuse.ensure(tc::fused_wpack_elems(net.dec[2], net.dec[1]) * sizeof(__nv_bfloat16)),
+                  "alloc fused weights")))
+      return s;
     LaunchScope ls(*this, "pack_bf16", st);
     tc::pack_fused_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const float*)w32.p + net.w_off(L_DEC3), net.dec[2],
                                                                   net.dec[1], (__nv_bfloat16*)wfuse.p);
     if ((s = cuda(cudaGetLastError(), "fused weights"))) return s;
+    const int nf = tc::kFinalN * net.dec[2];
+    tc::pack_final_kernel<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>((const float*)w32.p + net.w_off(L_FINAL),
+                                                                    net.dec[2], (__nv_bfloat16*)wfuse.p + n);
+    if ((s = cuda(cudaGetLastError(), "fused final weights"))) return s;
   }
   for (auto& pl : plans) {
     const size_t n = (size_t)pl.G * tc::taps(pl.mode) * pl.NT * pl.cin;
@@ -1446,6 +1540,7 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
     const int NT = net.dec[2], cin = net.dec[1];
     int ring = 4;  // 3 rows per tile + 1 ahead; more where shared memory allows
     while (ring < 3 + kPrefetchSteps && tc::fused_smem_bytes(NT, cin, ring + 1) <= kSmemLimit) ++ring;
+    if (fused_ring > 0) ring = std::min(ring, fused_ring);
     std::vector<tc::FusedPair> fps(n);
     long long units = 0;
     for (int i = 0; i < n; ++i) {
@@ -1536,9 +1631,9 @@ sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream
       fp.n_strips = r.fused_n_strips;
       fp.wpack = (const __nv_bfloat16*)wfuse.p;
       fp.bias = prm.bias;
-      fp.wf = W + net.w_off(L_FINAL);
       fp.bf = W + net.b_off(L_FINAL);
       fp.ring = r.fused_ring;
+      fp.pf = fused_prefetch;
       fp.err = (int*)err_flag.p;
       fp.spin = spin_limit;
       LaunchScope ls(*this, "tc_dec3_final", st);

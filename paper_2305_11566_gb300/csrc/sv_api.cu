@@ -584,6 +584,18 @@ sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value) {
     c->drop_graphs();
     return SV_OK;
   }
+  if (!strcmp(key, "fused_prefetch")) {
+    if (value < 0 || value > 16) return c->fail(SV_ERR_INVALID_ARG, "fused_prefetch must be 0..16");
+    c->fused_prefetch = (int)value;
+    c->drop_graphs();
+    return SV_OK;
+  }
+  if (!strcmp(key, "fused_ring")) {
+    if (value != 0 && (value < 4 || value > 16)) return c->fail(SV_ERR_INVALID_ARG, "fused_ring must be 0 or 4..16");
+    c->fused_ring = (int)value;
+    c->drop_graphs();
+    return SV_OK;
+  }
   if (!strcmp(key, "debug_plans")) {
     if (value != 0 && value != 1) return c->fail(SV_ERR_INVALID_ARG, "debug_plans must be 0 or 1");
     c->debug_plans = (int)value;
