@@ -156,10 +156,11 @@ def test_device_wait_timeout_is_reported_and_recoverable(contexts):
     ("256x128 small net, 5-row strips", synth.NET_SMALL, 256, 128, 60.0, 7, 16, 5),
 ])
 def test_bf16_fused_final(contexts, name, shape, W, H, dmax, k, D, rows):
-    """The fused last-decoder-layer + final-conv kernel (d3 kept in shared memory; odd output
-    height handled by the last-row weights, even height by the zero tile below; column
-    strips overlapping by one input pixel; halo tiles above row strips) against the
-    unfused kernels of the same context and against the FP64 oracle."""
+    """The fused last-decoder-layer + final-conv kernel (d3 kept in shared memory, final conv
+    on the tensor cores; odd output height handled by negated-weight MMAs on the last row,
+    even height by the carried sums below; column strips overlapping by one input pixel;
+    halo tiles above row strips) against the unfused kernels of the same context and
+    against the FP64 oracle."""
     p = synth.make_pair(W, H, dmax, 8100 + W + rows)
     disp_o = oracle.coarse_match(p.left, p.right, k, D)[0]
     params = synth.he_normal_weights(shape, 7)
