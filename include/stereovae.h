@@ -241,6 +241,9 @@ SV_API sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream);
  *                    width is even; 0: separate kernels (d3 materialised in HBM)
  *   "fused_ring"     0 (default): the fused kernel stages as many input rows ahead as
  *                    shared memory holds; 4..16: at most this many rows in its ring
+ *   "enc1_tensor"    1 (default): the first encoder layer of an SV_BF16 context runs on the
+ *                    tensor cores (im2col tile in shared memory; widths 16, 32, 64); 0: CUDA
+ *                    cores (FP32 FMA)
  *   "fused_prefetch" 0..16 (default 4): the fused kernel's producer prefetches the input row
  *                    this many rows ahead into L2 (0: no prefetch)
  *   "host_copy"      sv_pipeline_host with device-accessible (pinned) host buffers: 0 one

@@ -1663,7 +1663,7 @@ sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream
   {
     LaunchScope ls(*this, "edge_enc1", st);
     if ((s = cuda(launch_edge_enc1(d_edges, r.n, r.maxW1, r.maxH1, W + net.w_off(L_ENC1), W + net.b_off(L_ENC1),
-                                   net.enc[0], st),
+                                   net.enc[0], (int*)err_flag.p, spin_limit, enc1_tensor != 0, st),
                   "enc1")))
       return s;
   }

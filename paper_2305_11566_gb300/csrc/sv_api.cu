@@ -547,8 +547,9 @@ sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream) {
     return s;
   if (code) {
     cudaMemset(c->err_flag.p, 0, sizeof(int));
-    static const char* where[] = {"", "producer", "MMA issuer", "MMA drain", "epilogue", "copy drain", "final-conv staging"};
-    return c->fail(SV_ERR_TIMEOUT, "a device-side wait ran out (%s, code %d)", code >= 1 && code <= 6 ? where[code] : "?",
+    static const char* where[] = {"",           "producer",           "MMA issuer", "MMA drain",
+                                  "epilogue",   "copy drain",         "final-conv staging", "enc1 MMA"};
+    return c->fail(SV_ERR_TIMEOUT, "a device-side wait ran out (%s, code %d)", code >= 1 && code <= 7 ? where[code] : "?",
                    code);
   }
   return SV_OK;
@@ -581,6 +582,12 @@ sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value) {
   if (!strcmp(key, "fused_final")) {
     if (value != 0 && value != 1) return c->fail(SV_ERR_INVALID_ARG, "fused_final must be 0 or 1");
     c->fused_final = (int)value;
+    c->drop_graphs();
+    return SV_OK;
+  }
+  if (!strcmp(key, "enc1_tensor")) {
+    if (value != 0 && value != 1) return c->fail(SV_ERR_INVALID_ARG, "enc1_tensor must be 0 or 1");
+    c->enc1_tensor = (int)value;
     c->drop_graphs();
     return SV_OK;
   }

@@ -108,6 +108,7 @@ struct Ctx {
   int fused_final = 1;                  // 1: last decoder layer + final conv in one kernel when possible
   int fused_ring = 0;                   // fused kernel's staged-row ring: 0 as deep as shared memory allows
   int fused_prefetch = 4;               // fused kernel: rows prefetched into L2 ahead of the loaded row
+  int enc1_tensor = 1;                  // 1: enc1 on the tensor cores where its width allows
   int host_copy = 1;                    // sv_pipeline_host: 0 copy calls, 1 gather kernel in, 2 kernels both ways
   bool last_fused = false;              // the last tensor-core call did not materialise d3
   int tc_ctas_per_sm = 0;               // 0: deepest row ring (one CTA per SM); k: ring sized for k

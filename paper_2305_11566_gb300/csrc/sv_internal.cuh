@@ -177,8 +177,10 @@ struct UpFixPair {          // one decoder layer of one pair (input, output, siz
   __nv_bfloat16* out;
   int Hi, Wi, Ho, Wo, Hu, Wu;
 };
+// enc1 for every pair of a call; `tensor`: the tensor-core kernel where C1 allows (16, 32,
+// 64), whose bounded wait records code 7 in `err`.
 cudaError_t launch_edge_enc1(const EdgePair* pairs, int n, int maxW1, int maxH1, const float* W, const float* B, int C1,
-                             cudaStream_t st);
+                             int* err, long long spin, bool tensor, cudaStream_t st);
 cudaError_t launch_edge_final(const EdgePair* pairs, int n, int maxW, int maxH, const float* W, const float* B, int C,
                               int* err, long long spin, cudaStream_t st);
 // Border pixels of a cropped nearest-x2 + 3x3 conv output that the 4-phase form folds

@@ -2,9 +2,11 @@
 // form, each one launch for all pairs of a call (blockIdx.z = pair):
 //
 //   edge_enc1    first conv (3x3 stride 2, 2 -> C1, ReLU) with its input built while
-//                staging: x0 = (L / 256, U / 256), U = 4 * bilinear(coarse) (a5, a6, a7).
-//                FP32 arithmetic, BF16 NHWC output; 4 output rows per thread.
-//   edge_final   last conv (3x3, C -> 1) + bias + U (residual), BF16 input, FP32 output (a11);
+//                staging: x0 = (L / 256, U / 256), U = 4 * bilinear(coarse).  FP32
+//                arithmetic, BF16 NHWC output; 4 output rows per thread.
+//   enc1_tc      the same layer with the 2 -> C1 products on the tensor cores (C1 = 16, 32,
+//                64): the staged input becomes an im2col A tile in shared memory.
+//   edge_final   last conv (3x3, C -> 1) + bias + U (residual), BF16 input, FP32 output;
 //                register-blocked packed-FP32 form for C = 16, 32, 64, 128.
 //   edge_up2fix  exact recomputation of the last row / column of an odd-sized (cropped)
 //                nearest-x2 + 3x3 conv output, which the 4-phase tensor-core form folds
@@ -26,6 +28,23 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_e(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait_e(uint32_t bar, uint32_t parity, long long spin) {
+  if (mbar_try_e(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_e(bar, parity))
+    if (clock64() - t0 > spin) return false;
+  return true;
 }
 
 constexpr int ETW = 32, ETH = 8;  // output tile of the edge kernels (256 threads)
@@ -181,6 +200,186 @@ __global__ void __launch_bounds__(256) edge_enc1(const EdgePair* __restrict__ pa
   }
 }
 
+// ------------------------------------------------------------------ enc1 on the tensor cores
+// The block's 32 x 32 output pixels are eight M = 128 tiles (tile t: output rows 4t .. 4t + 3,
+// pixel m = 32 j + column of row 4t + j).  A pixel's A row holds its 27 inputs, the 9 taps x
+// (L / 256, and U / 256 split into BF16 high and low parts), then 5 zeros: K = 32, in the
+// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix; K neighbours 128 B
+// apart, 8-row groups 512 B apart).  B holds the C1 x 32 weights (the same U weight for both
+// U parts) split into BF16 high and low parts, two MMA passes into the same accumulator, so
+// that the result keeps FP32 accuracy to about 2^-16 (L / 256 is exact in BF16).  One TMEM
+// accumulator of C1 columns per tile; the epilogue adds the bias, applies ReLU and stores
+// BF16 NHWC.
+__device__ __forceinline__ uint32_t smem_u32_e(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mma_bf16_e(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// descriptor of a no-swizzle K-major operand: start, LBO = 128 B (next 8 K), SBO (next 8 rows)
+__device__ __forceinline__ uint64_t desc_ns_e(uint32_t addr, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
+         (1ull << 46);
+}
+__device__ __forceinline__ void tmem_ld32_e(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%"
+      "20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16_e(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+constexpr uint32_t kE1Tile = 128 * 32 * 2;  // one A tile (128 pixels x K = 32, BF16)
+__host__ __device__ constexpr size_t enc1_tc_smem(int C1) {
+  return 128 + 8 * (size_t)kE1Tile + 2 * (size_t)C1 * 64 + (size_t)C1 * 4 + 16;
+}
+
+template <int C1>
+__global__ void __launch_bounds__(256) enc1_tc(const EdgePair* __restrict__ pairs, const float* __restrict__ W,
+                                               const float* __restrict__ B, int* err, long long spin) {
+  static_assert(C1 == 16 || C1 == 32 || C1 == 64, "enc1 widths");
+  __shared__ float xs[E1R][E1C][2];
+  __shared__ float T[E1CR][E1C];
+  extern __shared__ unsigned char e1dyn[];
+  const EdgePair* P = pairs + blockIdx.z;
+  const int H1 = (P->H + 1) / 2, W1 = (P->W + 1) / 2;
+  const int X0 = blockIdx.x * E1W, Y0 = blockIdx.y * E1H;
+  if (X0 >= W1 || Y0 >= H1) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t raw = smem_u32_e(e1dyn), base = (raw + 127u) & ~127u;
+  unsigned char* g = e1dyn + (base - raw);
+  const uint32_t sA = base, sBh = base + 8 * kE1Tile, sBl = sBh + C1 * 64;
+  float* bias_s = reinterpret_cast<float*>(g + 8 * kE1Tile + 2 * C1 * 64);
+  const uint32_t mbar = smem_u32_e(bias_s + C1);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bias_s + C1 + 2);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32_e(tslot)),
+                 "r"(8 * C1));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // B (high, low): element (n, k), k = 3 tap + part (0: L, 1 and 2: the two U parts)
+  for (int e = tid; e < C1 * 32; e += 256) {
+    const int n = e >> 5, k = e & 31;
+    float w = 0.f;
+    if (k < 27) w = W[(size_t)n * 18 + (k / 3) * 2 + (k % 3 == 0 ? 0 : 1)];
+    const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+    const uint32_t off = (uint32_t)((n & 7) * 8 + (n >> 3) * 256 + (k & 7) + (k >> 3) * 64) * 2;
+    *reinterpret_cast<__nv_bfloat16*>(g + 8 * kE1Tile + off) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(g + 8 * kE1Tile + C1 * 64 + off) = __float2bfloat16_rn(w - __bfloat162float(hi));
+  }
+  for (int e = tid; e < C1; e += 256) bias_s[e] = B[e];
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (P->coarse_f) enc1_stage(P, P->coarse_f, X0, Y0, xs, T);
+  else enc1_stage(P, P->coarse, X0, Y0, xs, T);
+  __syncthreads();
+  // A rows: warp w builds tile w; lane = output column, j = row within the tile
+#pragma unroll 1
+  for (int j = 0; j < 4; ++j) {
+    const int oy = 4 * warp + j;
+    float v[32];
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const float2 t = *reinterpret_cast<const float2*>(&xs[2 * oy + ky][2 * lane + kx][0]);
+        const float uh = __bfloat162float(__float2bfloat16_rn(t.y));
+        const int k = 3 * (ky * 3 + kx);
+        v[k] = t.x;
+        v[k + 1] = uh;
+        v[k + 2] = t.y - uh;
+      }
+#pragma unroll
+    for (int k = 27; k < 32; ++k) v[k] = 0.f;
+    const int m = 32 * j + lane;
+    unsigned char* row = g + (size_t)warp * kE1Tile + (m & 7) * 16 + (m >> 3) * 512;
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc)
+      *reinterpret_cast<uint4*>(row + kc * 128) =
+          make_uint4(pack_bf16x2(v[8 * kc], v[8 * kc + 1]), pack_bf16x2(v[8 * kc + 2], v[8 * kc + 3]),
+                     pack_bf16x2(v[8 * kc + 4], v[8 * kc + 5]), pack_bf16x2(v[8 * kc + 6], v[8 * kc + 7]));
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C1 >> 3) << 17) | ((128u >> 4) << 24);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const uint64_t a = desc_ns_e(sA + t * kE1Tile, 512);
+      const uint32_t d = tmem + t * C1;
+      // K step of 16 = two core matrices along K = +256 B (+16 in the start field)
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) mma_bf16_e(d, a + 16 * ks, desc_ns_e(sBh, 256 * 2) + 16 * ks, idesc, ks);
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) mma_bf16_e(d, a + 16 * ks, desc_ns_e(sBl, 256 * 2) + 16 * ks, idesc, 1u);
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+  }
+  __syncwarp();
+  // lane 0 of each warp waits for the accumulators and tells the warp
+  bool got = lane != 0 || mbar_wait_e(mbar, 0, spin);
+  got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+  if (!got) {
+    if (lane == 0) atomicCAS(err, 0, 7);
+    // the MMAs may still be running: wait (bounded) before the allocation is released
+    if (lane == 0) mbar_wait_e(mbar, 0, spin > 2000000000LL ? spin : 2000000000LL);
+    __syncwarp();
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (got) {
+    const int q = warp & 3;
+#pragma unroll 1
+    for (int t = warp >> 2; t < 8; t += 2) {
+      const int Y = Y0 + 4 * t + q, X = X0 + lane;
+      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t * C1);
+#pragma unroll
+      for (int c0 = 0; c0 < C1; c0 += 32) {
+        uint32_t r[32];
+        if (C1 >= 32) tmem_ld32_e(taddr + c0, r);
+        else tmem_ld16_e(taddr + c0, r);
+        constexpr int CW = C1 >= 32 ? 32 : C1;
+        if (X < W1 && Y < H1) {
+          uint32_t pk[CW / 2];
+#pragma unroll
+          for (int e = 0; e < CW; e += 2) {
+            const float2 v = __fadd2_rn(make_float2(__uint_as_float(r[e]), __uint_as_float(r[e + 1])),
+                                        make_float2(bias_s[c0 + e], bias_s[c0 + e + 1]));
+            const __nv_bfloat162 h = __hmax2(__floats2bfloat162_rn(v.x, v.y), __float2bfloat162_rn(0.f));
+            pk[e / 2] = *reinterpret_cast<const uint32_t*>(&h);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(P->e1 + ((size_t)Y * W1 + X) * C1 + c0);
+#pragma unroll
+          for (int i = 0; i < CW / 8; ++i) dst[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(8 * C1));
+}
+
 // final: (ETH + 2) x (ETW + 2) x C BF16 tile in shared memory with an 80-byte-per-32-channel
 // pixel stride (conflict-free 16-byte reads), weights [9][C] FP32.
 template <int C>
@@ -244,23 +443,6 @@ struct FinalGeo {
   static constexpr uint32_t tile_bytes = (uint32_t)SR * SC * C * 2;
   static constexpr size_t smem = tile_bytes + 128 + 9 * C * 4;  // tile (+ alignment slack), FP32 weights
 };
-
-__device__ __forceinline__ bool mbar_try_e(uint32_t bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-__device__ __forceinline__ bool mbar_wait_e(uint32_t bar, uint32_t parity, long long spin) {
-  if (mbar_try_e(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_e(bar, parity))
-    if (clock64() - t0 > spin) return false;
-  return true;
-}
 
 template <int C>
 __global__ void __launch_bounds__(FinalGeo<C>::NTH) edge_final_rb(const EdgePair* __restrict__ pairs,
@@ -538,9 +720,22 @@ cudaError_t launch_bf16_to_f32(const bf16* a, float* b, size_t n, cudaStream_t s
   return cudaGetLastError();
 }
 
+template <int C1>
+static cudaError_t run_enc1_tc(const EdgePair* pairs, dim3 grid, const float* W, const float* B, int* err, long long spin,
+                               cudaStream_t st) {
+  const size_t smem = enc1_tc_smem(C1);
+  cudaError_t e = cudaFuncSetAttribute(enc1_tc<C1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  enc1_tc<C1><<<grid, 256, smem, st>>>(pairs, W, B, err, spin);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_edge_enc1(const EdgePair* pairs, int n, int maxW1, int maxH1, const float* W, const float* B, int C1,
-                             cudaStream_t st) {
+                             int* err, long long spin, bool tensor, cudaStream_t st) {
   dim3 grid((maxW1 + E1W - 1) / E1W, (maxH1 + E1H - 1) / E1H, n);
+  if (tensor && C1 == 32) return run_enc1_tc<32>(pairs, grid, W, B, err, spin, st);
+  if (tensor && C1 == 16) return run_enc1_tc<16>(pairs, grid, W, B, err, spin, st);
+  if (tensor && C1 == 64) return run_enc1_tc<64>(pairs, grid, W, B, err, spin, st);
   edge_enc1<<<grid, 256, sizeof(float) * 19 * C1, st>>>(pairs, W, B, C1);
   return cudaGetLastError();
 }
