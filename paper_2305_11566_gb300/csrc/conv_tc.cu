@@ -1032,44 +1032,43 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(fine0 + 8 * fb);  // partial-sum buffer read out
-          float P[2][9];
+          // d3 row r adds S_0 to output row r + 1, S_1 to row r, S_2 to row r - 1, with
+          // S_ky(x) = P_r(x - 1, ky, 0) + P_r(x, ky, 1) + P_r(x + 1, ky, 2).  The four sums
+          // this tile contributes to (rows 2 ip - 1 .. 2 ip + 2, from d3 rows 2 ip and 2 ip + 1)
+          // are formed per kx first, so that only 4 values cross to each neighbour.
+          const auto p0 = [&](int t) { return __uint_as_float(q0[t]); };
+          const auto p1 = [&](int t) { return __uint_as_float(q1[t]); };
+          float part[3][4];  // [kx][row 2 ip - 1 + i]
 #pragma unroll
-          for (int t = 0; t < 9; ++t) {
-            P[0][t] = __uint_as_float(q0[t]);
-            P[1][t] = __uint_as_float(q1[t]);
+          for (int kx = 0; kx < 3; ++kx) {
+            part[kx][0] = p0(6 + kx);
+            part[kx][1] = p0(3 + kx) + p1(6 + kx);
+            part[kx][2] = p0(kx) + p1(3 + kx);
+            part[kx][3] = p1(kx);
           }
-          // kx = 0 taps come from column x - 1, kx = 2 taps from x + 1: lanes 0 and 31 take
-          // them from the neighbouring warps through shared memory
+          // kx = 0 parts go to the right neighbour, kx = 2 parts to the left one; lanes 0
+          // and 31 exchange with the neighbouring warps through shared memory
           float* eb = edge_s + (fseq & 1) * 128;
-          if (lane == 31) {
-#pragma unroll
-            for (int rho = 0; rho < 2; ++rho)
-#pragma unroll
-              for (int ky = 0; ky < 3; ++ky) eb[(warp * 2 + 0) * 8 + 3 * rho + ky] = P[rho][3 * ky];
-          }
-          if (lane == 0) {
-#pragma unroll
-            for (int rho = 0; rho < 2; ++rho)
-#pragma unroll
-              for (int ky = 0; ky < 3; ++ky) eb[(warp * 2 + 1) * 8 + 3 * rho + ky] = P[rho][3 * ky + 2];
-          }
+          if (lane == 31) *reinterpret_cast<float4*>(eb + (warp * 2 + 0) * 8) = make_float4(part[0][0], part[0][1], part[0][2], part[0][3]);
+          if (lane == 0) *reinterpret_cast<float4*>(eb + (warp * 2 + 1) * 8) = make_float4(part[2][0], part[2][1], part[2][2], part[2][3]);
           named_sync_epi();
-          float S[2][3];
+          float4 le = make_float4(0.f, 0.f, 0.f, 0.f), re = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (lane == 0 && warp > 0) le = *reinterpret_cast<const float4*>(eb + ((warp - 1) * 2 + 0) * 8);
+          if (lane == 31 && warp < 7) re = *reinterpret_cast<const float4*>(eb + ((warp + 1) * 2 + 1) * 8);
+          const float lev[4] = {le.x, le.y, le.z, le.w}, rev[4] = {re.x, re.y, re.z, re.w};
+          float Tsum[4];
 #pragma unroll
-          for (int rho = 0; rho < 2; ++rho)
-#pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
-              float l = __shfl_up_sync(0xffffffffu, P[rho][3 * ky], 1);
-              float r = __shfl_down_sync(0xffffffffu, P[rho][3 * ky + 2], 1);
-              if (lane == 0) l = warp > 0 ? eb[((warp - 1) * 2 + 0) * 8 + 3 * rho + ky] : 0.f;
-              if (lane == 31) r = warp < 7 ? eb[((warp + 1) * 2 + 1) * 8 + 3 * rho + ky] : 0.f;
-              S[rho][ky] = l + P[rho][3 * ky + 1] + r;
-            }
-          // d3 row r adds S_0 to output row r + 1, S_1 to row r, S_2 to row r - 1
-          const float outA = c1 + S[0][2];            // row 2 ip - 1: complete
-          const float outB = c2 + S[0][1] + S[1][2];  // row 2 ip: complete
-          c1 = S[0][0] + S[1][1];                     // row 2 ip + 1
-          c2 = S[1][0];                               // row 2 ip + 2
+          for (int i = 0; i < 4; ++i) {
+            float l = __shfl_up_sync(0xffffffffu, part[0][i], 1);
+            float r = __shfl_down_sync(0xffffffffu, part[2][i], 1);
+            if (lane == 0) l = lev[i];
+            if (lane == 31) r = rev[i];
+            Tsum[i] = l + part[1][i] + r;
+          }
+          const float outA = c1 + Tsum[0];  // row 2 ip - 1: complete
+          const float outB = c2 + Tsum[1];  // row 2 ip: complete
+          c1 = Tsum[2];                     // row 2 ip + 1
+          c2 = Tsum[3];                     // row 2 ip + 2
           ++fseq;
           if (ip >= st.i0 && col_out) {
             const float b = bf_s[0];
