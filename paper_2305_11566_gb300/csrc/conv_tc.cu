@@ -563,11 +563,10 @@ struct FusedParams {
 };
 
 constexpr int kFusedNpx = 130;
-constexpr int kFinalN = 16;  // final conv MMA width: the nine taps and 7 zero rows (one B for the
-                             // BF16 high parts of the weights, one for the low parts)
+constexpr int kFinalN = 32;  // final conv MMA width: 9 high parts, 9 low parts, 14 zero rows
 __host__ __device__ inline uint32_t fused_kbs(int rb) { return (uint32_t)((kFusedNpx * rb + 1023) / 1024 * 1024); }
 __host__ __device__ inline size_t fused_wpack_elems(int NT, int cin) {
-  return (size_t)16 * NT * cin + (size_t)2 * kFinalN * NT;
+  return (size_t)16 * NT * cin + (size_t)kFinalN * NT;
 }
 // decoder bias [NT], final bias (+ 3 pad), tap-sum exchange [2 parities][8 warps][2 sides][8]
 __host__ __device__ inline size_t fused_param_bytes(int NT) { return (size_t)(NT + 4 + 256) * 4; }
@@ -602,24 +601,27 @@ __host__ __device__ constexpr uint32_t idesc_n(int N) {
 // The 16 (phase, tap) products of a tile read 9 distinct views of the staged rows: phase
 // (py, px) with tap (ro, co) reads staged row py + ro at pixel shift px + co.  Each view is
 // one MMA whose N stacks the phases reading it, so the accumulators of those phases must be
-// adjacent in TMEM: blocks (units of NT columns) 0: (0, 0), 1: (0, 1), 2: (1, 1), 3: (1, 0),
-// 4: a second partial sum of (0, 0), which closes the cycle (0,0)-(0,1)-(1,1)-(1,0)-(0,0).
-// A view's weights are `nb` consecutive packed blocks starting at `blk` (pack_fused_kernel
-// writes them in this order); `col` is its first accumulator block.  (The issue loops are
-// unrolled, so every call below folds to constants.)
+// adjacent in TMEM: blocks (units of NT columns) 0: (0, 0), 1: (0, 1), 2: (1, 1), 3: (1, 0).
+// The four phases form the cycle (0,0)-(0,1)-(1,1)-(1,0)-(0,0) under "share a view"; the
+// view (1, 0), shared by (1, 0) and (0, 0), closes it and is issued as two MMAs: 10 MMAs
+// per K step.  A view's weights are `nb` consecutive packed blocks starting at `blk`
+// (pack_fused_kernel writes them in this order); `col` is its first accumulator block.
+// (The issue loops are unrolled, so every call below folds to constants.)
 struct FusedView {
   int r, s, blk, nb, col;
 };
+constexpr int kFusedViewMMAs = 10;
 __host__ __device__ constexpr FusedView fused_view(int v) {
   switch (v) {
-    case 0: return {1, 1, 0, 4, 1};   // (0,1) t(1,0), (1,1) t(0,0), (1,0) t(0,1), (0,0)' t(1,1)
-    case 1: return {0, 0, 12, 1, 0};  // (0,0) t(0,0)
-    case 2: return {0, 1, 4, 2, 0};   // (0,0) t(0,1), (0,1) t(0,0)
-    case 3: return {2, 1, 6, 2, 2};   // (1,1) t(1,0), (1,0) t(1,1)
-    case 4: return {1, 2, 8, 2, 1};   // (0,1) t(1,1), (1,1) t(0,1)
-    case 5: return {1, 0, 10, 2, 3};  // (1,0) t(0,0), (0,0)' t(1,0)
-    case 6: return {0, 2, 13, 1, 1};  // (0,1) t(0,1)
-    case 7: return {2, 0, 14, 1, 3};  // (1,0) t(1,0)
+    case 0: return {1, 1, 0, 4, 0};   // (0,0) t(1,1), (0,1) t(1,0), (1,1) t(0,0), (1,0) t(0,1)
+    case 1: return {0, 1, 4, 2, 0};   // (0,0) t(0,1), (0,1) t(0,0)
+    case 2: return {2, 1, 6, 2, 2};   // (1,1) t(1,0), (1,0) t(1,1)
+    case 3: return {1, 2, 8, 2, 1};   // (0,1) t(1,1), (1,1) t(0,1)
+    case 4: return {1, 0, 10, 1, 3};  // (1,0) t(0,0)
+    case 5: return {1, 0, 11, 1, 0};  // (0,0) t(1,0)
+    case 6: return {0, 0, 12, 1, 0};  // (0,0) t(0,0)
+    case 7: return {0, 2, 13, 1, 1};  // (0,1) t(0,1)
+    case 8: return {2, 0, 14, 1, 3};  // (1,0) t(1,0)
     default: return {2, 2, 15, 1, 2};  // (1,1) t(1,1)
   }
 }
@@ -628,8 +630,8 @@ __host__ __device__ constexpr FusedView fused_view(int v) {
 // (1, px), tap (1, co), which holds kernel row 2 alone with the same column folding.
 __host__ __device__ constexpr FusedView fused_crop_view(int v) {
   switch (v) {
-    case 0: return {1, 0, 14, 1, 4};  // (0,0)' t(1,0) - row 2 of (1,0) t(1,0)
-    case 1: return {1, 1, 7, 1, 4};   // (0,0)' t(1,1) - row 2 of (1,0) t(1,1)
+    case 0: return {1, 0, 14, 1, 0};  // (0,0) t(1,0) - row 2 of (1,0) t(1,0)
+    case 1: return {1, 1, 7, 1, 0};   // (0,0) t(1,1) - row 2 of (1,0) t(1,1)
     case 2: return {1, 1, 6, 1, 1};   // (0,1) t(1,0) - row 2 of (1,1) t(1,0)
     default: return {1, 2, 15, 1, 1};  // (0,1) t(1,1) - row 2 of (1,1) t(1,1)
   }
@@ -637,7 +639,7 @@ __host__ __device__ constexpr FusedView fused_crop_view(int v) {
 // packed block -> phase 2 py + px (high digit) and tap 2 ro + co (low digit), in the
 // order of fused_view
 __host__ __device__ constexpr int fused_block_pt(int blk) {
-  constexpr int pt[16] = {12, 30, 21, 3, 1, 10, 32, 23, 13, 31, 20, 2, 0, 11, 22, 33};
+  constexpr int pt[16] = {3, 12, 30, 21, 1, 10, 32, 23, 13, 31, 20, 2, 0, 11, 22, 33};
   return pt[blk];
 }
 
@@ -650,8 +652,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
   constexpr uint32_t PXB = NT * 2;                             // bytes per d3 pixel
   constexpr uint32_t BBLK = NT * CIN * 2;                      // one (phase, tap) weight block
   constexpr int FKS = NT / 16;                                 // K steps of the final conv
-  constexpr uint32_t kCols = 512;                              // 2 x 5 x NT accumulators + 2 x 64 partials
-  constexpr uint32_t FCOL = 10 * NT;                           // first TMEM column of the final partials
+  constexpr uint32_t kCols = 512;                              // 2 x 4 x NT accumulators + 2 x 128 partials
+  constexpr uint32_t FCOL = 8 * NT;                            // first TMEM column of the final partials
   static_assert(NT == 16 || NT == 32, "fused decoder widths");
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -660,7 +662,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
   const uint32_t ring = (uint32_t)p.ring;
   const uint32_t sB = base;
   const uint32_t sF = sB + 16 * BBLK;                          // final conv B [32 x NT]
-  const uint32_t sPar = sF + 2 * kFinalN * NT * 2;
+  const uint32_t sPar = sF + kFinalN * NT * 2;
   const uint32_t sA = (sPar + (uint32_t)fused_param_bytes(NT) + 1023u) & ~1023u;
   const uint32_t sD = sA + ring * KBS;                         // d3 rows [4][256][NCH] x 16 B
   const uint32_t bars = sD + 4 * 256 * PXB;
@@ -677,7 +679,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
   {
     const uint4* src = reinterpret_cast<const uint4*>(p.wpack);
     uint4* dst = reinterpret_cast<uint4*>(gbase);
-    for (int e = tid; e < (int)((16 * BBLK + 2 * kFinalN * NT * 2) / 16); e += kFusedThreads) dst[e] = src[e];
+    for (int e = tid; e < (int)((16 * BBLK + kFinalN * NT * 2) / 16); e += kFusedThreads) dst[e] = src[e];
     for (int e = tid; e < NT; e += kFusedThreads) bias_s[e] = p.bias[e];
     if (tid == 0) bf_s[0] = p.bf[0];
   }
@@ -751,7 +753,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
       constexpr uint32_t b_hi = desc_hi((uint32_t)CIN * 16, 0);
       constexpr uint32_t fa_hi = desc_hi(8 * PXB, swz_layout(PXB));  // d3 rows: swizzled K-major
       constexpr uint32_t fb_hi = desc_hi((uint32_t)NT * 16, 0);
-      const uint32_t fbh = desc_lo(sF, 128), fbl = desc_lo(sF + kFinalN * NT * 2, 128);
+      const uint32_t fb0 = desc_lo(sF, 128);
       uint32_t tseq = 0, fseq = 0;
       RingPos wt, tb;
       // Final conv MMAs of the tile with sequence number fseq and image row i (d3 rows 2i and
@@ -767,13 +769,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
 #pragma unroll
           for (int mu = 0; mu < 2; ++mu) {
             const uint32_t a0 = desc_lo(sD + ((uint32_t)((2 * i + rho) & 3) * 256u + 128u * mu) * PXB, 16);
-            const uint32_t d = tmem + FCOL + b * 64 + 16 * (2 * rho + mu);
-            // high parts, then the low parts into the same accumulator (w = hi + lo)
+            const uint32_t d = tmem + FCOL + b * 128 + 32 * (2 * rho + mu);
 #pragma unroll
             for (int ks = 0; ks < FKS; ++ks)
-              mma_bf16(d, a0 + 2 * ks, fa_hi, fbh + 16 * ks, fb_hi, fdesc, ks != 0 ? 1u : 0u);
-#pragma unroll
-            for (int ks = 0; ks < FKS; ++ks) mma_bf16(d, a0 + 2 * ks, fa_hi, fbl + 16 * ks, fb_hi, fdesc, 1u);
+              mma_bf16(d, a0 + 2 * ks, fa_hi, fb0 + 16 * ks, fb_hi, fdesc, ks != 0 ? 1u : 0u);
           }
         mma_commit(finf0 + 8 * b);
         ++fseq;
@@ -808,19 +807,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
           }
           const bool crop_row = (first + k == Hu - 1) && (Ho & 1);  // odd height: last row's py = 0
           // One MMA per staged view (row r, pixel shift s) and K step, N = the phases that
-          // read that view stacked (fused_view); the first two views initialise all five
-          // accumulator blocks.  The crop case then subtracts the kernel row that falls on
-          // the cropped-away half (B negated through the instruction descriptor).
-          const uint32_t dbase = tmem + buf * (5 * NT);
+          // read that view stacked (fused_view); the first view (all four phases)
+          // initialises the accumulators.  The crop case then subtracts the kernel row that
+          // falls on the cropped-away half (B negated through the instruction descriptor).
+          const uint32_t dbase = tmem + buf * (4 * NT);
 #pragma unroll
-          for (int v = 0; v < 9; ++v) {
+          for (int v = 0; v < kFusedViewMMAs; ++v) {
             const FusedView fv = fused_view(v);
             const uint32_t a0 = desc_lo(slot_of_row[fv.r] + (uint32_t)fv.s * RB, 16);
             const uint32_t b0 = desc_lo(sB + (uint32_t)fv.blk * BBLK, 128);
             const uint32_t vdesc = idesc_n(NT * fv.nb);
 #pragma unroll
             for (int k4 = 0; k4 < KPR; ++k4)
-              mma_bf16(dbase + fv.col * NT, a0 + 2 * k4, a_hi, b0 + 16 * k4, b_hi, vdesc, (v >= 2 || k4 != 0) ? 1u : 0u);
+              mma_bf16(dbase + fv.col * NT, a0 + 2 * k4, a_hi, b0 + 16 * k4, b_hi, vdesc, (v != 0 || k4 != 0) ? 1u : 0u);
           }
           if (crop_row) {
 #pragma unroll
@@ -942,39 +941,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
             break;
           }
           tc_fence_after();
-          // accumulator blocks (units of NT columns): phase (0, 0) = blocks 0 + 4, (0, 1) = 1,
-          // (1, 1) = 2, (1, 0) = 3
-          const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + buf * (5 * NT);
+          // accumulator blocks (units of NT columns): phase (0, 0) = 0, (0, 1) = 1, (1, 1) = 2,
+          // (1, 0) = 3; this group's phases (grp, 0), (grp, 1)
+          const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + buf * (4 * NT);
+          const uint32_t c0 = grp == 0 ? 0u : 3u * NT, c1 = grp == 0 ? (uint32_t)NT : 2u * NT;
           uint32_t rr[2][32];
-          if (grp == 0) {
-            uint32_t rx[32];
-            if (NT == 32) {
-              tmem_ld32_nowait(trow, rr[0]);
-              tmem_ld32_nowait(trow + 4 * NT, rx);
-              tmem_ld32_nowait(trow + NT, rr[1]);
-            } else {
-              tmem_ld16_nowait(trow, rr[0]);
-              tmem_ld16_nowait(trow + 4 * NT, rx);
-              tmem_ld16_nowait(trow + NT, rr[1]);
-            }
-            tmem_wait_ld();
-#pragma unroll
-            for (int c = 0; c < NT; c += 2) {
-              const float2 v = __fadd2_rn(make_float2(__uint_as_float(rr[0][c]), __uint_as_float(rr[0][c + 1])),
-                                          make_float2(__uint_as_float(rx[c]), __uint_as_float(rx[c + 1])));
-              rr[0][c] = __float_as_uint(v.x);
-              rr[0][c + 1] = __float_as_uint(v.y);
-            }
+          if (NT == 32) {
+            tmem_ld32_nowait(trow + c0, rr[0]);
+            tmem_ld32_nowait(trow + c1, rr[1]);
           } else {
-            if (NT == 32) {
-              tmem_ld32_nowait(trow + 3 * NT, rr[0]);
-              tmem_ld32_nowait(trow + 2 * NT, rr[1]);
-            } else {
-              tmem_ld16_nowait(trow + 3 * NT, rr[0]);
-              tmem_ld16_nowait(trow + 2 * NT, rr[1]);
-            }
-            tmem_wait_ld();
+            tmem_ld16_nowait(trow + c0, rr[0]);
+            tmem_ld16_nowait(trow + c1, rr[1]);
           }
+          tmem_wait_ld();
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int px = h;
@@ -1025,9 +1004,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
           }
           tc_fence_after();
           uint32_t q0[32], q1[32];
-          const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + FCOL + fb * 64 + 16 * grp;
+          const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + FCOL + fb * 128 + 32 * grp;
           tmem_ld16_nowait(taddr, q0);
-          tmem_ld16_nowait(taddr + 32, q1);
+          tmem_ld2_nowait(taddr + 16, q0[16], q0[17]);
+          tmem_ld16_nowait(taddr + 64, q1);
+          tmem_ld2_nowait(taddr + 64 + 16, q1[16], q1[17]);
           tmem_wait_ld();
           tc_fence_before();
           __syncwarp();
@@ -1036,8 +1017,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
           // S_ky(x) = P_r(x - 1, ky, 0) + P_r(x, ky, 1) + P_r(x + 1, ky, 2).  The four sums
           // this tile contributes to (rows 2 ip - 1 .. 2 ip + 2, from d3 rows 2 ip and 2 ip + 1)
           // are formed per kx first, so that only 4 values cross to each neighbour.
-          const auto p0 = [&](int t) { return __uint_as_float(q0[t]); };
-          const auto p1 = [&](int t) { return __uint_as_float(q1[t]); };
+          // tap products: high part + low part of the weights
+          const auto p0 = [&](int t) { return __uint_as_float(q0[t]) + __uint_as_float(q0[t + 9]); };
+          const auto p1 = [&](int t) { return __uint_as_float(q1[t]) + __uint_as_float(q1[t + 9]); };
           float part[3][4];  // [kx][row 2 ip - 1 + i]
 #pragma unroll
           for (int kx = 0; kx < 3; ++kx) {
@@ -1164,22 +1146,22 @@ __global__ void pack_fused_kernel(const float* __restrict__ W, int NT, int cin, 
   out[dst] = __float2bfloat16_rn(v);
 }
 
-// Packed B of the fused kernel's final conv: two blocks of [16 rows x NT channels] in the same
-// core-matrix layout, the BF16 high parts hi = bf16(w) of the nine taps' weights (row
-// 3 ky + kx; rows 9-15 zero), then the low parts bf16(w - hi).  hi + lo equals the FP32
-// weight to about 2^-16 relative, so the tensor-core final conv keeps FP32-weight accuracy.
+// Packed B of the fused kernel's final conv: [32 rows x NT channels] in the same core-matrix
+// layout.  Rows 0-8: the BF16 high parts hi = bf16(w) of the nine taps' weights (row
+// 3 ky + kx), rows 9-17: the low parts bf16(w - hi), rows 18-31: zero.  hi + lo equals the
+// FP32 weight to about 2^-16 relative, so the tensor-core final conv keeps FP32-weight
+// accuracy.
 __global__ void pack_final_kernel(const float* __restrict__ wf, int NT, bf16* __restrict__ out) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 2 * kFinalN * NT) return;
-  const int k = idx % NT, n = (idx / NT) % kFinalN, part = idx / (NT * kFinalN);
+  if (idx >= kFinalN * NT) return;
+  const int k = idx % NT, n = idx / NT;
   float v = 0.f;
-  if (n < 9) {
-    const float w = wf[n * NT + k];
+  if (n < 18) {
+    const float w = wf[(n % 9) * NT + k];
     const float hi = __bfloat162float(__float2bfloat16_rn(w));
-    v = part == 0 ? hi : w - hi;
+    v = n < 9 ? hi : w - hi;
   }
-  out[(size_t)part * kFinalN * NT + (size_t)(n % 8) * 8 + (size_t)(n / 8) * NT * 8 + (k % 8) + (size_t)(k / 8) * 64] =
-      __float2bfloat16_rn(v);
+  out[(size_t)(n % 8) * 8 + (size_t)(n / 8) * NT * 8 + (k % 8) + (size_t)(k / 8) * 64] = __float2bfloat16_rn(v);
 }
 
 template <int NT, int RB>
@@ -1438,7 +1420,7 @@ sv_status Ctx::pack_bf16_weights(cudaStream_t st) {
     tc::pack_fused_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const float*)w32.p + net.w_off(L_DEC3), net.dec[2],
                                                                   net.dec[1], (__nv_bfloat16*)wfuse.p);
     if ((s = cuda(cudaGetLastError(), "fused weights"))) return s;
-    const int nf = 2 * tc::kFinalN * net.dec[2];
+    const int nf = tc::kFinalN * net.dec[2];
     tc::pack_final_kernel<<<(unsigned)((nf + 255) / 256), 256, 0, st>>>((const float*)w32.p + net.w_off(L_FINAL),
                                                                     net.dec[2], (__nv_bfloat16*)wfuse.p + n);
     if ((s = cuda(cudaGetLastError(), "fused final weights"))) return s;
