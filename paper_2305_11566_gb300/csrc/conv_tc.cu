@@ -127,6 +127,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
     if (clock64() - t0 > spin) return false;
   }
 }
+// Every lane of the warp waits (one shared-memory access per try for the warp); the result
+// is made warp-uniform.
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, long long spin) {
+  return __all_sync(0xffffffffu, mbar_wait(bar, parity, spin));
+}
 // position in the ring of staged rows, advanced without division
 struct RingPos {
   uint32_t slot = 0, pass = 0;  // pass = number of completed trips round the ring
@@ -185,6 +190,22 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint32_t alo, uint32_t
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// Warp-wide forms: the whole warp runs the issue loop (its descriptors are warp-uniform) and
+// one lane, chosen by elect.sync, issues each instruction.
+__device__ __forceinline__ void mma_bf16_elect(uint32_t tmem_d, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
+                                               uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .b64 da, db;\n .reg .pred p, e;\n .reg .b32 r;\n elect.sync r|e, 0xffffffff;\n"
+      " mov.b64 da, {%1, %2};\n mov.b64 db, {%3, %4};\n setp.ne.b32 p, %6, 0;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n}\n" ::"r"(tmem_d),
+      "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit_elect(uint32_t bar) {
+  asm volatile(
+      "{\n .reg .pred e;\n .reg .b32 r;\n elect.sync r|e, 0xffffffff;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(bar)
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -746,8 +767,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
     }
     __syncwarp();
   } else if (warp == 8) {
-    // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    // ------------------------------------------------------------ MMA issuer (the whole warp
+    // runs the loop with warp-uniform descriptors; one elected lane issues each instruction)
+    {
       const uint32_t fdesc = idesc_n(kFinalN);
       constexpr uint32_t a_hi = desc_hi(8 * RB, swz_layout(RB));
       constexpr uint32_t b_hi = desc_hi((uint32_t)CIN * 16, 0);
@@ -761,8 +783,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
       // the tile's accumulators) and has read out the partial-sum buffer's previous use.
       auto issue_final = [&](int i) -> bool {
         const uint32_t b = fseq & 1, use = fseq >> 1;
-        if (!mbar_wait(acce0 + 8 * b, use & 1, p.spin)) return false;
-        if (use > 0 && !mbar_wait(fine0 + 8 * b, (use - 1) & 1, p.spin)) return false;
+        if (!mbar_wait_warp(acce0 + 8 * b, use & 1, p.spin)) return false;
+        if (use > 0 && !mbar_wait_warp(fine0 + 8 * b, (use - 1) & 1, p.spin)) return false;
         tc_fence_after();
 #pragma unroll
         for (int rho = 0; rho < 2; ++rho)
@@ -772,9 +794,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
             const uint32_t d = tmem + FCOL + b * 128 + 32 * (2 * rho + mu);
 #pragma unroll
             for (int ks = 0; ks < FKS; ++ks)
-              mma_bf16(d, a0 + 2 * ks, fa_hi, fb0 + 16 * ks, fb_hi, fdesc, ks != 0 ? 1u : 0u);
+              mma_bf16_elect(d, a0 + 2 * ks, fa_hi, fb0 + 16 * ks, fb_hi, fdesc, ks != 0 ? 1u : 0u);
           }
-        mma_commit(finf0 + 8 * b);
+        mma_commit_elect(finf0 + 8 * b);
         ++fseq;
         return true;
       };
@@ -787,15 +809,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
         for (int k = 0; k < ntiles && ok; ++k) {
           const int rlo = k == 0 ? 0 : k - 1 + RA;
           for (int r = rlo; r < k + RA; ++r, wt.next(ring)) {
-            if (!mbar_wait(full0 + 8 * wt.slot, wt.pass & 1, p.spin)) {
+            if (!mbar_wait_warp(full0 + 8 * wt.slot, wt.pass & 1, p.spin)) {
               ok = false;
               break;
             }
           }
           const uint32_t buf = tseq & 1, use = tseq >> 1;
-          if (ok && use > 0 && !mbar_wait(acce0 + 8 * buf, (use - 1) & 1, p.spin)) ok = false;
+          if (ok && use > 0 && !mbar_wait_warp(acce0 + 8 * buf, (use - 1) & 1, p.spin)) ok = false;
           if (!ok) {
-            atomicCAS(p.err, 0, 2);
+            if (lane == 0) atomicCAS(p.err, 0, 2);
             break;
           }
           tc_fence_after();
@@ -819,7 +841,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
             const uint32_t vdesc = idesc_n(NT * fv.nb);
 #pragma unroll
             for (int k4 = 0; k4 < KPR; ++k4)
-              mma_bf16(dbase + fv.col * NT, a0 + 2 * k4, a_hi, b0 + 16 * k4, b_hi, vdesc, (v != 0 || k4 != 0) ? 1u : 0u);
+              mma_bf16_elect(dbase + fv.col * NT, a0 + 2 * k4, a_hi, b0 + 16 * k4, b_hi, vdesc, (v != 0 || k4 != 0) ? 1u : 0u);
           }
           if (crop_row) {
 #pragma unroll
@@ -829,17 +851,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
               const uint32_t b0 = desc_lo(sB + (uint32_t)fv.blk * BBLK, 128);
 #pragma unroll
               for (int k4 = 0; k4 < KPR; ++k4)
-                mma_bf16(dbase + fv.col * NT, a0 + 2 * k4, a_hi, b0 + 16 * k4, b_hi, idesc_n(NT) | (1u << 14), 1u);
+                mma_bf16_elect(dbase + fv.col * NT, a0 + 2 * k4, a_hi, b0 + 16 * k4, b_hi, idesc_n(NT) | (1u << 14), 1u);
             }
           }
-          mma_commit(accf0 + 8 * buf);
+          mma_commit_elect(accf0 + 8 * buf);
           // rows no later tile of the strip reads go back to the producer when these MMAs
           // complete (one commit per row on its empty barrier)
           {
             const int nrel = k + 1 < ntiles ? 1 : RA;
             for (int r = 0; r < nrel; ++r) {
               const uint32_t sl = tb.slot + r;
-              mma_commit(empty0 + 8 * (sl >= ring ? sl - ring : sl));
+              mma_commit_elect(empty0 + 8 * (sl >= ring ? sl - ring : sl));
             }
           }
           tb.slot += 1;
@@ -848,23 +870,23 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
           ++tseq;
           // the previous tile's final conv runs while this tile's decoder MMAs are queued
           if (k > 0 && !issue_final(first + k - 1)) {
-            atomicCAS(p.err, 0, 2);
+            if (lane == 0) atomicCAS(p.err, 0, 2);
             ok = false;
           }
         }
         if (ok && ntiles > 0 && !issue_final(first + ntiles - 1)) {
-          atomicCAS(p.err, 0, 2);
+          if (lane == 0) atomicCAS(p.err, 0, 2);
           ok = false;
         }
       }
       const long long drain = p.spin > 2000000000LL ? p.spin : 2000000000LL;
       if (tseq > 0) {
         const uint32_t last = tseq - 1;
-        if (!mbar_wait(accf0 + 8 * (last & 1), (last >> 1) & 1, drain)) atomicCAS(p.err, 0, 3);
+        if (!mbar_wait_warp(accf0 + 8 * (last & 1), (last >> 1) & 1, drain) && lane == 0) atomicCAS(p.err, 0, 3);
       }
       if (fseq > 0) {
         const uint32_t last = fseq - 1;
-        if (!mbar_wait(finf0 + 8 * (last & 1), (last >> 1) & 1, drain)) atomicCAS(p.err, 0, 3);
+        if (!mbar_wait_warp(finf0 + 8 * (last & 1), (last >> 1) & 1, drain) && lane == 0) atomicCAS(p.err, 0, 3);
       }
     }
     __syncwarp();
