@@ -387,8 +387,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
     }
     __syncwarp();
   } else if (warp == 4) {
-    // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    // ------------------------------------------------------------ MMA issuer (the whole warp
+    // runs the loop with warp-uniform descriptors; one elected lane issues each instruction)
+    {
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((128u >> 4) << 24);
       const uint32_t bsz = NT * cin * 2;
       // A: swizzled K-major pixel rows, SBO = 8 pixels (LBO unused: one swizzle span per
@@ -411,15 +412,15 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
         for (int ii = 0; ii < st.cnt && ok; ++ii) {
           const int rlo = ii == 0 ? 0 : STEP * (ii - 1) + RA;  // rows not waited for yet
           for (int r = rlo; r < STEP * ii + RA; ++r, wt.next(ring)) {
-            if (!mbar_wait(full0 + 8 * wt.slot, wt.pass & 1, p.spin)) {
+            if (!mbar_wait_warp(full0 + 8 * wt.slot, wt.pass & 1, p.spin)) {
               ok = false;
               break;
             }
           }
           const uint32_t buf = tseq & 1, use = tseq >> 1;
-          if (ok && use > 0 && !mbar_wait(acce0 + 8 * buf, (use - 1) & 1, p.spin)) ok = false;
+          if (ok && use > 0 && !mbar_wait_warp(acce0 + 8 * buf, (use - 1) & 1, p.spin)) ok = false;
           if (!ok) {
-            atomicCAS(p.err, 0, 2);
+            if (lane == 0) atomicCAS(p.err, 0, 2);
             break;
           }
           tc_fence_after();
@@ -446,17 +447,17 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
 #pragma unroll
               for (int k4 = 0; k4 < KPR; ++k4)
                 // next 16 channels: +32 B inside the swizzled pixel row, +256 B in B
-                mma_bf16(dcol, a0[t] + ak + 2 * k4, a_hi, b0[t] + bk + 16 * k4, b_hi, idesc,
+                mma_bf16_elect(dcol, a0[t] + ak + 2 * k4, a_hi, b0[t] + bk + 16 * k4, b_hi, idesc,
                          (kb | t | k4) != 0 ? 1u : 0u);
           }
-          mma_commit(accf0 + 8 * buf);
+          mma_commit_elect(accf0 + 8 * buf);
           // the rows the strip's next tile no longer reads go back to the producer as soon as
           // these MMAs complete: one commit per row, arriving on that row's empty barrier
           {
             const int nrel = ii + 1 < st.cnt ? STEP : RA;
             for (int r = 0; r < nrel; ++r) {
               const uint32_t sl = tb.slot + r;
-              mma_commit(empty0 + 8 * (sl >= ring ? sl - ring : sl));
+              mma_commit_elect(empty0 + 8 * (sl >= ring ? sl - ring : sl));
             }
           }
           tb.slot += STEP;            // first row of the next tile (the strip's last tile: + RA)
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       if (tseq > 0) {
         const uint32_t last = tseq - 1;
         const long long drain = p.spin > 2000000000LL ? p.spin : 2000000000LL;
-        if (!mbar_wait(accf0 + 8 * (last & 1), (last >> 1) & 1, drain)) atomicCAS(p.err, 0, 3);
+        if (!mbar_wait_warp(accf0 + 8 * (last & 1), (last >> 1) & 1, drain) && lane == 0) atomicCAS(p.err, 0, 3);
       }
     }
     __syncwarp();
