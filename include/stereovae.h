@@ -241,6 +241,9 @@ SV_API sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream);
  *                    width is even; 0: separate kernels (d3 materialised in HBM)
  *   "fused_ring"     0 (default): the fused kernel stages as many input rows ahead as
  *                    shared memory holds; 4..16: at most this many rows in its ring
+ *   "split_rows"     1 (default): a tensor-core layer whose shared memory holds no staged
+ *                    row beyond its tile's own stages channel blocks of rows, so that the
+ *                    next tile's input loads while the current tile still computes; 0: rows
  *   "enc1_tensor"    1 (default): the first encoder layer of an SV_BF16 context runs on the
  *                    tensor cores (im2col tile in shared memory; widths 16, 32, 64); 0: CUDA
  *                    cores (FP32 FMA)

@@ -66,7 +66,8 @@ struct Params {
   int n_strips;
   const bf16* wpack;  // [G][T][NT * cin] in the core-matrix layout
   const float* bias;  // [cout]
-  int cin, cout, G, relu, ring;
+  int cin, cout, G, relu, ring;  // ring: staged units (rows, or channel blocks of rows if split)
+  int split;                      // 1: a ring unit is one channel block of a row
   int* err;
   long long spin;
 };
@@ -94,8 +95,10 @@ __host__ __device__ inline size_t row_bytes(int mode, int cin) {
 }
 __host__ __device__ inline int taps(int mode) { return mode == TM_S2 ? 9 : mode == TM_UP2 ? 4 : 1; }
 __host__ __device__ inline size_t b_bytes(int mode, int NT, int cin) { return (size_t)taps(mode) * NT * cin * 2; }
-__host__ __device__ inline size_t smem_bytes(int mode, int NT, int cin, int ring) {
-  return 1024 + (b_bytes(mode, NT, cin) + (size_t)NT * 4 + 1023) / 1024 * 1024 + (size_t)ring * row_bytes(mode, cin) +
+// ring: staged units, whole rows or (split) one channel block of a row each
+__host__ __device__ inline size_t smem_bytes(int mode, int NT, int cin, int ring, bool split = false) {
+  const size_t unit = split ? row_bytes(mode, cin) / (cin * 2 / rb_of(cin)) : row_bytes(mode, cin);
+  return 1024 + (b_bytes(mode, NT, cin) + (size_t)NT * 4 + 1023) / 1024 * 1024 + (size_t)ring * unit +
          (size_t)(2 * ring + 4) * kBarBytes + 16;
 }
 
@@ -293,11 +296,14 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   const int cin = p.cin;
   const uint32_t ring = (uint32_t)p.ring;
   const int KB = cin * 2 / RB;  // channel blocks
-  const uint32_t rowb = NSET * KB * KBS;
+  // ring units: whole rows, or (split) one channel block of a row, so that a row's first
+  // blocks can be reloaded while its last ones are still read
+  const int UPR = p.split ? KB : 1, KPU = KB / UPR;  // units per row, channel blocks per unit
+  const uint32_t unitb = NSET * KPU * KBS;
   const uint32_t sB = base;
   const uint32_t sBias = sB + (uint32_t)T * NT * cin * 2;
   const uint32_t sA = (sBias + NT * 4 + 1023u) & ~1023u;
-  const uint32_t bars = sA + ring * rowb;
+  const uint32_t bars = sA + ring * unitb;
   const uint32_t full0 = bars, empty0 = bars + ring * 8, accf0 = bars + 2 * ring * 8, acce0 = accf0 + 16;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + (acce0 + 16 - base));
   const float* bias_s = reinterpret_cast<const float*>(gbase + (sBias - base));
@@ -345,8 +351,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   if (warp == 5) {
     // ------------------------------------------------------------ TMA producer (one thread)
     if (lane == 0) {
-      const uint32_t row_tx = (uint32_t)(NSET * KB * NPX * RB);
-      RingPos w;  // slot of the next row to load; row q goes to slot q % ring on pass q / ring
+      const uint32_t unit_tx = (uint32_t)(NSET * KPU * NPX * RB);
+      RingPos w;  // slot of the next unit to load; unit q goes to slot q % ring on pass q / ring
       uint32_t q = 0;
       int last_pair = -1;
       Strip nxt = crank < p.n_strips ? p.strips[crank] : Strip{};
@@ -360,22 +366,23 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
         }
         const int nrows = STEP * (st.cnt - 1) + RA;
         const int y0 = first_row<MODE>(st.i0, py);
-        for (int r = 0; r < nrows; ++r, ++q, w.next(ring)) {
-          // the slot's previous row must have been consumed (pass > 0: released once)
-          if (w.pass > 0 && !mbar_wait(empty0 + 8 * w.slot, (w.pass - 1) & 1, p.spin)) {
-            atomicCAS(p.err, 0, 1);
-            ok = false;
-            break;
+        for (int r = 0; r < nrows && ok; ++r)
+          for (int u = 0; u < UPR; ++u, ++q, w.next(ring)) {
+            // the slot's previous unit must have been consumed (pass > 0: released once)
+            if (w.pass > 0 && !mbar_wait(empty0 + 8 * w.slot, (w.pass - 1) & 1, p.spin)) {
+              atomicCAS(p.err, 0, 1);
+              ok = false;
+              break;
+            }
+            const uint32_t fb = full0 + 8 * w.slot;
+            mbar_expect_tx(fb, unit_tx);
+            const uint32_t dst0 = sA + w.slot * unitb;
+            for (int k = 0; k < NSET; ++k) {
+              const int x0 = set_x0<MODE>(k, st.j0, px);
+              for (int kk = 0; kk < KPU; ++kk)
+                tma_load3(dst0 + (k * KPU + kk) * KBS, &L->tm[k], (u * KPU + kk) * (RB / 2), x0, y0 + r, fb);
+            }
           }
-          const uint32_t fb = full0 + 8 * w.slot;
-          mbar_expect_tx(fb, row_tx);
-          const uint32_t dst0 = sA + w.slot * rowb;
-          for (int k = 0; k < NSET; ++k) {
-            const int x0 = set_x0<MODE>(k, st.j0, px);
-            for (int kb = 0; kb < KB; ++kb)
-              tma_load3(dst0 + (k * KB + kb) * KBS, &L->tm[k], kb * (RB / 2), x0, y0 + r, fb);
-          }
-        }
       }
       // no copy may still be writing shared memory when the CTA ends (also after a
       // timeout): wait for the most recent load of every slot
@@ -402,66 +409,66 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
 #pragma unroll
       for (int t = 0; t < T; ++t) b0[t] = desc_lo(sB + t * bsz, 128);
       uint32_t tseq = 0;
-      RingPos wt;  // next row to wait for (rows are waited for in load order)
-      RingPos tb;  // slot of the first row of the current tile
+      RingPos wt;  // next unit to wait for (units are waited for in load order)
+      RingPos tb;  // slot of the first unit of the current tile
       Strip nxt = crank < p.n_strips ? p.strips[crank] : Strip{};
       for (int s = crank; s < p.n_strips && ok; s += cpg) {
         const Strip st = nxt;
         if (s + cpg < p.n_strips) nxt = p.strips[s + cpg];
-        const int nrows = STEP * (st.cnt - 1) + RA;
+        int waited = 0;  // units of this strip waited for
         for (int ii = 0; ii < st.cnt && ok; ++ii) {
-          const int rlo = ii == 0 ? 0 : STEP * (ii - 1) + RA;  // rows not waited for yet
-          for (int r = rlo; r < STEP * ii + RA; ++r, wt.next(ring)) {
-            if (!mbar_wait_warp(full0 + 8 * wt.slot, wt.pass & 1, p.spin)) {
-              ok = false;
-              break;
-            }
-          }
           const uint32_t buf = tseq & 1, use = tseq >> 1;
-          if (ok && use > 0 && !mbar_wait_warp(acce0 + 8 * buf, (use - 1) & 1, p.spin)) ok = false;
-          if (!ok) {
-            if (lane == 0) atomicCAS(p.err, 0, 2);
-            break;
-          }
-          tc_fence_after();
+          if (use > 0 && !mbar_wait_warp(acce0 + 8 * buf, (use - 1) & 1, p.spin)) ok = false;
           const uint32_t dcol = tmem + buf * NT;
-          uint32_t slot_of_row[RA];
+          const int nrel = ii + 1 < st.cnt ? STEP : RA;  // rows the strip's next tile no longer reads
+          for (int kb = 0; kb < KB && ok; ++kb) {
+            const int u = kb / KPU, kk = kb - u * KPU;
+            if (kk == 0) {
+              // every unit up to (last row of the tile, u), in load order
+              const int upto = (STEP * ii + RA - 1) * UPR + u;
+              for (; waited <= upto; ++waited, wt.next(ring))
+                if (!mbar_wait_warp(full0 + 8 * wt.slot, wt.pass & 1, p.spin)) {
+                  ok = false;
+                  break;
+                }
+              if (!ok) break;
+              tc_fence_after();
+            }
+            // A descriptors (K step 0) of every tap in channel block kb; the MMAs of the
+            // block then issue back to back from independent additions
+            uint32_t a0[T];
 #pragma unroll
-          for (int r = 0; r < RA; ++r) {
-            const uint32_t sl = tb.slot + r;
-            slot_of_row[r] = sA + (sl >= ring ? sl - ring : sl) * rowb;
-          }
-          // A descriptors (K step 0) of every tap for this tile's staged rows; all MMAs
-          // of a channel block then issue back to back from independent additions
-          uint32_t a0[T];
-#pragma unroll
-          for (int t = 0; t < T; ++t) {
-            int ro, se, co;
-            tap_geo<MODE>(t, ro, se, co);
-            a0[t] = desc_lo(slot_of_row[ro] + (uint32_t)(se * KB) * KBS + (uint32_t)co * RB, 16);
-          }
-          for (int kb = 0; kb < KB; ++kb) {
-            const uint32_t ak = (uint32_t)kb * (KBS >> 4), bk = (uint32_t)kb * (16 * KPR);
+            for (int t = 0; t < T; ++t) {
+              int ro, se, co;
+              tap_geo<MODE>(t, ro, se, co);
+              const uint32_t sl = tb.slot + (uint32_t)(ro * UPR + u);
+              a0[t] = desc_lo(sA + (sl >= ring ? sl - ring : sl) * unitb + (uint32_t)(se * KPU + kk) * KBS +
+                                  (uint32_t)co * RB,
+                              16);
+            }
+            const uint32_t bk = (uint32_t)kb * (16 * KPR);
 #pragma unroll
             for (int t = 0; t < T; ++t)
 #pragma unroll
               for (int k4 = 0; k4 < KPR; ++k4)
                 // next 16 channels: +32 B inside the swizzled pixel row, +256 B in B
-                mma_bf16_elect(dcol, a0[t] + ak + 2 * k4, a_hi, b0[t] + bk + 16 * k4, b_hi, idesc,
-                         (kb | t | k4) != 0 ? 1u : 0u);
-          }
-          mma_commit_elect(accf0 + 8 * buf);
-          // the rows the strip's next tile no longer reads go back to the producer as soon as
-          // these MMAs complete: one commit per row, arriving on that row's empty barrier
-          {
-            const int nrel = ii + 1 < st.cnt ? STEP : RA;
-            for (int r = 0; r < nrel; ++r) {
-              const uint32_t sl = tb.slot + r;
-              mma_commit_elect(empty0 + 8 * (sl >= ring ? sl - ring : sl));
+                mma_bf16_elect(dcol, a0[t] + 2 * k4, a_hi, b0[t] + bk + 16 * k4, b_hi, idesc,
+                               (kb | t | k4) != 0 ? 1u : 0u);
+            if (kk == KPU - 1) {
+              // unit u of the rows the next tile no longer reads goes back to the producer
+              // as soon as these MMAs complete (a commit arriving on its empty barrier)
+              for (int r = 0; r < nrel; ++r) {
+                const uint32_t sl = tb.slot + (uint32_t)(r * UPR + u);
+                mma_commit_elect(empty0 + 8 * (sl >= ring ? sl - ring : sl));
+              }
             }
           }
-          tb.slot += STEP;            // first row of the next tile (the strip's last tile: + RA)
-          if (ii + 1 == st.cnt) tb.slot += RA - STEP;
+          if (!ok) {
+            if (lane == 0) atomicCAS(p.err, 0, 2);
+            break;
+          }
+          mma_commit_elect(accf0 + 8 * buf);
+          tb.slot += (uint32_t)(nrel * UPR);  // first unit of the next tile
           while (tb.slot >= ring) tb.slot -= ring;
           ++tseq;
         }
@@ -1500,6 +1507,31 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
       pl.smem = tc::smem_bytes(pl.mode, pl.NT, pl.cin, pl.ring);
     }
   }
+  // a layer whose ring holds no row beyond the tile's own (the weights fill shared memory)
+  // stages channel blocks instead of whole rows: a row's first blocks are reloaded while the
+  // tile still reads its last ones, so the next tile's input arrives ahead of it
+  for (size_t li = 0; li < r.plans.size(); ++li) {
+    TcLayerPlan& pl = r.plans[li];
+    pl.split = 0;
+    const int RA = pl.mode == tc::TM_S2 ? 3 : pl.mode == tc::TM_UP2 ? 2 : 1;
+    const int KB = pl.cin * 2 / tc::rb_of(pl.cin);
+    if (!split_rows || pl.ring > RA || KB < 2) continue;
+    const int k = tc_ctas_override[li] > 0 ? tc_ctas_override[li] : tc_ctas_per_sm;
+    size_t budget = kSmemLimit;
+    if (k > 1) {
+      int per_sm = 0, reserved = 0;
+      cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
+      const size_t share = (size_t)per_sm / k - (size_t)reserved;
+      if (pl.smem <= share) budget = share;  // else k CTAs do not fit anyway: one per SM
+    }
+    int units = RA * KB;
+    while (units < 3 * RA * KB && tc::smem_bytes(pl.mode, pl.NT, pl.cin, units + 1, true) <= budget) ++units;
+    if (units <= RA * KB) continue;  // no unit of look-ahead fits
+    pl.split = 1;
+    pl.ring = units;
+    pl.smem = tc::smem_bytes(pl.mode, pl.NT, pl.cin, units, true);
+  }
   sv_status s;
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
@@ -1584,8 +1616,10 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
     r.tabs[li].grid = grid;
     r.tabs[li].hs = hs;
     if (debug_plans)
-      fprintf(stderr, "[sv] tc layer %d: mode %d cin %d cout %d NT %d ring %d smem %zu blocks/SM %d grid %d strips %zu rows %d\n",
-              pl.layer, pl.mode, pl.cin, pl.cout, pl.NT, pl.ring, pl.smem, bps, grid, strips.size(), hs);
+      fprintf(stderr,
+              "[sv] tc layer %d: mode %d cin %d cout %d NT %d ring %d%s smem %zu blocks/SM %d grid %d strips %zu rows %d\n",
+              pl.layer, pl.mode, pl.cin, pl.cout, pl.NT, pl.ring, pl.split ? " (channel blocks)" : "", pl.smem, bps, grid,
+              strips.size(), hs);
     int mb = 0;
     for (int i = 0; i < n; ++i) mb = std::max(mb, upfix_segments(lps[i].Ho, lps[i].Wo));
     r.tabs[li].fix_segments = mb;
@@ -1685,6 +1719,7 @@ sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream
     prm.G = pl.G;
     prm.relu = pl.relu;
     prm.ring = pl.ring;
+    prm.split = pl.split;
     prm.err = (int*)err_flag.p;
     prm.spin = spin_limit;
     if (tl && pl.layer == L_MU) {

@@ -585,6 +585,12 @@ sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value) {
     c->drop_graphs();
     return SV_OK;
   }
+  if (!strcmp(key, "split_rows")) {
+    if (value != 0 && value != 1) return c->fail(SV_ERR_INVALID_ARG, "split_rows must be 0 or 1");
+    c->split_rows = (int)value;
+    c->drop_graphs();
+    return SV_OK;
+  }
   if (!strcmp(key, "enc1_tensor")) {
     if (value != 0 && value != 1) return c->fail(SV_ERR_INVALID_ARG, "enc1_tensor must be 0 or 1");
     c->enc1_tensor = (int)value;

@@ -25,6 +25,7 @@ struct DevBuf {
 // Launch plan of one tensor-core layer.
 struct TcLayerPlan {
   int layer, mode, NT, G, ring, cin, cout, relu;
+  int split;  // 1: ring units are channel blocks of rows (ring counts units)
   size_t wofs, smem;
   size_t fix_wofs;  // decoder layers: BF16 [co][3][3][ci] weights of the border fix
 };
@@ -109,6 +110,7 @@ struct Ctx {
   int fused_ring = 0;                   // fused kernel's staged-row ring: 0 as deep as shared memory allows
   int fused_prefetch = 4;               // fused kernel: rows prefetched into L2 ahead of the loaded row
   int enc1_tensor = 1;                  // 1: enc1 on the tensor cores where its width allows
+  int split_rows = 1;                   // 1: layers without a spare staged row stage channel blocks
   int host_copy = 1;                    // sv_pipeline_host: 0 copy calls, 1 gather kernel in, 2 kernels both ways
   bool last_fused = false;              // the last tensor-core call did not materialise d3
   int tc_ctas_per_sm = 0;               // 0: deepest row ring (one CTA per SM); k: ring sized for k
