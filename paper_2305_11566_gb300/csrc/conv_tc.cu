@@ -283,7 +283,7 @@ __device__ __forceinline__ void tap_geo(int t, int& row, int& set, int& col) {
   }
 }
 
-template <int MODE, int NT, int RB>
+template <int MODE, int NT, int RB, bool SPLIT = false>
 __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_constant__ Params p) {
   using G_ = Geo<MODE>;
   constexpr int RA = G_::RA, STEP = G_::STEP, T = G_::T, NSET = G_::NSET, NPX = G_::NPX;
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   const int KB = cin * 2 / RB;  // channel blocks
   // ring units: whole rows, or (split) one channel block of a row, so that a row's first
   // blocks can be reloaded while its last ones are still read
-  const int UPR = p.split ? KB : 1, KPU = KB / UPR;  // units per row, channel blocks per unit
+  const int UPR = SPLIT ? KB : 1, KPU = KB / UPR;  // units per row, channel blocks per unit (KB or 1)
   const uint32_t unitb = NSET * KPU * KBS;
   const uint32_t sB = base;
   const uint32_t sBias = sB + (uint32_t)T * NT * cin * 2;
@@ -418,56 +418,83 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
         int waited = 0;  // units of this strip waited for
         for (int ii = 0; ii < st.cnt && ok; ++ii) {
           const uint32_t buf = tseq & 1, use = tseq >> 1;
-          if (use > 0 && !mbar_wait_warp(acce0 + 8 * buf, (use - 1) & 1, p.spin)) ok = false;
           const uint32_t dcol = tmem + buf * NT;
           const int nrel = ii + 1 < st.cnt ? STEP : RA;  // rows the strip's next tile no longer reads
-          for (int kb = 0; kb < KB && ok; ++kb) {
-            const int u = kb / KPU, kk = kb - u * KPU;
-            if (kk == 0) {
-              // every unit up to (last row of the tile, u), in load order
-              const int upto = (STEP * ii + RA - 1) * UPR + u;
-              for (; waited <= upto; ++waited, wt.next(ring))
-                if (!mbar_wait_warp(full0 + 8 * wt.slot, wt.pass & 1, p.spin)) {
-                  ok = false;
-                  break;
-                }
-              if (!ok) break;
+          if (!SPLIT) {
+            // whole-row units: the tile's rows, then one descriptor set for all channel blocks
+            for (; waited < STEP * ii + RA; ++waited, wt.next(ring))
+              if (!mbar_wait_warp(full0 + 8 * wt.slot, wt.pass & 1, p.spin)) {
+                ok = false;
+                break;
+              }
+            if (ok && use > 0 && !mbar_wait_warp(acce0 + 8 * buf, (use - 1) & 1, p.spin)) ok = false;
+            if (ok) {
               tc_fence_after();
+              // A descriptors (K step 0) of every tap for this tile's staged rows; all MMAs
+              // of a channel block then issue back to back from independent additions
+              uint32_t a0[T];
+#pragma unroll
+              for (int t = 0; t < T; ++t) {
+                int ro, se, co;
+                tap_geo<MODE>(t, ro, se, co);
+                const uint32_t sl = tb.slot + (uint32_t)ro;
+                a0[t] = desc_lo(sA + (sl >= ring ? sl - ring : sl) * unitb + (uint32_t)(se * KB) * KBS + (uint32_t)co * RB,
+                                16);
+              }
+              for (int kb = 0; kb < KB; ++kb) {
+                const uint32_t ak = (uint32_t)kb * (KBS >> 4), bk = (uint32_t)kb * (16 * KPR);
+#pragma unroll
+                for (int t = 0; t < T; ++t)
+#pragma unroll
+                  for (int k4 = 0; k4 < KPR; ++k4)
+                    // next 16 channels: +32 B inside the swizzled pixel row, +256 B in B
+                    mma_bf16_elect(dcol, a0[t] + ak + 2 * k4, a_hi, b0[t] + bk + 16 * k4, b_hi, idesc,
+                                   (kb | t | k4) != 0 ? 1u : 0u);
+              }
+              mma_commit_elect(accf0 + 8 * buf);
+              // the rows the strip's next tile no longer reads go back to the producer as
+              // soon as these MMAs complete (one commit per row on its empty barrier)
+              for (int r = 0; r < nrel; ++r) {
+                const uint32_t sl = tb.slot + (uint32_t)r;
+                mma_commit_elect(empty0 + 8 * (sl >= ring ? sl - ring : sl));
+              }
             }
-            // A descriptors (K step 0) of every tap in channel block kb; the MMAs of the
-            // block then issue back to back from independent additions
+          }
+          if (SPLIT && use > 0 && !mbar_wait_warp(acce0 + 8 * buf, (use - 1) & 1, p.spin)) ok = false;
+          for (int kb = 0; SPLIT && kb < KB && ok; ++kb) {
+            // channel-block units (KPU = 1): wait, issue and release block by block
+            for (const int upto = (STEP * ii + RA - 1) * UPR + kb; waited <= upto; ++waited, wt.next(ring))
+              if (!mbar_wait_warp(full0 + 8 * wt.slot, wt.pass & 1, p.spin)) {
+                ok = false;
+                break;
+              }
+            if (!ok) break;
+            tc_fence_after();
             uint32_t a0[T];
 #pragma unroll
             for (int t = 0; t < T; ++t) {
               int ro, se, co;
               tap_geo<MODE>(t, ro, se, co);
-              const uint32_t sl = tb.slot + (uint32_t)(ro * UPR + u);
-              a0[t] = desc_lo(sA + (sl >= ring ? sl - ring : sl) * unitb + (uint32_t)(se * KPU + kk) * KBS +
-                                  (uint32_t)co * RB,
-                              16);
+              const uint32_t sl = tb.slot + (uint32_t)(ro * UPR + kb);
+              a0[t] = desc_lo(sA + (sl >= ring ? sl - ring : sl) * unitb + (uint32_t)se * KBS + (uint32_t)co * RB, 16);
             }
             const uint32_t bk = (uint32_t)kb * (16 * KPR);
 #pragma unroll
             for (int t = 0; t < T; ++t)
 #pragma unroll
               for (int k4 = 0; k4 < KPR; ++k4)
-                // next 16 channels: +32 B inside the swizzled pixel row, +256 B in B
-                mma_bf16_elect(dcol, a0[t] + 2 * k4, a_hi, b0[t] + bk + 16 * k4, b_hi, idesc,
-                               (kb | t | k4) != 0 ? 1u : 0u);
-            if (kk == KPU - 1) {
-              // unit u of the rows the next tile no longer reads goes back to the producer
-              // as soon as these MMAs complete (a commit arriving on its empty barrier)
-              for (int r = 0; r < nrel; ++r) {
-                const uint32_t sl = tb.slot + (uint32_t)(r * UPR + u);
-                mma_commit_elect(empty0 + 8 * (sl >= ring ? sl - ring : sl));
-              }
+                mma_bf16_elect(dcol, a0[t] + 2 * k4, a_hi, b0[t] + bk + 16 * k4, b_hi, idesc, (kb | t | k4) != 0 ? 1u : 0u);
+            // block kb of the rows the next tile no longer reads goes back to the producer
+            for (int r = 0; r < nrel; ++r) {
+              const uint32_t sl = tb.slot + (uint32_t)(r * UPR + kb);
+              mma_commit_elect(empty0 + 8 * (sl >= ring ? sl - ring : sl));
             }
           }
           if (!ok) {
             if (lane == 0) atomicCAS(p.err, 0, 2);
             break;
           }
-          mma_commit_elect(accf0 + 8 * buf);
+          if (SPLIT) mma_commit_elect(accf0 + 8 * buf);
           tb.slot += (uint32_t)(nrel * UPR);  // first unit of the next tile
           while (tb.slot >= ring) tb.slot -= ring;
           ++tseq;
@@ -1219,7 +1246,13 @@ bool fused_supported(int cout, int cin) {
 
 template <int MODE, int NT, int RB>
 cudaError_t launch_mode_nt(const Params& p, int grid, size_t smem, cudaStream_t st) {
+  // channel-block rings are planned only for up-sampling layers with 128-byte channel blocks
   auto k = conv_tc_kernel<MODE, NT, RB>;
+  if constexpr (MODE == TM_UP2 && RB == 128) {
+    if (p.split) k = conv_tc_kernel<MODE, NT, RB, true>;
+  } else {
+    if (p.split) return cudaErrorInvalidValue;
+  }
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // all of the SM's unified L1 / shared storage as shared memory: co-resident CTAs
@@ -1515,7 +1548,7 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
     pl.split = 0;
     const int RA = pl.mode == tc::TM_S2 ? 3 : pl.mode == tc::TM_UP2 ? 2 : 1;
     const int KB = pl.cin * 2 / tc::rb_of(pl.cin);
-    if (!split_rows || pl.ring > RA || KB < 2) continue;
+    if (!split_rows || pl.mode != tc::TM_UP2 || tc::rb_of(pl.cin) != 128 || pl.ring > RA || KB < 2) continue;
     const int k = tc_ctas_override[li] > 0 ? tc_ctas_override[li] : tc_ctas_per_sm;
     size_t budget = kSmemLimit;
     if (k > 1) {
