@@ -183,3 +183,34 @@ def test_bf16_fused_final(contexts, name, shape, W, H, dmax, k, D, rows):
     assert d.max() <= 5e-3, f"{name}: fused vs unfused max |dY| = {d.max():.2e}"
     ref = oracle.refine_forward(shape, params, p.left, disp_o.astype(np.float64))
     check_output(Yf, ref, p.gt, name)
+
+
+def test_bf16_kernel_variants_agree(contexts):
+    """Variants of the same layers behind options: the channel-block staging ring of dec1
+    (split_rows) must give bit-identical results to whole-row staging (same MMAs, same
+    order); enc1 on the tensor cores (high/low BF16 parts, FP32 accumulation) against the
+    CUDA-core FP32 kernel: e1 within one BF16 rounding, and both refined outputs at the
+    oracle's bar."""
+    shape, W, H, dmax, k, D = synth.NET_WIDE, 333, 97, 60.0, 5, 24
+    p = synth.make_pair(W, H, dmax, 7400)
+    disp_o = oracle.coarse_match(p.left, p.right, k, D)[0]
+    ctx = contexts(shape, k)
+    dp = binding.to_device(p, D)
+    cm = [torch.from_numpy(disp_o.astype(np.int16)).cuda()]
+    out = {}
+    try:
+        for key, val in (("split_rows", 0), ("split_rows", 1), ("enc1_tensor", 0), ("enc1_tensor", 1)):
+            ctx.set_option(key, val)
+            y = ctx.refine([dp], cm)[0].cpu().numpy().astype(np.float64)
+            ctx.synchronize()
+            out[(key, val)] = (y, ctx.debug_activation(0, 0, act_shape(shape, H, W, "e1")))
+    finally:
+        ctx.set_option("split_rows", 1)
+        ctx.set_option("enc1_tensor", 1)
+    assert np.array_equal(out[("split_rows", 0)][0], out[("split_rows", 1)][0])
+    e_t, e_c = out[("enc1_tensor", 1)][1], out[("enc1_tensor", 0)][1]
+    scale = np.abs(e_c).max()
+    assert np.abs(e_t - e_c).max() <= scale * 2.0 ** -7, "enc1 tensor-core vs CUDA-core"
+    ref = oracle.refine_forward(shape, synth.he_normal_weights(shape, 7), p.left, disp_o.astype(np.float64))
+    for v in (0, 1):
+        check_output(out[("enc1_tensor", v)][0], ref, p.gt, f"enc1_tensor {v}")
