@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "pairs/s at 1242×375 D=48 (plain FP32 vs BF16-batched), ΔEPE vs FP64 oracle"
 W, H, D, WIN = 1242, 375, 48, 9
 DMAX = 190.0
+SGM_P1, SGM_P2 = 0.1, 0.5  # penalties of Eq. 4 for the semi-global matching leg (unstated in the paper)
 FP32_PEAK_TFLOPS_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
 
 
@@ -49,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
+    ap.add_argument("--sgm", action="store_true",
+                    help="also time the semi-global matching coarse stage (4 paths) on the same pairs")
     ap.add_argument("--train-pairs", type=int, default=16)
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch plans (fixed launch order, e.g. for profiler captures)")
@@ -469,6 +472,34 @@ def run_ours(args):
                  "loss_last": float(Lt.item())}
         tctx.close()
 
+    sgm = None
+    if args.sgm:
+        # the semi-global matching variant of the coarse stage on the same pairs: ZNCC cost
+        # volume, 4 aggregation paths, winner-take-all (sv_coarse_match_sgm)
+        sctx = binding.Context(shape, WIN, "bf16", dev)
+        with torch.cuda.stream(st):
+            for _ in range(args.warmup):
+                sctx.coarse_match_sgm(dps, SGM_P1, SGM_P2, 4, stream=st)
+        torch.cuda.synchronize()
+        sctx.profile(True)
+        sctx.profile_read(reset=True)
+        sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with torch.cuda.stream(st):
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)
+                sev[k][0].record(st)
+                sctx.coarse_match_sgm(dps, SGM_P1, SGM_P2, 4, stream=st)
+                sev[k][1].record(st)
+        torch.cuda.synchronize()
+        sprof = sctx.profile_read(reset=True)
+        sctx.profile(False)
+        sms = max_over_ranks(sum(a.elapsed_time(b) for a, b in sev)) / args.steps
+        vol_bytes = B * (W // 4) * (H // 4) * D * 4
+        sgm = {"pairs_per_s": whole_job_value(B, world, sms), "ms_per_step": sms, "P1": SGM_P1, "P2": SGM_P2,
+               "npaths": 4, "kernel_ms_per_step": {kn: v[1] / args.steps for kn, v in sprof.items()},
+               "cost_volume_bytes": vol_bytes}
+        sctx.close()
+
     value = whole_job_value(B, world, R["ms_per_step"])
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
@@ -492,6 +523,8 @@ def run_ours(args):
         "tuning": tuning,
         "train_step": train,
     }
+    if sgm is not None:
+        line["sgm"] = sgm
     if rank == 0:
         print(json.dumps(line))
     for r in results.values():
@@ -521,7 +554,8 @@ def run_reference(args):
     el = time.perf_counter() - t
     value = args.steps / el
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": 0, "steps": args.steps,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "1 synthetic 1242x375 stereo pair per step, D=48, 9x9 ZNCC window, "

@@ -133,6 +133,21 @@ SV_API sv_status sv_coarse_match(sv_ctx* ctx, const sv_pair* pairs, int n_pairs,
 SV_API sv_status sv_refine(sv_ctx* ctx, const sv_pair* pairs, const int16_t* const* coarse, int n_pairs,
                     float* const* disp_out, sv_stream stream);
 
+/* Semi-global matching variant of the coarse stage (Sec. III-A, Eq. 1 and 4-6).  For every
+ * pair: the quarter-size images (4 x 4 box sums), the ZNCC cost volume C = 1 - rho of Eq. 1-3
+ * (window side = the context's window, clamp-to-edge windows; candidates with x - d < 0 cost
+ * 2, the largest value of Eq. 1), aggregated by Eq. 4 along `npaths` directions taken in the
+ * order left-to-right, right-to-left, top-to-bottom, bottom-to-top (1..4) and summed (Eq. 5),
+ * then winner-take-all (Eq. 6, lowest d on ties) into disp_out[i] ((H/4) x (W/4) int16,
+ * device).  P1 (change of one disparity) and P2 (larger changes) are the penalties of Eq. 4,
+ * both >= 0; the paper does not give their values.  cost_out (nullable array; entries
+ * nullable) receives the aggregated volume [H/4][W/4][max_disp] FP32 (device).  Returns
+ * SV_ERR_INVALID_ARG for a negative penalty, npaths outside 1..4 or a NULL disp_out entry,
+ * SV_ERR_UNSUPPORTED when 2 x window x (W/4) x 4 bytes exceed 227 KB.  Asynchronous on
+ * `stream`; the context's work buffers are reused by the next call. */
+SV_API sv_status sv_coarse_match_sgm(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, float P1, float P2, int npaths,
+                                     int16_t* const* disp_out, float* const* cost_out, sv_stream stream);
+
 /* Coarse matching followed by refinement (sv_coarse_match + sv_refine) with the
  * coarse maps kept in the context's workspace. */
 SV_API sv_status sv_pipeline(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, float* const* disp_out, sv_stream stream);

@@ -18,6 +18,10 @@ Parity status per function (what pins each one, in tests/test_oracle_*.py):
                    nearest-x2 via torch interpolate
   refine_forward   composed of the pinned pieces; layer-by-layer against torch FP64
   refine_backward  central finite differences in FP64 and torch FP64 autograd
+  sgm_path / sgm   brute-force minimum over every disparity sequence of a path (tiny D, w);
+                   P1 = P2 = 0 reduces to the cost itself; constant-shift invariance;
+                   direction symmetry under flips / transposes; 0 <= C_r - C <= P2
+  sgm_wta          ties to the lowest d; equals the plain argmin of C when P1 = P2 = 0
   end-to-end disparity error vs synthetic ground truth: parity unpinned
   (random weights; the paper's trained weights and KITTI are absent).
 """
@@ -58,6 +62,9 @@ def lib():
         L.orc_zncc_volume.argtypes = [P, P, c_int, c_int, c_int, c_int, P]
         L.orc_zncc_wta.argtypes = [P, P, c_int, c_int, c_int, c_int, P, P, P]
         L.orc_upsample4.argtypes = [P, c_int, c_int, c_int, c_int, P]
+        L.orc_sgm_path.argtypes = [P, c_int, c_int, c_int, c_double, c_double, c_int, P]
+        L.orc_sgm.argtypes = [P, c_int, c_int, c_int, c_double, c_double, c_int, P]
+        L.orc_sgm_wta.argtypes = [P, c_int, c_int, c_int, P]
         L.orc_upsample4_backward.argtypes = [P, c_int, c_int, c_int, c_int, P]
         L.orc_conv2d.argtypes = [P, c_int, c_int, c_int, P, P, c_int, c_int, c_int, c_int, c_int, c_int, c_int,
                                  c_int, P]
@@ -139,6 +146,40 @@ def zncc_wta(SL, SR, k: int, D: int):
 def coarse_match(left: np.ndarray, right: np.ndarray, k: int, D: int):
     """Downsample both images and run ZNCC + WTA: (disp, best, second)."""
     return zncc_wta(downsample4(left), downsample4(right), k, D)
+
+
+# ---------------------------------------------------------------- semi-global matching
+def sgm_cost(rho: np.ndarray) -> np.ndarray:
+    """Cost volume of Eq. 1, C = 1 - rho, with the largest cost (2) where x - d < 0."""
+    return np.where(np.isnan(rho), 2.0, 1.0 - rho)
+
+
+def sgm_path(C: np.ndarray, P1: float, P2: float, direction: int) -> np.ndarray:
+    """C_r of Eq. 4 along one direction (0: left to right, 1: right to left, 2: top to
+    bottom, 3: bottom to top), FP64 [h, w, D]."""
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    h, w, D = C.shape
+    out = np.zeros_like(C)
+    lib().orc_sgm_path(_p(C), w, h, D, float(P1), float(P2), int(direction), _p(out))
+    return out
+
+
+def sgm(C: np.ndarray, P1: float, P2: float, npaths: int = 4) -> np.ndarray:
+    """C_SGM of Eq. 5: the sum of sgm_path over the first `npaths` directions."""
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    h, w, D = C.shape
+    out = np.zeros_like(C)
+    lib().orc_sgm(_p(C), w, h, D, float(P1), float(P2), int(npaths), _p(out))
+    return out
+
+
+def sgm_wta(Csgm: np.ndarray) -> np.ndarray:
+    """Eq. 6 on an aggregated volume: argmin over d, lowest d on ties (int32 [h, w])."""
+    Csgm = np.ascontiguousarray(Csgm, dtype=np.float64)
+    h, w, D = Csgm.shape
+    disp = np.zeros((h, w), dtype=np.int32)
+    lib().orc_sgm_wta(_p(Csgm), w, h, D, _p(disp))
+    return disp
 
 
 def upsample4(disp: np.ndarray, W: int, H: int) -> np.ndarray:

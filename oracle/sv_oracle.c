@@ -24,6 +24,8 @@
  *   orc_refine_forward   the refinement net and the residual onto the upsampled map
  *   orc_loss             smooth-L1 reconstruction + KL of the latent (Sec. III-B2, Eq. 9-11)
  *   orc_refine_backward  hand-derived gradient of orc_loss through the net (FP64)
+ *   orc_sgm_path         semi-global aggregation along one direction (Sec. III-A, Eq. 4)
+ *   orc_sgm              sum over directions (Eq. 5); orc_sgm_wta: Eq. 6 on the sum
  *
  * Readings of the paper (where it is silent, garbled or inconsistent):
  *   - cost range: Eq. 1 gives 1 - rho, which lies in [0, 2], not [0, 1]; the
@@ -605,5 +607,69 @@ void orc_adam(double* p, double* m, double* v, const double* g, size_t n, int t,
     m[i] = b1 * m[i] + (1 - b1) * g[i];
     v[i] = b2 * v[i] + (1 - b2) * g[i] * g[i];
     p[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+  }
+}
+
+/* ------------------------------------------------------------------ semi-global matching
+ * Sec. III-A (Eq. 4-6) on a coarse cost volume C [h][w][D], C = 1 - rho of Eq. 1.
+ * Readings (the paper leaves them open): candidates with x - d < 0 carry the largest cost
+ * of Eq. 1, 2; four path directions; P1, P2 are arguments.
+ *
+ * orc_sgm_path: the cost C_r aggregated along one direction r by Eq. 4.  dir 0: r = (1, 0),
+ * paths run left to right along each row; 1: right to left; 2: top to bottom along each
+ * column; 3: bottom to top.  The first pixel of a path keeps its own cost (no predecessor).
+ * The terms with d - 1 < 0 or d + 1 >= D are absent.  Eq. 4's minimum over i excludes d and
+ * d +- 1; taking it over all disparities gives the same value, since those three are
+ * already in the minimum with smaller penalties. */
+void orc_sgm_path(const double* C, int w, int h, int D, double P1, double P2, int dir, double* Cr) {
+  const int dx = dir == 0 ? 1 : dir == 1 ? -1 : 0;
+  const int dy = dir == 2 ? 1 : dir == 3 ? -1 : 0;
+  const int nlines = dy == 0 ? h : w, len = dy == 0 ? w : h;
+#pragma omp parallel for schedule(static)
+  for (int line = 0; line < nlines; ++line) {
+    for (int s = 0; s < len; ++s) {
+      const int x = dx == 0 ? line : dx > 0 ? s : w - 1 - s;
+      const int y = dy == 0 ? line : dy > 0 ? s : h - 1 - s;
+      const double* c = C + ((size_t)y * w + x) * D;
+      double* cur = Cr + ((size_t)y * w + x) * D;
+      if (s == 0) {
+        for (int d = 0; d < D; ++d) cur[d] = c[d];
+        continue;
+      }
+      const double* prev = Cr + ((size_t)(y - dy) * w + (x - dx)) * D;
+      double mprev = prev[0];
+      for (int k = 1; k < D; ++k)
+        if (prev[k] < mprev) mprev = prev[k];
+      for (int d = 0; d < D; ++d) {
+        double best = prev[d];
+        if (d > 0 && prev[d - 1] + P1 < best) best = prev[d - 1] + P1;
+        if (d + 1 < D && prev[d + 1] + P1 < best) best = prev[d + 1] + P1;
+        if (mprev + P2 < best) best = mprev + P2;
+        cur[d] = c[d] + best - mprev;
+      }
+    }
+  }
+}
+
+/* C_SGM = sum over the first npaths directions of orc_sgm_path (Eq. 5), npaths in 1..4. */
+void orc_sgm(const double* C, int w, int h, int D, double P1, double P2, int npaths, double* Csgm) {
+  const size_t n = (size_t)w * h * D;
+  double* Cr = malloc(n * sizeof(double));
+  for (size_t i = 0; i < n; ++i) Csgm[i] = 0.0;
+  for (int dir = 0; dir < npaths; ++dir) {
+    orc_sgm_path(C, w, h, D, P1, P2, dir, Cr);
+    for (size_t i = 0; i < n; ++i) Csgm[i] += Cr[i];
+  }
+  free(Cr);
+}
+
+/* Eq. 6 on an aggregated volume: the disparity of the smallest cost, lowest d on ties. */
+void orc_sgm_wta(const double* Csgm, int w, int h, int D, int32_t* disp) {
+  for (size_t p = 0; p < (size_t)w * h; ++p) {
+    const double* c = Csgm + p * D;
+    int best = 0;
+    for (int d = 1; d < D; ++d)
+      if (c[d] < c[best]) best = d;
+    disp[p] = best;
   }
 }

@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, c_char_p, c_double, c_int, c_size_t, c_void_p
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int, c_size_t, c_void_p
 from dataclasses import dataclass
 
 import numpy as np
@@ -54,6 +54,8 @@ API = {
     "sv_get_weights": ([c_void_p, c_void_p, c_size_t], c_int),
     "sv_coarse_match": ([c_void_p, POINTER(SvPair), c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
                          c_void_p], c_int),
+    "sv_coarse_match_sgm": ([c_void_p, POINTER(SvPair), c_int, c_float, c_float, c_int, POINTER(c_void_p),
+                             POINTER(c_void_p), c_void_p], c_int),
     "sv_refine": ([c_void_p, POINTER(SvPair), POINTER(c_void_p), c_int, POINTER(c_void_p), c_void_p], c_int),
     "sv_pipeline": ([c_void_p, POINTER(SvPair), c_int, POINTER(c_void_p), c_void_p], c_int),
     "sv_refine_train": ([c_void_p, POINTER(SvPair), POINTER(c_void_p), POINTER(c_void_p), c_int, POINTER(c_void_p),
@@ -225,6 +227,17 @@ class Context:
                                           _ptrs(best) if scores else None, _ptrs(second) if scores else None,
                                           _stream(stream)))
         return (disp, best, second) if scores else disp
+
+    def coarse_match_sgm(self, pairs, P1: float, P2: float, npaths: int = 4, costs: bool = False, stream=None):
+        """sv_coarse_match_sgm: int16 coarse maps (and the aggregated FP32 cost volumes
+        [h, w, D] when `costs`)."""
+        import torch
+        dev = pairs[0].left.device if pairs else "cuda"
+        disp = [torch.empty(p.coarse_hw, dtype=torch.int16, device=dev) for p in pairs]
+        vols = [torch.empty((*p.coarse_hw, p.max_disp), dtype=torch.float32, device=dev) for p in pairs] if costs else None
+        self._check(lib().sv_coarse_match_sgm(self._h, _pairs_array(pairs), len(pairs), float(P1), float(P2), int(npaths),
+                                              _ptrs(disp), _ptrs(vols) if costs else None, _stream(stream)))
+        return (disp, vols) if costs else disp
 
     def refine(self, pairs, coarse, stream=None, out=None):
         import torch
