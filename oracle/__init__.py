@@ -22,6 +22,9 @@ Parity status per function (what pins each one, in tests/test_oracle_*.py):
                    P1 = P2 = 0 reduces to the cost itself; constant-shift invariance;
                    direction symmetry under flips / transposes; 0 <= C_r - C <= P2
   sgm_wta          ties to the lowest d; equals the plain argmin of C when P1 = P2 = 0
+  smp              hand-made collisions; injective rows unchanged; no two valid pixels share a
+                   target afterwards
+  median3          scipy.ndimage.median_filter (3 x 3, nearest) as an independent routine
   end-to-end disparity error vs synthetic ground truth: parity unpinned
   (random weights; the paper's trained weights and KITTI are absent).
 """
@@ -65,6 +68,8 @@ def lib():
         L.orc_sgm_path.argtypes = [P, c_int, c_int, c_int, c_double, c_double, c_int, P]
         L.orc_sgm.argtypes = [P, c_int, c_int, c_int, c_double, c_double, c_int, P]
         L.orc_sgm_wta.argtypes = [P, c_int, c_int, c_int, P]
+        L.orc_smp.argtypes = [P, c_int, c_int, c_int, P]
+        L.orc_median3.argtypes = [P, c_int, c_int, P]
         L.orc_upsample4_backward.argtypes = [P, c_int, c_int, c_int, c_int, P]
         L.orc_conv2d.argtypes = [P, c_int, c_int, c_int, P, P, c_int, c_int, c_int, c_int, c_int, c_int, c_int,
                                  c_int, P]
@@ -180,6 +185,25 @@ def sgm_wta(Csgm: np.ndarray) -> np.ndarray:
     disp = np.zeros((h, w), dtype=np.int32)
     lib().orc_sgm_wta(_p(Csgm), w, h, D, _p(disp))
     return disp
+
+
+def smp(disp: np.ndarray, D: int) -> np.ndarray:
+    """Single-matching-phase check (Eq. 7 read as uniqueness of the target column): invalid
+    pixels take the nearest valid disparity of their row (int32 [h, w])."""
+    d = np.ascontiguousarray(disp, dtype=np.int32)
+    h, w = d.shape
+    out = np.zeros_like(d)
+    lib().orc_smp(_p(d), w, h, int(D), _p(out))
+    return out
+
+
+def median3(disp: np.ndarray) -> np.ndarray:
+    """3 x 3 median filter with edge clamping (int32 [h, w])."""
+    d = np.ascontiguousarray(disp, dtype=np.int32)
+    h, w = d.shape
+    out = np.zeros_like(d)
+    lib().orc_median3(_p(d), w, h, _p(out))
+    return out
 
 
 def upsample4(disp: np.ndarray, W: int, H: int) -> np.ndarray:

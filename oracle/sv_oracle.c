@@ -26,6 +26,8 @@
  *   orc_refine_backward  hand-derived gradient of orc_loss through the net (FP64)
  *   orc_sgm_path         semi-global aggregation along one direction (Sec. III-A, Eq. 4)
  *   orc_sgm              sum over directions (Eq. 5); orc_sgm_wta: Eq. 6 on the sum
+ *   orc_smp, orc_median3 single-matching-phase occlusion check and median filter (Eq. 7
+ *                        and the text after it)
  *
  * Readings of the paper (where it is silent, garbled or inconsistent):
  *   - cost range: Eq. 1 gives 1 - rho, which lies in [0, 2], not [0, 1]; the
@@ -672,4 +674,58 @@ void orc_sgm_wta(const double* Csgm, int w, int h, int D, int32_t* disp) {
       if (c[d] < c[best]) best = d;
     disp[p] = best;
   }
+}
+
+/* ------------------------------------------------------------------ post-processing
+ * Sec. III-A (Eq. 7 and the text after it), on a coarse disparity map disp [h][w].
+ * Readings: Eq. 7 as printed (|x - D(x) - (x - k - D(x - k))| <= 1 for every k in (0, D))
+ * contradicts the uniqueness it states in words ("no pixel of the reference image is matched
+ * by two or more pixels of the target image"); the oracle takes the words: pixel x is valid
+ * iff no pixel x - k to its left, 0 < k < D, is matched to the same target column
+ * (x - D(x) != x - k - D(x - k)), so of two pixels sharing a target the left one keeps it.
+ * An invalid pixel takes the disparity of the nearest valid pixel of its row (the left one
+ * at equal distance); a row without a valid pixel is left as it is. */
+void orc_smp(const int32_t* disp, int w, int h, int D, int32_t* out) {
+  unsigned char* valid = malloc((size_t)w);
+  for (int y = 0; y < h; ++y) {
+    const int32_t* row = disp + (size_t)y * w;
+    int any = 0;
+    for (int x = 0; x < w; ++x) {
+      int ok = 1;
+      for (int k = 1; k < D && x - k >= 0; ++k)
+        if (x - row[x] == x - k - row[x - k]) ok = 0;
+      valid[x] = (unsigned char)ok;
+      any |= ok;
+    }
+    for (int x = 0; x < w; ++x) {
+      int v = row[x];
+      if (!valid[x] && any) {
+        for (int dist = 1; dist < w; ++dist) {
+          if (x - dist >= 0 && valid[x - dist]) { v = row[x - dist]; break; }
+          if (x + dist < w && valid[x + dist]) { v = row[x + dist]; break; }
+        }
+      }
+      out[(size_t)y * w + x] = v;
+    }
+  }
+  free(valid);
+}
+
+/* The median filter of the same passage (size not given; reading: 3 x 3, window pixels
+ * outside the map take the nearest edge pixel): the 5th smallest of the 9 values. */
+void orc_median3(const int32_t* disp, int w, int h, int32_t* out) {
+  for (int y = 0; y < h; ++y)
+    for (int x = 0; x < w; ++x) {
+      int32_t v[9];
+      int n = 0;
+      for (int j = -1; j <= 1; ++j)
+        for (int i = -1; i <= 1; ++i) v[n++] = disp[(size_t)clampi(y + j, 0, h - 1) * w + clampi(x + i, 0, w - 1)];
+      for (int a = 1; a < 9; ++a)  /* insertion sort */
+        for (int b = a; b > 0 && v[b - 1] > v[b]; --b) {
+          int32_t t = v[b];
+          v[b] = v[b - 1];
+          v[b - 1] = t;
+        }
+      out[(size_t)y * w + x] = v[4];
+    }
 }

@@ -1,8 +1,10 @@
-"""Pins of the oracle's semi-global matching (Sec. III-A, Eq. 4-6), on the CPU.
+"""Pins of the oracle's semi-global matching (Sec. III-A, Eq. 4-6) and post-processing
+(Eq. 7 and the text after it), on the CPU.
 
 Each check is independent of the oracle's own recursion: an exhaustive minimum over
 every disparity sequence of a path, closed forms of special penalties, invariances of
-Eq. 4 and the symmetry of its directions."""
+Eq. 4 and the symmetry of its directions; hand-made collisions and the uniqueness
+property for the occlusion check; a library median filter."""
 import itertools
 
 import numpy as np
@@ -113,3 +115,52 @@ def test_sgm_cost_of_the_zncc_volume():
     # Eq. 1: cost 1 - rho; invalid candidates (x - d < 0) take the largest cost
     rho = np.array([[[1.0, np.nan], [-0.5, 0.25]]])
     np.testing.assert_array_equal(oracle.sgm_cost(rho), [[[0.0, 2.0], [1.5, 0.75]]])
+
+
+# ------------------------------------------------------------------ post-processing (Eq. 7)
+def test_smp_resolves_a_shared_target_column():
+    # targets x - d = 0, 1, 2, 2, 2, 3: pixels 3 and 4 match column 2 like pixel 2, which
+    # keeps it (leftmost).  Pixel 3 takes its nearest valid neighbour's disparity (pixel 2,
+    # left, distance 1); pixel 4 has no valid pixel at distance 1 on the left (pixel 3) but
+    # pixel 5 on the right (d = 2)
+    row = np.array([[0, 0, 0, 1, 2, 2]], dtype=np.int32)
+    np.testing.assert_array_equal(oracle.smp(row, D=8), [[0, 0, 0, 0, 2, 2]])
+    # a collision farther apart than the disparity range is no collision
+    far = np.array([[0, 0, 0, 3]], dtype=np.int32)  # pixel 3 matches column 0 like pixel 0
+    np.testing.assert_array_equal(oracle.smp(far, D=3), far)
+    np.testing.assert_array_equal(oracle.smp(far, D=4), [[0, 0, 0, 0]])
+
+
+def test_smp_leaves_injective_rows_and_leaves_no_collision():
+    # a constant disparity maps every pixel to its own column: nothing changes
+    const = np.full((3, 12), 4, dtype=np.int32)
+    np.testing.assert_array_equal(oracle.smp(const, D=8), const)
+    # random maps: after the check, the pixels that were valid keep their value, and no two
+    # of them within D share a target
+    rng = np.random.default_rng(21)
+    D = 6
+    disp = rng.integers(0, D, size=(4, 30)).astype(np.int32)
+    for x in range(30):
+        disp[:, x] = np.minimum(disp[:, x], x)  # a candidate needs x - d >= 0
+    out = oracle.smp(disp, D)
+    for y in range(4):
+        valid = [all(x - disp[y, x] != x - k - disp[y, x - k] for k in range(1, min(D, x + 1))) for x in range(30)]
+        for x in range(30):
+            if valid[x]:
+                assert out[y, x] == disp[y, x]
+        tv = [x - disp[y, x] for x in range(30) if valid[x]]
+        xs = [x for x in range(30) if valid[x]]
+        for i in range(len(xs)):
+            for j in range(i + 1, len(xs)):
+                if xs[j] - xs[i] < D:
+                    assert tv[i] != tv[j]
+
+
+def test_median3_matches_the_library_filter():
+    ndi = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(22)
+    d = rng.integers(0, 40, size=(9, 13)).astype(np.int32)
+    np.testing.assert_array_equal(oracle.median3(d), ndi.median_filter(d, size=3, mode="nearest"))
+    spike = np.full((5, 5), 7, dtype=np.int32)
+    spike[2, 2] = 30
+    np.testing.assert_array_equal(oracle.median3(spike), np.full((5, 5), 7, dtype=np.int32))
