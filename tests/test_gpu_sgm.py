@@ -91,3 +91,16 @@ def test_sgm_rejects_bad_arguments(ctx_for):
     for P1, P2, npaths in ((-0.1, 0.3, 4), (0.1, 0.3, 0), (0.1, 0.3, 5)):
         with pytest.raises(binding.SvError):
             ctx.coarse_match_sgm([dp], P1, P2, npaths)
+
+
+def test_sgm_edges(ctx_for):
+    # an empty batch is a no-op; the largest disparity range (128) at a wide, short map
+    ctx = ctx_for(11)
+    assert ctx.coarse_match_sgm([], 0.1, 0.5) == []
+    W, H, D = 1024, 64, 128
+    p = synth.make_pair(W, H, 400.0, 9300)
+    C = oracle_volume(p, 11, D)
+    disp, vols = ctx.coarse_match_sgm([binding.to_device(p, D)], 0.1, 0.5, 4, costs=True)
+    A = oracle.sgm(C, 0.1, 0.5, 4)
+    np.testing.assert_allclose(vols[0].cpu().numpy(), A, rtol=0, atol=1e-3)
+    check_decisions(disp[0].cpu().numpy(), A, 1e-3)
