@@ -184,18 +184,8 @@ __host__ __device__ constexpr uint32_t desc_hi(uint32_t sbo, uint32_t layout) {
 }
 __host__ __device__ constexpr uint32_t swz_layout(int rb) { return rb == 128 ? 2u : rb == 64 ? 4u : 6u; }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
-                                         uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .b64 da, db;\n .reg .pred p;\n mov.b64 da, {%1, %2};\n mov.b64 db, {%3, %4};\n"
-      " setp.ne.b32 p, %6, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n}\n" ::"r"(tmem_d),
-      "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-// Warp-wide forms: the whole warp runs the issue loop (its descriptors are warp-uniform) and
-// one lane, chosen by elect.sync, issues each instruction.
+// MMA issue and commit, warp-wide: the whole warp runs the issue loop (its descriptors are
+// warp-uniform values) and one lane, chosen by elect.sync, issues each instruction.
 __device__ __forceinline__ void mma_bf16_elect(uint32_t tmem_d, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
                                                uint32_t idesc, uint32_t acc) {
   asm volatile(
