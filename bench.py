@@ -505,11 +505,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
-        "config": {"workload": f"{B} synthetic 1242x375 stereo pairs per GPU, D=48, 9x9 ZNCC window, "
-                               f"32/64/128 encoder, 128 latent, 128/64/32 decoder ({head} form)",
-                   "global_batch": B * world, "pairs_per_gpu": B, "width": W, "height": H, "max_disp": D,
-                   "window": WIN, "l2": "flushed between steps (512 MB write outside the timed events)",
-                   "parallelism": f"replicas x{world} (pairs sharded, no collective)"},
+        "config": arm_config(B, world, head),
         "roofline": roof,
         "kernel_time_share": shares,
         "cpu_baseline": cpu,
@@ -531,6 +527,15 @@ def run_ours(args):
         r["ctx"].close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def arm_config(B, world, head):
+    """The workload both arms report (the reference arm times samples of it)."""
+    return {"workload": f"{B} synthetic 1242x375 stereo pairs per GPU, D=48, 9x9 ZNCC window, "
+                        f"32/64/128 encoder, 128 latent, 128/64/32 decoder ({head} form)",
+            "global_batch": B * world, "pairs_per_gpu": B, "width": W, "height": H, "max_disp": D,
+            "window": WIN, "l2": "flushed between steps (512 MB write outside the timed events)",
+            "parallelism": f"replicas x{world} (pairs sharded, no collective)"}
 
 
 # ------------------------------------------------------------------ reference arm: the CPU oracle
@@ -558,10 +563,10 @@ def run_reference(args):
         "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "1 synthetic 1242x375 stereo pair per step, D=48, 9x9 ZNCC window, "
-                               "32/64/128 encoder, 128 latent, 128/64/32 decoder", "global_batch": 1},
+        "config": arm_config(args.pairs, args.gpus, "bf16"),
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
-                         "sample": f"one pair per step (of the {args.steps} timed), FP64 oracle, {cores} threads"},
+                         "sample": f"one pair of the workload per step ({args.steps} timed), coarse match + "
+                                   f"refinement, FP64 oracle, {cores} threads"},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
