@@ -567,9 +567,10 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
 // ------------------------------------------------------------------ fused dec3 + final
 // The last decoder layer (nearest x2 + crop + 3x3 conv + ReLU), the final 3x3 conv to one
 // channel and the residual onto U in one kernel, so that d3 never leaves the SM.  A CTA
-// computes all four output phases of 128 input pixels of one row per tile (16 MMAs per
-// phase into four TMEM accumulators) and writes the two resulting d3 rows (BF16, 256
-// columns) into shared memory, in the swizzled K-major layout of an MMA operand.  The
+// computes all four output phases of 128 input pixels of one row per tile (one MMA per
+// staged view and K step, the phases reading the view stacked along N: 10 MMAs per K step
+// into four TMEM accumulators, see fused_view) and writes the two resulting d3 rows (BF16,
+// 256 columns) into shared memory, in the swizzled K-major layout of an MMA operand.  The
 // final conv runs on the tensor cores as well: with a d3 row as A (M = 128 columns, K = the
 // d3 channels) and one B holding all nine taps' weights (N = 32: each weight split into a
 // BF16 high part and a BF16 low part, hi + lo = w to about 2^-16 relative), one MMA pass
