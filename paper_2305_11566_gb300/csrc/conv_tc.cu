@@ -9,7 +9,8 @@
 // operand of every tap is the same staged rows seen from a start address shifted by
 // whole pixels (matrix descriptor: swizzled K-major, SBO = 8 pixels); the K steps of 16
 // channels inside a pixel row advance the start by 32 bytes.  Consecutive tiles of a CTA
-// walk down the rows of a column strip and reuse staged rows (ring of row slots).
+// walk down the rows of a column strip and reuse staged rows (ring of row slots, or of
+// one-channel-block slots where the weights leave no room for a spare row).
 //
 // Modes:
 //   TM_S2  3x3 stride-2 conv (encoder): staged rows 2i-1, 2i, 2i+1 with odd and even
@@ -22,8 +23,9 @@
 //   TM_P1  1x1 conv (latent mean head).
 //
 // Warp roles (192 threads): warps 0-3 epilogue (TMEM lanes 0-127: tcgen05.ld, bias,
-// ReLU, BF16 store), warp 4 TMEM allocation + one thread issuing tcgen05.mma (descriptors
-// advanced by constant increments, no per-MMA address arithmetic), warp 5 one thread
+// ReLU, BF16 store), warp 4 TMEM allocation + MMA issue (the whole warp runs the loop with
+// warp-uniform descriptors advanced by constant increments; one elect.sync lane issues each
+// tcgen05.mma / tcgen05.commit), warp 5 one thread
 // loading every staged row with TMA (cp.async.bulk.tensor, one box of RB / 2 channels x
 // the staged pixels per channel block and pixel set; the hardware fills the halo outside
 // the image with zeros) and signalling the row's mbarrier by transaction count.  Every wait is bounded; on
