@@ -495,9 +495,10 @@ def run_ours(args):
         sctx.profile(False)
         sms = max_over_ranks(sum(a.elapsed_time(b) for a, b in sev)) / args.steps
         vol_bytes = B * (W // 4) * (H // 4) * D * 4
+        kms = {kn: v[1] / args.steps for kn, v in sprof.items()}
         sgm = {"pairs_per_s": whole_job_value(B, world, sms), "ms_per_step": sms, "P1": SGM_P1, "P2": SGM_P2,
-               "npaths": 4, "kernel_ms_per_step": {kn: v[1] / args.steps for kn, v in sprof.items()},
-               "cost_volume_bytes": vol_bytes}
+               "npaths": 4, "kernel_ms_per_step": kms, "cost_volume_bytes": vol_bytes,
+               "roofline": sgm_path_roofline(vol_bytes, kms.get("sgm_path", float("nan")), 4, pk["hbm_gbs"], pk_kind)}
         sctx.close()
 
     value = whole_job_value(B, world, R["ms_per_step"])
@@ -527,6 +528,20 @@ def run_ours(args):
         r["ctx"].close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def sgm_path_roofline(vol_bytes, path_ms_per_call, npaths, hbm_peak_gbs, peak_kind):
+    """HBM roofline of the SGM path kernels (Eq. 4): per call the first direction reads the
+    cost volume and writes the aggregated one, every later direction reads both and writes
+    the aggregated one, so 2 + 3 (npaths - 1) volumes of algorithmic traffic."""
+    volumes = 2 + 3 * (npaths - 1)
+    per_launch_bytes = vol_bytes * volumes / npaths
+    launch_s = path_ms_per_call / npaths / 1e3
+    achieved = per_launch_bytes / launch_s / 1e9
+    return {"bound": "hbm", "kernel": "sgm_path", "achieved": achieved, "peak": hbm_peak_gbs, "unit": "GB/s",
+            "frac": achieved / hbm_peak_gbs, "per_launch_bytes": per_launch_bytes,
+            "avg_launch_ms": path_ms_per_call / npaths, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)",
+            "traffic": None}
 
 
 def arm_config(B, world, head):

@@ -37,3 +37,13 @@ def test_reference_arm_line():
 
 def test_reference_arm_other_ranks_are_silent():
     assert run_reference({"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_sgm_path_roofline_arithmetic():
+    # 4 directions: 2 + 3 * 3 = 11 volume passes over 4 launches
+    r = bench.sgm_path_roofline(vol_bytes=1e9, path_ms_per_call=4.0, npaths=4, hbm_peak_gbs=5000.0,
+                                peak_kind="measured")
+    assert r["bound"] == "hbm" and r["kernel"] == "sgm_path"
+    assert abs(r["per_launch_bytes"] - 11e9 / 4) < 1
+    assert abs(r["avg_launch_ms"] - 1.0) < 1e-12
+    assert abs(r["achieved"] - 2750.0) < 1e-6 and abs(r["frac"] - 0.55) < 1e-12
