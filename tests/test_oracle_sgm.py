@@ -164,3 +164,20 @@ def test_median3_matches_the_library_filter():
     spike = np.full((5, 5), 7, dtype=np.int32)
     spike[2, 2] = 30
     np.testing.assert_array_equal(oracle.median3(spike), np.full((5, 5), 7, dtype=np.int32))
+
+
+def test_sgm_degenerate_shapes():
+    rng = np.random.default_rng(23)
+    # one disparity: no neighbour terms and the previous minimum is the previous cost, so
+    # every path returns the cost itself
+    C = rng.random((4, 6, 1)) * 2.0
+    for d in range(4):
+        np.testing.assert_allclose(oracle.sgm_path(C, 0.3, 0.9, d), C, atol=1e-12)
+    np.testing.assert_array_equal(oracle.sgm_wta(oracle.sgm(C, 0.3, 0.9)), np.zeros((4, 6), dtype=np.int32))
+    # one column / one row: the paths across it have a single pixel and keep the cost
+    col = rng.random((5, 1, 4)) * 2.0
+    np.testing.assert_allclose(oracle.sgm_path(col, 0.3, 0.9, 0), col, atol=1e-12)
+    np.testing.assert_allclose(oracle.sgm_path(col, 0.3, 0.9, 1), col, atol=1e-12)
+    row = rng.random((1, 5, 4)) * 2.0
+    np.testing.assert_allclose(oracle.sgm_path(row, 0.3, 0.9, 2), row, atol=1e-12)
+    np.testing.assert_allclose(oracle.sgm_path(row, 0.3, 0.9, 3), row, atol=1e-12)
