@@ -288,19 +288,21 @@ SV_API sv_status sv_debug_activation(sv_ctx* ctx, int which, int pair, void* dst
 /* sv_coarse_match without any device allocation, and without a context.
  *
  * For callers that cannot allocate device memory at the moment they need a coarse map:
- * code recording a CUDA graph in global capture mode (cudaMalloc is refused while the
- * capture is open), real-time loops that must not block on the allocator (cudaMalloc can
- * synchronise the device), and plugins whose host owns the whole device memory budget.
- * The paper has no counterpart: this is a deployment entry point.
+ * real-time loops that must not block on the allocator (cudaMalloc can synchronise the
+ * device), and plugins whose host owns the whole device memory budget and hands the
+ * library only its inputs and outputs.  The paper has no counterpart: this is a
+ * deployment entry point.
  *
- * Same inputs, outputs and results as sv_coarse_match; `window` is the ZNCC window side
- * (odd, 3..15).  The call's work tables are kept in a fixed array compiled into the
- * library (540,672 bytes, held on every GPU that loads the library until the process
- * exits): at most 256 pairs and 32768 jobs per call, where a pair of W x H needs
+ * Same inputs, outputs, results and status codes as sv_coarse_match; `window` is the ZNCC
+ * window side (odd, 3..15).  The call's work tables are kept in a fixed array compiled
+ * into the library (540,672 bytes, held on every GPU that loads the library until the
+ * process exits): at most 256 pairs and 32768 jobs per call, where a pair of W x H needs
  * ceil((H/4) / 8) * ceil((W/4) / (8 * TX)) jobs (TX = 32, 24, 16, 12 for D up to 32, 64,
  * 96, 128).  Larger calls return SV_ERR_UNSUPPORTED and launch nothing; other invalid
- * arguments return SV_ERR_INVALID_ARG.  The first call on a device looks up the array's
- * device address with that device current: make it before any stream capture.  All calls
+ * arguments return SV_ERR_INVALID_ARG.  The tables are uploaded on `stream` from host
+ * memory that lives only for the duration of the call.  The first call on a device looks
+ * up the array's device address with that device current and caches it for the life of
+ * the process: do not call this entry point on a device after cudaDeviceReset.  All calls
  * share the one array and each overwrites it: calls whose work can overlap on the GPU
  * (other streams, no ordering between them) race and must be ordered by the caller.  It
  * calls no cudaMalloc, cudaFree or allocating library routine. */

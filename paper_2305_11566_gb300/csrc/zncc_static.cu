@@ -1,16 +1,16 @@
 // zncc_static.cu -- a coarse-matching entry point that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc when they need a disparity map: a stream that is
-// being captured into a CUDA graph in global capture mode (cudaMalloc is refused there),
-// a real-time loop that must not block on the allocator (cudaMalloc may synchronise the
-// device and has no latency bound), or a plugin whose host owns every byte of device
-// memory.  sv_coarse_match keeps its per-call work tables in memory its context
-// allocated; this variant keeps them in a fixed array that is part of the library image
-// instead, so a call needs nothing but the caller's inputs and outputs.
+// Some callers cannot call cudaMalloc when they need a disparity map: a real-time loop
+// that must not block on the allocator (cudaMalloc may synchronise the device and has no
+// latency bound), or a plugin whose host owns every byte of device memory and hands the
+// library only its inputs and outputs.  sv_coarse_match keeps its per-call work tables in
+// memory its context allocated; this variant keeps them in a fixed array that is part of
+// the library image instead, so a call needs nothing but the caller's inputs and outputs.
+// The tables are uploaded from host memory that lives only for the duration of the call.
 #include <mutex>
 #include <vector>
 
-#include "sv_internal.cuh"
+#include "sv_ctx.cuh"
 
 namespace {
 
@@ -28,8 +28,11 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_zncc_scratch on the current device (looked up once per device).
-// In host code the symbol's name is only a host-side handle, never a device pointer.
+// Device address of g_zncc_scratch on the current device, looked up once per device
+// ordinal and cached.  In host code the symbol's name is only a host-side handle, never a
+// device pointer.  The cache assumes the device's primary context lives as long as the
+// process: after cudaDeviceReset the cached address is stale, so a process that resets a
+// device must not call this entry point on it again.
 cudaError_t scratch_address(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -46,13 +49,15 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
-bool pair_ok(const sv_pair& p, int k) {
-  if (!p.left || !p.right) return false;
-  if (((uintptr_t)p.left & 15) || ((uintptr_t)p.right & 15)) return false;
-  if (p.pitch % 16 || p.pitch < p.width) return false;
-  if (p.width < 4 * k || p.height < 4 * k || p.width > 16384 || p.height > 16384) return false;
-  if (p.max_disp < 1 || p.max_disp > 128 || p.max_disp > p.width / 4) return false;
-  return true;
+// The validation of sv_coarse_match, with the same status codes.
+sv_status pair_check(const sv_pair& p, int k) {
+  if (!p.left || !p.right) return SV_ERR_INVALID_ARG;
+  if (((uintptr_t)p.left & 15) || ((uintptr_t)p.right & 15)) return SV_ERR_INVALID_ARG;
+  if (p.pitch % 16 || p.pitch < p.width) return SV_ERR_INVALID_ARG;
+  if (p.width < 4 * k || p.height < 4 * k) return SV_ERR_INVALID_ARG;
+  if (p.width > sv::kMaxSide || p.height > sv::kMaxSide) return SV_ERR_UNSUPPORTED;
+  if (p.max_disp < 1 || p.max_disp > sv::kMaxDisp || p.max_disp > p.width / 4) return SV_ERR_INVALID_ARG;
+  return SV_OK;
 }
 
 }  // namespace
@@ -65,7 +70,9 @@ extern "C" sv_status sv_coarse_match_static(const sv_pair* pairs, int n_pairs, i
   if (n_pairs > kStaticMaxPairs) return SV_ERR_UNSUPPORTED;
   int maxD = 1;
   for (int i = 0; i < n_pairs; ++i) {
-    if (!pair_ok(pairs[i], window) || !disp_out[i]) return SV_ERR_INVALID_ARG;
+    const sv_status ps = pair_check(pairs[i], window);
+    if (ps != SV_OK) return ps;
+    if (!disp_out[i]) return SV_ERR_INVALID_ARG;
     if (pairs[i].max_disp > maxD) maxD = pairs[i].max_disp;
   }
   const int gx = sv::kZnccWarps * sv::zncc_tx(sv::zncc_kd(maxD));

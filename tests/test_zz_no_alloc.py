@@ -1,8 +1,8 @@
 """The allocation-free coarse matcher, sv_coarse_match_static.
 
 It exists for callers that cannot allocate device memory when they need a coarse map:
-code recording a CUDA graph in global capture mode, real-time loops that must not wait
-on the allocator, plugins whose host owns all device memory.  Its work tables live in a
+real-time loops that must not wait on the allocator, plugins whose host owns all device
+memory.  Its work tables live in a
 fixed array inside the library instead of memory a context allocates.
 
 Checked here through the C ABI: two calls in a row (different batches, so the shared
@@ -74,6 +74,13 @@ def test_static_rejects_oversize_calls(svlib):
     assert s == binding.SV_ERR_UNSUPPORTED
     torch.cuda.synchronize()
     assert bool((disp[0] == -1).all())
+    # a side above the library's limit: the same status as sv_coarse_match
+    wide = binding.SvPair.from_buffer_copy(dp.sv())
+    wide.width = 16400
+    wide.pitch = 16400
+    arr = (binding.SvPair * 1)(wide)
+    assert svlib.sv_coarse_match_static(arr, 1, 7, binding._ptrs([disp[0]]), None, None, None) == \
+        binding.SV_ERR_UNSUPPORTED
     assert svlib.sv_coarse_match_static(None, 0, 7, None, None, None, None) == binding.SV_OK
     arr = (binding.SvPair * 1)(dp.sv())
     assert svlib.sv_coarse_match_static(arr, 1, 8, binding._ptrs([disp[0]]), None, None, None) == \
