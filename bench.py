@@ -45,8 +45,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="auto", choices=["auto", "fp32", "bf16", "both"])
     ap.add_argument("--pairs", type=int, default=64, help="pairs per step per GPU")
-    ap.add_argument("--distinct", type=int, default=16, help="distinct synthetic pairs (cycled)")
-    ap.add_argument("--cpu-sample", type=int, default=2, help="pairs timed on the CPU oracle")
+    ap.add_argument("--distinct", type=int, default=0,
+                    help="distinct synthetic pairs per GPU, cycled over the batch (0 = one per pair)")
+    ap.add_argument("--cpu-sample", type=int, default=8,
+                    help="pairs computed by the CPU oracle (timed baseline and accuracy of every form)")
+    ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (0 = all host cores)")
+    ap.add_argument("--no-uneven", action="store_true",
+                    help="skip the uneven-batch leg (64 pairs of widths 320..1242, BF16, tuned, graph-replayed)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
@@ -167,13 +172,24 @@ def levels(h, w):
     return out
 
 
-def work_per_pair(shape):
-    """{kernel name: (unit count per pair, unit)}: FLOPs for convolutions, bytes for ZNCC."""
+def upfix_pixels(Ho, Wo):
+    """Border pixels of a cropped nearest-x2 + 3x3 layer recomputed by the border-fix kernel."""
+    return (Wo if Ho & 1 else 0) + ((Ho - (Ho & 1)) if Wo & 1 else 0)
+
+
+def pair_work(shape, W, H):
+    """Algorithmic work of one W x H pair per profiled kernel: {name: (units, bound)}.
+
+    bound "hbm": bytes that must cross HBM (inputs read once, outputs written once);
+    "tensor" / "alu": multiply-adds x 2 of the method, counted on the tensor-core
+    form's own arithmetic (decoder: 4 output phases of 2x2 taps on the low-resolution
+    grid, i.e. 4 taps per output pixel instead of 9)."""
     (H0, W0), (H1, W1), (H2, W2), (H3, W3) = levels(H, W)
+    w, h = W // 4, H // 4
     c1, c2, c3 = shape.enc
     d1, d2, d3 = shape.dec
     lat = shape.latent
-    f = {
+    dense = {  # the plain form's direct convolutions (9 taps everywhere)
         "enc1": 2 * H1 * W1 * c1 * 9 * 2,
         "enc2": 2 * H2 * W2 * c2 * 9 * c1,
         "enc3": 2 * H3 * W3 * c3 * 9 * c2,
@@ -183,17 +199,82 @@ def work_per_pair(shape):
         "dec3": 2 * H0 * W0 * d3 * 9 * d2,
         "final": 2 * H0 * W0 * 9 * d3,
     }
-    # tensor-core decoder: 4 output phases x 2x2 taps on the low-resolution grid
-    f["tc_dec1"] = 2 * (2 * H3) * (2 * W3) * d1 * 4 * lat
-    f["tc_dec2"] = 2 * (2 * H2) * (2 * W2) * d2 * 4 * d1
-    f["tc_dec3"] = 2 * (2 * H1) * (2 * W1) * d3 * 4 * d2
-    f["tc_enc2"], f["tc_enc3"], f["tc_latent"] = f["enc2"], f["enc3"], f["latent"]
-    f["edge_enc1"], f["edge_final"] = f["enc1"], f["final"]
-    # fused last decoder layer + final conv: its tensor-core work (the final conv's FP32
-    # FLOPs run on the CUDA cores beside it)
-    f["tc_dec3_final"] = f["tc_dec3"]
-    zbytes = 2 * W * H + 2 * (W // 4) * (H // 4)
-    return f, zbytes
+    out = {k: (v, "alu") for k, v in dense.items()}
+    out["zncc_wta"] = (2 * W * H + 2 * w * h, "hbm")
+    out["edge_enc1"] = (W * H + 2 * w * h + 2 * H1 * W1 * c1, "hbm")
+    out["tc_enc2"] = (dense["enc2"], "tensor")
+    out["tc_enc3"] = (dense["enc3"], "tensor")
+    out["tc_latent"] = (dense["latent"], "tensor")
+    out["tc_dec1"] = (2 * H2 * W2 * d1 * 4 * lat, "tensor")
+    out["tc_dec2"] = (2 * H1 * W1 * d2 * 4 * d1, "tensor")
+    out["tc_dec3"] = (2 * H0 * W0 * d3 * 4 * d2, "tensor")
+    out["tc_dec3_final"] = (out["tc_dec3"][0] + dense["final"], "tensor")
+    out["edge_up2fix"] = (2 * 6 * (upfix_pixels(H2, W2) * d1 * lat + upfix_pixels(H1, W1) * d2 * d1), "alu")
+    out["edge_final"] = (2 * H0 * W0 * d3 + 2 * w * h + 4 * H0 * W0, "hbm")
+    return out
+
+
+def work_per_pair(shape):
+    """{kernel: FLOPs per 1242x375 pair} and the ZNCC kernel's algorithmic bytes per pair."""
+    f = {k: v for k, (v, _) in pair_work(shape, W, H).items()}
+    return f, f["zncc_wta"]
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    """FP32 FMA lanes x 2 flop x clock: 152 SMs x 128 lanes x 2 x f."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measure_sgemm_tflops():
+    """cuBLAS FP32 SGEMM (TF32 off) 8192^3, best of 5, as a measured CUDA-core FP32 figure."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        n = 8192
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        c = torch.empty(n, n, device="cuda")
+        for _ in range(2):
+            torch.matmul(a, b, out=c)
+        best = float("inf")
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b, c
+        return 2 * n ** 3 / (best / 1e3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def kernel_rooflines(prof, steps, shape, sizes, pk, pk_kind, sustained, alu_peak):
+    """Roofline of every profiled kernel: algorithmic units of one step (summed over the
+    step's pairs) / the kernel's measured time per step, against the matching peak."""
+    work = {}
+    for (Wp, Hp) in sizes:
+        for k, (u, b) in pair_work(shape, Wp, Hp).items():
+            work[k] = (work.get(k, (0, b))[0] + u, b)
+    table = {}
+    for name, (nl, tot_ms) in sorted(prof.items()):
+        if name not in work or tot_ms <= 0:
+            continue
+        units, bound = work[name]
+        ms = tot_ms / steps
+        if bound == "hbm":
+            ach, peak, unit, src = units / (ms / 1e3) / 1e9, pk["hbm_gbs"], "GB/s", f"{pk_kind} hbm_gbs"
+        elif bound == "tensor":
+            key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+            ach, peak, unit, src = units / (ms / 1e3) / 1e12, pk[key], "TFLOP/s", f"{pk_kind} {key}"
+        else:
+            ach, peak, unit, src = units / (ms / 1e3) / 1e12, alu_peak, "TFLOP/s", "derived: " + FP32_PEAK_TFLOPS_NOTE
+        table[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                       "units_per_step": units, "ms_per_step": ms, "launches_per_step": nl / steps,
+                       "peak_source": src}
+    return table
 
 
 # ------------------------------------------------------------------ ranks (host side)
@@ -225,6 +306,109 @@ def whole_job_value(pairs_per_rank: int, world: int, ms_per_step: float) -> floa
 
 
 # ------------------------------------------------------------------ our implementation
+def time_pipeline(ctx, dps, outs, steps, warmup, st, flush, dev, barrier):
+    """Warm up, then time `steps` sv_pipeline calls (CUDA events on the launching stream,
+    the L2 flushed before each, outside the events), with per-kernel profiling and clock
+    samples.  Returns the per-step times and what was recorded."""
+    import torch
+    with torch.cuda.stream(st):
+        for _ in range(warmup):
+            ctx.pipeline(dps, out=outs)
+    torch.cuda.synchronize()
+    ctx.synchronize(st)
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    l0 = ctx.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    clk = ClockSampler(gpu_id_for(dev))
+    barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    t_wall0 = time.perf_counter()
+    with torch.cuda.stream(st):
+        for k in range(steps):
+            flush.fill_(k & 0xFF)  # L2 flush between steps, outside the events
+            ev[k][0].record(st)
+            ctx.pipeline(dps, out=outs)
+            ev[k][1].record(st)
+            ctx.profile_read(reset=False)  # read this step's per-kernel events (graph replays reuse them)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    rows = clk.stop()
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    launches = ctx.launch_count() - l0
+    clocks = ClockSampler.summarise(rows)
+    if clocks["samples"] < 3:  # short timed region: sample the same step for ~1.5 s
+        clk2 = ClockSampler(gpu_id_for(dev))
+        clk2.start()
+        t = time.perf_counter()
+        while time.perf_counter() - t < 1.5:
+            with torch.cuda.stream(st):
+                ctx.pipeline(dps, out=outs)
+            torch.cuda.synchronize()
+        c2 = ClockSampler.summarise(clk2.stop())
+        c2["note"] = "timed region shorter than the sampling period: sampled while repeating the step"
+        clocks = c2
+    ctx.synchronize(st)
+    return dict(step_ms=step_ms, prof=prof, launches=launches, clocks=clocks, wall_s=wall)
+
+
+def dominant_roofline(table, measured_traffic_bytes=None):
+    """The roofline entry of the kernel with the largest time share."""
+    name = max(table, key=lambda k: table[k]["ms_per_step"])
+    r = dict(table[name])
+    r["kernel"] = name
+    r["traffic"] = measured_traffic_bytes
+    return r
+
+
+def accuracy_report(d_gpu, d_orc, best_o, sec_o, Y_gpu, Y_orc, gt):
+    """Errors of one form against the FP64 oracle over a sample of pairs: refined disparity
+    (max / mean |dY| everywhere and outside the receptive field of WTA differences), EPE
+    change against the ground truth, and the fraction of WTA disparities that differ."""
+    import numpy as np
+    errs, kept, flips, near, npx, epe_g, epe_o = [], [], 0, 0, 0, [], []
+    for dg, do, bo, so, Yg, Yo, g in zip(d_gpu, d_orc, best_o, sec_o, Y_gpu, Y_orc, gt):
+        Hh, Ww = Yo.shape
+        diff = dg != do
+        flips += int(diff.sum())
+        near += int((diff & ((bo - so) > 1e-4)).sum())
+        npx += diff.size
+        m = np.zeros_like(diff)
+        for y, x in zip(*np.nonzero(diff)):
+            m[max(0, y - 16):y + 17, max(0, x - 16):x + 17] = True
+        keep = ~np.repeat(np.repeat(m, 4, 0), 4, 1)
+        keep = np.pad(keep, ((0, Hh - keep.shape[0]), (0, Ww - keep.shape[1])), mode="edge")
+        e = np.abs(Yg.astype(np.float64) - Yo)
+        errs.append(e.ravel())
+        kept.append(e[keep].ravel())
+        epe_g.append(np.abs(Yg - g).mean())
+        epe_o.append(np.abs(Yo - g).mean())
+    e = np.concatenate(errs)
+    k = np.concatenate(kept)
+    return {"max_abs_dy_px": float(e.max()), "mean_abs_dy_px": float(e.mean()),
+            "max_abs_dy_px_outside_wta_flips": float(k.max()), "mean_abs_dy_px_outside_wta_flips": float(k.mean()),
+            "epe_gpu_vs_gt_px": float(np.mean(epe_g)), "epe_oracle_vs_gt_px": float(np.mean(epe_o)),
+            "delta_epe_px": float(np.mean(epe_g) - np.mean(epe_o)),
+            "wta_flips": flips, "wta_flip_fraction": flips / npx, "wta_flips_off_near_ties": near,
+            "pairs": len(Y_orc)}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            low = line.lower()
+            if low.startswith("model name") or low.startswith("cpu part"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -243,11 +427,14 @@ def run_ours(args):
     shape = synth.NET_WIDE
     params = synth.he_normal_weights(shape, 7)
     B = args.pairs
-    distinct = [synth.make_pair(W, H, DMAX, sd) for sd in rank_pair_seeds(rank, B, args.distinct)]
+    n_distinct = B if args.distinct <= 0 else min(args.distinct, B)
+    distinct = [synth.make_pair(W, H, DMAX, sd) for sd in rank_pair_seeds(rank, B, n_distinct)]
     pairs = [distinct[i % len(distinct)] for i in range(B)]
     dps_distinct = [binding.to_device(p, D) for p in distinct]
     dps = [dps_distinct[i % len(distinct)] for i in range(B)]
     pk, pk_kind = peaks()
+    alu_peak = fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+    sgemm = measure_sgemm_tflops()
 
     barrier, max_over_ranks = rank_reducers(world, dist, "cuda")
 
@@ -277,97 +464,29 @@ def run_ours(args):
             with torch.cuda.stream(st):
                 ctx.pipeline(dps[:1], out=outs[:1])
             torch.cuda.synchronize()
-        except binding.SvError as e:
+        except binding.SvError:
             if form == "bf16":
                 ctx.close()
                 continue
             raise
         if form == "bf16" and not args.no_tune:
             tuning = ctx.autotune(dps, stream=st)
-        with torch.cuda.stream(st):
-            for _ in range(args.warmup):
-                ctx.pipeline(dps, out=outs)
-        torch.cuda.synchronize()
-        ctx.synchronize(st)
-        ctx.profile(True)
-        ctx.profile_read(reset=True)
-        l0 = ctx.launch_count()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        clk = ClockSampler(gpu_id_for(dev))
-        barrier()
-        torch.cuda.synchronize()
-        clk.start()
-        t_wall0 = time.perf_counter()
-        with torch.cuda.stream(st):
-            for k in range(args.steps):
-                flush.fill_(k & 0xFF)  # L2 flush between steps, outside the events
-                ev[k][0].record(st)
-                ctx.pipeline(dps, out=outs)
-                ev[k][1].record(st)
-                ctx.profile_read(reset=False)  # read this step's per-kernel events (graph replays reuse them)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t_wall0
-        rows = clk.stop()
-        barrier()
-        step_ms = [a.elapsed_time(b) for a, b in ev]
-        prof = ctx.profile_read(reset=True)
-        ctx.profile(False)
-        launches = ctx.launch_count() - l0
-        clocks = ClockSampler.summarise(rows)
-        if clocks["samples"] < 3:  # short timed region: sample the same step for ~1.5 s
-            clk2 = ClockSampler(gpu_id_for(dev))
-            clk2.start()
-            t = time.perf_counter()
-            while time.perf_counter() - t < 1.5:
-                with torch.cuda.stream(st):
-                    ctx.pipeline(dps, out=outs)
-                torch.cuda.synchronize()
-            c2 = ClockSampler.summarise(clk2.stop())
-            c2["note"] = "timed region shorter than the sampling period: sampled while repeating the step"
-            clocks = c2
-        total_ms = max_over_ranks(sum(step_ms))
-        ms_per_step = total_ms / args.steps
-        ctx.synchronize(st)
-        results[form] = dict(ctx=ctx, outs=outs, ms_per_step=ms_per_step, prof=prof, launches=launches,
-                             clocks=clocks, wall_s=wall, step_ms=step_ms)
+        t = time_pipeline(ctx, dps, outs, args.steps, args.warmup, st, flush, dev, barrier)
+        total_ms = max_over_ranks(sum(t["step_ms"]))
+        t.update(ctx=ctx, outs=outs, ms_per_step=total_ms / args.steps)
+        results[form] = t
 
-    # -------------------------------------------------------------- roofline of the dominant kernel
+    # -------------------------------------------------------------- rooflines of every kernel
     head = "bf16" if "bf16" in results else "fp32"
     R = results[head]
-    flops, zbytes = work_per_pair(shape)
-    prof = R["prof"]
-    top = max(prof.items(), key=lambda kv: kv[1][1])
-    name, (nl, tot_ms) = top
-    avg_s = tot_ms / nl / 1e3
-    if name == "zncc_wta":
-        per_launch = zbytes * B
-        achieved = per_launch / avg_s / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s"}
-    elif name in ("edge_final", "edge_enc1", "edge_up2fix"):
-        # CUDA-core layers of the tensor-core form, all pairs in one launch
-        per_launch = flops.get(name, 0) * B
-        achieved = per_launch / avg_s / 1e12
-        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s"}
-    elif name.startswith("tc_"):
-        pairs_per_launch = B
-        per_launch = flops[name] * pairs_per_launch
-        achieved = per_launch / avg_s / 1e12
-        sustained = R["ms_per_step"] * args.steps > 1000
-        roof = {"bound": "tensor", "achieved": achieved,
-                "peak": pk["bf16_tflops_sustained" if sustained else "bf16_tflops"], "unit": "TFLOP/s"}
-    else:
-        per_launch = flops[name]  # the plain form launches one pair at a time
-        achieved = per_launch / avg_s / 1e12
-        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = name
-    roof["per_launch_units"] = per_launch
-    roof["avg_launch_ms"] = avg_s * 1e3
-    roof["peak_source"] = ("derived: " + FP32_PEAK_TFLOPS_NOTE) if roof["bound"] == "alu" else f"{pk_kind} (MEASURED_PEAKS.json)"
-    roof["traffic"] = measured_traffic(name, B)
-    shares = {k: round(v[1] / sum(x[1] for x in prof.values()), 4) for k, v in sorted(prof.items())}
+    sizes = [(W, H)] * B
+    tables = {}
+    for form, r in results.items():
+        sustained = r["ms_per_step"] * args.steps > 1000
+        tables[form] = kernel_rooflines(r["prof"], args.steps, shape, sizes, pk, pk_kind, sustained, alu_peak)
+    roof = dominant_roofline(tables[head])
+    roof["traffic"] = measured_traffic(roof["kernel"], B)
+    shares = {k: round(v[1] / sum(x[1] for x in R["prof"].values()), 4) for k, v in sorted(R["prof"].items())}
 
     # -------------------------------------------------------------- e2e through the host-buffer API
     e2e = None
@@ -393,6 +512,29 @@ def run_ours(args):
                "d2h_bytes_per_step": int(sum(x.numel() * 4 for x in ho)),
                "api": "sv_pipeline_host (pinned host images in, host disparity maps out)"}
 
+    # -------------------------------------------------------------- the uneven batch (64 pairs, widths 320..1242)
+    uneven = None
+    if not args.no_uneven and "bf16" in results:
+        ub = synth.batch_uneven(B, seed=2000 + 1000 * rank)
+        udps = [binding.to_device(p, Dp) for p, Dp in ub]
+        uctx = binding.Context(shape, WIN, "bf16", dev)
+        uctx.set_weights(params)
+        uouts = [torch.empty((p.height, p.width), dtype=torch.float32, device="cuda") for p, _ in ub]
+        utune = uctx.autotune(udps, stream=st) if not args.no_tune else None
+        ut = time_pipeline(uctx, udps, uouts, args.steps, args.warmup, st, flush, dev, barrier)
+        ums = max_over_ranks(sum(ut["step_ms"])) / args.steps
+        usizes = [(p.width, p.height) for p, _ in ub]
+        utable = kernel_rooflines(ut["prof"], args.steps, shape, usizes, pk, pk_kind, ums * args.steps > 1000, alu_peak)
+        widths = [p.width for p, _ in ub]
+        uneven = {"workload": f"{B} synthetic pairs per GPU, widths drawn from {{320, 640, 960, 1242}} "
+                              f"({', '.join(f'{w}: {widths.count(w)}' for w in (320, 640, 960, 1242))}), "
+                              "H = round(0.302 W), D = ceil(W / 26), 9x9 window, 32/64/128 net, BF16, "
+                              "autotuned, CUDA-graph replay",
+                  "pairs_per_s": whole_job_value(B, world, ums), "ms_per_step": ums,
+                  "launches_per_step": ut["launches"] / args.steps, "clocks": ut["clocks"],
+                  "roofline": dominant_roofline(utable), "rooflines": utable, "tuning": utune}
+        uctx.close()
+
     # -------------------------------------------------------------- CPU oracle baseline + accuracy
     cpu = None
     accuracy = {}
@@ -400,30 +542,24 @@ def run_ours(args):
         import oracle
         oracle.build()
         n = max(1, min(args.cpu_sample, len(distinct)))
-        cores = os.cpu_count() or 1
+        cores = args.cpu_threads if args.cpu_threads > 0 else (os.cpu_count() or 1)
         oracle.set_threads(cores)
         t = time.perf_counter()
         ref = []
         for i in range(n):
             p = distinct[i]
-            Yo, do, bo, so = oracle.pipeline(shape, params, p.left, p.right, WIN, D)
-            ref.append((Yo, do, bo, so))
+            ref.append(oracle.pipeline(shape, params, p.left, p.right, WIN, D))
         el = time.perf_counter() - t
         cpu = {"value": n / el, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "cpu_model": cpu_model(), "nproc": os.cpu_count(),
                "sample": f"{n} of the {B} pairs (1242x375, D=48): coarse match + refinement, FP64, "
                          f"{cores} OpenMP threads, {el:.1f} s"}
         for form, r in results.items():
-            errs, flips, epe_g, epe_o = [], 0, [], []
-            for i in range(n):
-                Yg = r["outs"][i].cpu().numpy().astype(np.float64)
-                Yo, do, bo, so = ref[i]
-                errs.append(np.abs(Yg - Yo))
-                epe_g.append(np.abs(Yg - distinct[i].gt).mean())
-                epe_o.append(np.abs(Yo - distinct[i].gt).mean())
-            e = np.concatenate([x.ravel() for x in errs])
-            accuracy[form] = {"mean_abs_dy_px": float(e.mean()), "max_abs_dy_px": float(e.max()),
-                              "epe_gpu_vs_gt_px": float(np.mean(epe_g)), "epe_oracle_vs_gt_px": float(np.mean(epe_o)),
-                              "delta_epe_px": float(np.mean(epe_g) - np.mean(epe_o)), "pairs": n}
+            dg = [d.cpu().numpy() for d in r["ctx"].coarse_match(dps_distinct[:n], stream=st)]
+            torch.cuda.synchronize()
+            accuracy[form] = accuracy_report(dg, [x[1] for x in ref], [x[2] for x in ref], [x[3] for x in ref],
+                                             [r["outs"][i].cpu().numpy() for i in range(n)], [x[0] for x in ref],
+                                             [distinct[i].gt for i in range(n)])
 
     # -------------------------------------------------------------- training step (differentiation form)
     train = None
@@ -436,7 +572,6 @@ def run_ours(args):
         tp = [distinct[i % len(distinct)] for i in range(nt)]
         tdp = [dps_distinct[i % len(distinct)] for i in range(nt)]
         H3, W3 = binding.latent_hw(H, W)
-        tco = [torch.from_numpy(np.full((H // 4, W // 4), 10.0, np.float32)).cuda() for _ in range(nt)]
         with torch.cuda.stream(st):
             coarse_i = tctx.coarse_match(tdp)
         st.synchronize()
@@ -506,18 +641,25 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
-        "config": arm_config(B, world, head),
+        "config": arm_config(B, world, head, n_distinct),
         "roofline": roof,
+        "rooflines": tables[head],
         "kernel_time_share": shares,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(R["launches"]),
         "clocks": R["clocks"],
+        "fp32_peaks": {"derived_tflops": alu_peak, "derived_from": FP32_PEAK_TFLOPS_NOTE,
+                       "measured_sgemm_tflops": sgemm,
+                       "measured_how": "cuBLAS SGEMM 8192^3, TF32 off, best of 5, CUDA events"},
         "forms": {f: {"pairs_per_s": B * world / (r["ms_per_step"] / 1e3), "ms_per_step": r["ms_per_step"],
-                      "launches_per_step": r["launches"] / args.steps, **accuracy.get(f, {})}
+                      "launches_per_step": r["launches"] / args.steps, **accuracy.get(f, {}),
+                      **({"rooflines": tables[f]} if f != head else {})}
                   for f, r in results.items()},
         "delta_epe_px": accuracy.get(head, {}).get("delta_epe_px"),
+        "wta_flip_fraction": accuracy.get(head, {}).get("wta_flip_fraction"),
         "tuning": tuning,
+        "uneven_batch": uneven,
         "train_step": train,
     }
     if sgm is not None:
@@ -544,10 +686,12 @@ def sgm_path_roofline(vol_bytes, path_ms_per_call, npaths, hbm_peak_gbs, peak_ki
             "traffic": None}
 
 
-def arm_config(B, world, head):
+def arm_config(B, world, head, distinct=None):
     """The workload both arms report (the reference arm times samples of it)."""
+    distinct = B if distinct is None else distinct
     return {"workload": f"{B} synthetic 1242x375 stereo pairs per GPU, D=48, 9x9 ZNCC window, "
                         f"32/64/128 encoder, 128 latent, 128/64/32 decoder ({head} form)",
+            "distinct_pairs_per_gpu": distinct,
             "global_batch": B * world, "pairs_per_gpu": B, "width": W, "height": H, "max_disp": D,
             "window": WIN, "l2": "flushed between steps (512 MB write outside the timed events)",
             "parallelism": f"replicas x{world} (pairs sharded, no collective)"}
