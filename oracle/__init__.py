@@ -24,6 +24,12 @@ Parity status per function (what pins each one, in tests/test_oracle_*.py):
   sgm_wta          ties to the lowest d; equals the plain argmin of C when P1 = P2 = 0
   smp              hand-made collisions; injective rows unchanged; no two valid pixels share a
                    target afterwards
+  census_volume    hand-made 3 x 3 codes; invariance under increasing intensity maps; zero
+                   cost of an image against itself and of a constant shift at its disparity;
+                   the mirror identity (both images flipped, roles swapped)
+  dt_aggregate     uniform guide: scipy.signal.lfilter (first-order recursive filter) along
+                   each axis; constant slices unchanged; a hard edge (sigma_r -> 0) separates
+                   the two sides exactly; linearity in the cost; bounds min C <= out <= max C
   median3          scipy.ndimage.median_filter (3 x 3, nearest) as an independent routine
   end-to-end disparity error vs synthetic ground truth: parity unpinned
   (random weights; the paper's trained weights and KITTI are absent).
@@ -70,6 +76,8 @@ def lib():
         L.orc_sgm_wta.argtypes = [P, c_int, c_int, c_int, P]
         L.orc_smp.argtypes = [P, c_int, c_int, c_int, P]
         L.orc_median3.argtypes = [P, c_int, c_int, P]
+        L.orc_census_volume.argtypes = [P, P, c_int, c_int, c_int, c_int, P]
+        L.orc_dt_aggregate.argtypes = [P, c_int, c_int, c_int, P, c_double, c_double, c_int, P]
         L.orc_upsample4_backward.argtypes = [P, c_int, c_int, c_int, c_int, P]
         L.orc_conv2d.argtypes = [P, c_int, c_int, c_int, P, P, c_int, c_int, c_int, c_int, c_int, c_int, c_int,
                                  c_int, P]
@@ -204,6 +212,39 @@ def median3(disp: np.ndarray) -> np.ndarray:
     out = np.zeros_like(d)
     lib().orc_median3(_p(d), w, h, _p(out))
     return out
+
+
+# ---------------------------------------------------------------- census cost, DT aggregation
+def census_volume(SL, SR, kc: int, D: int) -> np.ndarray:
+    """Census cost [h, w, D] (FP64, integer valued) of the quarter-size box sums: Hamming
+    distance of the kc x kc census codes of (x, y) and (x - d, y); kc^2 - 1 where x - d < 0."""
+    SL = np.ascontiguousarray(SL, dtype=np.int32)
+    SR = np.ascontiguousarray(SR, dtype=np.int32)
+    h, w = SL.shape
+    out = np.zeros((h, w, D), dtype=np.float64)
+    lib().orc_census_volume(_p(SL), _p(SR), w, h, int(kc), int(D), _p(out))
+    return out
+
+
+def dt_aggregate(C: np.ndarray, guide: np.ndarray, sigma_s: float, sigma_r: float, iters: int) -> np.ndarray:
+    """Domain-transform aggregation of a cost volume [h, w, D] guided by the left box sums
+    [h, w] (intensity = sum / 16): recursive edge-aware filter along rows then columns,
+    both ways, `iters` times."""
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    g = np.ascontiguousarray(guide, dtype=np.int32)
+    h, w, D = C.shape
+    out = np.zeros_like(C)
+    lib().orc_dt_aggregate(_p(C), w, h, D, _p(g), float(sigma_s), float(sigma_r), int(iters), _p(out))
+    return out
+
+
+def coarse_cost(left, right, cost: str, k: int, D: int, census_window: int = 5):
+    """The cost volume of the chosen matcher on the quarter-size pair: "zncc" (1 - rho of
+    Eq. 1, 2 where x - d < 0) or "census"."""
+    SL, SR = downsample4(left), downsample4(right)
+    if cost == "zncc":
+        return sgm_cost(zncc_volume(SL, SR, k, D))
+    return census_volume(SL, SR, census_window, D)
 
 
 def upsample4(disp: np.ndarray, W: int, H: int) -> np.ndarray:

@@ -28,6 +28,8 @@
  *   orc_sgm              sum over directions (Eq. 5); orc_sgm_wta: Eq. 6 on the sum
  *   orc_smp, orc_median3 single-matching-phase occlusion check and median filter (Eq. 7
  *                        and the text after it)
+ *   orc_census_volume    census matching cost (Sec. IV-C settings S1, S2)
+ *   orc_dt_aggregate     domain-transform cost aggregation (Sec. IV-C settings S1, S3)
  *
  * Readings of the paper (where it is silent, garbled or inconsistent):
  *   - cost range: Eq. 1 gives 1 - rho, which lies in [0, 2], not [0, 1]; the
@@ -728,4 +730,109 @@ void orc_median3(const int32_t* disp, int w, int h, int32_t* out) {
         }
       out[(size_t)y * w + x] = v[4];
     }
+}
+
+/* ------------------------------------------------------------------ census cost
+ * Sec. IV-C (settings S1 "Census+DT" and S2 "Census+SGM"): the census matching cost as an
+ * alternative to ZNCC.  The paper names the method only; the reading taken here is the
+ * textbook census transform on the quarter-size images (4 x 4 box sums S):
+ *   census(x, y) = the bit string over the kc x kc window offsets (i, j) != (0, 0) (raster
+ *                  order) with bit = 1 iff S(x + i, y + j) < S(x, y), window pixels clamped
+ *                  to the image as for ZNCC;
+ *   C(x, y, d)   = number of differing bits of census_L(x, y) and census_R(x - d, y), for
+ *                  x - d >= 0; candidates with x - d < 0 take the largest cost, kc^2 - 1.
+ * kc is odd, 3..7 (at most 48 bits).  The cost is an integer, stored as a double. */
+static uint64_t census_code(const int32_t* S, int w, int h, int kc, int x, int y) {
+  const int r = kc / 2;
+  const int32_t c = S[(size_t)y * w + x];
+  uint64_t code = 0;
+  int bit = 0;
+  for (int j = -r; j <= r; ++j)
+    for (int i = -r; i <= r; ++i) {
+      if (i == 0 && j == 0) continue;
+      const int32_t v = S[(size_t)clampi(y + j, 0, h - 1) * w + clampi(x + i, 0, w - 1)];
+      if (v < c) code |= (uint64_t)1 << bit;
+      ++bit;
+    }
+  return code;
+}
+
+static int popcount64(uint64_t v) {
+  int n = 0;
+  for (; v; v &= v - 1) ++n;
+  return n;
+}
+
+void orc_census_volume(const int32_t* SL, const int32_t* SR, int w, int h, int kc, int D, double* C) {
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < h; ++y)
+    for (int x = 0; x < w; ++x) {
+      const uint64_t cl = census_code(SL, w, h, kc, x, y);
+      for (int d = 0; d < D; ++d) {
+        double* out = C + ((size_t)y * w + x) * D + d;
+        if (x - d < 0) {
+          *out = (double)(kc * kc - 1);
+          continue;
+        }
+        *out = (double)popcount64(cl ^ census_code(SR, w, h, kc, x - d, y));
+      }
+    }
+}
+
+/* ------------------------------------------------------------------ domain-transform aggregation
+ * Sec. IV-C (settings S1 "Census+DT" and S3 "ZNCC+DT").  The paper does not define DT; the
+ * reading taken here is cost aggregation by the domain transform, each disparity slice of the
+ * cost volume smoothed by the recursive edge-aware filter of the domain transform, guided by
+ * the left quarter-size image I = S_L / 16 (mean intensity of each 4 x 4 block, 0..255):
+ *   between neighbours n - 1 and n of a row (or a column) the transformed distance is
+ *   t(n) = 1 + (sigma_s / sigma_r) |I(n) - I(n - 1)|;
+ *   iteration i = 1..N uses sigma_i = sigma_s sqrt(3) 2^(N - i) / sqrt(4^N - 1) and
+ *   a_i = exp(-sqrt(2) / sigma_i); one iteration filters every row left to right,
+ *   J(n) = J(n) + a_i^t(n) (J(n - 1) - J(n)), then right to left,
+ *   J(n) = J(n) + a_i^t(n + 1) (J(n + 1) - J(n)), then every column the same way, top to
+ *   bottom and bottom to top.
+ * C, out: [h][w][D] (out may equal C).  guide: [h][w] box sums of the left image. */
+void orc_dt_aggregate(const double* C, int w, int h, int D, const int32_t* guide, double sigma_s, double sigma_r,
+                      int iters, double* out) {
+  const size_t n = (size_t)w * h * D;
+  if (out != C)
+    for (size_t i = 0; i < n; ++i) out[i] = C[i];
+  const double ratio = sigma_s / sigma_r;
+  for (int it = 1; it <= iters; ++it) {
+    const double sig = sigma_s * sqrt(3.0) * pow(2.0, iters - it) / sqrt(pow(4.0, iters) - 1.0);
+    const double lna = -sqrt(2.0) / sig; /* log a_i */
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < h; ++y)
+      for (int d = 0; d < D; ++d) {
+        for (int x = 1; x < w; ++x) {
+          const double t = 1.0 + ratio * fabs(guide[(size_t)y * w + x] / 16.0 - guide[(size_t)y * w + x - 1] / 16.0);
+          const double a = exp(lna * t);
+          double* J = out + ((size_t)y * w + x) * D + d;
+          *J += a * (*(J - D) - *J);
+        }
+        for (int x = w - 2; x >= 0; --x) {
+          const double t = 1.0 + ratio * fabs(guide[(size_t)y * w + x + 1] / 16.0 - guide[(size_t)y * w + x] / 16.0);
+          const double a = exp(lna * t);
+          double* J = out + ((size_t)y * w + x) * D + d;
+          *J += a * (*(J + D) - *J);
+        }
+      }
+#pragma omp parallel for schedule(static)
+    for (int x = 0; x < w; ++x)
+      for (int d = 0; d < D; ++d) {
+        const size_t row = (size_t)w * D;
+        for (int y = 1; y < h; ++y) {
+          const double t = 1.0 + ratio * fabs(guide[(size_t)y * w + x] / 16.0 - guide[(size_t)(y - 1) * w + x] / 16.0);
+          const double a = exp(lna * t);
+          double* J = out + ((size_t)y * w + x) * D + d;
+          *J += a * (*(J - row) - *J);
+        }
+        for (int y = h - 2; y >= 0; --y) {
+          const double t = 1.0 + ratio * fabs(guide[(size_t)(y + 1) * w + x] / 16.0 - guide[(size_t)y * w + x] / 16.0);
+          const double a = exp(lna * t);
+          double* J = out + ((size_t)y * w + x) * D + d;
+          *J += a * (*(J + row) - *J);
+        }
+      }
+  }
 }
