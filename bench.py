@@ -55,8 +55,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
-    ap.add_argument("--sgm", action="store_true",
-                    help="also time the semi-global matching coarse stage (4 paths) on the same pairs")
+    ap.add_argument("--coarse", action="store_true",
+                    help="also time the coarse-stage variants (ZNCC / census cost, SGM / DT aggregation, occlusion "
+                         "check and median filter) on the same pairs")
     ap.add_argument("--train-pairs", type=int, default=16)
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch plans (fixed launch order, e.g. for profiler captures)")
@@ -607,34 +608,9 @@ def run_ours(args):
                  "loss_last": float(Lt.item())}
         tctx.close()
 
-    sgm = None
-    if args.sgm:
-        # the semi-global matching variant of the coarse stage on the same pairs: ZNCC cost
-        # volume, 4 aggregation paths, winner-take-all (sv_coarse_match_sgm)
-        sctx = binding.Context(shape, WIN, "bf16", dev)
-        with torch.cuda.stream(st):
-            for _ in range(args.warmup):
-                sctx.coarse_match_sgm(dps, SGM_P1, SGM_P2, 4, stream=st)
-        torch.cuda.synchronize()
-        sctx.profile(True)
-        sctx.profile_read(reset=True)
-        sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        with torch.cuda.stream(st):
-            for k in range(args.steps):
-                flush.fill_(k & 0xFF)
-                sev[k][0].record(st)
-                sctx.coarse_match_sgm(dps, SGM_P1, SGM_P2, 4, stream=st)
-                sev[k][1].record(st)
-        torch.cuda.synchronize()
-        sprof = sctx.profile_read(reset=True)
-        sctx.profile(False)
-        sms = max_over_ranks(sum(a.elapsed_time(b) for a, b in sev)) / args.steps
-        vol_bytes = B * (W // 4) * (H // 4) * D * 4
-        kms = {kn: v[1] / args.steps for kn, v in sprof.items()}
-        sgm = {"pairs_per_s": whole_job_value(B, world, sms), "ms_per_step": sms, "P1": SGM_P1, "P2": SGM_P2,
-               "npaths": 4, "kernel_ms_per_step": kms, "cost_volume_bytes": vol_bytes,
-               "roofline": sgm_path_roofline(vol_bytes, kms.get("sgm_path", float("nan")), 4, pk["hbm_gbs"], pk_kind)}
-        sctx.close()
+    coarse = None
+    if args.coarse:
+        coarse = coarse_variants(binding, shape, dev, dps, B, world, args, st, flush, pk, pk_kind, max_over_ranks)
 
     value = whole_job_value(B, world, R["ms_per_step"])
     line = {
@@ -662,8 +638,8 @@ def run_ours(args):
         "uneven_batch": uneven,
         "train_step": train,
     }
-    if sgm is not None:
-        line["sgm"] = sgm
+    if coarse is not None:
+        line["coarse_variants"] = coarse
     if rank == 0:
         print(json.dumps(line))
     for r in results.values():
@@ -672,18 +648,84 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def sgm_path_roofline(vol_bytes, path_ms_per_call, npaths, hbm_peak_gbs, peak_kind):
-    """HBM roofline of the SGM path kernels (Eq. 4): per call the first direction reads the
-    cost volume and writes the aggregated one, every later direction reads both and writes
-    the aggregated one, so 2 + 3 (npaths - 1) volumes of algorithmic traffic."""
-    volumes = 2 + 3 * (npaths - 1)
-    per_launch_bytes = vol_bytes * volumes / npaths
-    launch_s = path_ms_per_call / npaths / 1e3
-    achieved = per_launch_bytes / launch_s / 1e9
-    return {"bound": "hbm", "kernel": "sgm_path", "achieved": achieved, "peak": hbm_peak_gbs, "unit": "GB/s",
-            "frac": achieved / hbm_peak_gbs, "per_launch_bytes": per_launch_bytes,
-            "avg_launch_ms": path_ms_per_call / npaths, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)",
-            "traffic": None}
+# Coarse-stage variants timed by --coarse: (name, sv_coarse_opts keywords).  The penalties
+# and DT scales are not given by the paper: P1, P2 on the ZNCC cost's [0, 2] range and in
+# bits for the 5 x 5 census cost, sigma_s in coarse pixels, sigma_r in intensity levels.
+COARSE_VARIANTS = [
+    ("S4 ZNCC+SGM", dict(cost="zncc", aggregation="sgm", P1=SGM_P1, P2=SGM_P2, npaths=4)),
+    ("S4 ZNCC+SGM+SMP+median", dict(cost="zncc", aggregation="sgm", P1=SGM_P1, P2=SGM_P2, npaths=4, smp=True,
+                                    median=True)),
+    ("S2 census+SGM", dict(cost="census", census_window=5, aggregation="sgm", P1=2.0, P2=12.0, npaths=4)),
+    ("S3 ZNCC+DT", dict(cost="zncc", aggregation="dt", dt_sigma_s=8.0, dt_sigma_r=20.0, dt_iters=2)),
+    ("S1 census+DT", dict(cost="census", census_window=5, aggregation="dt", dt_sigma_s=8.0, dt_sigma_r=20.0,
+                          dt_iters=2)),
+]
+
+
+def coarse_kernel_bytes(name, W, H, D, npaths=4, dt_iters=2):
+    """Algorithmic HBM bytes of one call's kernel `name` for one W x H pair with D
+    disparities (summed over that kernel's launches in the call): the FP32 cost volume V
+    = 4 w h D bytes is the unit; maps are int16, codes uint64, box sums int32."""
+    w, h = W // 4, H // 4
+    V = 4 * w * h * D
+    return {
+        "zncc_cost": 2 * W * H + V + 2 * w * h,           # images in, volume and map out
+        "box4": 2 * W * H + 8 * w * h,                    # images in, box sums out
+        "census_codes": 8 * w * h + 16 * w * h,           # box sums in, codes out
+        "census_cost": 16 * w * h + V,                    # codes in, volume out
+        # first direction: C in, A out; middle ones: C, A in, A out; the last: C, A in, map out
+        "sgm_path": (2 * V if npaths == 1 else 2 * V + 3 * V * (npaths - 2) + 2 * V) + 2 * w * h,
+        "dt_rows": dt_iters * (2 * V + 4 * w * h),        # volume in and out, guide in
+        "dt_cols": dt_iters * (2 * V + 4 * w * h),
+        "vol_wta": V + 2 * w * h,
+        "smp": 4 * w * h,                                 # map in, map out
+        "median3": 4 * w * h,
+    }.get(name, 0)
+
+
+def coarse_variants(binding, shape, dev, dps, B, world, args, st, flush, pk, pk_kind, max_over_ranks):
+    """Time every coarse-stage variant on the step's pairs: pairs/s and the HBM roofline of
+    each of its kernels."""
+    import torch
+    ctx = binding.Context(shape, WIN, "bf16", dev)
+    out = {}
+    try:
+        for name, kw in COARSE_VARIANTS:
+            opts = binding.coarse_opts(**kw)
+            with torch.cuda.stream(st):
+                for _ in range(args.warmup):
+                    ctx.coarse_match_ex(dps, opts, stream=st)
+            torch.cuda.synchronize()
+            ctx.profile(True)
+            ctx.profile_read(reset=True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            with torch.cuda.stream(st):
+                for k in range(args.steps):
+                    flush.fill_(k & 0xFF)
+                    ev[k][0].record(st)
+                    ctx.coarse_match_ex(dps, opts, stream=st)
+                    ev[k][1].record(st)
+            torch.cuda.synchronize()
+            prof = ctx.profile_read(reset=True)
+            ctx.profile(False)
+            ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev)) / args.steps
+            kernels = {}
+            for kn, (nl, tot) in sorted(prof.items()):
+                kms = tot / args.steps
+                units = sum(coarse_kernel_bytes(kn, dp.width, dp.height, dp.max_disp, kw.get("npaths", 4),
+                                                kw.get("dt_iters", 2)) for dp in dps)
+                e = {"ms_per_step": kms, "launches_per_step": nl / args.steps}
+                if units:
+                    ach = units / (kms / 1e3) / 1e9
+                    e.update({"bound": "hbm", "bytes_per_step": units, "achieved": ach, "peak": pk["hbm_gbs"],
+                              "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "peak_source": f"{pk_kind} hbm_gbs"})
+                kernels[kn] = e
+            out[name] = {"options": kw, "pairs_per_s": whole_job_value(B, world, ms), "ms_per_step": ms,
+                         "kernels": kernels}
+    finally:
+        ctx.close()
+    return out
 
 
 def arm_config(B, world, head, distinct=None):

@@ -134,19 +134,81 @@ SV_API sv_status sv_refine(sv_ctx* ctx, const sv_pair* pairs, const int16_t* con
                     float* const* disp_out, sv_stream stream);
 
 /* Semi-global matching variant of the coarse stage (Sec. III-A, Eq. 1 and 4-6).  For every
- * pair: the quarter-size images (4 x 4 box sums), the ZNCC cost volume C = 1 - rho of Eq. 1-3
- * (window side = the context's window, clamp-to-edge windows; candidates with x - d < 0 cost
- * 2, the largest value of Eq. 1), aggregated by Eq. 4 along `npaths` directions taken in the
- * order left-to-right, right-to-left, top-to-bottom, bottom-to-top (1..4) and summed (Eq. 5),
- * then winner-take-all (Eq. 6, lowest d on ties) into disp_out[i] ((H/4) x (W/4) int16,
- * device).  P1 (change of one disparity) and P2 (larger changes) are the penalties of Eq. 4,
- * both >= 0; the paper does not give their values.  cost_out (nullable array; entries
- * nullable) receives the aggregated volume [H/4][W/4][max_disp] FP32 (device).  Returns
- * SV_ERR_INVALID_ARG for a negative penalty, npaths outside 1..4 or a NULL disp_out entry,
- * SV_ERR_UNSUPPORTED when 2 x window x (W/4) x 4 bytes exceed 227 KB.  Asynchronous on
- * `stream`; the context's work buffers are reused by the next call. */
+ * pair: the ZNCC cost volume C = 1 - rho of Eq. 1-3 on the quarter-size images (window side =
+ * the context's window, clamp-to-edge windows; candidates with x - d < 0 cost 2, the largest
+ * value of Eq. 1), aggregated by Eq. 4 along `npaths` directions taken in the order
+ * left-to-right, right-to-left, top-to-bottom, bottom-to-top (1..4) and summed (Eq. 5), then
+ * winner-take-all (Eq. 6, lowest d on ties) into disp_out[i] ((H/4) x (W/4) int16, device).
+ * P1 (change of one disparity) and P2 (larger changes) are the penalties of Eq. 4, both >= 0;
+ * the paper does not give their values.  cost_out (nullable array; entries nullable)
+ * receives the aggregated volume [H/4][W/4][max_disp] FP32 (device).  Returns
+ * SV_ERR_INVALID_ARG for a negative penalty, npaths outside 1..4 or a NULL disp_out entry.
+ * Equivalent to sv_coarse_match_ex with SV_COST_ZNCC, SV_AGG_SGM and no post-processing.
+ * Asynchronous on `stream`; the context's work buffers are reused by the next call. */
 SV_API sv_status sv_coarse_match_sgm(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, float P1, float P2, int npaths,
                                      int16_t* const* disp_out, float* const* cost_out, sv_stream stream);
+
+/* Matching cost of the coarse stage: ZNCC (Eq. 1-3) or the census cost the paper's
+ * robustness study pairs with it (Sec. IV-C, settings S1 and S2). */
+typedef enum { SV_COST_ZNCC = 0, SV_COST_CENSUS = 1 } sv_cost_kind;
+
+/* Cost aggregation: none (plain winner-take-all, Eq. 6), semi-global matching (Eq. 4-5) or
+ * the domain-transform aggregation of the robustness study (Sec. IV-C, settings S1, S3). */
+typedef enum { SV_AGG_NONE = 0, SV_AGG_SGM = 1, SV_AGG_DT = 2 } sv_aggregation;
+
+/* Post-processing of the winner-take-all map (Sec. III-A, Eq. 7 and the text after it),
+ * applied in this order when both are set. */
+enum { SV_POST_SMP = 1, SV_POST_MEDIAN = 2 };
+
+/* Options of sv_coarse_match_ex / sv_pipeline_ex.
+ *  census_window: SV_COST_CENSUS: odd side kc of the census window, 3, 5 or 7 (bit = 1 where a
+ *                 window pixel of the quarter-size image is below the centre, clamped window;
+ *                 cost = Hamming distance of the codes of (x, y) and (x - d, y), kc^2 - 1 where
+ *                 x - d < 0).
+ *  P1, P2, npaths: SV_AGG_SGM: penalties (>= 0, units of the cost) and directions (1..4), as
+ *                 for sv_coarse_match_sgm.
+ *  dt_sigma_s, dt_sigma_r, dt_iters: SV_AGG_DT: spatial scale (coarse pixels, > 0), range
+ *                 scale (intensity levels 0..255 of the quarter-size left image, > 0) and
+ *                 iterations (1..8) of the recursive domain-transform filter applied to every
+ *                 disparity slice, rows (both ways) then columns (both ways) per iteration,
+ *                 iteration i of N at scale dt_sigma_s sqrt(3) 2^(N-i) / sqrt(4^N - 1).
+ *  post:          SV_POST_* flags. */
+typedef struct {
+  int cost;
+  int census_window;
+  int aggregation;
+  float P1, P2;
+  int npaths;
+  float dt_sigma_s, dt_sigma_r;
+  int dt_iters;
+  int post;
+} sv_coarse_opts;
+
+/* Coarse stage with a chosen cost, aggregation and post-processing.  For every pair: the cost
+ * volume of `opts->cost` on the quarter-size images (ZNCC: C = 1 - rho with the context's
+ * window, 2 where x - d < 0), aggregated by `opts->aggregation`, winner-take-all (argmin over
+ * d, lowest d on ties; with SV_COST_ZNCC and SV_AGG_NONE the exact argmax of rho of
+ * sv_coarse_match), then the single-matching-phase check (SV_POST_SMP: of two pixels of a row
+ * matched to the same target column x - d within D, the left one keeps its disparity; every
+ * other pixel takes the disparity of the nearest kept pixel of its row, the left one at equal
+ * distance) and a 3 x 3 median filter with clamped edges (SV_POST_MEDIAN).  disp_out[i]:
+ * (H/4) x (W/4) int16 (device).  cost_out (nullable array; entries nullable): the aggregated
+ * volume [H/4][W/4][max_disp] FP32 (the raw cost with SV_AGG_NONE).  SV_ERR_INVALID_ARG for a
+ * NULL or out-of-range option.  Asynchronous on `stream`. */
+SV_API sv_status sv_coarse_match_ex(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, const sv_coarse_opts* opts,
+                                    int16_t* const* disp_out, float* const* cost_out, sv_stream stream);
+
+/* The post-processing of sv_coarse_match_ex alone, on given coarse maps: disp_in[i] and
+ * disp_out[i] are (H/4) x (W/4) int16 device maps of pair i (sizes and max_disp are taken
+ * from pairs[i]; the image pointers are not read and may be NULL); post = SV_POST_* flags
+ * (0 copies).  disp_out[i] must not overlap disp_in[i].  Asynchronous on `stream`. */
+SV_API sv_status sv_postprocess(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, const int16_t* const* disp_in,
+                                int post, int16_t* const* disp_out, sv_stream stream);
+
+/* sv_pipeline with the coarse stage of sv_coarse_match_ex: coarse maps by `opts`, then the
+ * refinement of sv_refine (the context's form), into disp_out[i] (H x W FP32, device). */
+SV_API sv_status sv_pipeline_ex(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, const sv_coarse_opts* opts,
+                                float* const* disp_out, sv_stream stream);
 
 /* Coarse matching followed by refinement (sv_coarse_match + sv_refine) with the
  * coarse maps kept in the context's workspace. */

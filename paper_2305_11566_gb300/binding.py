@@ -32,6 +32,30 @@ class SvPair(ctypes.Structure):
                 ("max_disp", c_int)]
 
 
+class SvCoarseOpts(ctypes.Structure):
+    _fields_ = [("cost", c_int), ("census_window", c_int), ("aggregation", c_int), ("P1", c_float), ("P2", c_float),
+                ("npaths", c_int), ("dt_sigma_s", c_float), ("dt_sigma_r", c_float), ("dt_iters", c_int),
+                ("post", c_int)]
+
+
+SV_COST_ZNCC, SV_COST_CENSUS = 0, 1
+SV_AGG_NONE, SV_AGG_SGM, SV_AGG_DT = 0, 1, 2
+SV_POST_SMP, SV_POST_MEDIAN = 1, 2
+
+
+def coarse_opts(cost="zncc", aggregation="none", census_window=5, P1=0.1, P2=0.5, npaths=4, dt_sigma_s=8.0,
+                dt_sigma_r=20.0, dt_iters=2, smp=False, median=False) -> SvCoarseOpts:
+    """sv_coarse_opts from names: cost "zncc" | "census", aggregation "none" | "sgm" | "dt"."""
+    o = SvCoarseOpts()
+    o.cost = {"zncc": SV_COST_ZNCC, "census": SV_COST_CENSUS}[cost]
+    o.census_window = census_window
+    o.aggregation = {"none": SV_AGG_NONE, "sgm": SV_AGG_SGM, "dt": SV_AGG_DT}[aggregation]
+    o.P1, o.P2, o.npaths = P1, P2, npaths
+    o.dt_sigma_s, o.dt_sigma_r, o.dt_iters = dt_sigma_s, dt_sigma_r, dt_iters
+    o.post = (SV_POST_SMP if smp else 0) | (SV_POST_MEDIAN if median else 0)
+    return o
+
+
 class SvProfileEntry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong), ("total_ms", c_double)]
 
@@ -56,6 +80,11 @@ API = {
                          c_void_p], c_int),
     "sv_coarse_match_sgm": ([c_void_p, POINTER(SvPair), c_int, c_float, c_float, c_int, POINTER(c_void_p),
                              POINTER(c_void_p), c_void_p], c_int),
+    "sv_coarse_match_ex": ([c_void_p, POINTER(SvPair), c_int, POINTER(SvCoarseOpts), POINTER(c_void_p),
+                            POINTER(c_void_p), c_void_p], c_int),
+    "sv_postprocess": ([c_void_p, POINTER(SvPair), c_int, POINTER(c_void_p), c_int, POINTER(c_void_p), c_void_p],
+                       c_int),
+    "sv_pipeline_ex": ([c_void_p, POINTER(SvPair), c_int, POINTER(SvCoarseOpts), POINTER(c_void_p), c_void_p], c_int),
     "sv_refine": ([c_void_p, POINTER(SvPair), POINTER(c_void_p), c_int, POINTER(c_void_p), c_void_p], c_int),
     "sv_pipeline": ([c_void_p, POINTER(SvPair), c_int, POINTER(c_void_p), c_void_p], c_int),
     "sv_refine_train": ([c_void_p, POINTER(SvPair), POINTER(c_void_p), POINTER(c_void_p), c_int, POINTER(c_void_p),
@@ -238,6 +267,34 @@ class Context:
         self._check(lib().sv_coarse_match_sgm(self._h, _pairs_array(pairs), len(pairs), float(P1), float(P2), int(npaths),
                                               _ptrs(disp), _ptrs(vols) if costs else None, _stream(stream)))
         return (disp, vols) if costs else disp
+
+    def coarse_match_ex(self, pairs, opts: SvCoarseOpts, costs: bool = False, stream=None):
+        """sv_coarse_match_ex: int16 coarse maps (and the aggregated FP32 volumes [h, w, D]
+        when `costs`)."""
+        import torch
+        dev = pairs[0].left.device if pairs else "cuda"
+        disp = [torch.empty(p.coarse_hw, dtype=torch.int16, device=dev) for p in pairs]
+        vols = [torch.empty((*p.coarse_hw, p.max_disp), dtype=torch.float32, device=dev) for p in pairs] if costs else None
+        self._check(lib().sv_coarse_match_ex(self._h, _pairs_array(pairs), len(pairs), ctypes.byref(opts), _ptrs(disp),
+                                             _ptrs(vols) if costs else None, _stream(stream)))
+        return (disp, vols) if costs else disp
+
+    def postprocess(self, pairs, maps, smp: bool = True, median: bool = True, stream=None):
+        """sv_postprocess: occlusion check and / or median filter of given int16 coarse maps."""
+        import torch
+        outs = [torch.empty_like(m) for m in maps]
+        post = (SV_POST_SMP if smp else 0) | (SV_POST_MEDIAN if median else 0)
+        self._check(lib().sv_postprocess(self._h, _pairs_array(pairs), len(pairs), _ptrs(maps), post, _ptrs(outs),
+                                         _stream(stream)))
+        return outs
+
+    def pipeline_ex(self, pairs, opts: SvCoarseOpts, stream=None, out=None):
+        import torch
+        outs = out if out is not None else [
+            torch.empty((p.height, p.width), dtype=torch.float32, device=p.left.device) for p in pairs]
+        self._check(lib().sv_pipeline_ex(self._h, _pairs_array(pairs), len(pairs), ctypes.byref(opts), _ptrs(outs),
+                                         _stream(stream)))
+        return outs
 
     def refine(self, pairs, coarse, stream=None, out=None):
         import torch

@@ -99,7 +99,8 @@ struct Ctx {
   bool train_ready = false;
   DevBuf host_img, host_out;     // device staging of sv_pipeline_host
   DevBuf host_jobs;              // row-copy job tables of sv_pipeline_host (gather + scatter)
-  DevBuf sgm_s, sgm_c, sgm_a, sgm_tab;  // semi-global matching: box sums, cost, aggregated cost, pairs
+  DevBuf sgm_s, sgm_c, sgm_a, sgm_tab;  // coarse-stage variants: box sums, cost, aggregated cost, pairs
+  DevBuf x_codes, x_maps;               // census codes; winner-take-all and intermediate maps
   cudaStream_t copy_stream = nullptr;    // sv_pipeline_host: results go back here while the
   cudaEvent_t chunk_done[4] = {nullptr, nullptr, nullptr, nullptr};  // next part computes
   int host_chunks = 3;                  // parts of an sv_pipeline_host batch (>= 8 pairs each)
@@ -148,8 +149,12 @@ struct Ctx {
 
   sv_status coarse(const sv_pair* pairs, int n, int16_t* const* disp, float* const* best, float* const* second,
                    cudaStream_t st);
-  sv_status coarse_sgm(const sv_pair* pairs, int n, float P1, float P2, int npaths, int16_t* const* disp,
+  sv_status coarse_ext(const sv_pair* pairs, int n, const sv_coarse_opts& o, int16_t* const* disp,
                        float* const* cost_out, cudaStream_t st);
+  sv_status post_launch(const void* table, int n, int maxw, int maxh, int post, cudaStream_t st);
+  sv_status postprocess(const sv_pair* pairs, int n, const int16_t* const* in, int post, int16_t* const* out,
+                        cudaStream_t st);
+  sv_status pipeline_ex(const sv_pair* pairs, int n, const sv_coarse_opts& o, float* const* out, cudaStream_t st);
   template <typename T> const T* weights() const;
   template <typename T>
   sv_status refine_direct(const sv_pair& p, const void* coarse_map, bool coarse_int16, const T* eps, T* Y, T* mu_out,
@@ -223,7 +228,7 @@ struct Ctx {
     for (auto e : ev_free) cudaEventDestroy(e);
     ev_free.clear();
     host_img.release(); host_out.release(); host_jobs.release(); err_flag.release(); tune_out.release();
-    sgm_s.release(); sgm_c.release(); sgm_a.release(); sgm_tab.release();
+    sgm_s.release(); sgm_c.release(); sgm_a.release(); sgm_tab.release(); x_codes.release(); x_maps.release();
     w32.release(); w64.release(); wbf.release(); wfuse.release(); zpairs.release(); zjobs.release();
     coarse_maps.release();
     for (auto& b : act) b.release();

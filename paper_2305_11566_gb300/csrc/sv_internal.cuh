@@ -26,6 +26,7 @@ struct ZPair {
   int16_t* disp;     // [h][w]
   float* best;       // [h][w] or nullptr
   float* second;     // [h][w] or nullptr
+  float* cost;       // [h][w][D] cost volume 1 - rho (2 where x - d < 0), or nullptr
 };
 
 // One CTA job: rows [y0, y0 + kZnccTY) and columns [x0, x0 + group width) of a pair.
@@ -68,19 +69,21 @@ inline size_t zncc_smem_bytes(int r, int D) { return zlayout(r, D, zncc_tx(zncc_
 
 // Fused downsample + ZNCC + WTA over the given jobs, one entry per window radius
 // r = 1..7 (each compiled in its own translation unit).
+// with_cost: the pairs' cost pointers are set and the kernel also writes the cost volume.
 #define SV_ZNCC_DECL(r)                                                                              \
   cudaError_t launch_zncc_wta_r##r(const ZPair* d_pairs, const ZJob* d_jobs, int n_jobs, int maxD, \
-                                   cudaStream_t st);
+                                   bool with_cost, cudaStream_t st);
 SV_ZNCC_DECL(1) SV_ZNCC_DECL(2) SV_ZNCC_DECL(3) SV_ZNCC_DECL(4) SV_ZNCC_DECL(5) SV_ZNCC_DECL(6) SV_ZNCC_DECL(7)
-inline cudaError_t launch_zncc_wta(const ZPair* p, const ZJob* j, int n, int r, int maxD, cudaStream_t st) {
+inline cudaError_t launch_zncc_wta(const ZPair* p, const ZJob* j, int n, int r, int maxD, cudaStream_t st,
+                                   bool with_cost = false) {
   switch (r) {
-    case 1: return launch_zncc_wta_r1(p, j, n, maxD, st);
-    case 2: return launch_zncc_wta_r2(p, j, n, maxD, st);
-    case 3: return launch_zncc_wta_r3(p, j, n, maxD, st);
-    case 4: return launch_zncc_wta_r4(p, j, n, maxD, st);
-    case 5: return launch_zncc_wta_r5(p, j, n, maxD, st);
-    case 6: return launch_zncc_wta_r6(p, j, n, maxD, st);
-    case 7: return launch_zncc_wta_r7(p, j, n, maxD, st);
+    case 1: return launch_zncc_wta_r1(p, j, n, maxD, with_cost, st);
+    case 2: return launch_zncc_wta_r2(p, j, n, maxD, with_cost, st);
+    case 3: return launch_zncc_wta_r3(p, j, n, maxD, with_cost, st);
+    case 4: return launch_zncc_wta_r4(p, j, n, maxD, with_cost, st);
+    case 5: return launch_zncc_wta_r5(p, j, n, maxD, with_cost, st);
+    case 6: return launch_zncc_wta_r6(p, j, n, maxD, with_cost, st);
+    case 7: return launch_zncc_wta_r7(p, j, n, maxD, with_cost, st);
   }
   return cudaErrorInvalidValue;
 }

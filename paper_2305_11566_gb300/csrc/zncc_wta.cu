@@ -15,6 +15,9 @@
 //           rho = float(n) * (1/sigma_L) * (1/sigma_R).  The argmax over d is two warp
 //           reductions (__reduce_max_sync on an order-preserving integer key, then
 //           __reduce_min_sync on d among the maxima: lowest d wins ties).
+//           With COST, every lane also stores the cost 1 - rho of its candidates (Eq. 1; 2,
+//           the largest value, where x - d < 0) into the pair's volume [h][w][D]: lanes hold
+//           consecutive d, so a warp's stores of one pixel are contiguous.
 #include "sv_internal.cuh"
 
 namespace sv {
@@ -109,7 +112,7 @@ __device__ void window_stats(const uint16_t* s, int ncols, int* cs, unsigned* cs
   __syncthreads();
 }
 
-template <int R, int KD, int TX>
+template <int R, int KD, int TX, bool COST>
 __global__ void __launch_bounds__(kZnccWarps * 32, (KD == 1 || (KD == 2 && R <= 5)) ? 2 : 1)
 zncc_wta_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ jobs) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -199,6 +202,9 @@ zncc_wta_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ jobs) 
         const long long n = N * (long long)run[k] - (long long)sl * (long long)sumR[rs];
         const float rho = (float)n * il * invR[rs];
         const bool valid = d < D && d <= x && x < w;
+        if constexpr (COST) {
+          if (d < D && x < w && y < h) P.cost[((size_t)y * w + x) * D + d] = d <= x ? 1.0f - rho : 2.0f;
+        }
         const int key = valid ? order_key(rho) : INT_MIN;
         if (key > bk) { sk = bk; bk = key; bd = d; }
         else if (key > sk) { sk = key; }
@@ -218,10 +224,10 @@ zncc_wta_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ jobs) 
   }
 }
 
-template <int R, int KD>
+template <int R, int KD, bool COST>
 cudaError_t launch_rk(const ZPair* p, const ZJob* j, int n, int maxD, cudaStream_t st) {
   constexpr int TX = KD == 1 ? 32 : KD == 2 ? 24 : KD == 3 ? 16 : 12;
-  auto kern = zncc_wta_kernel<R, KD, TX>;
+  auto kern = zncc_wta_kernel<R, KD, TX, COST>;
   const size_t smem = zlayout(R, maxD, TX).total;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -237,15 +243,21 @@ cudaError_t launch_rk(const ZPair* p, const ZJob* j, int n, int maxD, cudaStream
 
 #define SV_CAT2(a, b) a##b
 #define SV_CAT(a, b) SV_CAT2(a, b)
-cudaError_t SV_CAT(launch_zncc_wta_r, SV_ZNCC_R)(const ZPair* p, const ZJob* j, int n, int maxD, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
+template <bool COST>
+cudaError_t launch_r(const ZPair* p, const ZJob* j, int n, int maxD, cudaStream_t st) {
   switch (zncc_kd(maxD)) {
-    case 1: return launch_rk<SV_ZNCC_R, 1>(p, j, n, maxD, st);
-    case 2: return launch_rk<SV_ZNCC_R, 2>(p, j, n, maxD, st);
-    case 3: return launch_rk<SV_ZNCC_R, 3>(p, j, n, maxD, st);
-    case 4: return launch_rk<SV_ZNCC_R, 4>(p, j, n, maxD, st);
+    case 1: return launch_rk<SV_ZNCC_R, 1, COST>(p, j, n, maxD, st);
+    case 2: return launch_rk<SV_ZNCC_R, 2, COST>(p, j, n, maxD, st);
+    case 3: return launch_rk<SV_ZNCC_R, 3, COST>(p, j, n, maxD, st);
+    case 4: return launch_rk<SV_ZNCC_R, 4, COST>(p, j, n, maxD, st);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t SV_CAT(launch_zncc_wta_r, SV_ZNCC_R)(const ZPair* p, const ZJob* j, int n, int maxD, bool with_cost,
+                                                  cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  return with_cost ? launch_r<true>(p, j, n, maxD, st) : launch_r<false>(p, j, n, maxD, st);
 }
 
 }  // namespace sv

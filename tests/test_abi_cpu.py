@@ -80,3 +80,26 @@ def test_create_without_device_fails_cleanly(svlib):
     h = ctypes.c_void_p()
     assert svlib.sv_create(ctypes.byref(c), 0, ctypes.byref(h)) == binding.SV_ERR_CUDA
     assert not h.value
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the ABI's structs have the C compiler's sizes and offsets."""
+    import subprocess
+    fields = {"sv_pair": (binding.SvPair, ["left", "right", "width", "height", "pitch", "max_disp"]),
+              "sv_config": (binding.SvConfig, ["window", "enc_ch", "latent_ch", "dec_ch", "precision", "flags"]),
+              "sv_coarse_opts": (binding.SvCoarseOpts, [f for f, _ in binding.SvCoarseOpts._fields_])}
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "stereovae.h"', "int main(void) {"]
+    for st, (_, names) in fields.items():
+        src.append(f'  printf("{st} %zu\\n", sizeof({st}));')
+        for n in names:
+            src.append(f'  printf("{st}.{n} %zu\\n", offsetof({st}, {n}));')
+    src.append("  return 0;\n}")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(c)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for st, (cls, names) in fields.items():
+        assert int(got[st]) == ctypes.sizeof(cls), st
+        for n in names:
+            assert int(got[f"{st}.{n}"]) == getattr(cls, n).offset, (st, n)

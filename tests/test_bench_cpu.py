@@ -39,14 +39,12 @@ def test_reference_arm_other_ranks_are_silent():
     assert run_reference({"RANK": "1", "WORLD_SIZE": "2"}) == []
 
 
-def test_sgm_path_roofline_arithmetic():
-    # 4 directions: 2 + 3 * 3 = 11 volume passes over 4 launches
-    r = bench.sgm_path_roofline(vol_bytes=1e9, path_ms_per_call=4.0, npaths=4, hbm_peak_gbs=5000.0,
-                                peak_kind="measured")
-    assert r["bound"] == "hbm" and r["kernel"] == "sgm_path"
-    assert abs(r["per_launch_bytes"] - 11e9 / 4) < 1
-    assert abs(r["avg_launch_ms"] - 1.0) < 1e-12
-    assert abs(r["achieved"] - 2750.0) < 1e-6 and abs(r["frac"] - 0.55) < 1e-12
+def test_coarse_kernel_bytes():
+    # SGM, 4 directions: 2 + 3 + 3 + 2 = 10 volume passes (the last direction writes only the
+    # winner-take-all map); DT: every iteration reads and writes the volume once per pass
+    V = 4 * 310 * 93 * 48
+    assert bench.coarse_kernel_bytes("sgm_path", 1242, 375, 48, 4) == 10 * V + 2 * 310 * 93
+    assert bench.coarse_kernel_bytes("dt_rows", 1242, 375, 48, dt_iters=3) == 3 * (2 * V + 4 * 310 * 93)
 
 
 def test_kernel_rooflines_arithmetic():
