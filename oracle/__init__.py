@@ -27,6 +27,13 @@ Parity status per function (what pins each one, in tests/test_oracle_*.py):
   census_volume    hand-made 3 x 3 codes; invariance under increasing intensity maps; zero
                    cost of an image against itself and of a constant shift at its disparity;
                    the mirror identity (both images flipped, roles swapped)
+  t1_layer         torch.nn.functional conv2d / conv_transpose2d / leaky_relu in FP64
+  t1_inputs        torch avg_pool2d and interpolate (bilinear, half-pixel centres) where the
+                   sizes are exact multiples
+  t1_forward       the same network composed from torch FP64 library routines (torch.cat,
+                   conv2d, conv_transpose2d, leaky_relu), with and without eps
+  t1_loss          closed forms of the weighted L1 term; torch.distributions.kl_divergence
+                   of Normal(mu - 1, exp(sigma - 1)) from Normal(0, 1)
   dt_aggregate     uniform guide: scipy.signal.lfilter (first-order recursive filter) along
                    each axis; constant slices unchanged; a hard edge (sigma_r -> 0) separates
                    the two sides exactly; linearity in the cost; bounds min C <= out <= max C
@@ -77,6 +84,14 @@ def lib():
         L.orc_smp.argtypes = [P, c_int, c_int, c_int, P]
         L.orc_median3.argtypes = [P, c_int, c_int, P]
         L.orc_census_volume.argtypes = [P, P, c_int, c_int, c_int, c_int, P]
+        L.orc_t1_param_offset.argtypes = [c_int, c_int]
+        L.orc_t1_param_offset.restype = c_size_t
+        L.orc_t1_param_count.restype = c_size_t
+        L.orc_t1_layer.argtypes = [P, c_int, c_int, c_int, P, P, c_int, c_int, c_int, c_int, c_int, c_int, P]
+        L.orc_t1_inputs.argtypes = [P, c_int, c_int, c_int, P, c_int, c_int, P, P]
+        L.orc_t1_forward.argtypes = [P, P, c_int, c_int, c_int, P, c_int, c_int, P, P, P, P, c_int, P]
+        L.orc_t1_loss.argtypes = [P, P, P, c_size_t, P, P, c_size_t, P]
+        L.orc_t1_loss.restype = c_double
         L.orc_dt_aggregate.argtypes = [P, c_int, c_int, c_int, P, c_double, c_double, c_int, P]
         L.orc_upsample4_backward.argtypes = [P, c_int, c_int, c_int, c_int, P]
         L.orc_conv2d.argtypes = [P, c_int, c_int, c_int, P, P, c_int, c_int, c_int, c_int, c_int, c_int, c_int,
@@ -245,6 +260,104 @@ def coarse_cost(left, right, cost: str, k: int, D: int, census_window: int = 5):
     if cost == "zncc":
         return sgm_cost(zncc_volume(SL, SR, k, D))
     return census_volume(SL, SR, census_window, D)
+
+
+# ---------------------------------------------------------------- the paper's Table I network
+T1_LAYERS = ["FE_1", "FE_2", "EN_1", "EN_1_R", "EN_2", "EN_2_R", "heads", "D_1", "D_1_R", "D_2", "D_2_R", "D", "Y"]
+T1_ACTS = ["FE_1", "FE_2", "EN_1", "EN_1_R", "EN_2", "EN_2_R", "heads", "D_1", "D_1_R", "D_2", "D_2_R", "D", "X_0",
+           "X_1"]
+
+
+def t1_levels(H: int, W: int):
+    """(H, W), half, quarter and eighth resolution sizes (ceil at every halving)."""
+    out = [(H, W)]
+    for _ in range(3):
+        H, W = (H + 1) // 2, (W + 1) // 2
+        out.append((H, W))
+    return out
+
+
+def t1_param_count() -> int:
+    return int(lib().orc_t1_param_count())
+
+
+def t1_param_slices():
+    """{layer name: (W slice, b slice)} into the flat Table I parameter vector."""
+    out = {}
+    for i, n in enumerate(T1_LAYERS):
+        a = lib().orc_t1_param_offset(i, 0)
+        b = lib().orc_t1_param_offset(i, 1)
+        c = lib().orc_t1_param_offset(i + 1, 0)
+        out[n] = (slice(a, b), slice(b, c))
+    return out
+
+
+def t1_layer(x: np.ndarray, wt: np.ndarray, b: np.ndarray, mode: int, out_hw, act: bool) -> np.ndarray:
+    """One Table I layer: mode 0 conv s1, 1 conv s2, 2 deconv s2 (cropped to out_hw); x
+    [Hi, Wi, Ci], wt [Co, k, k, Ci] float32, b [Co]; leaky ReLU 0.1 when act."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    wt = np.ascontiguousarray(wt, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    Hi, Wi, Ci = x.shape
+    Co, k = wt.shape[0], wt.shape[1]
+    Ho, Wo = out_hw
+    out = np.zeros((Ho, Wo, Co), dtype=np.float64)
+    lib().orc_t1_layer(_p(x), Hi, Wi, Ci, _p(wt), _p(b), Co, k, int(mode), Ho, Wo, int(act), _p(out))
+    return out
+
+
+def t1_inputs(left: np.ndarray, coarse: np.ndarray):
+    """(X_0, X_1) at half resolution from the left image and the coarse map (coarse pixels)."""
+    left = np.ascontiguousarray(left, dtype=np.uint8)
+    H, W = left.shape
+    c = np.ascontiguousarray(coarse, dtype=np.float64)
+    h, w = c.shape
+    Hh, Wh = (H + 1) // 2, (W + 1) // 2
+    X0 = np.zeros((Hh, Wh), dtype=np.float64)
+    X1 = np.zeros((Hh, Wh), dtype=np.float64)
+    lib().orc_t1_inputs(_p(left), W, H, W, _p(c), w, h, _p(X0), _p(X1))
+    return X0, X1
+
+
+def t1_forward(params: np.ndarray, left: np.ndarray, coarse: np.ndarray, eps=None, act: str | None = None):
+    """Forward pass of the Table I network: {"Y": [H, W] normalised disparity (256 Y in pixels),
+    "mu", "sigma": [H8, W8]} and, with `act`, that activation."""
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    left = np.ascontiguousarray(left, dtype=np.uint8)
+    H, W = left.shape
+    c = np.ascontiguousarray(coarse, dtype=np.float64)
+    h, w = c.shape
+    (_, _), (H2, W2), (H4, W4), (H8, W8) = t1_levels(H, W)
+    Y = np.zeros((H, W), dtype=np.float64)
+    mu = np.zeros((H8, W8), dtype=np.float64)
+    sg = np.zeros((H8, W8), dtype=np.float64)
+    e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64).reshape(H8, W8)
+    which, buf = -1, None
+    if act is not None:
+        which = T1_ACTS.index(act)
+        lv = {"FE_1": (H2, W2, 32), "FE_2": (H2, W2, 32), "EN_1": (H4, W4, 16), "EN_1_R": (H4, W4, 8),
+              "EN_2": (H8, W8, 32), "EN_2_R": (H8, W8, 16), "heads": (H8, W8, 2), "D_1": (H8, W8, 32),
+              "D_1_R": (H8, W8, 16), "D_2": (H4, W4, 16), "D_2_R": (H4, W4, 8), "D": (H2, W2, 16),
+              "X_0": (H2, W2, 1), "X_1": (H2, W2, 1)}[act]
+        buf = np.zeros(lv, dtype=np.float64)
+    lib().orc_t1_forward(_p(params), _p(left), W, H, W, _p(c), w, h, _opt(e), _p(Y), _p(mu), _p(sg), which,
+                         _opt(buf))
+    out = {"Y": Y, "mu": mu, "sigma": sg}
+    if act is not None:
+        out[act] = buf
+    return out
+
+
+def t1_loss(Y, gt, noc, mu, sigma):
+    """Loss of Eq. 9-11 for the Table I network: (total, Loss_1, Loss_2)."""
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    gt = np.ascontiguousarray(gt, dtype=np.float32)
+    noc = np.ascontiguousarray(noc, dtype=np.uint8)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    parts = np.zeros(2, dtype=np.float64)
+    tot = lib().orc_t1_loss(_p(Y), _p(gt), _p(noc), Y.size, _p(mu), _p(sigma), mu.size, _p(parts))
+    return float(tot), float(parts[0]), float(parts[1])
 
 
 def upsample4(disp: np.ndarray, W: int, H: int) -> np.ndarray:

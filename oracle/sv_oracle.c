@@ -30,6 +30,7 @@
  *                        and the text after it)
  *   orc_census_volume    census matching cost (Sec. IV-C settings S1, S2)
  *   orc_dt_aggregate     domain-transform cost aggregation (Sec. IV-C settings S1, S3)
+ *   orc_t1_*             the paper's Table I network (Sec. III-B1) and its loss (Eq. 8-11)
  *
  * Readings of the paper (where it is silent, garbled or inconsistent):
  *   - cost range: Eq. 1 gives 1 - rho, which lies in [0, 2], not [0, 1]; the
@@ -835,4 +836,239 @@ void orc_dt_aggregate(const double* C, int w, int h, int D, const int32_t* guide
         }
       }
   }
+}
+
+/* ------------------------------------------------------------------ the paper's Table I network
+ * Sec. III-B1 (Table I) and Sec. III-B2 (Eq. 8-11).  Readings (the paper leaves them open):
+ *  - inputs at half resolution Hh x Wh = ceil(H/2) x ceil(W/2) ("quarter size" = a quarter of
+ *    the pixels, Table I "H/2 * W/2"): X_1 = the left image's 2 x 2 box mean / 256 (the last row
+ *    / column of an odd size clamped), X_0 = the coarse disparity map (quarter-size matcher, in
+ *    coarse pixels) upsampled bilinearly x2 with half-pixel centres and clamped sources, times 4
+ *    (full-resolution pixels), / 256 (Sec. III-B2: data normalised, factor 256);
+ *  - every conv and deconv has a bias and "same" zero padding (2 for 5 x 5); stride-2 convs give
+ *    ceil(n / 2); the 5 x 5 stride-2 deconvolutions give 2 n, cropped to the size of the level
+ *    they return to (H/4, H/2, H); a 1 x 1 deconvolution is a 1 x 1 conv;
+ *  - leaky ReLU with slope 0.1 after every layer except the mu / sigma heads and the output;
+ *  - "mu & sigma" is one 1 x 1 conv with two output channels (channel 0 mu, 1 sigma);
+ *  - the inputs of a layer listed as "A & B & ..." are concatenated along channels in that
+ *    order; the decoder's residual blocks D_1_R, D_2_R are single 5 x 5 stride-1 convs;
+ *  - Eq. 8 as printed: gaussian = (mu - 1) + eps exp(sigma - 1), eps ~ N(0, 1) (inference:
+ *    eps = 0); the network's output Y is the normalised disparity, 256 Y the disparity in
+ *    full-resolution pixels (no residual onto the input map: Table I feeds X_0 to the last
+ *    layer instead).
+ * Layers (index: name, input -> output channels, kernel, kind):
+ *   0 FE_1 1->32 5 conv   1 FE_2 1->32 5 conv   2 EN_1 64->16 5 conv s2  3 EN_1_R 16->8 5 conv
+ *   4 EN_2 24->32 5 conv s2  5 EN_2_R 32->16 5 conv  6 heads 48->2 1 conv  7 D_1 1->32 1 deconv
+ *   8 D_1_R 80->16 5 conv  9 D_2 96->16 5 deconv s2  10 D_2_R 40->8 5 conv  11 D 48->16 5 deconv s2
+ *   12 Y 81->1 5 deconv s2.  Parameters: per layer W[co][ky][kx][ci] then b[co]. */
+static const int T1_CO[13] = {32, 32, 16, 8, 32, 16, 2, 32, 16, 16, 8, 16, 1};
+static const int T1_CI[13] = {1, 1, 64, 16, 24, 32, 48, 1, 80, 96, 40, 48, 81};
+static const int T1_K[13] = {5, 5, 5, 5, 5, 5, 1, 1, 5, 5, 5, 5, 5};
+
+size_t orc_t1_param_offset(int l, int want_bias) {
+  size_t o = 0;
+  for (int i = 0; i < l; ++i) o += (size_t)T1_CO[i] * T1_K[i] * T1_K[i] * T1_CI[i] + T1_CO[i];
+  if (want_bias) o += (size_t)T1_CO[l] * T1_K[l] * T1_K[l] * T1_CI[l];
+  return o;
+}
+
+size_t orc_t1_param_count(void) { return orc_t1_param_offset(13, 0); }
+
+/* Generic layer of the Table I network.  mode 0: conv stride 1, 1: conv stride 2, 2: deconv
+ * stride 2 (out(oy, ox) += in(iy, ix) w(ky, kx) for oy = 2 iy + ky - pad, ox = 2 ix + kx - pad,
+ * outputs outside [0, Ho) x [0, Wo) dropped: the 2n output cropped).  pad = ks / 2.
+ * act 1: leaky ReLU 0.1. */
+void orc_t1_layer(const double* in, int Hi, int Wi, int Ci, const float* wt, const float* b, int Co, int ks, int mode,
+                  int Ho, int Wo, int act, double* out) {
+  const int pad = ks / 2;
+  for (size_t i = 0; i < (size_t)Ho * Wo * Co; ++i) out[i] = b[i % Co];
+  if (mode < 2) {
+    const int s = mode == 1 ? 2 : 1;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < Ho; ++y)
+      for (int x = 0; x < Wo; ++x)
+        for (int co = 0; co < Co; ++co) {
+          double acc = 0.0;
+          for (int ky = 0; ky < ks; ++ky) {
+            const int iy = y * s + ky - pad;
+            if (iy < 0 || iy >= Hi) continue;
+            for (int kx = 0; kx < ks; ++kx) {
+              const int ix = x * s + kx - pad;
+              if (ix < 0 || ix >= Wi) continue;
+              const double* ip = in + ((size_t)iy * Wi + ix) * Ci;
+              const float* wp = wt + (((size_t)co * ks + ky) * ks + kx) * Ci;
+              for (int ci = 0; ci < Ci; ++ci) acc += (double)wp[ci] * ip[ci];
+            }
+          }
+          out[((size_t)y * Wo + x) * Co + co] += acc;
+        }
+  } else {
+    /* scatter form, written as a gather per output row so that rows are independent */
+#pragma omp parallel for schedule(static)
+    for (int oy = 0; oy < Ho; ++oy)
+      for (int iy = 0; iy < Hi; ++iy) {
+        const int ky = oy - 2 * iy + pad;
+        if (ky < 0 || ky >= ks) continue;
+        for (int ix = 0; ix < Wi; ++ix)
+          for (int kx = 0; kx < ks; ++kx) {
+            const int ox = 2 * ix + kx - pad;
+            if (ox < 0 || ox >= Wo) continue;
+            const double* ip = in + ((size_t)iy * Wi + ix) * Ci;
+            double* op = out + ((size_t)oy * Wo + ox) * Co;
+            for (int co = 0; co < Co; ++co) {
+              const float* wp = wt + (((size_t)co * ks + ky) * ks + kx) * Ci;
+              double acc = 0.0;
+              for (int ci = 0; ci < Ci; ++ci) acc += (double)wp[ci] * ip[ci];
+              op[co] += acc;
+            }
+          }
+      }
+  }
+  if (act)
+    for (size_t i = 0; i < (size_t)Ho * Wo * Co; ++i)
+      if (out[i] < 0) out[i] *= 0.1;
+}
+
+/* Network inputs at half resolution: X_0 (disparity) and X_1 (left image), see above. */
+void orc_t1_inputs(const uint8_t* left, int W, int H, int pitch, const double* coarse, int w, int h, double* X0,
+                   double* X1) {
+  const int Wh = (W + 1) / 2, Hh = (H + 1) / 2;
+  for (int y = 0; y < Hh; ++y)
+    for (int x = 0; x < Wh; ++x) {
+      const int y1 = 2 * y + 1 < H ? 2 * y + 1 : H - 1, x1 = 2 * x + 1 < W ? 2 * x + 1 : W - 1;
+      const double s = (double)left[(size_t)(2 * y) * pitch + 2 * x] + left[(size_t)(2 * y) * pitch + x1] +
+                       left[(size_t)y1 * pitch + 2 * x] + left[(size_t)y1 * pitch + x1];
+      X1[(size_t)y * Wh + x] = s / 4.0 / 256.0;
+      double sx = (x + 0.5) / 2.0 - 0.5, sy = (y + 0.5) / 2.0 - 0.5;
+      if (sx < 0) sx = 0;
+      if (sx > w - 1) sx = w - 1;
+      if (sy < 0) sy = 0;
+      if (sy > h - 1) sy = h - 1;
+      const int a = (int)floor(sx), c = (int)floor(sy);
+      const int a1 = a + 1 < w ? a + 1 : w - 1, c1 = c + 1 < h ? c + 1 : h - 1;
+      const double fx = sx - a, fy = sy - c;
+      const double top = (1 - fx) * coarse[(size_t)c * w + a] + fx * coarse[(size_t)c * w + a1];
+      const double bot = (1 - fx) * coarse[(size_t)c1 * w + a] + fx * coarse[(size_t)c1 * w + a1];
+      X0[(size_t)y * Wh + x] = 4.0 * ((1 - fy) * top + fy * bot) / 256.0;
+    }
+}
+
+/* channel concatenation of up to four NHWC tensors of the same spatial size */
+static double* t1_cat(size_t P, const double* a, int ca, const double* b, int cb, const double* c, int cc,
+                      const double* d, int cd) {
+  const int C = ca + cb + cc + cd;
+  double* o = malloc(P * C * sizeof(double));
+  for (size_t p = 0; p < P; ++p) {
+    double* q = o + p * C;
+    for (int i = 0; i < ca; ++i) *q++ = a[p * ca + i];
+    for (int i = 0; i < cb; ++i) *q++ = b[p * cb + i];
+    for (int i = 0; i < cc; ++i) *q++ = c[p * cc + i];
+    for (int i = 0; i < cd; ++i) *q++ = d[p * cd + i];
+  }
+  return o;
+}
+
+/* Forward pass of the Table I network.  coarse: h x w map in coarse pixels (real valued);
+ * eps: H8 x W8 noise or NULL (inference, eps = 0).  Y: H x W normalised disparity (256 Y in
+ * pixels); mu, sigma: H8 x W8 (nullable).  acts (nullable): receives a copy of activation
+ * `which` (0 FE_1, 1 FE_2, 2 EN_1, 3 EN_1_R, 4 EN_2, 5 EN_2_R, 6 heads, 7 D_1, 8 D_1_R, 9 D_2,
+ * 10 D_2_R, 11 D, 12 X_0, 13 X_1). */
+void orc_t1_forward(const float* params, const uint8_t* left, int W, int H, int pitch, const double* coarse, int w,
+                    int h, const double* eps, double* Y, double* mu, double* sigma, int which, double* acts) {
+  const int H2 = (H + 1) / 2, W2 = (W + 1) / 2, H4 = (H2 + 1) / 2, W4 = (W2 + 1) / 2, H8 = (H4 + 1) / 2,
+            W8 = (W4 + 1) / 2;
+  const size_t P2 = (size_t)H2 * W2, P4 = (size_t)H4 * W4, P8 = (size_t)H8 * W8;
+#define T1W(l) (params + orc_t1_param_offset(l, 0))
+#define T1B(l) (params + orc_t1_param_offset(l, 1))
+  double* X0 = malloc(P2 * sizeof(double));
+  double* X1 = malloc(P2 * sizeof(double));
+  orc_t1_inputs(left, W, H, pitch, coarse, w, h, X0, X1);
+  double* fe1 = malloc(P2 * 32 * sizeof(double));
+  double* fe2 = malloc(P2 * 32 * sizeof(double));
+  orc_t1_layer(X0, H2, W2, 1, T1W(0), T1B(0), 32, 5, 0, H2, W2, 1, fe1);
+  orc_t1_layer(X1, H2, W2, 1, T1W(1), T1B(1), 32, 5, 0, H2, W2, 1, fe2);
+  double* in = t1_cat(P2, fe1, 32, fe2, 32, NULL, 0, NULL, 0);
+  double* en1 = malloc(P4 * 16 * sizeof(double));
+  orc_t1_layer(in, H2, W2, 64, T1W(2), T1B(2), 16, 5, 1, H4, W4, 1, en1);
+  free(in);
+  double* en1r = malloc(P4 * 8 * sizeof(double));
+  orc_t1_layer(en1, H4, W4, 16, T1W(3), T1B(3), 8, 5, 0, H4, W4, 1, en1r);
+  in = t1_cat(P4, en1, 16, en1r, 8, NULL, 0, NULL, 0);
+  double* en2 = malloc(P8 * 32 * sizeof(double));
+  orc_t1_layer(in, H4, W4, 24, T1W(4), T1B(4), 32, 5, 1, H8, W8, 1, en2);
+  free(in);
+  double* en2r = malloc(P8 * 16 * sizeof(double));
+  orc_t1_layer(en2, H8, W8, 32, T1W(5), T1B(5), 16, 5, 0, H8, W8, 1, en2r);
+  in = t1_cat(P8, en2, 32, en2r, 16, NULL, 0, NULL, 0);
+  double* heads = malloc(P8 * 2 * sizeof(double));
+  orc_t1_layer(in, H8, W8, 48, T1W(6), T1B(6), 2, 1, 0, H8, W8, 0, heads);
+  free(in);
+  double* g = malloc(P8 * sizeof(double));
+  for (size_t p = 0; p < P8; ++p) {
+    const double m = heads[2 * p], s = heads[2 * p + 1];
+    g[p] = (m - 1.0) + (eps ? eps[p] * exp(s - 1.0) : 0.0);
+    if (mu) mu[p] = m;
+    if (sigma) sigma[p] = s;
+  }
+  double* d1 = malloc(P8 * 32 * sizeof(double));
+  orc_t1_layer(g, H8, W8, 1, T1W(7), T1B(7), 32, 1, 0, H8, W8, 1, d1);
+  in = t1_cat(P8, d1, 32, en2, 32, en2r, 16, NULL, 0);
+  double* d1r = malloc(P8 * 16 * sizeof(double));
+  orc_t1_layer(in, H8, W8, 80, T1W(8), T1B(8), 16, 5, 0, H8, W8, 1, d1r);
+  free(in);
+  in = t1_cat(P8, d1, 32, en2, 32, en2r, 16, d1r, 16);
+  double* d2 = malloc(P4 * 16 * sizeof(double));
+  orc_t1_layer(in, H8, W8, 96, T1W(9), T1B(9), 16, 5, 2, H4, W4, 1, d2);
+  free(in);
+  in = t1_cat(P4, d2, 16, en1, 16, en1r, 8, NULL, 0);
+  double* d2r = malloc(P4 * 8 * sizeof(double));
+  orc_t1_layer(in, H4, W4, 40, T1W(10), T1B(10), 8, 5, 0, H4, W4, 1, d2r);
+  free(in);
+  in = t1_cat(P4, d2, 16, en1, 16, en1r, 8, d2r, 8);
+  double* dd = malloc(P2 * 16 * sizeof(double));
+  orc_t1_layer(in, H4, W4, 48, T1W(11), T1B(11), 16, 5, 2, H2, W2, 1, dd);
+  free(in);
+  in = t1_cat(P2, dd, 16, X0, 1, fe1, 32, fe2, 32);
+  orc_t1_layer(in, H2, W2, 81, T1W(12), T1B(12), 1, 5, 2, H, W, 0, Y);
+  free(in);
+  if (acts) {
+    const double* src[14] = {fe1, fe2, en1, en1r, en2, en2r, heads, d1, d1r, d2, d2r, dd, X0, X1};
+    const size_t n[14] = {P2 * 32, P2 * 32, P4 * 16, P4 * 8, P8 * 32, P8 * 16, P8 * 2, P8 * 32, P8 * 16, P4 * 16,
+                          P4 * 8, P2 * 16, P2, P2};
+    if (which >= 0 && which < 14) memcpy(acts, src[which], n[which] * sizeof(double));
+  }
+  free(X0); free(X1); free(fe1); free(fe2); free(en1); free(en1r); free(en2); free(en2r); free(heads); free(g);
+  free(d1); free(d1r); free(d2); free(d2r); free(dd);
+#undef T1W
+#undef T1B
+}
+
+/* Loss of Sec. III-B2 for the Table I network (Eq. 9-11), readings:
+ *   Loss_1 (Eq. 10): (sum over non-occluded pixels of |gt / 256 - Y| + sum over all pixels of
+ *            |gt / 256 - Y|) / (number of pixels): non-occluded pixels weigh twice the
+ *            occluded ones, as the text states (gt_noc: the ground truth where the pixel is
+ *            visible in both views, gt_occ: everywhere);
+ *   Loss_2 (Eq. 11, garbled): the KL divergence of N(mu - 1, exp(sigma - 1)^2) (the
+ *            distribution Eq. 8 samples) from N(0, 1), 0.5 ((mu - 1)^2 + exp(2 (sigma - 1)) - 1
+ *            - 2 (sigma - 1)), averaged over the latent elements (zero at mu = sigma = 1);
+ *   Loss_total (Eq. 9) = 256 (Loss_1 + Loss_2).
+ * noc[p] != 0 marks a non-occluded pixel.  parts (nullable): Loss_1, Loss_2. */
+double orc_t1_loss(const double* Y, const float* gt, const uint8_t* noc, size_t P, const double* mu,
+                   const double* sigma, size_t nl, double* parts) {
+  double l1 = 0.0, l2 = 0.0;
+  for (size_t p = 0; p < P; ++p) {
+    const double e = fabs((double)gt[p] / 256.0 - Y[p]);
+    l1 += noc[p] ? 2.0 * e : e;
+  }
+  l1 /= (double)P;
+  for (size_t i = 0; i < nl; ++i) {
+    const double m = mu[i] - 1.0, s = sigma[i] - 1.0;
+    l2 += 0.5 * (m * m + exp(2.0 * s) - 1.0 - 2.0 * s);
+  }
+  l2 /= (double)nl;
+  if (parts) {
+    parts[0] = l1;
+    parts[1] = l2;
+  }
+  return 256.0 * (l1 + l2);
 }

@@ -207,6 +207,25 @@ def he_normal_weights(shape: NetShape, seed: int = 7) -> np.ndarray:
     return np.concatenate(parts)
 
 
+# The paper's Table I network (Sec. III-B1): (name, cout, cin, k) in the flat parameter order.
+TABLE1_LAYERS = [
+    ("FE_1", 32, 1, 5), ("FE_2", 32, 1, 5), ("EN_1", 16, 64, 5), ("EN_1_R", 8, 16, 5), ("EN_2", 32, 24, 5),
+    ("EN_2_R", 16, 32, 5), ("heads", 2, 48, 1), ("D_1", 32, 1, 1), ("D_1_R", 16, 80, 5), ("D_2", 16, 96, 5),
+    ("D_2_R", 8, 40, 5), ("D", 16, 48, 5), ("Y", 1, 81, 5),
+]
+
+
+def table1_weights(seed: int = 7) -> np.ndarray:
+    """Flat float32 parameters of the Table I network: per layer W[cout][k][k][cin] then
+    b[cout], W ~ N(0, 2 / (cin k k)) (He-normal), b = 0."""
+    st = Stream(seed, 5)
+    parts = []
+    for _, co, ci, k in TABLE1_LAYERS:
+        parts.append((st.normal(co * k * k * ci) * math.sqrt(2.0 / (ci * k * k))).astype(np.float32))
+        parts.append(np.zeros(co, dtype=np.float32))
+    return np.concatenate(parts)
+
+
 def reparam_noise(n: int, seed: int) -> np.ndarray:
     """epsilon ~ N(0, 1) for the reparameterisation (float32)."""
     return Stream(seed, 3).normal(n).astype(np.float32)
