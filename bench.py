@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
+    ap.add_argument("--no-table1", action="store_true",
+                    help="skip the leg of the paper's Table I network (FP32, same pairs)")
     ap.add_argument("--coarse", action="store_true",
                     help="also time the coarse-stage variants (ZNCC / census cost, SGM / DT aggregation, occlusion "
                          "check and median filter) on the same pairs")
@@ -212,6 +214,28 @@ def pair_work(shape, W, H):
     out["tc_dec3_final"] = (out["tc_dec3"][0] + dense["final"], "tensor")
     out["edge_up2fix"] = (2 * 6 * (upfix_pixels(H2, W2) * d1 * lat + upfix_pixels(H1, W1) * d2 * d1), "alu")
     out["edge_final"] = (2 * H0 * W0 * d3 + 2 * w * h + 4 * H0 * W0, "hbm")
+    return out
+
+
+# Layers of the paper's Table I network: (profile name, mode, k, cout, cin, output level);
+# mode 0 conv, 1 stride-2 conv, 2 stride-2 deconvolution; level 0 full, 1 half, 2 quarter,
+# 3 eighth resolution.
+T1_LAYERS = [("t1_fe1", 0, 5, 32, 1, 1), ("t1_fe2", 0, 5, 32, 1, 1), ("t1_en1", 1, 5, 16, 64, 2),
+             ("t1_en1r", 0, 5, 8, 16, 2), ("t1_en2", 1, 5, 32, 24, 3), ("t1_en2r", 0, 5, 16, 32, 3),
+             ("t1_heads", 0, 1, 2, 48, 3), ("t1_d1", 0, 1, 32, 1, 3), ("t1_d1r", 0, 5, 16, 80, 3),
+             ("t1_d2", 2, 5, 16, 96, 2), ("t1_d2r", 0, 5, 8, 40, 2), ("t1_d", 2, 5, 16, 48, 1),
+             ("t1_y", 2, 5, 1, 81, 0)]
+
+
+def t1_work(W, H):
+    """FLOPs (multiply-add = 2) of every Table I layer for one W x H pair: a conv k^2 taps per
+    output, a stride-2 deconvolution k^2 / 4 (each output phase reads only its own taps)."""
+    lv = levels(H, W)
+    out = {}
+    for name, mode, k, co, ci, lev in T1_LAYERS:
+        Ho, Wo = lv[lev]
+        taps = k * k / 4.0 if mode == 2 else k * k
+        out[name] = 2.0 * Ho * Wo * co * ci * taps
     return out
 
 
@@ -608,6 +632,30 @@ def run_ours(args):
                  "loss_last": float(Lt.item())}
         tctx.close()
 
+    table1 = None
+    if not args.no_table1:
+        tctx = binding.Context("table1", WIN, "fp32", dev)
+        tctx.set_weights(synth.table1_weights(7))
+        touts = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in range(B)]
+        tt = time_pipeline(tctx, dps, touts, args.steps, args.warmup, st, flush, dev, barrier)
+        tms = max_over_ranks(sum(tt["step_ms"])) / args.steps
+        tw_ = t1_work(W, H)
+        ttab = {}
+        for kn, (nl, tot) in sorted(tt["prof"].items()):
+            kms = tot / args.steps
+            e = {"ms_per_step": kms, "launches_per_step": nl / args.steps}
+            if kn in tw_:
+                ach = tw_[kn] * B / (kms / 1e3) / 1e12
+                e.update({"bound": "alu", "flops_per_step": tw_[kn] * B, "achieved": ach, "peak": alu_peak,
+                          "unit": "TFLOP/s", "frac": ach / alu_peak, "peak_source": "derived: " + FP32_PEAK_TFLOPS_NOTE})
+            ttab[kn] = e
+        table1 = {"workload": f"{B} synthetic 1242x375 pairs per GPU: ZNCC + WTA coarse maps (D=48, 9x9) refined by "
+                              "the paper's Table I network (FP32 CUDA cores, all pairs per launch)",
+                  "pairs_per_s": whole_job_value(B, world, tms), "ms_per_step": tms,
+                  "gflop_per_pair": sum(tw_.values()) / 1e9, "launches_per_step": tt["launches"] / args.steps,
+                  "kernels": ttab}
+        tctx.close()
+
     coarse = None
     if args.coarse:
         coarse = coarse_variants(binding, shape, dev, dps, B, world, args, st, flush, pk, pk_kind, max_over_ranks)
@@ -636,6 +684,7 @@ def run_ours(args):
         "wta_flip_fraction": accuracy.get(head, {}).get("wta_flip_fraction"),
         "tuning": tuning,
         "uneven_batch": uneven,
+        "table1_net": table1,
         "train_step": train,
     }
     if coarse is not None:

@@ -64,6 +64,29 @@ typedef enum {
  * SV_FP64_CHECK: FP64 CUDA-core convolutions, for gradient checks on small crops. */
 typedef enum { SV_FP32 = 0, SV_BF16 = 1, SV_FP64_CHECK = 2 } sv_precision;
 
+/* sv_config.flags: selects the refinement network.
+ * 0: the small VAE-style net described above (widths from enc_ch / latent_ch / dec_ch).
+ * SV_NET_TABLE1: the paper's own network (Sec. III-B1, Table I), FP32 only (precision
+ *   SV_FP32; the width fields are ignored).  At half resolution (ceil(H/2) x ceil(W/2)) the
+ *   inputs are X_0 = 4 x bilinear x2 of the coarse map / 256 (the disparity in
+ *   full-resolution pixels, normalised) and X_1 = 2 x 2 box mean of the left image / 256;
+ *   FE_1 = conv5(X_0) and FE_2 = conv5(X_1) (32 channels each); encoder EN_1 = conv5 s2
+ *   (FE_1 & FE_2) -> 16, EN_1_R = conv5(EN_1) -> 8, EN_2 = conv5 s2 (EN_1 & EN_1_R) -> 32,
+ *   EN_2_R = conv5(EN_2) -> 16, heads = conv1(EN_2 & EN_2_R) -> mu, sigma; decoder input
+ *   (mu - 1) + eps exp(sigma - 1) (Eq. 8; eps = 0 at inference), D_1 = conv1 -> 32, D_1_R =
+ *   conv5(D_1 & EN_2 & EN_2_R) -> 16, D_2 = deconv5 s2 (D_1 & EN_2 & EN_2_R & D_1_R) -> 16,
+ *   D_2_R = conv5(D_2 & EN_1 & EN_1_R) -> 8, D = deconv5 s2 (D_2 & EN_1 & EN_1_R & D_2_R) -> 16;
+ *   output Y = deconv5 s2 (D & X_0 & FE_1 & FE_2) -> 1 at H x W; "&" concatenates channels
+ *   in that order; leaky ReLU 0.1 after every layer but the heads and Y; every conv and
+ *   deconv has a bias and padding 2 (5 x 5); a stride-2 conv gives ceil(n/2) and a stride-2
+ *   deconv 2n cropped to the size of the level it returns to.  The refined disparity is 256 Y
+ *   (pixels).  Parameters: per layer in the order above W[co][ky][kx][ci] then b[co]
+ *   (162,380).  sv_refine / sv_pipeline / sv_pipeline_ex / sv_pipeline_host run it;
+ *   sv_refine_train runs its training forward (eps and mu / sigma of [H8][W8][1], sigma in the
+ *   logvar_out slot); sv_loss_paper is its loss; sv_refine_backward, sv_loss, sv_adam_step,
+ *   sv_autotune and sv_debug_activation return SV_ERR_UNSUPPORTED on such a context. */
+enum { SV_NET_TABLE1 = 1 };
+
 /* Network and matcher configuration (copied by sv_create). */
 typedef struct {
   int window;     /* ZNCC window side k: odd, 3 <= k <= 15 (Eq. 1-3 window W) */
@@ -71,7 +94,7 @@ typedef struct {
   int latent_ch;  /* latent (mean / logvar) width, multiple of 16, <= 256 */
   int dec_ch[3];  /* decoder widths, each a multiple of 16, <= 256 */
   int precision;  /* sv_precision */
-  int flags;      /* reserved, must be 0 */
+  int flags;      /* 0 or SV_NET_TABLE1 */
 } sv_config;
 
 /* One stereo pair.  left / right: device, [height][pitch] uint8. */
@@ -249,6 +272,23 @@ SV_API sv_status sv_refine_backward(sv_ctx* ctx, const void* const* grad_disp, c
 SV_API sv_status sv_loss(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, const void* const* disp, const float* const* gt,
                   const void* const* mu, const void* const* logvar, double kl_weight, void* loss_out,
                   void* const* grad_disp, void* const* grad_mu, void* const* grad_logvar, sv_stream stream);
+
+/* Loss of the paper's Table I network (Sec. III-B2, Eq. 9-11), as read here:
+ * Loss_1 = (sum over non-occluded pixels of |gt - Y| / 256 + sum over all pixels of
+ * |gt - Y| / 256) / (number of pixels), i.e. non-occluded pixels weigh twice the occluded
+ * ones; Loss_2 = mean over the latent elements of the KL divergence of N(mu - 1,
+ * exp(sigma - 1)^2) (the distribution Eq. 8 samples) from N(0, 1),
+ * 0.5 ((mu - 1)^2 + exp(2 (sigma - 1)) - 1 - 2 (sigma - 1)); total = 256 (Loss_1 + Loss_2).
+ * Sums run over all pairs of the call.  Y[i], gt[i]: H x W FP32 disparities in pixels (device);
+ * noc[i]: H x W uint8, non-zero where the pixel is not occluded; mu[i], sigma[i]: [H8][W8] FP32
+ * (H8 = ceil(ceil(ceil(H/2)/2)/2)).  loss_out: device, 3 doubles (total, Loss_1, Loss_2).
+ * grad_* (arrays or entries nullable): FP32 gradients of the total w.r.t. Y, mu and sigma
+ * (the subgradient 0 where Y = gt).  The reduction order is fixed: repeated calls give
+ * identical sums.  Available on every context. */
+SV_API sv_status sv_loss_paper(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, const float* const* Y,
+                               const float* const* gt, const uint8_t* const* noc, const float* const* mu,
+                               const float* const* sigma, double* loss_out, float* const* grad_Y,
+                               float* const* grad_mu, float* const* grad_sigma, sv_stream stream);
 
 /* One Adam step (Sec. IV-A) on the context's master weights with gradient grad
  * (device, sv_param_count elements, context element type): t = step (1-based),

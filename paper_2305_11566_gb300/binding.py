@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libstereova
 
 SV_OK, SV_ERR_INVALID_ARG, SV_ERR_CUDA, SV_ERR_OOM, SV_ERR_UNSUPPORTED, SV_ERR_TIMEOUT, SV_ERR_STATE = range(7)
 SV_FP32, SV_BF16, SV_FP64_CHECK = 0, 1, 2
+SV_NET_TABLE1 = 1
 PRECISIONS = {"fp32": SV_FP32, "bf16": SV_BF16, "fp64": SV_FP64_CHECK}
 
 
@@ -95,6 +96,9 @@ API = {
                  POINTER(c_void_p), c_double, c_void_p, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
                  c_void_p], c_int),
     "sv_adam_step": ([c_void_p, c_void_p, c_int, c_double, c_double, c_double, c_double, c_void_p], c_int),
+    "sv_loss_paper": ([c_void_p, POINTER(SvPair), c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
+                       POINTER(c_void_p), POINTER(c_void_p), c_void_p, POINTER(c_void_p), POINTER(c_void_p),
+                       POINTER(c_void_p), c_void_p], c_int),
     "sv_pipeline_host": ([c_void_p, POINTER(SvPair), c_int, POINTER(c_void_p), c_void_p], c_int),
     "sv_profile_enable": ([c_void_p, c_int], c_int),
     "sv_profile_read": ([c_void_p, POINTER(SvProfileEntry), c_int, POINTER(c_int), c_int], c_int),
@@ -131,14 +135,17 @@ def _status_name(s: int) -> str:
         return str(s)
 
 
-def make_config(shape: synth.NetShape, window: int, precision: str | int = "fp32") -> SvConfig:
+def make_config(shape, window: int, precision: str | int = "fp32") -> SvConfig:
+    """sv_config for a NetShape, or for the paper's Table I network when shape is "table1"."""
     c = SvConfig()
     c.window = window
-    c.enc_ch[:] = list(shape.enc)
-    c.latent_ch = shape.latent
-    c.dec_ch[:] = list(shape.dec)
+    t1 = isinstance(shape, str) and shape == "table1"
+    if not t1:
+        c.enc_ch[:] = list(shape.enc)
+        c.latent_ch = shape.latent
+        c.dec_ch[:] = list(shape.dec)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    c.flags = 0
+    c.flags = SV_NET_TABLE1 if t1 else 0
     return c
 
 
@@ -197,10 +204,12 @@ def _pairs_array(pairs):
 
 
 class Context:
-    """One sv_ctx: configuration, weights and workspaces on one GPU."""
+    """One sv_ctx: configuration, weights and workspaces on one GPU.  shape: a NetShape, or
+    "table1" for the paper's Table I network (FP32)."""
 
-    def __init__(self, shape: synth.NetShape, window: int, precision: str = "fp32", device: int = 0):
+    def __init__(self, shape, window: int, precision: str = "fp32", device: int = 0):
         self.shape = shape
+        self.latent = 1 if isinstance(shape, str) else shape.latent
         self.window = window
         self.precision = precision
         self.device = device
@@ -370,8 +379,8 @@ class Context:
         mu, lv = [], []
         for p in pairs:
             H3, W3 = latent_hw(p.height, p.width)
-            mu.append(torch.empty((H3, W3, self.shape.latent), dtype=dt, device=dev))
-            lv.append(torch.empty((H3, W3, self.shape.latent), dtype=dt, device=dev))
+            mu.append(torch.empty((H3, W3, self.latent), dtype=dt, device=dev))
+            lv.append(torch.empty((H3, W3, self.latent), dtype=dt, device=dev))
         self._check(lib().sv_refine_train(self._h, _pairs_array(pairs), _ptrs(coarse), _ptrs(eps), len(pairs),
                                           _ptrs(Y), _ptrs(mu), _ptrs(lv), _stream(stream)))
         return Y, mu, lv
@@ -400,6 +409,21 @@ class Context:
                                   _ptrs(gY) if want_grads else None, _ptrs(gmu) if want_grads else None,
                                   _ptrs(glv) if want_grads else None, _stream(stream)))
         return out, gY, gmu, glv
+
+    def loss_paper(self, pairs, Y, gt, noc, mu, sigma, want_grads=True, stream=None):
+        """sv_loss_paper (Eq. 9-11 of the Table I network): (float64 [total, Loss_1, Loss_2],
+        grad_Y, grad_mu, grad_sigma)."""
+        import torch
+        dev = Y[0].device
+        out = torch.empty(3, dtype=torch.float64, device=dev)
+        gY = [torch.empty_like(t) for t in Y] if want_grads else None
+        gmu = [torch.empty_like(t) for t in mu] if want_grads else None
+        gsg = [torch.empty_like(t) for t in sigma] if want_grads else None
+        self._check(lib().sv_loss_paper(self._h, _pairs_array(pairs), len(pairs), _ptrs(Y), _ptrs(gt), _ptrs(noc),
+                                        _ptrs(mu), _ptrs(sigma), c_void_p(out.data_ptr()),
+                                        _ptrs(gY) if want_grads else None, _ptrs(gmu) if want_grads else None,
+                                        _ptrs(gsg) if want_grads else None, _stream(stream)))
+        return out, gY, gmu, gsg
 
     def adam_step(self, grad, step: int, lr=5e-4, beta1=0.99, beta2=0.999, eps=1e-8, stream=None):
         self._check(lib().sv_adam_step(self._h, c_void_p(grad.data_ptr()), int(step), lr, beta1, beta2, eps,

@@ -225,6 +225,7 @@ template sv_status Ctx::refine_direct<double>(const sv_pair&, const void*, bool,
                                               double*, double* const*, cudaStream_t);
 
 sv_status Ctx::refresh_weight_copies_async(cudaStream_t st) {
+  if (t1) return SV_OK;  // the Table I network runs on the FP32 master copy
   sv_status s;
   const size_t n = net.count();
   if ((s = cuda(w64.ensure(n * sizeof(double)), "alloc fp64 weights"))) return s;
@@ -273,6 +274,7 @@ const char* sv_last_error(const sv_ctx* ctx) {
 static bool config_ok(const sv_config* c) {
   if (!c) return false;
   if (c->window < 3 || c->window > 15 || c->window % 2 == 0) return false;
+  if (c->flags == SV_NET_TABLE1) return c->precision == SV_FP32;  // widths fixed by Table I
   for (int i = 0; i < 3; ++i)
     if (!sv::valid_width_pub(c->enc_ch[i]) || !sv::valid_width_pub(c->dec_ch[i])) return false;
   if (!sv::valid_width_pub(c->latent_ch)) return false;
@@ -283,6 +285,7 @@ static bool config_ok(const sv_config* c) {
 
 size_t sv_param_count(const sv_config* c) {
   if (!config_ok(c)) return 0;
+  if (c->flags == SV_NET_TABLE1) return sv::t1_param_count();
   sv::NetDims n{{c->enc_ch[0], c->enc_ch[1], c->enc_ch[2]}, c->latent_ch, {c->dec_ch[0], c->dec_ch[1], c->dec_ch[2]}};
   return n.count();
 }
@@ -301,9 +304,11 @@ sv_status sv_create(const sv_config* cfg, int device, sv_ctx** out) {
   Ctx* c = new Ctx();
   c->cfg = *cfg;
   c->device = device;
-  c->net = sv::NetDims{{cfg->enc_ch[0], cfg->enc_ch[1], cfg->enc_ch[2]}, cfg->latent_ch,
-                       {cfg->dec_ch[0], cfg->dec_ch[1], cfg->dec_ch[2]}};
-  const size_t n = c->net.count();
+  c->t1 = cfg->flags == SV_NET_TABLE1;
+  if (!c->t1)
+    c->net = sv::NetDims{{cfg->enc_ch[0], cfg->enc_ch[1], cfg->enc_ch[2]}, cfg->latent_ch,
+                         {cfg->dec_ch[0], cfg->dec_ch[1], cfg->dec_ch[2]}};
+  const size_t n = c->n_params();
   sv_status s = c->cuda(c->err_flag.ensure(sizeof(int)), "alloc error flag");
   if (!s) s = c->cuda(cudaMemset(c->err_flag.p, 0, sizeof(int)), "zero error flag");
   if (!s) s = c->cuda(c->w32.ensure(n * sizeof(float)), "alloc weights");
@@ -333,7 +338,7 @@ sv_status sv_set_weights(sv_ctx* ctx, const float* params, size_t n) {
   if (!ctx) return SV_ERR_INVALID_ARG;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   if (!params) return c->fail(SV_ERR_INVALID_ARG, "params is NULL");
-  if (n != c->net.count()) return c->fail(SV_ERR_INVALID_ARG, "expected %zu parameters, got %zu", c->net.count(), n);
+  if (n != c->n_params()) return c->fail(SV_ERR_INVALID_ARG, "expected %zu parameters, got %zu", c->n_params(), n);
   DeviceGuard g(c->device);
   sv_status s = c->cuda(cudaMemcpy(c->w32.p, params, n * sizeof(float), cudaMemcpyDefault), "copy weights");
   if (s) return s;
@@ -345,7 +350,7 @@ sv_status sv_get_weights(sv_ctx* ctx, float* params, size_t n) {
   if (!ctx) return SV_ERR_INVALID_ARG;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   if (!params) return c->fail(SV_ERR_INVALID_ARG, "params is NULL");
-  if (n != c->net.count()) return c->fail(SV_ERR_INVALID_ARG, "expected %zu parameters, got %zu", c->net.count(), n);
+  if (n != c->n_params()) return c->fail(SV_ERR_INVALID_ARG, "expected %zu parameters, got %zu", c->n_params(), n);
   DeviceGuard g(c->device);
   return c->cuda(cudaMemcpy(params, c->w32.p, n * sizeof(float), cudaMemcpyDefault), "copy weights out");
 }
@@ -631,6 +636,7 @@ sv_status sv_set_option(sv_ctx* ctx, const char* key, long long value) {
 sv_status sv_debug_activation(sv_ctx* ctx, int which, int pair, void* dst, size_t bytes) {
   if (!ctx) return SV_ERR_INVALID_ARG;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (c->t1) return c->fail(SV_ERR_UNSUPPORTED, "not available for the Table I network");
   if (which < 0 || which > 6 || pair < 0 || pair >= (int)c->tc_off.size() || !dst)
     return c->fail(SV_ERR_INVALID_ARG, "no such activation");
   if (bytes != c->tc_len[pair][which] * sizeof(__nv_bfloat16))

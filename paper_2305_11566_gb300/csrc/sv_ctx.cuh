@@ -74,9 +74,13 @@ struct GraphEntry {
   long long last_use = 0;
 };
 
+size_t t1_param_count();  // the paper's Table I network (t1net.cu)
+
 struct Ctx {
   sv_config cfg{};
   NetDims net{};
+  bool t1 = false;               // the paper's Table I network (sv_config.flags SV_NET_TABLE1)
+  size_t n_params() const { return t1 ? t1_param_count() : net.count(); }
   int device = 0;
   std::string err;
 
@@ -101,6 +105,8 @@ struct Ctx {
   DevBuf host_jobs;              // row-copy job tables of sv_pipeline_host (gather + scatter)
   DevBuf sgm_s, sgm_c, sgm_a, sgm_tab;  // coarse-stage variants: box sums, cost, aggregated cost, pairs
   DevBuf x_codes, x_maps;               // census codes; winner-take-all and intermediate maps
+  DevBuf t1_act, t1_tab;                // Table I network: activations, per-call tables
+  DevBuf loss_slots;                    // per-block partial sums of sv_loss_paper
   cudaStream_t copy_stream = nullptr;    // sv_pipeline_host: results go back here while the
   cudaEvent_t chunk_done[4] = {nullptr, nullptr, nullptr, nullptr};  // next part computes
   int host_chunks = 3;                  // parts of an sv_pipeline_host batch (>= 8 pairs each)
@@ -155,6 +161,12 @@ struct Ctx {
   sv_status postprocess(const sv_pair* pairs, int n, const int16_t* const* in, int post, int16_t* const* out,
                         cudaStream_t st);
   sv_status pipeline_ex(const sv_pair* pairs, int n, const sv_coarse_opts& o, float* const* out, cudaStream_t st);
+  sv_status t1_forward(const sv_pair* pairs, int n, const int16_t* const* coarse_i, const float* const* coarse_f,
+                       const float* const* eps, float* const* Y, float* const* mu, float* const* sigma,
+                       cudaStream_t st);
+  sv_status loss_paper(const sv_pair* pairs, int n, const float* const* Y, const float* const* gt,
+                       const uint8_t* const* noc, const float* const* mu, const float* const* sigma, double* out,
+                       float* const* gY, float* const* gmu, float* const* gsigma, cudaStream_t st);
   template <typename T> const T* weights() const;
   template <typename T>
   sv_status refine_direct(const sv_pair& p, const void* coarse_map, bool coarse_int16, const T* eps, T* Y, T* mu_out,
@@ -229,6 +241,7 @@ struct Ctx {
     ev_free.clear();
     host_img.release(); host_out.release(); host_jobs.release(); err_flag.release(); tune_out.release();
     sgm_s.release(); sgm_c.release(); sgm_a.release(); sgm_tab.release(); x_codes.release(); x_maps.release();
+    t1_act.release(); t1_tab.release(); loss_slots.release();
     w32.release(); w64.release(); wbf.release(); wfuse.release(); zpairs.release(); zjobs.release();
     coarse_maps.release();
     for (auto& b : act) b.release();

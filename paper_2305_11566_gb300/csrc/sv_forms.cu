@@ -9,6 +9,7 @@ namespace sv {
 
 sv_status Ctx::refine_infer(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out,
                             cudaStream_t st) {
+  if (t1) return t1_forward(pairs, n, coarse, nullptr, nullptr, out, nullptr, nullptr, st);
   if (cfg.precision == SV_BF16) return refine_tc(pairs, coarse, n, out, st);
   if (cfg.precision == SV_FP64_CHECK)
     return fail(SV_ERR_UNSUPPORTED, "inference entry points produce FP32; use sv_refine_train on FP64_CHECK contexts");

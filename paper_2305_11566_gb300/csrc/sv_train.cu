@@ -375,6 +375,10 @@ sv_status sv_refine_train(sv_ctx* ctx, const sv_pair* pairs, const void* const* 
     if (!coarse[i] || !eps[i] || !disp_out[i]) return c->fail(SV_ERR_INVALID_ARG, "pair %d: NULL buffer", i);
   sv::DeviceGuardInt g(c->device);
   c->train_ready = false;
+  if (c->t1)  // forward with the reparameterisation of Eq. 8; logvar_out receives sigma
+    return c->t1_forward(pairs, n_pairs, nullptr, (const float* const*)coarse, (const float* const*)eps,
+                         (float* const*)disp_out, (float* const*)mu_out, (float* const*)logvar_out,
+                         (cudaStream_t)stream);
   if (c->cfg.precision == SV_FP64_CHECK)
     return c->train_forward<double>(pairs, coarse, eps, n_pairs, disp_out, mu_out, logvar_out, (cudaStream_t)stream);
   if (c->cfg.precision == SV_BF16)
@@ -388,6 +392,7 @@ sv_status sv_refine_backward(sv_ctx* ctx, const void* const* grad_disp, const vo
   if (!ctx) return SV_ERR_INVALID_ARG;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   c->err.clear();
+  if (c->t1) return c->fail(SV_ERR_UNSUPPORTED, "no backward for the Table I network");
   if (!c->train_ready) return c->fail(SV_ERR_STATE, "sv_refine_backward needs a preceding sv_refine_train");
   if (!grad_disp || !grad_params) return c->fail(SV_ERR_INVALID_ARG, "grad_disp / grad_params is NULL");
   for (size_t i = 0; i < c->train_pairs.size(); ++i)
@@ -406,6 +411,7 @@ sv_status sv_loss(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, const void* co
   if (!ctx) return SV_ERR_INVALID_ARG;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   c->err.clear();
+  if (c->t1) return c->fail(SV_ERR_UNSUPPORTED, "the Table I network's loss is sv_loss_paper");
   sv_status s = c->check_pairs(pairs, n_pairs);
   if (s) return s;
   if (n_pairs == 0 || !disp || !gt || !mu || !logvar || !loss_out) return c->fail(SV_ERR_INVALID_ARG, "NULL argument");
@@ -424,6 +430,7 @@ sv_status sv_adam_step(sv_ctx* ctx, const void* grad, int step, double lr, doubl
   if (!ctx) return SV_ERR_INVALID_ARG;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   c->err.clear();
+  if (c->t1) return c->fail(SV_ERR_UNSUPPORTED, "no training step for the Table I network");
   if (!grad || step < 1) return c->fail(SV_ERR_INVALID_ARG, "grad is NULL or step < 1");
   sv::DeviceGuardInt g(c->device);
   if (c->cfg.precision == SV_FP64_CHECK)
