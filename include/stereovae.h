@@ -399,7 +399,7 @@ SV_API sv_status sv_debug_activation(sv_ctx* ctx, int which, int pair, void* dst
  * window side (odd, 3..15).  The call's work tables are kept in a fixed array compiled
  * into the library (540,672 bytes, held on every GPU that loads the library until the
  * process exits): at most 256 pairs and 32768 jobs per call, where a pair of W x H needs
- * ceil((H/4) / 8) * ceil((W/4) / (8 * TX)) jobs (TX = 32, 24, 16, 12 for D up to 32, 64,
+ * ceil((H/4) / 8) * ceil((W/4) / (8 * TX)) jobs (TX = 32, 20, 16, 12 for D up to 32, 64,
  * 96, 128).  Larger calls return SV_ERR_UNSUPPORTED and launch nothing; other invalid
  * arguments return SV_ERR_INVALID_ARG.  The tables are uploaded on `stream` from host
  * memory that lives only for the duration of the call.  The first call on a device looks

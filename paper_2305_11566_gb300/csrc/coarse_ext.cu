@@ -543,7 +543,7 @@ sv_status Ctx::coarse_ext(const sv_pair* pairs, int n, const sv_coarse_opts& o, 
       return s;
     LaunchScope ls(*this, with_cost ? "zncc_cost" : "zncc_wta", st);
     if ((s = cuda(launch_zncc_wta((const ZPair*)zpairs.p, (const ZJob*)zjobs.p, (int)z.jobs.size(), cfg.window / 2,
-                                  z.maxD, st, with_cost),
+                                  z.maxD, st, with_cost ? 2 : 0),
                   "zncc cost")))
       return s;
   }

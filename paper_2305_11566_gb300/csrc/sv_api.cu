@@ -128,7 +128,10 @@ void Ctx::coarse_prepare(const sv_pair* pairs, int n, int16_t* const* disp, floa
 sv_status Ctx::coarse_launch(const ZRun& z, const ZPair* d_pairs, const ZJob* d_jobs, cudaStream_t st) {
   if (z.jobs.empty()) return SV_OK;
   LaunchScope ls(*this, "zncc_wta", st);
-  return cuda(launch_zncc_wta(d_pairs, d_jobs, (int)z.jobs.size(), cfg.window / 2, z.maxD, st), "zncc_wta launch");
+  bool scores = false;
+  for (const ZPair& q : z.pairs) scores |= q.best != nullptr || q.second != nullptr;
+  return cuda(launch_zncc_wta(d_pairs, d_jobs, (int)z.jobs.size(), cfg.window / 2, z.maxD, st, scores ? 1 : 0),
+              "zncc_wta launch");
 }
 
 sv_status Ctx::coarse(const sv_pair* pairs, int n, int16_t* const* disp, float* const* best, float* const* second,

@@ -38,12 +38,12 @@ constexpr int kZnccTY = 8;      // coarse rows per job
 constexpr int kZnccWarps = 8;   // warps per CTA; each owns a column tile of TX(KD) columns
 
 inline int zncc_kd(int D) { return (D + 31) / 32; }
-inline int zncc_tx(int kd) { return kd == 1 ? 32 : kd == 2 ? 24 : kd == 3 ? 16 : 12; }
+inline int zncc_tx(int kd) { return kd == 1 ? 32 : kd == 2 ? 20 : kd == 3 ? 16 : 12; }
 
 // Shared-memory layout of one ZNCC job (window radius r, disparity count D, tile TX).
 struct ZLayout {
   int nlc, nrc, gx, nrs;  // staged left / right columns, job width, right-window columns
-  size_t off_sl, off_sr, off_suml, off_invl, off_sumr, off_invr, off_cs, off_cs2, total;
+  size_t off_sl, off_sr, off_suml, off_invl, off_statr, off_cs, off_cs2, total;
 };
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 __host__ __device__ inline ZLayout zlayout(int r, int D, int tx) {
@@ -58,8 +58,7 @@ __host__ __device__ inline ZLayout zlayout(int r, int D, int tx) {
   z.off_sr = o; o = align16(o + sizeof(uint16_t) * (TY + 2 * r) * z.nrc);
   z.off_suml = o; o = align16(o + sizeof(int) * TY * z.gx);
   z.off_invl = o; o = align16(o + sizeof(float) * TY * z.gx);
-  z.off_sumr = o; o = align16(o + sizeof(int) * TY * z.nrs);
-  z.off_invr = o; o = align16(o + sizeof(float) * TY * z.nrs);
+  z.off_statr = o; o = align16(o + 2 * sizeof(int) * TY * z.nrs);  // {sum, 1/sigma} per right window
   z.off_cs = o; o = align16(o + sizeof(int) * TY * z.nrc);
   z.off_cs2 = o; o = align16(o + sizeof(unsigned) * TY * z.nrc);
   z.total = o;
@@ -69,21 +68,22 @@ inline size_t zncc_smem_bytes(int r, int D) { return zlayout(r, D, zncc_tx(zncc_
 
 // Fused downsample + ZNCC + WTA over the given jobs, one entry per window radius
 // r = 1..7 (each compiled in its own translation unit).
-// with_cost: the pairs' cost pointers are set and the kernel also writes the cost volume.
+// mode 0: disparities only; 1: also the best / second scores of the pairs that ask for them;
+// 2: also the cost volume (the pairs' cost pointers are set).
 #define SV_ZNCC_DECL(r)                                                                              \
   cudaError_t launch_zncc_wta_r##r(const ZPair* d_pairs, const ZJob* d_jobs, int n_jobs, int maxD, \
-                                   bool with_cost, cudaStream_t st);
+                                   int mode, cudaStream_t st);
 SV_ZNCC_DECL(1) SV_ZNCC_DECL(2) SV_ZNCC_DECL(3) SV_ZNCC_DECL(4) SV_ZNCC_DECL(5) SV_ZNCC_DECL(6) SV_ZNCC_DECL(7)
 inline cudaError_t launch_zncc_wta(const ZPair* p, const ZJob* j, int n, int r, int maxD, cudaStream_t st,
-                                   bool with_cost = false) {
+                                   int mode) {
   switch (r) {
-    case 1: return launch_zncc_wta_r1(p, j, n, maxD, with_cost, st);
-    case 2: return launch_zncc_wta_r2(p, j, n, maxD, with_cost, st);
-    case 3: return launch_zncc_wta_r3(p, j, n, maxD, with_cost, st);
-    case 4: return launch_zncc_wta_r4(p, j, n, maxD, with_cost, st);
-    case 5: return launch_zncc_wta_r5(p, j, n, maxD, with_cost, st);
-    case 6: return launch_zncc_wta_r6(p, j, n, maxD, with_cost, st);
-    case 7: return launch_zncc_wta_r7(p, j, n, maxD, with_cost, st);
+    case 1: return launch_zncc_wta_r1(p, j, n, maxD, mode, st);
+    case 2: return launch_zncc_wta_r2(p, j, n, maxD, mode, st);
+    case 3: return launch_zncc_wta_r3(p, j, n, maxD, mode, st);
+    case 4: return launch_zncc_wta_r4(p, j, n, maxD, mode, st);
+    case 5: return launch_zncc_wta_r5(p, j, n, maxD, mode, st);
+    case 6: return launch_zncc_wta_r6(p, j, n, maxD, mode, st);
+    case 7: return launch_zncc_wta_r7(p, j, n, maxD, mode, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -100,8 +100,10 @@ extern "C" sv_status sv_coarse_match_static(const sv_pair* pairs, int n_pairs, i
   if (cudaMemcpyAsync(b + kJobOffset, jobs.data(), sizeof(sv::ZJob) * jobs.size(), cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return SV_ERR_CUDA;
+  bool scores = false;
+  for (const sv::ZPair& q : zp) scores |= q.best != nullptr || q.second != nullptr;
   if (sv::launch_zncc_wta(reinterpret_cast<const sv::ZPair*>(b), reinterpret_cast<const sv::ZJob*>(b + kJobOffset),
-                          (int)jobs.size(), window / 2, maxD, st) != cudaSuccess)
+                          (int)jobs.size(), window / 2, maxD, st, scores ? 1 : 0) != cudaSuccess)
     return SV_ERR_CUDA;
   return SV_OK;
 }

@@ -15,7 +15,7 @@
 //           rho = float(n) * (1/sigma_L) * (1/sigma_R).  The argmax over d is two warp
 //           reductions (__reduce_max_sync on an order-preserving integer key, then
 //           __reduce_min_sync on d among the maxima: lowest d wins ties).
-//           With COST, every lane also stores the cost 1 - rho of its candidates (Eq. 1; 2,
+//           MODE 2 (cost volume): every lane also stores the cost 1 - rho of its candidates (Eq. 1; 2,
 //           the largest value, where x - d < 0) into the pair's volume [h][w][D]: lanes hold
 //           consecutive d, so a warp's stores of one pixel are contiguous.
 #include "sv_internal.cuh"
@@ -70,10 +70,11 @@ __device__ __forceinline__ void stage_box(const uint8_t* __restrict__ img, int p
 
 // Vertical then horizontal window sums of S over rows [yi, yi + 2r] for each of the
 // TY output rows; writes sum and 1/sigma for `ncols_out` windows starting at column
-// `c0` of the staged array (staged column c0 + t is the window's left edge).
+// `c0` of the staged array (staged column c0 + t is the window's left edge), either to
+// sum_out / inv_out or, packed as {sum, bits of 1/sigma}, to packed.
 template <int R>
 __device__ void window_stats(const uint16_t* s, int ncols, int* cs, unsigned* cs2, int* sum_out, float* inv_out,
-                             int ncols_out) {
+                             int2* packed, int ncols_out) {
   const int TY = kZnccTY;
   for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
     int a = 0;
@@ -106,13 +107,19 @@ __device__ void window_stats(const uint16_t* s, int ncols, int* cs, unsigned* cs
       a2 += cs2[yi * ncols + t + i];
     }
     long long v = N * (long long)a2 - (long long)a * a;
-    sum_out[e] = a;
-    inv_out[e] = v > 0 ? __frsqrt_rn((float)v) : 0.0f;
+    const float inv = v > 0 ? __frsqrt_rn((float)v) : 0.0f;
+    if (packed) {
+      packed[e] = make_int2(a, __float_as_int(inv));
+    } else {
+      sum_out[e] = a;
+      inv_out[e] = inv;
+    }
   }
   __syncthreads();
 }
 
-template <int R, int KD, int TX, bool COST>
+// MODE 0: disparity only; 1: also best / second scores; 2: also the cost volume.
+template <int R, int KD, int TX, int MODE>
 __global__ void __launch_bounds__(kZnccWarps * 32, (KD == 1 || (KD == 2 && R <= 5)) ? 2 : 1)
 zncc_wta_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ jobs) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -125,8 +132,7 @@ zncc_wta_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ jobs) 
   uint16_t* sR = reinterpret_cast<uint16_t*>(smem + Z.off_sr);
   int* sumL = reinterpret_cast<int*>(smem + Z.off_suml);
   float* invL = reinterpret_cast<float*>(smem + Z.off_invl);
-  int* sumR = reinterpret_cast<int*>(smem + Z.off_sumr);
-  float* invR = reinterpret_cast<float*>(smem + Z.off_invr);
+  int2* statR = reinterpret_cast<int2*>(smem + Z.off_statr);  // {sum, 1/sigma bits} of each right window
   int* cs = reinterpret_cast<int*>(smem + Z.off_cs);
   unsigned* cs2 = reinterpret_cast<unsigned*>(smem + Z.off_cs2);
   const int y0 = job.y0, x0 = job.x0;
@@ -138,12 +144,13 @@ zncc_wta_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ jobs) 
   stage_box<R>(P.R, P.pitch, w, h, rbase, y0, Z.nrc, sR);
   __syncthreads();
   // ---- stage 2: window statistics (left windows at x0 + t; right windows at rbase + R + t)
-  window_stats<R>(sL, Z.nlc, cs, cs2, sumL, invL, Z.gx);
-  window_stats<R>(sR, Z.nrc, cs, cs2, sumR, invR, Z.nrs);
+  window_stats<R>(sL, Z.nlc, cs, cs2, sumL, invL, nullptr, Z.gx);
+  window_stats<R>(sR, Z.nrc, cs, cs2, nullptr, nullptr, statR, Z.nrs);
 
   // ---- stage 3: sliding ZNCC + WTA
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int xw = x0 + warp * TX;          // first output column of this warp
+  if (xw >= w) return;                    // all of this warp's columns lie beyond the image
   const int lc0 = warp * TX;              // staged left column of u = xw - R
   const long long N = (long long)(2 * R + 1) * (2 * R + 1);
   int dd[KD], rc0[KD];
@@ -194,40 +201,54 @@ zncc_wta_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ jobs) 
       const int x = xw + t;
       const int sl = sumL[yi * Z.gx + lc0 + t];
       const float il = invL[yi * Z.gx + lc0 + t];
-      int bk = INT_MIN, sk = INT_MIN, bd = 0x7FFFFFFF;
+      // the lane's best (and second) candidate, compared as floats: ties keep the lower k,
+      // i.e. the lower d; -4 marks "none" (every score lies in [-1, 1])
+      float bv = -4.0f, sv = -4.0f;
+      int bd = 0x7FFFFFFF;
 #pragma unroll
       for (int k = 0; k < KD; ++k) {
         const int d = lane + 32 * k;
-        const int rs = yi * Z.nrs + lc0 + t - dd[k] + (D - 1);  // right window at x - d
-        const long long n = N * (long long)run[k] - (long long)sl * (long long)sumR[rs];
-        const float rho = (float)n * il * invR[rs];
+        const int2 sr = statR[yi * Z.nrs + lc0 + t - dd[k] + (D - 1)];  // right window at x - d
+        const long long n = N * (long long)run[k] - (long long)sl * (long long)sr.x;
+        const float rho = (float)n * il * __int_as_float(sr.y);
         const bool valid = d < D && d <= x && x < w;
-        if constexpr (COST) {
+        if constexpr (MODE == 2) {
           if (d < D && x < w && y < h) P.cost[((size_t)y * w + x) * D + d] = d <= x ? 1.0f - rho : 2.0f;
         }
-        const int key = valid ? order_key(rho) : INT_MIN;
-        if (key > bk) { sk = bk; bk = key; bd = d; }
-        else if (key > sk) { sk = key; }
+        if (valid && rho > bv) {
+          if constexpr (MODE == 1) sv = bv;
+          bv = rho;
+          bd = d;
+        } else if (MODE == 1 && valid && rho > sv) {
+          sv = rho;
+        }
       }
+      const int bk = bv > -3.0f ? order_key(bv) : INT_MIN;
       const int gbest = __reduce_max_sync(0xFFFFFFFFu, bk);
       const unsigned dstar = __reduce_min_sync(0xFFFFFFFFu, (bk == gbest) ? (unsigned)bd : 0x7FFFFFFFu);
-      const int gsec = __reduce_max_sync(0xFFFFFFFFu, ((unsigned)bd == dstar) ? sk : bk);
+      int gsec = INT_MIN;
+      if constexpr (MODE == 1) {
+        const int sk = sv > -3.0f ? order_key(sv) : INT_MIN;
+        gsec = __reduce_max_sync(0xFFFFFFFFu, ((unsigned)bd == dstar) ? sk : bk);
+      }
       if (lane == t) { my_d = (int)dstar; my_b = gbest; my_s = gsec; }
     }
     const int x = xw + lane;
     if (lane < TX && x < w && y < h) {
       const size_t o = (size_t)y * w + x;
       P.disp[o] = (int16_t)my_d;
-      if (P.best) P.best[o] = key_value(my_b);
-      if (P.second) P.second[o] = key_value(my_s);
+      if constexpr (MODE == 1) {
+        if (P.best) P.best[o] = key_value(my_b);
+        if (P.second) P.second[o] = key_value(my_s);
+      }
     }
   }
 }
 
-template <int R, int KD, bool COST>
+template <int R, int KD, int MODE>
 cudaError_t launch_rk(const ZPair* p, const ZJob* j, int n, int maxD, cudaStream_t st) {
-  constexpr int TX = KD == 1 ? 32 : KD == 2 ? 24 : KD == 3 ? 16 : 12;
-  auto kern = zncc_wta_kernel<R, KD, TX, COST>;
+  constexpr int TX = KD == 1 ? 32 : KD == 2 ? 20 : KD == 3 ? 16 : 12;  // == zncc_tx(KD)
+  auto kern = zncc_wta_kernel<R, KD, TX, MODE>;
   const size_t smem = zlayout(R, maxD, TX).total;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -243,21 +264,30 @@ cudaError_t launch_rk(const ZPair* p, const ZJob* j, int n, int maxD, cudaStream
 
 #define SV_CAT2(a, b) a##b
 #define SV_CAT(a, b) SV_CAT2(a, b)
-template <bool COST>
+// Internal linkage: every radius has its own translation unit, and a template with external
+// linkage instantiated in all of them would be merged by the linker into one radius's copy.
+namespace {
+template <int MODE>
 cudaError_t launch_r(const ZPair* p, const ZJob* j, int n, int maxD, cudaStream_t st) {
   switch (zncc_kd(maxD)) {
-    case 1: return launch_rk<SV_ZNCC_R, 1, COST>(p, j, n, maxD, st);
-    case 2: return launch_rk<SV_ZNCC_R, 2, COST>(p, j, n, maxD, st);
-    case 3: return launch_rk<SV_ZNCC_R, 3, COST>(p, j, n, maxD, st);
-    case 4: return launch_rk<SV_ZNCC_R, 4, COST>(p, j, n, maxD, st);
+    case 1: return launch_rk<SV_ZNCC_R, 1, MODE>(p, j, n, maxD, st);
+    case 2: return launch_rk<SV_ZNCC_R, 2, MODE>(p, j, n, maxD, st);
+    case 3: return launch_rk<SV_ZNCC_R, 3, MODE>(p, j, n, maxD, st);
+    case 4: return launch_rk<SV_ZNCC_R, 4, MODE>(p, j, n, maxD, st);
   }
   return cudaErrorInvalidValue;
 }
+}  // namespace
 
-cudaError_t SV_CAT(launch_zncc_wta_r, SV_ZNCC_R)(const ZPair* p, const ZJob* j, int n, int maxD, bool with_cost,
+cudaError_t SV_CAT(launch_zncc_wta_r, SV_ZNCC_R)(const ZPair* p, const ZJob* j, int n, int maxD, int mode,
                                                   cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  return with_cost ? launch_r<true>(p, j, n, maxD, st) : launch_r<false>(p, j, n, maxD, st);
+  switch (mode) {
+    case 0: return launch_r<0>(p, j, n, maxD, st);
+    case 1: return launch_r<1>(p, j, n, maxD, st);
+    case 2: return launch_r<2>(p, j, n, maxD, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace sv
