@@ -625,11 +625,19 @@ def run_ours(args):
                 Lt = train_step(t)
             e1.record(st)
             st.synchronize()
+            # one more step with per-kernel events: where the step's time goes
+            tctx.profile(True)
+            tctx.profile_read(reset=True)
+            train_step(3 + tsteps)
+            st.synchronize()
+            tprof = tctx.profile_read(reset=True)
+            tctx.profile(False)
         tms = e0.elapsed_time(e1) / tsteps
         train = {"workload": f"training step: {nt} synthetic 1242x375 pairs, 16/32/64 net, BF16 tensor-core forward, "
                              "FP32 master weights and backward (encoder recomputed), smooth-L1 + 1e-3 KL, Adam",
                  "ms_per_step": tms, "steps_per_s": 1e3 / tms, "pairs_per_s": nt * 1e3 / tms,
-                 "loss_last": float(Lt.item())}
+                 "loss_last": float(Lt.item()),
+                 "kernel_ms_profiled_step": {k: round(v[1], 4) for k, v in sorted(tprof.items(), key=lambda kv: -kv[1][1])}}
         tctx.close()
 
     table1 = None

@@ -96,6 +96,7 @@ struct Ctx {
   DevBuf adam_m, adam_v;
   // differentiation form: state saved by the last training forward
   DevBuf train_saved, train_scratch, loss_acc, train_mu;
+  DevBuf wgrad_slots;            // per-CTA partial weight gradients of the FP32 backward
   std::vector<sv_pair> train_pairs;
   std::vector<const void*> train_coarse;
   std::vector<size_t> train_off;
@@ -247,7 +248,7 @@ struct Ctx {
     for (auto& b : act) b.release();
     for (auto& b : tc_act) b.release();
     tc_tables.release(); adam_m.release(); adam_v.release();
-    train_saved.release(); train_scratch.release(); loss_acc.release(); train_mu.release();
+    train_saved.release(); train_scratch.release(); loss_acc.release(); train_mu.release(); wgrad_slots.release();
   }
 };
 

@@ -204,6 +204,18 @@ cudaError_t launch_train_latent_bf16(const __nv_bfloat16* e3, int P, int Ci, con
                                      float* lv, __nv_bfloat16* z, cudaStream_t st);
 cudaError_t launch_bf16_to_f32(const __nv_bfloat16* a, float* b, size_t n, cudaStream_t st);
 
+// FP32 gradients of a conv read through its input view (bwd_tiled.cu): dgrad writes (or adds
+// to) the input gradient, masked by the input activation's ReLU; wgrad adds the weight and
+// bias gradients, reducing per-CTA partial sums (slots, wgrad_slot_floats floats) in a fixed
+// order.
+cudaError_t launch_dgrad_tiled(const float* gout, int Ho, int Wo, int Co, const float* w, int ks, int mode,
+                               const float* mask_act, int Hi, int Wi, int Ci, int accumulate, float* gin,
+                               cudaStream_t st);
+cudaError_t launch_wgrad_tiled(const float* gout, int Ho, int Wo, int Co, const float* in, int Hi, int Wi, int Ci,
+                               int ks, int mode, float* gw, float* gb, float* slots, size_t slot_cap,
+                               cudaStream_t st);
+size_t wgrad_slot_floats(int Ho, int Wo, int Co, int Ci, int ks);
+
 // latent heads: mu = 1x1(e3) + b; optionally logvar and z = mu + eps * exp(lv / 2).
 template <typename T>
 cudaError_t launch_latent(const T* e3, int P, int Ci, const T* wmu, const T* bmu, const T* wlv, const T* blv,

@@ -3,6 +3,7 @@
 // upsampling (the encoder is recomputed, not stored), loss and Adam.  FP32 for SV_FP32 /
 // SV_BF16 contexts, FP64 for SV_FP64_CHECK contexts.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "sv_ctx.cuh"
@@ -193,6 +194,29 @@ sv_status Ctx::train_backward(const void* const* gY, const void* const* gmu_ext,
     need = std::max(need, t);
   }
   if ((s = cuda(train_scratch.ensure(need * sizeof(T)), "alloc backward scratch"))) return s;
+  // FP32: the tiled gradient kernels (per-CTA weight-gradient slots, reduced in a fixed
+  // order); FP64 (the check form): the plain gather kernels
+  if constexpr (std::is_same<T, float>::value) {
+    size_t maxw = 0;
+    for (int l = 0; l < L_COUNT; ++l)
+      maxw = std::max(maxw, (size_t)net.cout(l) * net.ks(l) * net.ks(l) * net.cin(l) + net.cout(l));
+    if ((s = cuda(wgrad_slots.ensure(4 * 152 * maxw * sizeof(float)), "alloc weight-gradient slots"))) return s;
+  }
+  auto DG = [&](const T* go, int Ho, int Wo, int Co, const T* wt, int ks, int mode, const T* mask, int Hi, int Wi, int Ci,
+                int accum, T* gi) -> cudaError_t {
+    if constexpr (std::is_same<T, float>::value)
+      return launch_dgrad_tiled(go, Ho, Wo, Co, wt, ks, mode, mask, Hi, Wi, Ci, accum, gi, st);
+    else
+      return launch_dgrad<T>(go, Ho, Wo, Co, wt, ks, mode, mask, Hi, Wi, Ci, accum, gi, st);
+  };
+  auto WG = [&](const T* go, int Ho, int Wo, int Co, const T* in, int Hi, int Wi, int Ci, int ks, int mode, T* gw,
+                T* gb) -> cudaError_t {
+    if constexpr (std::is_same<T, float>::value)
+      return launch_wgrad_tiled(go, Ho, Wo, Co, in, Hi, Wi, Ci, ks, mode, gw, gb, (float*)wgrad_slots.p,
+                                wgrad_slots.n / sizeof(float), st);
+    else
+      return launch_wgrad<T>(go, Ho, Wo, Co, in, Hi, Wi, Ci, ks, mode, gw, gb, st);
+  };
   for (int i = 0; i < n; ++i) {
     const sv_pair& p = train_pairs[i];
     const Levels lv(p.height, p.width);
@@ -222,21 +246,21 @@ sv_status Ctx::train_backward(const void* const* gY, const void* const* gmu_ext,
     if ((s = cuda((expr), name))) return s;    \
   }
     // final: Y = U + conv(d3) + b
-    SV_BW("bwd_final_dgrad", launch_dgrad<T>(gYi, H, W, 1, Wl(L_FINAL), 3, CM_S1, sv[S_D3], H, W, net.dec[2], 0, gd3, st));
-    SV_BW("bwd_final_wgrad", launch_wgrad<T>(gYi, H, W, 1, sv[S_D3], H, W, net.dec[2], 3, CM_S1, GW(L_FINAL), GB(L_FINAL), st));
+    SV_BW("bwd_final_dgrad", DG(gYi, H, W, 1, Wl(L_FINAL), 3, CM_S1, sv[S_D3], H, W, net.dec[2], 0, gd3));
+    SV_BW("bwd_final_wgrad", WG(gYi, H, W, 1, sv[S_D3], H, W, net.dec[2], 3, CM_S1, GW(L_FINAL), GB(L_FINAL)));
     // decoder (nearest x2 + crop + 3x3 conv + ReLU)
-    SV_BW("bwd_dec3_dgrad", launch_dgrad<T>(gd3, H, W, net.dec[2], Wl(L_DEC3), 3, CM_UP2, sv[S_D2], lv.H[1], lv.W[1],
-                                            net.dec[1], 0, gd2, st));
-    SV_BW("bwd_dec3_wgrad", launch_wgrad<T>(gd3, H, W, net.dec[2], sv[S_D2], lv.H[1], lv.W[1], net.dec[1], 3, CM_UP2,
-                                            GW(L_DEC3), GB(L_DEC3), st));
-    SV_BW("bwd_dec2_dgrad", launch_dgrad<T>(gd2, lv.H[1], lv.W[1], net.dec[1], Wl(L_DEC2), 3, CM_UP2, sv[S_D1], lv.H[2],
-                                            lv.W[2], net.dec[0], 0, gd1, st));
-    SV_BW("bwd_dec2_wgrad", launch_wgrad<T>(gd2, lv.H[1], lv.W[1], net.dec[1], sv[S_D1], lv.H[2], lv.W[2], net.dec[0], 3,
-                                            CM_UP2, GW(L_DEC2), GB(L_DEC2), st));
-    SV_BW("bwd_dec1_dgrad", launch_dgrad<T>(gd1, lv.H[2], lv.W[2], net.dec[0], Wl(L_DEC1), 3, CM_UP2, nullptr, lv.H[3],
-                                            lv.W[3], net.lat, 0, gz, st));
-    SV_BW("bwd_dec1_wgrad", launch_wgrad<T>(gd1, lv.H[2], lv.W[2], net.dec[0], sv[S_Z], lv.H[3], lv.W[3], net.lat, 3,
-                                            CM_UP2, GW(L_DEC1), GB(L_DEC1), st));
+    SV_BW("bwd_dec3_dgrad", DG(gd3, H, W, net.dec[2], Wl(L_DEC3), 3, CM_UP2, sv[S_D2], lv.H[1], lv.W[1],
+                                            net.dec[1], 0, gd2));
+    SV_BW("bwd_dec3_wgrad", WG(gd3, H, W, net.dec[2], sv[S_D2], lv.H[1], lv.W[1], net.dec[1], 3, CM_UP2,
+                                            GW(L_DEC3), GB(L_DEC3)));
+    SV_BW("bwd_dec2_dgrad", DG(gd2, lv.H[1], lv.W[1], net.dec[1], Wl(L_DEC2), 3, CM_UP2, sv[S_D1], lv.H[2],
+                                            lv.W[2], net.dec[0], 0, gd1));
+    SV_BW("bwd_dec2_wgrad", WG(gd2, lv.H[1], lv.W[1], net.dec[1], sv[S_D1], lv.H[2], lv.W[2], net.dec[0], 3,
+                                            CM_UP2, GW(L_DEC2), GB(L_DEC2)));
+    SV_BW("bwd_dec1_dgrad", DG(gd1, lv.H[2], lv.W[2], net.dec[0], Wl(L_DEC1), 3, CM_UP2, nullptr, lv.H[3],
+                                            lv.W[3], net.lat, 0, gz));
+    SV_BW("bwd_dec1_wgrad", WG(gd1, lv.H[2], lv.W[2], net.dec[0], sv[S_Z], lv.H[3], lv.W[3], net.lat, 3,
+                                            CM_UP2, GW(L_DEC1), GB(L_DEC1)));
     // latent: z = mu + eps exp(lv / 2), plus the loss's own terms
     SV_BW("bwd_latent", launch_latent_bwd<T>(gz, sv[S_EPS], sv[S_LV], gmu_ext && gmu_ext[i] ? (const T*)gmu_ext[i] : nullptr,
                                              glv_ext && glv_ext[i] ? (const T*)glv_ext[i] : nullptr, P3 * net.lat, gmu, glv, st));
@@ -262,30 +286,30 @@ sv_status Ctx::train_backward(const void* const* gY, const void* const* gmu_ext,
     }
     const T *e1 = rec[0], *e2 = rec[1], *e3 = rec[2];
     // latent heads (1x1): e3 -> mu, e3 -> logvar
-    SV_BW("bwd_mu_dgrad", launch_dgrad<T>(gmu, lv.H[3], lv.W[3], net.lat, Wl(L_MU), 1, CM_S1, e3, lv.H[3], lv.W[3],
-                                          net.enc[2], 0, ge3, st));
-    SV_BW("bwd_lv_dgrad", launch_dgrad<T>(glv, lv.H[3], lv.W[3], net.lat, Wl(L_LV), 1, CM_S1, e3, lv.H[3], lv.W[3],
-                                          net.enc[2], 1, ge3, st));
-    SV_BW("bwd_mu_wgrad", launch_wgrad<T>(gmu, lv.H[3], lv.W[3], net.lat, e3, lv.H[3], lv.W[3], net.enc[2], 1, CM_S1,
-                                          GW(L_MU), GB(L_MU), st));
-    SV_BW("bwd_lv_wgrad", launch_wgrad<T>(glv, lv.H[3], lv.W[3], net.lat, e3, lv.H[3], lv.W[3], net.enc[2], 1, CM_S1,
-                                          GW(L_LV), GB(L_LV), st));
+    SV_BW("bwd_mu_dgrad", DG(gmu, lv.H[3], lv.W[3], net.lat, Wl(L_MU), 1, CM_S1, e3, lv.H[3], lv.W[3],
+                                          net.enc[2], 0, ge3));
+    SV_BW("bwd_lv_dgrad", DG(glv, lv.H[3], lv.W[3], net.lat, Wl(L_LV), 1, CM_S1, e3, lv.H[3], lv.W[3],
+                                          net.enc[2], 1, ge3));
+    SV_BW("bwd_mu_wgrad", WG(gmu, lv.H[3], lv.W[3], net.lat, e3, lv.H[3], lv.W[3], net.enc[2], 1, CM_S1,
+                                          GW(L_MU), GB(L_MU)));
+    SV_BW("bwd_lv_wgrad", WG(glv, lv.H[3], lv.W[3], net.lat, e3, lv.H[3], lv.W[3], net.enc[2], 1, CM_S1,
+                                          GW(L_LV), GB(L_LV)));
     // encoder (3x3 stride 2 + ReLU)
-    SV_BW("bwd_enc3_dgrad", launch_dgrad<T>(ge3, lv.H[3], lv.W[3], net.enc[2], Wl(L_ENC3), 3, CM_S2, e2, lv.H[2], lv.W[2],
-                                            net.enc[1], 0, ge2, st));
-    SV_BW("bwd_enc3_wgrad", launch_wgrad<T>(ge3, lv.H[3], lv.W[3], net.enc[2], e2, lv.H[2], lv.W[2], net.enc[1], 3, CM_S2,
-                                            GW(L_ENC3), GB(L_ENC3), st));
-    SV_BW("bwd_enc2_dgrad", launch_dgrad<T>(ge2, lv.H[2], lv.W[2], net.enc[1], Wl(L_ENC2), 3, CM_S2, e1, lv.H[1], lv.W[1],
-                                            net.enc[0], 0, ge1, st));
-    SV_BW("bwd_enc2_wgrad", launch_wgrad<T>(ge2, lv.H[2], lv.W[2], net.enc[1], e1, lv.H[1], lv.W[1], net.enc[0], 3, CM_S2,
-                                            GW(L_ENC2), GB(L_ENC2), st));
+    SV_BW("bwd_enc3_dgrad", DG(ge3, lv.H[3], lv.W[3], net.enc[2], Wl(L_ENC3), 3, CM_S2, e2, lv.H[2], lv.W[2],
+                                            net.enc[1], 0, ge2));
+    SV_BW("bwd_enc3_wgrad", WG(ge3, lv.H[3], lv.W[3], net.enc[2], e2, lv.H[2], lv.W[2], net.enc[1], 3, CM_S2,
+                                            GW(L_ENC3), GB(L_ENC3)));
+    SV_BW("bwd_enc2_dgrad", DG(ge2, lv.H[2], lv.W[2], net.enc[1], Wl(L_ENC2), 3, CM_S2, e1, lv.H[1], lv.W[1],
+                                            net.enc[0], 0, ge1));
+    SV_BW("bwd_enc2_wgrad", WG(ge2, lv.H[2], lv.W[2], net.enc[1], e1, lv.H[1], lv.W[1], net.enc[0], 3, CM_S2,
+                                            GW(L_ENC2), GB(L_ENC2)));
     SV_BW("bwd_build_x0", launch_build_x0<T>(p.left, p.pitch, W, H, coarse, w, h, x0, st));
-    SV_BW("bwd_enc1_wgrad", launch_wgrad<T>(ge1, lv.H[1], lv.W[1], net.enc[0], x0, H, W, 2, 3, CM_S2, GW(L_ENC1),
-                                            GB(L_ENC1), st));
+    SV_BW("bwd_enc1_wgrad", WG(ge1, lv.H[1], lv.W[1], net.enc[0], x0, H, W, 2, 3, CM_S2, GW(L_ENC1),
+                                            GB(L_ENC1)));
     if (gcoarse && gcoarse[i]) {
       // through the network input (channel U / 256) and the residual Y = U + ...
-      SV_BW("bwd_enc1_dgrad", launch_dgrad<T>(ge1, lv.H[1], lv.W[1], net.enc[0], Wl(L_ENC1), 3, CM_S2, nullptr, H, W, 2, 0,
-                                              gx0, st));
+      SV_BW("bwd_enc1_dgrad", DG(ge1, lv.H[1], lv.W[1], net.enc[0], Wl(L_ENC1), 3, CM_S2, nullptr, H, W, 2, 0,
+                                              gx0));
       SV_BW("bwd_upsample4", launch_up4_bwd<T>(gYi, gx0, W, H, w, h, (T*)gcoarse[i], st));
     }
 #undef SV_BW

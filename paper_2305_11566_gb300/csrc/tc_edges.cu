@@ -681,23 +681,36 @@ __global__ void __launch_bounds__(256) edge_up2fix(const UpFixPair* __restrict__
 }
 
 // Training latent: one thread per (latent pixel, channel).
+// A thread per (pixel, output channel).  staged: the weights of both heads are staged
+// transposed in shared memory ([ci][co]: consecutive threads read consecutive output
+// channels); else (widths whose weights do not fit) read from global memory.
 __global__ void train_latent_bf16(const bf16* __restrict__ e3, int P, int Ci, const float* __restrict__ wmu,
                                   const float* __restrict__ bmu, const float* __restrict__ wlv,
                                   const float* __restrict__ blv, int lat, const float* __restrict__ eps,
-                                  float* __restrict__ mu, float* __restrict__ lv, bf16* __restrict__ z) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (size_t)P * lat) return;
-  const int co = (int)(i % lat);
-  const bf16* x = e3 + (i / lat) * Ci;
-  float m = bmu[co], l = blv[co];
-  for (int ci = 0; ci < Ci; ++ci) {
-    const float xv = __bfloat162float(x[ci]);
-    m = fmaf(wmu[(size_t)co * Ci + ci], xv, m);
-    l = fmaf(wlv[(size_t)co * Ci + ci], xv, l);
+                                  float* __restrict__ mu, float* __restrict__ lv, bf16* __restrict__ z, int staged) {
+  extern __shared__ float tl_sm[];
+  float* wm = tl_sm;              // [Ci][lat]
+  float* wl = tl_sm + Ci * lat;   // [Ci][lat]
+  for (int e = threadIdx.x; staged && e < Ci * lat; e += blockDim.x) {
+    const int ci = e / lat, co = e - ci * lat;
+    wm[e] = wmu[(size_t)co * Ci + ci];
+    wl[e] = wlv[(size_t)co * Ci + ci];
   }
-  mu[i] = m;
-  lv[i] = l;
-  z[i] = __float2bfloat16_rn(m + eps[i] * expf(0.5f * l));
+  __syncthreads();
+  const size_t n = (size_t)P * lat;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int co = (int)(i % lat);
+    const bf16* x = e3 + (i / lat) * Ci;
+    float m = bmu[co], l = blv[co];
+    for (int ci = 0; ci < Ci; ++ci) {
+      const float xv = __bfloat162float(x[ci]);
+      m = fmaf(staged ? wm[ci * lat + co] : wmu[(size_t)co * Ci + ci], xv, m);
+      l = fmaf(staged ? wl[ci * lat + co] : wlv[(size_t)co * Ci + ci], xv, l);
+    }
+    mu[i] = m;
+    lv[i] = l;
+    z[i] = __float2bfloat16_rn(m + eps[i] * expf(0.5f * l));
+  }
 }
 
 __global__ void bf16_to_f32(const bf16* __restrict__ a, float* __restrict__ b, size_t n) {
@@ -711,7 +724,12 @@ cudaError_t launch_train_latent_bf16(const bf16* e3, int P, int Ci, const float*
                                      const float* wlv, const float* blv, int lat, const float* eps, float* mu,
                                      float* lv, bf16* z, cudaStream_t st) {
   const size_t n = (size_t)P * lat;
-  train_latent_bf16<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e3, P, Ci, wmu, bmu, wlv, blv, lat, eps, mu, lv, z);
+  const bool staged = 2 * sizeof(float) * Ci * lat <= 160 * 1024;
+  const size_t smem = staged ? 2 * sizeof(float) * Ci * lat : 0;
+  cudaError_t e = cudaFuncSetAttribute(train_latent_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 4 * 152);
+  train_latent_bf16<<<grid, 256, smem, st>>>(e3, P, Ci, wmu, bmu, wlv, blv, lat, eps, mu, lv, z, staged ? 1 : 0);
   return cudaGetLastError();
 }
 
