@@ -224,8 +224,10 @@ def test_backward_without_forward_is_a_state_error(svlib):
 def test_bf16_training_step_matches_oracle(svlib):
     """BF16 forward on the tensor cores with FP32 master weights (the training form of the
     batched path): the training forward within the BF16 output bar of the FP64 oracle,
-    the FP32 backward's gradient aligned with the oracle's (cosine >= 0.99 per layer, max
-    deviation <= 15% of the layer's largest entry), and a few Adam steps lower the loss."""
+    the FP32 backward's gradient aligned with the oracle's (cosine >= 0.998 per layer, max
+    deviation <= 8% of the layer's largest entry: the BF16 activations the backward reads
+    leave up to ~5% on the logvar head, whose gradient is the smallest), and a few Adam
+    steps lower the loss."""
     shape, params, _, _, _, k, D = case()
     pairs = [synth.make_pair(W, H, 40.0, 950 + W) for W, H in ((256, 128), (130, 67))]
     ctx = binding.Context(shape, k, "bf16")
@@ -260,8 +262,8 @@ def test_bf16_training_step_matches_oracle(svlib):
             n = int(np.prod(wshape))
             a, b = gpn[ow:ow + n], go[ow:ow + n]
             cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
-            assert cos >= 0.99, (name, cos)
-            assert np.abs(a - b).max() <= 0.15 * np.abs(b).max(), name
+            assert cos >= 0.998, (name, cos)
+            assert np.abs(a - b).max() <= 0.08 * np.abs(b).max(), name
         # a few steps of the autograd route on the BF16 form
         w = torch.from_numpy(params).cuda().requires_grad_(True)
         losses = []
