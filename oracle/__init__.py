@@ -27,6 +27,11 @@ Parity status per function (what pins each one, in tests/test_oracle_*.py):
   census_volume    hand-made 3 x 3 codes; invariance under increasing intensity maps; zero
                    cost of an image against itself and of a constant shift at its disparity;
                    the mirror identity (both images flipped, roles swapped)
+  e4m3             torch's float8_e4m3fn conversion (round to nearest even) over the whole
+                   finite range, saturation above 448
+  refine_forward_q with its roundings off: refine_forward (the folded decoder interior and
+                   the unfolded border recompute together equal the plain nearest-x2 conv);
+                   activations on the E4M3 grid; the BF16 form's bar against refine_forward
   t1_layer         torch.nn.functional conv2d / conv_transpose2d / leaky_relu in FP64
   t1_inputs        torch avg_pool2d and interpolate (bilinear, half-pixel centres) where the
                    sizes are exact multiples
@@ -84,6 +89,9 @@ def lib():
         L.orc_smp.argtypes = [P, c_int, c_int, c_int, P]
         L.orc_median3.argtypes = [P, c_int, c_int, P]
         L.orc_census_volume.argtypes = [P, P, c_int, c_int, c_int, c_int, P]
+        L.orc_e4m3.argtypes = [c_double]
+        L.orc_e4m3.restype = c_double
+        L.orc_refine_forward_q.argtypes = [P, P, P, c_int, c_int, c_int, P, c_int, c_int, c_int, P, c_int, P]
         L.orc_t1_param_offset.argtypes = [c_int, c_int]
         L.orc_t1_param_offset.restype = c_size_t
         L.orc_t1_param_count.restype = c_size_t
@@ -453,6 +461,39 @@ def refine_forward(shape, params: np.ndarray, left: np.ndarray, coarse: np.ndarr
 
 
 ACTIVATIONS = ["U", "e1", "e2", "e3", "mu", "logvar", "z", "d1", "d2", "d3", "Y"]
+
+
+def e4m3(x: float) -> float:
+    """E4M3 (FP8) rounding of the quantised form: nearest, ties to even, saturating at 448."""
+    return float(lib().orc_e4m3(float(x)))
+
+
+def refine_forward_q(shape, params: np.ndarray, left: np.ndarray, coarse: np.ndarray, quant: bool = True,
+                     act: str | None = None):
+    """The FP8 form's refinement (inference): {"Y": [H, W]} and, with `act`, that activation
+    ("e1" .. "d3") as the layer passes it on.  quant=False skips every rounding."""
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    left = np.ascontiguousarray(left, dtype=np.uint8)
+    H, W = left.shape
+    c = np.ascontiguousarray(coarse, dtype=np.float64)
+    h, w = c.shape
+    w7 = widths7(shape)
+    Y = np.zeros((H, W), dtype=np.float64)
+    names = ["e1", "e2", "e3", "z", "d1", "d2", "d3"]
+    which, buf = -1, None
+    if act is not None:
+        which = names.index(act)
+        L0, L1, L2, L3 = level_sizes(H, W)
+        c1, c2, c3 = shape.enc
+        d1, d2, d3 = shape.dec
+        shp = {"e1": (*L1, c1), "e2": (*L2, c2), "e3": (*L3, c3), "z": (*L3, shape.latent), "d1": (*L2, d1),
+               "d2": (*L1, d2), "d3": (*L0, d3)}[act]
+        buf = np.zeros(shp, dtype=np.float64)
+    lib().orc_refine_forward_q(_p(w7), _p(params), _p(left), W, H, W, _p(c), w, h, int(quant), _p(Y), which, _opt(buf))
+    out = {"Y": Y}
+    if act is not None:
+        out[act] = buf
+    return out
 
 
 def refine_activation(shape, params, left, coarse, which: str, eps=None) -> np.ndarray:

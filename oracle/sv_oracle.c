@@ -31,6 +31,7 @@
  *   orc_census_volume    census matching cost (Sec. IV-C settings S1, S2)
  *   orc_dt_aggregate     domain-transform cost aggregation (Sec. IV-C settings S1, S3)
  *   orc_t1_*             the paper's Table I network (Sec. III-B1) and its loss (Eq. 8-11)
+ *   orc_refine_forward_q the FP8 (E4M3) quantised refinement (Sec. V future work) and orc_e4m3
  *
  * Readings of the paper (where it is silent, garbled or inconsistent):
  *   - cost range: Eq. 1 gives 1 - rho, which lies in [0, 2], not [0, 1]; the
@@ -1071,4 +1072,223 @@ double orc_t1_loss(const double* Y, const float* gt, const uint8_t* noc, size_t 
     parts[1] = l2;
   }
   return 256.0 * (l1 + l2);
+}
+
+/* ------------------------------------------------------------------ quantised refinement
+ * Sec. V (future work: "compress the network through quantization").  The paper gives no
+ * scheme; the one defined here is the FP8 form of this build, written out step by step:
+ *   - number format E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits, subnormals,
+ *     largest finite 448, no infinity); rounding to nearest, ties to even, saturating at 448;
+ *   - weights of a tensor-core layer quantised per output channel co: scale s[co] =
+ *     max |v| / 448 over the values v the layer multiplies (FP32, 1 if all are zero), codes
+ *     e4m3(v / s[co]) (the division in FP32);  for the nearest-x2 decoder layers the values
+ *     are the phase-folded weights (the 3 x 3 kernel rows / columns {0} and {1, 2} for phase
+ *     0, {0, 1} and {2} for phase 1, summed in FP32 in row-major tap order), for stride-2
+ *     and 1 x 1 layers the weights themselves;
+ *   - activations between layers (e1, e2, e3, z, d1, d2) rounded to E4M3 with scale 1; e1
+ *     first to BF16 (the first layer's output format), d3 to BF16 (the last layer's input
+ *     format is BF16, as in the BF16 form);
+ *   - a layer's output: relu(s[co] * sum(a_code * w_code) + b[co]) (no relu after the
+ *     latent head); inference uses z = mu;
+ *   - decoder border pixels left wrong by the phase folding (the last output row of an odd
+ *     height, the last column of an odd width) use the 3 x 3 weights unfolded, quantised
+ *     per output channel the same way, on the cropped up-sampled input;
+ *   - the first layer (2 input channels) and the final conv keep FP32 weights (FP64 here),
+ *     as in the BF16 form.
+ * quant = 0 skips every rounding (codes = values, scales 1): the result must then equal
+ * orc_refine_forward up to the order of the sums. */
+
+/* E4M3 round to nearest even, saturating to +-448. */
+double orc_e4m3(double x) {
+  if (x != x) return x;
+  const double a = fabs(x);
+  if (a == 0.0) return x;
+  if (a >= 448.0) return x < 0 ? -448.0 : 448.0;
+  int e;
+  frexp(a, &e);            /* a = f 2^e, f in [0.5, 1): the leading bit has weight 2^(e-1) */
+  int q = e - 1 - 3;       /* quantum of a normal number: 3 mantissa bits below the leading one */
+  if (q < -9) q = -9;      /* subnormal quantum 2^-9 (exponent field 0) */
+  const double r = ldexp(nearbyint(ldexp(a, -q)), q);  /* default rounding mode: to nearest even */
+  return x < 0 ? -(r > 448.0 ? 448.0 : r) : (r > 448.0 ? 448.0 : r);
+}
+
+/* BF16 round to nearest even of a double (through FP32, as the GPU stores FP32 results). */
+static double orc_bf16(double x) {
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return f;
+  u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+  memcpy(&f, &u, 4);
+  return f;
+}
+
+/* phase-folded weights of a nearest-x2 + 3 x 3 layer, FP32 sums in row-major tap order:
+ * Wf[((ph * 4 + t) * co_n + co) * ci_n + ci], ph = 2 py + px, t = 2 a + b */
+static void fold_weights(const float* Wt, int co_n, int ci_n, float* Wf) {
+  for (int ph = 0; ph < 4; ++ph)
+    for (int t = 0; t < 4; ++t)
+      for (int co = 0; co < co_n; ++co)
+        for (int ci = 0; ci < ci_n; ++ci) {
+          const int py = ph >> 1, px = ph & 1, a = t >> 1, b = t & 1;
+          const int ky0 = py == 0 ? (a == 0 ? 0 : 1) : (a == 0 ? 0 : 2);
+          const int ky1 = py == 0 ? (a == 0 ? 0 : 2) : (a == 0 ? 1 : 2);
+          const int kx0 = px == 0 ? (b == 0 ? 0 : 1) : (b == 0 ? 0 : 2);
+          const int kx1 = px == 0 ? (b == 0 ? 0 : 2) : (b == 0 ? 1 : 2);
+          float v = 0.f;
+          for (int ky = ky0; ky <= ky1; ++ky)
+            for (int kx = kx0; kx <= kx1; ++kx) v += Wt[((size_t)co * 9 + ky * 3 + kx) * ci_n + ci];
+          Wf[((size_t)(ph * 4 + t) * co_n + co) * ci_n + ci] = v;
+        }
+}
+
+/* per-output-channel scales and codes of n_per_co values per channel laid out
+ * [group][co][...]: values v(co, j) at vals[(g * co_n + co) * per + j] for g < groups */
+static void quantise_per_co(const float* vals, int groups, int co_n, int per, int quant, float* scale, double* codes) {
+  for (int co = 0; co < co_n; ++co) {
+    float m = 0.f;
+    for (int g = 0; g < groups; ++g)
+      for (int j = 0; j < per; ++j) {
+        const float a = fabsf(vals[((size_t)g * co_n + co) * per + j]);
+        if (a > m) m = a;
+      }
+    const float s = (quant && m > 0.f) ? m / 448.0f : 1.0f;
+    scale[co] = s;
+    for (int g = 0; g < groups; ++g)
+      for (int j = 0; j < per; ++j) {
+        const size_t i = ((size_t)g * co_n + co) * per + j;
+        codes[i] = quant ? orc_e4m3((double)(vals[i] / s)) : (double)vals[i];
+      }
+  }
+}
+
+/* one quantised conv layer: mode 0 stride 2 (3 x 3, pad 1), 1 pointwise (1 x 1), 2 nearest x2
+ * + crop + 3 x 3 (folded interior, unfolded border). in: [Hi][Wi][Ci] codes; out values. */
+static void qconv(const double* in, int Hi, int Wi, int Ci, const float* Wt, const float* bias, int Co, int mode,
+                  int Ho, int Wo, int relu, int quant, double* out) {
+  if (mode != 2) {
+    const int ks = mode == 0 ? 3 : 1, per = ks * ks * Ci;
+    float* sc = malloc(sizeof(float) * Co);
+    double* q = malloc(sizeof(double) * Co * per);
+    quantise_per_co(Wt, 1, Co, per, quant, sc, q);
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < Ho; ++y)
+      for (int x = 0; x < Wo; ++x)
+        for (int co = 0; co < Co; ++co) {
+          double acc = 0.0;
+          for (int ky = 0; ky < ks; ++ky)
+            for (int kx = 0; kx < ks; ++kx) {
+              const int iy = mode == 0 ? 2 * y + ky - 1 : y, ix = mode == 0 ? 2 * x + kx - 1 : x;
+              if (iy < 0 || ix < 0 || iy >= Hi || ix >= Wi) continue;
+              const double* ip = in + ((size_t)iy * Wi + ix) * Ci;
+              const double* wp = q + (size_t)co * per + (ky * ks + kx) * Ci;
+              for (int ci = 0; ci < Ci; ++ci) acc += ip[ci] * wp[ci];
+            }
+          double v = (double)sc[co] * acc + (double)bias[co];
+          if (relu && v < 0) v = 0;
+          out[((size_t)y * Wo + x) * Co + co] = v;
+        }
+    free(sc);
+    free(q);
+    return;
+  }
+  float* Wf = malloc(sizeof(float) * 16 * Co * Ci);
+  fold_weights(Wt, Co, Ci, Wf);
+  float* scf = malloc(sizeof(float) * Co);
+  float* scu = malloc(sizeof(float) * Co);
+  double* qf = malloc(sizeof(double) * 16 * Co * Ci);
+  double* qu = malloc(sizeof(double) * 9 * Co * Ci);
+  /* folded values of one channel: 16 groups (phase, tap) of Ci each */
+  quantise_per_co(Wf, 16, Co, Ci, quant, scf, qf);
+  quantise_per_co(Wt, 1, Co, 9 * Ci, quant, scu, qu);
+#pragma omp parallel for schedule(static)
+  for (int oy = 0; oy < Ho; ++oy)
+    for (int ox = 0; ox < Wo; ++ox) {
+      const int border = ((Ho & 1) && oy == Ho - 1) || ((Wo & 1) && ox == Wo - 1);
+      for (int co = 0; co < Co; ++co) {
+        double acc = 0.0, s;
+        if (border) {
+          for (int ky = 0; ky < 3; ++ky)
+            for (int kx = 0; kx < 3; ++kx) {
+              const int vy = oy + ky - 1, vx = ox + kx - 1;
+              if (vy < 0 || vx < 0 || vy >= Ho || vx >= Wo) continue;
+              const double* ip = in + ((size_t)(vy / 2) * Wi + vx / 2) * Ci;
+              const double* wp = qu + ((size_t)co * 9 + ky * 3 + kx) * Ci;
+              for (int ci = 0; ci < Ci; ++ci) acc += ip[ci] * wp[ci];
+            }
+          s = scu[co];
+        } else {
+          const int py = oy & 1, px = ox & 1, i = oy >> 1, j = ox >> 1, ph = 2 * py + px;
+          for (int t = 0; t < 4; ++t) {
+            const int a = t >> 1, b = t & 1, iy = i + py + a - 1, ix = j + px + b - 1;
+            if (iy < 0 || ix < 0 || iy >= Hi || ix >= Wi) continue;
+            const double* ip = in + ((size_t)iy * Wi + ix) * Ci;
+            const double* wp = qf + ((size_t)(ph * 4 + t) * Co + co) * Ci;
+            for (int ci = 0; ci < Ci; ++ci) acc += ip[ci] * wp[ci];
+          }
+          s = scf[co];
+        }
+        double v = s * acc + (double)bias[co];
+        if (relu && v < 0) v = 0;
+        out[((size_t)oy * Wo + ox) * Co + co] = v;
+      }
+    }
+  free(Wf); free(scf); free(scu); free(qf); free(qu);
+}
+
+static void round_act(double* a, size_t n, int quant, int bf16_first) {
+  if (!quant) return;
+  for (size_t i = 0; i < n; ++i) a[i] = orc_e4m3(bf16_first ? orc_bf16(a[i]) : a[i]);
+}
+
+/* The FP8 form's refinement (inference, z = mu); outputs as orc_refine_activation /
+ * orc_refine_forward: Y [H*W]; act (nullable) receives activation `which` (0 e1 .. 6 d3, the
+ * values each layer passes on: codes for e1-d2, BF16 values for d3). */
+void orc_refine_forward_q(const int* widths7, const float* params, const uint8_t* left, int W, int H, int pitch,
+                          const double* coarse, int w, int h, int quant, double* Y, int which, double* act) {
+  orc_net n = {{widths7[0], widths7[1], widths7[2]}, widths7[3], {widths7[4], widths7[5], widths7[6]}};
+  orc_acts a;
+  acts_alloc(&n, H, W, &a);
+  int co, ci, ks;
+  orc_upsample4(coarse, w, h, W, H, a.U);
+  for (int yy = 0; yy < H; ++yy)
+    for (int xx = 0; xx < W; ++xx) {
+      a.x0[((size_t)yy * W + xx) * 2 + 0] = left[(size_t)yy * pitch + xx] / 256.0;
+      a.x0[((size_t)yy * W + xx) * 2 + 1] = a.U[(size_t)yy * W + xx] / 256.0;
+    }
+  const size_t P0 = (size_t)H * W, P1 = (size_t)a.H1 * a.W1, P2 = (size_t)a.H2 * a.W2, P3 = (size_t)a.H3 * a.W3;
+  layer_dims(&n, L_ENC1, &co, &ci, &ks);
+  orc_conv2d(a.x0, H, W, 2, Wl(params, widths7, L_ENC1), Bl(params, widths7, L_ENC1), co, 3, 2, 1, 0, a.H1, a.W1, 1,
+             a.e1);
+  round_act(a.e1, P1 * n.enc[0], quant, 1);
+  qconv(a.e1, a.H1, a.W1, n.enc[0], Wl(params, widths7, L_ENC2), Bl(params, widths7, L_ENC2), n.enc[1], 0, a.H2, a.W2, 1,
+        quant, a.e2);
+  round_act(a.e2, P2 * n.enc[1], quant, 0);
+  qconv(a.e2, a.H2, a.W2, n.enc[1], Wl(params, widths7, L_ENC3), Bl(params, widths7, L_ENC3), n.enc[2], 0, a.H3, a.W3, 1,
+        quant, a.e3);
+  round_act(a.e3, P3 * n.enc[2], quant, 0);
+  qconv(a.e3, a.H3, a.W3, n.enc[2], Wl(params, widths7, L_MU), Bl(params, widths7, L_MU), n.lat, 1, a.H3, a.W3, 0, quant,
+        a.z);
+  round_act(a.z, P3 * n.lat, quant, 0);
+  qconv(a.z, a.H3, a.W3, n.lat, Wl(params, widths7, L_DEC1), Bl(params, widths7, L_DEC1), n.dec[0], 2, a.H2, a.W2, 1,
+        quant, a.d1);
+  round_act(a.d1, P2 * n.dec[0], quant, 0);
+  qconv(a.d1, a.H2, a.W2, n.dec[0], Wl(params, widths7, L_DEC2), Bl(params, widths7, L_DEC2), n.dec[1], 2, a.H1, a.W1, 1,
+        quant, a.d2);
+  round_act(a.d2, P1 * n.dec[1], quant, 0);
+  qconv(a.d2, a.H1, a.W1, n.dec[1], Wl(params, widths7, L_DEC3), Bl(params, widths7, L_DEC3), n.dec[2], 2, H, W, 1, quant,
+        a.d3);
+  if (quant)
+    for (size_t i = 0; i < P0 * n.dec[2]; ++i) a.d3[i] = orc_bf16(a.d3[i]);
+  orc_conv2d(a.d3, H, W, n.dec[2], Wl(params, widths7, L_FINAL), Bl(params, widths7, L_FINAL), 1, 3, 1, 1, 0, H, W, 0,
+             a.Y);
+  for (size_t p = 0; p < P0; ++p) a.Y[p] += a.U[p];
+  if (Y) memcpy(Y, a.Y, P0 * sizeof(double));
+  if (act && which >= 0 && which <= 6) {
+    const double* src[7] = {a.e1, a.e2, a.e3, a.z, a.d1, a.d2, a.d3};
+    const size_t nn[7] = {P1 * n.enc[0], P2 * n.enc[1], P3 * n.enc[2], P3 * n.lat, P2 * n.dec[0], P1 * n.dec[1],
+                          P0 * n.dec[2]};
+    memcpy(act, src[which], nn[which] * sizeof(double));
+  }
+  acts_free(&a);
 }
