@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="auto", choices=["auto", "fp32", "bf16", "both"])
+    ap.add_argument("--form", default="auto", choices=["auto", "fp32", "bf16", "fp8", "both"])
     ap.add_argument("--pairs", type=int, default=64, help="pairs per step per GPU")
     ap.add_argument("--distinct", type=int, default=0,
                     help="distinct synthetic pairs per GPU, cycled over the batch (0 = one per pair)")
@@ -214,6 +214,7 @@ def pair_work(shape, W, H):
     out["tc_dec3_final"] = (out["tc_dec3"][0] + dense["final"], "tensor")
     out["edge_up2fix"] = (2 * 6 * (upfix_pixels(H2, W2) * d1 * lat + upfix_pixels(H1, W1) * d2 * d1), "alu")
     out["edge_final"] = (2 * H0 * W0 * d3 + 2 * w * h + 4 * H0 * W0, "hbm")
+    out["e1_to_e4m3"] = (3 * H1 * W1 * c1, "hbm")  # FP8 form: BF16 e1 read, E4M3 codes written
     return out
 
 
@@ -276,9 +277,14 @@ def measure_sgemm_tflops():
         torch.backends.cuda.matmul.allow_tf32 = prev
 
 
-def kernel_rooflines(prof, steps, shape, sizes, pk, pk_kind, sustained, alu_peak):
+# FP8 dense tensor peak from the measured BF16 one: NVIDIA's nominal dense ratio 4.5 / 2.25.
+FP8_OVER_BF16 = 2.0
+
+
+def kernel_rooflines(prof, steps, shape, sizes, pk, pk_kind, sustained, alu_peak, fp8=False):
     """Roofline of every profiled kernel: algorithmic units of one step (summed over the
-    step's pairs) / the kernel's measured time per step, against the matching peak."""
+    step's pairs) / the kernel's measured time per step, against the matching peak (fp8:
+    the tensor-core layers against the FP8 peak, the measured BF16 peak x 2)."""
     work = {}
     for (Wp, Hp) in sizes:
         for k, (u, b) in pair_work(shape, Wp, Hp).items():
@@ -294,6 +300,8 @@ def kernel_rooflines(prof, steps, shape, sizes, pk, pk_kind, sustained, alu_peak
         elif bound == "tensor":
             key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
             ach, peak, unit, src = units / (ms / 1e3) / 1e12, pk[key], "TFLOP/s", f"{pk_kind} {key}"
+            if fp8 and name.startswith("tc_"):
+                peak, src = peak * FP8_OVER_BF16, src + " x 2 (nominal dense FP8 / BF16 ratio 4.5 / 2.25)"
         else:
             ach, peak, unit, src = units / (ms / 1e3) / 1e12, alu_peak, "TFLOP/s", "derived: " + FP32_PEAK_TFLOPS_NOTE
         table[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
@@ -466,12 +474,13 @@ def run_ours(args):
     forms = []
     if args.form in ("auto", "both"):
         forms = ["fp32"]
-        try:
-            c = binding.Context(shape, WIN, "bf16", dev)
-            c.close()
-            forms = ["fp32", "bf16"]
-        except Exception:
-            pass
+        for f in ("bf16", "fp8"):
+            try:
+                c = binding.Context(shape, WIN, f, dev)
+                c.close()
+                forms.append(f)
+            except Exception:
+                pass
     else:
         forms = [args.form]
 
@@ -490,7 +499,7 @@ def run_ours(args):
                 ctx.pipeline(dps[:1], out=outs[:1])
             torch.cuda.synchronize()
         except binding.SvError:
-            if form == "bf16":
+            if form in ("bf16", "fp8"):
                 ctx.close()
                 continue
             raise
@@ -508,7 +517,8 @@ def run_ours(args):
     tables = {}
     for form, r in results.items():
         sustained = r["ms_per_step"] * args.steps > 1000
-        tables[form] = kernel_rooflines(r["prof"], args.steps, shape, sizes, pk, pk_kind, sustained, alu_peak)
+        tables[form] = kernel_rooflines(r["prof"], args.steps, shape, sizes, pk, pk_kind, sustained, alu_peak,
+                                        fp8=form == "fp8")
     roof = dominant_roofline(tables[head])
     roof["traffic"] = measured_traffic(roof["kernel"], B)
     shares = {k: round(v[1] / sum(x[1] for x in R["prof"].values()), 4) for k, v in sorted(R["prof"].items())}
@@ -585,6 +595,14 @@ def run_ours(args):
             accuracy[form] = accuracy_report(dg, [x[1] for x in ref], [x[2] for x in ref], [x[3] for x in ref],
                                              [r["outs"][i].cpu().numpy() for i in range(n)], [x[0] for x in ref],
                                              [distinct[i].gt for i in range(n)])
+        if "fp8" in results:
+            # the FP8 form against the oracle's own quantised refinement (same WTA map), one pair
+            Yq = oracle.refine_forward_q(shape, params, distinct[0].left, ref[0][1].astype(np.float64))["Y"]
+            e = np.abs(results["fp8"]["outs"][0].cpu().numpy().astype(np.float64) - Yq)
+            accuracy["fp8"].update({"vs_quantised_oracle_max_abs_dy_px": float(e.max()),
+                                    "vs_quantised_oracle_mean_abs_dy_px": float(e.mean()),
+                                    "quantised_oracle_delta_epe_px": float(np.abs(Yq - distinct[0].gt).mean()
+                                                                           - np.abs(ref[0][0] - distinct[0].gt).mean())})
 
     # -------------------------------------------------------------- training step (differentiation form)
     train = None

@@ -61,8 +61,20 @@ typedef enum {
  * SV_FP32: FP32 CUDA-core direct convolutions (the plain method).
  * SV_BF16: implicit-GEMM convolutions on the tcgen05 tensor cores, BF16 operands,
  *          FP32 accumulation; the last conv and the residual stay FP32.
- * SV_FP64_CHECK: FP64 CUDA-core convolutions, for gradient checks on small crops. */
-typedef enum { SV_FP32 = 0, SV_BF16 = 1, SV_FP64_CHECK = 2 } sv_precision;
+ * SV_FP64_CHECK: FP64 CUDA-core convolutions, for gradient checks on small crops.
+ * SV_FP8: the quantised refinement the paper names as future work (Sec. V), inference
+ *          only: the five middle tensor-core layers (enc2, enc3, latent, dec1 .. dec3) take
+ *          E4M3 operands (tcgen05 kind::f8f6f4, FP32 accumulation).  Weights: per layer and
+ *          output channel co the scale s_co = max |w| / 448 over the channel's GEMM operand
+ *          (for dec1 .. dec3 the FP32 sums of the nearest-x2 phase folding; the border pixels
+ *          of an odd crop use the unfolded 3 x 3 weights with their own scales), codes
+ *          E4M3(w / s_co) (round to nearest even, saturating at 448).  Activations carry scale
+ *          1: e1 (BF16 from the first layer) and the outputs of enc2 .. dec2 are stored as
+ *          E4M3 codes of relu(s_co * acc + bias); dec3 writes BF16; the first and last layers,
+ *          the upsampling and the residual are as SV_BF16.  enc, latent and dec1 / dec2 widths
+ *          are multiples of 32.  sv_refine_train returns SV_ERR_UNSUPPORTED; sv_autotune
+ *          tunes only SV_BF16 contexts; sv_debug_activation returns e2 .. d2 as E4M3 bytes. */
+typedef enum { SV_FP32 = 0, SV_BF16 = 1, SV_FP64_CHECK = 2, SV_FP8 = 3 } sv_precision;
 
 /* sv_config.flags: selects the refinement network.
  * 0: the small VAE-style net described above (widths from enc_ch / latent_ch / dec_ch).

@@ -32,6 +32,10 @@ Parity status per function (what pins each one, in tests/test_oracle_*.py):
   refine_forward_q with its roundings off: refine_forward (the folded decoder interior and
                    the unfolded border recompute together equal the plain nearest-x2 conv);
                    activations on the E4M3 grid; the BF16 form's bar against refine_forward
+  qconv_layer      the layer refine_forward_q applies: chaining it layer by layer gives that
+                   forward's activations exactly; stride-2 and pointwise layers whose weights
+                   are E4M3 values times 2^-8 (each channel reaching 448 x 2^-8, so its scale
+                   is 2^-8 and every code exact) equal torch's FP64 conv2d
   t1_layer         torch.nn.functional conv2d / conv_transpose2d / leaky_relu in FP64
   t1_inputs        torch avg_pool2d and interpolate (bilinear, half-pixel centres) where the
                    sizes are exact multiples
@@ -92,6 +96,7 @@ def lib():
         L.orc_e4m3.argtypes = [c_double]
         L.orc_e4m3.restype = c_double
         L.orc_refine_forward_q.argtypes = [P, P, P, c_int, c_int, c_int, P, c_int, c_int, c_int, P, c_int, P]
+        L.orc_qconv_layer.argtypes = [P, c_int, c_int, c_int, P, P, c_int, c_int, c_int, c_int, c_int, c_int, P]
         L.orc_t1_param_offset.argtypes = [c_int, c_int]
         L.orc_t1_param_offset.restype = c_size_t
         L.orc_t1_param_count.restype = c_size_t
@@ -493,6 +498,23 @@ def refine_forward_q(shape, params: np.ndarray, left: np.ndarray, coarse: np.nda
     out = {"Y": Y}
     if act is not None:
         out[act] = buf
+    return out
+
+
+def qconv_layer(x: np.ndarray, wt: np.ndarray, b: np.ndarray, mode: int, out_hw, relu: bool = True,
+                out_round: str = "e4m3") -> np.ndarray:
+    """One FP8-form layer from the given input values x [Hi, Wi, Ci]: wt [Co, k, k, Ci] FP32
+    weights (k = 3, or 1 for mode 1), mode 0 stride-2 3 x 3, 1 pointwise, 2 nearest x2 + crop +
+    3 x 3; out_round "none", "e4m3" or "bf16".  Returns [Ho, Wo, Co]."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    wt = np.ascontiguousarray(wt, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    Hi, Wi, Ci = x.shape
+    Co = wt.shape[0]
+    Ho, Wo = out_hw
+    out = np.zeros((Ho, Wo, Co), dtype=np.float64)
+    r = {"none": 0, "e4m3": 1, "bf16": 2}[out_round]
+    lib().orc_qconv_layer(_p(x), Hi, Wi, Ci, _p(wt), _p(b), Co, mode, Ho, Wo, int(relu), r, _p(out))
     return out
 
 

@@ -1241,6 +1241,19 @@ static void round_act(double* a, size_t n, int quant, int bf16_first) {
   for (size_t i = 0; i < n; ++i) a[i] = orc_e4m3(bf16_first ? orc_bf16(a[i]) : a[i]);
 }
 
+/* One layer of the FP8 form on its own: in [Hi][Wi][Ci] (the values the previous layer passed
+ * on), the layer's FP32 weights W[co][ky][kx][ci] and bias; mode 0 stride 2 (3 x 3, pad 1),
+ * 1 pointwise, 2 nearest x2 + crop + 3 x 3; weights quantised per output channel as in
+ * orc_refine_forward_q; out_round 0 passes the values on, 1 rounds them to E4M3, 2 to BF16. */
+void orc_qconv_layer(const double* in, int Hi, int Wi, int Ci, const float* Wt, const float* bias, int Co, int mode,
+                     int Ho, int Wo, int relu, int out_round, double* out) {
+  qconv(in, Hi, Wi, Ci, Wt, bias, Co, mode, Ho, Wo, relu, 1, out);
+  const size_t n = (size_t)Ho * Wo * Co;
+  if (out_round == 1) round_act(out, n, 1, 0);
+  if (out_round == 2)
+    for (size_t i = 0; i < n; ++i) out[i] = orc_bf16(out[i]);
+}
+
 /* The FP8 form's refinement (inference, z = mu); outputs as orc_refine_activation /
  * orc_refine_forward: Y [H*W]; act (nullable) receives activation `which` (0 e1 .. 6 d3, the
  * values each layer passes on: codes for e1-d2, BF16 values for d3). */

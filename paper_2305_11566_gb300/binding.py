@@ -18,9 +18,9 @@ from . import synth
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libstereovae.so")
 
 SV_OK, SV_ERR_INVALID_ARG, SV_ERR_CUDA, SV_ERR_OOM, SV_ERR_UNSUPPORTED, SV_ERR_TIMEOUT, SV_ERR_STATE = range(7)
-SV_FP32, SV_BF16, SV_FP64_CHECK = 0, 1, 2
+SV_FP32, SV_BF16, SV_FP64_CHECK, SV_FP8 = 0, 1, 2, 3
 SV_NET_TABLE1 = 1
-PRECISIONS = {"fp32": SV_FP32, "bf16": SV_BF16, "fp64": SV_FP64_CHECK}
+PRECISIONS = {"fp32": SV_FP32, "bf16": SV_BF16, "fp64": SV_FP64_CHECK, "fp8": SV_FP8}
 
 
 class SvConfig(ctypes.Structure):
@@ -346,9 +346,14 @@ class Context:
         self._check(lib().sv_set_option(self._h, key.encode(), int(value)))
 
     def debug_activation(self, which: int, pair: int, shape) -> np.ndarray:
-        """BF16 activation of the last tensor-core refinement, as float32 [H, W, C]."""
+        """Activation of the last tensor-core refinement as float32 [H, W, C]: BF16 values, or
+        on an FP8 context the E4M3 codes of e2 .. d2 (which 1 .. 5) decoded."""
         import torch
         n = int(np.prod(shape))
+        if self.precision == "fp8" and 1 <= which <= 5:
+            buf = torch.empty(n, dtype=torch.uint8)
+            self._check(lib().sv_debug_activation(self._h, which, pair, c_void_p(buf.data_ptr()), n))
+            return buf.view(torch.float8_e4m3fn).float().numpy().reshape(shape)
         buf = torch.empty(n, dtype=torch.bfloat16)
         self._check(lib().sv_debug_activation(self._h, which, pair, c_void_p(buf.data_ptr()), n * 2))
         return buf.float().numpy().reshape(shape)

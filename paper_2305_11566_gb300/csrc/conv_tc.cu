@@ -35,6 +35,7 @@
 #include <vector>
 
 #include <cuda.h>
+#include <cuda_fp8.h>
 #include <type_traits>
 #include <cudaTypedefs.h>
 
@@ -72,6 +73,12 @@ struct Params {
   int split;                      // 1: a ring unit is one channel block of a row
   int* err;
   long long spin;
+  // FP8 form (E4M3 operands): cin counts pairs of FP8 channels (the operand bytes / 2, so
+  // that every byte-level layout is the BF16 one); scale [cout] dequantises the
+  // accumulator (per-output-channel weight scale); out_f8: the output is stored as E4M3
+  // codes (else BF16)
+  const float* scale;
+  int out_f8;
 };
 
 // RA staged rows per tile, STEP new rows per next tile, T taps, NSET pixel sets per row
@@ -98,9 +105,10 @@ __host__ __device__ inline size_t row_bytes(int mode, int cin) {
 __host__ __device__ inline int taps(int mode) { return mode == TM_S2 ? 9 : mode == TM_UP2 ? 4 : 1; }
 __host__ __device__ inline size_t b_bytes(int mode, int NT, int cin) { return (size_t)taps(mode) * NT * cin * 2; }
 // ring: staged units, whole rows or (split) one channel block of a row each
-__host__ __device__ inline size_t smem_bytes(int mode, int NT, int cin, int ring, bool split = false) {
+// f8: the FP8 form also keeps a per-channel scale beside the bias
+__host__ __device__ inline size_t smem_bytes(int mode, int NT, int cin, int ring, bool split = false, bool f8 = false) {
   const size_t unit = split ? row_bytes(mode, cin) / (cin * 2 / rb_of(cin)) : row_bytes(mode, cin);
-  return 1024 + (b_bytes(mode, NT, cin) + (size_t)NT * 4 + 1023) / 1024 * 1024 + (size_t)ring * unit +
+  return 1024 + (b_bytes(mode, NT, cin) + (size_t)NT * (f8 ? 8 : 4) + 1023) / 1024 * 1024 + (size_t)ring * unit +
          (size_t)(2 * ring + 4) * kBarBytes + 16;
 }
 
@@ -196,6 +204,23 @@ __device__ __forceinline__ void mma_bf16_elect(uint32_t tmem_d, uint32_t alo, ui
       " @e tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n}\n" ::"r"(tmem_d),
       "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc));
 }
+// The same with E4M3 A and B (kind::f8f6f4: K = 32 elements, the same 32 bytes per K step).
+__device__ __forceinline__ void mma_f8_elect(uint32_t tmem_d, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
+                                             uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .b64 da, db;\n .reg .pred p, e;\n .reg .b32 r;\n elect.sync r|e, 0xffffffff;\n"
+      " mov.b64 da, {%1, %2};\n mov.b64 db, {%3, %4};\n setp.ne.b32 p, %6, 0;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], da, db, %5, p;\n}\n" ::"r"(tmem_d),
+      "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc));
+}
+template <bool F8>
+__device__ __forceinline__ void mma_elect(uint32_t tmem_d, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
+                                          uint32_t idesc, uint32_t acc) {
+  if constexpr (F8)
+    mma_f8_elect(tmem_d, alo, ahi, blo, bhi, idesc, acc);
+  else
+    mma_bf16_elect(tmem_d, alo, ahi, blo, bhi, idesc, acc);
+}
 __device__ __forceinline__ void mma_commit_elect(uint32_t bar) {
   asm volatile(
       "{\n .reg .pred e;\n .reg .b32 r;\n elect.sync r|e, 0xffffffff;\n"
@@ -275,7 +300,7 @@ __device__ __forceinline__ void tap_geo(int t, int& row, int& set, int& col) {
   }
 }
 
-template <int MODE, int NT, int RB, bool SPLIT = false>
+template <int MODE, int NT, int RB, bool SPLIT = false, bool F8 = false>
 __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_constant__ Params p) {
   using G_ = Geo<MODE>;
   constexpr int RA = G_::RA, STEP = G_::STEP, T = G_::T, NSET = G_::NSET, NPX = G_::NPX;
@@ -294,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   const uint32_t unitb = NSET * KPU * KBS;
   const uint32_t sB = base;
   const uint32_t sBias = sB + (uint32_t)T * NT * cin * 2;
-  const uint32_t sA = (sBias + NT * 4 + 1023u) & ~1023u;
+  const uint32_t sA = (sBias + NT * (F8 ? 8 : 4) + 1023u) & ~1023u;
   const uint32_t bars = sA + ring * unitb;
   const uint32_t full0 = bars, empty0 = bars + ring * 8, accf0 = bars + 2 * ring * 8, acce0 = accf0 + 16;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + (acce0 + 16 - base));
@@ -315,6 +340,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
     for (int e = tid; e < n16; e += kThreads) dst[e] = src[e];
     float* bs = reinterpret_cast<float*>(gbase + (sBias - base));
     for (int e = tid; e < NT; e += kThreads) bs[e] = p.bias[n0 + e];
+    if constexpr (F8)
+      for (int e = tid; e < NT; e += kThreads) bs[NT + e] = p.scale[n0 + e];
   }
   if (tid == 0) {
     for (uint32_t r = 0; r < ring; ++r) {
@@ -389,7 +416,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
     // ------------------------------------------------------------ MMA issuer (the whole warp
     // runs the loop with warp-uniform descriptors; one elected lane issues each instruction)
     {
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((128u >> 4) << 24);
+      // FP32 accumulator; A, B BF16 (format 1) or E4M3 (format 0); K-major; N; M = 128
+      const uint32_t idesc = (1u << 4) | (F8 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(NT >> 3) << 17) |
+                             ((128u >> 4) << 24);
       const uint32_t bsz = NT * cin * 2;
       // A: swizzled K-major pixel rows, SBO = 8 pixels (LBO unused: one swizzle span per
       // row); B: no-swizzle K-major core matrices, LBO = 128 B (next 8 channels), SBO =
@@ -440,8 +469,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
 #pragma unroll
                   for (int k4 = 0; k4 < KPR; ++k4)
                     // next 16 channels: +32 B inside the swizzled pixel row, +256 B in B
-                    mma_bf16_elect(dcol, a0[t] + ak + 2 * k4, a_hi, b0[t] + bk + 16 * k4, b_hi, idesc,
-                                   (kb | t | k4) != 0 ? 1u : 0u);
+                    mma_elect<F8>(dcol, a0[t] + ak + 2 * k4, a_hi, b0[t] + bk + 16 * k4, b_hi, idesc,
+                                  (kb | t | k4) != 0 ? 1u : 0u);
               }
               mma_commit_elect(accf0 + 8 * buf);
               // the rows the strip's next tile no longer reads go back to the producer as
@@ -475,7 +504,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
             for (int t = 0; t < T; ++t)
 #pragma unroll
               for (int k4 = 0; k4 < KPR; ++k4)
-                mma_bf16_elect(dcol, a0[t] + 2 * k4, a_hi, b0[t] + bk + 16 * k4, b_hi, idesc, (kb | t | k4) != 0 ? 1u : 0u);
+                mma_elect<F8>(dcol, a0[t] + 2 * k4, a_hi, b0[t] + bk + 16 * k4, b_hi, idesc, (kb | t | k4) != 0 ? 1u : 0u);
             // block kb of the rows the next tile no longer reads goes back to the producer
             for (int r = 0; r < nrel; ++r) {
               const uint32_t sl = tb.slot + (uint32_t)(r * UPR + kb);
@@ -535,12 +564,40 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
           if (NT >= 32) tmem_ld32(trow + c0, r);
           else tmem_ld16(trow + c0, r);
           constexpr int CW = NT >= 32 ? 32 : NT;
-          if (valid) {
+          if (valid && F8 && p.out_f8) {
+            // E4M3 codes: relu(scale * acc + bias), 4 per word, 16 per 16-byte store
+            uint32_t packed[CW / 4];
+#pragma unroll
+            for (int e = 0; e < CW; e += 4) {
+              float v[4];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                v[q] = fmaf(__uint_as_float(r[e + q]), bias_s[NT + c0 + e + q], bias_s[c0 + e + q]);
+                if (p.relu) v[q] = fmaxf(v[q], 0.f);
+              }
+              const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[0], v[1]), __NV_SATFINITE, __NV_E4M3);
+              const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v[2], v[3]), __NV_SATFINITE, __NV_E4M3);
+              packed[e / 4] = lo | (hi << 16);
+            }
+            uint8_t* ob = reinterpret_cast<uint8_t*>(out) + ((size_t)oy * Wo + ox) * p.cout + n0 + c0;
+            if constexpr (CW >= 16) {
+              uint4* dst = reinterpret_cast<uint4*>(ob);
+#pragma unroll
+              for (int v = 0; v < CW / 16; ++v)
+                dst[v] = make_uint4(packed[4 * v], packed[4 * v + 1], packed[4 * v + 2], packed[4 * v + 3]);
+            }
+          } else if (valid) {
             uint32_t packed[CW / 2];
 #pragma unroll
             for (int e = 0; e < CW; e += 2) {
-              float a = __uint_as_float(r[e]) + bias_s[c0 + e];
-              float b = __uint_as_float(r[e + 1]) + bias_s[c0 + e + 1];
+              float a = __uint_as_float(r[e]), b = __uint_as_float(r[e + 1]);
+              if constexpr (F8) {
+                a = fmaf(a, bias_s[NT + c0 + e], bias_s[c0 + e]);
+                b = fmaf(b, bias_s[NT + c0 + e + 1], bias_s[c0 + e + 1]);
+              } else {
+                a += bias_s[c0 + e];
+                b += bias_s[c0 + e + 1];
+              }
               if (p.relu) {
                 a = fmaxf(a, 0.f);
                 b = fmaxf(b, 0.f);
@@ -1134,6 +1191,76 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
 }
 
 // ------------------------------------------------------------------ weight packing
+// Value the tensor-core form multiplies for output channel co, input channel k and tap t
+// (phase ph of an up-sampling layer): the weight itself (stride-2, 1 x 1), or the sum of the
+// 3 x 3 weights the phase folds onto the tap (rows / columns {0} and {1, 2} for phase 0,
+// {0, 1} and {2} for phase 1), summed in FP32 in row-major tap order.
+__device__ __forceinline__ float tc_weight(const float* __restrict__ W, int mode, int ph, int t, int co, int k, int cin) {
+  if (mode == TM_P1) return W[(size_t)co * cin + k];
+  if (mode == TM_S2) return W[((size_t)co * 9 + t) * cin + k];
+  const int py = ph >> 1, px = ph & 1, a = t >> 1, b = t & 1;
+  const int ky0 = py == 0 ? (a == 0 ? 0 : 1) : (a == 0 ? 0 : 2);
+  const int ky1 = py == 0 ? (a == 0 ? 0 : 2) : (a == 0 ? 1 : 2);
+  const int kx0 = px == 0 ? (b == 0 ? 0 : 1) : (b == 0 ? 0 : 2);
+  const int kx1 = px == 0 ? (b == 0 ? 0 : 2) : (b == 0 ? 1 : 2);
+  float v = 0.f;
+  for (int ky = ky0; ky <= ky1; ++ky)
+    for (int kx = kx0; kx <= kx1; ++kx) v += W[((size_t)co * 9 + ky * 3 + kx) * cin + k];
+  return v;
+}
+
+// FP8 form: per-output-channel scale max |v| / 448 over every value the layer multiplies for
+// that channel (all phases and taps; 1 if all are zero).  unfolded: the 3 x 3 weights as they
+// are (the border recompute of up-sampling layers).
+__global__ void fp8_scale_kernel(const float* __restrict__ W, int mode, int cin, int cout, int unfolded,
+                                 float* __restrict__ scale) {
+  const int co = blockIdx.x * blockDim.x + threadIdx.x;
+  if (co >= cout) return;
+  float m = 0.f;
+  if (unfolded) {
+    for (int i = 0; i < 9 * cin; ++i) m = fmaxf(m, fabsf(W[(size_t)co * 9 * cin + i]));
+  } else {
+    const int T = taps(mode), NPH = mode == TM_UP2 ? 4 : 1;
+    for (int ph = 0; ph < NPH; ++ph)
+      for (int t = 0; t < T; ++t)
+        for (int k = 0; k < cin; ++k) m = fmaxf(m, fabsf(tc_weight(W, mode, ph, t, co, k, cin)));
+  }
+  scale[co] = m > 0.f ? m / 448.0f : 1.0f;
+}
+
+// Packed B of the FP8 form: the E4M3 codes of v / scale[co] in the byte layout of the BF16
+// pack with cin / 2 channels (two FP8 channels per BF16 slot, the even one first).
+__global__ void pack_fp8_kernel(const float* __restrict__ W, int mode, int NT, int G, int cin, int cout,
+                                const float* __restrict__ scale, uint8_t* __restrict__ out) {
+  const int T = taps(mode);
+  const size_t total = (size_t)G * T * NT * cin;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int k = (int)(idx % cin);
+  size_t r = idx / cin;
+  const int n = (int)(r % NT);
+  r /= NT;
+  const int t = (int)(r % T);
+  const int g = (int)(r / T);
+  const int nsl = mode == TM_UP2 ? g / 4 : g;
+  const int co = nsl * NT + n;
+  uint8_t q = 0;
+  if (co < cout)
+    q = (uint8_t)__nv_cvt_float_to_fp8(tc_weight(W, mode, g % 4, t, co, k, cin) / scale[co], __NV_SATFINITE, __NV_E4M3);
+  const int cb = cin / 2, kb = k >> 1;
+  const size_t slot = (size_t)(n % 8) * 8 + (size_t)(n / 8) * cb * 8 + (kb % 8) + (size_t)(kb / 8) * 64;
+  out[((size_t)g * T + t) * NT * cin + 2 * slot + (k & 1)] = q;
+}
+
+// E4M3 codes of the unfolded 3 x 3 weights [co][3][3][ci] (the border recompute).
+__global__ void quant_unfolded_kernel(const float* __restrict__ W, int cout, int cin, const float* __restrict__ scale,
+                                      uint8_t* __restrict__ out) {
+  const size_t n = (size_t)cout * 9 * cin;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = (uint8_t)__nv_cvt_float_to_fp8(W[i] / scale[i / (9 * (size_t)cin)], __NV_SATFINITE, __NV_E4M3);
+}
+
 // Packed B of one layer: [G][T][NT rows (output channels) x cin] in the no-swizzle
 // K-major core-matrix layout: element (n, k) at (n%8)*8 + (n/8)*cin*8 + (k%8) + (k/8)*64.
 __global__ void pack_kernel(const float* __restrict__ W, int mode, int NT, int G, int cin, int cout,
@@ -1150,23 +1277,7 @@ __global__ void pack_kernel(const float* __restrict__ W, int mode, int NT, int G
   const int g = (int)(r / T);
   const int nsl = mode == TM_UP2 ? g / 4 : g;
   const int co = nsl * NT + n;
-  float v = 0.f;
-  if (co < cout) {
-    if (mode == TM_P1) {
-      v = W[(size_t)co * cin + k];
-    } else if (mode == TM_S2) {
-      v = W[((size_t)co * 9 + t) * cin + k];
-    } else {
-      const int ph = g % 4, py = ph >> 1, px = ph & 1, a = t >> 1, b = t & 1;
-      // rows of the 3x3 kernel folded into tap row a of phase py: {0} / {1,2} (py = 0), {0,1} / {2} (py = 1)
-      const int ky0 = py == 0 ? (a == 0 ? 0 : 1) : (a == 0 ? 0 : 2);
-      const int ky1 = py == 0 ? (a == 0 ? 0 : 2) : (a == 0 ? 1 : 2);
-      const int kx0 = px == 0 ? (b == 0 ? 0 : 1) : (b == 0 ? 0 : 2);
-      const int kx1 = px == 0 ? (b == 0 ? 0 : 2) : (b == 0 ? 1 : 2);
-      for (int ky = ky0; ky <= ky1; ++ky)
-        for (int kx = kx0; kx <= kx1; ++kx) v += W[((size_t)co * 9 + ky * 3 + kx) * cin + k];
-    }
-  }
+  const float v = co < cout ? tc_weight(W, mode, g % 4, t, co, k, cin) : 0.f;
   const size_t dst = ((size_t)g * T + t) * NT * cin + (size_t)(n % 8) * 8 + (size_t)(n / 8) * cin * 8 + (k % 8) +
                      (size_t)(k / 8) * 64;
   out[dst] = __float2bfloat16_rn(v);
@@ -1237,12 +1348,12 @@ bool fused_supported(int cout, int cin) {
   return (cout == 16 || cout == 32) && (cin == 32 || cin == 64) && fused_smem_bytes(cout, cin, 4) <= 232448;
 }
 
-template <int MODE, int NT, int RB>
+template <int MODE, int NT, int RB, bool F8>
 cudaError_t launch_mode_nt(const Params& p, int grid, size_t smem, cudaStream_t st) {
   // channel-block rings are planned only for up-sampling layers with 128-byte channel blocks
-  auto k = conv_tc_kernel<MODE, NT, RB>;
+  auto k = conv_tc_kernel<MODE, NT, RB, false, F8>;
   if constexpr (MODE == TM_UP2 && RB == 128) {
-    if (p.split) k = conv_tc_kernel<MODE, NT, RB, true>;
+    if (p.split) k = conv_tc_kernel<MODE, NT, RB, true, F8>;
   } else {
     if (p.split) return cudaErrorInvalidValue;
   }
@@ -1255,33 +1366,36 @@ cudaError_t launch_mode_nt(const Params& p, int grid, size_t smem, cudaStream_t 
   return cudaGetLastError();
 }
 
-template <int MODE, int RB>
+template <int MODE, int RB, bool F8>
 cudaError_t launch_mode_rb(const Params& p, int NT, int grid, size_t smem, cudaStream_t st) {
   switch (NT) {
-    case 16: return launch_mode_nt<MODE, 16, RB>(p, grid, smem, st);
-    case 32: return launch_mode_nt<MODE, 32, RB>(p, grid, smem, st);
-    case 64: return launch_mode_nt<MODE, 64, RB>(p, grid, smem, st);
-    case 128: return launch_mode_nt<MODE, 128, RB>(p, grid, smem, st);
-    case 256: return launch_mode_nt<MODE, 256, RB>(p, grid, smem, st);
+    case 16: return launch_mode_nt<MODE, 16, RB, F8>(p, grid, smem, st);
+    case 32: return launch_mode_nt<MODE, 32, RB, F8>(p, grid, smem, st);
+    case 64: return launch_mode_nt<MODE, 64, RB, F8>(p, grid, smem, st);
+    case 128: return launch_mode_nt<MODE, 128, RB, F8>(p, grid, smem, st);
+    case 256:
+      if constexpr (!F8) return launch_mode_nt<MODE, 256, RB, F8>(p, grid, smem, st);  // FP8 plans cap N at 128
+      break;
   }
   return cudaErrorInvalidValue;
 }
 
-template <int MODE>
+template <int MODE, bool F8>
 cudaError_t launch_mode(const Params& p, int NT, int grid, size_t smem, cudaStream_t st) {
   switch (rb_of(p.cin)) {
-    case 128: return launch_mode_rb<MODE, 128>(p, NT, grid, smem, st);
-    case 64: return launch_mode_rb<MODE, 64>(p, NT, grid, smem, st);
-    case 32: return launch_mode_rb<MODE, 32>(p, NT, grid, smem, st);
+    case 128: return launch_mode_rb<MODE, 128, F8>(p, NT, grid, smem, st);
+    case 64: return launch_mode_rb<MODE, 64, F8>(p, NT, grid, smem, st);
+    case 32: return launch_mode_rb<MODE, 32, F8>(p, NT, grid, smem, st);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_conv(int mode, const Params& p, int NT, int grid, size_t smem, cudaStream_t st) {
+cudaError_t launch_conv(int mode, const Params& p, int NT, int grid, size_t smem, cudaStream_t st, bool f8 = false) {
   switch (mode) {
-    case TM_S2: return launch_mode<TM_S2>(p, NT, grid, smem, st);
-    case TM_UP2: return launch_mode<TM_UP2>(p, NT, grid, smem, st);
-    case TM_P1: return launch_mode<TM_P1>(p, NT, grid, smem, st);
+    case TM_S2: return f8 ? launch_mode<TM_S2, true>(p, NT, grid, smem, st) : launch_mode<TM_S2, false>(p, NT, grid, smem, st);
+    case TM_UP2:
+      return f8 ? launch_mode<TM_UP2, true>(p, NT, grid, smem, st) : launch_mode<TM_UP2, false>(p, NT, grid, smem, st);
+    case TM_P1: return f8 ? launch_mode<TM_P1, true>(p, NT, grid, smem, st) : launch_mode<TM_P1, false>(p, NT, grid, smem, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -1410,7 +1524,9 @@ __global__ void to_bf16_kernel(const float* __restrict__ a, __nv_bfloat16* __res
   if (i < n) b[i] = __float2bfloat16_rn(a[i]);
 }
 
-static void plan_layers(const NetDims& net, std::vector<TcLayerPlan>& plans, size_t& total) {
+// f8: the FP8 form, whose operands are E4M3 bytes: a layer of cin channels is planned as cin / 2
+// BF16-sized channels (the same bytes), N at most 128, bias and scale beside the weights.
+static void plan_layers(const NetDims& net, std::vector<TcLayerPlan>& plans, size_t& total, bool f8 = false) {
   plans.clear();
   total = 0;
   const int layers[6] = {L_ENC2, L_ENC3, L_MU, L_DEC1, L_DEC2, L_DEC3};
@@ -1418,15 +1534,15 @@ static void plan_layers(const NetDims& net, std::vector<TcLayerPlan>& plans, siz
     TcLayerPlan pl{};
     pl.layer = l;
     pl.mode = (l == L_ENC2 || l == L_ENC3) ? tc::TM_S2 : l == L_MU ? tc::TM_P1 : tc::TM_UP2;
-    pl.cin = net.cin(l);
+    pl.cin = f8 ? net.cin(l) / 2 : net.cin(l);
     pl.cout = net.cout(l);
     pl.relu = l != L_MU;
     const int RA = pl.mode == tc::TM_S2 ? 3 : pl.mode == tc::TM_UP2 ? 2 : 1;
     const int STEP = pl.mode == tc::TM_S2 ? 2 : 1;
-    int NT = std::min(256, pl.cout & -pl.cout);  // a power of two dividing cout (widths are multiples of 16)
+    int NT = std::min(f8 ? 128 : 256, pl.cout & -pl.cout);  // a power of two dividing cout (widths are multiples of 16)
     int ring = RA + STEP;
     while (true) {
-      size_t sm = tc::smem_bytes(pl.mode, NT, pl.cin, ring);
+      size_t sm = tc::smem_bytes(pl.mode, NT, pl.cin, ring, false, f8);
       if (sm <= kSmemLimit) break;
       if (ring > RA) { --ring; continue; }
       NT /= 2;
@@ -1434,12 +1550,13 @@ static void plan_layers(const NetDims& net, std::vector<TcLayerPlan>& plans, siz
     }
     // spend leftover shared memory on deeper row prefetch: a staged row is needed by one
     // tile of MMAs only, so many rows in flight hide the load latency
-    while (ring < RA + kPrefetchSteps * STEP && tc::smem_bytes(pl.mode, NT, pl.cin, ring + 1) <= kSmemLimit) ++ring;
+    while (ring < RA + kPrefetchSteps * STEP && tc::smem_bytes(pl.mode, NT, pl.cin, ring + 1, false, f8) <= kSmemLimit)
+      ++ring;
     pl.NT = NT;
     pl.ring = ring;
     const int nsl = (pl.cout + NT - 1) / NT;
     pl.G = pl.mode == tc::TM_UP2 ? 4 * nsl : nsl;
-    pl.smem = tc::smem_bytes(pl.mode, NT, pl.cin, ring);
+    pl.smem = tc::smem_bytes(pl.mode, NT, pl.cin, ring, false, f8);
     pl.wofs = total;
     pl.fix_wofs = 0;
     total += (size_t)pl.G * tc::taps(pl.mode) * NT * pl.cin;
@@ -1491,6 +1608,62 @@ sv_status Ctx::pack_bf16_weights(cudaStream_t st) {
   return SV_OK;
 }
 
+// FP8 form: per layer the E4M3 codes of the packed operand (in the BF16 pack's byte layout)
+// and its per-output-channel scales; for the decoder layers also the codes of the unfolded
+// 3 x 3 weights and their scales (the border recompute).  Offsets: the plan's wofs (BF16
+// units of wf8), scale offsets f8_scale_ofs[6] and f8_unf_ofs / f8_unf_scale_ofs[3].
+sv_status Ctx::pack_fp8_weights(cudaStream_t st) {
+  std::vector<TcLayerPlan> plans;
+  size_t total;
+  plan_layers(net, plans, total, true);
+  const int dl[3] = {L_DEC1, L_DEC2, L_DEC3};
+  size_t unf_bytes = 0, nscale = 0;
+  for (int k = 0; k < 3; ++k) {
+    f8_unf_ofs[k] = unf_bytes;
+    unf_bytes += ((size_t)net.cout(dl[k]) * 9 * net.cin(dl[k]) + 15) / 16 * 16;
+  }
+  for (size_t li = 0; li < plans.size(); ++li) {
+    f8_scale_ofs[li] = nscale;
+    nscale += (size_t)(plans[li].cout + 3) / 4 * 4;
+  }
+  for (int k = 0; k < 3; ++k) {
+    f8_unf_scale_ofs[k] = nscale;
+    nscale += (size_t)(net.cout(dl[k]) + 3) / 4 * 4;
+  }
+  sv_status s;
+  if ((s = cuda(wf8.ensure(total * 2), "alloc FP8 weights"))) return s;
+  if ((s = cuda(wf8u.ensure(std::max<size_t>(unf_bytes, 16)), "alloc FP8 unfolded weights"))) return s;
+  if ((s = cuda(wf8s.ensure(nscale * sizeof(float)), "alloc FP8 scales"))) return s;
+  float* sc = (float*)wf8s.p;
+  const float* W = (const float*)w32.p;
+  for (size_t li = 0; li < plans.size(); ++li) {
+    const TcLayerPlan& pl = plans[li];
+    const int cin = net.cin(pl.layer);
+    LaunchScope ls(*this, "pack_fp8", st);
+    tc::fp8_scale_kernel<<<(pl.cout + 127) / 128, 128, 0, st>>>(W + net.w_off(pl.layer), pl.mode, cin, pl.cout, 0,
+                                                               sc + f8_scale_ofs[li]);
+    if ((s = cuda(cudaGetLastError(), "FP8 scales"))) return s;
+    const size_t n = (size_t)pl.G * tc::taps(pl.mode) * pl.NT * cin;
+    tc::pack_fp8_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W + net.w_off(pl.layer), pl.mode, pl.NT, pl.G, cin,
+                                                                     pl.cout, sc + f8_scale_ofs[li],
+                                                                     (uint8_t*)((__nv_bfloat16*)wf8.p + pl.wofs));
+    if ((s = cuda(cudaGetLastError(), "pack FP8 weights"))) return s;
+  }
+  for (int k = 0; k < 3; ++k) {
+    const int cout = net.cout(dl[k]), cin = net.cin(dl[k]);
+    LaunchScope ls(*this, "pack_fp8", st);
+    tc::fp8_scale_kernel<<<(cout + 127) / 128, 128, 0, st>>>(W + net.w_off(dl[k]), tc::TM_S2, cin, cout, 1,
+                                                            sc + f8_unf_scale_ofs[k]);
+    if ((s = cuda(cudaGetLastError(), "FP8 unfolded scales"))) return s;
+    const size_t n = (size_t)cout * 9 * cin;
+    tc::quant_unfolded_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W + net.w_off(dl[k]), cout, cin,
+                                                                           sc + f8_unf_scale_ofs[k],
+                                                                           (uint8_t*)wf8u.p + f8_unf_ofs[k]);
+    if ((s = cuda(cudaGetLastError(), "FP8 unfolded weights"))) return s;
+  }
+  return SV_OK;
+}
+
 // Host side of one tensor-core refinement call: activation workspaces (allocated here),
 // per-layer descriptor and strip tables (built here, uploaded by the caller) and launch
 // geometry.  Nothing is enqueued on a stream.
@@ -1499,7 +1672,8 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
   using tc::LayerPair;
   using tc::Strip;
   size_t wtotal;
-  plan_layers(net, r.plans, wtotal);
+  const bool f8 = cfg.precision == SV_FP8;
+  plan_layers(net, r.plans, wtotal, f8);
   for (size_t li = 0; li < r.plans.size(); ++li) {
     if (tc_nt_override[li] > 0 && tc_nt_override[li] <= r.plans[li].NT) {
       // autotuned narrower N slice (more weight sets, more CTAs per pair)
@@ -1510,9 +1684,10 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
       pl.G = pl.mode == tc::TM_UP2 ? 4 * nsl : nsl;
       const int RA = pl.mode == tc::TM_S2 ? 3 : pl.mode == tc::TM_UP2 ? 2 : 1;
       const int STEP = pl.mode == tc::TM_S2 ? 2 : 1;
-      while (pl.ring < RA + kPrefetchSteps * STEP && tc::smem_bytes(pl.mode, NT, pl.cin, pl.ring + 1) <= kSmemLimit)
+      while (pl.ring < RA + kPrefetchSteps * STEP &&
+             tc::smem_bytes(pl.mode, NT, pl.cin, pl.ring + 1, false, f8) <= kSmemLimit)
         ++pl.ring;
-      pl.smem = tc::smem_bytes(pl.mode, NT, pl.cin, pl.ring);
+      pl.smem = tc::smem_bytes(pl.mode, NT, pl.cin, pl.ring, false, f8);
     }
   }
   {
@@ -1529,8 +1704,8 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
       const size_t budget = (size_t)per_sm / k - (size_t)reserved;
       const int RA = pl.mode == tc::TM_S2 ? 3 : pl.mode == tc::TM_UP2 ? 2 : 1;
       const int STEP = pl.mode == tc::TM_S2 ? 2 : 1;
-      while (pl.ring > RA + STEP && tc::smem_bytes(pl.mode, pl.NT, pl.cin, pl.ring) > budget) --pl.ring;
-      pl.smem = tc::smem_bytes(pl.mode, pl.NT, pl.cin, pl.ring);
+      while (pl.ring > RA + STEP && tc::smem_bytes(pl.mode, pl.NT, pl.cin, pl.ring, false, f8) > budget) --pl.ring;
+      pl.smem = tc::smem_bytes(pl.mode, pl.NT, pl.cin, pl.ring, false, f8);
     }
   }
   // a layer whose ring holds no row beyond the tile's own (the weights fill shared memory)
@@ -1552,11 +1727,11 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
       if (pl.smem <= share) budget = share;  // else k CTAs do not fit anyway: one per SM
     }
     int units = RA * KB;
-    while (units < 3 * RA * KB && tc::smem_bytes(pl.mode, pl.NT, pl.cin, units + 1, true) <= budget) ++units;
+    while (units < 3 * RA * KB && tc::smem_bytes(pl.mode, pl.NT, pl.cin, units + 1, true, f8) <= budget) ++units;
     if (units <= RA * KB) continue;  // no unit of look-ahead fits
     pl.split = 1;
     pl.ring = units;
-    pl.smem = tc::smem_bytes(pl.mode, pl.NT, pl.cin, units, true);
+    pl.smem = tc::smem_bytes(pl.mode, pl.NT, pl.cin, units, true, f8);
   }
   sv_status s;
   int nsm = 0;
@@ -1572,14 +1747,23 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
                             P[2] * net.dec[0], P[1] * net.dec[1], P[0] * net.dec[2]};
     for (int k = 0; k < 7; ++k) {
       off[i][k] = cnt[k];
-      cnt[k] += (need[k] + 7) / 8 * 8;  // 16-byte aligned per pair
+      cnt[k] += (need[k] + 15) / 16 * 16;  // 16-byte aligned per pair (BF16 and E4M3)
     }
     lens.push_back({need[0], need[1], need[2], need[3], need[4], need[5], need[6]});
   }
+  // BF16 activations; the FP8 form keeps e2 .. d2 as E4M3 codes (one byte per channel) and
+  // the E4M3 codes of e1 in tc_act[7] (e1 itself, from the first layer, stays BF16, as d3)
+  auto esize = [&](int k) { return f8 && k >= 1 && k <= 5 ? (size_t)1 : sizeof(__nv_bfloat16); };
   for (int k = 0; k < 7; ++k)
-    if ((s = cuda(tc_act[k].ensure(std::max<size_t>(cnt[k], 8) * sizeof(__nv_bfloat16)), "alloc bf16 activations")))
-      return s;
-  auto act = [&](int k, int i) { return (__nv_bfloat16*)tc_act[k].p + off[i][k]; };
+    if ((s = cuda(tc_act[k].ensure(std::max<size_t>(cnt[k], 16) * esize(k)), "alloc activations"))) return s;
+  if (f8 && (s = cuda(tc_act[7].ensure(std::max<size_t>(cnt[0], 16)), "alloc FP8 e1"))) return s;
+  // (an FP8 tensor is addressed as BF16 of half the channels: offsets are element counts / 2)
+  auto act = [&](int k, int i) {
+    return esize(k) == 1 ? (__nv_bfloat16*)((uint8_t*)tc_act[k].p + off[i][k]) : (__nv_bfloat16*)tc_act[k].p + off[i][k];
+  };
+  auto act_in = [&](int k, int i) {  // a tensor-core layer's input: e1 as E4M3 codes in the FP8 form
+    return f8 && k == 0 ? (__nv_bfloat16*)((uint8_t*)tc_act[7].p + off[i][0]) : act(k, i);
+  };
   tc_off = off;
   tc_len = lens;
   r.host.clear();
@@ -1605,7 +1789,7 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
     for (int i = 0; i < n; ++i) {
       LayerPair& L = lps[i];
       memset(&L, 0, sizeof(L));
-      L.in = act(in_act, i);
+      L.in = act_in(in_act, i);
       L.out = act(out_act, i);
       L.Hi = lv[i].H[lin]; L.Wi = lv[i].W[lin];
       L.Ho = lv[i].H[lout]; L.Wo = lv[i].W[lout];
@@ -1666,12 +1850,13 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
   }
   r.edge_ofs = put(eps_.data(), sizeof(EdgePair) * n);
   r.n = n;
+  r.e1_count = cnt[0];
 
   // fused last decoder layer + final conv: inference only (training keeps d3 for backward)
   r.fused = false;
   bool even = true;
   for (int i = 0; i < n; ++i) even = even && (pairs[i].width % 2 == 0);
-  if (!coarse_f && fused_final && even && tc::fused_supported(net.dec[2], net.dec[1]) && wfuse.p) {
+  if (!f8 && !coarse_f && fused_final && even && tc::fused_supported(net.dec[2], net.dec[1]) && wfuse.p) {
     const int NT = net.dec[2], cin = net.dec[1];
     int ring = 4;  // 3 rows per tile + 1 ahead; more where shared memory allows
     while (ring < 3 + kPrefetchSteps && tc::fused_smem_bytes(NT, cin, ring + 1) <= kSmemLimit) ++ring;
@@ -1731,6 +1916,13 @@ sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream
                   "enc1")))
       return s;
   }
+  const bool f8 = cfg.precision == SV_FP8;
+  if (f8) {
+    LaunchScope ls(*this, "e1_to_e4m3", st);
+    if ((s = cuda(launch_bf16_to_e4m3((const __nv_bfloat16*)tc_act[0].p, (uint8_t*)tc_act[7].p, r.e1_count, st),
+                  "e1 to E4M3")))
+      return s;
+  }
   static const char* names[6] = {"tc_enc2", "tc_enc3", "tc_latent", "tc_dec1", "tc_dec2", "tc_dec3"};
   for (size_t li = 0; li < r.plans.size(); ++li) {
     const TcLayerPlan& pl = r.plans[li];
@@ -1738,8 +1930,10 @@ sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream
     prm.lp = (const LayerPair*)(tables + r.tabs[li].lp_ofs);
     prm.strips = (const Strip*)(tables + r.tabs[li].strip_ofs);
     prm.n_strips = r.tabs[li].n_strips;
-    prm.wpack = (const __nv_bfloat16*)wbf.p + pl.wofs;
+    prm.wpack = (const __nv_bfloat16*)(f8 ? wf8.p : wbf.p) + pl.wofs;
     prm.bias = W + net.b_off(pl.layer);
+    prm.scale = f8 ? (const float*)wf8s.p + f8_scale_ofs[li] : nullptr;
+    prm.out_f8 = f8 && pl.layer != L_DEC3;
     prm.cin = pl.cin;
     prm.cout = pl.cout;
     prm.G = pl.G;
@@ -1779,9 +1973,18 @@ sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream
     }
     {
       LaunchScope ls(*this, names[li], st);
-      if ((s = cuda(tc::launch_conv(pl.mode, prm, pl.NT, r.tabs[li].grid, pl.smem, st), names[li]))) return s;
+      if ((s = cuda(tc::launch_conv(pl.mode, prm, pl.NT, r.tabs[li].grid, pl.smem, st, f8), names[li]))) return s;
     }
-    if (pl.mode == tc::TM_UP2 && r.tabs[li].fix_segments > 0) {
+    if (f8 && pl.mode == tc::TM_UP2 && r.tabs[li].fix_segments > 0) {
+      const int k = pl.layer == L_DEC1 ? 0 : pl.layer == L_DEC2 ? 1 : 2;
+      LaunchScope ls(*this, "edge_up2fix", st);
+      if ((s = cuda(launch_edge_up2fix_f8((const UpFixPair*)(tables + r.tabs[li].fix_ofs), r.n, r.tabs[li].fix_segments,
+                                          (const uint8_t*)wf8u.p + f8_unf_ofs[k],
+                                          (const float*)wf8s.p + f8_unf_scale_ofs[k], prm.bias, net.cin(pl.layer),
+                                          pl.cout, 1, prm.out_f8, st),
+                    "border fix")))
+        return s;
+    } else if (pl.mode == tc::TM_UP2 && r.tabs[li].fix_segments > 0) {
       LaunchScope ls(*this, "edge_up2fix", st);
       if ((s = cuda(launch_edge_up2fix((const UpFixPair*)(tables + r.tabs[li].fix_ofs), r.n, r.tabs[li].fix_segments,
                                        (const __nv_bfloat16*)wbf.p + pl.fix_wofs, prm.bias, pl.cin, pl.cout, 1, st),

@@ -239,6 +239,8 @@ sv_status Ctx::refresh_weight_copies_async(cudaStream_t st) {
   }
   if (cfg.precision == SV_BF16)
     if ((s = pack_bf16_weights(st))) return s;
+  if (cfg.precision == SV_FP8)
+    if ((s = pack_fp8_weights(st))) return s;
   return SV_OK;
 }
 
@@ -281,7 +283,13 @@ static bool config_ok(const sv_config* c) {
   for (int i = 0; i < 3; ++i)
     if (!sv::valid_width_pub(c->enc_ch[i]) || !sv::valid_width_pub(c->dec_ch[i])) return false;
   if (!sv::valid_width_pub(c->latent_ch)) return false;
-  if (c->precision < SV_FP32 || c->precision > SV_FP64_CHECK) return false;
+  if (c->precision < SV_FP32 || c->precision > SV_FP8) return false;
+  if (c->precision == SV_FP8) {
+    // E4M3 operands: a tensor-core layer's input width is a whole number of 32-element K steps
+    const int in_w[6] = {c->enc_ch[0], c->enc_ch[1], c->enc_ch[2], c->latent_ch, c->dec_ch[0], c->dec_ch[1]};
+    for (int w : in_w)
+      if (w % 32) return false;
+  }
   if (c->flags != 0) return false;
   return true;
 }
@@ -642,12 +650,14 @@ sv_status sv_debug_activation(sv_ctx* ctx, int which, int pair, void* dst, size_
   if (c->t1) return c->fail(SV_ERR_UNSUPPORTED, "not available for the Table I network");
   if (which < 0 || which > 6 || pair < 0 || pair >= (int)c->tc_off.size() || !dst)
     return c->fail(SV_ERR_INVALID_ARG, "no such activation");
-  if (bytes != c->tc_len[pair][which] * sizeof(__nv_bfloat16))
-    return c->fail(SV_ERR_INVALID_ARG, "activation has %zu bytes", c->tc_len[pair][which] * sizeof(__nv_bfloat16));
+  // FP8 contexts keep e2 .. d2 as E4M3 codes (one byte per element)
+  const size_t es = c->cfg.precision == SV_FP8 && which >= 1 && which <= 5 ? 1 : sizeof(__nv_bfloat16);
+  if (bytes != c->tc_len[pair][which] * es)
+    return c->fail(SV_ERR_INVALID_ARG, "activation has %zu bytes", c->tc_len[pair][which] * es);
   if (which == 6 && c->last_fused)
     return c->fail(SV_ERR_STATE, "d3 stayed on chip (fused final conv); set option fused_final 0 to keep it");
   DeviceGuard g(c->device);
-  return c->cuda(cudaMemcpy(dst, (__nv_bfloat16*)c->tc_act[which].p + c->tc_off[pair][which], bytes,
+  return c->cuda(cudaMemcpy(dst, (const unsigned char*)c->tc_act[which].p + c->tc_off[pair][which] * es, bytes,
                             cudaMemcpyDeviceToHost), "copy activation");
 }
 

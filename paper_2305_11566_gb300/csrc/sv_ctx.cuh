@@ -41,6 +41,7 @@ struct TcRun {
   std::vector<unsigned char> host;
   size_t edge_ofs = 0;
   int n = 0, maxW = 0, maxH = 0, maxW1 = 0, maxH1 = 0;
+  size_t e1_count = 0;  // elements of the e1 workspace (all pairs)
   // fused last decoder layer + final conv (inference, even output widths)
   bool fused = false;
   size_t fused_fp_ofs = 0, fused_strip_ofs = 0, fused_smem = 0;
@@ -86,6 +87,8 @@ struct Ctx {
 
   DevBuf w32, w64, wbf;          // FP32 master, FP64 copy, packed BF16 GEMM operands
   DevBuf wfuse;                  // packed BF16 operands of the fused last decoder layer
+  DevBuf wf8, wf8u, wf8s;        // FP8 form: packed E4M3 operands, unfolded decoder E4M3 weights, scales
+  size_t f8_scale_ofs[6] = {0}, f8_unf_ofs[3] = {0}, f8_unf_scale_ofs[3] = {0};
   DevBuf zpairs, zjobs;          // coarse-matcher tables
   DevBuf coarse_maps;            // int16 coarse maps of sv_pipeline
   DevBuf act[7];                 // activations e1 e2 e3 z d1 d2 d3 (direct path)
@@ -178,6 +181,7 @@ struct Ctx {
   sv_status refresh_weight_copies();
   sv_status refresh_weight_copies_async(cudaStream_t st);
   sv_status pack_bf16_weights(cudaStream_t st = 0);
+  sv_status pack_fp8_weights(cudaStream_t st = 0);
   template <typename T>
   sv_status train_forward(const sv_pair* pairs, const void* const* coarse, const void* const* eps, int n,
                           void* const* Y, void* const* mu, void* const* lv, cudaStream_t st);
@@ -243,7 +247,7 @@ struct Ctx {
     host_img.release(); host_out.release(); host_jobs.release(); err_flag.release(); tune_out.release();
     sgm_s.release(); sgm_c.release(); sgm_a.release(); sgm_tab.release(); x_codes.release(); x_maps.release();
     t1_act.release(); t1_tab.release(); loss_slots.release();
-    w32.release(); w64.release(); wbf.release(); wfuse.release(); zpairs.release(); zjobs.release();
+    w32.release(); w64.release(); wbf.release(); wfuse.release(); wf8.release(); wf8u.release(); wf8s.release(); zpairs.release(); zjobs.release();
     coarse_maps.release();
     for (auto& b : act) b.release();
     for (auto& b : tc_act) b.release();

@@ -10,7 +10,7 @@ namespace sv {
 sv_status Ctx::refine_infer(const sv_pair* pairs, const int16_t* const* coarse, int n, float* const* out,
                             cudaStream_t st) {
   if (t1) return t1_forward(pairs, n, coarse, nullptr, nullptr, out, nullptr, nullptr, st);
-  if (cfg.precision == SV_BF16) return refine_tc(pairs, coarse, n, out, st);
+  if (cfg.precision == SV_BF16 || cfg.precision == SV_FP8) return refine_tc(pairs, coarse, n, out, st);
   if (cfg.precision == SV_FP64_CHECK)
     return fail(SV_ERR_UNSUPPORTED, "inference entry points produce FP32; use sv_refine_train on FP64_CHECK contexts");
   for (int i = 0; i < n; ++i) {
@@ -21,7 +21,7 @@ sv_status Ctx::refine_infer(const sv_pair* pairs, const int16_t* const* coarse, 
 }
 
 sv_status Ctx::pipeline(const sv_pair* pairs, int n, float* const* out, cudaStream_t st) {
-  if (cfg.precision == SV_BF16 && use_graphs && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread)
+  if ((cfg.precision == SV_BF16 || cfg.precision == SV_FP8) && use_graphs && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread)
     return pipeline_graph(pairs, n, out, st);
   std::vector<size_t> off(n + 1, 0);
   for (int i = 0; i < n; ++i) off[i + 1] = off[i] + (size_t)(pairs[i].width / 4) * (pairs[i].height / 4);
@@ -63,7 +63,8 @@ sv_status Ctx::pipeline_graph(const sv_pair* pairs, int n, float* const* out, cu
   }
   k((uint64_t)(uintptr_t)coarse_maps.p);
   for (auto& b : tc_act) k((uint64_t)(uintptr_t)b.p);
-  k((uint64_t)(uintptr_t)w32.p); k((uint64_t)(uintptr_t)wbf.p); k((uint64_t)(uintptr_t)err_flag.p);
+  k((uint64_t)(uintptr_t)w32.p); k((uint64_t)(uintptr_t)wbf.p); k((uint64_t)(uintptr_t)wf8.p);
+  k((uint64_t)(uintptr_t)wf8u.p); k((uint64_t)(uintptr_t)wf8s.p); k((uint64_t)(uintptr_t)err_flag.p);
   k((uint64_t)spin_limit);
   k((uint64_t)prof_on);
   for (auto& t : r.tabs) k(((uint64_t)t.hs << 32) | (uint32_t)t.grid);

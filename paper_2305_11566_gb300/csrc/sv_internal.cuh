@@ -197,6 +197,14 @@ inline int upfix_segments(int Ho, int Wo) {
 cudaError_t launch_edge_up2fix(const UpFixPair* pairs, int n, int max_segments, const __nv_bfloat16* Wb,
                                const float* bias, int cin, int cout, int relu, cudaStream_t st);
 
+// FP8 form: border recompute on E4M3 input codes with E4M3 unfolded weights and their
+// per-output-channel scale (output E4M3 codes, or BF16 when out_f8 = 0); E4M3 codes of a
+// BF16 tensor.
+cudaError_t launch_edge_up2fix_f8(const UpFixPair* pairs, int n, int max_segments, const uint8_t* Wq,
+                                  const float* wscale, const float* bias, int cin, int cout, int relu, int out_f8,
+                                  cudaStream_t st);
+cudaError_t launch_bf16_to_e4m3(const __nv_bfloat16* a, uint8_t* b, size_t n, cudaStream_t st);
+
 // Training latent of the tensor-core form: mu, logvar (FP32, caller's buffers) from BF16
 // e3 with FP32 weights, z = mu + eps exp(logvar / 2) stored as BF16 for the decoder.
 cudaError_t launch_train_latent_bf16(const __nv_bfloat16* e3, int P, int Ci, const float* wmu, const float* bmu,

@@ -403,6 +403,7 @@ sv_status sv_refine_train(sv_ctx* ctx, const sv_pair* pairs, const void* const* 
     return c->t1_forward(pairs, n_pairs, nullptr, (const float* const*)coarse, (const float* const*)eps,
                          (float* const*)disp_out, (float* const*)mu_out, (float* const*)logvar_out,
                          (cudaStream_t)stream);
+  if (c->cfg.precision == SV_FP8) return c->fail(SV_ERR_UNSUPPORTED, "the FP8 form is inference only");
   if (c->cfg.precision == SV_FP64_CHECK)
     return c->train_forward<double>(pairs, coarse, eps, n_pairs, disp_out, mu_out, logvar_out, (cudaStream_t)stream);
   if (c->cfg.precision == SV_BF16)

@@ -11,6 +11,8 @@
 //   edge_up2fix  exact recomputation of the last row / column of an odd-sized (cropped)
 //                nearest-x2 + 3x3 conv output, which the 4-phase tensor-core form folds
 //                wrongly: segments of 64 border pixels x 32 channels per block.
+#include <cuda_fp8.h>
+
 #include "sv_ctx.cuh"
 
 namespace sv {
@@ -680,8 +682,92 @@ __global__ void __launch_bounds__(256) edge_up2fix(const UpFixPair* __restrict__
   }
 }
 
-// Training latent: one thread per (latent pixel, channel).
-// A thread per (pixel, output channel).  staged: the weights of both heads are staged
+// The border recompute of the FP8 form: the same geometry and pixel / channel mapping, on
+// E4M3 input codes (`in` holds bytes) and the E4M3 codes of the unfolded 3 x 3 weights with
+// their per-output-channel scale: relu(scale * sum(code * code) + bias), stored as E4M3
+// codes (out_f8) or BF16 (the last decoder layer, whose output feeds the BF16 final conv).
+__device__ __forceinline__ float e4m3_value(uint8_t c) {
+  __nv_fp8_e4m3 x;
+  x.__x = c;
+  return static_cast<float>(x);
+}
+
+__global__ void __launch_bounds__(256) edge_up2fix_f8(const UpFixPair* __restrict__ pairs, const uint8_t* __restrict__ Wq,
+                                                      const float* __restrict__ wscale, const float* __restrict__ bias,
+                                                      int cin, int cout, int relu, int out_f8) {
+  extern __shared__ __align__(16) float xsm8[];
+  float* S = xsm8;                          // [2][kFixQ][kFixCk]
+  float* Wf = xsm8 + 2 * kFixQ * kFixCk;    // [6][kFixCk][32]
+  const UpFixPair L = pairs[blockIdx.z];
+  const uint8_t* in = reinterpret_cast<const uint8_t*>(L.in);
+  const int nrow = (L.Ho & 1) ? L.Wo : 0;
+  const int ncol = (L.Wo & 1) ? L.Ho - (L.Ho & 1) : 0;
+  const int segr = (nrow + kUpFixSeg - 1) / kUpFixSeg, segc = (ncol + kUpFixSeg - 1) / kUpFixSeg;
+  int seg = blockIdx.x;
+  if (seg >= segr + segc) return;
+  const bool rowfix = seg < segr;
+  if (!rowfix) seg -= segr;
+  const int p0 = seg * kUpFixSeg;
+  const int npix = min(kUpFixSeg, (rowfix ? nrow : ncol) - p0);
+  const int cb = blockIdx.y * 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+  for (int c0 = 0; c0 < cin; c0 += kFixCk) {
+    const int ck = min(kFixCk, cin - c0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * kFixQ * ck; e += blockDim.x) {
+      const int a = e / (kFixQ * ck), r = e - a * kFixQ * ck, q = r / ck, c = r - q * ck;
+      const int uy = rowfix ? L.Ho - 2 + a : p0 - 1 + q;
+      const int ux = rowfix ? p0 - 1 + q : L.Wo - 2 + a;
+      float v = 0.f;
+      if (uy >= 0 && uy < L.Ho && ux >= 0 && ux < L.Wo)
+        v = e4m3_value(in[((size_t)(uy >> 1) * L.Wi + (ux >> 1)) * cin + c0 + c]);
+      S[((size_t)a * kFixQ + q) * kFixCk + c] = v;
+    }
+    for (int e = threadIdx.x; e < 6 * ck * 32; e += blockDim.x) {
+      const int o = e & 31, r = e >> 5, t = r / ck, c = r - t * ck;
+      const int a = t / 3, b = t - 3 * a, ky = rowfix ? a : b, kx = rowfix ? b : a;
+      Wf[((size_t)t * kFixCk + c) * 32 + o] =
+          cb + o < cout ? e4m3_value(Wq[((size_t)((cb + o) * 3 + ky) * 3 + kx) * cin + c0 + c]) : 0.f;
+    }
+    __syncthreads();
+    for (int t = 0; t < 6; ++t) {
+      const int a = t / 3, b = t - 3 * a;
+      const float* sp = S + ((size_t)a * kFixQ + warp * 8 + b) * kFixCk;
+      const float* wp = Wf + (size_t)t * kFixCk * 32 + lane;
+      for (int c = 0; c < ck; ++c) {
+        const float wv = wp[c * 32];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = fmaf(wv, sp[j * kFixCk + c], acc[j]);
+      }
+    }
+  }
+  const int co = cb + lane;
+  if (co >= cout) return;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int p = warp * 8 + j;
+    if (p >= npix) break;
+    const int Y = rowfix ? L.Ho - 1 : p0 + p, X = rowfix ? p0 + p : L.Wo - 1;
+    float v = fmaf(acc[j], wscale[co], bias[co]);
+    if (relu) v = fmaxf(v, 0.f);
+    const size_t o = ((size_t)Y * L.Wo + X) * cout + co;
+    if (out_f8)
+      reinterpret_cast<uint8_t*>(L.out)[o] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    else
+      L.out[o] = __float2bfloat16_rn(v);
+  }
+}
+
+// E4M3 codes of a BF16 activation (the first layer's output in the FP8 form).
+__global__ void bf16_to_e4m3(const bf16* __restrict__ a, uint8_t* __restrict__ b, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (uint8_t)__nv_cvt_float_to_fp8(__bfloat162float(a[i]), __NV_SATFINITE, __NV_E4M3);
+}
+
+// Training latent heads: a thread per (pixel, output channel).  staged: the weights of both heads are staged
 // transposed in shared memory ([ci][co]: consecutive threads read consecutive output
 // channels); else (widths whose weights do not fit) read from global memory.
 __global__ void train_latent_bf16(const bf16* __restrict__ e3, int P, int Ci, const float* __restrict__ wmu,
@@ -730,6 +816,23 @@ cudaError_t launch_train_latent_bf16(const bf16* e3, int P, int Ci, const float*
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 4 * 152);
   train_latent_bf16<<<grid, 256, smem, st>>>(e3, P, Ci, wmu, bmu, wlv, blv, lat, eps, mu, lv, z, staged ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_edge_up2fix_f8(const UpFixPair* pairs, int n, int max_segments, const uint8_t* Wq,
+                                  const float* wscale, const float* bias, int cin, int cout, int relu, int out_f8,
+                                  cudaStream_t st) {
+  if (n <= 0 || max_segments <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(edge_up2fix_f8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixSmem);
+  if (e != cudaSuccess) return e;
+  edge_up2fix_f8<<<dim3(max_segments, (cout + 31) / 32, n), 256, kFixSmem, st>>>(pairs, Wq, wscale, bias, cin, cout,
+                                                                                  relu, out_f8);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bf16_to_e4m3(const bf16* a, uint8_t* b, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  bf16_to_e4m3<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n);
   return cudaGetLastError();
 }
 

@@ -50,11 +50,23 @@ def test_invalid_configs_rejected(svlib):
     bad.append(c)
     c = binding.make_config(synth.NET_SMALL, 7, 5)    # precision
     bad.append(c)
+    c = binding.make_config(synth.NET_SMALL, 7, "fp8")  # FP8: a 16-wide input to a tensor-core layer
+    bad.append(c)
+    c = binding.make_config(synth.NetShape((32, 64, 128), 128, (128, 48, 32)), 7, "fp8")  # dec2 width 48
+    bad.append(c)
     for c in bad:
         assert svlib.sv_param_count(ctypes.byref(c)) == 0
         h = ctypes.c_void_p()
         assert svlib.sv_create(ctypes.byref(c), 0, ctypes.byref(h)) == binding.SV_ERR_INVALID_ARG
         assert not h.value
+
+
+def test_fp8_config_accepted(svlib):
+    # widths that are multiples of 32 where a tensor-core layer reads them (the last decoder
+    # width feeds the FP32 final conv and may be 16)
+    for shape in (synth.NET_WIDE, synth.NetShape((32, 64, 128), 128, (128, 64, 16))):
+        c = binding.make_config(shape, 9, "fp8")
+        assert svlib.sv_param_count(ctypes.byref(c)) == shape.n_params()
 
 
 def test_status_strings(svlib):

@@ -57,3 +57,51 @@ def test_quantised_activations_lie_on_the_grids():
     d3 = oracle.refine_forward_q(shape, params, p.left, coarse, act="d3")["d3"]
     bf = torch.from_numpy(d3.astype(np.float32)).bfloat16().double().numpy()
     np.testing.assert_array_equal(d3, bf)
+
+
+def _grid_weights(rng, co, k, ci):
+    """Weights E4M3 value x 2^-8 with every output channel reaching 448 x 2^-8."""
+    grid = torch.arange(0, 127, dtype=torch.uint8).view(torch.float8_e4m3fn).float().numpy()
+    grid = grid[np.isfinite(grid)]
+    c = rng.choice(np.concatenate([grid, -grid]), size=(co, k, k, ci))
+    c.reshape(co, -1)[:, 0] = 448.0
+    return (c * 2.0 ** -8).astype(np.float32)
+
+
+@pytest.mark.parametrize("mode,k,stride", [(0, 3, 2), (1, 1, 1)])
+def test_qconv_layer_with_exact_codes_is_conv2d(mode, k, stride):
+    rng = np.random.default_rng(5 + mode)
+    co, ci, Hi, Wi = 24, 16, 13, 18
+    wt = _grid_weights(rng, co, k, ci)
+    b = rng.normal(size=co).astype(np.float32)
+    x = rng.normal(size=(Hi, Wi, ci))
+    Ho, Wo = ((Hi + 1) // 2, (Wi + 1) // 2) if mode == 0 else (Hi, Wi)
+    got = oracle.qconv_layer(x, wt, b, mode, (Ho, Wo), relu=False, out_round="none")
+    xt = torch.from_numpy(x).permute(2, 0, 1)[None]
+    wt_t = torch.from_numpy(wt.astype(np.float64)).permute(0, 3, 1, 2)
+    want = torch.nn.functional.conv2d(xt, wt_t, torch.from_numpy(b.astype(np.float64)), stride=stride,
+                                      padding=k // 2)[0].permute(1, 2, 0).numpy()
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
+def test_qconv_layers_chain_to_the_quantised_forward():
+    shape = synth.NET_WIDE
+    params = synth.he_normal_weights(shape, 7)
+    H, W = 75, 130
+    p = synth.make_pair(W, H, 40.0, 701)
+    coarse = np.random.default_rng(3).integers(0, 12, size=(H // 4, W // 4)).astype(np.float64)
+    sl = oracle.param_slices(shape)
+    (_, _), L1, L2, L3 = oracle.level_sizes(H, W)
+    acts = {a: oracle.refine_forward_q(shape, params, p.left, coarse, act=a)[a]
+            for a in ("e1", "e2", "e3", "z", "d1", "d2", "d3")}
+    chain = [("enc2", "e1", "e2", 0, L2, "e4m3", True), ("enc3", "e2", "e3", 0, L3, "e4m3", True),
+             ("mu", "e3", "z", 1, L3, "e4m3", False), ("dec1", "z", "d1", 2, L2, "e4m3", True),
+             ("dec2", "d1", "d2", 2, L1, "e4m3", True), ("dec3", "d2", "d3", 2, (H, W), "bf16", True)]
+    names = [n for n, *_ in shape.layers()]
+    for layer, a_in, a_out, mode, hw, rnd, relu in chain:
+        assert layer in names, layer
+        ow, wshape, ob, co = sl[layer]
+        wt = params[ow:ow + int(np.prod(wshape))].reshape(wshape)
+        b = params[ob:ob + co]
+        got = oracle.qconv_layer(acts[a_in], wt, b, mode, hw, relu=relu, out_round=rnd)
+        np.testing.assert_array_equal(got, acts[a_out], err_msg=layer)
