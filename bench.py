@@ -511,7 +511,7 @@ def run_ours(args):
         results[form] = t
 
     # -------------------------------------------------------------- rooflines of every kernel
-    head = "bf16" if "bf16" in results else "fp32"
+    head = next(f for f in ("bf16", "fp8", "fp32") if f in results)
     R = results[head]
     sizes = [(W, H)] * B
     tables = {}
@@ -690,7 +690,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16" if head == "bf16" else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"bf16": "bf16", "fp8": "e4m3", "fp32": "f32"}[head], "data": "synthetic",
         "config": arm_config(B, world, head, n_distinct),
         "roofline": roof,
         "rooflines": tables[head],

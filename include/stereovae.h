@@ -73,7 +73,7 @@ typedef enum {
  *          E4M3 codes of relu(s_co * acc + bias); dec3 writes BF16; the first and last layers,
  *          the upsampling and the residual are as SV_BF16.  enc, latent and dec1 / dec2 widths
  *          are multiples of 32.  sv_refine_train returns SV_ERR_UNSUPPORTED; sv_autotune
- *          tunes only SV_BF16 contexts; sv_debug_activation returns e2 .. d2 as E4M3 bytes. */
+ *          tunes only SV_BF16 contexts; sv_debug_activation returns e1 .. d2 as E4M3 bytes. */
 typedef enum { SV_FP32 = 0, SV_BF16 = 1, SV_FP64_CHECK = 2, SV_FP8 = 3 } sv_precision;
 
 /* sv_config.flags: selects the refinement network.

@@ -1839,7 +1839,8 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
   for (int i = 0; i < n; ++i) {
     const sv_pair& p = pairs[i];
     eps_[i] = {p.left, p.pitch, p.width, p.height, p.width / 4, p.height / 4, coarse ? coarse[i] : nullptr,
-               coarse_f ? coarse_f[i] : nullptr, act(0, i), act(6, i), out[i], CUtensorMap{}};
+               coarse_f ? coarse_f[i] : nullptr, act(0, i), act(6, i), out[i],
+               f8 && enc1_on_tc() ? (uint8_t*)act_in(0, i) : nullptr, CUtensorMap{}};
     if (final_staged_by_tma(net.dec[2]) &&
         !make_tmap_tile(&eps_[i].d3_map, act(6, i), net.dec[2], p.width, p.height, 34, final_tile_rows(net.dec[2]) + 2))
       return fail(SV_ERR_CUDA, "pair %d: cuTensorMapEncodeTiled failed (final conv)", i);
@@ -1917,7 +1918,7 @@ sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream
       return s;
   }
   const bool f8 = cfg.precision == SV_FP8;
-  if (f8) {
+  if (f8 && !enc1_on_tc()) {  // (the tensor-core enc1 writes the codes itself)
     LaunchScope ls(*this, "e1_to_e4m3", st);
     if ((s = cuda(launch_bf16_to_e4m3((const __nv_bfloat16*)tc_act[0].p, (uint8_t*)tc_act[7].p, r.e1_count, st),
                   "e1 to E4M3")))

@@ -650,14 +650,16 @@ sv_status sv_debug_activation(sv_ctx* ctx, int which, int pair, void* dst, size_
   if (c->t1) return c->fail(SV_ERR_UNSUPPORTED, "not available for the Table I network");
   if (which < 0 || which > 6 || pair < 0 || pair >= (int)c->tc_off.size() || !dst)
     return c->fail(SV_ERR_INVALID_ARG, "no such activation");
-  // FP8 contexts keep e2 .. d2 as E4M3 codes (one byte per element)
-  const size_t es = c->cfg.precision == SV_FP8 && which >= 1 && which <= 5 ? 1 : sizeof(__nv_bfloat16);
+  // FP8 contexts keep e1 .. d2 as E4M3 codes (one byte per element; e1's codes in tc_act[7])
+  const bool f8 = c->cfg.precision == SV_FP8 && which <= 5;
+  const size_t es = f8 ? 1 : sizeof(__nv_bfloat16);
+  const int buf = f8 && which == 0 ? 7 : which;
   if (bytes != c->tc_len[pair][which] * es)
     return c->fail(SV_ERR_INVALID_ARG, "activation has %zu bytes", c->tc_len[pair][which] * es);
   if (which == 6 && c->last_fused)
     return c->fail(SV_ERR_STATE, "d3 stayed on chip (fused final conv); set option fused_final 0 to keep it");
   DeviceGuard g(c->device);
-  return c->cuda(cudaMemcpy(dst, (const unsigned char*)c->tc_act[which].p + c->tc_off[pair][which] * es, bytes,
+  return c->cuda(cudaMemcpy(dst, (const unsigned char*)c->tc_act[buf].p + c->tc_off[pair][which] * es, bytes,
                             cudaMemcpyDeviceToHost), "copy activation");
 }
 

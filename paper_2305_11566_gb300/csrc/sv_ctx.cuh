@@ -122,6 +122,7 @@ struct Ctx {
   int fused_ring = 0;                   // fused kernel's staged-row ring: 0 as deep as shared memory allows
   int fused_prefetch = 4;               // fused kernel: rows prefetched into L2 ahead of the loaded row
   int enc1_tensor = 1;                  // 1: enc1 on the tensor cores where its width allows
+  bool enc1_on_tc() const { return enc1_tensor && (net.enc[0] == 16 || net.enc[0] == 32 || net.enc[0] == 64); }
   int split_rows = 1;                   // 1: layers without a spare staged row stage channel blocks
   int host_copy = 1;                    // sv_pipeline_host: 0 copy calls, 1 gather kernel in, 2 kernels both ways
   bool last_fused = false;              // the last tensor-core call did not materialise d3

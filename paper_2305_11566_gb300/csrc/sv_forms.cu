@@ -68,7 +68,11 @@ sv_status Ctx::pipeline_graph(const sv_pair* pairs, int n, float* const* out, cu
   k((uint64_t)spin_limit);
   k((uint64_t)prof_on);
   for (auto& t : r.tabs) k(((uint64_t)t.hs << 32) | (uint32_t)t.grid);
-  for (auto& p : r.plans) k(((uint64_t)p.NT << 32) | (uint32_t)p.ring);
+  for (auto& p : r.plans) k(((uint64_t)p.NT << 32) | ((uint64_t)p.split << 31) | (uint32_t)p.ring);
+  // launch choices baked into the captured kernels' arguments
+  k((uint64_t)enc1_tensor | ((uint64_t)r.fused << 1) | ((uint64_t)(uint32_t)fused_prefetch << 2) |
+    ((uint64_t)(uint32_t)r.fused_ring << 34));
+  k(((uint64_t)(uint32_t)r.fused_hs << 32) | (uint32_t)r.fused_grid);
   ++graph_clock;
   for (auto& g : graphs) {
     if (g.key != key) continue;

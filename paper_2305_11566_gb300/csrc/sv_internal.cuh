@@ -145,6 +145,7 @@ struct alignas(64) EdgePair {
   __nv_bfloat16* e1;        // enc1 output [H1][W1][C1]
   const __nv_bfloat16* d3;  // last decoder output [H][W][C]
   float* Y;                 // refined disparity [H][W]
+  uint8_t* e1q;             // FP8 form: the tensor-core enc1 writes E4M3 codes of e1 here instead
   CUtensorMap d3_map;       // TMA view of d3 for the final conv (final_staged_by_tma(C))
 };
 // Row copy between device-accessible buffers (host_io.cu): `height` rows of `width`

@@ -361,7 +361,22 @@ __global__ void __launch_bounds__(256) enc1_tc(const EdgePair* __restrict__ pair
         if (C1 >= 32) tmem_ld32_e(taddr + c0, r);
         else tmem_ld16_e(taddr + c0, r);
         constexpr int CW = C1 >= 32 ? 32 : C1;
-        if (X < W1 && Y < H1) {
+        if (X < W1 && Y < H1 && P->e1q) {
+          // FP8 form: E4M3 codes of the BF16-rounded output (16 per 16-byte store)
+          uint32_t pk[CW / 4];
+#pragma unroll
+          for (int e = 0; e < CW; e += 4) {
+            float q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              q[u] = __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(r[e + u]) + bias_s[c0 + e + u], 0.f)));
+            pk[e / 4] = (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(q[0], q[1]), __NV_SATFINITE, __NV_E4M3) |
+                        ((uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(q[2], q[3]), __NV_SATFINITE, __NV_E4M3) << 16);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(P->e1q + ((size_t)Y * W1 + X) * C1 + c0);
+#pragma unroll
+          for (int i = 0; i < CW / 16; ++i) dst[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+        } else if (X < W1 && Y < H1) {
           uint32_t pk[CW / 2];
 #pragma unroll
           for (int e = 0; e < CW; e += 2) {

@@ -75,22 +75,27 @@ def layer_weights(params, name):
     return params[ow:ow + int(np.prod(wshape))].reshape(wshape), params[ob:ob + co]
 
 
-@pytest.mark.parametrize("W,H,D", [(256, 128, 16), (333, 97, 24), (250, 131, 20)])
-def test_fp8_layers_match_the_quantised_oracle(ctx, W, H, D):
+@pytest.mark.parametrize("W,H,D,enc1_tc", [(256, 128, 16, 1), (333, 97, 24, 1), (250, 131, 20, 1), (333, 97, 24, 0)])
+def test_fp8_layers_match_the_quantised_oracle(ctx, W, H, D, enc1_tc):
+    """enc1_tc 1: the tensor-core first layer writes the E4M3 codes of e1 itself; 0: the
+    CUDA-core first layer writes BF16 and a separate kernel converts it."""
     p = synth.make_pair(W, H, 50.0, 8100 + W)
     disp_o = oracle.coarse_match(p.left, p.right, 5, D)[0]
     params = synth.he_normal_weights(SHAPE, 7)
     dp = binding.to_device(p, D)
-    Y = ctx.refine([dp], [torch.from_numpy(disp_o.astype(np.int16)).cuda()])[0]
-    ctx.synchronize()
+    ctx.set_option("enc1_tensor", enc1_tc)
+    try:
+        Y = ctx.refine([dp], [torch.from_numpy(disp_o.astype(np.int16)).cuda()])[0]
+        ctx.synchronize()
+    finally:
+        ctx.set_option("enc1_tensor", 1)
     g = {a: ctx.debug_activation(i, 0, act_shape(H, W, a)).astype(np.float64)
          for i, a in enumerate(["e1", "e2", "e3", "z", "d1", "d2", "d3"])}
-    # e1: the first layer's BF16 output (as the BF16 form); the tensor-core layers read its codes
-    e1_ref = oracle.refine_activation(SHAPE, params, p.left, disp_o.astype(np.float64), "e1")
-    assert np.abs(g["e1"] - e1_ref).max() <= 3e-2 * np.abs(e1_ref).max()
-    e1_codes = torch.from_numpy(g["e1"].astype(np.float32)).to(torch.float8_e4m3fn).double().numpy()
+    # e1: E4M3 codes of the first layer's BF16-rounded output, against the oracle's
+    e1_o = oracle.refine_forward_q(SHAPE, params, p.left, disp_o.astype(np.float64), act="e1")["e1"]
+    check_codes(g["e1"], e1_o, e4m3_ordinal, f"{W}x{H} enc1")
     (_, _), L1, L2, L3 = oracle.level_sizes(H, W)
-    chain = [("enc2", e1_codes, "e2", 0, L2, "e4m3", True), ("enc3", g["e2"], "e3", 0, L3, "e4m3", True),
+    chain = [("enc2", g["e1"], "e2", 0, L2, "e4m3", True), ("enc3", g["e2"], "e3", 0, L3, "e4m3", True),
              ("mu", g["e3"], "z", 1, L3, "e4m3", False), ("dec1", g["z"], "d1", 2, L2, "e4m3", True),
              ("dec2", g["d1"], "d2", 2, L1, "e4m3", True), ("dec3", g["d2"], "d3", 2, (H, W), "bf16", True)]
     for name, x, out, mode, hw, rnd, relu in chain:
