@@ -6,8 +6,9 @@
 //                       output size (decoder); bias + optional ReLU epilogue.
 //   enc1 source         the network input x0 = (L / 256, U / 256) built while staging:
 //                       U = 4 * bilinear(coarse) (upsampling fused into the first conv).
-//   final_kernel        3x3 conv to one channel + bias + U recomputed (the residual).
-//   latent_kernel       mean / log-variance heads (1x1) and z = mu + eps exp(lv / 2).
+//   final_tiled_kernel  3x3 conv to one channel + bias + U recomputed (the residual).
+//   latent heads        1x1 convolutions (conv_direct_kernel); reparam_kernel z = mu + eps exp(lv / 2)
+//                       (latent_kernel computes both heads per thread where an output is absent).
 #include "sv_internal.cuh"
 
 namespace sv {
@@ -64,10 +65,6 @@ struct SrcEnc1 {
 template <typename OutT, typename T> __device__ __forceinline__ OutT to_out(T v) { return (OutT)v; }
 template <> __device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16, float>(float v) {
   return __float2bfloat16_rn(v);
-}
-template <typename T, typename InT> __device__ __forceinline__ T from_in(InT v) { return (T)v; }
-template <> __device__ __forceinline__ float from_in<float, __nv_bfloat16>(__nv_bfloat16 v) {
-  return __bfloat162float(v);
 }
 
 // One CTA: TH x TW output pixels x COT output channels; input channels in chunks of CIC
@@ -139,30 +136,50 @@ cudaError_t run_conv(const Src& src, int Ci, const T* wt, const T* bias, int Co,
   return cudaGetLastError();
 }
 
-// final layer: Y = U + b + sum_{tap, ci} w * d3 (zero padded), one pixel per thread
-template <typename T, typename CoarseT, typename OutT, typename InT = T>
-__global__ void __launch_bounds__(256)
-final_kernel(const InT* __restrict__ in, int W, int H, int Ci, const T* __restrict__ wt, const T* __restrict__ bias,
-             const CoarseT* __restrict__ coarse, int w, int h, OutT* __restrict__ Y) {
-  extern __shared__ __align__(16) unsigned char fsm[];
-  T* ws = reinterpret_cast<T*>(fsm);
-  for (int e = threadIdx.x; e < 9 * Ci; e += blockDim.x) ws[e] = wt[e];
-  __syncthreads();
-  const int X = blockIdx.x * blockDim.x + threadIdx.x, Yy = blockIdx.y;
-  if (X >= W) return;
-  T acc = bias[0];
-  for (int ky = 0; ky < 3; ++ky) {
-    int vy = Yy + ky - 1;
-    if (vy < 0 || vy >= H) continue;
-    for (int kx = 0; kx < 3; ++kx) {
-      int vx = X + kx - 1;
-      if (vx < 0 || vx >= W) continue;
-      const InT* ip = in + ((size_t)vy * W + vx) * Ci;
-      const T* wp = ws + (ky * 3 + kx) * Ci;
-      for (int ci = 0; ci < Ci; ++ci) acc = fma(wp[ci], from_in<T, InT>(ip[ci]), acc);
+// final layer, tiled: a CTA computes an FH x FW output tile; the (FH + 2) x (FW + 2) input
+// window is staged channel-planar in shared memory, FCIC channels at a time (zero outside the
+// image), with the chunk's weights; one output pixel per thread.
+constexpr int FW = 32, FH = 8, FCIC = 8;
+template <typename T, typename CoarseT, typename OutT>
+__global__ void __launch_bounds__(FW * FH)
+final_tiled_kernel(const T* __restrict__ in, int W, int H, int Ci, const T* __restrict__ wt, const T* __restrict__ bias,
+                   const CoarseT* __restrict__ coarse, int w, int h, OutT* __restrict__ Y) {
+  __shared__ T tile[FCIC][FH + 2][FW + 2];
+  __shared__ T ws[9][FCIC];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FW + tx;
+  const int X0 = blockIdx.x * FW, Y0 = blockIdx.y * FH;
+  T acc = (T)0;
+  for (int ci0 = 0; ci0 < Ci; ci0 += FCIC) {
+    for (int e = tid; e < (FH + 2) * (FW + 2) * FCIC; e += FW * FH) {
+      const int ci = e % FCIC, px = e / FCIC;
+      const int r = px / (FW + 2), c = px - r * (FW + 2);
+      const int vy = Y0 - 1 + r, vx = X0 - 1 + c;
+      const bool ok = vy >= 0 && vy < H && vx >= 0 && vx < W && ci0 + ci < Ci;
+      tile[ci][r][c] = ok ? in[((size_t)vy * W + vx) * Ci + ci0 + ci] : (T)0;
     }
+    for (int e = tid; e < 9 * FCIC; e += FW * FH) {
+      const int ci = e % FCIC, tap = e / FCIC;
+      ws[tap][ci] = ci0 + ci < Ci ? wt[(size_t)tap * Ci + ci0 + ci] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+        for (int ci = 0; ci < FCIC; ++ci) acc = fma(ws[ky * 3 + kx][ci], tile[ci][ty + ky][tx + kx], acc);
+    __syncthreads();
   }
-  Y[(size_t)Yy * W + X] = (OutT)(upsample4_at<T, CoarseT>(coarse, w, h, X, Yy) + acc);
+  const int X = X0 + tx, Yy = Y0 + ty;
+  if (X < W && Yy < H) Y[(size_t)Yy * W + X] = (OutT)(upsample4_at<T, CoarseT>(coarse, w, h, X, Yy) + (bias[0] + acc));
+}
+
+// z = mu + eps exp(lv / 2) (training form of the latent, after the two 1x1 heads)
+template <typename T>
+__global__ void reparam_kernel(const T* __restrict__ mu, const T* __restrict__ lv, const T* __restrict__ eps, size_t n,
+                               T* __restrict__ z) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = mu[i] + eps[i] * exp((T)0.5 * lv[i]);
 }
 
 template <typename T>
@@ -223,15 +240,33 @@ cudaError_t launch_enc1(const uint8_t* L, int pitch, int W, int H, const CoarseT
 template <typename T, typename CoarseT, typename OutT>
 cudaError_t launch_final(const T* in, int W, int H, int Ci, const T* wt, const T* bias, const CoarseT* coarse, int w,
                          int h, OutT* Y, cudaStream_t st) {
-  dim3 grid((W + 127) / 128, H);
-  final_kernel<T, CoarseT, OutT><<<grid, 128, sizeof(T) * 9 * Ci, st>>>(in, W, H, Ci, wt, bias, coarse, w, h, Y);
+  dim3 grid((W + FW - 1) / FW, (H + FH - 1) / FH);
+  final_tiled_kernel<T, CoarseT, OutT><<<grid, dim3(FW, FH), 0, st>>>(in, W, H, Ci, wt, bias, coarse, w, h, Y);
   return cudaGetLastError();
 }
 
+// Latent heads on the [H3][W3] grid.  Inference (no eps): z = the mean head, a 1x1
+// convolution.  Training with both head outputs given: the two heads as 1x1 convolutions
+// into mu and lv, then the reparameterisation; otherwise one thread per (pixel, channel)
+// computing both heads.
 template <typename T>
-cudaError_t launch_latent(const T* e3, int P, int Ci, const T* wmu, const T* bmu, const T* wlv, const T* blv, int lat,
-                          const T* eps, T* mu, T* lv, T* z, cudaStream_t st) {
-  size_t n = (size_t)P * lat;
+cudaError_t launch_latent(const T* e3, int H3, int W3, int Ci, const T* wmu, const T* bmu, const T* wlv, const T* blv,
+                          int lat, const T* eps, T* mu, T* lv, T* z, cudaStream_t st) {
+  const int P = H3 * W3;
+  const size_t n = (size_t)P * lat;
+  if (!eps && !lv && !mu && z) {
+    DirectConvArgs<T> a{e3, H3, W3, Ci, wmu, bmu, lat, H3, W3, 0, z};
+    return launch_conv_direct<T>(a, CM_S1, 1, st);
+  }
+  if (eps && mu && lv && z) {
+    DirectConvArgs<T> a{e3, H3, W3, Ci, wmu, bmu, lat, H3, W3, 0, mu};
+    cudaError_t e = launch_conv_direct<T>(a, CM_S1, 1, st);
+    if (e != cudaSuccess) return e;
+    a = {e3, H3, W3, Ci, wlv, blv, lat, H3, W3, 0, lv};
+    if ((e = launch_conv_direct<T>(a, CM_S1, 1, st)) != cudaSuccess) return e;
+    reparam_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mu, lv, eps, n, z);
+    return cudaGetLastError();
+  }
   latent_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(e3, P, Ci, wmu, bmu, wlv, blv, lat, eps, mu, lv, z);
   return cudaGetLastError();
 }
@@ -254,9 +289,9 @@ template cudaError_t launch_final<float, float, float>(const float*, int, int, i
                                                        const float*, int, int, float*, cudaStream_t);
 template cudaError_t launch_final<double, double, double>(const double*, int, int, int, const double*, const double*,
                                                           const double*, int, int, double*, cudaStream_t);
-template cudaError_t launch_latent<float>(const float*, int, int, const float*, const float*, const float*,
+template cudaError_t launch_latent<float>(const float*, int, int, int, const float*, const float*, const float*,
                                           const float*, int, const float*, float*, float*, float*, cudaStream_t);
-template cudaError_t launch_latent<double>(const double*, int, int, const double*, const double*, const double*,
+template cudaError_t launch_latent<double>(const double*, int, int, int, const double*, const double*, const double*,
                                            const double*, int, const double*, double*, double*, double*, cudaStream_t);
 
 }  // namespace sv

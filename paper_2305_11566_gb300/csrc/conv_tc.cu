@@ -49,7 +49,7 @@ using bf16 = __nv_bfloat16;
 
 enum Mode { TM_S2 = 0, TM_UP2 = 1, TM_P1 = 2 };
 
-struct alignas(64) LayerPair {
+struct alignas(128) LayerPair {
   const bf16* in;
   bf16* out;
   int Hi, Wi;  // input size
@@ -106,10 +106,13 @@ __host__ __device__ inline int taps(int mode) { return mode == TM_S2 ? 9 : mode 
 __host__ __device__ inline size_t b_bytes(int mode, int NT, int cin) { return (size_t)taps(mode) * NT * cin * 2; }
 // ring: staged units, whole rows or (split) one channel block of a row each
 // f8: the FP8 form also keeps a per-channel scale beside the bias
+// epilogue staging: per epilogue warp 32 pixels x 32 BF16 channels (the stores leave shared
+// memory as whole 64-byte pixel segments instead of one 16-byte piece per pixel and lane)
+constexpr uint32_t kStageBytes = 4 * 32 * 64;
 __host__ __device__ inline size_t smem_bytes(int mode, int NT, int cin, int ring, bool split = false, bool f8 = false) {
   const size_t unit = split ? row_bytes(mode, cin) / (cin * 2 / rb_of(cin)) : row_bytes(mode, cin);
-  return 1024 + (b_bytes(mode, NT, cin) + (size_t)NT * (f8 ? 8 : 4) + 1023) / 1024 * 1024 + (size_t)ring * unit +
-         (size_t)(2 * ring + 4) * kBarBytes + 16;
+  return 1024 + (b_bytes(mode, NT, cin) + (size_t)NT * (f8 ? 8 : 4) + kStageBytes + 1023) / 1024 * 1024 +
+         (size_t)ring * unit + (size_t)(2 * ring + 4) * kBarBytes + 16;
 }
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -319,7 +322,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   const uint32_t unitb = NSET * KPU * KBS;
   const uint32_t sB = base;
   const uint32_t sBias = sB + (uint32_t)T * NT * cin * 2;
-  const uint32_t sA = (sBias + NT * (F8 ? 8 : 4) + 1023u) & ~1023u;
+  const uint32_t sStage = sBias + NT * (F8 ? 8 : 4);  // 16-byte aligned (NT >= 16)
+  const uint32_t sA = (sStage + kStageBytes + 1023u) & ~1023u;
   const uint32_t bars = sA + ring * unitb;
   const uint32_t full0 = bars, empty0 = bars + ring * 8, accf0 = bars + 2 * ring * 8, acce0 = accf0 + 16;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + (acce0 + 16 - base));
@@ -462,23 +466,27 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
                 a0[t] = desc_lo(sA + (sl >= ring ? sl - ring : sl) * unitb + (uint32_t)(se * KB) * KBS + (uint32_t)co * RB,
                                 16);
               }
+              // taps run in row order (T / RA taps per staged row); in the last channel block a
+              // row the strip's next tile no longer reads goes back to the producer as soon as
+              // the MMAs issued up to its last tap complete (a commit on its empty barrier), so
+              // that its reload overlaps the rest of the tile's MMAs
+              constexpr int TPR = T / RA;
               for (int kb = 0; kb < KB; ++kb) {
                 const uint32_t ak = (uint32_t)kb * (KBS >> 4), bk = (uint32_t)kb * (16 * KPR);
 #pragma unroll
-                for (int t = 0; t < T; ++t)
+                for (int t = 0; t < T; ++t) {
 #pragma unroll
                   for (int k4 = 0; k4 < KPR; ++k4)
                     // next 16 channels: +32 B inside the swizzled pixel row, +256 B in B
                     mma_elect<F8>(dcol, a0[t] + ak + 2 * k4, a_hi, b0[t] + bk + 16 * k4, b_hi, idesc,
                                   (kb | t | k4) != 0 ? 1u : 0u);
+                  if (kb == KB - 1 && (t + 1) % TPR == 0 && (t + 1) / TPR <= nrel) {
+                    const uint32_t sl = tb.slot + (uint32_t)((t + 1) / TPR - 1);
+                    mma_commit_elect(empty0 + 8 * (sl >= ring ? sl - ring : sl));
+                  }
+                }
               }
               mma_commit_elect(accf0 + 8 * buf);
-              // the rows the strip's next tile no longer reads go back to the producer as
-              // soon as these MMAs complete (one commit per row on its empty barrier)
-              for (int r = 0; r < nrel; ++r) {
-                const uint32_t sl = tb.slot + (uint32_t)r;
-                mma_commit_elect(empty0 + 8 * (sl >= ring ? sl - ring : sl));
-              }
             }
           }
           if (SPLIT && use > 0 && !mbar_wait_warp(acce0 + 8 * buf, (use - 1) & 1, p.spin)) ok = false;
@@ -564,29 +572,32 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
           if (NT >= 32) tmem_ld32(trow + c0, r);
           else tmem_ld16(trow + c0, r);
           constexpr int CW = NT >= 32 ? 32 : NT;
-          if (valid && F8 && p.out_f8) {
-            // E4M3 codes: relu(scale * acc + bias), 4 per word, 16 per 16-byte store
-            uint32_t packed[CW / 4];
+          const bool f8out = F8 && p.out_f8;  // warp-uniform
+          if (f8out) {
+            if (valid) {
+              // E4M3 codes: relu(scale * acc + bias), 4 per word, 16 per 16-byte store
+              uint32_t packed[CW / 4];
 #pragma unroll
-            for (int e = 0; e < CW; e += 4) {
-              float v[4];
+              for (int e = 0; e < CW; e += 4) {
+                float v[4];
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                v[q] = fmaf(__uint_as_float(r[e + q]), bias_s[NT + c0 + e + q], bias_s[c0 + e + q]);
-                if (p.relu) v[q] = fmaxf(v[q], 0.f);
+                for (int q = 0; q < 4; ++q) {
+                  v[q] = fmaf(__uint_as_float(r[e + q]), bias_s[NT + c0 + e + q], bias_s[c0 + e + q]);
+                  if (p.relu) v[q] = fmaxf(v[q], 0.f);
+                }
+                const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[0], v[1]), __NV_SATFINITE, __NV_E4M3);
+                const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v[2], v[3]), __NV_SATFINITE, __NV_E4M3);
+                packed[e / 4] = lo | (hi << 16);
               }
-              const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[0], v[1]), __NV_SATFINITE, __NV_E4M3);
-              const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v[2], v[3]), __NV_SATFINITE, __NV_E4M3);
-              packed[e / 4] = lo | (hi << 16);
-            }
-            uint8_t* ob = reinterpret_cast<uint8_t*>(out) + ((size_t)oy * Wo + ox) * p.cout + n0 + c0;
-            if constexpr (CW >= 16) {
-              uint4* dst = reinterpret_cast<uint4*>(ob);
+              uint8_t* ob = reinterpret_cast<uint8_t*>(out) + ((size_t)oy * Wo + ox) * p.cout + n0 + c0;
+              if constexpr (CW >= 16) {
+                uint4* dst = reinterpret_cast<uint4*>(ob);
 #pragma unroll
-              for (int v = 0; v < CW / 16; ++v)
-                dst[v] = make_uint4(packed[4 * v], packed[4 * v + 1], packed[4 * v + 2], packed[4 * v + 3]);
+                for (int v = 0; v < CW / 16; ++v)
+                  dst[v] = make_uint4(packed[4 * v], packed[4 * v + 1], packed[4 * v + 2], packed[4 * v + 3]);
+              }
             }
-          } else if (valid) {
+          } else {
             uint32_t packed[CW / 2];
 #pragma unroll
             for (int e = 0; e < CW; e += 2) {
@@ -605,10 +616,32 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
               __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
               packed[e / 2] = *reinterpret_cast<uint32_t*>(&h);
             }
-            uint4* dst = reinterpret_cast<uint4*>(op + c0);
+            if constexpr (CW == 32) {
+              // through the warp's stage: lane = pixel writes its four 16-byte pieces (piece
+              // q at slot q ^ ((pixel >> 1) & 3): conflict-free), then four lanes per pixel
+              // store its 64 bytes, eight pixels per instruction
+              uint4* sw = reinterpret_cast<uint4*>(gbase + (sStage - base)) + warp * 128;
 #pragma unroll
-            for (int v = 0; v < CW / 8; ++v)
-              dst[v] = make_uint4(packed[4 * v], packed[4 * v + 1], packed[4 * v + 2], packed[4 * v + 3]);
+              for (int q = 0; q < 4; ++q)
+                sw[lane * 4 + (q ^ ((lane >> 1) & 3))] =
+                    make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+              __syncwarp();
+#pragma unroll
+              for (int s8 = 0; s8 < 4; ++s8) {
+                const int pp = 8 * s8 + (lane >> 2), q = lane & 3;
+                const uint4 v = sw[pp * 4 + (q ^ ((pp >> 1) & 3))];
+                const int jp = st.j0 + warp * 32 + pp;
+                const int oxp = MODE == TM_UP2 ? 2 * jp + px : jp;
+                if (i < Hu && jp < Wu && oy < Ho && oxp < Wo)
+                  *reinterpret_cast<uint4*>(out + ((size_t)oy * Wo + oxp) * p.cout + n0 + c0 + 8 * q) = v;
+              }
+              __syncwarp();
+            } else if (valid) {
+              uint4* dst = reinterpret_cast<uint4*>(op + c0);
+#pragma unroll
+              for (int v = 0; v < CW / 8; ++v)
+                dst[v] = make_uint4(packed[4 * v], packed[4 * v + 1], packed[4 * v + 2], packed[4 * v + 3]);
+            }
           }
         }
         tc_fence_before();
@@ -647,7 +680,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
 // subtract the kernel row that falls on the cropped half (4 extra MMA groups with B
 // negated, reusing phase-1 blocks), which gives the cropped conv.  Odd output widths are not
 // handled here.
-struct alignas(64) FusedPair {
+struct alignas(128) FusedPair {
   float* Y;                    // refined disparity [Ho][Wo]
   const int16_t* coarse;       // coarse map [h4][w4]
   int Hu, Wu, Ho, Wo, w4, h4;  // input (d2) rows / cols, output size, coarse-map size
@@ -1768,7 +1801,7 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
   tc_len = lens;
   r.host.clear();
   auto put = [&](const void* src, size_t bytes) {
-    size_t o = (r.host.size() + 63) / 64 * 64;  // tensor maps need 64-byte alignment
+    size_t o = (r.host.size() + 127) / 128 * 128;  // the structs holding tensor maps are 128-byte aligned
     r.host.resize(o + bytes);
     memcpy(r.host.data() + o, src, bytes);
     return o;

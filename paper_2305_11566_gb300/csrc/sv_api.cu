@@ -195,7 +195,7 @@ sv_status Ctx::refine_direct(const sv_pair& p, const void* coarse_map, bool coar
   { SV_SCOPE(enc3); s = cuda(launch_conv_direct<T>(a, CM_S2, 3, st), "enc3"); }
   if (s) return s;
   const bool train = eps != nullptr || lv_out != nullptr;
-  { SV_SCOPE(latent); s = cuda(launch_latent<T>(e3, (int)P3, net.enc[2], Wl(L_MU), Bl(L_MU), Wl(L_LV), Bl(L_LV), net.lat, eps, mu_out,
+  { SV_SCOPE(latent); s = cuda(launch_latent<T>(e3, lv.H[3], lv.W[3], net.enc[2], Wl(L_MU), Bl(L_MU), Wl(L_LV), Bl(L_LV), net.lat, eps, mu_out,
                                  train ? lv_out : nullptr, z, st),
                 "latent"); }
   if (s) return s;

@@ -137,7 +137,7 @@ cudaError_t launch_final(const T* in, int W, int H, int Ci, const T* wt, const T
                          int w, int h, OutT* Y, cudaStream_t st);
 
 // Per-pair descriptors of the batched CUDA-core layers of the tensor-core form.
-struct alignas(64) EdgePair {
+struct alignas(128) EdgePair {
   const uint8_t* L;
   int pitch, W, H, w, h;
   const int16_t* coarse;    // integer coarse map (inference), or
@@ -225,9 +225,9 @@ cudaError_t launch_wgrad_tiled(const float* gout, int Ho, int Wo, int Co, const 
                                cudaStream_t st);
 size_t wgrad_slot_floats(int Ho, int Wo, int Co, int Ci, int ks);
 
-// latent heads: mu = 1x1(e3) + b; optionally logvar and z = mu + eps * exp(lv / 2).
+// latent heads on the H3 x W3 grid: mu = 1x1(e3) + b; optionally logvar and z = mu + eps * exp(lv / 2).
 template <typename T>
-cudaError_t launch_latent(const T* e3, int P, int Ci, const T* wmu, const T* bmu, const T* wlv, const T* blv,
+cudaError_t launch_latent(const T* e3, int H3, int W3, int Ci, const T* wmu, const T* bmu, const T* wlv, const T* blv,
                           int lat, const T* eps, T* mu, T* lv, T* z, cudaStream_t st);
 
 }  // namespace sv
