@@ -69,61 +69,78 @@ __device__ __forceinline__ void coarse_axis(float v, int n, int& i0, int& i1, fl
   f = s - (float)i0;
 }
 
+// The window's global loads (image bytes and the coarse values of T), all issued in one pass
+// before any is used, so that their latency overlaps whatever the kernel does next.
+constexpr int E1NTT = (E1CR * E1C + 255) / 256, E1NXS = (E1R * E1C + 255) / 256;
+struct E1Loads {
+  uint32_t lv[E1NXS];
+  float c0v[E1NTT], c1v[E1NTT], fxv[E1NTT];
+  int cy_lo;
+};
 template <typename CT>
-__device__ __forceinline__ void enc1_stage(const EdgePair* P, const CT* __restrict__ cmap, int X0, int Y0,
-                                           float (*xs)[E1C][2], float (*T)[E1C]) {
+__device__ __forceinline__ void enc1_stage_load(const EdgePair* P, const CT* __restrict__ cmap, int X0, int Y0,
+                                                E1Loads& ld) {
   const int Wd = P->W, Hd = P->H, w4 = P->w, h4 = P->h, pitch = P->pitch;
   const uint8_t* Lp = P->L;
-  int cy_lo, dummy;
+  int dummy;
   float fdummy;
-  coarse_axis<CT>((float)max(0, 2 * Y0 - 1), h4, cy_lo, dummy, fdummy);
-  // every load of a pass is issued before any is used (one memory round trip per pass)
-  constexpr int NTT = (E1CR * E1C + 255) / 256, NXS = (E1R * E1C + 255) / 256;
-  {
-    float c0v[NTT], c1v[NTT], fxv[NTT];
+  coarse_axis<CT>((float)max(0, 2 * Y0 - 1), h4, ld.cy_lo, dummy, fdummy);
 #pragma unroll
-    for (int i = 0; i < NTT; ++i) {
-      const int e = min((int)threadIdx.x + 256 * i, E1CR * E1C - 1);
-      const int ry = e / E1C, c = e - ry * E1C;
-      const int cy = min(cy_lo + ry, h4 - 1);
-      const int vx = min(max(2 * X0 - 1 + c, 0), Wd - 1);
-      int x0, x1;
-      coarse_axis<CT>((float)vx, w4, x0, x1, fxv[i]);
-      c0v[i] = (float)cmap[(size_t)cy * w4 + x0];
-      c1v[i] = (float)cmap[(size_t)cy * w4 + x1];
-    }
-#pragma unroll
-    for (int i = 0; i < NTT; ++i) {
-      const int e = (int)threadIdx.x + 256 * i;
-      if (e < E1CR * E1C) T[e / E1C][e % E1C] = (1.f - fxv[i]) * c0v[i] + fxv[i] * c1v[i];
-    }
-  }
-  uint32_t lv[NXS];
-#pragma unroll
-  for (int i = 0; i < NXS; ++i) {
+  for (int i = 0; i < E1NXS; ++i) {
     const int e = (int)threadIdx.x + 256 * i;
     const int r = e / E1C, c = e - r * E1C;
     const int vy = 2 * Y0 - 1 + r, vx = 2 * X0 - 1 + c;
-    lv[i] = (e < E1R * E1C && vy >= 0 && vy < Hd && vx >= 0 && vx < Wd) ? (uint32_t)Lp[(size_t)vy * pitch + vx] : 256u;
+    ld.lv[i] = (e < E1R * E1C && vy >= 0 && vy < Hd && vx >= 0 && vx < Wd) ? (uint32_t)Lp[(size_t)vy * pitch + vx] : 256u;
+  }
+#pragma unroll
+  for (int i = 0; i < E1NTT; ++i) {
+    const int e = min((int)threadIdx.x + 256 * i, E1CR * E1C - 1);
+    const int ry = e / E1C, c = e - ry * E1C;
+    const int cy = min(ld.cy_lo + ry, h4 - 1);
+    const int vx = min(max(2 * X0 - 1 + c, 0), Wd - 1);
+    int x0, x1;
+    coarse_axis<CT>((float)vx, w4, x0, x1, ld.fxv[i]);
+    ld.c0v[i] = (float)cmap[(size_t)cy * w4 + x0];
+    ld.c1v[i] = (float)cmap[(size_t)cy * w4 + x1];
+  }
+}
+// x0 = (L / 256, U / 256) on the window from the loaded values: the coarse rows
+// interpolated along x (T), then every position along y.  Ends with the block synchronised.
+template <typename CT>
+__device__ __forceinline__ void enc1_stage_finish(const EdgePair* P, int Y0, const E1Loads& ld, float (*xs)[E1C][2],
+                                                  float (*T)[E1C]) {
+  const int h4 = P->h;
+#pragma unroll
+  for (int i = 0; i < E1NTT; ++i) {
+    const int e = (int)threadIdx.x + 256 * i;
+    if (e < E1CR * E1C) T[e / E1C][e % E1C] = (1.f - ld.fxv[i]) * ld.c0v[i] + ld.fxv[i] * ld.c1v[i];
   }
   __syncthreads();  // T complete
 #pragma unroll
-  for (int i = 0; i < NXS; ++i) {
+  for (int i = 0; i < E1NXS; ++i) {
     const int e = (int)threadIdx.x + 256 * i;
     if (e >= E1R * E1C) break;
     const int r = e / E1C, c = e - r * E1C;
     const int vy = 2 * Y0 - 1 + r;
     float l = 0.f, u = 0.f;
-    if (lv[i] != 256u) {  // inside the image
+    if (ld.lv[i] != 256u) {  // inside the image
       int y0, y1;
       float fy;
       coarse_axis<CT>((float)vy, h4, y0, y1, fy);
-      l = (float)lv[i] * (1.f / 256.f);
-      u = 4.f * ((1.f - fy) * T[y0 - cy_lo][c] + fy * T[y1 - cy_lo][c]) * (1.f / 256.f);
+      l = (float)ld.lv[i] * (1.f / 256.f);
+      u = 4.f * ((1.f - fy) * T[y0 - ld.cy_lo][c] + fy * T[y1 - ld.cy_lo][c]) * (1.f / 256.f);
     }
     xs[r][c][0] = l;
     xs[r][c][1] = u;
   }
+  __syncthreads();
+}
+template <typename CT>
+__device__ __forceinline__ void enc1_stage(const EdgePair* P, const CT* __restrict__ cmap, int X0, int Y0,
+                                           float (*xs)[E1C][2], float (*T)[E1C]) {
+  E1Loads ld;
+  enc1_stage_load(P, cmap, X0, Y0, ld);
+  enc1_stage_finish<CT>(P, Y0, ld, xs, T);
 }
 
 __global__ void __launch_bounds__(256) edge_enc1(const EdgePair* __restrict__ pairs, const float* __restrict__ W,
@@ -264,6 +281,9 @@ __global__ void __launch_bounds__(256) enc1_tc(const EdgePair* __restrict__ pair
   const int X0 = blockIdx.x * E1W, Y0 = blockIdx.y * E1H;
   if (X0 >= W1 || Y0 >= H1) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  E1Loads ld;  // the window's loads go out first: their latency overlaps the set-up below
+  if (P->coarse_f) enc1_stage_load(P, P->coarse_f, X0, Y0, ld);
+  else enc1_stage_load(P, P->coarse, X0, Y0, ld);
   const uint32_t raw = smem_u32_e(e1dyn), base = (raw + 127u) & ~127u;
   unsigned char* g = e1dyn + (base - raw);
   const uint32_t sA = base, sBh = base + 8 * kE1Tile, sBl = sBh + C1 * 64;
@@ -290,9 +310,8 @@ __global__ void __launch_bounds__(256) enc1_tc(const EdgePair* __restrict__ pair
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (P->coarse_f) enc1_stage(P, P->coarse_f, X0, Y0, xs, T);
-  else enc1_stage(P, P->coarse, X0, Y0, xs, T);
-  __syncthreads();
+  if (P->coarse_f) enc1_stage_finish<float>(P, Y0, ld, xs, T);
+  else enc1_stage_finish<int16_t>(P, Y0, ld, xs, T);
   // A rows: warp w builds tile w; lane = output column, j = row within the tile
 #pragma unroll 1
   for (int j = 0; j < 4; ++j) {
@@ -376,6 +395,31 @@ __global__ void __launch_bounds__(256) enc1_tc(const EdgePair* __restrict__ pair
           uint4* dst = reinterpret_cast<uint4*>(P->e1q + ((size_t)Y * W1 + X) * C1 + c0);
 #pragma unroll
           for (int i = 0; i < CW / 16; ++i) dst[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+        } else if (!P->e1q && CW == 32) {
+          // through a 2 KB stage per warp in the (now free) A tiles: lane = pixel writes its
+          // four 16-byte pieces (piece q at slot q ^ ((pixel >> 1) & 3): conflict-free), then
+          // four lanes per pixel store its 64 bytes, eight pixels (512 bytes) per instruction
+          uint32_t pk[16];
+#pragma unroll
+          for (int e = 0; e < 32; e += 2) {
+            const float2 v = __fadd2_rn(make_float2(__uint_as_float(r[e]), __uint_as_float(r[e + 1])),
+                                        make_float2(bias_s[c0 + e], bias_s[c0 + e + 1]));
+            const __nv_bfloat162 h = __hmax2(__floats2bfloat162_rn(v.x, v.y), __float2bfloat162_rn(0.f));
+            pk[e / 2] = *reinterpret_cast<const uint32_t*>(&h);
+          }
+          uint4* sw = reinterpret_cast<uint4*>(g) + warp * 128;
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq)
+            sw[lane * 4 + (qq ^ ((lane >> 1) & 3))] = make_uint4(pk[4 * qq], pk[4 * qq + 1], pk[4 * qq + 2], pk[4 * qq + 3]);
+          __syncwarp();
+#pragma unroll
+          for (int s8 = 0; s8 < 4; ++s8) {
+            const int pp = 8 * s8 + (lane >> 2), qq = lane & 3;
+            const uint4 v = sw[pp * 4 + (qq ^ ((pp >> 1) & 3))];
+            if (X0 + pp < W1 && Y < H1)
+              *reinterpret_cast<uint4*>(P->e1 + ((size_t)Y * W1 + X0 + pp) * C1 + c0 + 8 * qq) = v;
+          }
+          __syncwarp();
         } else if (X < W1 && Y < H1) {
           uint32_t pk[CW / 2];
 #pragma unroll
