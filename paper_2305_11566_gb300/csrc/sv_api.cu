@@ -474,41 +474,68 @@ sv_status sv_pipeline_host(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, float
     }
   }
   if ((s = c->check_pairs(dev.data(), n_pairs))) return s;
-  if (direct) {
+  if (direct && !scatter) {
+    // the batch in parts of at least 8 pairs: each part's images are gathered on the input
+    // stream ahead of its compute (the next part's arrive while the current one computes),
+    // and its results go back on the copy stream while the next part computes
     const size_t jb = sizeof(sv::HostRowCopy) * jobs.size();
     if ((s = c->cuda(c->host_jobs.ensure(jb), "alloc copy jobs"))) return s;
-    if ((s = c->cuda(cudaMemcpyAsync(c->host_jobs.p, jobs.data(), jb, cudaMemcpyHostToDevice, st), "copy jobs")))
-      return s;
-    const sv::HostRowCopy* dj = (const sv::HostRowCopy*)c->host_jobs.p;
-    if ((s = c->cuda(sv::launch_copy_rows(dj, 2 * n_pairs, max_rows, 1, st), "gather images"))) return s;
-    if (scatter) {
-      if ((s = c->pipeline(dev.data(), n_pairs, dout.data(), st))) return s;
-      if ((s = c->cuda(sv::launch_copy_rows(dj + 2 * n_pairs, n_pairs, max_rows, 1, st), "scatter results")))
-        return s;
-      return c->cuda(cudaStreamSynchronize(st), "synchronise");
-    }
-    // the batch in parts of at least 8 pairs: a part's results are copied back on the
-    // context's copy stream while the next part computes
     const int nch = std::max(1, std::min(c->host_chunks, n_pairs / 8));
     if (!c->copy_stream && (s = c->cuda(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "stream")))
       return s;
-    for (auto& e : c->chunk_done)
-      if (!e && (s = c->cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event"))) return s;
-    int start = 0;
-    for (int ch = 0; ch < nch; ++ch) {
-      const int cnt = ch + 1 == nch ? n_pairs - start : n_pairs / nch;
+    if (!c->in_stream && (s = c->cuda(cudaStreamCreateWithFlags(&c->in_stream, cudaStreamNonBlocking), "stream")))
+      return s;
+    for (auto* e : {&c->chunk_done[0], &c->chunk_done[1], &c->chunk_done[2], &c->chunk_done[3], &c->gather_done[0],
+                    &c->gather_done[1], &c->gather_done[2], &c->gather_done[3], &c->call_start})
+      if (!*e && (s = c->cuda(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "event"))) return s;
+    // the input stream starts after the work already queued on the caller's stream
+    if ((s = c->cuda(cudaEventRecord(c->call_start, st), "record"))) return s;
+    if ((s = c->cuda(cudaStreamWaitEvent(c->in_stream, c->call_start, 0), "wait"))) return s;
+    if ((s = c->cuda(cudaMemcpyAsync(c->host_jobs.p, jobs.data(), jb, cudaMemcpyHostToDevice, c->in_stream),
+                     "copy jobs")))
+      return s;
+    const sv::HostRowCopy* dj = (const sv::HostRowCopy*)c->host_jobs.p;
+    // part sizes in the ratio 1 : 2 : ... : 2 : 1 (two parts: 1 : 1): the first part's gather
+    // and the last part's copy-back are the only transfers nothing overlaps, so those parts
+    // are the small ones
+    std::vector<int> first(nch + 1, 0);
+    const int units = nch <= 2 ? nch : 2 * nch - 2;
+    for (int ch = 0, u = 0; ch < nch; ++ch) {
+      u += nch <= 2 || ch == 0 || ch == nch - 1 ? 1 : 2;
+      first[ch + 1] = ch + 1 == nch ? n_pairs : (int)((long long)n_pairs * u / units);
+    }
+    for (int ch = 0; ch < nch && !s; ++ch) {
+      int rows = 0;
+      for (int i = first[ch]; i < first[ch + 1]; ++i) rows = std::max(rows, pairs[i].height);
+      s = c->cuda(sv::launch_copy_rows(dj + 2 * first[ch], 2 * (first[ch + 1] - first[ch]), rows, 1, c->in_stream),
+                  "gather images");
+      if (!s) s = c->cuda(cudaEventRecord(c->gather_done[ch], c->in_stream), "record");
+    }
+    for (int ch = 0; ch < nch && !s; ++ch) {
+      const int start = first[ch], cnt = first[ch + 1] - first[ch];
+      if ((s = c->cuda(cudaStreamWaitEvent(st, c->gather_done[ch], 0), "wait"))) break;
       if ((s = c->pipeline(dev.data() + start, cnt, dout.data() + start, st))) break;
       if ((s = c->cuda(cudaEventRecord(c->chunk_done[ch], st), "record"))) break;
       if ((s = c->cuda(cudaStreamWaitEvent(c->copy_stream, c->chunk_done[ch], 0), "wait"))) break;
       for (int i = start; i < start + cnt && !s; ++i)
         s = c->cuda(cudaMemcpyAsync(disp_out[i], dout[i], sizeof(float) * pairs[i].width * pairs[i].height,
                                     cudaMemcpyDeviceToHost, c->copy_stream), "D2H");
-      if (s) break;
-      start += cnt;
     }
+    const sv_status s0 = c->cuda(cudaStreamSynchronize(c->in_stream), "synchronise gathers");
     const sv_status s1 = c->cuda(cudaStreamSynchronize(st), "synchronise");
     const sv_status s2 = c->cuda(cudaStreamSynchronize(c->copy_stream), "synchronise copies");
-    return s ? s : s1 ? s1 : s2;
+    return s ? s : s0 ? s0 : s1 ? s1 : s2;
+  }
+  if (direct) {  // gather and scatter kernels around one whole-batch pipeline
+    const size_t jb = sizeof(sv::HostRowCopy) * jobs.size();
+    if ((s = c->cuda(c->host_jobs.ensure(jb), "alloc copy jobs"))) return s;
+    if ((s = c->cuda(cudaMemcpyAsync(c->host_jobs.p, jobs.data(), jb, cudaMemcpyHostToDevice, st), "copy jobs")))
+      return s;
+    const sv::HostRowCopy* dj = (const sv::HostRowCopy*)c->host_jobs.p;
+    if ((s = c->cuda(sv::launch_copy_rows(dj, 2 * n_pairs, max_rows, 1, st), "gather images"))) return s;
+    if ((s = c->pipeline(dev.data(), n_pairs, dout.data(), st))) return s;
+    if ((s = c->cuda(sv::launch_copy_rows(dj + 2 * n_pairs, n_pairs, max_rows, 1, st), "scatter results"))) return s;
+    return c->cuda(cudaStreamSynchronize(st), "synchronise");
   }
   for (int i = 0; i < n_pairs; ++i) {
     const sv_pair& p = pairs[i];

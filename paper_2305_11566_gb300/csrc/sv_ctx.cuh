@@ -67,6 +67,9 @@ struct TcTrainLatent {
 // One captured batched step (coarse match + tensor-core refinement) and what it needs.
 struct GraphEntry {
   std::vector<uint64_t> key;
+  std::vector<uint64_t> pkey;  // the call signature that led to it (before any preparation)
+  std::vector<std::array<size_t, 7>> off, len;  // per-pair activation offsets of the call
+  bool fused = false;
   cudaGraphExec_t exec = nullptr;
   void* tables = nullptr;  // device copy of the step's tables (owned)
   struct Rec { std::string name; cudaEvent_t a, b; };
@@ -113,6 +116,9 @@ struct Ctx {
   DevBuf loss_slots;                    // per-block partial sums of sv_loss_paper
   cudaStream_t copy_stream = nullptr;    // sv_pipeline_host: results go back here while the
   cudaEvent_t chunk_done[4] = {nullptr, nullptr, nullptr, nullptr};  // next part computes
+  cudaStream_t in_stream = nullptr;      // sv_pipeline_host: parts' images gathered ahead of their compute
+  cudaEvent_t gather_done[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t call_start = nullptr;
   int host_chunks = 3;                  // parts of an sv_pipeline_host batch (>= 8 pairs each)
   std::vector<unsigned char> tc_host_tables;
   long long spin_limit = 4000000000LL;  // clock64 cycles a device-side wait may spin
@@ -236,13 +242,23 @@ struct Ctx {
     prof_flush();
     drop_graphs();
     if (copy_stream) cudaStreamSynchronize(copy_stream);
+    if (in_stream) cudaStreamSynchronize(in_stream);
     for (auto& e : chunk_done)
       if (e) {
         cudaEventDestroy(e);
         e = nullptr;
       }
+    for (auto& e : gather_done)
+      if (e) {
+        cudaEventDestroy(e);
+        e = nullptr;
+      }
+    if (call_start) cudaEventDestroy(call_start);
+    call_start = nullptr;
     if (copy_stream) cudaStreamDestroy(copy_stream);
     copy_stream = nullptr;
+    if (in_stream) cudaStreamDestroy(in_stream);
+    in_stream = nullptr;
     for (auto e : ev_free) cudaEventDestroy(e);
     ev_free.clear();
     host_img.release(); host_out.release(); host_jobs.release(); err_flag.release(); tune_out.release();

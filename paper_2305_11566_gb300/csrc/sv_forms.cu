@@ -40,6 +40,48 @@ sv_status Ctx::pipeline(const sv_pair* pairs, int n, float* const* out, cudaStre
 // profiling events are captured.  Tables are uploaded to a buffer the graph owns before
 // the capture; the capture itself holds kernel launches only.
 sv_status Ctx::pipeline_graph(const sv_pair* pairs, int n, float* const* out, cudaStream_t st) {
+  // Call signature from what the caller passes and what the plan depends on, known before any
+  // table is prepared: pair pointers, sizes, outputs, the workspace addresses (workspaces only
+  // grow, so a graph captured for these sizes stays valid while they are unchanged), weights,
+  // launch options and tuned overrides.  A match replays the graph without preparing the
+  // tables again (about 0.2 ms of host work per call at 64 pairs).
+  std::vector<uint64_t> pkey;
+  pkey.reserve(5 * n + 64);
+  {
+    auto k = [&](uint64_t v) { pkey.push_back(v); };
+    k((uint64_t)n);
+    for (int i = 0; i < n; ++i) {
+      k((uint64_t)(uintptr_t)pairs[i].left); k((uint64_t)(uintptr_t)pairs[i].right);
+      k(((uint64_t)pairs[i].width << 32) | (uint32_t)pairs[i].height);
+      k(((uint64_t)pairs[i].pitch << 32) | (uint32_t)pairs[i].max_disp);
+      k((uint64_t)(uintptr_t)out[i]);
+    }
+    k((uint64_t)(uintptr_t)coarse_maps.p);
+    for (auto& b : tc_act) k((uint64_t)(uintptr_t)b.p);
+    k((uint64_t)(uintptr_t)w32.p); k((uint64_t)(uintptr_t)wbf.p); k((uint64_t)(uintptr_t)wfuse.p);
+    k((uint64_t)(uintptr_t)wf8.p); k((uint64_t)(uintptr_t)wf8u.p); k((uint64_t)(uintptr_t)wf8s.p);
+    k((uint64_t)(uintptr_t)err_flag.p); k((uint64_t)spin_limit); k((uint64_t)prof_on);
+    k(((uint64_t)(uint32_t)enc1_tensor << 32) | (uint32_t)fused_final);
+    k(((uint64_t)(uint32_t)fused_ring << 32) | (uint32_t)fused_prefetch);
+    k(((uint64_t)(uint32_t)split_rows << 32) | (uint32_t)tc_ctas_per_sm);
+    k((uint64_t)(uint32_t)tc_strip_rows);
+    for (int l = 0; l < 6; ++l)
+      k(((uint64_t)(uint32_t)tc_rows_override[l] << 40) | ((uint64_t)(uint32_t)tc_nt_override[l] << 20) |
+        (uint32_t)tc_ctas_override[l]);
+  }
+  for (auto& g : graphs) {
+    if (g.pkey != pkey) continue;
+    g.last_use = ++graph_clock;
+    tc_off = g.off;
+    tc_len = g.len;
+    last_fused = g.fused;
+    sv_status s = cuda(cudaGraphLaunch(g.exec, st), "graph launch");
+    if (s) return s;
+    launches += g.kernels;
+    if (prof_on)
+      for (auto& rec : g.prof) prof_pending.push_back({rec.name, rec.a, rec.b, false});
+    return SV_OK;
+  }
   std::vector<size_t> off(n + 1, 0);
   for (int i = 0; i < n; ++i) off[i + 1] = off[i] + (size_t)(pairs[i].width / 4) * (pairs[i].height / 4);
   sv_status s = cuda(coarse_maps.ensure(off[n] * sizeof(int16_t)), "alloc coarse maps");
@@ -77,6 +119,7 @@ sv_status Ctx::pipeline_graph(const sv_pair* pairs, int n, float* const* out, cu
   for (auto& g : graphs) {
     if (g.key != key) continue;
     g.last_use = graph_clock;
+    g.pkey = pkey;
     if ((s = cuda(cudaGraphLaunch(g.exec, st), "graph launch"))) return s;
     launches += g.kernels;
     if (prof_on)
@@ -95,6 +138,10 @@ sv_status Ctx::pipeline_graph(const sv_pair* pairs, int n, float* const* out, cu
   }
   GraphEntry g;
   g.key = key;
+  g.pkey = pkey;
+  g.off = tc_off;
+  g.len = tc_len;
+  g.fused = r.fused;
   g.last_use = graph_clock;
   const size_t zp_bytes = sizeof(ZPair) * z.pairs.size(), zj_bytes = sizeof(ZJob) * z.jobs.size();
   const size_t zp_ofs = 0, zj_ofs = (zp_bytes + 255) / 256 * 256, tc_ofs = (zj_ofs + zj_bytes + 255) / 256 * 256;
