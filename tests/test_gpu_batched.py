@@ -176,3 +176,41 @@ def test_pipeline_host_two_halves(svlib):
             assert torch.equal(o, r.cpu())
     finally:
         ctx.close()
+
+
+def test_signature_replay_across_batches_and_options(svlib, batch):
+    """Graphs replayed from the call signature alone (no table preparation): alternating two
+    batches replays each one's own graph (outputs and the per-pair activation offsets of the
+    replayed batch), and a changed launch option (the fused decoder tail off) is a new
+    signature, not a stale replay."""
+    pairs, dps = batch
+    other = synth.batch_uneven(4, seed=9200)
+    dps2 = [binding.to_device(p, D) for p, D in other]
+    s = torch.cuda.Stream()
+    ctx = make_ctx()
+    try:
+        a1 = run(ctx, dps, s)
+        b1 = run(ctx, dps2, s)
+        a2 = run(ctx, dps, s)
+        for x, y in zip(a1, a2):
+            assert torch.equal(x, y)
+        # the replayed batch's activation offsets: pair 1 of the first batch reads its e1 shape
+        H, W = pairs[1].left.shape
+        L1 = oracle.level_sizes(H, W)[1]
+        e1 = ctx.debug_activation(0, 1, (*L1, synth.NET_WIDE.enc[0]))
+        b2 = run(ctx, dps2, s)
+        for x, y in zip(b1, b2):
+            assert torch.equal(x, y)
+        run(ctx, dps, s)
+        assert np.array_equal(ctx.debug_activation(0, 1, (*L1, synth.NET_WIDE.enc[0])), e1)
+        # the last decoder activation stays on chip with the fused tail; with it off it is kept
+        with pytest.raises(binding.SvError):
+            ctx.debug_activation(6, 0, (*pairs[0].left.shape, synth.NET_WIDE.dec[2]))
+        ctx.set_option("fused_final", 0)
+        a3 = run(ctx, dps, s)
+        d3 = ctx.debug_activation(6, 0, (*pairs[0].left.shape, synth.NET_WIDE.dec[2]))
+        assert np.isfinite(d3).all() and np.abs(d3).max() > 0
+        for x, y in zip(a1, a3):  # the unfused tail: same layers, FP32 final conv on CUDA cores
+            assert torch.allclose(x, y, atol=0.05, rtol=0)
+    finally:
+        ctx.close()
