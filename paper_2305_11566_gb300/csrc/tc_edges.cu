@@ -71,30 +71,38 @@ __device__ __forceinline__ void coarse_axis(float v, int n, int& i0, int& i1, fl
 
 // The window's global loads (image bytes and the coarse values of T), all issued in one pass
 // before any is used, so that their latency overlaps whatever the kernel does next.
-constexpr int E1NTT = (E1CR * E1C + 255) / 256, E1NXS = (E1R * E1C + 255) / 256;
+// Window of a block of BH e1 rows (x 32 columns): R staged full-resolution rows, CR coarse rows
+// of T (with a margin), NTT / NXS loads per thread of the two passes.
+template <int BH>
+struct E1Geo {
+  static constexpr int R = 2 * BH + 1, CR = BH == E1H ? E1CR : BH / 2 + 4;
+  static constexpr int NTT = (CR * E1C + 255) / 256, NXS = (R * E1C + 255) / 256;
+};
+template <int BH>
 struct E1Loads {
-  uint32_t lv[E1NXS];
-  float c0v[E1NTT], c1v[E1NTT], fxv[E1NTT];
+  uint32_t lv[E1Geo<BH>::NXS];
+  float c0v[E1Geo<BH>::NTT], c1v[E1Geo<BH>::NTT], fxv[E1Geo<BH>::NTT];
   int cy_lo;
 };
-template <typename CT>
+template <typename CT, int BH>
 __device__ __forceinline__ void enc1_stage_load(const EdgePair* P, const CT* __restrict__ cmap, int X0, int Y0,
-                                                E1Loads& ld) {
+                                                E1Loads<BH>& ld) {
+  using G = E1Geo<BH>;
   const int Wd = P->W, Hd = P->H, w4 = P->w, h4 = P->h, pitch = P->pitch;
   const uint8_t* Lp = P->L;
   int dummy;
   float fdummy;
   coarse_axis<CT>((float)max(0, 2 * Y0 - 1), h4, ld.cy_lo, dummy, fdummy);
 #pragma unroll
-  for (int i = 0; i < E1NXS; ++i) {
+  for (int i = 0; i < G::NXS; ++i) {
     const int e = (int)threadIdx.x + 256 * i;
     const int r = e / E1C, c = e - r * E1C;
     const int vy = 2 * Y0 - 1 + r, vx = 2 * X0 - 1 + c;
-    ld.lv[i] = (e < E1R * E1C && vy >= 0 && vy < Hd && vx >= 0 && vx < Wd) ? (uint32_t)Lp[(size_t)vy * pitch + vx] : 256u;
+    ld.lv[i] = (e < G::R * E1C && vy >= 0 && vy < Hd && vx >= 0 && vx < Wd) ? (uint32_t)Lp[(size_t)vy * pitch + vx] : 256u;
   }
 #pragma unroll
-  for (int i = 0; i < E1NTT; ++i) {
-    const int e = min((int)threadIdx.x + 256 * i, E1CR * E1C - 1);
+  for (int i = 0; i < G::NTT; ++i) {
+    const int e = min((int)threadIdx.x + 256 * i, G::CR * E1C - 1);
     const int ry = e / E1C, c = e - ry * E1C;
     const int cy = min(ld.cy_lo + ry, h4 - 1);
     const int vx = min(max(2 * X0 - 1 + c, 0), Wd - 1);
@@ -106,20 +114,21 @@ __device__ __forceinline__ void enc1_stage_load(const EdgePair* P, const CT* __r
 }
 // x0 = (L / 256, U / 256) on the window from the loaded values: the coarse rows
 // interpolated along x (T), then every position along y.  Ends with the block synchronised.
-template <typename CT>
-__device__ __forceinline__ void enc1_stage_finish(const EdgePair* P, int Y0, const E1Loads& ld, float (*xs)[E1C][2],
-                                                  float (*T)[E1C]) {
+template <typename CT, int BH>
+__device__ __forceinline__ void enc1_stage_finish(const EdgePair* P, int Y0, const E1Loads<BH>& ld,
+                                                  float (*xs)[E1C][2], float (*T)[E1C]) {
+  using G = E1Geo<BH>;
   const int h4 = P->h;
 #pragma unroll
-  for (int i = 0; i < E1NTT; ++i) {
+  for (int i = 0; i < G::NTT; ++i) {
     const int e = (int)threadIdx.x + 256 * i;
-    if (e < E1CR * E1C) T[e / E1C][e % E1C] = (1.f - ld.fxv[i]) * ld.c0v[i] + ld.fxv[i] * ld.c1v[i];
+    if (e < G::CR * E1C) T[e / E1C][e % E1C] = (1.f - ld.fxv[i]) * ld.c0v[i] + ld.fxv[i] * ld.c1v[i];
   }
   __syncthreads();  // T complete
 #pragma unroll
-  for (int i = 0; i < E1NXS; ++i) {
+  for (int i = 0; i < G::NXS; ++i) {
     const int e = (int)threadIdx.x + 256 * i;
-    if (e >= E1R * E1C) break;
+    if (e >= G::R * E1C) break;
     const int r = e / E1C, c = e - r * E1C;
     const int vy = 2 * Y0 - 1 + r;
     float l = 0.f, u = 0.f;
@@ -138,16 +147,16 @@ __device__ __forceinline__ void enc1_stage_finish(const EdgePair* P, int Y0, con
 template <typename CT>
 __device__ __forceinline__ void enc1_stage(const EdgePair* P, const CT* __restrict__ cmap, int X0, int Y0,
                                            float (*xs)[E1C][2], float (*T)[E1C]) {
-  E1Loads ld;
-  enc1_stage_load(P, cmap, X0, Y0, ld);
-  enc1_stage_finish<CT>(P, Y0, ld, xs, T);
+  E1Loads<E1H> ld;
+  enc1_stage_load<CT, E1H>(P, cmap, X0, Y0, ld);
+  enc1_stage_finish<CT, E1H>(P, Y0, ld, xs, T);
 }
 
 __global__ void __launch_bounds__(256) edge_enc1(const EdgePair* __restrict__ pairs, const float* __restrict__ W,
                                                  const float* __restrict__ B, int C1) {
   // blockDim.x must be 256 (the staging passes are unrolled for it)
-  __shared__ float xs[E1R][E1C][2];
-  __shared__ float T[E1CR][E1C];
+  __shared__ float xs[E1Geo<E1H>::R][E1C][2];
+  __shared__ float T[E1Geo<E1H>::CR][E1C];
   extern __shared__ __align__(16) float wsm[];  // [18][C1] then bias[C1]
   const EdgePair* P = pairs + blockIdx.z;
   const int H1 = (P->H + 1) / 2, W1 = (P->W + 1) / 2;
@@ -265,34 +274,40 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 }
 
 constexpr uint32_t kE1Tile = 128 * 32 * 2;  // one A tile (128 pixels x K = 32, BF16)
+constexpr int kE1TcBH = 16;                  // e1 rows per block of the tensor-core kernel
+constexpr int kE1Tiles = kE1TcBH / 4;        // its MMA tiles (4 rows x 32 columns each)
 __host__ __device__ constexpr size_t enc1_tc_smem(int C1) {
-  return 128 + 8 * (size_t)kE1Tile + 2 * (size_t)C1 * 64 + (size_t)C1 * 4 + 16;
+  return 128 + kE1Tiles * (size_t)kE1Tile + 2 * (size_t)C1 * 64 + (size_t)C1 * 4 + 16;
 }
 
+// Blocks of 16 x 32 e1 pixels (4 MMA tiles): half the shared memory and tensor memory of a
+// 32 x 32 block, so that more blocks share an SM and one block's staging latency hides
+// behind another's MMAs and stores.
 template <int C1>
 __global__ void __launch_bounds__(256) enc1_tc(const EdgePair* __restrict__ pairs, const float* __restrict__ W,
                                                const float* __restrict__ B, int* err, long long spin) {
   static_assert(C1 == 16 || C1 == 32 || C1 == 64, "enc1 widths");
-  __shared__ float xs[E1R][E1C][2];
-  __shared__ float T[E1CR][E1C];
+  constexpr int BH = kE1TcBH, NTILE = kE1Tiles, RPW = BH / 8;  // e1 rows per warp in the A build
+  __shared__ float xs[E1Geo<BH>::R][E1C][2];
+  __shared__ float T[E1Geo<BH>::CR][E1C];
   extern __shared__ unsigned char e1dyn[];
   const EdgePair* P = pairs + blockIdx.z;
   const int H1 = (P->H + 1) / 2, W1 = (P->W + 1) / 2;
-  const int X0 = blockIdx.x * E1W, Y0 = blockIdx.y * E1H;
+  const int X0 = blockIdx.x * E1W, Y0 = blockIdx.y * BH;
   if (X0 >= W1 || Y0 >= H1) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  E1Loads ld;  // the window's loads go out first: their latency overlaps the set-up below
-  if (P->coarse_f) enc1_stage_load(P, P->coarse_f, X0, Y0, ld);
-  else enc1_stage_load(P, P->coarse, X0, Y0, ld);
+  E1Loads<BH> ld;  // the window's loads go out first: their latency overlaps the set-up below
+  if (P->coarse_f) enc1_stage_load<float, BH>(P, P->coarse_f, X0, Y0, ld);
+  else enc1_stage_load<int16_t, BH>(P, P->coarse, X0, Y0, ld);
   const uint32_t raw = smem_u32_e(e1dyn), base = (raw + 127u) & ~127u;
   unsigned char* g = e1dyn + (base - raw);
-  const uint32_t sA = base, sBh = base + 8 * kE1Tile, sBl = sBh + C1 * 64;
-  float* bias_s = reinterpret_cast<float*>(g + 8 * kE1Tile + 2 * C1 * 64);
+  const uint32_t sA = base, sBh = base + NTILE * kE1Tile, sBl = sBh + C1 * 64;
+  float* bias_s = reinterpret_cast<float*>(g + NTILE * kE1Tile + 2 * C1 * 64);
   const uint32_t mbar = smem_u32_e(bias_s + C1);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bias_s + C1 + 2);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32_e(tslot)),
-                 "r"(8 * C1));
+                 "r"(NTILE * C1));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   // B (high, low): element (n, k), k = 3 tap + part (0: L, 1 and 2: the two U parts)
@@ -302,20 +317,22 @@ __global__ void __launch_bounds__(256) enc1_tc(const EdgePair* __restrict__ pair
     if (k < 27) w = W[(size_t)n * 18 + (k / 3) * 2 + (k % 3 == 0 ? 0 : 1)];
     const __nv_bfloat16 hi = __float2bfloat16_rn(w);
     const uint32_t off = (uint32_t)((n & 7) * 8 + (n >> 3) * 256 + (k & 7) + (k >> 3) * 64) * 2;
-    *reinterpret_cast<__nv_bfloat16*>(g + 8 * kE1Tile + off) = hi;
-    *reinterpret_cast<__nv_bfloat16*>(g + 8 * kE1Tile + C1 * 64 + off) = __float2bfloat16_rn(w - __bfloat162float(hi));
+    *reinterpret_cast<__nv_bfloat16*>(g + NTILE * kE1Tile + off) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(g + NTILE * kE1Tile + C1 * 64 + off) =
+        __float2bfloat16_rn(w - __bfloat162float(hi));
   }
   for (int e = tid; e < C1; e += 256) bias_s[e] = B[e];
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (P->coarse_f) enc1_stage_finish<float>(P, Y0, ld, xs, T);
-  else enc1_stage_finish<int16_t>(P, Y0, ld, xs, T);
-  // A rows: warp w builds tile w; lane = output column, j = row within the tile
+  if (P->coarse_f) enc1_stage_finish<float, BH>(P, Y0, ld, xs, T);
+  else enc1_stage_finish<int16_t, BH>(P, Y0, ld, xs, T);
+  // A rows: warp w builds block rows RPW w .. RPW w + RPW - 1 (tile oy / 4, row j = oy % 4);
+  // lane = output column
 #pragma unroll 1
-  for (int j = 0; j < 4; ++j) {
-    const int oy = 4 * warp + j;
+  for (int jj = 0; jj < RPW; ++jj) {
+    const int oy = RPW * warp + jj, j = oy & 3, tile = oy >> 2;
     float v[32];
 #pragma unroll
     for (int ky = 0; ky < 3; ++ky)
@@ -331,7 +348,7 @@ __global__ void __launch_bounds__(256) enc1_tc(const EdgePair* __restrict__ pair
 #pragma unroll
     for (int k = 27; k < 32; ++k) v[k] = 0.f;
     const int m = 32 * j + lane;
-    unsigned char* row = g + (size_t)warp * kE1Tile + (m & 7) * 16 + (m >> 3) * 512;
+    unsigned char* row = g + (size_t)tile * kE1Tile + (m & 7) * 16 + (m >> 3) * 512;
 #pragma unroll
     for (int kc = 0; kc < 4; ++kc)
       *reinterpret_cast<uint4*>(row + kc * 128) =
@@ -346,7 +363,7 @@ __global__ void __launch_bounds__(256) enc1_tc(const EdgePair* __restrict__ pair
   if (tid == 0) {
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C1 >> 3) << 17) | ((128u >> 4) << 24);
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
+    for (int t = 0; t < NTILE; ++t) {
       const uint64_t a = desc_ns_e(sA + t * kE1Tile, 512);
       const uint32_t d = tmem + t * C1;
       // K step of 16 = two core matrices along K = +256 B (+16 in the start field)
@@ -371,7 +388,7 @@ __global__ void __launch_bounds__(256) enc1_tc(const EdgePair* __restrict__ pair
   if (got) {
     const int q = warp & 3;
 #pragma unroll 1
-    for (int t = warp >> 2; t < 8; t += 2) {
+    for (int t = warp >> 2; t < NTILE; t += 2) {
       const int Y = Y0 + 4 * t + q, X = X0 + lane;
       const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t * C1);
 #pragma unroll
@@ -438,7 +455,7 @@ __global__ void __launch_bounds__(256) enc1_tc(const EdgePair* __restrict__ pair
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(8 * C1));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NTILE * C1));
 }
 
 // final: (ETH + 2) x (ETW + 2) x C BF16 tile in shared memory with an 80-byte-per-32-channel
@@ -912,10 +929,11 @@ static cudaError_t run_enc1_tc(const EdgePair* pairs, dim3 grid, const float* W,
 
 cudaError_t launch_edge_enc1(const EdgePair* pairs, int n, int maxW1, int maxH1, const float* W, const float* B, int C1,
                              int* err, long long spin, bool tensor, cudaStream_t st) {
+  const dim3 tgrid((maxW1 + E1W - 1) / E1W, (maxH1 + kE1TcBH - 1) / kE1TcBH, n);
+  if (tensor && C1 == 32) return run_enc1_tc<32>(pairs, tgrid, W, B, err, spin, st);
+  if (tensor && C1 == 16) return run_enc1_tc<16>(pairs, tgrid, W, B, err, spin, st);
+  if (tensor && C1 == 64) return run_enc1_tc<64>(pairs, tgrid, W, B, err, spin, st);
   dim3 grid((maxW1 + E1W - 1) / E1W, (maxH1 + E1H - 1) / E1H, n);
-  if (tensor && C1 == 32) return run_enc1_tc<32>(pairs, grid, W, B, err, spin, st);
-  if (tensor && C1 == 16) return run_enc1_tc<16>(pairs, grid, W, B, err, spin, st);
-  if (tensor && C1 == 64) return run_enc1_tc<64>(pairs, grid, W, B, err, spin, st);
   edge_enc1<<<grid, 256, sizeof(float) * 19 * C1, st>>>(pairs, W, B, C1);
   return cudaGetLastError();
 }
