@@ -1094,34 +1094,39 @@ __global__ void __launch_bounds__(kFusedThreads, 1) dec3f_kernel(const __grid_co
             tmem_ld16_nowait(trow + c1, rr[1]);
           }
           tmem_wait_ld();
+          const int oy = 2 * i + grp;
+          // lanes m and m ^ 4 store the two columns of a pixel pair in opposite order, so that
+          // each group of eight lanes fills both halves of a 128-byte bank row (with the
+          // chunk swizzle q ^ (m & 3): eight distinct 16-byte slots, no bank conflict)
+          const int sw = (m >> 2) & 1;
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int px = h;
-            const int oy = 2 * i + grp, ox = 2 * (j0 + m) + px;
-            const bool valid = oy < Ho && ox >= 0 && ox < Wo && j0 + m < Wu;
-            const int col = 2 * m + px;
-            if (valid) {
+          for (int q = 0; q < NCH; ++q) {
+            const float4 bl = *reinterpret_cast<const float4*>(bias_s + q * 8);
+            const float4 bh = *reinterpret_cast<const float4*>(bias_s + q * 8 + 4);
+            const float2 bv[4] = {make_float2(bl.x, bl.y), make_float2(bl.z, bl.w), make_float2(bh.x, bh.y),
+                                  make_float2(bh.z, bh.w)};
+            uint4 pk[2];
 #pragma unroll
-              for (int q = 0; q < NCH; ++q) {
-                const float4 bl = *reinterpret_cast<const float4*>(bias_s + q * 8);
-                const float4 bh = *reinterpret_cast<const float4*>(bias_s + q * 8 + 4);
-                const float2 bv[4] = {make_float2(bl.x, bl.y), make_float2(bl.z, bl.w), make_float2(bh.x, bh.y),
-                                      make_float2(bh.z, bh.w)};
-                uint32_t pk[4];
+            for (int h = 0; h < 2; ++h) {
+              const int ox = 2 * (j0 + m) + h;
+              // outside the output: the final conv's zero padding
+              const bool valid = oy < Ho && ox >= 0 && ox < Wo && j0 + m < Wu;
+              uint32_t w4[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                  const int c0 = q * 8 + 2 * e;
-                  // bias (packed add), BF16 rounding, then ReLU on the pair: rounding to
-                  // nearest commutes with max(., 0)
-                  const float2 v = __fadd2_rn(make_float2(__uint_as_float(rr[h][c0]), __uint_as_float(rr[h][c0 + 1])), bv[e]);
-                  const __nv_bfloat162 hh = __hmax2(__floats2bfloat162_rn(v.x, v.y), __float2bfloat162_rn(0.f));
-                  pk[e] = *reinterpret_cast<const uint32_t*>(&hh);
-                }
-                *ring_at(oy, col, q) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+              for (int e = 0; e < 4; ++e) {
+                const int c0 = q * 8 + 2 * e;
+                // bias (packed add), BF16 rounding, then ReLU on the pair: rounding to
+                // nearest commutes with max(., 0)
+                const float2 v = __fadd2_rn(make_float2(__uint_as_float(rr[h][c0]), __uint_as_float(rr[h][c0 + 1])), bv[e]);
+                const __nv_bfloat162 hh = __hmax2(__floats2bfloat162_rn(v.x, v.y), __float2bfloat162_rn(0.f));
+                w4[e] = valid ? *reinterpret_cast<const uint32_t*>(&hh) : 0u;
               }
-            } else {  // outside the output: the final conv's zero padding
+              pk[h] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            }
 #pragma unroll
-              for (int q = 0; q < NCH; ++q) *ring_at(oy, col, q) = make_uint4(0, 0, 0, 0);
+            for (int b = 0; b < 2; ++b) {
+              const int px = sw ^ b;
+              *ring_at(oy, 2 * m + px, q) = px ? pk[1] : pk[0];
             }
           }
           // the d3 rows are read by the tensor cores next: generic-proxy writes made visible
