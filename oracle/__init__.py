@@ -31,7 +31,8 @@ Parity status per function (what pins each one, in tests/test_oracle_*.py):
                    finite range, saturation above 448
   refine_forward_q with its roundings off: refine_forward (the folded decoder interior and
                    the unfolded border recompute together equal the plain nearest-x2 conv);
-                   activations on the E4M3 grid; the BF16 form's bar against refine_forward
+                   activations on the E4M3 grid (d2, d3 on the BF16 grid); the BF16 form's bar
+                   against refine_forward
   qconv_layer      the layer refine_forward_q applies: chaining it layer by layer gives that
                    forward's activations exactly; stride-2 and pointwise layers whose weights
                    are E4M3 values times 2^-8 (each channel reaching 448 x 2^-8, so its scale
@@ -96,7 +97,7 @@ def lib():
         L.orc_e4m3.argtypes = [c_double]
         L.orc_e4m3.restype = c_double
         L.orc_refine_forward_q.argtypes = [P, P, P, c_int, c_int, c_int, P, c_int, c_int, c_int, P, c_int, P]
-        L.orc_qconv_layer.argtypes = [P, c_int, c_int, c_int, P, P, c_int, c_int, c_int, c_int, c_int, c_int, P]
+        L.orc_qconv_layer.argtypes = [P, c_int, c_int, c_int, P, P, c_int, c_int, c_int, c_int, c_int, c_int, c_int, P]
         L.orc_t1_param_offset.argtypes = [c_int, c_int]
         L.orc_t1_param_offset.restype = c_size_t
         L.orc_t1_param_count.restype = c_size_t
@@ -502,10 +503,12 @@ def refine_forward_q(shape, params: np.ndarray, left: np.ndarray, coarse: np.nda
 
 
 def qconv_layer(x: np.ndarray, wt: np.ndarray, b: np.ndarray, mode: int, out_hw, relu: bool = True,
-                out_round: str = "e4m3") -> np.ndarray:
+                out_round: str = "e4m3", quant_weights: bool = True) -> np.ndarray:
     """One FP8-form layer from the given input values x [Hi, Wi, Ci]: wt [Co, k, k, Ci] FP32
     weights (k = 3, or 1 for mode 1), mode 0 stride-2 3 x 3, 1 pointwise, 2 nearest x2 + crop +
-    3 x 3; out_round "none", "e4m3" or "bf16".  Returns [Ho, Wo, Co]."""
+    3 x 3; weights quantised per output channel (quant_weights, the form's quantised layers)
+    or used as they are (its last decoder layer); out_round "none", "e4m3" or "bf16".
+    Returns [Ho, Wo, Co]."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     wt = np.ascontiguousarray(wt, dtype=np.float32)
     b = np.ascontiguousarray(b, dtype=np.float32)
@@ -514,7 +517,8 @@ def qconv_layer(x: np.ndarray, wt: np.ndarray, b: np.ndarray, mode: int, out_hw,
     Ho, Wo = out_hw
     out = np.zeros((Ho, Wo, Co), dtype=np.float64)
     r = {"none": 0, "e4m3": 1, "bf16": 2}[out_round]
-    lib().orc_qconv_layer(_p(x), Hi, Wi, Ci, _p(wt), _p(b), Co, mode, Ho, Wo, int(relu), r, _p(out))
+    lib().orc_qconv_layer(_p(x), Hi, Wi, Ci, _p(wt), _p(b), Co, mode, Ho, Wo, int(relu), int(quant_weights), r,
+                          _p(out))
     return out
 
 

@@ -1085,9 +1085,12 @@ double orc_t1_loss(const double* Y, const float* gt, const uint8_t* noc, size_t 
  *     are the phase-folded weights (the 3 x 3 kernel rows / columns {0} and {1, 2} for phase
  *     0, {0, 1} and {2} for phase 1, summed in FP32 in row-major tap order), for stride-2
  *     and 1 x 1 layers the weights themselves;
- *   - activations between layers (e1, e2, e3, z, d1, d2) rounded to E4M3 with scale 1; e1
- *     first to BF16 (the first layer's output format), d3 to BF16 (the last layer's input
- *     format is BF16, as in the BF16 form);
+ *   - the quantised layers are enc2, enc3, the latent head, dec1 and dec2; their inputs (e1,
+ *     e2, e3, z, d1) are rounded to E4M3 with scale 1, e1 first to BF16 (the first layer's
+ *     output format);
+ *   - the last decoder layer stays as in the BF16 form: d2 is rounded to BF16, dec3 uses the
+ *     FP32 weights (phase-folded sums as above, unquantised) and d3 is rounded to BF16 (the
+ *     final conv's input format);
  *   - a layer's output: relu(s[co] * sum(a_code * w_code) + b[co]) (no relu after the
  *     latent head); inference uses z = mu;
  *   - decoder border pixels left wrong by the phase folding (the last output row of an odd
@@ -1244,10 +1247,11 @@ static void round_act(double* a, size_t n, int quant, int bf16_first) {
 /* One layer of the FP8 form on its own: in [Hi][Wi][Ci] (the values the previous layer passed
  * on), the layer's FP32 weights W[co][ky][kx][ci] and bias; mode 0 stride 2 (3 x 3, pad 1),
  * 1 pointwise, 2 nearest x2 + crop + 3 x 3; weights quantised per output channel as in
- * orc_refine_forward_q; out_round 0 passes the values on, 1 rounds them to E4M3, 2 to BF16. */
+ * orc_refine_forward_q when quant_w (else the FP32 values, as the form's last decoder layer);
+ * out_round 0 passes the values on, 1 rounds them to E4M3, 2 to BF16. */
 void orc_qconv_layer(const double* in, int Hi, int Wi, int Ci, const float* Wt, const float* bias, int Co, int mode,
-                     int Ho, int Wo, int relu, int out_round, double* out) {
-  qconv(in, Hi, Wi, Ci, Wt, bias, Co, mode, Ho, Wo, relu, 1, out);
+                     int Ho, int Wo, int relu, int quant_w, int out_round, double* out) {
+  qconv(in, Hi, Wi, Ci, Wt, bias, Co, mode, Ho, Wo, relu, quant_w, out);
   const size_t n = (size_t)Ho * Wo * Co;
   if (out_round == 1) round_act(out, n, 1, 0);
   if (out_round == 2)
@@ -1256,7 +1260,7 @@ void orc_qconv_layer(const double* in, int Hi, int Wi, int Ci, const float* Wt, 
 
 /* The FP8 form's refinement (inference, z = mu); outputs as orc_refine_activation /
  * orc_refine_forward: Y [H*W]; act (nullable) receives activation `which` (0 e1 .. 6 d3, the
- * values each layer passes on: codes for e1-d2, BF16 values for d3). */
+ * values each layer passes on: codes for e1-d1, BF16 values for d2 and d3). */
 void orc_refine_forward_q(const int* widths7, const float* params, const uint8_t* left, int W, int H, int pitch,
                           const double* coarse, int w, int h, int quant, double* Y, int which, double* act) {
   orc_net n = {{widths7[0], widths7[1], widths7[2]}, widths7[3], {widths7[4], widths7[5], widths7[6]}};
@@ -1288,8 +1292,9 @@ void orc_refine_forward_q(const int* widths7, const float* params, const uint8_t
   round_act(a.d1, P2 * n.dec[0], quant, 0);
   qconv(a.d1, a.H2, a.W2, n.dec[0], Wl(params, widths7, L_DEC2), Bl(params, widths7, L_DEC2), n.dec[1], 2, a.H1, a.W1, 1,
         quant, a.d2);
-  round_act(a.d2, P1 * n.dec[1], quant, 0);
-  qconv(a.d2, a.H1, a.W1, n.dec[1], Wl(params, widths7, L_DEC3), Bl(params, widths7, L_DEC3), n.dec[2], 2, H, W, 1, quant,
+  if (quant)
+    for (size_t i = 0; i < P1 * n.dec[1]; ++i) a.d2[i] = orc_bf16(a.d2[i]);
+  qconv(a.d2, a.H1, a.W1, n.dec[1], Wl(params, widths7, L_DEC3), Bl(params, widths7, L_DEC3), n.dec[2], 2, H, W, 1, 0,
         a.d3);
   if (quant)
     for (size_t i = 0; i < P0 * n.dec[2]; ++i) a.d3[i] = orc_bf16(a.d3[i]);
