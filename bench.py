@@ -503,8 +503,10 @@ def run_ours(args):
                 ctx.close()
                 continue
             raise
-        if form == "bf16" and not args.no_tune:
-            tuning = ctx.autotune(dps, stream=st)
+        if form in ("bf16", "fp8") and not args.no_tune:
+            tu = ctx.autotune(dps, stream=st)
+            if form == "bf16" or tuning is None:
+                tuning = tu
         t = time_pipeline(ctx, dps, outs, args.steps, args.warmup, st, flush, dev, barrier)
         total_ms = max_over_ranks(sum(t["step_ms"]))
         t.update(ctx=ctx, outs=outs, ms_per_step=total_ms / args.steps)

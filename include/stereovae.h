@@ -63,17 +63,18 @@ typedef enum {
  *          FP32 accumulation; the last conv and the residual stay FP32.
  * SV_FP64_CHECK: FP64 CUDA-core convolutions, for gradient checks on small crops.
  * SV_FP8: the quantised refinement the paper names as future work (Sec. V), inference
- *          only: the five middle tensor-core layers (enc2, enc3, latent, dec1 .. dec3) take
- *          E4M3 operands (tcgen05 kind::f8f6f4, FP32 accumulation).  Weights: per layer and
- *          output channel co the scale s_co = max |w| / 448 over the channel's GEMM operand
- *          (for dec1 .. dec3 the FP32 sums of the nearest-x2 phase folding; the border pixels
- *          of an odd crop use the unfolded 3 x 3 weights with their own scales), codes
- *          E4M3(w / s_co) (round to nearest even, saturating at 448).  Activations carry scale
- *          1: e1 (BF16 from the first layer) and the outputs of enc2 .. dec2 are stored as
- *          E4M3 codes of relu(s_co * acc + bias); dec3 writes BF16; the first and last layers,
- *          the upsampling and the residual are as SV_BF16.  enc, latent and dec1 / dec2 widths
- *          are multiples of 32.  sv_refine_train returns SV_ERR_UNSUPPORTED; sv_autotune
- *          tunes only SV_BF16 contexts; sv_debug_activation returns e1 .. d2 as E4M3 bytes. */
+ *          only: the quantised layers enc2, enc3, latent, dec1 and dec2 take E4M3 operands
+ *          (tcgen05 kind::f8f6f4, FP32 accumulation).  Weights: per layer and output channel
+ *          co the scale s_co = max |w| / 448 over the channel's GEMM operand (for dec1 and dec2
+ *          the FP32 sums of the nearest-x2 phase folding; the border pixels of an odd crop use
+ *          the unfolded 3 x 3 weights with their own scales), codes E4M3(w / s_co) (round to
+ *          nearest even, saturating at 448).  Activations carry scale 1: e1 (BF16 from the
+ *          first layer) and the outputs of enc2 .. dec1 are stored as E4M3 codes of
+ *          relu(s_co * acc + bias); dec2 writes BF16.  The first layer, the last decoder layer
+ *          (fused with the final conv where the widths allow), the upsampling and the residual
+ *          are as SV_BF16.  enc, latent and dec1 widths are multiples of 32.  sv_refine_train
+ *          returns SV_ERR_UNSUPPORTED;
+ *          sv_debug_activation returns e1 .. d1 as E4M3 bytes. */
 typedef enum { SV_FP32 = 0, SV_BF16 = 1, SV_FP64_CHECK = 2, SV_FP8 = 3 } sv_precision;
 
 /* sv_config.flags: selects the refinement network.
@@ -334,14 +335,15 @@ SV_API sv_status sv_profile_enable(sv_ctx* ctx, int enable);
  * reset != 0 clears the totals afterwards. */
 SV_API sv_status sv_profile_read(sv_ctx* ctx, sv_profile_entry* out, int max_entries, int* n_out, int reset);
 
-/* Autotuner of the SV_BF16 form: for each tensor-core layer picks the strip height
- * (rows of 128-unit tiles one work item walks down), the output-channel slice per CTA and
+/* Autotuner of the tensor-core forms (SV_BF16, SV_FP8): for each tensor-core layer picks
+ * the strip height (rows of 128-unit tiles one work item walks down), the output-channel
+ * slice per CTA and
  * the number of CTAs sharing an SM (1-3; the row prefetch ring shrinks to fit) that run
  * fastest on this batch, timing every candidate with CUDA events on `stream`.
  * The choice stays in the context and applies to later calls.  cache_path (nullable): a
- * JSON-lines file; an entry for this (GPU, SM count, network, window, batch-shape bucket)
- * is loaded instead of tuning, a new result is appended.  Synchronous.  Returns
- * SV_ERR_UNSUPPORTED on other precisions. */
+ * JSON-lines file; an entry for this (GPU, SM count, network, window, precision,
+ * batch-shape bucket) is loaded instead of tuning, a new result is appended.  Synchronous.
+ * Returns SV_ERR_UNSUPPORTED on other precisions. */
 SV_API sv_status sv_autotune(sv_ctx* ctx, const sv_pair* pairs, int n_pairs, const char* cache_path,
                              sv_stream stream);
 
@@ -387,7 +389,7 @@ SV_API sv_status sv_synchronize(sv_ctx* ctx, sv_stream stream);
  *                    the next part computes
  *   "debug_plans"    1: print each tensor-core layer's launch plan (ring depth, shared
  *                    memory, CTAs per SM, grid, strips) to stderr when a call is prepared
- *   "graphs"         1 (default): sv_pipeline on an SV_BF16 context captures each batch
+ *   "graphs"         1 (default): sv_pipeline on an SV_BF16 or SV_FP8 context captures each batch
  *                    signature in a CUDA graph and replays it (not on the legacy or
  *                    per-thread default stream); 0: launch eagerly
  * Returns SV_ERR_INVALID_ARG for an unknown key or a value out of range. */

@@ -347,10 +347,10 @@ class Context:
 
     def debug_activation(self, which: int, pair: int, shape) -> np.ndarray:
         """Activation of the last tensor-core refinement as float32 [H, W, C]: BF16 values, or
-        on an FP8 context the E4M3 codes of e1 .. d2 (which 0 .. 5) decoded."""
+        on an FP8 context the E4M3 codes of e1 .. d1 (which 0 .. 4) decoded."""
         import torch
         n = int(np.prod(shape))
-        if self.precision == "fp8" and 0 <= which <= 5:
+        if self.precision == "fp8" and 0 <= which <= 4:
             buf = torch.empty(n, dtype=torch.uint8)
             self._check(lib().sv_debug_activation(self._h, which, pair, c_void_p(buf.data_ptr()), n))
             return buf.view(torch.float8_e4m3fn).float().numpy().reshape(shape)

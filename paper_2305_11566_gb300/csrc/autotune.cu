@@ -1,4 +1,4 @@
-// autotune.cu -- picks the launch shape of every tensor-core layer of the BF16 form on the
+// autotune.cu -- picks the launch shape of every tensor-core layer (BF16 and FP8 forms) on the
 // caller's own batch: for each layer, the strip height (rows of 128-unit tiles one work
 // item walks down, which trades staged-row reuse against load balance) and the N slice
 // (output channels per CTA; narrower slices give more CTAs per pair) and the number of
@@ -36,7 +36,7 @@ std::string tune_key(const Ctx& c, const sv_pair* pairs, int n) {
   std::ostringstream o;
   o << prop.name << "|sm" << prop.multiProcessorCount << "|net" << c.net.enc[0] << "-" << c.net.enc[1] << "-"
     << c.net.enc[2] << "-" << c.net.lat << "-" << c.net.dec[0] << "-" << c.net.dec[1] << "-" << c.net.dec[2] << "|k"
-    << c.cfg.window << "|n" << nb << "|max" << maxW << "x" << maxH << "|mpx" << (px + 500000) / 1000000;
+    << c.cfg.window << "|p" << c.cfg.precision << "|n" << nb << "|max" << maxW << "x" << maxH << "|mpx" << (px + 500000) / 1000000;
   std::string s = o.str();
   for (auto& ch : s)
     if (ch == '"' || ch == '\n') ch = '_';
@@ -144,11 +144,14 @@ sv_status Ctx::autotune(const sv_pair* pairs, int n, const char* cache_path, cud
         tc_ctas_override[i] = cc;
       }
       if (half) {
-        // half-width N slices where that still leaves at least 16 channels per slice
+        // half-width N slices where that still leaves at least 16 channels per slice, for the
+        // one-tap layer (the latent head; a multi-tap layer's packed weights are laid out for
+        // its planned width)
         TcRun probe;
         std::vector<TcLayerPlan> plans;
         if ((s = tc_prepare(pairs, cm.data(), n, outs.data(), probe))) break;
-        for (int i = 0; i < 6; ++i) tc_nt_override[i] = probe.plans[i].NT / 2 >= 16 ? probe.plans[i].NT / 2 : 0;
+        for (int i = 0; i < 6; ++i)
+          tc_nt_override[i] = probe.plans[i].layer == L_MU && probe.plans[i].NT / 2 >= 16 ? probe.plans[i].NT / 2 : 0;
       }
       prof_on = true;
       prof_tot.clear();
@@ -197,7 +200,8 @@ extern "C" sv_status sv_autotune(sv_ctx* ctx, const sv_pair* pairs, int n_pairs,
   if (!ctx) return SV_ERR_INVALID_ARG;
   sv::Ctx* c = reinterpret_cast<sv::Ctx*>(ctx);
   c->err.clear();
-  if (c->cfg.precision != SV_BF16) return c->fail(SV_ERR_UNSUPPORTED, "the autotuner tunes the BF16 tensor-core form");
+  if (c->cfg.precision != SV_BF16 && c->cfg.precision != SV_FP8)
+    return c->fail(SV_ERR_UNSUPPORTED, "the autotuner tunes the tensor-core forms (SV_BF16, SV_FP8)");
   sv_status s = c->check_pairs(pairs, n_pairs);
   if (s) return s;
   if (n_pairs == 0) return SV_OK;

@@ -573,7 +573,42 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
           else tmem_ld16(trow + c0, r);
           constexpr int CW = NT >= 32 ? 32 : NT;
           const bool f8out = F8 && p.out_f8;  // warp-uniform
-          if (f8out) {
+          if (f8out && CW == 32) {
+            // E4M3 codes: relu(scale * acc + bias), 4 per word, through the warp's stage: lane =
+            // pixel writes its two 16-byte pieces (piece q at slot q ^ ((pixel >> 2) & 1):
+            // conflict-free), then two lanes per pixel store its 32 bytes, sixteen pixels per
+            // instruction
+            uint32_t packed[8];
+#pragma unroll
+            for (int e = 0; e < 32; e += 4) {
+              float v[4];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                v[q] = fmaf(__uint_as_float(r[e + q]), bias_s[NT + c0 + e + q], bias_s[c0 + e + q]);
+                if (p.relu) v[q] = fmaxf(v[q], 0.f);
+              }
+              const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[0], v[1]), __NV_SATFINITE, __NV_E4M3);
+              const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v[2], v[3]), __NV_SATFINITE, __NV_E4M3);
+              packed[e / 4] = lo | (hi << 16);
+            }
+            uint4* sw = reinterpret_cast<uint4*>(gbase + (sStage - base)) + warp * 128;
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+              sw[lane * 2 + (q ^ ((lane >> 2) & 1))] =
+                  make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+            __syncwarp();
+#pragma unroll
+            for (int s16 = 0; s16 < 2; ++s16) {
+              const int pp = 16 * s16 + (lane >> 1), q = lane & 1;
+              const uint4 v = sw[pp * 2 + (q ^ ((pp >> 2) & 1))];
+              const int jp = st.j0 + warp * 32 + pp;
+              const int oxp = MODE == TM_UP2 ? 2 * jp + px : jp;
+              if (i < Hu && jp < Wu && oy < Ho && oxp < Wo)
+                *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(out) + ((size_t)oy * Wo + oxp) * p.cout + n0 + c0 +
+                                          16 * q) = v;
+            }
+            __syncwarp();
+          } else if (f8out) {
             if (valid) {
               // E4M3 codes: relu(scale * acc + bias), 4 per word, 16 per 16-byte store
               uint32_t packed[CW / 4];
@@ -1572,6 +1607,7 @@ static void plan_layers(const NetDims& net, std::vector<TcLayerPlan>& plans, siz
     TcLayerPlan pl{};
     pl.layer = l;
     pl.mode = (l == L_ENC2 || l == L_ENC3) ? tc::TM_S2 : l == L_MU ? tc::TM_P1 : tc::TM_UP2;
+    pl.f8 = f8 ? 1 : 0;
     pl.cin = f8 ? net.cin(l) / 2 : net.cin(l);
     pl.cout = net.cout(l);
     pl.relu = l != L_MU;
@@ -1646,9 +1682,9 @@ sv_status Ctx::pack_bf16_weights(cudaStream_t st) {
   return SV_OK;
 }
 
-// FP8 form: per layer the E4M3 codes of the packed operand (in the BF16 pack's byte layout)
-// and its per-output-channel scales; for the decoder layers also the codes of the unfolded
-// 3 x 3 weights and their scales (the border recompute).  Offsets: the plan's wofs (BF16
+// FP8 form: per quantised layer (enc2 .. dec2) the E4M3 codes of the packed operand (in the
+// BF16 pack's byte layout) and its per-output-channel scales; for dec1, dec2 also the codes of
+// the unfolded 3 x 3 weights and their scales (the border recompute).  Offsets: the plan's wofs (BF16
 // units of wf8), scale offsets f8_scale_ofs[6] and f8_unf_ofs / f8_unf_scale_ofs[3].
 sv_status Ctx::pack_fp8_weights(cudaStream_t st) {
   std::vector<TcLayerPlan> plans;
@@ -1676,6 +1712,7 @@ sv_status Ctx::pack_fp8_weights(cudaStream_t st) {
   const float* W = (const float*)w32.p;
   for (size_t li = 0; li < plans.size(); ++li) {
     const TcLayerPlan& pl = plans[li];
+    if (pl.layer == L_DEC3) continue;  // the last decoder layer runs from the BF16 packs
     const int cin = net.cin(pl.layer);
     LaunchScope ls(*this, "pack_fp8", st);
     tc::fp8_scale_kernel<<<(pl.cout + 127) / 128, 128, 0, st>>>(W + net.w_off(pl.layer), pl.mode, cin, pl.cout, 0,
@@ -1687,7 +1724,7 @@ sv_status Ctx::pack_fp8_weights(cudaStream_t st) {
                                                                      (uint8_t*)((__nv_bfloat16*)wf8.p + pl.wofs));
     if ((s = cuda(cudaGetLastError(), "pack FP8 weights"))) return s;
   }
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 2; ++k) {  // dec1, dec2 (dec3's border fix uses the BF16 weights)
     const int cout = net.cout(dl[k]), cin = net.cin(dl[k]);
     LaunchScope ls(*this, "pack_fp8", st);
     tc::fp8_scale_kernel<<<(cout + 127) / 128, 128, 0, st>>>(W + net.w_off(dl[k]), tc::TM_S2, cin, cout, 1,
@@ -1712,9 +1749,18 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
   size_t wtotal;
   const bool f8 = cfg.precision == SV_FP8;
   plan_layers(net, r.plans, wtotal, f8);
+  if (f8) {  // the FP8 form's last decoder layer runs as in the BF16 form (BF16 pack, BF16 d2)
+    std::vector<TcLayerPlan> bfp;
+    size_t bft;
+    plan_layers(net, bfp, bft, false);
+    for (size_t li = 0; li < r.plans.size(); ++li)
+      if (r.plans[li].layer == L_DEC3) r.plans[li] = bfp[li];
+  }
   for (size_t li = 0; li < r.plans.size(); ++li) {
-    if (tc_nt_override[li] > 0 && tc_nt_override[li] <= r.plans[li].NT) {
-      // autotuned narrower N slice (more weight sets, more CTAs per pair)
+    // autotuned narrower N slice (more weight sets, more CTAs per pair): only for one-tap
+    // layers, whose packed weights are the same bytes for any slice width (a multi-tap layer's
+    // pack interleaves the taps per slice of the planned width)
+    if (tc_nt_override[li] > 0 && tc_nt_override[li] <= r.plans[li].NT && r.plans[li].mode == tc::TM_P1) {
       TcLayerPlan& pl = r.plans[li];
       const int NT = tc_nt_override[li];
       pl.NT = NT;
@@ -1723,9 +1769,9 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
       const int RA = pl.mode == tc::TM_S2 ? 3 : pl.mode == tc::TM_UP2 ? 2 : 1;
       const int STEP = pl.mode == tc::TM_S2 ? 2 : 1;
       while (pl.ring < RA + kPrefetchSteps * STEP &&
-             tc::smem_bytes(pl.mode, NT, pl.cin, pl.ring + 1, false, f8) <= kSmemLimit)
+             tc::smem_bytes(pl.mode, NT, pl.cin, pl.ring + 1, false, pl.f8 != 0) <= kSmemLimit)
         ++pl.ring;
-      pl.smem = tc::smem_bytes(pl.mode, NT, pl.cin, pl.ring, false, f8);
+      pl.smem = tc::smem_bytes(pl.mode, NT, pl.cin, pl.ring, false, pl.f8 != 0);
     }
   }
   {
@@ -1742,8 +1788,8 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
       const size_t budget = (size_t)per_sm / k - (size_t)reserved;
       const int RA = pl.mode == tc::TM_S2 ? 3 : pl.mode == tc::TM_UP2 ? 2 : 1;
       const int STEP = pl.mode == tc::TM_S2 ? 2 : 1;
-      while (pl.ring > RA + STEP && tc::smem_bytes(pl.mode, pl.NT, pl.cin, pl.ring, false, f8) > budget) --pl.ring;
-      pl.smem = tc::smem_bytes(pl.mode, pl.NT, pl.cin, pl.ring, false, f8);
+      while (pl.ring > RA + STEP && tc::smem_bytes(pl.mode, pl.NT, pl.cin, pl.ring, false, pl.f8 != 0) > budget) --pl.ring;
+      pl.smem = tc::smem_bytes(pl.mode, pl.NT, pl.cin, pl.ring, false, pl.f8 != 0);
     }
   }
   // a layer whose ring holds no row beyond the tile's own (the weights fill shared memory)
@@ -1765,11 +1811,11 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
       if (pl.smem <= share) budget = share;  // else k CTAs do not fit anyway: one per SM
     }
     int units = RA * KB;
-    while (units < 3 * RA * KB && tc::smem_bytes(pl.mode, pl.NT, pl.cin, units + 1, true, f8) <= budget) ++units;
+    while (units < 3 * RA * KB && tc::smem_bytes(pl.mode, pl.NT, pl.cin, units + 1, true, pl.f8 != 0) <= budget) ++units;
     if (units <= RA * KB) continue;  // no unit of look-ahead fits
     pl.split = 1;
     pl.ring = units;
-    pl.smem = tc::smem_bytes(pl.mode, pl.NT, pl.cin, units, true, f8);
+    pl.smem = tc::smem_bytes(pl.mode, pl.NT, pl.cin, units, true, pl.f8 != 0);
   }
   sv_status s;
   int nsm = 0;
@@ -1789,9 +1835,9 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
     }
     lens.push_back({need[0], need[1], need[2], need[3], need[4], need[5], need[6]});
   }
-  // BF16 activations; the FP8 form keeps e2 .. d2 as E4M3 codes (one byte per channel) and
-  // the E4M3 codes of e1 in tc_act[7] (e1 itself, from the first layer, stays BF16, as d3)
-  auto esize = [&](int k) { return f8 && k >= 1 && k <= 5 ? (size_t)1 : sizeof(__nv_bfloat16); };
+  // BF16 activations; the FP8 form keeps e2 .. d1 (the inputs of its quantised layers) as E4M3
+  // codes (one byte per channel) and the E4M3 codes of e1 in tc_act[7]
+  auto esize = [&](int k) { return f8 && k >= 1 && k <= 4 ? (size_t)1 : sizeof(__nv_bfloat16); };
   for (int k = 0; k < 7; ++k)
     if ((s = cuda(tc_act[k].ensure(std::max<size_t>(cnt[k], 16) * esize(k)), "alloc activations"))) return s;
   if (f8 && (s = cuda(tc_act[7].ensure(std::max<size_t>(cnt[0], 16)), "alloc FP8 e1"))) return s;
@@ -1895,7 +1941,7 @@ sv_status Ctx::tc_prepare(const sv_pair* pairs, const int16_t* const* coarse, in
   r.fused = false;
   bool even = true;
   for (int i = 0; i < n; ++i) even = even && (pairs[i].width % 2 == 0);
-  if (!f8 && !coarse_f && fused_final && even && tc::fused_supported(net.dec[2], net.dec[1]) && wfuse.p) {
+  if (!coarse_f && fused_final && even && tc::fused_supported(net.dec[2], net.dec[1]) && wfuse.p) {
     const int NT = net.dec[2], cin = net.dec[1];
     int ring = 4;  // 3 rows per tile + 1 ahead; more where shared memory allows
     while (ring < 3 + kPrefetchSteps && tc::fused_smem_bytes(NT, cin, ring + 1) <= kSmemLimit) ++ring;
@@ -1969,10 +2015,11 @@ sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream
     prm.lp = (const LayerPair*)(tables + r.tabs[li].lp_ofs);
     prm.strips = (const Strip*)(tables + r.tabs[li].strip_ofs);
     prm.n_strips = r.tabs[li].n_strips;
-    prm.wpack = (const __nv_bfloat16*)(f8 ? wf8.p : wbf.p) + pl.wofs;
+    const bool lf8 = pl.f8 != 0;
+    prm.wpack = (const __nv_bfloat16*)(lf8 ? wf8.p : wbf.p) + pl.wofs;
     prm.bias = W + net.b_off(pl.layer);
-    prm.scale = f8 ? (const float*)wf8s.p + f8_scale_ofs[li] : nullptr;
-    prm.out_f8 = f8 && pl.layer != L_DEC3;
+    prm.scale = lf8 ? (const float*)wf8s.p + f8_scale_ofs[li] : nullptr;
+    prm.out_f8 = lf8 && pl.layer != L_DEC2;  // dec2 writes the BF16 d2 of the last decoder layer
     prm.cin = pl.cin;
     prm.cout = pl.cout;
     prm.G = pl.G;
@@ -2012,9 +2059,9 @@ sv_status Ctx::tc_launch(const TcRun& r, const unsigned char* tables, cudaStream
     }
     {
       LaunchScope ls(*this, names[li], st);
-      if ((s = cuda(tc::launch_conv(pl.mode, prm, pl.NT, r.tabs[li].grid, pl.smem, st, f8), names[li]))) return s;
+      if ((s = cuda(tc::launch_conv(pl.mode, prm, pl.NT, r.tabs[li].grid, pl.smem, st, lf8), names[li]))) return s;
     }
-    if (f8 && pl.mode == tc::TM_UP2 && r.tabs[li].fix_segments > 0) {
+    if (lf8 && pl.mode == tc::TM_UP2 && r.tabs[li].fix_segments > 0) {
       const int k = pl.layer == L_DEC1 ? 0 : pl.layer == L_DEC2 ? 1 : 2;
       LaunchScope ls(*this, "edge_up2fix", st);
       if ((s = cuda(launch_edge_up2fix_f8((const UpFixPair*)(tables + r.tabs[li].fix_ofs), r.n, r.tabs[li].fix_segments,

@@ -237,7 +237,8 @@ sv_status Ctx::refresh_weight_copies_async(cudaStream_t st) {
     f32_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const float*)w32.p, (double*)w64.p, n);
     if ((s = cuda(cudaGetLastError(), "weights to fp64"))) return s;
   }
-  if (cfg.precision == SV_BF16)
+  // (the FP8 form also runs its last decoder layer from the BF16 packs)
+  if (cfg.precision == SV_BF16 || cfg.precision == SV_FP8)
     if ((s = pack_bf16_weights(st))) return s;
   if (cfg.precision == SV_FP8)
     if ((s = pack_fp8_weights(st))) return s;
@@ -285,8 +286,8 @@ static bool config_ok(const sv_config* c) {
   if (!sv::valid_width_pub(c->latent_ch)) return false;
   if (c->precision < SV_FP32 || c->precision > SV_FP8) return false;
   if (c->precision == SV_FP8) {
-    // E4M3 operands: a tensor-core layer's input width is a whole number of 32-element K steps
-    const int in_w[6] = {c->enc_ch[0], c->enc_ch[1], c->enc_ch[2], c->latent_ch, c->dec_ch[0], c->dec_ch[1]};
+    // E4M3 operands: a quantised layer's input width is a whole number of 32-element K steps
+    const int in_w[5] = {c->enc_ch[0], c->enc_ch[1], c->enc_ch[2], c->latent_ch, c->dec_ch[0]};
     for (int w : in_w)
       if (w % 32) return false;
   }
@@ -677,8 +678,8 @@ sv_status sv_debug_activation(sv_ctx* ctx, int which, int pair, void* dst, size_
   if (c->t1) return c->fail(SV_ERR_UNSUPPORTED, "not available for the Table I network");
   if (which < 0 || which > 6 || pair < 0 || pair >= (int)c->tc_off.size() || !dst)
     return c->fail(SV_ERR_INVALID_ARG, "no such activation");
-  // FP8 contexts keep e1 .. d2 as E4M3 codes (one byte per element; e1's codes in tc_act[7])
-  const bool f8 = c->cfg.precision == SV_FP8 && which <= 5;
+  // FP8 contexts keep e1 .. d1 as E4M3 codes (one byte per element; e1's codes in tc_act[7])
+  const bool f8 = c->cfg.precision == SV_FP8 && which <= 4;
   const size_t es = f8 ? 1 : sizeof(__nv_bfloat16);
   const int buf = f8 && which == 0 ? 7 : which;
   if (bytes != c->tc_len[pair][which] * es)

@@ -28,6 +28,7 @@ struct TcLayerPlan {
   int split;  // 1: ring units are channel blocks of rows (ring counts units)
   size_t wofs, smem;
   size_t fix_wofs;  // decoder layers: BF16 [co][3][3][ci] weights of the border fix
+  int f8;           // E4M3 operands (the FP8 form's quantised layers; cin counts channel pairs)
 };
 
 // Prepared tensor-core refinement call: plans, table bytes and launch geometry.

@@ -768,6 +768,20 @@ __device__ __forceinline__ float e4m3_value(uint8_t c) {
   return static_cast<float>(x);
 }
 
+// sixteen E4M3 codes (one 16-byte word) to FP32, two at a time through the paired conversion
+__device__ __forceinline__ void e4m3x16_to_f32(const uint4& v, float* d) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((w[k] >> (16 * h)) & 0xFFFFu), __NV_E4M3);
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&hr));
+      d[4 * k + 2 * h] = f.x;
+      d[4 * k + 2 * h + 1] = f.y;
+    }
+}
+
 __global__ void __launch_bounds__(256) edge_up2fix_f8(const UpFixPair* __restrict__ pairs, const uint8_t* __restrict__ Wq,
                                                       const float* __restrict__ wscale, const float* __restrict__ bias,
                                                       int cin, int cout, int relu, int out_f8) {
@@ -793,20 +807,52 @@ __global__ void __launch_bounds__(256) edge_up2fix_f8(const UpFixPair* __restric
   for (int c0 = 0; c0 < cin; c0 += kFixCk) {
     const int ck = min(kFixCk, cin - c0);
     __syncthreads();
-    for (int e = threadIdx.x; e < 2 * kFixQ * ck; e += blockDim.x) {
-      const int a = e / (kFixQ * ck), r = e - a * kFixQ * ck, q = r / ck, c = r - q * ck;
-      const int uy = rowfix ? L.Ho - 2 + a : p0 - 1 + q;
-      const int ux = rowfix ? p0 - 1 + q : L.Wo - 2 + a;
-      float v = 0.f;
-      if (uy >= 0 && uy < L.Ho && ux >= 0 && ux < L.Wo)
-        v = e4m3_value(in[((size_t)(uy >> 1) * L.Wi + (ux >> 1)) * cin + c0 + c]);
-      S[((size_t)a * kFixQ + q) * kFixCk + c] = v;
+    // 16 codes per 16-byte load (cin is a multiple of 32); a thread's loads are all issued
+    // before any is decoded
+    const int c16 = ck / 16;
+    constexpr int U = 4;
+    for (int e0 = threadIdx.x; e0 < 2 * kFixQ * c16; e0 += U * blockDim.x) {
+      uint4 v[U];
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int e = e0 + i * (int)blockDim.x;
+        const int a = e / (kFixQ * c16), r = e - a * kFixQ * c16, q = r / c16, u = r - q * c16;
+        const int uy = rowfix ? L.Ho - 2 + a : p0 - 1 + q;
+        const int ux = rowfix ? p0 - 1 + q : L.Wo - 2 + a;
+        v[i] = make_uint4(0, 0, 0, 0);
+        if (e < 2 * kFixQ * c16 && uy >= 0 && uy < L.Ho && ux >= 0 && ux < L.Wo)
+          v[i] = *reinterpret_cast<const uint4*>(in + ((size_t)(uy >> 1) * L.Wi + (ux >> 1)) * cin + c0 + u * 16);
+      }
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int e = e0 + i * (int)blockDim.x;
+        if (e >= 2 * kFixQ * c16) break;
+        const int a = e / (kFixQ * c16), r = e - a * kFixQ * c16, q = r / c16, u = r - q * c16;
+        e4m3x16_to_f32(v[i], S + ((size_t)a * kFixQ + q) * kFixCk + u * 16);
+      }
     }
-    for (int e = threadIdx.x; e < 6 * ck * 32; e += blockDim.x) {
-      const int o = e & 31, r = e >> 5, t = r / ck, c = r - t * ck;
-      const int a = t / 3, b = t - 3 * a, ky = rowfix ? a : b, kx = rowfix ? b : a;
-      Wf[((size_t)t * kFixCk + c) * 32 + o] =
-          cb + o < cout ? e4m3_value(Wq[((size_t)((cb + o) * 3 + ky) * 3 + kx) * cin + c0 + c]) : 0.f;
+    for (int e0 = threadIdx.x; e0 < 6 * c16 * 32; e0 += U * blockDim.x) {
+      uint4 v[U];
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int e = e0 + i * (int)blockDim.x;
+        const int o = e & 31, r = e >> 5, t = r / c16, u = r - t * c16;
+        const int a = t / 3, b = t - 3 * a, ky = rowfix ? a : b, kx = rowfix ? b : a;
+        v[i] = make_uint4(0, 0, 0, 0);
+        if (e < 6 * c16 * 32 && cb + o < cout)
+          v[i] = *reinterpret_cast<const uint4*>(Wq + ((size_t)((cb + o) * 3 + ky) * 3 + kx) * cin + c0 + u * 16);
+      }
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int e = e0 + i * (int)blockDim.x;
+        if (e >= 6 * c16 * 32) break;
+        const int o = e & 31, r = e >> 5, t = r / c16, u = r - t * c16;
+        float f[16];
+        e4m3x16_to_f32(v[i], f);
+        float* d = Wf + ((size_t)t * kFixCk + u * 16) * 32 + o;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) d[j * 32] = f[j];
+      }
     }
     __syncthreads();
     for (int t = 0; t < 6; ++t) {

@@ -52,7 +52,7 @@ def test_invalid_configs_rejected(svlib):
     bad.append(c)
     c = binding.make_config(synth.NET_SMALL, 7, "fp8")  # FP8: a 16-wide input to a tensor-core layer
     bad.append(c)
-    c = binding.make_config(synth.NetShape((32, 64, 128), 128, (128, 48, 32)), 7, "fp8")  # dec2 width 48
+    c = binding.make_config(synth.NetShape((32, 64, 128), 128, (48, 64, 32)), 7, "fp8")  # dec1 width 48
     bad.append(c)
     for c in bad:
         assert svlib.sv_param_count(ctypes.byref(c)) == 0
@@ -62,9 +62,9 @@ def test_invalid_configs_rejected(svlib):
 
 
 def test_fp8_config_accepted(svlib):
-    # widths that are multiples of 32 where a tensor-core layer reads them (the last decoder
-    # width feeds the FP32 final conv and may be 16)
-    for shape in (synth.NET_WIDE, synth.NetShape((32, 64, 128), 128, (128, 64, 16))):
+    # widths that are multiples of 32 where a quantised layer reads them (dec2's and dec3's
+    # outputs feed BF16 layers and may be 16 wide)
+    for shape in (synth.NET_WIDE, synth.NetShape((32, 64, 128), 128, (128, 48, 16))):
         c = binding.make_config(shape, 9, "fp8")
         assert svlib.sv_param_count(ctypes.byref(c)) == shape.n_params()
 

@@ -99,6 +99,11 @@ def test_autotune_keeps_results_and_caches(svlib, batch, tmp_path):
         out2 = run(again, dps, s)
         for a, b in zip(out2, ref):
             assert torch.equal(a, b)
+        # the unfused decoder tail under the tuned plan (its own launch shapes) as well
+        base.set_option("fused_final", 0)
+        tuned.set_option("fused_final", 0)
+        for a, b in zip(run(tuned, dps, s), run(base, dps, s)):
+            assert torch.equal(a, b)
     finally:
         base.close()
         tuned.close()

@@ -1,13 +1,15 @@
 """GPU parity of the FP8 (E4M3) form, the quantised refinement of Sec. V, against the
 oracle's quantised refinement, through the C ABI.
 
-Layer by layer: each tensor-core layer's output is compared with the oracle's same layer
-(`oracle.qconv_layer`: per-output-channel weight scales, E4M3 weight codes, FP64 sums)
-applied to the GPU's own input codes, so that a wrong scale, code, byte layout, phase,
+Layer by layer: each quantised layer's output (enc2 .. dec2) is compared with the oracle's
+same layer (`oracle.qconv_layer`: per-output-channel weight scales, E4M3 weight codes, FP64
+sums) applied to the GPU's own input codes, so that a wrong scale, code, byte layout, phase,
 tap or border pixel shows in the layer where it happens.  The GPU sums E4M3 products in
 FP32 on the tensor cores, the oracle in FP64: a value within a few FP32 ulps of a rounding
 midpoint can land on either side.  Bar: at most 1e-3 of a layer's codes differ, and each
-differing code is a neighbour on the E4M3 grid (dec3's BF16 output: on the BF16 grid).
+differing code is a neighbour on its grid (E4M3; dec2's output: BF16).  The last decoder
+layer runs as in the BF16 form (BF16 weights): its d3 against the oracle's unquantised layer
+on the GPU's own d2, within the BF16 form's layer bar (3 % of the largest magnitude).
 
 End to end (refined disparity against `oracle.refine_forward_q` on the same coarse map):
 such single-step differences propagate through the later layers, so the bar is statistical
@@ -84,11 +86,13 @@ def test_fp8_layers_match_the_quantised_oracle(ctx, W, H, D, enc1_tc):
     params = synth.he_normal_weights(SHAPE, 7)
     dp = binding.to_device(p, D)
     ctx.set_option("enc1_tensor", enc1_tc)
+    ctx.set_option("fused_final", 0)  # keep d3 in HBM so that it can be compared
     try:
         Y = ctx.refine([dp], [torch.from_numpy(disp_o.astype(np.int16)).cuda()])[0]
         ctx.synchronize()
     finally:
         ctx.set_option("enc1_tensor", 1)
+        ctx.set_option("fused_final", 1)
     g = {a: ctx.debug_activation(i, 0, act_shape(H, W, a)).astype(np.float64)
          for i, a in enumerate(["e1", "e2", "e3", "z", "d1", "d2", "d3"])}
     # e1: E4M3 codes of the first layer's BF16-rounded output, against the oracle's
@@ -97,11 +101,14 @@ def test_fp8_layers_match_the_quantised_oracle(ctx, W, H, D, enc1_tc):
     (_, _), L1, L2, L3 = oracle.level_sizes(H, W)
     chain = [("enc2", g["e1"], "e2", 0, L2, "e4m3", True), ("enc3", g["e2"], "e3", 0, L3, "e4m3", True),
              ("mu", g["e3"], "z", 1, L3, "e4m3", False), ("dec1", g["z"], "d1", 2, L2, "e4m3", True),
-             ("dec2", g["d1"], "d2", 2, L1, "e4m3", True), ("dec3", g["d2"], "d3", 2, (H, W), "bf16", True)]
+             ("dec2", g["d1"], "d2", 2, L1, "bf16", True)]
     for name, x, out, mode, hw, rnd, relu in chain:
         wt, b = layer_weights(params, name)
         o = oracle.qconv_layer(x, wt, b, mode, hw, relu=relu, out_round=rnd)
         check_codes(g[out], o, e4m3_ordinal if rnd == "e4m3" else bf16_ordinal, f"{W}x{H} {name}")
+    wt, b = layer_weights(params, "dec3")
+    o = oracle.qconv_layer(g["d2"], wt, b, 2, (H, W), relu=True, out_round="bf16", quant_weights=False)
+    assert np.abs(g["d3"] - o).max() <= 3e-2 * np.abs(o).max(), f"{W}x{H} dec3"
     # the refined disparity against the oracle's whole quantised forward
     refq = oracle.refine_forward_q(SHAPE, params, p.left, disp_o.astype(np.float64))["Y"]
     keep = np.ones((H, W), dtype=bool)
@@ -109,6 +116,7 @@ def test_fp8_layers_match_the_quantised_oracle(ctx, W, H, D, enc1_tc):
 
 
 def test_fp8_full_size_against_the_quantised_and_plain_oracle(ctx):
+    """1242 x 375 through the default plan (the last decoder layer fused with the final conv)."""
     W, H, D = 1242, 375, 48
     p = synth.make_pair(W, H, 60.0, 8300)
     disp_o = oracle.coarse_match(p.left, p.right, 5, D)[0]
@@ -149,6 +157,35 @@ def test_fp8_batched_graph_pipeline(ctx):
         refq = oracle.refine_forward_q(SHAPE, params, p.left, disp_o.astype(np.float64))["Y"]
         parity.compare_refined(o.cpu().numpy(), refq, keep, MAX_PX, MEAN_PX, p.gt, EPE_PX,
                                f"fp8 graph {p.width}x{p.height}")
+
+
+def test_fp8_autotuned_plans_give_the_same_result(svlib):
+    """Tuned launch shapes (strip heights, N slices, CTAs per SM) change no arithmetic of an
+    output element: the tuned batch must equal the untuned one bit for bit, with the decoder
+    tail fused and unfused."""
+    pairs = synth.batch_uneven(6, seed=8800)
+    dps = [binding.to_device(p, D) for p, D in pairs]
+    s = torch.cuda.Stream()
+    plain = binding.Context(SHAPE, 9, "fp8")
+    tuned = binding.Context(SHAPE, 9, "fp8")
+    try:
+        for c in (plain, tuned):
+            c.set_weights(synth.he_normal_weights(SHAPE, 7))
+        tuned.autotune(dps, stream=s)
+        for fused in (1, 0):
+            outs = []
+            for c in (plain, tuned):
+                c.set_option("fused_final", fused)
+                with torch.cuda.stream(s):
+                    o = c.pipeline(dps)
+                s.synchronize()
+                c.synchronize(s)
+                outs.append([x.clone() for x in o])
+            for a, b in zip(*outs):
+                assert torch.equal(a, b), f"fused_final {fused}"
+    finally:
+        plain.close()
+        tuned.close()
 
 
 def test_fp8_is_inference_only(ctx):
