@@ -245,9 +245,129 @@ zncc_wta_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ jobs) 
   }
 }
 
+// Disparity ranges of 33-48 (MODE 0, disparities only): the two half-warps own TXH output
+// columns each (half h: columns xw + h TXH + t) and lane l = lane % 16 the disparities d = l +
+// 16 k, k < 3, so that all 48 candidates of a pixel fill the half's 48 slots (the full-warp
+// layout uses 64 slots for them).  A lane keeps its best candidate as a float (strict ">"
+// over ascending k: lowest d on exact ties); the half's argmax is one max reduction over a
+// packed key, the lane's order key with its low 6 bits replaced by 63 - d, so that among
+// scores equal to 2^-17 relative the lowest d wins.  Stages 1 and 2 as in zncc_wta_kernel.
+template <int R, int TXH>
+__global__ void __launch_bounds__(kZnccWarps * 32, 2)
+zncc_wta_hw_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ jobs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int KH = 3, TX = 2 * TXH;
+  const int TY = kZnccTY;
+  const ZJob job = jobs[blockIdx.x];
+  const ZPair P = pairs[job.pair];
+  const int D = P.D, w = P.w, h = P.h;
+  const ZLayout Z = zlayout(R, D, TX);
+  uint16_t* sL = reinterpret_cast<uint16_t*>(smem + Z.off_sl);
+  uint16_t* sR = reinterpret_cast<uint16_t*>(smem + Z.off_sr);
+  int* sumL = reinterpret_cast<int*>(smem + Z.off_suml);
+  float* invL = reinterpret_cast<float*>(smem + Z.off_invl);
+  int2* statR = reinterpret_cast<int2*>(smem + Z.off_statr);
+  int* cs = reinterpret_cast<int*>(smem + Z.off_cs);
+  unsigned* cs2 = reinterpret_cast<unsigned*>(smem + Z.off_cs2);
+  const int y0 = job.y0, x0 = job.x0;
+  const int lbase = x0 - R;
+  const int rbase = x0 - R - (D - 1);
+  stage_box<R>(P.L, P.pitch, w, h, lbase, y0, Z.nlc, sL);
+  stage_box<R>(P.R, P.pitch, w, h, rbase, y0, Z.nrc, sR);
+  __syncthreads();
+  window_stats<R>(sL, Z.nlc, cs, cs2, sumL, invL, nullptr, Z.gx);
+  window_stats<R>(sR, Z.nrc, cs, cs2, nullptr, nullptr, statR, Z.nrs);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, hf = lane >> 4, l = lane & 15;
+  const int xw = x0 + warp * TX;
+  if (xw >= w) return;                     // all of this warp's columns lie beyond the image
+  const int xh = xw + hf * TXH;            // this half's first output column
+  const int lc0 = warp * TX + hf * TXH;    // staged left column of u = xh - R
+  const long long N = (long long)(2 * R + 1) * (2 * R + 1);
+  int dd[KH], rc0[KH];
+#pragma unroll
+  for (int k = 0; k < KH; ++k) {
+    const int d = l + 16 * k;
+    dd[k] = d < D ? d : D - 1;             // reads stay in the staged range; masked below
+    rc0[k] = lc0 - dd[k] + (D - 1);
+  }
+  unsigned colsum[KH][TXH + 2 * R];
+#pragma unroll
+  for (int c = 0; c < TXH + 2 * R; ++c) {
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+      unsigned a = 0;
+#pragma unroll
+      for (int j = 0; j <= 2 * R; ++j) a += (unsigned)sL[j * Z.nlc + lc0 + c] * (unsigned)sR[j * Z.nrc + rc0[k] + c];
+      colsum[k][c] = a;
+    }
+  }
+  for (int yi = 0; yi < TY; ++yi) {
+    const int y = y0 + yi;
+    if (yi > 0) {
+      const int rin = yi + 2 * R, rout = yi - 1;
+#pragma unroll
+      for (int c = 0; c < TXH + 2 * R; ++c) {
+        const unsigned lin = sL[rin * Z.nlc + lc0 + c], lout = sL[rout * Z.nlc + lc0 + c];
+#pragma unroll
+        for (int k = 0; k < KH; ++k)
+          colsum[k][c] += lin * (unsigned)sR[rin * Z.nrc + rc0[k] + c] - lout * (unsigned)sR[rout * Z.nrc + rc0[k] + c];
+      }
+    }
+    unsigned run[KH];
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+      unsigned a = 0;
+#pragma unroll
+      for (int i = 0; i <= 2 * R; ++i) a += colsum[k][i];
+      run[k] = a;
+    }
+    int my_key = INT_MIN;
+#pragma unroll
+    for (int t = 0; t < TXH; ++t) {
+      if (t > 0) {
+#pragma unroll
+        for (int k = 0; k < KH; ++k) run[k] += colsum[k][t + 2 * R] - colsum[k][t - 1];
+      }
+      const int x = xh + t;
+      const int sl = sumL[yi * Z.gx + lc0 + t];
+      const float il = invL[yi * Z.gx + lc0 + t];
+      float bv = -4.0f;
+      int bd = 0;
+#pragma unroll
+      for (int k = 0; k < KH; ++k) {
+        const int d = l + 16 * k;
+        const int2 sr = statR[yi * Z.nrs + lc0 + t - dd[k] + (D - 1)];  // right window at x - d
+        const long long n = N * (long long)run[k] - (long long)sl * (long long)sr.x;
+        const float rho = (float)n * il * __int_as_float(sr.y);
+        if (d < D && d <= x && x < w && rho > bv) {
+          bv = rho;
+          bd = d;
+        }
+      }
+      int key = bv > -3.0f ? ((order_key(bv) & ~63) | (63 - bd)) : INT_MIN;
+#pragma unroll
+      for (int off = 8; off >= 1; off >>= 1) key = max(key, __shfl_xor_sync(0xFFFFFFFFu, key, off));
+      if (l == t) my_key = key;
+    }
+    const int x = xh + l;
+    if (l < TXH && x < w && y < h) P.disp[(size_t)y * w + x] = (int16_t)(my_key == INT_MIN ? 0 : 63 - (my_key & 63));
+  }
+}
+
 template <int R, int KD, int MODE>
 cudaError_t launch_rk(const ZPair* p, const ZJob* j, int n, int maxD, cudaStream_t st) {
   constexpr int TX = KD == 1 ? 32 : KD == 2 ? 20 : KD == 3 ? 16 : 12;  // == zncc_tx(KD)
+  if constexpr (MODE == 0 && KD == 2) {
+    if (maxD <= 48) {  // half-warp layout: 48 candidate slots per pixel, the same job geometry
+      auto kern = zncc_wta_hw_kernel<R, TX / 2>;
+      const size_t smem = zlayout(R, maxD, TX).total;
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      kern<<<n, kZnccWarps * 32, smem, st>>>(p, j);
+      return cudaGetLastError();
+    }
+  }
   auto kern = zncc_wta_kernel<R, KD, TX, MODE>;
   const size_t smem = zlayout(R, maxD, TX).total;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
