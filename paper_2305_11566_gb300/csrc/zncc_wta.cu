@@ -250,8 +250,8 @@ zncc_wta_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ jobs) 
 // 16 k, k < 3, so that all 48 candidates of a pixel fill the half's 48 slots (the full-warp
 // layout uses 64 slots for them).  A lane keeps its best candidate as a float (strict ">"
 // over ascending k: lowest d on exact ties); the half's argmax is one max reduction over a
-// packed key, the lane's order key with its low 6 bits replaced by 63 - d, so that among
-// scores equal to 2^-17 relative the lowest d wins.  Stages 1 and 2 as in zncc_wta_kernel.
+// 64-bit key, the lane's order key above 63 - d, so that the lowest d wins exact ties, as in
+// the full-warp kernel.  Stages 1 and 2 as in zncc_wta_kernel.
 template <int R, int TXH>
 __global__ void __launch_bounds__(kZnccWarps * 32, 2)
 zncc_wta_hw_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ jobs) {
@@ -322,7 +322,7 @@ zncc_wta_hw_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ job
       for (int i = 0; i <= 2 * R; ++i) a += colsum[k][i];
       run[k] = a;
     }
-    int my_key = INT_MIN;
+    long long my_key = LLONG_MIN;
 #pragma unroll
     for (int t = 0; t < TXH; ++t) {
       if (t > 0) {
@@ -345,13 +345,13 @@ zncc_wta_hw_kernel(const ZPair* __restrict__ pairs, const ZJob* __restrict__ job
           bd = d;
         }
       }
-      int key = bv > -3.0f ? ((order_key(bv) & ~63) | (63 - bd)) : INT_MIN;
+      long long key = bv > -3.0f ? (long long)order_key(bv) * 4294967296LL + (63 - bd) : LLONG_MIN;
 #pragma unroll
       for (int off = 8; off >= 1; off >>= 1) key = max(key, __shfl_xor_sync(0xFFFFFFFFu, key, off));
       if (l == t) my_key = key;
     }
     const int x = xh + l;
-    if (l < TXH && x < w && y < h) P.disp[(size_t)y * w + x] = (int16_t)(my_key == INT_MIN ? 0 : 63 - (my_key & 63));
+    if (l < TXH && x < w && y < h) P.disp[(size_t)y * w + x] = (int16_t)(my_key == LLONG_MIN ? 0 : 63 - (int)(my_key & 63));
   }
 }
 
