@@ -82,9 +82,9 @@ def peaks():
 # capture, per pair; valid only while the kernel's sources are unchanged since the capture
 # (checked by content hash), else the roofline reports traffic as null.
 MEASURED_TRAFFIC = {
-    "tc_dec3_final": {"bytes_per_pair": (242.958848e6 + 22.433024e6) / 16,
-                      "sources": {"paper_2305_11566_gb300/csrc/conv_tc.cu": "7ad8e4fba289",
-                                  "paper_2305_11566_gb300/csrc/sv_ctx.cuh": "e22901a154b3",
+    "tc_dec3_final": {"bytes_per_pair": (242.922752e6 + 22.4576e6) / 16,
+                      "sources": {"paper_2305_11566_gb300/csrc/conv_tc.cu": "78da2f067884",
+                                  "paper_2305_11566_gb300/csrc/sv_ctx.cuh": "a591b9b4c3ec",
                                   "paper_2305_11566_gb300/csrc/sv_internal.cuh": "acfab0daefd1"},
                       "capture": "profiles/dec3_final_fused_16x1242x375.md (16 pairs, scaled by pairs)"},
 }
