@@ -176,13 +176,24 @@ class DevicePair:
     height: int
     max_disp: int
 
+    def __setattr__(self, name, value):
+        object.__setattr__(self, name, value)
+        object.__setattr__(self, "_fields", None)  # the marshalled fields follow any change
+
     @property
     def pitch(self) -> int:
         return int(self.left.stride(0))
 
+    def fields(self) -> tuple:
+        """(left, right, width, height, pitch, max_disp) as the C struct holds them (cached)."""
+        f = self._fields
+        if f is None:
+            f = (self.left.data_ptr(), self.right.data_ptr(), self.width, self.height, self.pitch, self.max_disp)
+            object.__setattr__(self, "_fields", f)
+        return f
+
     def sv(self) -> SvPair:
-        return SvPair(self.left.data_ptr(), self.right.data_ptr(), self.width, self.height, self.pitch,
-                      self.max_disp)
+        return SvPair(*self.fields())
 
     @property
     def coarse_hw(self):
@@ -196,11 +207,17 @@ def to_device(pair: synth.Pair, max_disp: int, device="cuda") -> DevicePair:
     return DevicePair(L, R, pair.width, pair.height, max_disp)
 
 
+# numpy view of an sv_pair array: one array build instead of one ctypes struct per pair
+_SV_PAIR_DTYPE = np.dtype({"names": ["left", "right", "width", "height", "pitch", "max_disp"],
+                           "formats": ["<u8", "<u8", "<i4", "<i4", "<i4", "<i4"],
+                           "offsets": [SvPair.left.offset, SvPair.right.offset, SvPair.width.offset,
+                                       SvPair.height.offset, SvPair.pitch.offset, SvPair.max_disp.offset],
+                           "itemsize": ctypes.sizeof(SvPair)})
+
+
 def _pairs_array(pairs):
-    arr = (SvPair * max(1, len(pairs)))()
-    for i, p in enumerate(pairs):
-        arr[i] = p.sv()
-    return arr
+    a = np.array([p.fields() for p in pairs] if len(pairs) else [(0, 0, 0, 0, 0, 0)], dtype=_SV_PAIR_DTYPE)
+    return (SvPair * len(a)).from_buffer(a)
 
 
 class Context:
