@@ -115,3 +115,21 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[st]) == ctypes.sizeof(cls), st
         for n in names:
             assert int(got[f"{st}.{n}"]) == getattr(cls, n).offset, (st, n)
+
+
+def test_pair_array_marshalling():
+    """The pair array handed to the C ABI (one numpy buffer over the sv_pair layout) holds the
+    same bytes as sv_pair structs built field by field, and follows a pair whose image is
+    replaced (the cached fields are dropped on any attribute change)."""
+    import torch
+    imgs = [torch.zeros((8 + i, 32 + 16 * (i % 3)), dtype=torch.uint8) for i in range(5)]
+    dps = [binding.DevicePair(imgs[i], imgs[(i + 1) % 5], 30 + i, 8 + i, 20 + i) for i in range(5)]
+    arr = binding._pairs_array(dps)
+    ref = (binding.SvPair * 5)(*[binding.SvPair(p.left.data_ptr(), p.right.data_ptr(), p.width, p.height,
+                                                 int(p.left.stride(0)), p.max_disp) for p in dps])
+    assert bytes(memoryview(arr)) == bytes(memoryview(ref))
+    dps[2].left = imgs[4]
+    dps[2].max_disp = 7
+    arr = binding._pairs_array(dps)
+    assert arr[2].left == imgs[4].data_ptr() and arr[2].max_disp == 7 and arr[2].pitch == imgs[4].stride(0)
+    assert len(binding._pairs_array([])) == 1  # a one-element placeholder for empty calls
