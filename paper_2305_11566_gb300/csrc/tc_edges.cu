@@ -5,7 +5,8 @@
 //                staging: x0 = (L / 256, U / 256), U = 4 * bilinear(coarse).  FP32
 //                arithmetic, BF16 NHWC output; 4 output rows per thread.
 //   enc1_tc      the same layer with the 2 -> C1 products on the tensor cores (C1 = 16, 32,
-//                64): the staged input becomes an im2col A tile in shared memory.
+//                64): the staged input becomes an im2col A tile in shared memory; a
+//                persistent grid whose blocks walk the (pair, tile) list.
 //   edge_final   last conv (3x3, C -> 1) + bias + U (residual), BF16 input, FP32 output;
 //                register-blocked packed-FP32 form for C = 16, 32, 64, 128.
 //   edge_up2fix  exact recomputation of the last row / column of an odd-sized (cropped)
@@ -276,27 +277,45 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 constexpr uint32_t kE1Tile = 128 * 32 * 2;  // one A tile (128 pixels x K = 32, BF16)
 constexpr int kE1TcBH = 16;                  // e1 rows per block of the tensor-core kernel
 constexpr int kE1Tiles = kE1TcBH / 4;        // its MMA tiles (4 rows x 32 columns each)
+constexpr int kE1BlocksPerSm = 3;            // resident blocks of the persistent kernel
 __host__ __device__ constexpr size_t enc1_tc_smem(int C1) {
   return 128 + kE1Tiles * (size_t)kE1Tile + 2 * (size_t)C1 * 64 + (size_t)C1 * 4 + 16;
 }
 
-// Blocks of 16 x 32 e1 pixels (4 MMA tiles): half the shared memory and tensor memory of a
-// 32 x 32 block, so that more blocks share an SM and one block's staging latency hides
-// behind another's MMAs and stores.
+// Tiles of 16 x 32 e1 pixels (4 MMA tiles of 128 pixels), walked persistently: a block keeps
+// its tensor memory, split weights and mbarrier for all its tiles, and issues the next tile's
+// window loads before it waits for the current tile's MMAs, so that their latency hides behind
+// the wait and the epilogue's stores.  Tile t of the launch is pair t / (gx gy), block row
+// (t mod gx gy) / gx, block column t mod gx; a block takes tiles blockIdx.x, + gridDim.x, ...,
+// skipping those outside their pair (ragged batches).
+__device__ __forceinline__ int enc1_next_tile(const EdgePair* __restrict__ pairs, int t, int gx, int per, int ntiles,
+                                              int BH, int& X0, int& Y0) {
+  for (; t < ntiles; t += (int)gridDim.x) {
+    const int z = t / per, rem = t - z * per, by = rem / gx;
+    const EdgePair* P = pairs + z;
+    X0 = (rem - by * gx) * E1W;
+    Y0 = by * BH;
+    if (X0 < (P->W + 1) / 2 && Y0 < (P->H + 1) / 2) return t;
+  }
+  return ntiles;
+}
+
 template <int C1>
-__global__ void __launch_bounds__(256) enc1_tc(const EdgePair* __restrict__ pairs, const float* __restrict__ W,
-                                               const float* __restrict__ B, int* err, long long spin) {
+__global__ void __launch_bounds__(256, kE1BlocksPerSm)
+    enc1_tc(const EdgePair* __restrict__ pairs, int gx, int gy, int ntiles, const float* __restrict__ W,
+            const float* __restrict__ B, int* err, long long spin) {
   static_assert(C1 == 16 || C1 == 32 || C1 == 64, "enc1 widths");
   constexpr int BH = kE1TcBH, NTILE = kE1Tiles, RPW = BH / 8;  // e1 rows per warp in the A build
   __shared__ float xs[E1Geo<BH>::R][E1C][2];
   __shared__ float T[E1Geo<BH>::CR][E1C];
   extern __shared__ unsigned char e1dyn[];
-  const EdgePair* P = pairs + blockIdx.z;
-  const int H1 = (P->H + 1) / 2, W1 = (P->W + 1) / 2;
-  const int X0 = blockIdx.x * E1W, Y0 = blockIdx.y * BH;
-  if (X0 >= W1 || Y0 >= H1) return;
+  const int per = gx * gy;
+  int X0, Y0;
+  int t = enc1_next_tile(pairs, (int)blockIdx.x, gx, per, ntiles, BH, X0, Y0);
+  if (t >= ntiles) return;  // (uniform over the block)
+  const EdgePair* P = pairs + t / per;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  E1Loads<BH> ld;  // the window's loads go out first: their latency overlaps the set-up below
+  E1Loads<BH> ld;  // the first window's loads go out first: their latency overlaps the set-up below
   if (P->coarse_f) enc1_stage_load<float, BH>(P, P->coarse_f, X0, Y0, ld);
   else enc1_stage_load<int16_t, BH>(P, P->coarse, X0, Y0, ld);
   const uint32_t raw = smem_u32_e(e1dyn), base = (raw + 127u) & ~127u;
@@ -326,135 +345,161 @@ __global__ void __launch_bounds__(256) enc1_tc(const EdgePair* __restrict__ pair
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (P->coarse_f) enc1_stage_finish<float, BH>(P, Y0, ld, xs, T);
-  else enc1_stage_finish<int16_t, BH>(P, Y0, ld, xs, T);
-  // A rows: warp w builds block rows RPW w .. RPW w + RPW - 1 (tile oy / 4, row j = oy % 4);
-  // lane = output column
+  uint32_t tmem = 0, phase = 0;
 #pragma unroll 1
-  for (int jj = 0; jj < RPW; ++jj) {
-    const int oy = RPW * warp + jj, j = oy & 3, tile = oy >> 2;
-    float v[32];
+  for (;;) {
+    // (the previous tile's epilogue has left the A tiles and tensor memory: block barrier below)
+    if (P->coarse_f) enc1_stage_finish<float, BH>(P, Y0, ld, xs, T);
+    else enc1_stage_finish<int16_t, BH>(P, Y0, ld, xs, T);
+    // A rows: warp w builds block rows RPW w .. RPW w + RPW - 1 (tile oy / 4, row j = oy % 4);
+    // lane = output column
+#pragma unroll 1
+    for (int jj = 0; jj < RPW; ++jj) {
+      const int oy = RPW * warp + jj, j = oy & 3, tile = oy >> 2;
+      float v[32];
 #pragma unroll
-    for (int ky = 0; ky < 3; ++ky)
+      for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-      for (int kx = 0; kx < 3; ++kx) {
-        const float2 t = *reinterpret_cast<const float2*>(&xs[2 * oy + ky][2 * lane + kx][0]);
-        const float uh = __bfloat162float(__float2bfloat16_rn(t.y));
-        const int k = 3 * (ky * 3 + kx);
-        v[k] = t.x;
-        v[k + 1] = uh;
-        v[k + 2] = t.y - uh;
-      }
+        for (int kx = 0; kx < 3; ++kx) {
+          const float2 tv = *reinterpret_cast<const float2*>(&xs[2 * oy + ky][2 * lane + kx][0]);
+          const float uh = __bfloat162float(__float2bfloat16_rn(tv.y));
+          const int k = 3 * (ky * 3 + kx);
+          v[k] = tv.x;
+          v[k + 1] = uh;
+          v[k + 2] = tv.y - uh;
+        }
 #pragma unroll
-    for (int k = 27; k < 32; ++k) v[k] = 0.f;
-    const int m = 32 * j + lane;
-    unsigned char* row = g + (size_t)tile * kE1Tile + (m & 7) * 16 + (m >> 3) * 512;
+      for (int k = 27; k < 32; ++k) v[k] = 0.f;
+      const int m = 32 * j + lane;
+      unsigned char* row = g + (size_t)tile * kE1Tile + (m & 7) * 16 + (m >> 3) * 512;
 #pragma unroll
-    for (int kc = 0; kc < 4; ++kc)
-      *reinterpret_cast<uint4*>(row + kc * 128) =
-          make_uint4(pack_bf16x2(v[8 * kc], v[8 * kc + 1]), pack_bf16x2(v[8 * kc + 2], v[8 * kc + 3]),
-                     pack_bf16x2(v[8 * kc + 4], v[8 * kc + 5]), pack_bf16x2(v[8 * kc + 6], v[8 * kc + 7]));
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tslot;
-  if (tid == 0) {
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C1 >> 3) << 17) | ((128u >> 4) << 24);
-#pragma unroll
-    for (int t = 0; t < NTILE; ++t) {
-      const uint64_t a = desc_ns_e(sA + t * kE1Tile, 512);
-      const uint32_t d = tmem + t * C1;
-      // K step of 16 = two core matrices along K = +256 B (+16 in the start field)
-#pragma unroll
-      for (int ks = 0; ks < 2; ++ks) mma_bf16_e(d, a + 16 * ks, desc_ns_e(sBh, 256 * 2) + 16 * ks, idesc, ks);
-#pragma unroll
-      for (int ks = 0; ks < 2; ++ks) mma_bf16_e(d, a + 16 * ks, desc_ns_e(sBl, 256 * 2) + 16 * ks, idesc, 1u);
+      for (int kc = 0; kc < 4; ++kc)
+        *reinterpret_cast<uint4*>(row + kc * 128) =
+            make_uint4(pack_bf16x2(v[8 * kc], v[8 * kc + 1]), pack_bf16x2(v[8 * kc + 2], v[8 * kc + 3]),
+                       pack_bf16x2(v[8 * kc + 4], v[8 * kc + 5]), pack_bf16x2(v[8 * kc + 6], v[8 * kc + 7]));
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
-  }
-  __syncwarp();
-  // lane 0 of each warp waits for the accumulators and tells the warp
-  bool got = lane != 0 || mbar_wait_e(mbar, 0, spin);
-  got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
-  if (!got) {
-    if (lane == 0) atomicCAS(err, 0, 7);
-    // the MMAs may still be running: wait (bounded) before the allocation is released
-    if (lane == 0) mbar_wait_e(mbar, 0, spin > 2000000000LL ? spin : 2000000000LL);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem = *tslot;
+    if (tid == 0) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C1 >> 3) << 17) | ((128u >> 4) << 24);
+#pragma unroll
+      for (int tt = 0; tt < NTILE; ++tt) {
+        const uint64_t a = desc_ns_e(sA + tt * kE1Tile, 512);
+        const uint32_t d = tmem + tt * C1;
+        // K step of 16 = two core matrices along K = +256 B (+16 in the start field)
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) mma_bf16_e(d, a + 16 * ks, desc_ns_e(sBh, 256 * 2) + 16 * ks, idesc, ks);
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) mma_bf16_e(d, a + 16 * ks, desc_ns_e(sBl, 256 * 2) + 16 * ks, idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                   : "memory");
+    }
     __syncwarp();
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (got) {
-    const int q = warp & 3;
+    // the next tile's window loads go out now, ahead of the wait and the stores below
+    int nX0 = 0, nY0 = 0;
+    const int nt = enc1_next_tile(pairs, t + (int)gridDim.x, gx, per, ntiles, BH, nX0, nY0);
+    const EdgePair* nP = pairs + (nt < ntiles ? nt / per : 0);
+    if (nt < ntiles) {
+      if (nP->coarse_f) enc1_stage_load<float, BH>(nP, nP->coarse_f, nX0, nY0, ld);
+      else enc1_stage_load<int16_t, BH>(nP, nP->coarse, nX0, nY0, ld);
+    }
+    // lane 0 of each warp waits for the accumulators and tells the warp
+    bool got = lane != 0 || mbar_wait_e(mbar, phase, spin);
+    got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+    if (!got) {
+      if (lane == 0) atomicCAS(err, 0, 7);
+      // the MMAs may still be running: wait (bounded) before the allocation is released
+      if (lane == 0) mbar_wait_e(mbar, phase, spin > 2000000000LL ? spin : 2000000000LL);
+      __syncwarp();
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (got) {
+      const int q = warp & 3;
+      const int H1 = (P->H + 1) / 2, W1 = (P->W + 1) / 2;
+      // 16 accumulator columns per tensor-memory load, which keeps the registers of the
+      // epilogue low enough for the next window's loads to stay in flight beside it
 #pragma unroll 1
-    for (int t = warp >> 2; t < NTILE; t += 2) {
-      const int Y = Y0 + 4 * t + q, X = X0 + lane;
-      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t * C1);
+      for (int tt = warp >> 2; tt < NTILE; tt += 2) {
+        const int Y = Y0 + 4 * tt + q, X = X0 + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(tt * C1);
+        uint4* sw = reinterpret_cast<uint4*>(g) + warp * 128;
 #pragma unroll
-      for (int c0 = 0; c0 < C1; c0 += 32) {
-        uint32_t r[32];
-        if (C1 >= 32) tmem_ld32_e(taddr + c0, r);
-        else tmem_ld16_e(taddr + c0, r);
-        constexpr int CW = C1 >= 32 ? 32 : C1;
-        if (X < W1 && Y < H1 && P->e1q) {
-          // FP8 form: E4M3 codes of the BF16-rounded output (16 per 16-byte store)
-          uint32_t pk[CW / 4];
+        for (int c0 = 0; c0 < C1; c0 += 16) {
+          uint32_t r[32];
+          tmem_ld16_e(taddr + c0, r);
+          if (P->e1q) {
+            // FP8 form: E4M3 codes of the BF16-rounded output (16 per 16-byte store)
+            uint32_t pk[4];
 #pragma unroll
-          for (int e = 0; e < CW; e += 4) {
-            float q[4];
+            for (int e = 0; e < 16; e += 4) {
+              float qv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-              q[u] = __bfloat162float(__float2bfloat16_rn(fmaxf(__uint_as_float(r[e + u]) + bias_s[c0 + e + u], 0.f)));
-            pk[e / 4] = (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(q[0], q[1]), __NV_SATFINITE, __NV_E4M3) |
-                        ((uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(q[2], q[3]), __NV_SATFINITE, __NV_E4M3) << 16);
+              for (int u = 0; u < 4; ++u)
+                qv[u] = __bfloat162float(
+                    __float2bfloat16_rn(fmaxf(__uint_as_float(r[e + u]) + bias_s[c0 + e + u], 0.f)));
+              pk[e / 4] = (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(qv[0], qv[1]), __NV_SATFINITE, __NV_E4M3) |
+                          ((uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(qv[2], qv[3]), __NV_SATFINITE, __NV_E4M3)
+                           << 16);
+            }
+            if (X < W1 && Y < H1)
+              *reinterpret_cast<uint4*>(P->e1q + ((size_t)Y * W1 + X) * C1 + c0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            continue;
           }
-          uint4* dst = reinterpret_cast<uint4*>(P->e1q + ((size_t)Y * W1 + X) * C1 + c0);
+          uint32_t pk[8];
 #pragma unroll
-          for (int i = 0; i < CW / 16; ++i) dst[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
-        } else if (!P->e1q && CW == 32) {
-          // through a 2 KB stage per warp in the (now free) A tiles: lane = pixel writes its
-          // four 16-byte pieces (piece q at slot q ^ ((pixel >> 1) & 3): conflict-free), then
-          // four lanes per pixel store its 64 bytes, eight pixels (512 bytes) per instruction
-          uint32_t pk[16];
-#pragma unroll
-          for (int e = 0; e < 32; e += 2) {
+          for (int e = 0; e < 16; e += 2) {
             const float2 v = __fadd2_rn(make_float2(__uint_as_float(r[e]), __uint_as_float(r[e + 1])),
                                         make_float2(bias_s[c0 + e], bias_s[c0 + e + 1]));
             const __nv_bfloat162 h = __hmax2(__floats2bfloat162_rn(v.x, v.y), __float2bfloat162_rn(0.f));
             pk[e / 2] = *reinterpret_cast<const uint32_t*>(&h);
           }
-          uint4* sw = reinterpret_cast<uint4*>(g) + warp * 128;
-#pragma unroll
-          for (int qq = 0; qq < 4; ++qq)
-            sw[lane * 4 + (qq ^ ((lane >> 1) & 3))] = make_uint4(pk[4 * qq], pk[4 * qq + 1], pk[4 * qq + 2], pk[4 * qq + 3]);
-          __syncwarp();
-#pragma unroll
-          for (int s8 = 0; s8 < 4; ++s8) {
-            const int pp = 8 * s8 + (lane >> 2), qq = lane & 3;
-            const uint4 v = sw[pp * 4 + (qq ^ ((pp >> 1) & 3))];
-            if (X0 + pp < W1 && Y < H1)
-              *reinterpret_cast<uint4*>(P->e1 + ((size_t)Y * W1 + X0 + pp) * C1 + c0 + 8 * qq) = v;
+          if (C1 == 16) {
+            if (X < W1 && Y < H1) {
+              uint4* dst = reinterpret_cast<uint4*>(P->e1 + ((size_t)Y * W1 + X) * C1);
+              dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+              dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+            continue;
           }
-          __syncwarp();
-        } else if (X < W1 && Y < H1) {
-          uint32_t pk[CW / 2];
+          // through a 2 KB stage per warp in the (now free) A tiles: lane = pixel writes the
+          // four 16-byte pieces of a 32-channel group (piece qq at slot qq ^ ((pixel >> 1) & 3):
+          // conflict-free), two per 16-column load; then four lanes per pixel store its
+          // 64 bytes, eight pixels (512 bytes) per instruction
+          const int h = (c0 >> 4) & 1;
 #pragma unroll
-          for (int e = 0; e < CW; e += 2) {
-            const float2 v = __fadd2_rn(make_float2(__uint_as_float(r[e]), __uint_as_float(r[e + 1])),
-                                        make_float2(bias_s[c0 + e], bias_s[c0 + e + 1]));
-            const __nv_bfloat162 h = __hmax2(__floats2bfloat162_rn(v.x, v.y), __float2bfloat162_rn(0.f));
-            pk[e / 2] = *reinterpret_cast<const uint32_t*>(&h);
+          for (int u = 0; u < 2; ++u) {
+            const int qq = 2 * h + u;
+            sw[lane * 4 + (qq ^ ((lane >> 1) & 3))] = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
           }
-          uint4* dst = reinterpret_cast<uint4*>(P->e1 + ((size_t)Y * W1 + X) * C1 + c0);
+          if (h == 1) {
+            __syncwarp();
+            const int cg = c0 - 16;
 #pragma unroll
-          for (int i = 0; i < CW / 8; ++i) dst[i] = make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+            for (int s8 = 0; s8 < 4; ++s8) {
+              const int pp = 8 * s8 + (lane >> 2), qq = lane & 3;
+              const uint4 v = sw[pp * 4 + (qq ^ ((pp >> 1) & 3))];
+              if (X0 + pp < W1 && Y < H1)
+                *reinterpret_cast<uint4*>(P->e1 + ((size_t)Y * W1 + X0 + pp) * C1 + cg + 8 * qq) = v;
+            }
+            __syncwarp();
+          }
         }
       }
     }
+    // tensor memory read and the stage drained before the next tile's A build and MMAs
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    const int failed = __syncthreads_or(got ? 0 : 1);
+    phase ^= 1u;
+    if (failed || nt >= ntiles) break;
+    t = nt;
+    P = nP;
+    X0 = nX0;
+    Y0 = nY0;
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NTILE * C1));
 }
 
@@ -963,22 +1008,39 @@ cudaError_t launch_bf16_to_f32(const bf16* a, float* b, size_t n, cudaStream_t s
   return cudaGetLastError();
 }
 
+// Persistent launch: three blocks per SM (the register bound of the kernel and its shared
+// memory under the largest carveout allow three; the occupancy query, which takes the default
+// carveout, reports one), two for C1 = 64 (the 512 tensor-memory columns of an SM), never more
+// blocks than tiles.
+constexpr size_t kE1StaticSmem = sizeof(float) * (E1Geo<kE1TcBH>::R * E1C * 2 + E1Geo<kE1TcBH>::CR * E1C);
+static_assert(kE1BlocksPerSm * (enc1_tc_smem(64) + kE1StaticSmem + 1024) <= 228 * 1024,
+              "three enc1 blocks must fit the shared memory of an SM");
 template <int C1>
-static cudaError_t run_enc1_tc(const EdgePair* pairs, dim3 grid, const float* W, const float* B, int* err, long long spin,
-                               cudaStream_t st) {
+static cudaError_t run_enc1_tc(const EdgePair* pairs, int n, int maxW1, int maxH1, const float* W, const float* B,
+                               int* err, long long spin, cudaStream_t st) {
   const size_t smem = enc1_tc_smem(C1);
   cudaError_t e = cudaFuncSetAttribute(enc1_tc<C1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  enc1_tc<C1><<<grid, 256, smem, st>>>(pairs, W, B, err, spin);
+  e = cudaFuncSetAttribute(enc1_tc<C1>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int per_sm = std::min(kE1BlocksPerSm, 512 / (kE1Tiles * C1));
+  const int gx = (maxW1 + E1W - 1) / E1W, gy = (maxH1 + kE1TcBH - 1) / kE1TcBH;
+  const long long tiles = (long long)gx * gy * n;
+  if (tiles <= 0) return cudaSuccess;
+  if (tiles > INT_MAX) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<long long>(tiles, (long long)nsm * per_sm);
+  enc1_tc<C1><<<grid, 256, smem, st>>>(pairs, gx, gy, (int)tiles, W, B, err, spin);
   return cudaGetLastError();
 }
 
 cudaError_t launch_edge_enc1(const EdgePair* pairs, int n, int maxW1, int maxH1, const float* W, const float* B, int C1,
                              int* err, long long spin, bool tensor, cudaStream_t st) {
-  const dim3 tgrid((maxW1 + E1W - 1) / E1W, (maxH1 + kE1TcBH - 1) / kE1TcBH, n);
-  if (tensor && C1 == 32) return run_enc1_tc<32>(pairs, tgrid, W, B, err, spin, st);
-  if (tensor && C1 == 16) return run_enc1_tc<16>(pairs, tgrid, W, B, err, spin, st);
-  if (tensor && C1 == 64) return run_enc1_tc<64>(pairs, tgrid, W, B, err, spin, st);
+  if (tensor && C1 == 32) return run_enc1_tc<32>(pairs, n, maxW1, maxH1, W, B, err, spin, st);
+  if (tensor && C1 == 16) return run_enc1_tc<16>(pairs, n, maxW1, maxH1, W, B, err, spin, st);
+  if (tensor && C1 == 64) return run_enc1_tc<64>(pairs, n, maxW1, maxH1, W, B, err, spin, st);
   dim3 grid((maxW1 + E1W - 1) / E1W, (maxH1 + E1H - 1) / E1H, n);
   edge_enc1<<<grid, 256, sizeof(float) * 19 * C1, st>>>(pairs, W, B, C1);
   return cudaGetLastError();
